@@ -1,0 +1,256 @@
+"""ctypes wrapper around the C oracle (``spvar_oracle.c``).
+
+TEST INFRASTRUCTURE ONLY -- see the package docstring.  Arrays are numpy;
+every function mirrors one oracle entry point and cites the step it follows.
+"""
+import ctypes
+import dataclasses
+
+import numpy as np
+
+from . import build as _build
+
+_lib = None
+
+i32p = ctypes.POINTER(ctypes.c_int32)
+i64p = ctypes.POINTER(ctypes.c_int64)
+u32p = ctypes.POINTER(ctypes.c_uint32)
+i8p = ctypes.POINTER(ctypes.c_int8)
+f64p = ctypes.POINTER(ctypes.c_double)
+
+
+class OrParams(ctypes.Structure):
+    _fields_ = [
+        ("num_starts", ctypes.c_int32),
+        ("fixing_sample_size", ctypes.c_int32),
+        ("solving_sample_size", ctypes.c_int32),
+        ("num_sweeps", ctypes.c_int32),
+        ("elite_threshold", ctypes.c_double),
+        ("fix_num", ctypes.c_int32),
+        ("fix_den", ctypes.c_int32),
+        ("iterate", ctypes.c_int32),
+        ("max_fix_phases", ctypes.c_int32),
+        ("canon", ctypes.c_int32),
+    ]
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = ctypes.CDLL(path)
+        L.or_philox4x32_10.argtypes = [u32p, u32p, u32p]
+        L.or_csr_from_edges.argtypes = [ctypes.c_int32, ctypes.c_int64, i32p, i32p, i32p, i32p, i32p, i32p]
+        L.or_csr_from_edges.restype = ctypes.c_int
+        L.or_colour.argtypes = [ctypes.c_int32, i32p, i32p, i32p]
+        L.or_colour.restype = ctypes.c_int32
+        L.or_dmax.argtypes = [ctypes.c_int32, i32p, i32p, i32p]
+        L.or_dmax.restype = ctypes.c_int64
+        L.or_thresholds.argtypes = [ctypes.c_int32, f64p, ctypes.c_int32, ctypes.c_int32, u32p]
+        L.or_beta_geometric.argtypes = [ctypes.c_int32, ctypes.c_double, ctypes.c_double, f64p]
+        L.or_energy.argtypes = [ctypes.c_int32, i32p, i32p, i32p, i32p, i8p]
+        L.or_energy.restype = ctypes.c_int64
+        L.or_sample.argtypes = [ctypes.c_int32, i32p, i32p, i32p, i32p, i32p, ctypes.c_int32,
+                                ctypes.c_int32, u32p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64,
+                                ctypes.c_uint32, ctypes.c_uint32, i8p, i64p, i64p]
+        L.or_sample.restype = ctypes.c_int
+        L.or_elite_count.argtypes = [ctypes.c_double, ctypes.c_int32]
+        L.or_elite_count.restype = ctypes.c_int32
+        L.or_elite.argtypes = [ctypes.c_int32, i64p, ctypes.c_int32, i32p]
+        L.or_persistence.argtypes = [ctypes.c_int32, i32p, ctypes.c_int32, i8p, i64p, ctypes.c_int32,
+                                     ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, i32p, i8p, i32p]
+        L.or_persistence.restype = ctypes.c_int32
+        L.or_reduce.argtypes = [ctypes.c_int32, i32p, i32p, i32p, i32p, ctypes.c_int64, i32p, i8p,
+                                i32p, i32p, i32p, i32p, i32p, i64p, i32p, i32p]
+        L.or_reduce.restype = ctypes.c_int
+        L.or_solve.argtypes = [ctypes.c_int32, i32p, i32p, i32p, i32p, ctypes.c_int64,
+                               ctypes.POINTER(OrParams), u32p, ctypes.c_int32, ctypes.c_uint64,
+                               i64p, i32p, i32p, i32p, i8p, i64p, i8p]
+        L.or_solve.restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _p(a, t):
+    return a.ctypes.data_as(t)
+
+
+def _c(a, dtype):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+# -- Philox4x32-10 ---------------------------------------------------------
+def philox4x32_10(ctr, key):
+    """One Philox4x32-10 block: 4 counter words, 2 key words -> 4 words."""
+    c = _c(ctr, np.uint32)
+    k = _c(key, np.uint32)
+    out = np.zeros(4, np.uint32)
+    lib().or_philox4x32_10(_p(c, u32p), _p(k, u32p), _p(out, u32p))
+    return out
+
+
+# -- problem ---------------------------------------------------------------
+@dataclasses.dataclass
+class Csr:
+    n: int
+    row_ptr: np.ndarray
+    col: np.ndarray
+    val: np.ndarray
+    h: np.ndarray
+    offset: int = 0
+    scale: int = 1
+
+    @property
+    def nnz(self):
+        return int(self.row_ptr[-1])
+
+
+def csr_from_edges(n, ei, ej, J, h, offset=0, scale=1):
+    """Edge list (i != j, each pair once) -> symmetric CSR (Sec. I problem)."""
+    ei = _c(ei, np.int32); ej = _c(ej, np.int32); J = _c(J, np.int32)
+    m = len(ei)
+    rp = np.zeros(n + 1, np.int32)
+    col = np.zeros(max(2 * m, 1), np.int32)
+    val = np.zeros(max(2 * m, 1), np.int32)
+    rc = lib().or_csr_from_edges(n, m, _p(ei, i32p), _p(ej, i32p), _p(J, i32p),
+                                 _p(rp, i32p), _p(col, i32p), _p(val, i32p))
+    if rc != 0:
+        raise ValueError("invalid edge list")
+    return Csr(n, rp, col[:2 * m].copy(), val[:2 * m].copy(), _c(h, np.int32).copy(), int(offset), int(scale))
+
+
+def colour(p: Csr):
+    c = np.zeros(max(p.n, 1), np.int32)
+    ncol = lib().or_colour(p.n, _p(p.row_ptr, i32p), _p(_c(p.col, np.int32), i32p), _p(c, i32p))
+    return c[:p.n].copy(), int(ncol)
+
+
+def dmax(p: Csr):
+    return int(lib().or_dmax(p.n, _p(p.row_ptr, i32p), _p(_c(p.val, np.int32), i32p), _p(p.h, i32p)))
+
+
+def beta_geometric(T, beta0, beta1):
+    b = np.zeros(T, np.float64)
+    lib().or_beta_geometric(T, beta0, beta1, _p(b, f64p))
+    return b
+
+
+def thresholds(beta, dmax_, scale=1):
+    beta = _c(beta, np.float64)
+    T = len(beta)
+    thr = np.zeros((T, dmax_ + 1), np.uint32)
+    lib().or_thresholds(T, _p(beta, f64p), dmax_, scale, _p(thr, u32p))
+    return thr
+
+
+def energy(p: Csr, s):
+    s = _c(s, np.int8)
+    return int(lib().or_energy(p.n, _p(p.row_ptr, i32p), _p(_c(p.col, np.int32), i32p),
+                               _p(_c(p.val, np.int32), i32p), _p(p.h, i32p), _p(s, i8p)))
+
+
+def sample(p: Csr, thr, S, seed, start=0, phase=0, colours=None, check_incremental=False, r0=0):
+    """SA sample (Sec. III procedure; sampler of the paper's SA runs), replicas r0 .. r0+S-1.
+
+    Returns (spins int8 [S, n] of +-1, energies int64 [S] without offset,
+    largest incremental-vs-recomputed energy difference or None)."""
+    if colours is None:
+        colours = colour(p)
+    c, ncol = colours
+    thr = _c(thr, np.uint32)
+    T = thr.shape[0]
+    dm = thr.shape[1] - 1
+    spins = np.zeros((max(S, 1), max(p.n, 1)), np.int8)
+    e = np.zeros(max(S, 1), np.int64)
+    err = np.zeros(1, np.int64)
+    c = _c(c, np.int32) if p.n else np.zeros(1, np.int32)
+    rc = lib().or_sample(p.n, _p(p.row_ptr, i32p), _p(_c(p.col, np.int32), i32p),
+                         _p(_c(p.val, np.int32), i32p), _p(p.h, i32p), _p(c, i32p), ncol,
+                         T, _p(thr, u32p), dm, r0, S, seed, start, phase,
+                         _p(spins, i8p), _p(e, i64p), _p(err, i64p) if check_incremental else None)
+    if rc != 0:
+        raise ValueError("or_sample failed: %d" % rc)
+    return spins[:S, :p.n].copy(), e[:S].copy(), (int(err[0]) if check_incremental else None)
+
+
+def elite_count(elite, S):
+    return int(lib().or_elite_count(float(elite), int(S)))
+
+
+def elite(e, k):
+    e = _c(e, np.int64)
+    idx = np.zeros(max(k, 1), np.int32)
+    lib().or_elite(len(e), _p(e, i64p), k, _p(idx, i32p))
+    return idx[:k].copy()
+
+
+def persistence(p: Csr, spins, e, k, fix_num=1, fix_den=1, canon=0):
+    """Alg. 1 persistence step.  Returns (counts, fixed, nfixed, rho)."""
+    spins = _c(spins, np.int8)
+    e = _c(e, np.int64)
+    S = len(e)
+    cnt = np.zeros(max(p.n, 1), np.int32)
+    fixed = np.zeros(max(p.n, 1), np.int8)
+    rho = np.zeros(1, np.int32)
+    nf = lib().or_persistence(p.n, _p(p.row_ptr, i32p), S, _p(spins, i8p), _p(e, i64p), k,
+                              fix_num, fix_den, canon, _p(cnt, i32p), _p(fixed, i8p), _p(rho, i32p))
+    return cnt[:p.n].copy(), fixed[:p.n].copy(), int(nf), int(rho[0])
+
+
+def reduce(p: Csr, fixed, colours=None):
+    """Alg. 1 update of J and h.  Returns (reduced Csr, colours', old_of_new)."""
+    if colours is None:
+        colours = colour(p)
+    c = _c(colours[0], np.int32) if p.n else np.zeros(1, np.int32)
+    fixed = _c(fixed, np.int8) if p.n else np.zeros(1, np.int8)
+    n_out = np.zeros(1, np.int32)
+    rp = np.zeros(p.n + 1, np.int32)
+    col = np.zeros(max(p.nnz, 1), np.int32)
+    val = np.zeros(max(p.nnz, 1), np.int32)
+    h = np.zeros(max(p.n, 1), np.int32)
+    off = np.zeros(1, np.int64)
+    co = np.zeros(max(p.n, 1), np.int32)
+    oon = np.zeros(max(p.n, 1), np.int32)
+    lib().or_reduce(p.n, _p(p.row_ptr, i32p), _p(_c(p.col, np.int32), i32p), _p(_c(p.val, np.int32), i32p),
+                    _p(p.h, i32p), p.offset, _p(c, i32p), _p(fixed, i8p), _p(n_out, i32p), _p(rp, i32p),
+                    _p(col, i32p), _p(val, i32p), _p(h, i32p), _p(off, i64p), _p(co, i32p), _p(oon, i32p))
+    m = int(n_out[0])
+    nnz = int(rp[m])
+    red = Csr(m, rp[:m + 1].copy(), col[:nnz].copy(), val[:nnz].copy(), h[:m].copy(), int(off[0]), p.scale)
+    return red, (co[:m].copy(), colours[1]), oon[:m].copy()
+
+
+@dataclasses.dataclass
+class SolveResult:
+    energies: np.ndarray   # [starts, P, Smax]
+    counts: np.ndarray     # [starts, P]
+    nfree: np.ndarray      # [starts, P]
+    nphases: np.ndarray    # [starts]
+    fixed: np.ndarray      # [starts, n0]
+    best_e: np.ndarray     # [starts]
+    best_state: np.ndarray # [starts, n0]
+
+
+def solve(p: Csr, thr, seed, num_starts, fixing_sample_size, solving_sample_size, elite_threshold,
+          fix_num=1, fix_den=1, iterate=False, max_fix_phases=1, canon=-1):
+    """Multi-start SPVAR (Alg. 2) with SA; thr is the original problem's table."""
+    thr = _c(thr, np.uint32)
+    prm = OrParams(num_starts, fixing_sample_size, solving_sample_size, thr.shape[0], float(elite_threshold),
+                   fix_num, fix_den, 1 if iterate else 0, max_fix_phases, canon)
+    P = max_fix_phases + 1
+    Smax = max(fixing_sample_size, solving_sample_size)
+    n0 = p.n
+    en = np.zeros((num_starts, P, Smax), np.int64)
+    counts = np.zeros((num_starts, P), np.int32)
+    nfree = np.zeros((num_starts, P), np.int32)
+    nph = np.zeros(num_starts, np.int32)
+    fixed = np.zeros((num_starts, max(n0, 1)), np.int8)
+    best_e = np.zeros(num_starts, np.int64)
+    best_state = np.zeros((num_starts, max(n0, 1)), np.int8)
+    rc = lib().or_solve(n0, _p(p.row_ptr, i32p), _p(_c(p.col, np.int32), i32p), _p(_c(p.val, np.int32), i32p),
+                        _p(p.h, i32p), p.offset, ctypes.byref(prm), _p(thr, u32p), thr.shape[1] - 1, seed,
+                        _p(en, i64p), _p(counts, i32p), _p(nfree, i32p), _p(nph, i32p), _p(fixed, i8p),
+                        _p(best_e, i64p), _p(best_state, i8p))
+    if rc != 0:
+        raise ValueError("or_solve failed: %d" % rc)
+    return SolveResult(en, counts, nfree, nph, fixed[:, :n0], best_e, best_state[:, :n0])

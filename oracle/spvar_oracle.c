@@ -1,0 +1,495 @@
+/*
+ * spvar_oracle.c -- TEST INFRASTRUCTURE ONLY (see spvar_oracle.h).
+ *
+ * A plain single-threaded restatement of Alg. 1 (SPVAR) and Alg. 2
+ * (Multi-start SPVAR) with simulated annealing as the sampler.  Every loop
+ * follows the order the method states; nothing is blocked, fused or
+ * reordered.  It is deliberately slow and shares nothing with the CUDA
+ * library: tests compare the two element by element.
+ */
+#include "spvar_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ---------------------------------------------------------------------- */
+/* Philox4x32-10 (Salmon et al., SC'11): ten rounds of two 32x32->64       */
+/* multiplies with a Weyl-sequence key schedule.                            */
+/* ---------------------------------------------------------------------- */
+#define PHILOX_M0 0xD2511F53u
+#define PHILOX_M1 0xCD9E8D57u
+#define PHILOX_W0 0x9E3779B9u
+#define PHILOX_W1 0xBB67AE85u
+
+void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) {
+            k0 += PHILOX_W0;
+            k1 += PHILOX_W1;
+        }
+        uint64_t p0 = (uint64_t)PHILOX_M0 * (uint64_t)c0;
+        uint64_t p1 = (uint64_t)PHILOX_M1 * (uint64_t)c2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t n0 = hi1 ^ c1 ^ k0;
+        uint32_t n1 = lo1;
+        uint32_t n2 = hi0 ^ c3 ^ k1;
+        uint32_t n3 = lo0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Problem construction                                                     */
+/* ---------------------------------------------------------------------- */
+int or_csr_from_edges(int32_t n, int64_t m, const int32_t *ei, const int32_t *ej,
+                      const int32_t *J, int32_t *row_ptr, int32_t *col, int32_t *val)
+{
+    int64_t *deg = (int64_t *)calloc((size_t)n + 1, sizeof(int64_t));
+    if (!deg) return -1;
+    for (int64_t e = 0; e < m; ++e) {
+        if (ei[e] < 0 || ei[e] >= n || ej[e] < 0 || ej[e] >= n || ei[e] == ej[e]) {
+            free(deg);
+            return -1;
+        }
+        deg[ei[e]]++;
+        deg[ej[e]]++;
+    }
+    row_ptr[0] = 0;
+    for (int32_t i = 0; i < n; ++i) row_ptr[i + 1] = (int32_t)(row_ptr[i] + deg[i]);
+    /* place entries, then sort each row by column (insertion sort: rows are short) */
+    int64_t *fill = (int64_t *)calloc((size_t)n + 1, sizeof(int64_t));
+    if (!fill) { free(deg); return -1; }
+    for (int64_t e = 0; e < m; ++e) {
+        int32_t a = ei[e], b = ej[e];
+        int64_t pa = row_ptr[a] + fill[a]++;
+        col[pa] = b; val[pa] = J[e];
+        int64_t pb = row_ptr[b] + fill[b]++;
+        col[pb] = a; val[pb] = J[e];
+    }
+    int rc = 0;
+    for (int32_t i = 0; i < n && rc == 0; ++i) {
+        for (int32_t p = row_ptr[i] + 1; p < row_ptr[i + 1]; ++p) {
+            int32_t c = col[p], v = val[p];
+            int32_t q = p - 1;
+            while (q >= row_ptr[i] && col[q] > c) {
+                col[q + 1] = col[q];
+                val[q + 1] = val[q];
+                --q;
+            }
+            col[q + 1] = c;
+            val[q + 1] = v;
+        }
+        for (int32_t p = row_ptr[i] + 1; p < row_ptr[i + 1]; ++p)
+            if (col[p] == col[p - 1]) rc = -1; /* duplicate pair */
+    }
+    free(deg);
+    free(fill);
+    return rc;
+}
+
+int32_t or_colour(int32_t n, const int32_t *row_ptr, const int32_t *col, int32_t *colour)
+{
+    if (n == 0) return 0;
+    /* bipartite attempt: BFS from the lowest unvisited vertex, colour = parity */
+    int32_t *queue = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    for (int32_t i = 0; i < n; ++i) colour[i] = -1;
+    for (int32_t root = 0; root < n; ++root) {
+        if (colour[root] >= 0) continue;
+        int32_t head = 0, tail = 0;
+        colour[root] = 0;
+        queue[tail++] = root;
+        while (head < tail) {
+            int32_t v = queue[head++];
+            for (int32_t p = row_ptr[v]; p < row_ptr[v + 1]; ++p) {
+                int32_t u = col[p];
+                if (colour[u] < 0) {
+                    colour[u] = 1 - colour[v];
+                    queue[tail++] = u;
+                }
+            }
+        }
+    }
+    free(queue);
+    int bipartite = 1;
+    int32_t used = 1;
+    for (int32_t v = 0; v < n; ++v) {
+        if (colour[v] == 1) used = 2;
+        for (int32_t p = row_ptr[v]; p < row_ptr[v + 1]; ++p)
+            if (colour[col[p]] == colour[v]) bipartite = 0;
+    }
+    if (bipartite) return used;
+
+    /* first-fit greedy in index order: smallest colour no lower-index
+       neighbour already has */
+    int32_t *seen = (int32_t *)malloc(sizeof(int32_t) * ((size_t)n + 1));
+    for (int32_t c = 0; c <= n; ++c) seen[c] = -1;
+    int32_t ncol = 0;
+    for (int32_t v = 0; v < n; ++v) {
+        for (int32_t p = row_ptr[v]; p < row_ptr[v + 1]; ++p) {
+            int32_t u = col[p];
+            if (u < v) seen[colour[u]] = v;
+        }
+        int32_t c = 0;
+        while (seen[c] == v) ++c;
+        colour[v] = c;
+        if (c + 1 > ncol) ncol = c + 1;
+    }
+    free(seen);
+    return ncol;
+}
+
+int64_t or_dmax(int32_t n, const int32_t *row_ptr, const int32_t *val, const int32_t *h)
+{
+    int64_t best = 0;
+    for (int32_t i = 0; i < n; ++i) {
+        int64_t s = llabs((long long)h[i]);
+        for (int32_t p = row_ptr[i]; p < row_ptr[i + 1]; ++p) s += llabs((long long)val[p]);
+        if (s > best) best = s;
+    }
+    return 2 * best;
+}
+
+void or_thresholds(int32_t T, const double *beta, int32_t dmax, int32_t scale, uint32_t *thr)
+{
+    for (int32_t t = 0; t < T; ++t) {
+        for (int32_t d = 0; d <= dmax; ++d) {
+            double x = ldexp(exp(-beta[t] * (double)d / (double)scale), 32);
+            double f = floor(x);
+            uint32_t v = (f >= 4294967295.0) ? 0xFFFFFFFFu : (uint32_t)f;
+            thr[(int64_t)t * (dmax + 1) + d] = v;
+        }
+    }
+}
+
+void or_beta_geometric(int32_t T, double beta0, double beta1, double *beta)
+{
+    for (int32_t t = 0; t < T; ++t) {
+        if (T == 1) { beta[t] = beta0; continue; }
+        beta[t] = beta0 * pow(beta1 / beta0, (double)t / (double)(T - 1));
+    }
+}
+
+int64_t or_energy(int32_t n, const int32_t *row_ptr, const int32_t *col,
+                  const int32_t *val, const int32_t *h, const int8_t *s)
+{
+    int64_t e = 0;
+    for (int32_t i = 0; i < n; ++i) {
+        e += (int64_t)h[i] * s[i];
+        for (int32_t p = row_ptr[i]; p < row_ptr[i + 1]; ++p)
+            if (col[p] > i) e += (int64_t)val[p] * s[i] * s[col[p]];
+    }
+    return e;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Simulated annealing                                                      */
+/* ---------------------------------------------------------------------- */
+#define SWEEP_BITS 20u
+#define INIT_SLOT ((1u << SWEEP_BITS) - 1u)
+
+static uint32_t rng_word(uint64_t seed, uint32_t start, uint32_t phase, uint32_t slot,
+                         int32_t spin, int32_t replica)
+{
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t ctr[4] = {(uint32_t)spin, (phase << SWEEP_BITS) + slot, (uint32_t)replica >> 2, start};
+    uint32_t out[4];
+    or_philox4x32_10(ctr, key, out);
+    return out[replica & 3];
+}
+
+int or_sample(int32_t n, const int32_t *row_ptr, const int32_t *col, const int32_t *val,
+              const int32_t *h, const int32_t *colour, int32_t ncol,
+              int32_t T, const uint32_t *thr, int32_t dmax,
+              int32_t r0, int32_t S, uint64_t seed, uint32_t start, uint32_t phase,
+              int8_t *spins, int64_t *e, int64_t *incr_err)
+{
+    if (T < 0 || (uint32_t)T >= INIT_SLOT || phase >= (1u << 12) || S < 0 || r0 < 0) return -1;
+    /* sweep order: colour classes in increasing colour, index ascending */
+    int32_t *order = (int32_t *)malloc(sizeof(int32_t) * ((size_t)n + 1));
+    int32_t m = 0;
+    for (int32_t c = 0; c < ncol; ++c)
+        for (int32_t i = 0; i < n; ++i)
+            if (colour[i] == c) order[m++] = i;
+    if (m != n) { free(order); return -1; }
+    int64_t worst = 0;
+    int rc = 0;
+    for (int32_t row = 0; row < S && rc == 0; ++row) {
+        const int32_t r = r0 + row; /* replica index */
+        int8_t *s = spins + (int64_t)row * n;
+        for (int32_t i = 0; i < n; ++i)
+            s[i] = (rng_word(seed, start, phase, INIT_SLOT, i, r) >> 31) ? 1 : -1;
+        int64_t E = or_energy(n, row_ptr, col, val, h, s);
+        for (int32_t t = 0; t < T && rc == 0; ++t) {
+            const uint32_t *row = thr + (int64_t)t * (dmax + 1);
+            for (int32_t q = 0; q < n; ++q) {
+                int32_t i = order[q];
+                int64_t f = h[i];
+                for (int32_t p = row_ptr[i]; p < row_ptr[i + 1]; ++p) f += (int64_t)val[p] * s[col[p]];
+                int64_t dE = -2 * (int64_t)s[i] * f;
+                uint32_t u = rng_word(seed, start, phase, (uint32_t)t, i, r);
+                int accept;
+                if (dE <= 0) {
+                    accept = 1;
+                } else {
+                    if (dE > dmax) { rc = -2; break; }
+                    accept = u < row[dE];
+                }
+                if (accept) {
+                    s[i] = (int8_t)-s[i];
+                    E += dE;
+                }
+            }
+            if (incr_err) {
+                int64_t Er = or_energy(n, row_ptr, col, val, h, s);
+                int64_t d = llabs((long long)(Er - E));
+                if (d > worst) worst = d;
+            }
+        }
+        e[row] = E;
+    }
+    if (incr_err) *incr_err = worst;
+    free(order);
+    return rc;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Persistence (Alg. 1)                                                     */
+/* ---------------------------------------------------------------------- */
+int32_t or_elite_count(double elite, int32_t S)
+{
+    double x = ceil(elite * (double)S);
+    int32_t k = (x >= (double)S) ? S : (int32_t)x;
+    if (k < 1) k = 1;
+    if (k > S) k = S;
+    return k;
+}
+
+static const int64_t *g_sort_e; /* single-threaded oracle: plain qsort context */
+static int cmp_energy_index(const void *a, const void *b)
+{
+    int32_t x = *(const int32_t *)a, y = *(const int32_t *)b;
+    if (g_sort_e[x] != g_sort_e[y]) return g_sort_e[x] < g_sort_e[y] ? -1 : 1;
+    return x < y ? -1 : (x > y ? 1 : 0);
+}
+
+void or_elite(int32_t S, const int64_t *e, int32_t k, int32_t *idx)
+{
+    int32_t *all = (int32_t *)malloc(sizeof(int32_t) * ((size_t)S + 1));
+    for (int32_t r = 0; r < S; ++r) all[r] = r;
+    g_sort_e = e;
+    qsort(all, (size_t)S, sizeof(int32_t), cmp_energy_index);
+    for (int32_t q = 0; q < k; ++q) idx[q] = all[q];
+    free(all);
+}
+
+int32_t or_persistence(int32_t n, const int32_t *row_ptr, int32_t S, const int8_t *spins,
+                       const int64_t *e, int32_t k, int32_t fix_num, int32_t fix_den,
+                       int32_t canon, int32_t *cnt, int8_t *fixed, int32_t *rho_out)
+{
+    int32_t *elite = (int32_t *)malloc(sizeof(int32_t) * ((size_t)k + 1));
+    or_elite(S, e, k, elite);
+    int32_t rho = -1;
+    if (canon && n > 0) {
+        int32_t bestdeg = -1;
+        for (int32_t i = 0; i < n; ++i) {
+            int32_t d = row_ptr[i + 1] - row_ptr[i];
+            if (d > bestdeg) { bestdeg = d; rho = i; }
+        }
+    }
+    for (int32_t i = 0; i < n; ++i) cnt[i] = 0;
+    for (int32_t q = 0; q < k; ++q) {
+        const int8_t *s = spins + (int64_t)elite[q] * n;
+        int32_t sign = (rho >= 0) ? s[rho] : 1; /* multiply the row by s_rho */
+        for (int32_t i = 0; i < n; ++i)
+            if (s[i] * sign > 0) cnt[i]++;
+    }
+    int32_t nfixed = 0;
+    for (int32_t i = 0; i < n; ++i) {
+        int64_t diff = 2 * (int64_t)cnt[i] - k; /* k * mean of s_i over the elite */
+        int8_t v = 0;
+        if (diff > 0 && (int64_t)fix_den * diff >= (int64_t)fix_num * k) v = 1;
+        if (diff < 0 && (int64_t)fix_den * (-diff) >= (int64_t)fix_num * k) v = -1;
+        fixed[i] = v;
+        if (v) nfixed++;
+    }
+    if (rho_out) *rho_out = rho;
+    free(elite);
+    return nfixed;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Fold and compact (Alg. 1, update of J and h)                            */
+/* ---------------------------------------------------------------------- */
+int or_reduce(int32_t n, const int32_t *row_ptr, const int32_t *col, const int32_t *val,
+              const int32_t *h, int64_t offset, const int32_t *colour, const int8_t *fixed,
+              int32_t *n_out, int32_t *row_ptr_out, int32_t *col_out, int32_t *val_out,
+              int32_t *h_out, int64_t *offset_out, int32_t *colour_out, int32_t *old_of_new)
+{
+    int32_t *new_of_old = (int32_t *)malloc(sizeof(int32_t) * ((size_t)n + 1));
+    int32_t m = 0;
+    for (int32_t i = 0; i < n; ++i) {
+        if (fixed[i] == 0) {
+            new_of_old[i] = m;
+            old_of_new[m] = i;
+            ++m;
+        } else {
+            new_of_old[i] = -1;
+        }
+    }
+    /* constant: bias of fixed spins, couplers with both ends fixed (i<j once) */
+    int64_t off = offset;
+    for (int32_t i = 0; i < n; ++i) {
+        if (fixed[i] == 0) continue;
+        off += (int64_t)h[i] * fixed[i];
+        for (int32_t p = row_ptr[i]; p < row_ptr[i + 1]; ++p) {
+            int32_t j = col[p];
+            if (j > i && fixed[j] != 0) off += (int64_t)val[p] * fixed[i] * fixed[j];
+        }
+    }
+    /* fields and free-free couplers, in the old order */
+    int32_t nnz = 0;
+    row_ptr_out[0] = 0;
+    for (int32_t a = 0; a < m; ++a) {
+        int32_t i = old_of_new[a];
+        int64_t f = h[i];
+        for (int32_t p = row_ptr[i]; p < row_ptr[i + 1]; ++p) {
+            int32_t j = col[p];
+            if (fixed[j] != 0) {
+                f += (int64_t)val[p] * fixed[j];
+            } else {
+                col_out[nnz] = new_of_old[j];
+                val_out[nnz] = val[p];
+                ++nnz;
+            }
+        }
+        h_out[a] = (int32_t)f;
+        colour_out[a] = colour[i];
+        row_ptr_out[a + 1] = nnz;
+    }
+    *n_out = m;
+    *offset_out = off;
+    free(new_of_old);
+    return 0;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Multi-start SPVAR (Alg. 2)                                               */
+/* ---------------------------------------------------------------------- */
+static int all_zero(int32_t n, const int32_t *h)
+{
+    for (int32_t i = 0; i < n; ++i)
+        if (h[i] != 0) return 0;
+    return 1;
+}
+
+int or_solve(int32_t n0, const int32_t *row_ptr0, const int32_t *col0, const int32_t *val0,
+             const int32_t *h0, int64_t offset0, const or_params *prm,
+             const uint32_t *thr, int32_t dmax, uint64_t seed,
+             int64_t *energies, int32_t *counts, int32_t *nfree, int32_t *nphases,
+             int8_t *fixed, int64_t *best_e, int8_t *best_state)
+{
+    const int32_t P = prm->max_fix_phases + 1;
+    const int32_t Smax = prm->fixing_sample_size > prm->solving_sample_size
+                             ? prm->fixing_sample_size : prm->solving_sample_size;
+    const int64_t nnz0 = row_ptr0[n0];
+    if (prm->max_fix_phases < 1 || prm->fix_den <= 0 || prm->fix_num <= 0 ||
+        prm->fix_num > prm->fix_den || prm->fixing_sample_size < 1 || prm->solving_sample_size < 0)
+        return -1;
+
+    int32_t *colour0 = (int32_t *)malloc(sizeof(int32_t) * ((size_t)n0 + 1));
+    int32_t ncol = or_colour(n0, row_ptr0, col0, colour0);
+
+    /* current problem (two buffers, swapped after each reduction) */
+    int32_t *rp[2], *cl[2], *vl[2], *hh[2], *co[2];
+    for (int b = 0; b < 2; ++b) {
+        rp[b] = (int32_t *)malloc(sizeof(int32_t) * ((size_t)n0 + 1));
+        cl[b] = (int32_t *)malloc(sizeof(int32_t) * ((size_t)nnz0 + 1));
+        vl[b] = (int32_t *)malloc(sizeof(int32_t) * ((size_t)nnz0 + 1));
+        hh[b] = (int32_t *)malloc(sizeof(int32_t) * ((size_t)n0 + 1));
+        co[b] = (int32_t *)malloc(sizeof(int32_t) * ((size_t)n0 + 1));
+    }
+    int32_t *orig = (int32_t *)malloc(sizeof(int32_t) * ((size_t)n0 + 1));
+    int32_t *old_of_new = (int32_t *)malloc(sizeof(int32_t) * ((size_t)n0 + 1));
+    int32_t *tmp = (int32_t *)malloc(sizeof(int32_t) * ((size_t)n0 + 1));
+    int32_t *cnt = (int32_t *)malloc(sizeof(int32_t) * ((size_t)n0 + 1));
+    int8_t *fx = (int8_t *)malloc((size_t)n0 + 1);
+    int8_t *spins = (int8_t *)malloc((size_t)Smax * (size_t)n0 + 1);
+    int64_t *e = (int64_t *)malloc(sizeof(int64_t) * ((size_t)Smax + 1));
+    int32_t *elite = (int32_t *)malloc(sizeof(int32_t) * ((size_t)Smax + 1));
+    int rc = 0;
+
+    for (int32_t st = 0; st < prm->num_starts && rc == 0; ++st) {
+        int b = 0;
+        int32_t n = n0;
+        int64_t off = offset0;
+        memcpy(rp[0], row_ptr0, sizeof(int32_t) * ((size_t)n0 + 1));
+        memcpy(cl[0], col0, sizeof(int32_t) * (size_t)nnz0);
+        memcpy(vl[0], val0, sizeof(int32_t) * (size_t)nnz0);
+        memcpy(hh[0], h0, sizeof(int32_t) * (size_t)n0);
+        memcpy(co[0], colour0, sizeof(int32_t) * (size_t)n0);
+        for (int32_t i = 0; i < n0; ++i) orig[i] = i;
+        int8_t *fmap = fixed + (int64_t)st * n0;
+        int8_t *bstate = best_state + (int64_t)st * n0;
+        memset(fmap, 0, (size_t)n0);
+        best_e[st] = INT64_MAX;
+        int32_t phase = 0;
+
+        for (;;) {
+            int fixing = phase < prm->max_fix_phases &&
+                         (phase == 0 || (prm->iterate && n > 0));
+            int32_t S = fixing ? prm->fixing_sample_size : prm->solving_sample_size;
+            if (!fixing && S == 0) break;
+            rc = or_sample(n, rp[b], cl[b], vl[b], hh[b], co[b], ncol, prm->num_sweeps, thr, dmax,
+                           0, S, seed, (uint32_t)st, (uint32_t)phase, spins, e, NULL);
+            if (rc) break;
+            int64_t *rec = energies + ((int64_t)st * P + phase) * Smax;
+            for (int32_t r = 0; r < S; ++r) rec[r] = e[r] + off;
+            counts[st * P + phase] = S;
+            nfree[st * P + phase] = n;
+
+            /* best sample of this phase, lifted to the original variables */
+            or_elite(S, e, 1, elite);
+            if (e[elite[0]] + off < best_e[st]) {
+                best_e[st] = e[elite[0]] + off;
+                for (int32_t i = 0; i < n0; ++i) bstate[i] = fmap[i];
+                for (int32_t a = 0; a < n; ++a) bstate[orig[a]] = spins[(int64_t)elite[0] * n + a];
+            }
+            ++phase;
+            if (!fixing) break;
+
+            int32_t k = or_elite_count(prm->elite_threshold, S);
+            int32_t canon = prm->canon < 0 ? all_zero(n, hh[b]) : prm->canon;
+            int32_t nf = or_persistence(n, rp[b], S, spins, e, k, prm->fix_num, prm->fix_den,
+                                        canon, cnt, fx, NULL);
+            if (nf == 0 && prm->iterate && n > 0) {
+                /* stall rule: fix the lowest-index free spin to its value in
+                   the best elite sample, so every SPVAR phase makes progress */
+                or_elite(S, e, 1, elite);
+                fx[0] = spins[(int64_t)elite[0] * n + 0];
+            }
+            for (int32_t a = 0; a < n; ++a)
+                if (fx[a]) fmap[orig[a]] = fx[a];
+            int32_t n2;
+            int64_t off2;
+            or_reduce(n, rp[b], cl[b], vl[b], hh[b], off, co[b], fx, &n2, rp[1 - b], cl[1 - b],
+                      vl[1 - b], hh[1 - b], &off2, co[1 - b], old_of_new);
+            for (int32_t a = 0; a < n2; ++a) tmp[a] = orig[old_of_new[a]];
+            memcpy(orig, tmp, sizeof(int32_t) * (size_t)n2);
+            n = n2;
+            off = off2;
+            b = 1 - b;
+        }
+        nphases[st] = phase;
+    }
+
+    for (int b = 0; b < 2; ++b) { free(rp[b]); free(cl[b]); free(vl[b]); free(hh[b]); free(co[b]); }
+    free(colour0); free(orig); free(old_of_new); free(tmp); free(cnt); free(fx);
+    free(spins); free(e); free(elite);
+    return rc;
+}

@@ -1,0 +1,135 @@
+/*
+ * spvar_oracle.h -- plain, slow, single-threaded C restatement of the
+ * sample-persistence variable reduction method (SPVAR, Alg. 1; Multi-start
+ * SPVAR, Alg. 2, Sec. II.A-II.C) with simulated annealing as the sampler.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This oracle exists so that tests, the
+ * smoke check and the CPU baseline leg of the benchmark can check and time
+ * the CUDA library.  The product path never links, loads or calls it, and it
+ * shares no code, header, table or helper with the CUDA library.
+ *
+ * Conventions (Sec. I problem statement, readings listed in the design notes):
+ *   E(s) = sum_{i<j} J_ij s_i s_j + sum_i h_i s_i + offset,  s_i in {-1,+1}.
+ *   Symmetric CSR: every coupler appears in both rows with the same value,
+ *   columns strictly ascending inside a row, no diagonal entries.
+ *   Spins are int8 values -1/+1; energies are int64.
+ *
+ * Return codes: 0 = ok, negative = invalid input (documented per function).
+ */
+#ifndef SPVAR_ORACLE_H
+#define SPVAR_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Philox4x32 with 10 rounds (Salmon, Moraes, Dror, Shaw, SC'11):
+ * out = philox(ctr, key).  Parity pinned against cuRAND's host generator. */
+void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+
+/* Edge list (ei[e], ej[e], J[e]), e < m, i != j, no duplicates, J != 0
+ * allowed to be any int32 -> symmetric CSR (row_ptr[n+1], col/val[2m]).
+ * Returns 0, or -1 on a self loop / out-of-range index / duplicate pair. */
+int or_csr_from_edges(int32_t n, int64_t m, const int32_t *ei, const int32_t *ej,
+                      const int32_t *J, int32_t *row_ptr, int32_t *col, int32_t *val);
+
+/* Colour classes used for the sweep order.  If the graph is bipartite each
+ * connected component is 2-coloured by BFS distance parity from its
+ * lowest-index vertex; otherwise first-fit greedy in index order.  Writes
+ * colour[n], returns the number of colours (>= 1 for n >= 1, 0 for n == 0). */
+int32_t or_colour(int32_t n, const int32_t *row_ptr, const int32_t *col, int32_t *colour);
+
+/* Largest possible energy change of one flip:
+ * dmax = 2 * max_i (sum_j |J_ij| + |h_i|). */
+int64_t or_dmax(int32_t n, const int32_t *row_ptr, const int32_t *val, const int32_t *h);
+
+/* Acceptance thresholds: thr[t*(dmax+1)+d] =
+ * min(2^32-1, floor(2^32 * exp(-beta[t] * d / scale))), d = 0..dmax. */
+void or_thresholds(int32_t T, const double *beta, int32_t dmax, int32_t scale, uint32_t *thr);
+
+/* Geometric schedule beta_t = beta0 * (beta1/beta0)^(t/(T-1)), endpoints
+ * included (T == 1 gives beta0). */
+void or_beta_geometric(int32_t T, double beta0, double beta1, double *beta);
+
+/* E(s) without the offset. */
+int64_t or_energy(int32_t n, const int32_t *row_ptr, const int32_t *col,
+                  const int32_t *val, const int32_t *h, const int8_t *s);
+
+/* Simulated annealing sample (one independent run per replica r < S).
+ * Random word for (spin i, sweep slot t, replica r): word (r & 3) of
+ * philox(ctr = {i, phase*2^20 + t, r >> 2, start}, key = {seed lo, seed hi});
+ * slot 2^20-1 is the initial state (s_i = +1 iff the top bit is set).
+ * Replicas r0 .. r0+S-1 are computed (rows 0 .. S-1 of the output).
+ * Sweep t visits colour 0 ascending index, colour 1, ...; a flip with
+ * dE = -2 s_i (h_i + sum_j J_ij s_j) is accepted iff dE <= 0 or
+ * word < thr[t][dE].  Writes spins[S*n] (row r = replica r) and e[S]
+ * (energy without offset).  If incr_err != NULL, the running energy is
+ * compared with a full recomputation after every sweep of every replica and
+ * the largest absolute difference is stored there.
+ * Returns 0, -1 on bad sizes (T >= 2^20-1, phase >= 2^12), -2 if a dE
+ * exceeds dmax. */
+int or_sample(int32_t n, const int32_t *row_ptr, const int32_t *col, const int32_t *val,
+              const int32_t *h, const int32_t *colour, int32_t ncol,
+              int32_t T, const uint32_t *thr, int32_t dmax,
+              int32_t r0, int32_t S, uint64_t seed, uint32_t start, uint32_t phase,
+              int8_t *spins, int64_t *e, int64_t *incr_err);
+
+/* Elite sample size k = ceil(elite * S), clamped to [1, S] (Alg. 1). */
+int32_t or_elite_count(double elite, int32_t S);
+
+/* Indices of the k lowest-energy samples ordered by (energy, index). */
+void or_elite(int32_t S, const int64_t *e, int32_t k, int32_t *idx);
+
+/* Persistence pass (Alg. 1, Sec. II.C).  Over the elite rows, optionally
+ * multiplied by their value at the reference spin rho (the lowest-index spin
+ * of maximum degree) when canon != 0, counts cnt[i] = #{+1}; fixes
+ * v = sign(2cnt-k) when fix_den*|2cnt-k| >= fix_num*k.  Writes cnt[n],
+ * fixed[n] (0 free, +1, -1) and *rho_out (-1 without canonicalisation).
+ * Returns the number of fixed spins. */
+int32_t or_persistence(int32_t n, const int32_t *row_ptr, int32_t S, const int8_t *spins,
+                       const int64_t *e, int32_t k, int32_t fix_num, int32_t fix_den,
+                       int32_t canon, int32_t *cnt, int8_t *fixed, int32_t *rho_out);
+
+/* Fold and compact (Alg. 1 "update J and h").  Free spins keep their order;
+ * h'_i = h_i + sum_{j fixed} J_ij v_j; offset' = offset + sum_{i fixed} h_i v_i
+ * + sum_{i<j both fixed} J_ij v_i v_j; CSR of free-free couplers; colours
+ * inherited.  Output arrays must hold n+1 / nnz / n entries.  Writes
+ * *n_out, *offset_out, returns 0. */
+int or_reduce(int32_t n, const int32_t *row_ptr, const int32_t *col, const int32_t *val,
+              const int32_t *h, int64_t offset, const int32_t *colour, const int8_t *fixed,
+              int32_t *n_out, int32_t *row_ptr_out, int32_t *col_out, int32_t *val_out,
+              int32_t *h_out, int64_t *offset_out, int32_t *colour_out, int32_t *old_of_new);
+
+/* Multi-start SPVAR (Alg. 2) with SA as the sampler. */
+typedef struct or_params {
+    int32_t num_starts;
+    int32_t fixing_sample_size;
+    int32_t solving_sample_size;   /* 0: no solving phase */
+    int32_t num_sweeps;
+    double elite_threshold;
+    int32_t fix_num, fix_den;      /* fixing_threshold = fix_num / fix_den */
+    int32_t iterate;               /* 1: repeat SPVAR until no free spin (ISPVAR) */
+    int32_t max_fix_phases;        /* cap on SPVAR phases per start (>= 1) */
+    int32_t canon;                 /* -1: when every h is 0; 0: never; 1: always */
+} or_params;
+
+/* Outputs (caller-allocated, P = max_fix_phases + 1, Smax = max sample size):
+ *   energies[num_starts][P][Smax]  recorded full-problem energies
+ *   counts[num_starts][P]          samples recorded in each phase slot
+ *   nfree[num_starts][P]           free spins when that phase sampled
+ *   nphases[num_starts]            phase slots used
+ *   fixed[num_starts][n0]          final fix map in original indices
+ *   best_e[num_starts], best_state[num_starts][n0] (+1/-1)
+ * thr is the table for the original problem (dmax from or_dmax on it).
+ * Returns 0 or a negative code from a step. */
+int or_solve(int32_t n0, const int32_t *row_ptr0, const int32_t *col0, const int32_t *val0,
+             const int32_t *h0, int64_t offset0, const or_params *prm,
+             const uint32_t *thr, int32_t dmax, uint64_t seed,
+             int64_t *energies, int32_t *counts, int32_t *nfree, int32_t *nphases,
+             int8_t *fixed, int64_t *best_e, int8_t *best_state);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,181 @@
+"""Oracle pins for the persistence pass and fold/compact (Alg. 1) and for the
+Multi-start loop (Alg. 2).
+
+- elite order against numpy's lexsort; k = ceil(elite * S);
+- counts and the fixing rule against exact rational arithmetic;
+- the zero-bias canonicalisation is invariant under flipping any elite row;
+- reduction invariant: E_full(s) = E_reduced(s_free) + offset' for every
+  assignment consistent with the fixings (exhaustive for n <= 14);
+- solve: recorded energies are valid energies (>= brute-force minimum) and the
+  best state's energy, recomputed densely, equals the reported best energy.
+"""
+import itertools
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1706_07826_gb300 import instances as I
+
+
+def _csr(inst):
+    return O.csr_from_edges(inst.n, inst.ei, inst.ej, inst.J, inst.h, inst.offset, inst.scale)
+
+
+def _dense(inst):
+    M = np.zeros((inst.n, inst.n), np.int64)
+    for a, b, j in zip(inst.ei, inst.ej, inst.J):
+        M[min(a, b), max(a, b)] += j
+    return M
+
+
+def _E(inst, S):
+    S = np.atleast_2d(np.asarray(S, np.int64))
+    return np.einsum("si,ij,sj->s", S, _dense(inst), S) + S @ inst.h.astype(np.int64) + inst.offset
+
+
+def _E_csr(p, S):
+    """Energy of a Csr problem (incl. offset) through a dense matrix built here."""
+    S = np.atleast_2d(np.asarray(S, np.int64))
+    M = np.zeros((p.n, p.n), np.int64)
+    for i in range(p.n):
+        for q in range(p.row_ptr[i], p.row_ptr[i + 1]):
+            if p.col[q] > i:
+                M[i, p.col[q]] += p.val[q]
+    return np.einsum("si,ij,sj->s", S, M, S) + S @ p.h.astype(np.int64) + p.offset
+
+
+@pytest.mark.parametrize("S,elite,k", [(256, 0.1, 26), (1000, 0.1, 100), (250, 0.2, 50), (7, 1.0, 7),
+                                       (5, 1e-9, 1), (2000, 0.1, 200), (500, 0.3, 150)])
+def test_elite_count(S, elite, k):
+    assert O.elite_count(elite, S) == k
+
+
+def test_elite_order_matches_lexsort():
+    g = np.random.default_rng(1)
+    e = g.integers(-20, 5, 300).astype(np.int64)  # many ties
+    for k in (1, 17, 300):
+        ref = np.lexsort((np.arange(300), e))[:k]
+        assert np.array_equal(O.elite(e, k), ref)
+
+
+@pytest.mark.parametrize("canon", [0, 1])
+@pytest.mark.parametrize("tau", [(1, 1), (9, 10), (1, 2)])
+def test_persistence_counts_and_rule(canon, tau):
+    inst = I.random_graph(20, 45, 4)
+    p = _csr(inst)
+    g = np.random.default_rng(2)
+    S = 60
+    spins = np.where(g.random((S, 20)) < 0.8, 1, -1).astype(np.int8)
+    spins[:, 3] = 1
+    spins[:, 5] = -1
+    e = g.integers(-10, 10, S).astype(np.int64)
+    k = 13
+    cnt, fixed, nf, rho = O.persistence(p, spins, e, k, tau[0], tau[1], canon)
+    idx = np.lexsort((np.arange(S), e))[:k]
+    rows = spins[idx].astype(np.int64)
+    deg = np.diff(p.row_ptr)
+    if canon:
+        assert rho == int(np.argmax(deg))
+        rows = rows * rows[:, rho:rho + 1]
+    else:
+        assert rho == -1
+    assert np.array_equal(cnt, (rows > 0).sum(axis=0))
+    for i in range(20):
+        mean = Fraction(int(rows[:, i].sum()), k)
+        want = int(np.sign(mean.numerator)) if abs(mean) >= Fraction(tau[0], tau[1]) else 0
+        assert fixed[i] == want
+    assert nf == int((fixed != 0).sum())
+
+
+def test_canonicalisation_breaks_zero_bias_degeneracy():
+    inst = I.cubic3d(3, 2)
+    p = _csr(inst)
+    g = np.random.default_rng(5)
+    base = np.where(g.random(inst.n) < 0.5, 1, -1).astype(np.int8)
+    S = 40
+    spins = np.array([base if r % 2 == 0 else -base for r in range(S)], np.int8)
+    e = np.zeros(S, np.int64)
+    _, fixed0, nf0, _ = O.persistence(p, spins, e, S, 1, 1, 0)
+    assert nf0 == 0                      # each state appears with its reverse: nothing persists
+    _, fixed1, nf1, rho = O.persistence(p, spins, e, S, 1, 1, 1)
+    assert nf1 == inst.n                 # up to the global flip every row is the same state
+    assert np.array_equal(fixed1, base * base[rho])
+    flipped = spins.copy()
+    flipped[[1, 6, 7]] *= -1             # flipping elite rows changes nothing under canon
+    assert np.array_equal(O.persistence(p, flipped, e, S, 1, 1, 1)[1], fixed1)
+
+
+def _all_consistent(n, fixed):
+    free = np.flatnonzero(fixed == 0)
+    out = np.tile(fixed.astype(np.int64), (2 ** len(free), 1))
+    if len(free):
+        out[:, free] = np.array(list(itertools.product([-1, 1], repeat=len(free))), np.int64)
+    return out, free
+
+
+@pytest.mark.parametrize("pattern", ["none", "all", "one", "random", "half"])
+def test_reduction_invariant_exhaustive(pattern):
+    inst = I.random_graph(13, 30, 9, jmax=4, hmax=3)
+    inst.offset = 17
+    p = _csr(inst)
+    g = np.random.default_rng(11)
+    fixed = {"none": np.zeros(13), "all": g.choice([-1, 1], 13), "one": np.eye(13)[4] * -1,
+             "random": g.choice([-1, 0, 1], 13), "half": np.where(np.arange(13) % 2, 1, 0)}[pattern].astype(np.int8)
+    red, (col2, _), oon = O.reduce(p, fixed)
+    S, free = _all_consistent(13, fixed)
+    assert np.array_equal(oon, free)
+    assert red.n == len(free)
+    full = _E(inst, S)
+    sub = _E_csr(red, S[:, free]) if red.n else np.full(len(S), red.offset)
+    assert np.array_equal(full, sub)
+    colours, _ = O.colour(p)
+    assert np.array_equal(col2, colours[free])
+
+
+def test_reduction_invariant_sampled_scaled_problem():
+    inst = I.weak_strong(3, 6)
+    p = _csr(inst)
+    g = np.random.default_rng(12)
+    fixed = g.choice([-1, 0, 0, 1], inst.n).astype(np.int8)
+    red, _, oon = O.reduce(p, fixed)
+    S = g.choice([-1, 1], (10000, inst.n)).astype(np.int64)
+    S[:, fixed != 0] = fixed[fixed != 0]
+    assert np.array_equal(_E(inst, S), _E_csr(red, S[:, oon]))
+    # the reduced CSR stays symmetric with ascending columns
+    for i in range(red.n):
+        cols = red.col[red.row_ptr[i]:red.row_ptr[i + 1]]
+        assert np.all(np.diff(cols) > 0)
+
+
+def test_solve_energies_are_valid_and_best_state_consistent():
+    inst = I.random_graph(14, 36, 13, jmax=3, hmax=1)
+    p = _csr(inst)
+    thr = O.thresholds(O.beta_geometric(150, 0.1, 3.0), O.dmax(p), 1)
+    r = O.solve(p, thr, seed=5, num_starts=4, fixing_sample_size=24, solving_sample_size=16,
+                elite_threshold=0.25)
+    allS, _ = _all_consistent(14, np.zeros(14, np.int8))
+    e0 = _E(inst, allS).min()
+    for st in range(4):
+        assert r.nphases[st] == 2
+        assert list(r.counts[st]) == [24, 16]
+        assert r.nfree[st, 0] == 14 and r.nfree[st, 1] <= 14
+        rec = np.concatenate([r.energies[st, ph, :r.counts[st, ph]] for ph in range(2)])
+        assert rec.min() >= e0
+        assert r.best_e[st] == rec.min()
+        assert _E(inst, r.best_state[st])[0] == r.best_e[st]
+        assert 14 - r.nfree[st, 1] == int((r.fixed[st] != 0).sum())
+
+
+def test_ispvar_fixes_every_spin():
+    inst = I.cubic3d(3, 21)
+    p = _csr(inst)
+    thr = O.thresholds(O.beta_geometric(100, 0.1, 3.0), O.dmax(p), 1)
+    r = O.solve(p, thr, seed=9, num_starts=2, fixing_sample_size=32, solving_sample_size=0,
+                elite_threshold=0.1, iterate=True, max_fix_phases=inst.n)
+    for st in range(2):
+        assert np.all(r.fixed[st] != 0)
+        ph = r.nphases[st]
+        assert np.all(np.diff(r.nfree[st, :ph]) < 0)   # every phase fixes at least one spin
+        assert _E(inst, r.best_state[st])[0] == r.best_e[st]
