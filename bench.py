@@ -1,0 +1,356 @@
+"""Benchmark: SA spin-flip attempts/s and SPVAR TTS99 of Multi-start SPVAR
+(Alg. 2) on a Chimera C8 +-J problem (N = 512, 1472 couplers, h = 0):
+10 starts x (1000 fixing + 1000 solving) samples, 1000 sweeps, geometric
+beta 0.1 -> 3.0, elite 10 %, fixing threshold 1.
+
+One step = one full Multi-start SPVAR run (every start: sample, elite,
+persistence, fold/compact, solving sample) through the C-ABI library.
+``value`` is attempts/s of the batched (persistent + CUDA graph) form with the
+problem resident on the device; the plain one-launch-per-start form is timed
+beside it; ``e2e`` goes through spvar_problem_create + spvar_solve with host
+buffers.  ``--impl reference`` times the oracle on the host cores instead.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+import argparse
+import json
+import math
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "SA spin-flip attempts/s (SPVAR TTS99 beside it), batched vs plain form"
+UNIT = "spin-flip attempts/s"
+WORKLOAD = dict(workload="Chimera C8 +-J (N=512, 1472 couplers, h=0, instance seed 1200); Multi-start SPVAR: "
+                         "10 starts x (1000 fixing + 1000 solving) samples, 1000 sweeps, beta 0.1->3.0 geometric, "
+                         "elite 0.1, fixing threshold 1.0, zero-bias reference-spin canonicalisation",
+                instance="chimera(M=8, seed=1200)", num_starts=10, fixing_sample_size=1000,
+                solving_sample_size=1000, num_sweeps=1000, beta0=0.1, beta1=3.0, elite_threshold=0.1)
+INSTANCE_SEED = 1200
+RUN_SEED0 = 42
+L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
+SMS, LANES_PER_SM = 152, 128  # GB300: 152 SMs x 4 SMSPs x 32 lanes issue one int op per lane per clock
+PHILOX_OPS_PER_ATTEMPT = 15  # 10 rounds x (2 wide multiplies + 2 three-input xors + 2 key adds) / 4 replicas
+ACCEPT_OPS_PER_ATTEMPT = 3   # dE, dE <= 0 test, threshold compare
+
+
+def _instance():
+    from paper_1706_07826_gb300 import instances as I
+    return I.chimera(8, INSTANCE_SEED)
+
+
+def _params(form):
+    from paper_1706_07826_gb300 import spvar
+    return spvar.make_params(num_starts=10, fixing_sample_size=1000, solving_sample_size=1000, num_sweeps=1000,
+                             beta0=0.1, beta1=3.0, elite_threshold=0.1, fix_num=1, fix_den=1, iterate=False,
+                             max_fix_phases=1, canon=-1, form=form)
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc:
+            time.sleep(0.15)
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            f = [x.strip() for x in l.split(",")]
+            try:
+                sm.append(float(f[0]))
+                mx = max(mx, float(f[1]))
+            except (ValueError, IndexError):
+                continue
+            for name, v in zip(names, f[4:8]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        load = [x for x in sm if x > 0.5 * mx] if mx else sm
+        return {"sm_mhz": statistics.median(load) if load else None, "sm_max_mhz": mx or None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------- CPU baseline
+def _oracle_worker(args):
+    r0, R = args
+    sys.path.insert(0, ROOT)
+    from oracle import oracle as O
+    inst = _instance()
+    p = O.csr_from_edges(inst.n, inst.ei, inst.ej, inst.J, inst.h)
+    thr = O.thresholds(O.beta_geometric(1000, 0.1, 3.0), O.dmax(p), 1)
+    t0 = time.perf_counter()
+    O.sample(p, thr, R, RUN_SEED0, start=0, phase=0, r0=r0)
+    return time.perf_counter() - t0
+
+
+def cpu_oracle_rate(replicas_per_core, cores=None, pool=None):
+    """Oracle SA sample of the workload's first phase, replicas split across
+    the host cores (one process each).  Returns (attempts/s, cores, seconds)."""
+    cores = cores or os.cpu_count() or 1
+    own = pool is None
+    if own:
+        pool = mp.get_context("spawn").Pool(cores)
+        pool.map(_oracle_worker, [(0, 1)] * cores)  # start-up outside the timing
+    try:
+        t0 = time.perf_counter()
+        pool.map(_oracle_worker, [(c * replicas_per_core, replicas_per_core) for c in range(cores)])
+        dt = time.perf_counter() - t0
+    finally:
+        if own:
+            pool.close()
+            pool.join()
+    attempts = cores * replicas_per_core * 512 * 1000
+    return attempts / dt, cores, dt
+
+
+def reference_arm(args, rank, world):
+    if rank != 0:
+        return
+    R = args.ref_replicas
+    cores = os.cpu_count() or 1
+    pool = mp.get_context("spawn").Pool(cores)
+    for _ in range(args.warmup):
+        cpu_oracle_rate(1, cores, pool)
+    vals, secs = [], 0.0
+    for _ in range(args.steps):
+        v, _, dt = cpu_oracle_rate(R, cores, pool)
+        vals.append(v)
+        secs += dt
+    pool.close()
+    pool.join()
+    value = args.steps * cores * R * 512 * 1000 / secs
+    cfg = dict(WORKLOAD)
+    sample = ("oracle SA sample of the first phase of start 0: %d replicas x 512 spins x 1000 sweeps per step "
+              "(%d per core, one process per core)" % (cores * R, R))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * secs / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic", "config": cfg,
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------ GPU arm
+def _flush(buf):
+    buf.add_(1)
+
+
+def run_form(spvar, torch, plan, K, W, seeds0, flush, profile=False):
+    """W warm-up + K timed plan runs; returns (total ms, attempts list, outs)."""
+    stream = torch.cuda.current_stream()
+    attempts = []
+    for w in range(W):
+        plan.run(seeds0 + w, device=True)
+    torch.cuda.synchronize()
+    plan.set_profiling(profile)
+    sweep_ms, sweep_n = 0.0, 0
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    out = plan.alloc_outputs(True)
+    best = []
+    for k in range(K):
+        _flush(flush)
+        evs[k][0].record(stream)
+        plan.run(seeds0 + 100 + k, out=out, device=True)
+        evs[k][1].record(stream)
+        if profile:
+            ms, n = plan.sweep_time()
+            sweep_ms += ms
+            sweep_n += n
+        a, _ = plan.stats()
+        attempts.append(a)
+        best.append(out.best_energy.min().item())
+    torch.cuda.synchronize()
+    total = sum(a.elapsed_time(b) for a, b in evs)
+    plan.set_profiling(False)
+    return total, attempts, best, (sweep_ms, sweep_n), out
+
+
+def tts99(p, seconds_per_start):
+    if p <= 0:
+        return None
+    starts = 1.0 if p >= 1 else math.log(0.01) / math.log(1 - p)
+    return starts * seconds_per_start
+
+
+def gpu_arm(args, rank, world):
+    import torch
+    from paper_1706_07826_gb300 import build as B
+    from paper_1706_07826_gb300 import spvar
+    if args.build:
+        B.build()
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", dev))
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        # before any GPU work: spawned oracle processes on the host cores
+        R = args.cpu_replicas
+        rate, cores, dt = cpu_oracle_rate(R)
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": "oracle SA sample of the first phase (start 0, phase 0): %d replicas x 512 spins x 1000 "
+                         "sweeps (%d per core, one process per core, %.1f s wall)" % (cores * R, R, dt)}
+
+    inst = _instance()
+    seed_base = RUN_SEED0 + 100000 * rank  # each rank runs its own starts (weak scaling)
+    prob = spvar.Problem.from_instance(inst)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
+    K, W = args.steps, args.warmup
+
+    plan_b = spvar.Plan([prob], _params(spvar.FORM_BATCHED))
+    plan_p = spvar.Plan([prob], _params(spvar.FORM_PLAIN))
+
+    def barrier():
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    barrier()
+    with ClockSampler(dev) as clk:
+        tb, att_b, best_b, _, out_b = run_form(spvar, torch, plan_b, K, W, seed_base, flush)
+    barrier()
+    # profiled pass: same runs, sweep kernel timed with events on the launch stream
+    _, att_prof, _, (sweep_ms, sweep_n), _ = run_form(spvar, torch, plan_b, max(3, K // 5), 1, seed_base, flush,
+                                                       profile=True)
+    Kp = max(3, K // 5)
+    tp, att_p, best_p, _, out_p = run_form(spvar, torch, plan_p, Kp, 1, seed_base, flush)
+    barrier()
+
+    t_b = torch.tensor([tb], dtype=torch.float64, device="cuda")
+    n_b = torch.tensor([float(sum(att_b))], dtype=torch.float64, device="cuda")
+    if dist:
+        dist.all_reduce(t_b, op=dist.ReduceOp.MAX)
+        dist.all_reduce(n_b, op=dist.ReduceOp.SUM)
+    value = n_b.item() / (t_b.item() / 1000.0)
+    plain_value = sum(att_p) / (tp / 1000.0)
+
+    # TTS99 (Sec. III.A R99 with wall time): p = fraction of starts whose
+    # recorded energies reach the best energy known for the instance
+    e_known = min(min(best_b), min(best_p))
+    en = out_b.energies.cpu().numpy()
+    cnt = out_b.counts.cpu().numpy()
+    hit = [any(en[s, ph, :cnt[s, ph]].min() == e_known for ph in range(en.shape[1]) if cnt[s, ph] > 0)
+           for s in range(en.shape[0])]
+    p = sum(hit) / len(hit)
+    tts_b = tts99(p, tb / 1000.0 / K / 10)
+    tts_p = tts99(p, tp / 1000.0 / Kp / 10)
+
+    # e2e through the public API with host buffers
+    rp, col, val = spvar.csr_from_edges(inst.n, inst.ei, inst.ej, inst.J)
+    prm = _params(spvar.FORM_BATCHED)
+    h2d = rp.nbytes + col.nbytes + val.nbytes + inst.h.nbytes + 1000 * 13 * 4
+    e2e_times, e2e_att = [], []
+    for k in range(max(3, K // 5) + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        pr = spvar.Problem.create(inst.n, rp, col, val, inst.h)
+        o = spvar.solve(pr, prm, seed_base + 500 + k, device=False)
+        dt = time.perf_counter() - t0
+        if k > 0:
+            e2e_times.append(dt)
+            e2e_att.append(int((o.counts.astype(np.int64) * o.nfree).sum()) * 1000)
+        pr.close()
+    d2h = sum(getattr(o, f).nbytes for f in ("energies", "counts", "nfree", "nphases", "fixed", "best_energy",
+                                             "best_state"))
+    e2e_value = sum(e2e_att) / sum(e2e_times) * world
+
+    # roofline of the sweep kernel (integer ALU issue bound)
+    mean_deg = 2 * inst.m / inst.n
+    ops_per_attempt = PHILOX_OPS_PER_ATTEMPT + mean_deg + ACCEPT_OPS_PER_ATTEMPT
+    att_per_launch = sum(att_prof) / max(sweep_n, 1)
+    ms_per_launch = sweep_ms / max(sweep_n, 1)
+    achieved = att_per_launch * ops_per_attempt / (ms_per_launch / 1000.0) / 1e12
+    cs = clk.summary()
+    peak = SMS * LANES_PER_SM * 2070e6 / 1e12
+    shape = plan_b.shape()
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+        "ms_per_step": tb / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "int32", "data": "synthetic",
+        "config": dict(WORKLOAD, form="batched (persistent sweep + CUDA graph per phase)",
+                       l2="256 MB buffer written between timed steps", parallelism="starts sharded per rank"
+                       if world > 1 else "single GPU", sweep_shape=shape),
+        "plain": {"value": plain_value, "unit": UNIT, "ms_per_step": tp / Kp, "steps": Kp,
+                  "speedup_batched_over_plain": value / world / plain_value},
+        "tts99": {"p_success_per_start": p, "e_best_known": int(e_known), "e_known_kind": "best found by the runs "
+                  "of this benchmark (not proved optimal)", "batched_s": tts_b, "plain_s": tts_p,
+                  "starts_measured": len(hit)},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                "api": "spvar_problem_create + spvar_solve (host buffers, plan built per call)",
+                "ms_per_step": 1000 * statistics.mean(e2e_times)},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
+                     "traffic": None, "kernel": "k_sweep (SA colour-class sweep)",
+                     "ops_per_attempt": ops_per_attempt, "attempts_per_launch": att_per_launch,
+                     "ms_per_launch": ms_per_launch,
+                     "peak_note": "152 SMs x 128 int32 lanes x 2070 MHz (one warp instruction per SMSP per clock)"},
+        "gpu_launches": K * (1 + 2 * 6),
+        "clocks": cs,
+    }
+    if cpu:
+        line["cpu_baseline"] = cpu
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-replicas", type=int, default=400, help="oracle replicas per core (cpu_baseline)")
+    ap.add_argument("--ref-replicas", type=int, default=24, help="oracle replicas per core per step (reference arm)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-build", dest="build", action="store_false")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        reference_arm(args, rank, world)
+    else:
+        gpu_arm(args, rank, world)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,270 @@
+/*
+ * spvar.h -- C ABI of the GB300 (sm_103a) library for sample-persistence
+ * variable reduction with a simulated-annealing sampler.
+ *
+ * The method (Karimi, Rosenberg, Katzgraber, "Effective optimization using
+ * sample persistence"): minimise the Ising energy of Sec. I,
+ *
+ *     E(s) = sum_{i<j} J_ij s_i s_j + sum_i h_i s_i + offset,  s in {-1,+1}^N,
+ *
+ * by sampling low-energy states, fixing the variables that take the same
+ * value across the lowest-energy part of the sample (SPVAR, Alg. 1) and
+ * sampling the smaller problem that remains, over many independent starts
+ * (Multi-start SPVAR, Alg. 2).  The sampler is simulated annealing: Metropolis
+ * single-spin sweeps under an increasing inverse temperature (the SA solver
+ * of Sec. III.A).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Return value: SPVAR_OK (0) or a negative SPVAR_E* code; spvar_strerror()
+ *    names it.  On error nothing is written to outputs except where stated.
+ *  - Integers only: couplers, biases and energies are integers (a real-valued
+ *    problem is passed multiplied by an integer energy_scale), so every
+ *    result is exact and reproducible bit for bit.
+ *  - Problems are symmetric CSR: row i lists the neighbours j of spin i with
+ *    J_ij; each coupler appears in both rows with the same value, columns
+ *    strictly ascending, no diagonal, no zero-valued entries.
+ *  - Spin samples are bit-packed rows: sample r occupies W = ceil(n/32)
+ *    uint32 words; bit (i % 32) of word (i / 32) is 1 iff s_i = +1.
+ *  - "device" pointers are CUDA device memory of the current device (for
+ *    example torch tensor data_ptr()); "host" pointers are CPU memory.  The
+ *    caller owns every buffer it passes; the library copies inputs and never
+ *    retains caller pointers after a call returns.  Opaque objects are owned
+ *    by the library until their *_destroy call.
+ *  - stream: a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    Device-pointer outputs are written asynchronously on that stream; calls
+ *    that return host data synchronise the stream before returning.
+ *  - Randomness: Philox4x32-10 (Salmon et al., SC'11) keyed by the 64-bit
+ *    seed, counter (spin, phase * 2^20 + sweep, replica / 4, start), word
+ *    replica % 4.  Results therefore depend only on the logical coordinates,
+ *    never on launch shape, batching or scheduling.
+ */
+#ifndef SPVAR_H
+#define SPVAR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SPVAR_OK 0
+#define SPVAR_EINVAL (-1)    /* invalid argument or malformed problem */
+#define SPVAR_EOVERFLOW (-2) /* values would overflow the 32-bit energy arithmetic */
+#define SPVAR_ENOMEM (-3)    /* host or device allocation failed */
+#define SPVAR_EBUDGET (-4)   /* request does not fit the device-memory budget */
+#define SPVAR_ETIMEOUT (-5)  /* a bounded device-side wait gave up */
+#define SPVAR_ECUDA (-6)     /* a CUDA runtime call failed */
+#define SPVAR_ELIMIT (-7)    /* size beyond a documented library limit */
+
+/* Library limits (SPVAR_ELIMIT beyond them). */
+#define SPVAR_MAX_N 32768        /* spins per problem (shared-memory spin state) */
+#define SPVAR_MAX_DEGREE 32      /* couplers per spin */
+#define SPVAR_MAX_SWEEPS 1048574 /* sweeps per sample: 2^20 - 2 (slot 2^20-1 = initial state) */
+#define SPVAR_MAX_PHASE 4095     /* phase index < 2^12 */
+#define SPVAR_MAX_SAMPLES 16384  /* samples per (problem, phase) */
+
+const char *spvar_strerror(int code);
+
+/* Number of CUDA devices visible, or a negative code.  Loads no kernel. */
+int spvar_device_count(int *count);
+
+/* ------------------------------------------------------------------ */
+/* Problem (Sec. I)                                                    */
+/* ------------------------------------------------------------------ */
+typedef struct spvar_problem spvar_problem;
+
+typedef struct spvar_problem_info {
+    int32_t n;            /* spins */
+    int32_t nnz;          /* CSR entries (2 x couplers) */
+    int32_t ncol;         /* colour classes of the sweep order */
+    int32_t maxdeg;       /* largest row length */
+    int32_t dmax;         /* 2 * max_i (sum_j |J_ij| + |h_i|): largest flip cost */
+    int32_t hzero;        /* 1 iff every h_i == 0 */
+    int32_t pm1;          /* 1 iff every J_ij is -1 or +1 */
+    int32_t energy_scale; /* integer energies = real energies x energy_scale */
+    int64_t offset;       /* constant term */
+} spvar_problem_info;
+
+/* Host helper: edge list -> symmetric CSR with ascending columns.
+ * ei, ej, J: host [m], 0 <= ei, ej < n, ei != ej, each pair at most once.
+ * row_ptr: host [n+1]; col, val: host [2m].  SPVAR_EINVAL on a self loop,
+ * an index out of range or a repeated pair. */
+int spvar_csr_from_edges(int32_t n, int64_t m, const int32_t *ei, const int32_t *ej,
+                         const int32_t *J, int32_t *row_ptr, int32_t *col, int32_t *val);
+
+/* Create a problem on the current device from host CSR arrays
+ * (row_ptr [n+1], col/val [row_ptr[n]], h [n]; all host, copied).
+ * Validates symmetry, ordering, index ranges and the int32 energy range
+ * (sum_ij |J_ij| + sum_i |h_i| < 2^30), computes the colour classes of the
+ * sweep order (bipartite: BFS distance parity from the lowest index of each
+ * component; otherwise first-fit greedy in index order) and uploads the
+ * sweep layout.  energy_scale >= 1 only enters the acceptance table.
+ * Errors: EINVAL, EOVERFLOW, ELIMIT (n > SPVAR_MAX_N, degree >
+ * SPVAR_MAX_DEGREE, |J| > 32767), ENOMEM, ECUDA. */
+int spvar_problem_create(int32_t n, const int32_t *row_ptr, const int32_t *col,
+                         const int32_t *val, const int32_t *h, int64_t offset,
+                         int32_t energy_scale, void *stream, spvar_problem **out);
+
+void spvar_problem_destroy(spvar_problem *p);
+
+int spvar_problem_get_info(const spvar_problem *p, spvar_problem_info *info);
+
+/* Copy the problem back to host buffers (row_ptr [n+1], col/val [nnz],
+ * h [n], colour [n]); any pointer may be NULL.  Synchronises the stream. */
+int spvar_problem_download(const spvar_problem *p, int32_t *row_ptr, int32_t *col,
+                           int32_t *val, int32_t *h, int32_t *colour, void *stream);
+
+/* ------------------------------------------------------------------ */
+/* Annealing schedule                                                  */
+/* ------------------------------------------------------------------ */
+/* Host: beta[t] = beta0 * (beta1/beta0)^(t/(T-1)), t = 0..T-1 (T = 1: beta0). */
+int spvar_beta_geometric(int32_t T, double beta0, double beta1, double *beta);
+
+/* Host: acceptance table thr [T][dmax+1],
+ * thr[t][d] = min(2^32-1, floor(2^32 * exp(-beta[t] * d / energy_scale))),
+ * computed in double.  A flip that raises the energy by d > 0 at sweep t is
+ * accepted iff the flip's random word is < thr[t][d]. */
+int spvar_thresholds(int32_t T, const double *beta, int32_t dmax, int32_t energy_scale,
+                     uint32_t *thr);
+
+/* ------------------------------------------------------------------ */
+/* Sampler: simulated annealing (Sec. III.A; Alg. 1 "obtain sample")   */
+/* ------------------------------------------------------------------ */
+/* One independent annealing run per sample r < num_samples.
+ * Initial state: s_i = +1 iff the top bit of the random word at sweep slot
+ * 2^20-1 is set.  Sweep t = 0..num_sweeps-1 visits the colour classes in
+ * increasing order and, inside a class (no two spins coupled), proposes
+ * each spin once: dE = -2 s_i (h_i + sum_j J_ij s_j); accepted iff dE <= 0
+ * or word < thr[t * thr_stride + dE].
+ *   thr       device [num_sweeps][thr_stride], thr_stride >= dmax + 1
+ *   spins     device [num_samples][ceil(n/32)] final states (bit-packed)
+ *   energies  device [num_samples] final energies INCLUDING the offset
+ * Errors: EINVAL (sizes, thr_stride <= dmax), ELIMIT, ECUDA. */
+int spvar_sample(const spvar_problem *p, int32_t num_sweeps, const uint32_t *thr,
+                 int32_t thr_stride, int32_t num_samples, uint64_t seed, uint32_t start,
+                 uint32_t phase, uint32_t *spins, int64_t *energies, void *stream);
+
+/* ------------------------------------------------------------------ */
+/* Persistence (Alg. 1: elite sample, mean value, fixing rule)          */
+/* ------------------------------------------------------------------ */
+/* k = ceil(elite_threshold * num_samples) (clamped to [1, num_samples])
+ * lowest-energy samples, ordered by (energy, sample index), form the elite.
+ * If canon is 1 (or -1 and every h is 0) each elite row is multiplied by
+ * its value at the reference spin rho = the lowest-index spin of maximum
+ * degree, which breaks the two-fold degeneracy of zero-bias problems
+ * (Sec. II.C).  counts[i] = number of elite rows with s_i = +1;
+ * fixed[i] = sign(2 counts[i] - k) if fix_den * |2 counts[i] - k| >=
+ * fix_num * k (fixing_threshold = fix_num / fix_den, 0 < fix_num <= fix_den),
+ * else 0.
+ *   spins, energies  device, as written by spvar_sample
+ *   elite            device [k] out: sample indices in elite order
+ *   counts           device [n] out;  fixed  device int8 [n] out
+ *   nfixed           device [1] out: number of fixed spins
+ *   k_out            host, may be NULL: the elite size used */
+int spvar_persistence(const spvar_problem *p, int32_t num_samples, const uint32_t *spins,
+                      const int64_t *energies, double elite_threshold, int32_t fix_num,
+                      int32_t fix_den, int32_t canon, int32_t *elite, int32_t *counts,
+                      int8_t *fixed, int32_t *nfixed, int32_t *k_out, void *stream);
+
+/* ------------------------------------------------------------------ */
+/* Fold and compact (Alg. 1: update J and h)                            */
+/* ------------------------------------------------------------------ */
+/* New problem over the free spins (fixed[i] == 0), renumbered in increasing
+ * old index: h'_i = h_i + sum_{j fixed} J_ij v_j, offset' = offset +
+ * sum_{i fixed} h_i v_i + sum_{i<j both fixed} J_ij v_i v_j, couplers
+ * between free spins kept, colour classes inherited.
+ *   fixed       device int8 [n] (0, +1, -1)
+ *   old_of_new  device [n] out: old index of each new spin (first n' used)
+ * Synchronises the stream (the new size is read back). */
+int spvar_reduce(const spvar_problem *p, const int8_t *fixed, int32_t *old_of_new,
+                 void *stream, spvar_problem **out);
+
+/* ------------------------------------------------------------------ */
+/* Multi-start SPVAR (Alg. 2) on one or many problems                   */
+/* ------------------------------------------------------------------ */
+typedef struct spvar_params {
+    int32_t num_starts;          /* independent starts per problem */
+    int32_t fixing_sample_size;  /* samples in each SPVAR phase */
+    int32_t solving_sample_size; /* samples of the final reduced problem (0: none) */
+    int32_t num_sweeps;          /* sweeps per annealing run */
+    double beta0, beta1;         /* geometric schedule endpoints */
+    double elite_threshold;      /* elite fraction */
+    int32_t fix_num, fix_den;    /* fixing_threshold = fix_num / fix_den */
+    int32_t iterate;             /* 1: repeat SPVAR while spins remain (ISPVAR) */
+    int32_t max_fix_phases;      /* SPVAR phases per start, >= 1 */
+    int32_t canon;               /* -1: when h == 0; 0: never; 1: always */
+    int32_t form;                /* SPVAR_FORM_BATCHED or SPVAR_FORM_PLAIN */
+    int32_t replicas_per_block;  /* 0: autotune; else a multiple of 4 */
+} spvar_params;
+
+#define SPVAR_FORM_BATCHED 0 /* every start of every problem in one persistent launch per phase */
+#define SPVAR_FORM_PLAIN 1   /* one start at a time, one launch per kernel and start */
+
+/* Output buffers; P = max_fix_phases + 1 phase slots, Smax = max sample
+ * size, n_p = spins of problem p.  Rows are ordered problem-major then
+ * start.  Any pointer may be NULL (not written).  device = 1: pointers are
+ * device memory written on the stream without synchronising; device = 0:
+ * host memory, the call synchronises. */
+typedef struct spvar_result {
+    int32_t device;
+    int64_t *energies;    /* [starts][P][Smax] recorded full-problem energies */
+    int32_t *counts;      /* [starts][P] samples recorded per phase slot */
+    int32_t *nfree;       /* [starts][P] free spins when the phase sampled */
+    int32_t *nphases;     /* [starts] phase slots used */
+    int8_t *fixed;        /* [sum_p num_starts * n_p] final fix maps, original order */
+    int64_t *best_energy; /* [starts] */
+    int8_t *best_state;   /* [sum_p num_starts * n_p] best assignment (+1/-1) */
+} spvar_result;
+
+typedef struct spvar_plan spvar_plan;
+
+/* Build an executable plan: device workspace for every start, acceptance
+ * table, work queues and the captured per-phase CUDA graph.
+ * problems: host array [nproblems] of handles (all on the current device);
+ * the same table is used for all problems (dmax = largest dmax, scale of
+ * problems[0]; every problem must share energy_scale).
+ * Errors: EINVAL, ELIMIT, ENOMEM, EBUDGET (workspace > budget_bytes when
+ * budget_bytes > 0), ECUDA. */
+int spvar_plan_create(const spvar_problem *const *problems, int32_t nproblems,
+                      const spvar_params *prm, size_t budget_bytes, void *stream,
+                      spvar_plan **out);
+
+/* Device bytes the plan holds. */
+size_t spvar_plan_workspace_bytes(const spvar_plan *plan);
+
+/* Run Alg. 2 for every start of every problem.  seeds: host [nproblems]
+ * (problem p uses key seeds[p]; start s of it uses counter word start = s). */
+int spvar_plan_run(spvar_plan *plan, const uint64_t *seeds, const spvar_result *res,
+                   void *stream);
+
+void spvar_plan_destroy(spvar_plan *plan);
+
+/* Convenience: plan_create + plan_run + plan_destroy for one problem. */
+int spvar_solve(const spvar_problem *p, const spvar_params *prm, uint64_t seed,
+                const spvar_result *res, void *stream);
+
+/* Work statistics of the last plan_run: spin-flip attempts (sum over
+ * phases of samples x sweeps x free spins) and phases executed. */
+int spvar_plan_stats(const spvar_plan *plan, int64_t *attempts, int32_t *phases);
+
+/* Profiling: when on, plan_run waits for every phase and adds up the
+ * duration of the sweep kernel (CUDA events recorded on the run's stream
+ * around each sweep launch, also inside the captured graph). */
+int spvar_plan_set_profiling(spvar_plan *plan, int32_t on);
+
+/* Sum of sweep-kernel durations (ms) and sweep launches of the last
+ * profiled plan_run. */
+int spvar_plan_sweep_time(const spvar_plan *plan, double *total_ms, int32_t *launches);
+
+/* The sweep launch shape the plan chose (autotuned or requested): threads
+ * per CTA, replicas per CTA, 1 if the layout is staged in shared memory,
+ * persistent grid size. */
+int spvar_plan_shape(const spvar_plan *plan, int32_t *block, int32_t *replicas_per_block,
+                     int32_t *staged, int32_t *grid);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,487 @@
+// C ABI of the library: problem construction (Sec. I problem statement),
+// annealing schedule, and the standalone sample / persistence / reduce calls
+// of Alg. 1.  Host code only; kernels live in sweep.cu and persist.cu.
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "spvar_internal.h"
+
+using namespace spvar;
+
+namespace {
+
+inline cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+int device_smem_optin()
+{
+    int dev = 0, v = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    return v;
+}
+
+int device_sms()
+{
+    int dev = 0, v = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    return v > 0 ? v : 1;
+}
+
+// Colour classes of the sweep order.  Bipartite graphs: each connected
+// component 2-coloured by the parity of its BFS distance from the component's
+// lowest-index vertex.  Otherwise: first-fit greedy in increasing index.
+int colour_classes(int n, const int32_t *rp, const int32_t *col, std::vector<int32_t> &c)
+{
+    c.assign(n, -1);
+    std::vector<int32_t> queue;
+    queue.reserve(n);
+    for (int root = 0; root < n; ++root) {
+        if (c[root] >= 0) continue;
+        c[root] = 0;
+        queue.clear();
+        queue.push_back(root);
+        for (size_t head = 0; head < queue.size(); ++head) {
+            const int v = queue[head];
+            for (int p = rp[v]; p < rp[v + 1]; ++p)
+                if (c[col[p]] < 0) {
+                    c[col[p]] = c[v] ^ 1;
+                    queue.push_back(col[p]);
+                }
+        }
+    }
+    bool ok = true;
+    int ncol = n > 0 ? 1 : 0;
+    for (int v = 0; v < n && ok; ++v) {
+        if (c[v] == 1) ncol = 2;
+        for (int p = rp[v]; p < rp[v + 1]; ++p)
+            if (c[col[p]] == c[v]) { ok = false; break; }
+    }
+    if (ok) return ncol;
+    ncol = 0;
+    std::vector<int32_t> mark(n + 1, -1);
+    for (int v = 0; v < n; ++v) {
+        for (int p = rp[v]; p < rp[v + 1]; ++p)
+            if (col[p] < v) mark[c[col[p]]] = v;
+        int k = 0;
+        while (mark[k] == v) ++k;
+        c[v] = k;
+        ncol = std::max(ncol, k + 1);
+    }
+    return ncol;
+}
+
+}  // namespace
+
+namespace spvar {
+
+size_t prob_blob_bytes(int cap_n, int cap_nnz, int maxdeg)
+{
+    size_t b = align256(sizeof(DevProb));
+    b += align256(4 * ((size_t)cap_n + 1));          // row_ptr
+    b += 2 * align256(4 * (size_t)cap_nnz);          // col, val
+    b += 2 * align256(4 * (size_t)cap_n);            // h, colour
+    b += align256(4 * ((size_t)kMaxColours + 1));    // cptr
+    b += 3 * align256(4 * (size_t)cap_n);            // idx_of_pos, pos_of_idx, meta
+    b += align256(4 * (size_t)maxdeg * cap_n);       // ell
+    return b;
+}
+
+void prob_carve(DevProb *hdr, void *blob, int cap_n, int cap_nnz, int maxdeg)
+{
+    char *p = static_cast<char *>(blob);
+    size_t o = align256(sizeof(DevProb));
+    auto take = [&](size_t bytes) {
+        char *r = p + o;
+        o += align256(bytes);
+        return r;
+    };
+    hdr->cap_n = cap_n;
+    hdr->cap_nnz = cap_nnz;
+    hdr->maxdeg = maxdeg;
+    hdr->row_ptr = (int32_t *)take(4 * ((size_t)cap_n + 1));
+    hdr->col = (int32_t *)take(4 * (size_t)cap_nnz);
+    hdr->val = (int32_t *)take(4 * (size_t)cap_nnz);
+    hdr->h = (int32_t *)take(4 * (size_t)cap_n);
+    hdr->colour = (int32_t *)take(4 * (size_t)cap_n);
+    hdr->cptr = (int32_t *)take(4 * ((size_t)kMaxColours + 1));
+    hdr->idx_of_pos = (int32_t *)take(4 * (size_t)cap_n);
+    hdr->pos_of_idx = (int32_t *)take(4 * (size_t)cap_n);
+    hdr->meta = (uint32_t *)take(4 * (size_t)cap_n);
+    hdr->ell = (uint32_t *)take(4 * (size_t)maxdeg * cap_n);
+}
+
+}  // namespace spvar
+
+extern "C" {
+
+const char *spvar_strerror(int code)
+{
+    switch (code) {
+    case SPVAR_OK: return "ok";
+    case SPVAR_EINVAL: return "invalid argument or malformed problem";
+    case SPVAR_EOVERFLOW: return "values overflow the 32-bit energy arithmetic";
+    case SPVAR_ENOMEM: return "out of memory";
+    case SPVAR_EBUDGET: return "request exceeds the device-memory budget";
+    case SPVAR_ETIMEOUT: return "bounded device wait timed out";
+    case SPVAR_ECUDA: return "CUDA runtime error";
+    case SPVAR_ELIMIT: return "size beyond a library limit";
+    default: return "unknown error";
+    }
+}
+
+int spvar_device_count(int *count)
+{
+    if (!count) return SPVAR_EINVAL;
+    int c = 0;
+    if (cudaGetDeviceCount(&c) != cudaSuccess) c = 0;
+    *count = c;
+    return SPVAR_OK;
+}
+
+int spvar_csr_from_edges(int32_t n, int64_t m, const int32_t *ei, const int32_t *ej,
+                         const int32_t *J, int32_t *row_ptr, int32_t *col, int32_t *val)
+{
+    if (n < 0 || m < 0 || !row_ptr || (m > 0 && (!ei || !ej || !J || !col || !val)))
+        return SPVAR_EINVAL;
+    if (2 * m > INT32_MAX) return SPVAR_ELIMIT;
+    std::vector<int64_t> deg((size_t)n + 1, 0);
+    for (int64_t e = 0; e < m; ++e) {
+        if (ei[e] < 0 || ei[e] >= n || ej[e] < 0 || ej[e] >= n || ei[e] == ej[e]) return SPVAR_EINVAL;
+        deg[ei[e]]++;
+        deg[ej[e]]++;
+    }
+    row_ptr[0] = 0;
+    for (int i = 0; i < n; ++i) row_ptr[i + 1] = row_ptr[i] + (int32_t)deg[i];
+    // counting placement, then sort each row's (col, val) pairs
+    std::vector<int32_t> fill(row_ptr, row_ptr + n);
+    for (int64_t e = 0; e < m; ++e) {
+        int32_t a = ei[e], b = ej[e];
+        col[fill[a]] = b; val[fill[a]++] = J[e];
+        col[fill[b]] = a; val[fill[b]++] = J[e];
+    }
+    std::vector<std::pair<int32_t, int32_t>> row;
+    for (int i = 0; i < n; ++i) {
+        row.clear();
+        for (int p = row_ptr[i]; p < row_ptr[i + 1]; ++p) row.emplace_back(col[p], val[p]);
+        std::sort(row.begin(), row.end(),
+                  [](const std::pair<int32_t, int32_t> &x, const std::pair<int32_t, int32_t> &y) {
+                      return x.first < y.first;
+                  });
+        for (size_t q = 0; q < row.size(); ++q) {
+            if (q > 0 && row[q].first == row[q - 1].first) return SPVAR_EINVAL;
+            col[row_ptr[i] + q] = row[q].first;
+            val[row_ptr[i] + q] = row[q].second;
+        }
+    }
+    return SPVAR_OK;
+}
+
+int spvar_problem_create(int32_t n, const int32_t *row_ptr, const int32_t *col, const int32_t *val,
+                         const int32_t *h, int64_t offset, int32_t energy_scale, void *stream,
+                         spvar_problem **out)
+{
+    if (!out) return SPVAR_EINVAL;
+    *out = nullptr;
+    if (n < 0 || energy_scale < 1 || !row_ptr || (n > 0 && !h)) return SPVAR_EINVAL;
+    if (n > SPVAR_MAX_N) return SPVAR_ELIMIT;
+    if (row_ptr[0] != 0) return SPVAR_EINVAL;
+    for (int i = 0; i < n; ++i)
+        if (row_ptr[i + 1] < row_ptr[i]) return SPVAR_EINVAL;
+    const int nnz = row_ptr[n];
+    if (nnz > 0 && (!col || !val)) return SPVAR_EINVAL;
+    int maxdeg = 0;
+    long long total = 0;
+    long long maxrow = 0;
+    for (int i = 0; i < n; ++i) {
+        const int d = row_ptr[i + 1] - row_ptr[i];
+        if (d > SPVAR_MAX_DEGREE) return SPVAR_ELIMIT;
+        maxdeg = std::max(maxdeg, d);
+        long long rowsum = std::llabs((long long)h[i]);
+        total += 2 * std::llabs((long long)h[i]);
+        for (int p = row_ptr[i]; p < row_ptr[i + 1]; ++p) {
+            const int j = col[p];
+            if (j < 0 || j >= n || j == i) return SPVAR_EINVAL;
+            if (p > row_ptr[i] && col[p - 1] >= j) return SPVAR_EINVAL;
+            if (val[p] == 0) return SPVAR_EINVAL;
+            if (val[p] > 32767 || val[p] < -32767) return SPVAR_ELIMIT;
+            // symmetric partner (j, i) with the same value
+            const int32_t *b = col + row_ptr[j], *e = col + row_ptr[j + 1];
+            const int32_t *f = std::lower_bound(b, e, i);
+            if (f == e || *f != i || val[f - col] != val[p]) return SPVAR_EINVAL;
+            rowsum += std::llabs((long long)val[p]);
+            total += std::llabs((long long)val[p]);
+        }
+        maxrow = std::max(maxrow, rowsum);
+        if (total >= (1ll << 31)) return SPVAR_EOVERFLOW;
+    }
+    if (maxrow > 32767) return SPVAR_ELIMIT;  // h' and dmax/2 must fit int16
+
+    std::vector<int32_t> colour;
+    const int ncol = colour_classes(n, row_ptr, col, colour);
+    if (ncol > kMaxColours) return SPVAR_ELIMIT;
+
+    const int cap_n = std::max(n, 1), cap_nnz = std::max(nnz, 1), md = std::max(maxdeg, 1);
+    Problem *P = new (std::nothrow) Problem();
+    if (!P) return SPVAR_ENOMEM;
+    cudaGetDevice(&P->device);
+    P->blob_bytes = prob_blob_bytes(cap_n, cap_nnz, md);
+    if (cudaMalloc(&P->blob, P->blob_bytes) != cudaSuccess) {
+        delete P;
+        cudaGetLastError();
+        return SPVAR_ENOMEM;
+    }
+    DevProb &H = P->hdr;
+    std::memset(&H, 0, sizeof(H));
+    prob_carve(&H, P->blob, cap_n, cap_nnz, md);
+    P->dev = static_cast<DevProb *>(P->blob);
+    H.n = n;
+    H.nnz = nnz;
+    H.ncol = ncol;
+    H.dmax = (int32_t)(2 * maxrow);
+    H.offset = offset;
+    H.scale = energy_scale;
+    H.hzero = 1;
+    H.pm1 = 1;
+    for (int i = 0; i < n; ++i) if (h[i] != 0) H.hzero = 0;
+    for (int p = 0; p < nnz; ++p) if (val[p] != 1 && val[p] != -1) H.pm1 = 0;
+    H.rho = -1;
+    for (int i = 0, best = -1; i < n; ++i)
+        if (row_ptr[i + 1] - row_ptr[i] > best) { best = row_ptr[i + 1] - row_ptr[i]; H.rho = i; }
+
+    // sweep layout: positions colour class by colour class, index ascending
+    std::vector<int32_t> cptr(kMaxColours + 1, 0), idx_of_pos(cap_n, 0), pos_of_idx(cap_n, 0);
+    std::vector<uint32_t> meta(cap_n, 0), ell((size_t)md * cap_n, 0);
+    for (int i = 0; i < n; ++i) cptr[colour[i] + 1]++;
+    for (int c = 0; c < ncol; ++c) cptr[c + 1] += cptr[c];
+    for (int c = ncol + 1; c <= kMaxColours; ++c) cptr[c] = cptr[ncol];
+    {
+        std::vector<int32_t> fill(cptr.begin(), cptr.end());
+        for (int i = 0; i < n; ++i) {
+            const int pos = fill[colour[i]]++;
+            idx_of_pos[pos] = i;
+            pos_of_idx[i] = pos;
+        }
+    }
+    for (int i = 0; i < n; ++i) {
+        const int pos = pos_of_idx[i];
+        const int deg = row_ptr[i + 1] - row_ptr[i];
+        meta[pos] = ((uint32_t)(h[i] & 0xFFFF) << 16) | (uint32_t)deg;
+        for (int d = 0; d < deg; ++d) {
+            const int p = row_ptr[i] + d;
+            ell[(size_t)d * cap_n + pos] =
+                ((uint32_t)pos_of_idx[col[p]] & 0xFFFFu) | ((uint32_t)(val[p] & 0xFFFF) << 16);
+        }
+    }
+
+    cudaStream_t st = as_stream(stream);
+    bool ok = true;
+    auto up = [&](void *dst, const void *src, size_t bytes) {
+        if (bytes && ok) ok = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st) == cudaSuccess;
+    };
+    up(P->dev, &H, sizeof(DevProb));
+    up(H.row_ptr, row_ptr, 4 * ((size_t)n + 1));
+    up(H.col, col, 4 * (size_t)nnz);
+    up(H.val, val, 4 * (size_t)nnz);
+    up(H.h, h, 4 * (size_t)n);
+    up(H.colour, colour.data(), 4 * (size_t)n);
+    up(H.cptr, cptr.data(), 4 * cptr.size());
+    up(H.idx_of_pos, idx_of_pos.data(), 4 * (size_t)n);
+    up(H.pos_of_idx, pos_of_idx.data(), 4 * (size_t)n);
+    up(H.meta, meta.data(), 4 * (size_t)n);
+    up(H.ell, ell.data(), 4 * ell.size());
+    if (ok) ok = cudaStreamSynchronize(st) == cudaSuccess;
+    if (!ok) {
+        cudaFree(P->blob);
+        delete P;
+        cudaGetLastError();
+        return SPVAR_ECUDA;
+    }
+    *out = reinterpret_cast<spvar_problem *>(P);
+    return SPVAR_OK;
+}
+
+void spvar_problem_destroy(spvar_problem *p)
+{
+    if (!p) return;
+    Problem *P = reinterpret_cast<Problem *>(p);
+    cudaFree(P->blob);
+    delete P;
+}
+
+int spvar_problem_get_info(const spvar_problem *p, spvar_problem_info *info)
+{
+    if (!p || !info) return SPVAR_EINVAL;
+    const DevProb &H = reinterpret_cast<const Problem *>(p)->hdr;
+    info->n = H.n;
+    info->nnz = H.nnz;
+    info->ncol = H.ncol;
+    info->maxdeg = H.maxdeg;
+    info->dmax = H.dmax;
+    info->hzero = H.hzero;
+    info->pm1 = H.pm1;
+    info->energy_scale = H.scale;
+    info->offset = H.offset;
+    return SPVAR_OK;
+}
+
+int spvar_problem_download(const spvar_problem *p, int32_t *row_ptr, int32_t *col, int32_t *val,
+                           int32_t *h, int32_t *colour, void *stream)
+{
+    if (!p) return SPVAR_EINVAL;
+    const DevProb &H = reinterpret_cast<const Problem *>(p)->hdr;
+    cudaStream_t st = as_stream(stream);
+    auto dn = [&](void *dst, const void *src, size_t bytes) -> bool {
+        return !dst || !bytes || cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, st) == cudaSuccess;
+    };
+    bool ok = dn(row_ptr, H.row_ptr, 4 * ((size_t)H.n + 1)) && dn(col, H.col, 4 * (size_t)H.nnz) &&
+              dn(val, H.val, 4 * (size_t)H.nnz) && dn(h, H.h, 4 * (size_t)H.n) &&
+              dn(colour, H.colour, 4 * (size_t)H.n);
+    if (ok) ok = cudaStreamSynchronize(st) == cudaSuccess;
+    return ok ? SPVAR_OK : SPVAR_ECUDA;
+}
+
+int spvar_beta_geometric(int32_t T, double beta0, double beta1, double *beta)
+{
+    if (T < 1 || !beta || !(beta0 > 0.0) || !(beta1 > 0.0)) return SPVAR_EINVAL;
+    for (int t = 0; t < T; ++t)
+        beta[t] = (T == 1) ? beta0 : beta0 * std::pow(beta1 / beta0, (double)t / (double)(T - 1));
+    return SPVAR_OK;
+}
+
+int spvar_thresholds(int32_t T, const double *beta, int32_t dmax, int32_t energy_scale,
+                     uint32_t *thr)
+{
+    if (T < 0 || dmax < 0 || energy_scale < 1 || (T > 0 && (!beta || !thr))) return SPVAR_EINVAL;
+    const size_t w = (size_t)dmax + 1;
+    for (int t = 0; t < T; ++t) {
+        if (!(beta[t] >= 0.0)) return SPVAR_EINVAL;
+        for (int d = 0; d <= dmax; ++d) {
+            const double x = std::floor(std::ldexp(std::exp(-beta[t] * (double)d / (double)energy_scale), 32));
+            thr[(size_t)t * w + d] = (x >= 4294967295.0) ? 0xFFFFFFFFu : (uint32_t)x;
+        }
+    }
+    return SPVAR_OK;
+}
+
+int spvar_sample(const spvar_problem *p, int32_t num_sweeps, const uint32_t *thr, int32_t thr_stride,
+                 int32_t num_samples, uint64_t seed, uint32_t start, uint32_t phase, uint32_t *spins,
+                 int64_t *energies, void *stream)
+{
+    if (!p) return SPVAR_EINVAL;
+    const Problem *P = reinterpret_cast<const Problem *>(p);
+    const DevProb &H = P->hdr;
+    if (num_sweeps < 0 || num_samples < 0 || phase > SPVAR_MAX_PHASE) return SPVAR_EINVAL;
+    if (num_sweeps > SPVAR_MAX_SWEEPS || num_samples > SPVAR_MAX_SAMPLES) return SPVAR_ELIMIT;
+    if (num_samples == 0) return SPVAR_OK;
+    if ((num_sweeps > 0 && !thr) || thr_stride < H.dmax + 1 || !energies || (H.n > 0 && !spins))
+        return SPVAR_EINVAL;
+    const int quads = ceil_div(num_samples, 4);
+    const int sms = device_sms();
+    const int Q = std::max(1, std::min(8, quads / (2 * sms)));
+    const int block = (H.n >= 512) ? 256 : 128;
+    const int optin = device_smem_optin();
+    bool stage = sweep_smem_bytes(H.n, Q, thr_stride, H.maxdeg, true) <= (size_t)optin;
+    size_t smem = sweep_smem_bytes(H.n, Q, thr_stride, H.maxdeg, stage);
+    if (smem > (size_t)optin) return SPVAR_ELIMIT;
+
+    SweepLaunch L;
+    std::memset(&L, 0, sizeof(L));
+    L.single.prob = P->dev;
+    L.single.spins = spins;
+    L.single.energies = energies;
+    L.single.seed = seed;
+    L.single.S = num_samples;
+    L.single.W = ceil_div(std::max(H.n, 0), 32);
+    L.single.start = start;
+    L.single.phase = phase;
+    L.thr = thr;
+    L.thr_stride = thr_stride;
+    L.T = num_sweeps;
+    L.Q = Q;
+    L.stage_ell = stage ? 1 : 0;
+    L.max_n = H.n;
+    L.max_deg = H.maxdeg;
+    const int grid = ceil_div(quads, Q);
+    SPVAR_CUDA_TRY(launch_sweep(L, H.pm1 != 0, block, grid, smem, as_stream(stream)));
+    return SPVAR_OK;
+}
+
+int spvar_persistence(const spvar_problem *p, int32_t num_samples, const uint32_t *spins,
+                      const int64_t *energies, double elite_threshold, int32_t fix_num,
+                      int32_t fix_den, int32_t canon, int32_t *elite, int32_t *counts,
+                      int8_t *fixed, int32_t *nfixed, int32_t *k_out, void *stream)
+{
+    if (!p) return SPVAR_EINVAL;
+    const Problem *P = reinterpret_cast<const Problem *>(p);
+    const DevProb &H = P->hdr;
+    if (num_samples < 1 || !(elite_threshold > 0.0) || !(elite_threshold <= 1.0) || fix_num <= 0 ||
+        fix_den <= 0 || fix_num > fix_den || canon < -1 || canon > 1)
+        return SPVAR_EINVAL;
+    if (num_samples > elite_max_samples()) return SPVAR_ELIMIT;
+    if (!energies || !elite || !nfixed || (H.n > 0 && (!spins || !fixed))) return SPVAR_EINVAL;
+    // k = ceil(elite * S), clamped to [1, S]
+    const double x = std::ceil(elite_threshold * (double)num_samples);
+    int k = (x >= (double)num_samples) ? num_samples : (int)x;
+    k = std::max(1, std::min(k, num_samples));
+    const int ce = (canon < 0) ? H.hzero : canon;
+    cudaStream_t st = as_stream(stream);
+    SPVAR_CUDA_TRY(launch_elite_single(energies, num_samples, k, elite, st));
+    SPVAR_CUDA_TRY(launch_count_single(P->dev, H.n, spins, ceil_div(H.n, 32), elite, k, ce, fix_num,
+                                       fix_den, counts, fixed, nfixed, st));
+    if (k_out) *k_out = k;
+    return SPVAR_OK;
+}
+
+int spvar_reduce(const spvar_problem *p, const int8_t *fixed, int32_t *old_of_new, void *stream,
+                 spvar_problem **out)
+{
+    if (!p || !out) return SPVAR_EINVAL;
+    *out = nullptr;
+    const Problem *S = reinterpret_cast<const Problem *>(p);
+    const DevProb &H = S->hdr;
+    if (H.n > 0 && (!fixed || !old_of_new)) return SPVAR_EINVAL;
+    Problem *D = new (std::nothrow) Problem();
+    if (!D) return SPVAR_ENOMEM;
+    D->device = S->device;
+    D->blob_bytes = prob_blob_bytes(H.cap_n, H.cap_nnz, H.maxdeg);
+    int32_t *scratch = nullptr;
+    if (cudaMalloc(&D->blob, D->blob_bytes) != cudaSuccess) {
+        delete D;
+        cudaGetLastError();
+        return SPVAR_ENOMEM;
+    }
+    if (cudaMalloc(&scratch, 8 * (size_t)H.cap_n) != cudaSuccess) {
+        cudaFree(D->blob);
+        delete D;
+        cudaGetLastError();
+        return SPVAR_ENOMEM;
+    }
+    std::memset(&D->hdr, 0, sizeof(DevProb));
+    prob_carve(&D->hdr, D->blob, H.cap_n, H.cap_nnz, H.maxdeg);
+    D->dev = static_cast<DevProb *>(D->blob);
+    cudaStream_t st = as_stream(stream);
+    bool ok = cudaMemcpyAsync(D->dev, &D->hdr, sizeof(DevProb), cudaMemcpyHostToDevice, st) == cudaSuccess;
+    if (ok) ok = launch_reduce_single(S->dev, D->dev, fixed, old_of_new, scratch, st) == cudaSuccess;
+    DevProb back;
+    if (ok) ok = cudaMemcpyAsync(&back, D->dev, sizeof(DevProb), cudaMemcpyDeviceToHost, st) == cudaSuccess;
+    if (ok) ok = cudaStreamSynchronize(st) == cudaSuccess;
+    cudaFree(scratch);
+    if (!ok) {
+        cudaFree(D->blob);
+        delete D;
+        cudaGetLastError();
+        return SPVAR_ECUDA;
+    }
+    D->hdr = back;
+    *out = reinterpret_cast<spvar_problem *>(D);
+    return SPVAR_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,445 @@
+// Persistence pass (Alg. 1: elite sample, mean value of each variable,
+// fixing rule), fold/compact (Alg. 1: update J and h) and the per-start state
+// machine of Multi-start SPVAR (Alg. 2).
+//
+// Elite selection sorts (energy, index) keys of one sample set in shared
+// memory; the count kernel reads only the k elite rows of the bit-packed
+// sample (one broadcast word load per warp and row); fold/compact runs one
+// 1024-thread CTA per reduction with block-wide scans, writing the new CSR,
+// the inherited colour classes and the sweep layout of the smaller problem.
+#include <climits>
+
+#include "persist.cuh"
+
+namespace spvar {
+
+__device__ void reduce_core(const DevProb *S, DevProb *D, const int8_t *fixed, int32_t *old_of_new,
+                            int32_t *scratch)
+{
+    __shared__ int s_warp[32];
+    __shared__ unsigned long long s_off;
+    __shared__ int s_hnz;
+    __shared__ long long s_rho_key;
+    const int tid = threadIdx.x, B = blockDim.x;
+    const int n = S->n;
+    int32_t *new_of_old = scratch;          // [n]
+    int32_t *rowcnt = scratch + S->cap_n;   // [n']
+    if (tid == 0) {
+        s_off = 0ull;
+        s_hnz = 0;
+        s_rho_key = -1;
+    }
+    __syncthreads();
+
+    // free spins keep their order: new index = exclusive count of free spins before
+    int carry = 0;
+    for (int base = 0; base < n; base += B) {
+        const int i = base + tid;
+        const int f = (i < n && fixed[i] == 0) ? 1 : 0;
+        int tot;
+        const int ex = block_scan_excl(f, s_warp, &tot);
+        if (i < n) {
+            new_of_old[i] = f ? carry + ex : -1;
+            if (f) old_of_new[carry + ex] = i;
+        }
+        carry += tot;
+    }
+    const int m = carry;
+    __syncthreads();
+
+    // h'_i = h_i + sum_{j fixed} J_ij v_j ;  offset' = offset + sum_{i fixed} h_i v_i
+    //        + sum_{i<j both fixed} J_ij v_i v_j
+    long long off_part = 0;
+    for (int i = tid; i < n; i += B) {
+        const int vi = fixed[i];
+        long long hf = S->h[i];
+        int nfree = 0;
+        for (int p = S->row_ptr[i]; p < S->row_ptr[i + 1]; ++p) {
+            const int j = S->col[p];
+            const int vj = fixed[j];
+            if (vi) {
+                if (vj && j > i) off_part += (long long)S->val[p] * vi * vj;
+            } else {
+                if (vj) hf += (long long)S->val[p] * vj;
+                else ++nfree;
+            }
+        }
+        if (vi) {
+            off_part += (long long)S->h[i] * vi;
+        } else {
+            const int a = new_of_old[i];
+            D->h[a] = (int32_t)hf;
+            rowcnt[a] = nfree;
+            if (hf != 0) atomicOr(&s_hnz, 1);
+        }
+    }
+    atomicAdd(&s_off, (unsigned long long)off_part);
+    __syncthreads();
+
+    // row pointers of the free-free couplers
+    carry = 0;
+    for (int base = 0; base < m; base += B) {
+        const int a = base + tid;
+        const int c = (a < m) ? rowcnt[a] : 0;
+        int tot;
+        const int ex = block_scan_excl(c, s_warp, &tot);
+        if (a < m) D->row_ptr[a] = carry + ex;
+        carry += tot;
+    }
+    const int nnz2 = carry;
+    if (tid == 0) D->row_ptr[m] = nnz2;
+    __syncthreads();
+
+    for (int a = tid; a < m; a += B) {
+        const int i = old_of_new[a];
+        int q = D->row_ptr[a];
+        for (int p = S->row_ptr[i]; p < S->row_ptr[i + 1]; ++p) {
+            const int j = S->col[p];
+            if (fixed[j] == 0) {
+                D->col[q] = new_of_old[j];
+                D->val[q] = S->val[p];
+                ++q;
+            }
+        }
+        D->colour[a] = S->colour[i];
+    }
+    __syncthreads();
+
+    // inherited colour classes -> positions (class by class, increasing index)
+    const int ncol = S->ncol;
+    int cbase = 0;
+    for (int c = 0; c < ncol; ++c) {
+        if (tid == 0) D->cptr[c] = cbase;
+        int cc = 0;
+        for (int base = 0; base < m; base += B) {
+            const int a = base + tid;
+            const int f = (a < m && D->colour[a] == c) ? 1 : 0;
+            int tot;
+            const int ex = block_scan_excl(f, s_warp, &tot);
+            if (f) {
+                const int pos = cbase + cc + ex;
+                D->pos_of_idx[a] = pos;
+                D->idx_of_pos[pos] = a;
+            }
+            cc += tot;
+        }
+        cbase += cc;
+    }
+    if (tid == 0) D->cptr[ncol] = cbase;
+    __syncthreads();
+
+    // sweep layout: meta (h, degree) and ELL by position
+    const int cap = D->cap_n;
+    long long rk = -1;
+    for (int a = tid; a < m; a += B) {
+        const int pos = D->pos_of_idx[a];
+        const int r0 = D->row_ptr[a];
+        const int deg = D->row_ptr[a + 1] - r0;
+        D->meta[pos] = ((uint32_t)(D->h[a] & 0xFFFF) << 16) | (uint32_t)deg;
+        for (int d = 0; d < deg; ++d) {
+            const int j = D->col[r0 + d];
+            D->ell[(size_t)d * cap + pos] =
+                ((uint32_t)D->pos_of_idx[j] & 0xFFFFu) | ((uint32_t)(D->val[r0 + d] & 0xFFFF) << 16);
+        }
+        // reference spin: largest degree, lowest index among those
+        const long long key = ((long long)deg << 32) | (long long)(0x7FFFFFFF - a);
+        rk = max(rk, key);
+    }
+    atomicMax(&s_rho_key, rk);
+    __syncthreads();
+    if (tid == 0) {
+        D->n = m;
+        D->nnz = nnz2;
+        D->ncol = ncol;
+        D->maxdeg = S->maxdeg;
+        D->dmax = S->dmax;
+        D->hzero = s_hnz ? 0 : 1;
+        D->pm1 = S->pm1;
+        D->rho = (m > 0) ? (0x7FFFFFFF - (int)(s_rho_key & 0xFFFFFFFFll)) : -1;
+        D->offset = S->offset + (long long)s_off;
+        D->scale = S->scale;
+    }
+    __syncthreads();
+}
+
+namespace {
+
+// ---------------------------------------------------------------- standalone
+__global__ void __launch_bounds__(kBigBlock) k_elite_single(const int64_t *energies, int S, int k,
+                                                            int32_t *elite)
+{
+    extern __shared__ __align__(16) unsigned long long s_key[];
+    elite_core(energies, S, k, elite, s_key);
+}
+
+__global__ void __launch_bounds__(kCountBlock)
+    k_count_single(const DevProb *P, const uint32_t *spins, int W, const int32_t *elite, int k,
+                   int canon, int fix_num, int fix_den, int32_t *counts, int8_t *fixed,
+                   int32_t *nfixed)
+{
+    count_core(P, spins, W, elite, k, canon, fix_num, fix_den, counts, fixed, nfixed, nullptr,
+               nullptr);
+}
+
+__global__ void __launch_bounds__(kBigBlock) k_reduce_single(const DevProb *src, DevProb *dst,
+                                                             const int8_t *fixed,
+                                                             int32_t *old_of_new, int32_t *scratch)
+{
+    reduce_core(src, dst, fixed, old_of_new, scratch);
+}
+
+// ----------------------------------------------------------- multi-start slots
+__global__ void __launch_bounds__(256) k_slots_init(Slot *slots, SolveConsts C)
+{
+    Slot &s = slots[blockIdx.x];
+    for (int i = threadIdx.x; i < s.n0; i += blockDim.x) {
+        s.orig[0][i] = i;
+        s.fmap[i] = 0;
+        s.best_state[i] = 0;
+    }
+    for (int p = threadIdx.x; p < C.P; p += blockDim.x) {
+        s.rec_count[p] = 0;
+        s.rec_nfree[p] = 0;
+    }
+    if (threadIdx.x == 0) {
+        s.cur = s.orig_prob;
+        s.next = 0;
+        s.ocur = 0;
+        s.mode = kFixing;
+        s.phase = 0;
+        s.fix_done = 0;
+        s.nfixed = 0;
+        *s.best_e = LLONG_MAX;
+        *s.nphases = 0;
+    }
+}
+
+// Builds this phase's sweep jobs and work items (one item = Q quads of one
+// start) for every start that is not done, and resets the queue cursor.
+__global__ void __launch_bounds__(kBigBlock)
+    k_plan(Slot *slots, SolveConsts C, SweepJob *jobs, WorkItem *items, int32_t *nitems,
+           int32_t *queue)
+{
+    __shared__ int s_warp[32];
+    int carry = 0;
+    for (int base = 0; base < C.nslots; base += blockDim.x) {
+        const int si = base + threadIdx.x;
+        int groups = 0;
+        if (si < C.nslots) {
+            Slot &s = slots[si];
+            if (s.mode != kDone) {
+                const int S = (s.mode == kFixing) ? C.S_fix : C.S_solve;
+                SweepJob j;
+                j.prob = s.cur;
+                j.spins = s.spins;
+                j.energies = s.rec_e + (size_t)s.phase * C.Smax;
+                j.seed = s.seed;
+                j.S = S;
+                j.W = s.W0;
+                j.start = s.start;
+                j.phase = (uint32_t)s.phase;
+                jobs[si] = j;
+                groups = ceil_div(ceil_div(S, 4), C.Q);
+                s.rec_count[s.phase] = S;
+                s.rec_nfree[s.phase] = s.cur->n;
+                s.nfixed = 0;
+            }
+        }
+        int tot;
+        const int ex = block_scan_excl(groups, s_warp, &tot);
+        if (groups > 0) {
+            const int S = jobs[si].S;
+            const int nquads = ceil_div(S, 4);
+            for (int g = 0; g < groups; ++g) {
+                WorkItem w;
+                w.job = si;
+                w.quad0 = g * C.Q;
+                w.nq = min(C.Q, nquads - g * C.Q);
+                w.pad = 0;
+                items[carry + ex + g] = w;
+            }
+        }
+        carry += tot;
+    }
+    if (threadIdx.x == 0) {
+        *nitems = carry;
+        *queue = 0;
+    }
+}
+
+// Elite sample of each active start; also keeps the start's best assignment
+// (lifted to the original variables through its fix map).
+__global__ void __launch_bounds__(kBigBlock) k_elite_slots(Slot *slots, SolveConsts C)
+{
+    extern __shared__ __align__(16) unsigned long long s_key[];
+    __shared__ int s_better;
+    Slot &s = slots[blockIdx.x];
+    if (s.mode == kDone) return;
+    const int S = (s.mode == kFixing) ? C.S_fix : C.S_solve;
+    const int k = (s.mode == kFixing) ? C.k_fix : 1;
+    const int64_t *e = s.rec_e + (size_t)s.phase * C.Smax;
+    elite_core(e, S, k, s.elite, s_key);
+    const int rbest = s.elite[0];
+    const int64_t eb = e[rbest];
+    if (threadIdx.x == 0) {
+        s_better = eb < *s.best_e;
+        if (s_better) *s.best_e = eb;
+    }
+    __syncthreads();
+    if (!s_better) return;
+    for (int o = threadIdx.x; o < s.n0; o += blockDim.x) s.best_state[o] = s.fmap[o];
+    __syncthreads();
+    const int n = s.cur->n;
+    const int32_t *orig = s.orig[s.ocur];
+    const uint32_t *row = s.spins + (size_t)rbest * s.W0;
+    for (int a = threadIdx.x; a < n; a += blockDim.x)
+        s.best_state[orig[a]] = ((row[a >> 5] >> (a & 31)) & 1u) ? 1 : -1;
+}
+
+__global__ void __launch_bounds__(kCountBlock) k_count_slots(Slot *slots, SolveConsts C)
+{
+    Slot &s = slots[blockIdx.y];
+    if (s.mode != kFixing) return;
+    const DevProb *P = s.cur;
+    if ((int)(blockIdx.x * blockDim.x) >= P->n) return;
+    const int canon = (C.canon < 0) ? P->hzero : C.canon;
+    count_core(P, s.spins, s.W0, s.elite, C.k_fix, canon, C.fix_num, C.fix_den, s.counts, s.fixed,
+               &s.nfixed, s.fmap, s.orig[s.ocur]);
+}
+
+// Stall rule, fold/compact into the spare buffer, and the phase transition.
+__global__ void __launch_bounds__(kBigBlock) k_reduce_slots(Slot *slots, SolveConsts C)
+{
+    Slot &s = slots[blockIdx.x];
+    const int mode = s.mode;
+    if (mode == kDone) return;
+    if (mode == kSolving) {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            s.phase += 1;
+            *s.nphases = s.phase;
+            s.mode = kDone;
+        }
+        return;
+    }
+    const DevProb *P = s.cur;
+    const int n = P->n;
+    const int32_t *orig = s.orig[s.ocur];
+    if (threadIdx.x == 0 && C.iterate && s.nfixed == 0 && n > 0) {
+        // nothing fixed: fix the lowest-index spin to its value in the best
+        // elite sample so that every SPVAR phase makes progress
+        const uint32_t w = s.spins[(size_t)s.elite[0] * s.W0];
+        const int8_t v = (w & 1u) ? 1 : -1;
+        s.fixed[0] = v;
+        s.fmap[orig[0]] = v;
+    }
+    __syncthreads();
+    DevProb *D = s.buf[s.next];
+    reduce_core(P, D, s.fixed, s.old_of_new, s.scratch);
+    const int m = D->n;
+    int32_t *orig2 = s.orig[s.ocur ^ 1];
+    for (int a = threadIdx.x; a < m; a += blockDim.x) orig2[a] = orig[s.old_of_new[a]];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        s.cur = D;
+        s.next ^= 1;
+        s.ocur ^= 1;
+        s.phase += 1;
+        s.fix_done += 1;
+        *s.nphases = s.phase;
+        if (C.iterate && m > 0 && s.fix_done < C.max_fix) s.mode = kFixing;
+        else s.mode = (C.S_solve > 0) ? kSolving : kDone;
+    }
+}
+
+__global__ void k_count_active(const Slot *slots, int nslots, int32_t *nactive)
+{
+    __shared__ int s_n;
+    if (threadIdx.x == 0) s_n = 0;
+    __syncthreads();
+    int c = 0;
+    for (int i = threadIdx.x; i < nslots; i += blockDim.x) c += (slots[i].mode != kDone) ? 1 : 0;
+    atomicAdd(&s_n, c);
+    __syncthreads();
+    if (threadIdx.x == 0) *nactive = s_n;
+}
+
+size_t elite_smem(int S)
+{
+    int N2 = 1;
+    while (N2 < S) N2 <<= 1;
+    return (size_t)N2 * 8;
+}
+
+}  // namespace
+
+int elite_max_samples() { return SPVAR_MAX_SAMPLES; }
+
+cudaError_t launch_elite_single(const int64_t *energies, int S, int k, int32_t *elite,
+                                cudaStream_t stream)
+{
+    const size_t smem = elite_smem(S);
+    cudaFuncSetAttribute(k_elite_single, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_elite_single<<<1, kBigBlock, smem, stream>>>(energies, S, k, elite);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_count_single(const DevProb *prob, int n_host, const uint32_t *spins, int W,
+                                const int32_t *elite, int k, int canon, int fix_num, int fix_den,
+                                int32_t *counts, int8_t *fixed, int32_t *nfixed, cudaStream_t stream)
+{
+    cudaError_t e = cudaMemsetAsync(nfixed, 0, sizeof(int32_t), stream);
+    if (e != cudaSuccess) return e;
+    if (n_host <= 0) return cudaSuccess;
+    k_count_single<<<ceil_div(n_host, kCountBlock), kCountBlock, 0, stream>>>(
+        prob, spins, W, elite, k, canon, fix_num, fix_den, counts, fixed, nfixed);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_single(const DevProb *src, DevProb *dst, const int8_t *fixed,
+                                 int32_t *old_of_new, int32_t *scratch, cudaStream_t stream)
+{
+    k_reduce_single<<<1, kBigBlock, 0, stream>>>(src, dst, fixed, old_of_new, scratch);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_slots_init(Slot *slots, const SolveConsts &C, int, cudaStream_t st)
+{
+    k_slots_init<<<C.nslots, 256, 0, st>>>(slots, C);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_plan(Slot *slots, const SolveConsts &C, SweepJob *jobs, WorkItem *items,
+                        int32_t *nitems, int32_t *queue, cudaStream_t st)
+{
+    k_plan<<<1, kBigBlock, 0, st>>>(slots, C, jobs, items, nitems, queue);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_elite_slots(Slot *slots, const SolveConsts &C, cudaStream_t st)
+{
+    const size_t smem = elite_smem(C.Smax);
+    cudaFuncSetAttribute(k_elite_slots, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_elite_slots<<<C.nslots, kBigBlock, smem, st>>>(slots, C);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_count_slots(Slot *slots, const SolveConsts &C, int max_n0, cudaStream_t st)
+{
+    if (max_n0 <= 0) return cudaSuccess;
+    dim3 grid(ceil_div(max_n0, kCountBlock), C.nslots);
+    k_count_slots<<<grid, kCountBlock, 0, st>>>(slots, C);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_slots(Slot *slots, const SolveConsts &C, int32_t *nactive,
+                                cudaStream_t st)
+{
+    k_reduce_slots<<<C.nslots, kBigBlock, 0, st>>>(slots, C);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || !nactive) return e;
+    k_count_active<<<1, 256, 0, st>>>(slots, C.nslots, nactive);
+    return cudaGetLastError();
+}
+
+}  // namespace spvar

@@ -1,0 +1,585 @@
+// Multi-start SPVAR driver (Alg. 2; ISPVAR when iterate is set).
+//
+// A plan owns one device workspace for every start of every problem
+// ("slots"): two problem buffers of the original capacity for the reductions,
+// the sample buffer, the recorded energies and the fix maps.  One phase of all
+// slots is five launches -- plan (work list), persistent sweep, elite,
+// count/fix, fold/compact -- captured once into a CUDA graph and replayed;
+// control (which starts still fix, solve or are done, how large each reduced
+// problem is) stays on the device.  The plain form runs the same kernels one
+// start at a time without the graph, which is the comparison baseline.
+// A small autotuner times the sweep on the plan's own first phase for a few
+// (block, quads-per-CTA, staging) shapes; every shape gives bit-identical
+// results because randomness is keyed by logical coordinates only.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <new>
+#include <tuple>
+#include <vector>
+
+#include "spvar_internal.h"
+
+using namespace spvar;
+
+struct spvar_plan {
+    int device = 0;
+    std::vector<const Problem *> probs;
+    std::vector<int> starts_of;  // slot -> problem
+    spvar_params prm{};
+    SolveConsts C{};
+    int T = 0, thr_stride = 1, max_n0 = 0, max_deg = 1, iters_max = 1;
+    bool pm1 = true;
+    void *ws = nullptr;
+    size_t ws_bytes = 0;
+    Slot *d_slots = nullptr;
+    std::vector<Slot> h_slots;
+    Slot *h_slots_pinned = nullptr;
+    uint32_t *d_thr = nullptr;
+    SweepJob *d_jobs = nullptr;
+    WorkItem *d_items = nullptr;
+    int32_t *d_ctr = nullptr;       // [0] nitems, [1] queue, [2] nactive
+    int32_t *h_nactive = nullptr;   // pinned
+    int64_t *d_rec_e = nullptr;
+    int32_t *d_rec_count = nullptr, *d_rec_nfree = nullptr, *d_nphases = nullptr;
+    int64_t *d_best_e = nullptr;
+    int8_t *d_fmap = nullptr, *d_best = nullptr;
+    size_t fmap_total = 0;
+    int block = 256, Q = 1, stage = 1, sweep_grid = 1, sms = 1;
+    size_t sweep_smem = 0;
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t graph = nullptr;
+    cudaEvent_t ev_sweep[2] = {nullptr, nullptr};  // recorded around every sweep launch
+    int profiling = 0;
+    double sweep_ms = 0.0;
+    int32_t sweep_launches = 0;
+};
+
+namespace {
+
+inline cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct TuneKey {
+    int max_n, max_deg, pm1, S, nslots, form, thr_stride;
+    bool operator<(const TuneKey &o) const
+    {
+        return std::tie(max_n, max_deg, pm1, S, nslots, form, thr_stride) <
+               std::tie(o.max_n, o.max_deg, o.pm1, o.S, o.nslots, o.form, o.thr_stride);
+    }
+};
+std::map<TuneKey, std::tuple<int, int, int>> g_tune_cache;
+std::mutex g_tune_mu;
+
+SweepLaunch make_launch(const spvar_plan *pl, int T)
+{
+    SweepLaunch L;
+    std::memset(&L, 0, sizeof(L));
+    L.jobs = pl->d_jobs;
+    L.items = pl->d_items;
+    L.nitems = pl->d_ctr + 0;
+    L.queue = pl->d_ctr + 1;
+    L.thr = pl->d_thr;
+    L.thr_stride = pl->thr_stride;
+    L.T = T;
+    L.Q = pl->Q;
+    L.stage_ell = pl->stage;
+    L.max_n = pl->max_n0;
+    L.max_deg = pl->max_deg;
+    return L;
+}
+
+int grid_for(const spvar_plan *pl, int items)
+{
+    const int occ = std::max(1, sweep_max_active_blocks(pl->pm1, pl->block, pl->sweep_smem, pl->stage != 0));
+    return std::max(1, std::min(items, occ * pl->sms));
+}
+
+// One phase of the given slots (all of them in the batched form).
+cudaError_t launch_phase(spvar_plan *pl, Slot *slots, int nslots, int T, int grid, cudaStream_t st,
+                         bool count_active)
+{
+    SolveConsts C = pl->C;
+    C.nslots = nslots;
+    C.Q = pl->Q;
+    cudaError_t e = launch_plan(slots, C, pl->d_jobs, pl->d_items, pl->d_ctr + 0, pl->d_ctr + 1, st);
+    if (e != cudaSuccess) return e;
+    SweepLaunch L = make_launch(pl, T);
+    if ((e = cudaEventRecord(pl->ev_sweep[0], st)) != cudaSuccess) return e;
+    e = launch_sweep(L, pl->pm1, pl->block, grid, pl->sweep_smem, st);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaEventRecord(pl->ev_sweep[1], st)) != cudaSuccess) return e;
+    if ((e = launch_elite_slots(slots, C, st)) != cudaSuccess) return e;
+    if ((e = launch_count_slots(slots, C, pl->max_n0, st)) != cudaSuccess) return e;
+    return launch_reduce_slots(slots, C, count_active ? pl->d_ctr + 2 : nullptr, st);
+}
+
+int upload_slots(spvar_plan *pl, const uint64_t *seeds, cudaStream_t st)
+{
+    for (size_t s = 0; s < pl->h_slots.size(); ++s) {
+        Slot x = pl->h_slots[s];
+        x.seed = seeds ? seeds[pl->starts_of[s]] : 0;
+        pl->h_slots_pinned[s] = x;
+    }
+    SPVAR_CUDA_TRY(cudaMemcpyAsync(pl->d_slots, pl->h_slots_pinned, sizeof(Slot) * pl->h_slots.size(),
+                                   cudaMemcpyHostToDevice, st));
+    return SPVAR_OK;
+}
+
+// Times a short sweep of the plan's first phase for each candidate shape.
+void autotune(spvar_plan *pl, cudaStream_t st, int optin)
+{
+    const TuneKey key{pl->max_n0, pl->max_deg, pl->pm1 ? 1 : 0, pl->C.S_fix, pl->C.nslots,
+                      pl->prm.form, pl->thr_stride};
+    {
+        std::lock_guard<std::mutex> g(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            std::tie(pl->block, pl->Q, pl->stage) = it->second;
+            pl->sweep_smem = sweep_smem_bytes(pl->max_n0, pl->Q, pl->thr_stride, pl->max_deg, pl->stage != 0);
+            return;
+        }
+    }
+    const int Tt = std::min(pl->T, 8);
+    float best = 1e30f;
+    std::tuple<int, int, int> pick{256, 1, 0};
+    bool found = false;
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    const int blocks[3] = {128, 256, 512};
+    const int qs[4] = {1, 2, 4, 8};
+    for (int bi = 0; bi < 3; ++bi)
+        for (int qi = 0; qi < 4; ++qi)
+            for (int stg = 1; stg >= 0; --stg) {
+                const size_t smem = sweep_smem_bytes(pl->max_n0, qs[qi], pl->thr_stride, pl->max_deg, stg != 0);
+                if (smem > (size_t)optin) continue;
+                if (qs[qi] > 1 && ceil_div(pl->C.S_fix, 4) < qs[qi]) continue;
+                pl->block = blocks[bi];
+                pl->Q = qs[qi];
+                pl->stage = stg;
+                pl->sweep_smem = smem;
+                if (sweep_max_active_blocks(pl->pm1, pl->block, smem, stg != 0) < 1) continue;
+                const int nslots = (pl->prm.form == SPVAR_FORM_PLAIN) ? 1 : pl->C.nslots;
+                SolveConsts C = pl->C;
+                C.nslots = nslots;
+                C.Q = pl->Q;
+                launch_slots_init(pl->d_slots, C, pl->max_n0, st);
+                launch_plan(pl->d_slots, C, pl->d_jobs, pl->d_items, pl->d_ctr, pl->d_ctr + 1, st);
+                const int items = nslots * ceil_div(ceil_div(pl->C.Smax, 4), pl->Q);
+                const int grid = (pl->prm.form == SPVAR_FORM_PLAIN) ? items : grid_for(pl, items);
+                SweepLaunch L = make_launch(pl, Tt);
+                float ms = 0;
+                cudaEventRecord(a, st);
+                cudaError_t e = launch_sweep(L, pl->pm1, pl->block, grid, smem, st);
+                cudaEventRecord(b, st);
+                if (e != cudaSuccess || cudaEventSynchronize(b) != cudaSuccess) {
+                    cudaGetLastError();
+                    continue;
+                }
+                cudaEventElapsedTime(&ms, a, b);
+                // second run: the first includes one-time setup
+                launch_plan(pl->d_slots, C, pl->d_jobs, pl->d_items, pl->d_ctr, pl->d_ctr + 1, st);
+                cudaEventRecord(a, st);
+                launch_sweep(L, pl->pm1, pl->block, grid, smem, st);
+                cudaEventRecord(b, st);
+                cudaEventSynchronize(b);
+                cudaEventElapsedTime(&ms, a, b);
+                if (ms < best) {
+                    best = ms;
+                    pick = std::make_tuple(pl->block, pl->Q, stg);
+                    found = true;
+                }
+            }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (!found) pick = std::make_tuple(256, 1, 0);
+    std::tie(pl->block, pl->Q, pl->stage) = pick;
+    pl->sweep_smem = sweep_smem_bytes(pl->max_n0, pl->Q, pl->thr_stride, pl->max_deg, pl->stage != 0);
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    g_tune_cache[key] = pick;
+}
+
+void plan_free(spvar_plan *pl)
+{
+    if (!pl) return;
+    if (pl->graph) cudaGraphExecDestroy(pl->graph);
+    for (int i = 0; i < 2; ++i)
+        if (pl->ev_sweep[i]) cudaEventDestroy(pl->ev_sweep[i]);
+    if (pl->cap_stream) cudaStreamDestroy(pl->cap_stream);
+    if (pl->ws) cudaFree(pl->ws);
+    if (pl->h_slots_pinned) cudaFreeHost(pl->h_slots_pinned);
+    if (pl->h_nactive) cudaFreeHost(pl->h_nactive);
+    delete pl;
+}
+
+}  // namespace
+
+extern "C" {
+
+int spvar_plan_create(const spvar_problem *const *problems, int32_t nproblems,
+                      const spvar_params *prm, size_t budget_bytes, void *stream, spvar_plan **out)
+{
+    if (!out) return SPVAR_EINVAL;
+    *out = nullptr;
+    if (!problems || nproblems < 1 || !prm) return SPVAR_EINVAL;
+    const spvar_params &p = *prm;
+    if (p.num_starts < 1 || p.fixing_sample_size < 1 || p.solving_sample_size < 0 || p.num_sweeps < 0 ||
+        p.max_fix_phases < 1 || p.fix_num <= 0 || p.fix_den <= 0 || p.fix_num > p.fix_den ||
+        !(p.elite_threshold > 0.0) || !(p.elite_threshold <= 1.0) || !(p.beta0 > 0.0) || !(p.beta1 > 0.0) ||
+        p.canon < -1 || p.canon > 1 || (p.form != SPVAR_FORM_BATCHED && p.form != SPVAR_FORM_PLAIN) ||
+        p.replicas_per_block < 0 || (p.replicas_per_block % 4) != 0)
+        return SPVAR_EINVAL;
+    const int Smax = std::max(p.fixing_sample_size, p.solving_sample_size);
+    if (Smax > SPVAR_MAX_SAMPLES || p.num_sweeps > SPVAR_MAX_SWEEPS ||
+        p.max_fix_phases + 1 > SPVAR_MAX_PHASE)
+        return SPVAR_ELIMIT;
+    spvar_plan *pl = new (std::nothrow) spvar_plan();
+    if (!pl) return SPVAR_ENOMEM;
+    cudaGetDevice(&pl->device);
+    cudaDeviceGetAttribute(&pl->sms, cudaDevAttrMultiProcessorCount, pl->device);
+    int optin = 0;
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, pl->device);
+    pl->prm = p;
+    int dmax = 0, scale = 0;
+    for (int i = 0; i < nproblems; ++i) {
+        if (!problems[i]) { delete pl; return SPVAR_EINVAL; }
+        const Problem *P = reinterpret_cast<const Problem *>(problems[i]);
+        if (i == 0) scale = P->hdr.scale;
+        if (P->hdr.scale != scale) { delete pl; return SPVAR_EINVAL; }
+        pl->probs.push_back(P);
+        dmax = std::max(dmax, P->hdr.dmax);
+        pl->max_n0 = std::max(pl->max_n0, P->hdr.n);
+        pl->max_deg = std::max(pl->max_deg, P->hdr.maxdeg);
+        if (!P->hdr.pm1) pl->pm1 = false;
+    }
+    pl->T = p.num_sweeps;
+    pl->thr_stride = dmax + 1;
+    const int P_slots = p.max_fix_phases + 1;
+    const int nslots = nproblems * p.num_starts;
+    // elite count k = ceil(elite * S), clamped to [1, S]
+    const double x = std::ceil(p.elite_threshold * (double)p.fixing_sample_size);
+    int kfix = (x >= (double)p.fixing_sample_size) ? p.fixing_sample_size : (int)x;
+    kfix = std::max(1, std::min(kfix, p.fixing_sample_size));
+    SolveConsts &C = pl->C;
+    C.S_fix = p.fixing_sample_size;
+    C.S_solve = p.solving_sample_size;
+    C.k_fix = kfix;
+    C.iterate = p.iterate ? 1 : 0;
+    C.max_fix = p.max_fix_phases;
+    C.canon = p.canon;
+    C.fix_num = p.fix_num;
+    C.fix_den = p.fix_den;
+    C.P = P_slots;
+    C.Smax = Smax;
+    C.Q = 1;
+    C.nslots = nslots;
+    pl->iters_max = (p.iterate ? p.max_fix_phases : 1) + (p.solving_sample_size > 0 ? 1 : 0);
+
+    // workspace layout
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o = off; off += align256(bytes); return o; };
+    const size_t o_slots = take(sizeof(Slot) * nslots);
+    const size_t o_jobs = take(sizeof(SweepJob) * nslots);
+    const size_t max_items = (size_t)nslots * ceil_div(Smax, 4);
+    const size_t o_items = take(sizeof(WorkItem) * max_items);
+    const size_t o_ctr = take(16);
+    const size_t o_thr = take(4 * (size_t)std::max(pl->T, 1) * pl->thr_stride);
+    const size_t o_rec = take(8 * (size_t)nslots * P_slots * Smax);
+    const size_t o_rc = take(4 * (size_t)nslots * P_slots);
+    const size_t o_rn = take(4 * (size_t)nslots * P_slots);
+    const size_t o_nph = take(4 * (size_t)nslots);
+    const size_t o_be = take(8 * (size_t)nslots);
+    size_t fm_total = 0;
+    for (int s = 0; s < nslots; ++s) fm_total += (size_t)pl->probs[s / p.num_starts]->hdr.n;
+    pl->fmap_total = fm_total;
+    const size_t o_fmap = take(std::max<size_t>(fm_total, 1));
+    const size_t o_best = take(std::max<size_t>(fm_total, 1));
+    std::vector<size_t> o_slot(nslots);
+    for (int s = 0; s < nslots; ++s) {
+        const DevProb &H = pl->probs[s / p.num_starts]->hdr;
+        const int n0 = std::max(H.n, 1);
+        const size_t pb = prob_blob_bytes(H.cap_n, H.cap_nnz, H.maxdeg);
+        size_t b = 2 * align256(pb);
+        b += align256(4 * (size_t)Smax * ceil_div(n0, 32));
+        b += 2 * align256(4 * (size_t)n0);  // orig[2]
+        b += align256(4 * (size_t)Smax);    // elite
+        b += align256(4 * (size_t)n0);      // counts
+        b += align256((size_t)n0);          // fixed
+        b += align256(4 * (size_t)n0);      // old_of_new
+        b += align256(8 * (size_t)H.cap_n); // scratch
+        o_slot[s] = take(b);
+    }
+    pl->ws_bytes = off;
+    if (budget_bytes > 0 && off > budget_bytes) { plan_free(pl); return SPVAR_EBUDGET; }
+    if (cudaMalloc(&pl->ws, off) != cudaSuccess) { cudaGetLastError(); plan_free(pl); return SPVAR_ENOMEM; }
+    if (cudaMallocHost(&pl->h_slots_pinned, sizeof(Slot) * nslots) != cudaSuccess ||
+        cudaMallocHost(&pl->h_nactive, sizeof(int32_t)) != cudaSuccess) {
+        cudaGetLastError();
+        plan_free(pl);
+        return SPVAR_ENOMEM;
+    }
+    if (cudaEventCreate(&pl->ev_sweep[0]) != cudaSuccess || cudaEventCreate(&pl->ev_sweep[1]) != cudaSuccess) {
+        cudaGetLastError();
+        plan_free(pl);
+        return SPVAR_ECUDA;
+    }
+    char *w = static_cast<char *>(pl->ws);
+    pl->d_slots = (Slot *)(w + o_slots);
+    pl->d_jobs = (SweepJob *)(w + o_jobs);
+    pl->d_items = (WorkItem *)(w + o_items);
+    pl->d_ctr = (int32_t *)(w + o_ctr);
+    pl->d_thr = (uint32_t *)(w + o_thr);
+    pl->d_rec_e = (int64_t *)(w + o_rec);
+    pl->d_rec_count = (int32_t *)(w + o_rc);
+    pl->d_rec_nfree = (int32_t *)(w + o_rn);
+    pl->d_nphases = (int32_t *)(w + o_nph);
+    pl->d_best_e = (int64_t *)(w + o_be);
+    pl->d_fmap = (int8_t *)(w + o_fmap);
+    pl->d_best = (int8_t *)(w + o_best);
+
+    cudaStream_t st = as_stream(stream);
+    // acceptance table
+    {
+        std::vector<double> beta(std::max(pl->T, 1));
+        std::vector<uint32_t> thr((size_t)std::max(pl->T, 1) * pl->thr_stride, 0u);
+        if (pl->T > 0) {
+            spvar_beta_geometric(pl->T, p.beta0, p.beta1, beta.data());
+            spvar_thresholds(pl->T, beta.data(), dmax, scale, thr.data());
+        }
+        if (cudaMemcpyAsync(pl->d_thr, thr.data(), 4 * thr.size(), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess) {
+            cudaGetLastError();
+            plan_free(pl);
+            return SPVAR_ECUDA;
+        }
+    }
+    // slots and their problem buffers
+    pl->h_slots.resize(nslots);
+    pl->starts_of.resize(nslots);
+    std::vector<DevProb> hdrs;
+    std::vector<DevProb *> hdr_dst;
+    size_t fm_off = 0;
+    for (int s = 0; s < nslots; ++s) {
+        const int pi = s / p.num_starts;
+        const Problem *P = pl->probs[pi];
+        const DevProb &H = P->hdr;
+        const int n0 = std::max(H.n, 1);
+        Slot &S = pl->h_slots[s];
+        std::memset(&S, 0, sizeof(Slot));
+        pl->starts_of[s] = pi;
+        char *b = w + o_slot[s];
+        size_t o = 0;
+        auto carve = [&](size_t bytes) { char *r = b + o; o += align256(bytes); return r; };
+        const size_t pb = prob_blob_bytes(H.cap_n, H.cap_nnz, H.maxdeg);
+        for (int k = 0; k < 2; ++k) {
+            void *blob = carve(pb);
+            DevProb hd;
+            std::memset(&hd, 0, sizeof(hd));
+            prob_carve(&hd, blob, H.cap_n, H.cap_nnz, H.maxdeg);
+            hdrs.push_back(hd);
+            hdr_dst.push_back((DevProb *)blob);
+            S.buf[k] = (DevProb *)blob;
+        }
+        S.orig_prob = P->dev;
+        S.cur = P->dev;
+        S.n0 = H.n;
+        S.W0 = ceil_div(n0, 32);
+        S.start = (uint32_t)(s % p.num_starts);
+        S.spins = (uint32_t *)carve(4 * (size_t)Smax * S.W0);
+        S.orig[0] = (int32_t *)carve(4 * (size_t)n0);
+        S.orig[1] = (int32_t *)carve(4 * (size_t)n0);
+        S.elite = (int32_t *)carve(4 * (size_t)Smax);
+        S.counts = (int32_t *)carve(4 * (size_t)n0);
+        S.fixed = (int8_t *)carve((size_t)n0);
+        S.old_of_new = (int32_t *)carve(4 * (size_t)n0);
+        S.scratch = (int32_t *)carve(8 * (size_t)H.cap_n);
+        S.rec_e = pl->d_rec_e + (size_t)s * P_slots * Smax;
+        S.rec_count = pl->d_rec_count + (size_t)s * P_slots;
+        S.rec_nfree = pl->d_rec_nfree + (size_t)s * P_slots;
+        S.nphases = pl->d_nphases + s;
+        S.best_e = pl->d_best_e + s;
+        S.fmap = pl->d_fmap + fm_off;
+        S.best_state = pl->d_best + fm_off;
+        fm_off += (size_t)H.n;
+    }
+    bool ok = true;
+    for (size_t k = 0; k < hdrs.size() && ok; ++k)
+        ok = cudaMemcpyAsync(hdr_dst[k], &hdrs[k], sizeof(DevProb), cudaMemcpyHostToDevice, st) == cudaSuccess;
+    if (ok) ok = upload_slots(pl, nullptr, st) == SPVAR_OK;
+    if (ok) ok = cudaStreamSynchronize(st) == cudaSuccess;
+    if (!ok) { cudaGetLastError(); plan_free(pl); return SPVAR_ECUDA; }
+
+    // sweep shape
+    if (p.replicas_per_block > 0) {
+        pl->Q = p.replicas_per_block / 4;
+        pl->block = 256;
+        pl->stage = sweep_smem_bytes(pl->max_n0, pl->Q, pl->thr_stride, pl->max_deg, true) <= (size_t)optin;
+        pl->sweep_smem = sweep_smem_bytes(pl->max_n0, pl->Q, pl->thr_stride, pl->max_deg, pl->stage != 0);
+        if (pl->sweep_smem > (size_t)optin) { plan_free(pl); return SPVAR_ELIMIT; }
+    } else {
+        autotune(pl, st, optin);
+        if (pl->sweep_smem > (size_t)optin) { plan_free(pl); return SPVAR_ELIMIT; }
+    }
+    pl->C.Q = pl->Q;
+    const int items = nslots * ceil_div(ceil_div(Smax, 4), pl->Q);
+    pl->sweep_grid = grid_for(pl, items);
+
+    // capture one batched phase as a CUDA graph
+    if (p.form == SPVAR_FORM_BATCHED) {
+        if (cudaStreamCreateWithFlags(&pl->cap_stream, cudaStreamNonBlocking) == cudaSuccess) {
+            cudaGraph_t g = nullptr;
+            bool cap = cudaStreamBeginCapture(pl->cap_stream, cudaStreamCaptureModeRelaxed) == cudaSuccess;
+            if (cap) {
+                cudaError_t e = launch_phase(pl, pl->d_slots, nslots, pl->T, pl->sweep_grid, pl->cap_stream, true);
+                if (e == cudaSuccess)
+                    e = cudaMemcpyAsync(pl->h_nactive, pl->d_ctr + 2, sizeof(int32_t), cudaMemcpyDeviceToHost,
+                                        pl->cap_stream);
+                cudaError_t e2 = cudaStreamEndCapture(pl->cap_stream, &g);
+                if (e == cudaSuccess && e2 == cudaSuccess && g) {
+                    if (cudaGraphInstantiate(&pl->graph, g, 0) != cudaSuccess) pl->graph = nullptr;
+                }
+                if (g) cudaGraphDestroy(g);
+            }
+            cudaGetLastError();
+        }
+    }
+    *out = pl;
+    return SPVAR_OK;
+}
+
+size_t spvar_plan_workspace_bytes(const spvar_plan *plan) { return plan ? plan->ws_bytes : 0; }
+
+int spvar_plan_run(spvar_plan *pl, const uint64_t *seeds, const spvar_result *res, void *stream)
+{
+    if (!pl || !seeds) return SPVAR_EINVAL;
+    cudaStream_t st = as_stream(stream);
+    const int nslots = pl->C.nslots;
+    int rc = upload_slots(pl, seeds, st);
+    if (rc) return rc;
+    SPVAR_CUDA_TRY(launch_slots_init(pl->d_slots, pl->C, pl->max_n0, st));
+    const bool iterate = pl->prm.iterate != 0;
+    pl->sweep_ms = 0.0;
+    pl->sweep_launches = 0;
+    // profiling: wait for each phase and add up the sweep kernel's event time
+    auto profile_phase = [&]() -> int {
+        if (!pl->profiling) return SPVAR_OK;
+        SPVAR_CUDA_TRY(cudaEventSynchronize(pl->ev_sweep[1]));
+        float ms = 0.f;
+        SPVAR_CUDA_TRY(cudaEventElapsedTime(&ms, pl->ev_sweep[0], pl->ev_sweep[1]));
+        pl->sweep_ms += ms;
+        pl->sweep_launches += 1;
+        return SPVAR_OK;
+    };
+    if (pl->prm.form == SPVAR_FORM_BATCHED) {
+        for (int it = 0; it < pl->iters_max; ++it) {
+            if (pl->graph) {
+                SPVAR_CUDA_TRY(cudaGraphLaunch(pl->graph, st));
+            } else {
+                SPVAR_CUDA_TRY(launch_phase(pl, pl->d_slots, nslots, pl->T, pl->sweep_grid, st, true));
+                SPVAR_CUDA_TRY(cudaMemcpyAsync(pl->h_nactive, pl->d_ctr + 2, sizeof(int32_t),
+                                               cudaMemcpyDeviceToHost, st));
+            }
+            if ((rc = profile_phase()) != SPVAR_OK) return rc;
+            if (iterate && it + 1 < pl->iters_max) {
+                SPVAR_CUDA_TRY(cudaStreamSynchronize(st));
+                if (*pl->h_nactive == 0) break;
+            }
+        }
+    } else {
+        const int grid = ceil_div(ceil_div(pl->C.Smax, 4), pl->Q);
+        for (int s = 0; s < nslots; ++s) {
+            for (int it = 0; it < pl->iters_max; ++it) {
+                SPVAR_CUDA_TRY(launch_phase(pl, pl->d_slots + s, 1, pl->T, grid, st, iterate));
+                if ((rc = profile_phase()) != SPVAR_OK) return rc;
+                if (iterate && it + 1 < pl->iters_max) {
+                    SPVAR_CUDA_TRY(cudaMemcpyAsync(pl->h_nactive, pl->d_ctr + 2, sizeof(int32_t),
+                                                   cudaMemcpyDeviceToHost, st));
+                    SPVAR_CUDA_TRY(cudaStreamSynchronize(st));
+                    if (*pl->h_nactive == 0) break;
+                }
+            }
+        }
+    }
+    if (res) {
+        const cudaMemcpyKind kind = res->device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+        const size_t P_slots = pl->C.P, Smax = pl->C.Smax;
+        auto cp = [&](void *dst, const void *src, size_t bytes) -> bool {
+            return !dst || !bytes || cudaMemcpyAsync(dst, src, bytes, kind, st) == cudaSuccess;
+        };
+        bool ok = cp(res->energies, pl->d_rec_e, 8 * nslots * P_slots * Smax) &&
+                  cp(res->counts, pl->d_rec_count, 4 * nslots * P_slots) &&
+                  cp(res->nfree, pl->d_rec_nfree, 4 * nslots * P_slots) &&
+                  cp(res->nphases, pl->d_nphases, 4 * (size_t)nslots) &&
+                  cp(res->fixed, pl->d_fmap, pl->fmap_total) &&
+                  cp(res->best_energy, pl->d_best_e, 8 * (size_t)nslots) &&
+                  cp(res->best_state, pl->d_best, pl->fmap_total);
+        if (!ok) return SPVAR_ECUDA;
+        if (!res->device) SPVAR_CUDA_TRY(cudaStreamSynchronize(st));
+    }
+    return SPVAR_OK;
+}
+
+int spvar_plan_set_profiling(spvar_plan *plan, int32_t on)
+{
+    if (!plan) return SPVAR_EINVAL;
+    plan->profiling = on ? 1 : 0;
+    return SPVAR_OK;
+}
+
+int spvar_plan_sweep_time(const spvar_plan *plan, double *total_ms, int32_t *launches)
+{
+    if (!plan) return SPVAR_EINVAL;
+    if (total_ms) *total_ms = plan->sweep_ms;
+    if (launches) *launches = plan->sweep_launches;
+    return SPVAR_OK;
+}
+
+int spvar_plan_shape(const spvar_plan *plan, int32_t *block, int32_t *replicas_per_block,
+                     int32_t *staged, int32_t *grid)
+{
+    if (!plan) return SPVAR_EINVAL;
+    if (block) *block = plan->block;
+    if (replicas_per_block) *replicas_per_block = 4 * plan->Q;
+    if (staged) *staged = plan->stage;
+    if (grid) *grid = plan->sweep_grid;
+    return SPVAR_OK;
+}
+
+int spvar_plan_stats(const spvar_plan *plan, int64_t *attempts, int32_t *phases)
+{
+    if (!plan) return SPVAR_EINVAL;
+    spvar_plan *pl = const_cast<spvar_plan *>(plan);
+    const size_t n = (size_t)pl->C.nslots * pl->C.P;
+    std::vector<int32_t> cnt(n), nf(n);
+    if (cudaMemcpy(cnt.data(), pl->d_rec_count, 4 * n, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(nf.data(), pl->d_rec_nfree, 4 * n, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return SPVAR_ECUDA;
+    int64_t a = 0;
+    int32_t ph = 0;
+    for (size_t i = 0; i < n; ++i) {
+        a += (int64_t)cnt[i] * nf[i] * pl->T;
+        if (cnt[i] > 0) ++ph;
+    }
+    if (attempts) *attempts = a;
+    if (phases) *phases = ph;
+    return SPVAR_OK;
+}
+
+void spvar_plan_destroy(spvar_plan *plan) { plan_free(plan); }
+
+int spvar_solve(const spvar_problem *p, const spvar_params *prm, uint64_t seed, const spvar_result *res,
+                void *stream)
+{
+    spvar_plan *pl = nullptr;
+    const spvar_problem *arr[1] = {p};
+    int rc = spvar_plan_create(arr, 1, prm, 0, stream, &pl);
+    if (rc) return rc;
+    rc = spvar_plan_run(pl, &seed, res, stream);
+    plan_free(pl);
+    return rc;
+}
+
+}  // extern "C"

@@ -1,0 +1,145 @@
+// Internal declarations of the SPVAR CUDA library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "spvar.h"
+
+namespace spvar {
+
+// Colour classes are bounded by a first-fit colouring: <= max degree + 1.
+constexpr int kMaxColours = SPVAR_MAX_DEGREE + 1;
+constexpr uint32_t kSweepBits = 20;                 // counter word 1 = phase << 20 | sweep
+constexpr uint32_t kInitSlot = (1u << kSweepBits) - 1u;
+
+// Device-resident problem: CSR in index order plus the sweep layout.
+// "Positions" order the spins colour class by colour class, increasing index
+// inside a class; the sweep kernels work in positions so that one colour is
+// one contiguous range.  Everything lives in one device allocation with fixed
+// capacities (cap_n, cap_nnz, maxdeg) so that reductions can be written in
+// place of a buffer of the same capacity.
+struct DevProb {
+    int32_t n, nnz, ncol, maxdeg;  // maxdeg: ELL rows (an upper bound on every row length)
+    int32_t dmax, hzero, pm1, rho; // rho: lowest-index spin of maximum degree (-1 if n == 0)
+    int64_t offset;
+    int32_t cap_n, cap_nnz, scale, pad0;
+    int32_t *row_ptr;    // [cap_n + 1]
+    int32_t *col;        // [cap_nnz]
+    int32_t *val;        // [cap_nnz]
+    int32_t *h;          // [cap_n]
+    int32_t *colour;     // [cap_n]
+    int32_t *cptr;       // [kMaxColours + 1] position range of each colour
+    int32_t *idx_of_pos; // [cap_n]
+    int32_t *pos_of_idx; // [cap_n]
+    uint32_t *meta;      // [cap_n] (h as int16) << 16 | degree, by position
+    uint32_t *ell;       // [maxdeg][cap_n] (neighbour position) | (J as int16) << 16, by position
+};
+
+// Host handle of a problem: the device blob and a host copy of its header.
+struct Problem {
+    DevProb hdr;        // host copy (pointers are device pointers)
+    DevProb *dev;       // device copy of the header (inside the blob)
+    void *blob;
+    size_t blob_bytes;
+    int device;
+};
+
+size_t prob_blob_bytes(int cap_n, int cap_nnz, int maxdeg);
+// Carve a blob into a header with device pointers; the header itself sits at blob offset 0.
+void prob_carve(DevProb *hdr, void *blob, int cap_n, int cap_nnz, int maxdeg);
+
+// One sample job: anneal replicas [0, S) of one problem.
+struct SweepJob {
+    const DevProb *prob;
+    uint32_t *spins;    // [S][W] bit-packed output (W = words per row)
+    int64_t *energies;  // [S] output (with offset)
+    uint64_t seed;
+    int32_t S, W;
+    uint32_t start, phase;
+};
+
+// A unit of sweep work: quads [quad0, quad0 + nq) of job `job`.
+struct WorkItem {
+    int32_t job, quad0, nq, pad;
+};
+
+struct SweepLaunch {
+    const SweepJob *jobs;   // device array, or nullptr: use `single`
+    const WorkItem *items;  // device array (persistent queue), or nullptr: item = blockIdx.x
+    const int32_t *nitems;  // device counter of items (queue mode)
+    int32_t *queue;         // device atomic cursor (queue mode)
+    SweepJob single;
+    const uint32_t *thr;
+    int32_t thr_stride, T, Q, stage_ell;
+    int32_t max_n;          // largest n of any job (shared-memory carve-up)
+    int32_t max_deg;        // largest maxdeg of any job (staged ELL size)
+};
+
+// Per-start state of the multi-start driver (Alg. 2), in device memory.
+enum SlotMode : int32_t { kFixing = 0, kSolving = 1, kDone = 2 };
+
+struct Slot {
+    const DevProb *orig_prob;  // original problem (read-only, shared by its starts)
+    const DevProb *cur;        // problem sampled in the current phase
+    DevProb *buf[2];           // reduction targets (capacity of the original)
+    int32_t next;              // buffer the next reduction writes
+    int32_t mode, phase, fix_done;
+    int32_t nfixed, n0, W0, ocur;
+    uint64_t seed;
+    uint32_t start;
+    int32_t pad0;
+    uint32_t *spins;           // [Smax][W0] current sample
+    int64_t *rec_e;            // [P][Smax] recorded full-problem energies
+    int32_t *rec_count;        // [P]
+    int32_t *rec_nfree;        // [P]
+    int32_t *nphases;          // [1]
+    int64_t *best_e;           // [1]
+    int8_t *fmap;              // [n0] fix map in original order
+    int8_t *best_state;        // [n0]
+    int32_t *orig[2];          // [n0] original index of each current spin (double-buffered)
+    int32_t *elite;            // [Smax]
+    int32_t *counts;           // [n0]
+    int8_t *fixed;             // [n0]
+    int32_t *old_of_new;       // [n0]
+    int32_t *scratch;          // [2 * n0]
+};
+
+struct SolveConsts {
+    int32_t S_fix, S_solve, k_fix, iterate;
+    int32_t max_fix, canon, fix_num, fix_den;
+    int32_t P, Smax, Q, nslots;
+};
+
+cudaError_t launch_slots_init(Slot *slots, const SolveConsts &C, int max_n0, cudaStream_t st);
+cudaError_t launch_plan(Slot *slots, const SolveConsts &C, SweepJob *jobs, WorkItem *items,
+                        int32_t *nitems, int32_t *queue, cudaStream_t st);
+cudaError_t launch_elite_slots(Slot *slots, const SolveConsts &C, cudaStream_t st);
+cudaError_t launch_count_slots(Slot *slots, const SolveConsts &C, int max_n0, cudaStream_t st);
+cudaError_t launch_reduce_slots(Slot *slots, const SolveConsts &C, int32_t *nactive,
+                                cudaStream_t st);
+
+size_t sweep_smem_bytes(int max_n, int Q, int thr_stride, int maxdeg, bool stage_ell);
+cudaError_t launch_sweep(const SweepLaunch &L, bool pm1, int block, int grid, size_t smem,
+                         cudaStream_t stream);
+int sweep_max_active_blocks(bool pm1, int block, size_t smem, bool stage_ell);
+
+// Elite selection of one sample set (standalone form).
+cudaError_t launch_elite_single(const int64_t *energies, int S, int k, int32_t *elite,
+                                cudaStream_t stream);
+cudaError_t launch_count_single(const DevProb *prob, int n_host, const uint32_t *spins, int W,
+                                const int32_t *elite, int k, int canon, int fix_num, int fix_den,
+                                int32_t *counts, int8_t *fixed, int32_t *nfixed, cudaStream_t stream);
+cudaError_t launch_reduce_single(const DevProb *src, DevProb *dst, const int8_t *fixed,
+                                 int32_t *old_of_new, int32_t *scratch, cudaStream_t stream);
+int elite_max_samples();
+
+__host__ __device__ inline int ceil_div(int a, int b) { return (a + b - 1) / b; }
+
+}  // namespace spvar
+
+#define SPVAR_CUDA_TRY(expr)                                   \
+    do {                                                       \
+        cudaError_t _e = (expr);                               \
+        if (_e != cudaSuccess) return SPVAR_ECUDA;             \
+    } while (0)

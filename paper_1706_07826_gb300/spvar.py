@@ -1,0 +1,391 @@
+"""Thin ctypes binding of ``libspvar.so`` (declared in ``include/spvar.h``).
+
+Argument marshalling only: every step of the method runs in the CUDA library.
+PyTorch supplies device memory (tensors) and streams; numpy arrays carry host
+inputs.  The library must have been built (``__graft_entry__.build()`` or
+``python -m paper_1706_07826_gb300.build``); there is no fallback of any kind.
+"""
+import ctypes
+import dataclasses
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libspvar.so")
+
+OK, EINVAL, EOVERFLOW, ENOMEM, EBUDGET, ETIMEOUT, ECUDA, ELIMIT = 0, -1, -2, -3, -4, -5, -6, -7
+FORM_BATCHED, FORM_PLAIN = 0, 1
+MAX_N, MAX_DEGREE, MAX_SWEEPS, MAX_PHASE, MAX_SAMPLES = 32768, 32, 1048574, 4095, 16384
+
+vp = ctypes.c_void_p
+i32 = ctypes.c_int32
+i64 = ctypes.c_int64
+u32 = ctypes.c_uint32
+u64 = ctypes.c_uint64
+
+
+class SpvarError(RuntimeError):
+    def __init__(self, code, what):
+        self.code = code
+        super().__init__("%s failed: %s (%d)" % (what, _strerror(code), code))
+
+
+class ProblemInfo(ctypes.Structure):
+    _fields_ = [("n", i32), ("nnz", i32), ("ncol", i32), ("maxdeg", i32), ("dmax", i32),
+                ("hzero", i32), ("pm1", i32), ("energy_scale", i32), ("offset", i64)]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("num_starts", i32), ("fixing_sample_size", i32), ("solving_sample_size", i32),
+                ("num_sweeps", i32), ("beta0", ctypes.c_double), ("beta1", ctypes.c_double),
+                ("elite_threshold", ctypes.c_double), ("fix_num", i32), ("fix_den", i32),
+                ("iterate", i32), ("max_fix_phases", i32), ("canon", i32), ("form", i32),
+                ("replicas_per_block", i32)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("device", i32), ("energies", vp), ("counts", vp), ("nfree", vp), ("nphases", vp),
+                ("fixed", vp), ("best_energy", vp), ("best_state", vp)]
+
+
+_lib = None
+
+
+def lib():
+    """Load the CUDA library; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libspvar.so is missing (%s): build it with __graft_entry__.build(); "
+                               "there is no CPU fallback" % LIB_PATH)
+        L = ctypes.CDLL(LIB_PATH)
+        L.spvar_strerror.restype = ctypes.c_char_p
+        L.spvar_strerror.argtypes = [ctypes.c_int]
+        L.spvar_device_count.argtypes = [ctypes.POINTER(ctypes.c_int)]
+        L.spvar_csr_from_edges.argtypes = [i32, i64, vp, vp, vp, vp, vp, vp]
+        L.spvar_problem_create.argtypes = [i32, vp, vp, vp, vp, i64, i32, vp, ctypes.POINTER(vp)]
+        L.spvar_problem_destroy.argtypes = [vp]
+        L.spvar_problem_destroy.restype = None
+        L.spvar_problem_get_info.argtypes = [vp, ctypes.POINTER(ProblemInfo)]
+        L.spvar_problem_download.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+        L.spvar_beta_geometric.argtypes = [i32, ctypes.c_double, ctypes.c_double, vp]
+        L.spvar_thresholds.argtypes = [i32, vp, i32, i32, vp]
+        L.spvar_sample.argtypes = [vp, i32, vp, i32, i32, u64, u32, u32, vp, vp, vp]
+        L.spvar_persistence.argtypes = [vp, i32, vp, vp, ctypes.c_double, i32, i32, i32, vp, vp, vp, vp,
+                                        ctypes.POINTER(i32), vp]
+        L.spvar_reduce.argtypes = [vp, vp, vp, vp, ctypes.POINTER(vp)]
+        L.spvar_plan_create.argtypes = [ctypes.POINTER(vp), i32, ctypes.POINTER(Params), ctypes.c_size_t, vp,
+                                        ctypes.POINTER(vp)]
+        L.spvar_plan_workspace_bytes.argtypes = [vp]
+        L.spvar_plan_workspace_bytes.restype = ctypes.c_size_t
+        L.spvar_plan_run.argtypes = [vp, ctypes.POINTER(u64), ctypes.POINTER(Result), vp]
+        L.spvar_plan_destroy.argtypes = [vp]
+        L.spvar_plan_destroy.restype = None
+        L.spvar_plan_stats.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i32)]
+        L.spvar_solve.argtypes = [vp, ctypes.POINTER(Params), u64, ctypes.POINTER(Result), vp]
+        L.spvar_plan_set_profiling.argtypes = [vp, i32]
+        L.spvar_plan_sweep_time.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i32)]
+        L.spvar_plan_shape.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32),
+                                       ctypes.POINTER(i32)]
+        _lib = L
+    return _lib
+
+
+def _strerror(code):
+    try:
+        return lib().spvar_strerror(code).decode()
+    except Exception:  # library not loadable: still report the code
+        return "error"
+
+
+def _check(rc, what):
+    if rc != OK:
+        raise SpvarError(rc, what)
+
+
+def _host(a, dtype):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+def _hp(a):
+    return a.ctypes.data_as(vp) if a is not None and a.size else None
+
+
+def _dp(t):
+    """Device pointer of a CUDA tensor (or None)."""
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    return vp(t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return vp(s.cuda_stream)
+
+
+def device_count():
+    c = ctypes.c_int(0)
+    _check(lib().spvar_device_count(ctypes.byref(c)), "spvar_device_count")
+    return c.value
+
+
+# --------------------------------------------------------------- problem
+def csr_from_edges(n, ei, ej, J):
+    """Edge list -> symmetric CSR (host); each pair once, i != j."""
+    ei, ej, J = _host(ei, np.int32), _host(ej, np.int32), _host(J, np.int32)
+    m = len(ei)
+    rp = np.zeros(n + 1, np.int32)
+    col = np.zeros(max(2 * m, 1), np.int32)
+    val = np.zeros(max(2 * m, 1), np.int32)
+    _check(lib().spvar_csr_from_edges(n, m, _hp(ei), _hp(ej), _hp(J), _hp(rp), _hp(col), _hp(val)),
+           "spvar_csr_from_edges")
+    return rp, col[:2 * m].copy(), val[:2 * m].copy()
+
+
+class Problem:
+    """Owning handle of a device-resident problem (Sec. I)."""
+
+    def __init__(self, handle):
+        self.handle = handle
+
+    @classmethod
+    def create(cls, n, row_ptr, col, val, h, offset=0, scale=1, stream=None):
+        rp, c, v, hh = (_host(row_ptr, np.int32), _host(col, np.int32), _host(val, np.int32),
+                        _host(h, np.int32))
+        out = vp()
+        _check(lib().spvar_problem_create(n, _hp(rp), _hp(c), _hp(v), _hp(hh), int(offset), int(scale),
+                                          _stream(stream), ctypes.byref(out)), "spvar_problem_create")
+        return cls(out)
+
+    @classmethod
+    def from_instance(cls, inst, stream=None):
+        rp, c, v = csr_from_edges(inst.n, inst.ei, inst.ej, inst.J)
+        return cls.create(inst.n, rp, c, v, inst.h, inst.offset, inst.scale, stream)
+
+    def info(self):
+        i = ProblemInfo()
+        _check(lib().spvar_problem_get_info(self.handle, ctypes.byref(i)), "spvar_problem_get_info")
+        return i
+
+    @property
+    def n(self):
+        return self.info().n
+
+    def download(self, stream=None):
+        i = self.info()
+        rp = np.zeros(i.n + 1, np.int32)
+        col = np.zeros(max(i.nnz, 1), np.int32)
+        val = np.zeros(max(i.nnz, 1), np.int32)
+        h = np.zeros(max(i.n, 1), np.int32)
+        colour = np.zeros(max(i.n, 1), np.int32)
+        _check(lib().spvar_problem_download(self.handle, _hp(rp), _hp(col), _hp(val), _hp(h), _hp(colour),
+                                            _stream(stream)), "spvar_problem_download")
+        return dict(n=i.n, row_ptr=rp, col=col[:i.nnz], val=val[:i.nnz], h=h[:i.n], colour=colour[:i.n],
+                    offset=i.offset, ncol=i.ncol, dmax=i.dmax, hzero=i.hzero, pm1=i.pm1)
+
+    def close(self):
+        if self.handle:
+            lib().spvar_problem_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# -------------------------------------------------------------- schedule
+def beta_geometric(T, beta0, beta1):
+    b = np.zeros(max(T, 1), np.float64)
+    _check(lib().spvar_beta_geometric(T, beta0, beta1, _hp(b)), "spvar_beta_geometric")
+    return b[:T]
+
+
+def thresholds(beta, dmax, scale=1):
+    beta = _host(beta, np.float64)
+    thr = np.zeros((len(beta), dmax + 1), np.uint32)
+    _check(lib().spvar_thresholds(len(beta), _hp(beta), dmax, scale, _hp(thr)), "spvar_thresholds")
+    return thr
+
+
+def thresholds_device(thr):
+    """Host uint32 table -> CUDA int32 tensor holding the same bits."""
+    import torch
+    return torch.from_numpy(_host(thr, np.uint32).view(np.int32)).cuda()
+
+
+# ------------------------------------------------------------------ calls
+def sample(problem, thr_dev, thr_stride, num_sweeps, num_samples, seed, start=0, phase=0,
+           spins=None, energies=None, stream=None):
+    """SA sample (Alg. 1 "obtain sample").  Returns (spins int32 [S, W], energies int64 [S])."""
+    import torch
+    n = problem.n
+    W = (n + 31) // 32
+    if spins is None:
+        spins = torch.empty((max(num_samples, 1), max(W, 1)), dtype=torch.int32, device="cuda")
+    if energies is None:
+        energies = torch.empty(max(num_samples, 1), dtype=torch.int64, device="cuda")
+    _check(lib().spvar_sample(problem.handle, num_sweeps, _dp(thr_dev), thr_stride, num_samples, seed, start,
+                              phase, _dp(spins), _dp(energies), _stream(stream)), "spvar_sample")
+    return spins, energies
+
+
+def persistence(problem, num_samples, spins, energies, elite_threshold, fix_num=1, fix_den=1, canon=-1,
+                stream=None):
+    """Alg. 1 persistence.  Returns (elite [k], counts [n], fixed int8 [n], nfixed [1], k)."""
+    import torch
+    n = problem.n
+    elite = torch.empty(max(num_samples, 1), dtype=torch.int32, device="cuda")
+    counts = torch.empty(max(n, 1), dtype=torch.int32, device="cuda")
+    fixed = torch.empty(max(n, 1), dtype=torch.int8, device="cuda")
+    nfixed = torch.empty(1, dtype=torch.int32, device="cuda")
+    k = i32(0)
+    _check(lib().spvar_persistence(problem.handle, num_samples, _dp(spins), _dp(energies), float(elite_threshold),
+                                   fix_num, fix_den, canon, _dp(elite), _dp(counts), _dp(fixed), _dp(nfixed),
+                                   ctypes.byref(k), _stream(stream)), "spvar_persistence")
+    return elite[:k.value], counts[:n], fixed[:n], nfixed, k.value
+
+
+def reduce(problem, fixed, stream=None):
+    """Alg. 1 update of J and h.  Returns (reduced Problem, old_of_new int32 [n'])."""
+    import torch
+    n = problem.n
+    old_of_new = torch.empty(max(n, 1), dtype=torch.int32, device="cuda")
+    out = vp()
+    _check(lib().spvar_reduce(problem.handle, _dp(fixed), _dp(old_of_new), _stream(stream), ctypes.byref(out)),
+           "spvar_reduce")
+    red = Problem(out)
+    return red, old_of_new[:red.n]
+
+
+def make_params(num_starts=1, fixing_sample_size=100, solving_sample_size=100, num_sweeps=1000, beta0=0.1,
+                beta1=3.0, elite_threshold=0.1, fix_num=1, fix_den=1, iterate=False, max_fix_phases=1, canon=-1,
+                form=FORM_BATCHED, replicas_per_block=0):
+    return Params(num_starts, fixing_sample_size, solving_sample_size, num_sweeps, beta0, beta1, elite_threshold,
+                  fix_num, fix_den, 1 if iterate else 0, max_fix_phases, canon, form, replicas_per_block)
+
+
+@dataclasses.dataclass
+class SolveOutput:
+    energies: object     # [starts, P, Smax]
+    counts: object       # [starts, P]
+    nfree: object        # [starts, P]
+    nphases: object      # [starts]
+    fixed: object        # [sum n_p * starts]
+    best_energy: object  # [starts]
+    best_state: object   # [sum n_p * starts]
+
+
+def _alloc_outputs(nslots, P, Smax, fm_total, device):
+    if device:
+        import torch
+        mk = lambda shape, dt: torch.empty(shape, dtype=dt, device="cuda")  # noqa: E731
+        return SolveOutput(mk((nslots, P, Smax), torch.int64), mk((nslots, P), torch.int32),
+                           mk((nslots, P), torch.int32), mk(nslots, torch.int32), mk(max(fm_total, 1), torch.int8),
+                           mk(nslots, torch.int64), mk(max(fm_total, 1), torch.int8))
+    return SolveOutput(np.zeros((nslots, P, Smax), np.int64), np.zeros((nslots, P), np.int32),
+                       np.zeros((nslots, P), np.int32), np.zeros(nslots, np.int32), np.zeros(max(fm_total, 1), np.int8),
+                       np.zeros(nslots, np.int64), np.zeros(max(fm_total, 1), np.int8))
+
+
+def _result_struct(o, device):
+    ptr = (lambda t: vp(t.data_ptr())) if device else _hp
+    return Result(1 if device else 0, ptr(o.energies), ptr(o.counts), ptr(o.nfree), ptr(o.nphases), ptr(o.fixed),
+                  ptr(o.best_energy), ptr(o.best_state))
+
+
+class Plan:
+    """Executable Multi-start SPVAR plan (Alg. 2) over one or more problems."""
+
+    def __init__(self, problems, params, budget_bytes=0, stream=None):
+        self.problems = list(problems)
+        self.params = params
+        arr = (vp * len(self.problems))(*[p.handle for p in self.problems])
+        out = vp()
+        _check(lib().spvar_plan_create(arr, len(self.problems), ctypes.byref(params), budget_bytes, _stream(stream),
+                                       ctypes.byref(out)), "spvar_plan_create")
+        self.handle = out
+        self.nslots = len(self.problems) * params.num_starts
+        self.P = params.max_fix_phases + 1
+        self.Smax = max(params.fixing_sample_size, params.solving_sample_size)
+        self.fm_total = sum(p.n for p in self.problems) * params.num_starts
+
+    def workspace_bytes(self):
+        return int(lib().spvar_plan_workspace_bytes(self.handle))
+
+    def alloc_outputs(self, device=True):
+        return _alloc_outputs(self.nslots, self.P, self.Smax, self.fm_total, device)
+
+    def run(self, seeds, out=None, device=True, stream=None):
+        seeds = list(seeds) if np.ndim(seeds) else [int(seeds)] * len(self.problems)
+        sarr = (u64 * len(seeds))(*[int(s) for s in seeds])
+        if out is None:
+            out = self.alloc_outputs(device)
+        res = _result_struct(out, device)
+        _check(lib().spvar_plan_run(self.handle, sarr, ctypes.byref(res), _stream(stream)), "spvar_plan_run")
+        return out
+
+    def stats(self):
+        a, p = i64(0), i32(0)
+        _check(lib().spvar_plan_stats(self.handle, ctypes.byref(a), ctypes.byref(p)), "spvar_plan_stats")
+        return a.value, p.value
+
+    def set_profiling(self, on=True):
+        _check(lib().spvar_plan_set_profiling(self.handle, 1 if on else 0), "spvar_plan_set_profiling")
+
+    def sweep_time(self):
+        ms, n = ctypes.c_double(0), i32(0)
+        _check(lib().spvar_plan_sweep_time(self.handle, ctypes.byref(ms), ctypes.byref(n)), "spvar_plan_sweep_time")
+        return ms.value, n.value
+
+    def shape(self):
+        b, r, s, g = i32(0), i32(0), i32(0), i32(0)
+        _check(lib().spvar_plan_shape(self.handle, ctypes.byref(b), ctypes.byref(r), ctypes.byref(s), ctypes.byref(g)),
+               "spvar_plan_shape")
+        return dict(block=b.value, replicas_per_block=r.value, staged=s.value, grid=g.value)
+
+    def close(self):
+        if self.handle:
+            lib().spvar_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def solve(problem, params, seed, device=False, stream=None):
+    """One-call Multi-start SPVAR (Alg. 2) of one problem; host outputs by default."""
+    nslots = params.num_starts
+    P = params.max_fix_phases + 1
+    Smax = max(params.fixing_sample_size, params.solving_sample_size)
+    out = _alloc_outputs(nslots, P, Smax, problem.n * nslots, device)
+    res = _result_struct(out, device)
+    _check(lib().spvar_solve(problem.handle, ctypes.byref(params), int(seed), ctypes.byref(res), _stream(stream)),
+           "spvar_solve")
+    return out
+
+
+def unpack_spins(words, n):
+    """Bit-packed rows (int32/uint32 [S, W]) -> int8 +-1 [S, n] (host)."""
+    w = np.ascontiguousarray(np.asarray(words)).view(np.uint32)
+    S = w.shape[0]
+    bits = (w[:, :, None] >> np.arange(32, dtype=np.uint32)[None, None, :]) & 1
+    return (bits.reshape(S, -1)[:, :n].astype(np.int8) * 2 - 1)
+
+
+def pack_spins(s):
+    """int8 +-1 [S, n] -> uint32 [S, ceil(n/32)] (host)."""
+    s = np.asarray(s)
+    S, n = s.shape
+    W = (n + 31) // 32
+    b = np.zeros((S, W * 32), np.uint32)
+    b[:, :n] = (s > 0)
+    return (b.reshape(S, W, 32) << np.arange(32, dtype=np.uint32)).sum(axis=2).astype(np.uint32)

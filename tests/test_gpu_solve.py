@@ -1,0 +1,116 @@
+"""GPU parity of Multi-start SPVAR (spvar_solve / plans, Alg. 2) against the
+oracle: recorded energies, phase sizes, fix maps and best states are
+identical in the batched (persistent + CUDA graph) and plain forms, for every
+sweep shape, and for several problems of uneven size in one plan."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1706_07826_gb300 import instances as I
+
+from gpu_cases import gpu_problem, oracle_problem, table
+
+pytestmark = pytest.mark.gpu
+
+
+def _oracle_solve(inst, T, seed, **kw):
+    return O.solve(oracle_problem(inst), table(inst, T), seed, **kw)
+
+
+def _check(out, ref, starts, P, n, slot0=0, fm0=0):
+    for s in range(starts):
+        g = slot0 + s
+        assert int(out.nphases[g]) == ref.nphases[s]
+        assert np.array_equal(np.asarray(out.counts[g]), ref.counts[s])
+        assert np.array_equal(np.asarray(out.nfree[g]), ref.nfree[s])
+        for ph in range(ref.nphases[s]):
+            c = ref.counts[s, ph]
+            assert np.array_equal(np.asarray(out.energies[g, ph, :c]), ref.energies[s, ph, :c]), (s, ph)
+        assert int(out.best_energy[g]) == ref.best_e[s]
+        a = fm0 + s * n
+        assert np.array_equal(np.asarray(out.fixed[a:a + n]), ref.fixed[s])
+        assert np.array_equal(np.asarray(out.best_state[a:a + n]), ref.best_state[s])
+
+
+SCASES = [
+    # name, instance, T, starts, S_fix, S_solve, elite, iterate, max_fix
+    ("cubic_L4_ispvar", lambda: I.cubic3d(4, 1100), 120, 1, 256, 0, 0.1, True, 64),
+    ("chimera_C4", lambda: I.chimera(4, 1200), 100, 3, 100, 100, 0.1, False, 1),
+    ("weak_strong_C3", lambda: I.weak_strong(3, 1300), 80, 4, 40, 40, 0.2, False, 1),
+    ("cubic_L5_odd_ispvar3", lambda: I.cubic3d(5, 1401), 60, 2, 64, 30, 0.2, True, 3),
+    ("random_h", lambda: I.random_graph(30, 70, 3, jmax=3, hmax=2), 60, 3, 33, 19, 0.3, False, 1),
+]
+
+
+@pytest.mark.parametrize("form", [0, 1], ids=["batched", "plain"])
+@pytest.mark.parametrize("name,make,T,starts,Sf,Ss,elite,iterate,mf", SCASES, ids=[c[0] for c in SCASES])
+def test_solve_parity(cuda_lib, form, name, make, T, starts, Sf, Ss, elite, iterate, mf):
+    from paper_1706_07826_gb300 import spvar
+    inst = make()
+    seed = 4242
+    ref = _oracle_solve(inst, T, seed, num_starts=starts, fixing_sample_size=Sf, solving_sample_size=Ss,
+                        elite_threshold=elite, iterate=iterate, max_fix_phases=mf)
+    prm = spvar.make_params(num_starts=starts, fixing_sample_size=Sf, solving_sample_size=Ss, num_sweeps=T,
+                            elite_threshold=elite, iterate=iterate, max_fix_phases=mf, form=form)
+    out = spvar.solve(gpu_problem(inst), prm, seed)
+    _check(out, ref, starts, mf + 1, inst.n)
+
+
+@pytest.mark.parametrize("rpb", [4, 8, 32])
+def test_solve_identical_for_every_sweep_shape(cuda_lib, rpb):
+    from paper_1706_07826_gb300 import spvar
+    inst = I.chimera(3, 9)
+    T, seed = 50, 17
+    ref = _oracle_solve(inst, T, seed, num_starts=2, fixing_sample_size=45, solving_sample_size=45,
+                        elite_threshold=0.2)
+    prm = spvar.make_params(num_starts=2, fixing_sample_size=45, solving_sample_size=45, num_sweeps=T,
+                            elite_threshold=0.2, replicas_per_block=rpb)
+    _check(spvar.solve(gpu_problem(inst), prm, seed), ref, 2, 2, inst.n)
+
+
+def test_uneven_problems_in_one_plan(cuda_lib):
+    """Problems of different sizes (3 colours for odd L) share one persistent launch per phase."""
+    from paper_1706_07826_gb300 import spvar
+    insts = [I.cubic3d(L, 1400 + L) for L in (3, 6, 5, 4)]
+    T, starts, Sf, Ss = 60, 2, 48, 24
+    dmax = max(O.dmax(oracle_problem(i)) for i in insts)
+    seeds = [11, 12, 13, 14]
+    plan = spvar.Plan([gpu_problem(i) for i in insts],
+                      spvar.make_params(num_starts=starts, fixing_sample_size=Sf, solving_sample_size=Ss,
+                                        num_sweeps=T, elite_threshold=0.1))
+    out = plan.run(seeds, device=False)
+    fm0 = 0
+    for pi, inst in enumerate(insts):
+        ref = O.solve(oracle_problem(inst), table(inst, T, dmax=dmax), seeds[pi], num_starts=starts,
+                      fixing_sample_size=Sf, solving_sample_size=Ss, elite_threshold=0.1)
+        _check(out, ref, starts, 2, inst.n, slot0=pi * starts, fm0=fm0)
+        fm0 += starts * inst.n
+    # a second run of the same plan (graph replay) reproduces the first
+    out2 = plan.run(seeds, device=False)
+    assert np.array_equal(out2.energies, out.energies) or all(
+        np.array_equal(out2.energies[s, p, :out.counts[s, p]], out.energies[s, p, :out.counts[s, p]])
+        for s in range(len(insts) * starts) for p in range(2))
+    attempts, phases = plan.stats()
+    assert attempts == sum(int(out.counts[s, p]) * int(out.nfree[s, p]) * T
+                           for s in range(len(insts) * starts) for p in range(2))
+
+
+def test_chimera_c8_full_size_properties(cuda_lib):
+    """The benchmark's workload (Chimera C8, 10 starts x (1000 + 1000) samples,
+    1000 sweeps): phase-0 energies of sampled replicas match the oracle one by
+    one, and every best state's recomputed energy is the reported best energy."""
+    from paper_1706_07826_gb300 import spvar
+    inst = I.chimera(8, 1200)
+    T, seed, starts = 1000, 42, 10
+    prm = spvar.make_params(num_starts=starts, fixing_sample_size=1000, solving_sample_size=1000,
+                            num_sweeps=T, elite_threshold=0.1)
+    out = spvar.solve(gpu_problem(inst), prm, seed)
+    op = oracle_problem(inst)
+    thr = table(inst, T)
+    for st, r in ((0, 0), (3, 517), (9, 999)):
+        _, e, _ = O.sample(op, thr, 1, seed, start=st, phase=0, r0=r)
+        assert out.energies[st, 0, r] == e[0]
+    for st in range(starts):
+        assert out.best_energy[st] == O.energy(op, out.best_state[st * inst.n:(st + 1) * inst.n])
+        assert out.best_energy[st] == min(out.energies[st, 0].min(), out.energies[st, 1].min())
+        assert out.nfree[st, 1] == inst.n - int((out.fixed[st * inst.n:(st + 1) * inst.n] != 0).sum())
