@@ -196,8 +196,14 @@ typedef struct spvar_params {
     int32_t max_fix_phases;      /* SPVAR phases per start, >= 1 */
     int32_t canon;               /* -1: when h == 0; 0: never; 1: always */
     int32_t form;                /* SPVAR_FORM_BATCHED or SPVAR_FORM_PLAIN */
-    int32_t replicas_per_block;  /* 0: autotune; else a multiple of 4 */
+    int32_t replicas_per_block;  /* 0: autotune the sweep shape; else a multiple of 4 */
+    int32_t sweep_kernel;        /* with replicas_per_block > 0: SPVAR_SWEEP_* */
+    int32_t sweep_block;         /* with replicas_per_block > 0: threads per CTA (128/256/512), 0 = 256 */
 } spvar_params;
+
+#define SPVAR_SWEEP_AUTO 0    /* register kernel when eligible, else general */
+#define SPVAR_SWEEP_GENERAL 1 /* general integer-coupler kernel */
+#define SPVAR_SWEEP_PM1 2     /* register-resident kernel: |J| = 1, degree <= 8, dmax <= 254 */
 
 #define SPVAR_FORM_BATCHED 0 /* every start of every problem in one persistent launch per phase */
 #define SPVAR_FORM_PLAIN 1   /* one start at a time, one launch per kernel and start */
@@ -259,8 +265,9 @@ int spvar_plan_set_profiling(spvar_plan *plan, int32_t on);
 int spvar_plan_sweep_time(const spvar_plan *plan, double *total_ms, int32_t *launches);
 
 /* The sweep launch shape the plan chose (autotuned or requested): threads
- * per CTA, replicas per CTA, 1 if the layout is staged in shared memory,
- * persistent grid size. */
+ * per CTA, replicas per CTA, kernel (0: general kernel reading its layout
+ * from global memory, 1: general kernel with the layout staged in shared
+ * memory, 2: register-resident +-1 kernel), persistent grid size. */
 int spvar_plan_shape(const spvar_plan *plan, int32_t *block, int32_t *replicas_per_block,
                      int32_t *staged, int32_t *grid);
 

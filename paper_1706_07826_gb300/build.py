@@ -14,8 +14,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OBJDIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libspvar.so")
-SOURCES = ["api.cpp", "sweep.cu", "persist.cu", "plan.cu"]
-HEADERS = ["spvar_internal.h", "philox.cuh", "persist.cuh"]
+SOURCES = ["api.cpp", "sweep.cu", "sweep_pm1.cu", "persist.cu", "plan.cu"]
+HEADERS = ["spvar_internal.h", "philox.cuh", "persist.cuh", "sweep_common.cuh"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 

@@ -385,10 +385,18 @@ int spvar_sample(const spvar_problem *p, int32_t num_sweeps, const uint32_t *thr
     const int quads = ceil_div(num_samples, 4);
     const int sms = device_sms();
     const int Q = std::max(1, std::min(8, quads / (2 * sms)));
-    const int block = (H.n >= 512) ? 256 : 128;
     const int optin = device_smem_optin();
-    bool stage = sweep_smem_bytes(H.n, Q, thr_stride, H.maxdeg, true) <= (size_t)optin;
-    size_t smem = sweep_smem_bytes(H.n, Q, thr_stride, H.maxdeg, stage);
+    // shape: the register-resident +-1 kernel when it applies, else the general one
+    SweepShape sh{0, (H.n >= 512) ? 256 : 128, Q, 1, 0, 0};
+    if (pm1_kernel_eligible(H.pm1 != 0, H.dmax, H.maxdeg)) {
+        for (int blk : {256, 512, 128}) {
+            const int ns = pm1_nslot(H.n, Q, blk);
+            const int md = H.maxdeg <= 6 ? 6 : 8;
+            if (ns > 0 && pm1_shape_ok(blk, ns, md)) { sh = SweepShape{1, blk, Q, 0, ns, md}; break; }
+        }
+    }
+    if (sh.kind == 0 && sweep_shape_smem(sh, H.n, thr_stride, H.maxdeg) > (size_t)optin) sh.stage = 0;
+    const size_t smem = sweep_shape_smem(sh, H.n, thr_stride, H.maxdeg);
     if (smem > (size_t)optin) return SPVAR_ELIMIT;
 
     SweepLaunch L;
@@ -405,11 +413,11 @@ int spvar_sample(const spvar_problem *p, int32_t num_sweeps, const uint32_t *thr
     L.thr_stride = thr_stride;
     L.T = num_sweeps;
     L.Q = Q;
-    L.stage_ell = stage ? 1 : 0;
+    L.stage_ell = sh.stage;
     L.max_n = H.n;
     L.max_deg = H.maxdeg;
     const int grid = ceil_div(quads, Q);
-    SPVAR_CUDA_TRY(launch_sweep(L, H.pm1 != 0, block, grid, smem, as_stream(stream)));
+    SPVAR_CUDA_TRY(launch_sweep_shape(L, sh, H.pm1 != 0, grid, smem, as_stream(stream)));
     return SPVAR_OK;
 }
 

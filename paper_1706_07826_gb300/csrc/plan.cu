@@ -47,7 +47,8 @@ struct spvar_plan {
     int64_t *d_best_e = nullptr;
     int8_t *d_fmap = nullptr, *d_best = nullptr;
     size_t fmap_total = 0;
-    int block = 256, Q = 1, stage = 1, sweep_grid = 1, sms = 1;
+    SweepShape shape{0, 256, 1, 0, 0, 0};
+    int sweep_grid = 1, sms = 1, dmax = 0;
     size_t sweep_smem = 0;
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t graph = nullptr;
@@ -70,7 +71,7 @@ struct TuneKey {
                std::tie(o.max_n, o.max_deg, o.pm1, o.S, o.nslots, o.form, o.thr_stride);
     }
 };
-std::map<TuneKey, std::tuple<int, int, int>> g_tune_cache;
+std::map<TuneKey, SweepShape> g_tune_cache;
 std::mutex g_tune_mu;
 
 SweepLaunch make_launch(const spvar_plan *pl, int T)
@@ -84,8 +85,8 @@ SweepLaunch make_launch(const spvar_plan *pl, int T)
     L.thr = pl->d_thr;
     L.thr_stride = pl->thr_stride;
     L.T = T;
-    L.Q = pl->Q;
-    L.stage_ell = pl->stage;
+    L.Q = pl->shape.Q;
+    L.stage_ell = pl->shape.stage;
     L.max_n = pl->max_n0;
     L.max_deg = pl->max_deg;
     return L;
@@ -93,24 +94,28 @@ SweepLaunch make_launch(const spvar_plan *pl, int T)
 
 int grid_for(const spvar_plan *pl, int items)
 {
-    const int occ = std::max(1, sweep_max_active_blocks(pl->pm1, pl->block, pl->sweep_smem, pl->stage != 0));
+    const int occ = std::max(1, sweep_shape_occupancy(pl->shape, pl->pm1, pl->sweep_smem));
     return std::max(1, std::min(items, occ * pl->sms));
 }
 
 // One phase of the given slots (all of them in the batched form).
 cudaError_t launch_phase(spvar_plan *pl, Slot *slots, int nslots, int T, int grid, cudaStream_t st,
-                         bool count_active)
+                         bool count_active, bool capturing = false)
 {
+    // inside stream capture an event record only becomes a graph node when external
+    auto record = [&](cudaEvent_t ev) {
+        return capturing ? cudaEventRecordWithFlags(ev, st, cudaEventRecordExternal) : cudaEventRecord(ev, st);
+    };
     SolveConsts C = pl->C;
     C.nslots = nslots;
-    C.Q = pl->Q;
+    C.Q = pl->shape.Q;
     cudaError_t e = launch_plan(slots, C, pl->d_jobs, pl->d_items, pl->d_ctr + 0, pl->d_ctr + 1, st);
     if (e != cudaSuccess) return e;
     SweepLaunch L = make_launch(pl, T);
-    if ((e = cudaEventRecord(pl->ev_sweep[0], st)) != cudaSuccess) return e;
-    e = launch_sweep(L, pl->pm1, pl->block, grid, pl->sweep_smem, st);
+    if ((e = record(pl->ev_sweep[0])) != cudaSuccess) return e;
+    e = launch_sweep_shape(L, pl->shape, pl->pm1, grid, pl->sweep_smem, st);
     if (e != cudaSuccess) return e;
-    if ((e = cudaEventRecord(pl->ev_sweep[1], st)) != cudaSuccess) return e;
+    if ((e = record(pl->ev_sweep[1])) != cudaSuccess) return e;
     if ((e = launch_elite_slots(slots, C, st)) != cudaSuccess) return e;
     if ((e = launch_count_slots(slots, C, pl->max_n0, st)) != cudaSuccess) return e;
     return launch_reduce_slots(slots, C, count_active ? pl->d_ctr + 2 : nullptr, st);
@@ -128,7 +133,36 @@ int upload_slots(spvar_plan *pl, const uint64_t *seeds, cudaStream_t st)
     return SPVAR_OK;
 }
 
-// Times a short sweep of the plan's first phase for each candidate shape.
+// Candidate sweep shapes for a plan: the general kernel with and without the
+// staged layout, and (for +-1 problems) the register-resident kernel.
+std::vector<SweepShape> candidate_shapes(const spvar_plan *pl, int optin)
+{
+    std::vector<SweepShape> out;
+    const int blocks[3] = {128, 256, 512};
+    const int qs[4] = {1, 2, 4, 8};
+    const int quads = ceil_div(pl->C.S_fix, 4);
+    for (int bi = 0; bi < 3; ++bi)
+        for (int qi = 0; qi < 4; ++qi) {
+            const int Q = qs[qi];
+            if (Q > 1 && quads < Q) continue;
+            for (int stg = 1; stg >= 0; --stg) {
+                SweepShape sh{0, blocks[bi], Q, stg, 0, 0};
+                if (sweep_shape_smem(sh, pl->max_n0, pl->thr_stride, pl->max_deg) <= (size_t)optin) out.push_back(sh);
+            }
+            if (pm1_kernel_eligible(pl->pm1, pl->dmax, pl->max_deg)) {
+                const int ns = pm1_nslot(pl->max_n0, Q, blocks[bi]);
+                const int md = pl->max_deg <= 6 ? 6 : 8;
+                SweepShape sh{1, blocks[bi], Q, 0, ns, md};
+                if (ns > 0 && pm1_shape_ok(blocks[bi], ns, md) &&
+                    sweep_shape_smem(sh, pl->max_n0, pl->thr_stride, pl->max_deg) <= (size_t)optin)
+                    out.push_back(sh);
+            }
+        }
+    return out;
+}
+
+// Times the plan's first phase (a short anneal) for every candidate shape and
+// keeps the fastest; results are cached per problem/plan geometry.
 void autotune(spvar_plan *pl, cudaStream_t st, int optin)
 {
     const TuneKey key{pl->max_n0, pl->max_deg, pl->pm1 ? 1 : 0, pl->C.S_fix, pl->C.nslots,
@@ -137,67 +171,54 @@ void autotune(spvar_plan *pl, cudaStream_t st, int optin)
         std::lock_guard<std::mutex> g(g_tune_mu);
         auto it = g_tune_cache.find(key);
         if (it != g_tune_cache.end()) {
-            std::tie(pl->block, pl->Q, pl->stage) = it->second;
-            pl->sweep_smem = sweep_smem_bytes(pl->max_n0, pl->Q, pl->thr_stride, pl->max_deg, pl->stage != 0);
+            pl->shape = it->second;
+            pl->sweep_smem = sweep_shape_smem(pl->shape, pl->max_n0, pl->thr_stride, pl->max_deg);
             return;
         }
     }
-    const int Tt = std::min(pl->T, 8);
+    const int Tt = std::min(pl->T, 48);
     float best = 1e30f;
-    std::tuple<int, int, int> pick{256, 1, 0};
+    SweepShape pick{0, 256, 1, 0, 0, 0};
     bool found = false;
     cudaEvent_t a, b;
     cudaEventCreate(&a);
     cudaEventCreate(&b);
-    const int blocks[3] = {128, 256, 512};
-    const int qs[4] = {1, 2, 4, 8};
-    for (int bi = 0; bi < 3; ++bi)
-        for (int qi = 0; qi < 4; ++qi)
-            for (int stg = 1; stg >= 0; --stg) {
-                const size_t smem = sweep_smem_bytes(pl->max_n0, qs[qi], pl->thr_stride, pl->max_deg, stg != 0);
-                if (smem > (size_t)optin) continue;
-                if (qs[qi] > 1 && ceil_div(pl->C.S_fix, 4) < qs[qi]) continue;
-                pl->block = blocks[bi];
-                pl->Q = qs[qi];
-                pl->stage = stg;
-                pl->sweep_smem = smem;
-                if (sweep_max_active_blocks(pl->pm1, pl->block, smem, stg != 0) < 1) continue;
-                const int nslots = (pl->prm.form == SPVAR_FORM_PLAIN) ? 1 : pl->C.nslots;
-                SolveConsts C = pl->C;
-                C.nslots = nslots;
-                C.Q = pl->Q;
-                launch_slots_init(pl->d_slots, C, pl->max_n0, st);
-                launch_plan(pl->d_slots, C, pl->d_jobs, pl->d_items, pl->d_ctr, pl->d_ctr + 1, st);
-                const int items = nslots * ceil_div(ceil_div(pl->C.Smax, 4), pl->Q);
-                const int grid = (pl->prm.form == SPVAR_FORM_PLAIN) ? items : grid_for(pl, items);
-                SweepLaunch L = make_launch(pl, Tt);
-                float ms = 0;
-                cudaEventRecord(a, st);
-                cudaError_t e = launch_sweep(L, pl->pm1, pl->block, grid, smem, st);
-                cudaEventRecord(b, st);
-                if (e != cudaSuccess || cudaEventSynchronize(b) != cudaSuccess) {
-                    cudaGetLastError();
-                    continue;
-                }
-                cudaEventElapsedTime(&ms, a, b);
-                // second run: the first includes one-time setup
-                launch_plan(pl->d_slots, C, pl->d_jobs, pl->d_items, pl->d_ctr, pl->d_ctr + 1, st);
-                cudaEventRecord(a, st);
-                launch_sweep(L, pl->pm1, pl->block, grid, smem, st);
-                cudaEventRecord(b, st);
-                cudaEventSynchronize(b);
-                cudaEventElapsedTime(&ms, a, b);
-                if (ms < best) {
-                    best = ms;
-                    pick = std::make_tuple(pl->block, pl->Q, stg);
-                    found = true;
-                }
-            }
+    for (const SweepShape &sh : candidate_shapes(pl, optin)) {
+        pl->shape = sh;
+        pl->sweep_smem = sweep_shape_smem(sh, pl->max_n0, pl->thr_stride, pl->max_deg);
+        if (sweep_shape_occupancy(sh, pl->pm1, pl->sweep_smem) < 1) continue;
+        const int nslots = (pl->prm.form == SPVAR_FORM_PLAIN) ? 1 : pl->C.nslots;
+        SolveConsts C = pl->C;
+        C.nslots = nslots;
+        C.Q = sh.Q;
+        launch_slots_init(pl->d_slots, C, pl->max_n0, st);
+        const int items = nslots * ceil_div(ceil_div(pl->C.Smax, 4), sh.Q);
+        const int grid = (pl->prm.form == SPVAR_FORM_PLAIN) ? items : grid_for(pl, items);
+        SweepLaunch L = make_launch(pl, Tt);
+        float ms = 1e30f;
+        bool ok = true;
+        for (int rep = 0; rep < 2 && ok; ++rep) {
+            launch_plan(pl->d_slots, C, pl->d_jobs, pl->d_items, pl->d_ctr, pl->d_ctr + 1, st);
+            cudaEventRecord(a, st);
+            ok = launch_sweep_shape(L, sh, pl->pm1, grid, pl->sweep_smem, st) == cudaSuccess;
+            cudaEventRecord(b, st);
+            if (!ok || cudaEventSynchronize(b) != cudaSuccess) { ok = false; break; }
+            float m = 0.f;
+            cudaEventElapsedTime(&m, a, b);
+            ms = std::min(ms, m);  // the first repetition includes one-time setup
+        }
+        if (!ok) { cudaGetLastError(); continue; }
+        if (ms < best) {
+            best = ms;
+            pick = sh;
+            found = true;
+        }
+    }
     cudaEventDestroy(a);
     cudaEventDestroy(b);
-    if (!found) pick = std::make_tuple(256, 1, 0);
-    std::tie(pl->block, pl->Q, pl->stage) = pick;
-    pl->sweep_smem = sweep_smem_bytes(pl->max_n0, pl->Q, pl->thr_stride, pl->max_deg, pl->stage != 0);
+    if (!found) pick = SweepShape{0, 256, 1, 0, 0, 0};
+    pl->shape = pick;
+    pl->sweep_smem = sweep_shape_smem(pl->shape, pl->max_n0, pl->thr_stride, pl->max_deg);
     std::lock_guard<std::mutex> g(g_tune_mu);
     g_tune_cache[key] = pick;
 }
@@ -230,7 +251,9 @@ int spvar_plan_create(const spvar_problem *const *problems, int32_t nproblems,
         p.max_fix_phases < 1 || p.fix_num <= 0 || p.fix_den <= 0 || p.fix_num > p.fix_den ||
         !(p.elite_threshold > 0.0) || !(p.elite_threshold <= 1.0) || !(p.beta0 > 0.0) || !(p.beta1 > 0.0) ||
         p.canon < -1 || p.canon > 1 || (p.form != SPVAR_FORM_BATCHED && p.form != SPVAR_FORM_PLAIN) ||
-        p.replicas_per_block < 0 || (p.replicas_per_block % 4) != 0)
+        p.replicas_per_block < 0 || (p.replicas_per_block % 4) != 0 || p.sweep_kernel < 0 ||
+        p.sweep_kernel > 2 || (p.sweep_block != 0 && p.sweep_block != 128 && p.sweep_block != 256 &&
+                               p.sweep_block != 512))
         return SPVAR_EINVAL;
     const int Smax = std::max(p.fixing_sample_size, p.solving_sample_size);
     if (Smax > SPVAR_MAX_SAMPLES || p.num_sweeps > SPVAR_MAX_SWEEPS ||
@@ -257,6 +280,7 @@ int spvar_plan_create(const spvar_problem *const *problems, int32_t nproblems,
     }
     pl->T = p.num_sweeps;
     pl->thr_stride = dmax + 1;
+    pl->dmax = dmax;
     const int P_slots = p.max_fix_phases + 1;
     const int nslots = nproblems * p.num_starts;
     // elite count k = ceil(elite * S), clamped to [1, S]
@@ -414,17 +438,28 @@ int spvar_plan_create(const spvar_problem *const *problems, int32_t nproblems,
 
     // sweep shape
     if (p.replicas_per_block > 0) {
-        pl->Q = p.replicas_per_block / 4;
-        pl->block = 256;
-        pl->stage = sweep_smem_bytes(pl->max_n0, pl->Q, pl->thr_stride, pl->max_deg, true) <= (size_t)optin;
-        pl->sweep_smem = sweep_smem_bytes(pl->max_n0, pl->Q, pl->thr_stride, pl->max_deg, pl->stage != 0);
+        // requested shape: replicas per CTA, kernel and block size
+        const int Q = p.replicas_per_block / 4;
+        const int blk = p.sweep_block ? p.sweep_block : 256;
+        const bool elig = pm1_kernel_eligible(pl->pm1, pl->dmax, pl->max_deg);
+        SweepShape sh{0, blk, Q, 1, 0, 0};
+        if (p.sweep_kernel == SPVAR_SWEEP_PM1 || (p.sweep_kernel == SPVAR_SWEEP_AUTO && elig)) {
+            const int ns = pm1_nslot(pl->max_n0, Q, blk);
+            const int md = pl->max_deg <= 6 ? 6 : 8;
+            if (!elig || ns == 0 || !pm1_shape_ok(blk, ns, md)) { plan_free(pl); return SPVAR_ELIMIT; }
+            sh = SweepShape{1, blk, Q, 0, ns, md};
+        } else if (sweep_shape_smem(sh, pl->max_n0, pl->thr_stride, pl->max_deg) > (size_t)optin) {
+            sh.stage = 0;
+        }
+        pl->shape = sh;
+        pl->sweep_smem = sweep_shape_smem(sh, pl->max_n0, pl->thr_stride, pl->max_deg);
         if (pl->sweep_smem > (size_t)optin) { plan_free(pl); return SPVAR_ELIMIT; }
     } else {
         autotune(pl, st, optin);
         if (pl->sweep_smem > (size_t)optin) { plan_free(pl); return SPVAR_ELIMIT; }
     }
-    pl->C.Q = pl->Q;
-    const int items = nslots * ceil_div(ceil_div(Smax, 4), pl->Q);
+    pl->C.Q = pl->shape.Q;
+    const int items = nslots * ceil_div(ceil_div(Smax, 4), pl->shape.Q);
     pl->sweep_grid = grid_for(pl, items);
 
     // capture one batched phase as a CUDA graph
@@ -433,7 +468,8 @@ int spvar_plan_create(const spvar_problem *const *problems, int32_t nproblems,
             cudaGraph_t g = nullptr;
             bool cap = cudaStreamBeginCapture(pl->cap_stream, cudaStreamCaptureModeRelaxed) == cudaSuccess;
             if (cap) {
-                cudaError_t e = launch_phase(pl, pl->d_slots, nslots, pl->T, pl->sweep_grid, pl->cap_stream, true);
+                cudaError_t e =
+                    launch_phase(pl, pl->d_slots, nslots, pl->T, pl->sweep_grid, pl->cap_stream, true, true);
                 if (e == cudaSuccess)
                     e = cudaMemcpyAsync(pl->h_nactive, pl->d_ctr + 2, sizeof(int32_t), cudaMemcpyDeviceToHost,
                                         pl->cap_stream);
@@ -489,7 +525,7 @@ int spvar_plan_run(spvar_plan *pl, const uint64_t *seeds, const spvar_result *re
             }
         }
     } else {
-        const int grid = ceil_div(ceil_div(pl->C.Smax, 4), pl->Q);
+        const int grid = ceil_div(ceil_div(pl->C.Smax, 4), pl->shape.Q);
         for (int s = 0; s < nslots; ++s) {
             for (int it = 0; it < pl->iters_max; ++it) {
                 SPVAR_CUDA_TRY(launch_phase(pl, pl->d_slots + s, 1, pl->T, grid, st, iterate));
@@ -541,9 +577,9 @@ int spvar_plan_shape(const spvar_plan *plan, int32_t *block, int32_t *replicas_p
                      int32_t *staged, int32_t *grid)
 {
     if (!plan) return SPVAR_EINVAL;
-    if (block) *block = plan->block;
-    if (replicas_per_block) *replicas_per_block = 4 * plan->Q;
-    if (staged) *staged = plan->stage;
+    if (block) *block = plan->shape.block;
+    if (replicas_per_block) *replicas_per_block = 4 * plan->shape.Q;
+    if (staged) *staged = plan->shape.kind == 1 ? 2 : plan->shape.stage;
     if (grid) *grid = plan->sweep_grid;
     return SPVAR_OK;
 }

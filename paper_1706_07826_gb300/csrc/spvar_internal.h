@@ -124,6 +124,45 @@ cudaError_t launch_sweep(const SweepLaunch &L, bool pm1, int block, int grid, si
                          cudaStream_t stream);
 int sweep_max_active_blocks(bool pm1, int block, size_t smem, bool stage_ell);
 
+// Register-resident +-1 sweep (sweep_pm1.cu).
+bool pm1_shape_ok(int block, int nslot, int maxd);
+size_t pm1_smem_bytes(int max_n, int Q);
+cudaError_t launch_sweep_pm1(const SweepLaunch &L, int block, int nslot, int maxd, int grid, size_t smem,
+                             cudaStream_t st);
+int pm1_max_active_blocks(int block, int nslot, int maxd, size_t smem);
+
+// Launch shape of a sweep: kind 0 = general kernel (stage: layout staged in
+// shared memory), kind 1 = register-resident +-1 kernel (nslot items per
+// thread, maxd neighbour registers per item).
+struct SweepShape {
+    int kind, block, Q, stage, nslot, maxd;
+};
+// The register kernel applies to +-1 couplers, degree <= 8 and dmax <= 254.
+inline bool pm1_kernel_eligible(bool pm1, int dmax, int maxdeg) { return pm1 && dmax <= 254 && maxdeg <= 8; }
+// Smallest slot count (1, 2, 4) covering max_n * Q items with `block` threads, 0 if none.
+inline int pm1_nslot(int max_n, int Q, int block)
+{
+    const long long items = (long long)max_n * Q;
+    for (int ns = 1; ns <= 4; ns <<= 1)
+        if ((long long)ns * block >= items) return ns;
+    return 0;
+}
+inline size_t sweep_shape_smem(const SweepShape &s, int max_n, int thr_stride, int max_deg)
+{
+    return s.kind == 1 ? pm1_smem_bytes(max_n, s.Q) : sweep_smem_bytes(max_n, s.Q, thr_stride, max_deg, s.stage != 0);
+}
+inline cudaError_t launch_sweep_shape(const SweepLaunch &L, const SweepShape &s, bool pm1, int grid, size_t smem,
+                                      cudaStream_t st)
+{
+    return s.kind == 1 ? launch_sweep_pm1(L, s.block, s.nslot, s.maxd, grid, smem, st)
+                       : launch_sweep(L, pm1, s.block, grid, smem, st);
+}
+inline int sweep_shape_occupancy(const SweepShape &s, bool pm1, size_t smem)
+{
+    return s.kind == 1 ? pm1_max_active_blocks(s.block, s.nslot, s.maxd, smem)
+                       : sweep_max_active_blocks(pm1, s.block, smem, s.stage != 0);
+}
+
 // Elite selection of one sample set (standalone form).
 cudaError_t launch_elite_single(const int64_t *energies, int S, int k, int32_t *elite,
                                 cudaStream_t stream);

@@ -18,8 +18,7 @@
 // In queue mode the grid is persistent: each CTA pulls work items (job,
 // quad range) from an atomic cursor until the list is exhausted, so jobs of
 // uneven size share one launch.
-#include "philox.cuh"
-#include "spvar_internal.h"
+#include "sweep_common.cuh"
 
 namespace spvar {
 
@@ -86,43 +85,6 @@ __device__ __forceinline__ uint32_t flip_mask(uint32_t own, uint32_t meta, const
         flip |= (uint32_t)acc << (8 * r);
     }
     return flip;
-}
-
-// Twice the energy contribution of one spin for the four replicas:
-// s_i (h_i + f_i) with f_i = h_i + sum_j J_ij s_j  (sum over i gives 2E).
-template <bool PM1>
-__device__ __forceinline__ void energy2(uint32_t own, uint32_t meta, const uint32_t *ell, int ld,
-                                        int p, const uint32_t *swq, int out[4])
-{
-    const int deg = (int)(meta & 0xFFFFu);
-    const int h = (int)meta >> 16;
-    if (PM1) {
-        uint32_t acc = 0;
-        for (int d = 0; d < deg; ++d) {
-            const uint32_t e = ell[d * ld + p];
-            acc += own ^ swq[e & 0xFFFFu] ^ ((e >> 31) ? 0x01010101u : 0u);
-        }
-#pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            const int s = 2 * (int)((own >> (8 * r)) & 1u) - 1;
-            out[r] = 2 * s * h + deg - 2 * (int)((acc >> (8 * r)) & 0xFFu);
-        }
-    } else {
-        int a[4] = {0, 0, 0, 0}, sumJ = 0;
-        for (int d = 0; d < deg; ++d) {
-            const uint32_t e = ell[d * ld + p];
-            const int Jv = (int)e >> 16;
-            const uint32_t w = swq[e & 0xFFFFu];
-            sumJ += Jv;
-#pragma unroll
-            for (int r = 0; r < 4; ++r) a[r] += Jv * (int)((w >> (8 * r)) & 1u);
-        }
-#pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            const int s = 2 * (int)((own >> (8 * r)) & 1u) - 1;
-            out[r] = s * (h + h - sumJ + 2 * a[r]);
-        }
-    }
 }
 
 template <bool PM1, bool STAGE, int B>

@@ -16,6 +16,7 @@ LIB_PATH = os.path.join(HERE, "libspvar.so")
 
 OK, EINVAL, EOVERFLOW, ENOMEM, EBUDGET, ETIMEOUT, ECUDA, ELIMIT = 0, -1, -2, -3, -4, -5, -6, -7
 FORM_BATCHED, FORM_PLAIN = 0, 1
+SWEEP_AUTO, SWEEP_GENERAL, SWEEP_PM1 = 0, 1, 2
 MAX_N, MAX_DEGREE, MAX_SWEEPS, MAX_PHASE, MAX_SAMPLES = 32768, 32, 1048574, 4095, 16384
 
 vp = ctypes.c_void_p
@@ -41,7 +42,7 @@ class Params(ctypes.Structure):
                 ("num_sweeps", i32), ("beta0", ctypes.c_double), ("beta1", ctypes.c_double),
                 ("elite_threshold", ctypes.c_double), ("fix_num", i32), ("fix_den", i32),
                 ("iterate", i32), ("max_fix_phases", i32), ("canon", i32), ("form", i32),
-                ("replicas_per_block", i32)]
+                ("replicas_per_block", i32), ("sweep_kernel", i32), ("sweep_block", i32)]
 
 
 class Result(ctypes.Structure):
@@ -265,9 +266,10 @@ def reduce(problem, fixed, stream=None):
 
 def make_params(num_starts=1, fixing_sample_size=100, solving_sample_size=100, num_sweeps=1000, beta0=0.1,
                 beta1=3.0, elite_threshold=0.1, fix_num=1, fix_den=1, iterate=False, max_fix_phases=1, canon=-1,
-                form=FORM_BATCHED, replicas_per_block=0):
+                form=FORM_BATCHED, replicas_per_block=0, sweep_kernel=SWEEP_AUTO, sweep_block=0):
     return Params(num_starts, fixing_sample_size, solving_sample_size, num_sweeps, beta0, beta1, elite_threshold,
-                  fix_num, fix_den, 1 if iterate else 0, max_fix_phases, canon, form, replicas_per_block)
+                  fix_num, fix_den, 1 if iterate else 0, max_fix_phases, canon, form, replicas_per_block,
+                  sweep_kernel, sweep_block)
 
 
 @dataclasses.dataclass
@@ -347,7 +349,8 @@ class Plan:
         b, r, s, g = i32(0), i32(0), i32(0), i32(0)
         _check(lib().spvar_plan_shape(self.handle, ctypes.byref(b), ctypes.byref(r), ctypes.byref(s), ctypes.byref(g)),
                "spvar_plan_shape")
-        return dict(block=b.value, replicas_per_block=r.value, staged=s.value, grid=g.value)
+        return dict(block=b.value, replicas_per_block=r.value, kernel=("general", "general-staged", "pm1-register")[s.value],
+                    grid=g.value)
 
     def close(self):
         if self.handle:

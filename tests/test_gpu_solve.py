@@ -56,16 +56,44 @@ def test_solve_parity(cuda_lib, form, name, make, T, starts, Sf, Ss, elite, iter
     _check(out, ref, starts, mf + 1, inst.n)
 
 
-@pytest.mark.parametrize("rpb", [4, 8, 32])
-def test_solve_identical_for_every_sweep_shape(cuda_lib, rpb):
+SHAPES = [(4, 1, 256), (8, 1, 128), (32, 1, 512), (4, 2, 256), (8, 2, 128), (4, 2, 512), (16, 2, 256),
+          (32, 2, 128)]
+
+
+@pytest.mark.parametrize("rpb,kernel,block", SHAPES, ids=["%d-%d-%d" % s for s in SHAPES])
+@pytest.mark.parametrize("make", [lambda: I.chimera(3, 9), lambda: I.cubic3d(5, 19)], ids=["chimera", "cubic_odd"])
+def test_solve_identical_for_every_sweep_shape(cuda_lib, rpb, kernel, block, make):
+    """General and register-resident kernels, several replicas per CTA and
+    block sizes (1, 2 or 4 register slots per thread): all identical."""
     from paper_1706_07826_gb300 import spvar
-    inst = I.chimera(3, 9)
+    inst = make()
     T, seed = 50, 17
     ref = _oracle_solve(inst, T, seed, num_starts=2, fixing_sample_size=45, solving_sample_size=45,
                         elite_threshold=0.2)
     prm = spvar.make_params(num_starts=2, fixing_sample_size=45, solving_sample_size=45, num_sweeps=T,
-                            elite_threshold=0.2, replicas_per_block=rpb)
-    _check(spvar.solve(gpu_problem(inst), prm, seed), ref, 2, 2, inst.n)
+                            elite_threshold=0.2, replicas_per_block=rpb, sweep_kernel=kernel, sweep_block=block)
+    plan = spvar.Plan([gpu_problem(inst)], prm)
+    assert plan.shape()["kernel"] == ("pm1-register" if kernel == 2 else plan.shape()["kernel"])
+    _check(plan.run(seed, device=False), ref, 2, 2, inst.n)
+
+
+def test_register_kernel_rejects_general_couplers(cuda_lib):
+    from paper_1706_07826_gb300 import spvar
+    prm = spvar.make_params(num_starts=1, fixing_sample_size=8, solving_sample_size=8, num_sweeps=4,
+                            replicas_per_block=4, sweep_kernel=spvar.SWEEP_PM1)
+    with pytest.raises(spvar.SpvarError):
+        spvar.Plan([gpu_problem(I.weak_strong(2, 1))], prm)
+
+
+def test_profiling_reports_sweep_time(cuda_lib):
+    from paper_1706_07826_gb300 import spvar
+    inst = I.chimera(4, 3)
+    plan = spvar.Plan([gpu_problem(inst)], spvar.make_params(num_starts=2, fixing_sample_size=64,
+                                                             solving_sample_size=32, num_sweeps=40))
+    plan.set_profiling(True)
+    plan.run(5, device=False)
+    ms, n = plan.sweep_time()
+    assert n == 2 and ms > 0
 
 
 def test_uneven_problems_in_one_plan(cuda_lib):
