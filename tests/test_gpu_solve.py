@@ -57,7 +57,7 @@ def test_solve_parity(cuda_lib, form, name, make, T, starts, Sf, Ss, elite, iter
 
 
 SHAPES = [(4, 1, 256), (8, 1, 128), (32, 1, 512), (4, 2, 256), (8, 2, 128), (4, 2, 512), (16, 2, 256),
-          (32, 2, 128)]
+          (16, 2, 128)]
 
 
 @pytest.mark.parametrize("rpb,kernel,block", SHAPES, ids=["%d-%d-%d" % s for s in SHAPES])
