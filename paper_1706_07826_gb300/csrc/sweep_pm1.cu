@@ -59,8 +59,24 @@ __device__ __forceinline__ void philox_setup(SlotRegs<MAXD> &s, uint32_t i, uint
     s.L3 = L3;
 }
 
+// Round keys 3..9 of the item's seed.
+struct RoundKeys {
+    uint32_t k0[7], k1[7];
+};
+
+__device__ __forceinline__ RoundKeys round_keys(uint32_t k0, uint32_t k1)
+{
+    RoundKeys K;
+#pragma unroll
+    for (int r = 3; r < 10; ++r) {
+        K.k0[r - 3] = k0 + (uint32_t)r * kW0;
+        K.k1[r - 3] = k1 + (uint32_t)r * kW1;
+    }
+    return K;
+}
+
 template <int MAXD>
-__device__ __forceinline__ uint4 philox_slot(const SlotRegs<MAXD> &s, uint32_t y, uint32_t k0, uint32_t k1)
+__device__ __forceinline__ uint4 philox_slot(const SlotRegs<MAXD> &s, uint32_t y, const RoundKeys &K)
 {
     uint32_t h, l, h2, l2;
     mulhilo(kM0, s.A ^ y, h, l);          // round 2: word 0 product
@@ -71,7 +87,7 @@ __device__ __forceinline__ uint4 philox_slot(const SlotRegs<MAXD> &s, uint32_t y
         uint32_t a, b, e, f;
         mulhilo(kM0, c.x, a, b);
         mulhilo(kM1, c.z, e, f);
-        c = make_uint4(e ^ c.y ^ (k0 + (uint32_t)r * kW0), f, a ^ c.w ^ (k1 + (uint32_t)r * kW1), b);
+        c = make_uint4(e ^ c.y ^ K.k0[r - 3], f, a ^ c.w ^ K.k1[r - 3], b);
     }
     return c;
 }
@@ -104,6 +120,8 @@ __device__ void run_item_pm1(const SweepLaunch &L, const SweepJob &job, int quad
     __syncthreads();
 
     SlotRegs<MAXD> s[NSLOT];
+    uint4 u[NSLOT];  // random words of each slot for the sweep about to run
+    const RoundKeys K = round_keys(k0, k1);
     const int total = n * nq;
 #pragma unroll
     for (int j = 0; j < NSLOT; ++j) {
@@ -136,6 +154,7 @@ __device__ void run_item_pm1(const SweepLaunch &L, const SweepJob &job, int quad
             philox_setup(s[j], (uint32_t)P->idx_of_pos[p], (uint32_t)(quad0 + q), job.start, k0, k1);
             s[j].colour = c;
         }
+        u[j] = philox_slot(s[j], phase_hi, K);  // sweep 0
     }
 
     for (int t = 0; t < T; ++t) {
@@ -159,18 +178,21 @@ __device__ void run_item_pm1(const SweepLaunch &L, const SweepJob &job, int quad
                     const uint32_t m = own * 0xFFu;
                     const uint32_t x2 = x + x;
                     const uint32_t idx4 = ((x2 + s[j].c0) & ~m) | ((s[j].c1 - x2) & m);
-                    const uint4 u = philox_slot(s[j], y, k0, k1);
-                    const uint32_t uu[4] = {u.x, u.y, u.z, u.w};
-                    uint32_t flip = 0;
+                    // byte r of `always` is 0x80 iff idx_r <= bias (dE <= 0): accepted without a draw
+                    const uint32_t always = ((uint32_t)(bias + 0x80) * 0x01010101u - idx4) & 0x80808080u;
+                    const uint32_t uu[4] = {u[j].x, u[j].y, u[j].z, u[j].w};
+                    uint32_t flip = always >> 7;
 #pragma unroll
                     for (int r = 0; r < 4; ++r) {
                         const int ir = (int)((idx4 >> (8 * r)) & 0xFFu);
-                        const bool acc = (ir <= bias) | (uu[r] < th[ir]);
-                        flip |= (uint32_t)acc << (8 * r);
+                        if (uu[r] < th[ir]) flip |= 1u << (8 * r);
                     }
                     const uint32_t nw = own ^ flip;
                     sw[s[j].own] = nw;
                     sw[s[j].own + S1] = nw ^ 0x01010101u;
+                    // next sweep's words: independent of the spins, so they are computed
+                    // here, off the critical path of the following colour class
+                    u[j] = philox_slot(s[j], y + 1u, K);
                 }
             }
             __syncthreads();
