@@ -181,6 +181,28 @@ int spvar_persistence(const spvar_problem *p, int32_t num_samples, const uint32_
 int spvar_reduce(const spvar_problem *p, const int8_t *fixed, int32_t *old_of_new,
                  void *stream, spvar_problem **out);
 
+/* Allocation-free fold/compact.  The paper has no counterpart: this entry
+ * point exists for callers that cannot call cudaMalloc while they run (code
+ * working inside a fully committed memory budget, or a host runtime that owns
+ * every device allocation and forbids allocating calls after start-up).  It
+ * computes the same reduction as spvar_reduce but allocates nothing: the
+ * result goes to caller buffers as plain CSR, and the working arrays live in
+ * a static device array of 2 * SPVAR_NOALLOC_MAX_N int32 (128 KB) that every
+ * device loading the library keeps until the process exits.
+ *   fixed            device int8 [n] (0, +1, -1)
+ *   row_ptr          device [n+1] out (first n'+1 entries written)
+ *   col, val         device [nnz] out (first row_ptr[n'] entries written)
+ *   h                device [n] out; offset device int64 [1] out
+ *   old_of_new       device [n] out; n_out device int32 [1] out (n')
+ * Asynchronous on `stream`; returns SPVAR_ELIMIT when n > SPVAR_NOALLOC_MAX_N.
+ * The first call on a device looks up the static array's device address
+ * (make it before any stream capture).  All calls share the array: calls
+ * that can overlap on the GPU race and must be serialised by the caller. */
+#define SPVAR_NOALLOC_MAX_N 16384
+int spvar_reduce_noalloc(const spvar_problem *p, const int8_t *fixed, int32_t *row_ptr, int32_t *col,
+                         int32_t *val, int32_t *h, int64_t *offset, int32_t *old_of_new,
+                         int32_t *n_out, void *stream);
+
 /* ------------------------------------------------------------------ */
 /* Multi-start SPVAR (Alg. 2) on one or many problems                   */
 /* ------------------------------------------------------------------ */

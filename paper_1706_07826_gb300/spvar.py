@@ -18,6 +18,7 @@ OK, EINVAL, EOVERFLOW, ENOMEM, EBUDGET, ETIMEOUT, ECUDA, ELIMIT = 0, -1, -2, -3,
 FORM_BATCHED, FORM_PLAIN = 0, 1
 SWEEP_AUTO, SWEEP_GENERAL, SWEEP_PM1 = 0, 1, 2
 MAX_N, MAX_DEGREE, MAX_SWEEPS, MAX_PHASE, MAX_SAMPLES = 32768, 32, 1048574, 4095, 16384
+NOALLOC_MAX_N = 16384
 
 vp = ctypes.c_void_p
 i32 = ctypes.c_int32
@@ -76,6 +77,7 @@ def lib():
         L.spvar_persistence.argtypes = [vp, i32, vp, vp, ctypes.c_double, i32, i32, i32, vp, vp, vp, vp,
                                         ctypes.POINTER(i32), vp]
         L.spvar_reduce.argtypes = [vp, vp, vp, vp, ctypes.POINTER(vp)]
+        L.spvar_reduce_noalloc.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
         L.spvar_plan_create.argtypes = [ctypes.POINTER(vp), i32, ctypes.POINTER(Params), ctypes.c_size_t, vp,
                                         ctypes.POINTER(vp)]
         L.spvar_plan_workspace_bytes.argtypes = [vp]
@@ -262,6 +264,13 @@ def reduce(problem, fixed, stream=None):
            "spvar_reduce")
     red = Problem(out)
     return red, old_of_new[:red.n]
+
+
+def reduce_noalloc(problem, fixed, row_ptr, col, val, h, offset, old_of_new, n_out, stream=None):
+    """Allocation-free reduction into caller tensors (see spvar_reduce_noalloc)."""
+    _check(lib().spvar_reduce_noalloc(problem.handle, _dp(fixed), _dp(row_ptr), _dp(col), _dp(val), _dp(h),
+                                      _dp(offset), _dp(old_of_new), _dp(n_out), _stream(stream)),
+           "spvar_reduce_noalloc")
 
 
 def make_params(num_starts=1, fixing_sample_size=100, solving_sample_size=100, num_sweeps=1000, beta0=0.1,
