@@ -200,6 +200,24 @@ def run_form(spvar, torch, plan, K, W, seeds0, flush, profile=False):
     return total, attempts, best, (sweep_ms, sweep_n), out
 
 
+def profiled_traffic(kernel_kind):
+    """DRAM bytes per launch of the sweep kernel from the committed ncu
+    summary, or None when the kernel's source changed since the capture."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "k_sweep_pm1_chimera_c8.md")
+    if kernel_kind != "pm1-register" or not os.path.exists(path):
+        return None
+    text = open(path).read()
+    vals = dict(l.split(": ", 1) for l in text.splitlines()
+                if l.startswith(("dram_bytes_per_launch:", "kernel_source_sha256_16:")))
+    h = hashlib.sha256()
+    for f in ("sweep_pm1.cu", "sweep_common.cuh", "philox.cuh", "spvar_internal.h"):
+        h.update(open(os.path.join(ROOT, "paper_1706_07826_gb300", "csrc", f), "rb").read())
+    if vals.get("kernel_source_sha256_16") != h.hexdigest()[:16]:
+        return None
+    return int(vals["dram_bytes_per_launch"])
+
+
 def tts99(p, seconds_per_start):
     if p <= 0:
         return None
@@ -319,7 +337,7 @@ def gpu_arm(args, rank, world):
                 "api": "spvar_problem_create + spvar_solve (host buffers, plan built per call)",
                 "ms_per_step": 1000 * statistics.mean(e2e_times)},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
-                     "traffic": None, "kernel": "k_sweep (SA colour-class sweep)",
+                     "traffic": profiled_traffic(shape["kernel"]), "kernel": "k_sweep (SA colour-class sweep)",
                      "ops_per_attempt": ops_per_attempt, "attempts_per_launch": att_per_launch,
                      "ms_per_launch": ms_per_launch,
                      "peak_note": "152 SMs x 128 int32 lanes x 2070 MHz (one warp instruction per SMSP per clock)"},
