@@ -221,6 +221,7 @@ typedef struct spvar_params {
     int32_t replicas_per_block;  /* 0: autotune the sweep shape; else a multiple of 4 */
     int32_t sweep_kernel;        /* with replicas_per_block > 0: SPVAR_SWEEP_* */
     int32_t sweep_block;         /* with replicas_per_block > 0: threads per CTA (128/256/512), 0 = 256 */
+    int32_t start_offset;        /* start s of a problem uses counter word start_offset + s (sharding) */
 } spvar_params;
 
 #define SPVAR_SWEEP_AUTO 0    /* register kernel when eligible, else general */

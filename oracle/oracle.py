@@ -31,6 +31,7 @@ class OrParams(ctypes.Structure):
         ("iterate", ctypes.c_int32),
         ("max_fix_phases", ctypes.c_int32),
         ("canon", ctypes.c_int32),
+        ("start0", ctypes.c_int32),
     ]
 
 
@@ -232,11 +233,11 @@ class SolveResult:
 
 
 def solve(p: Csr, thr, seed, num_starts, fixing_sample_size, solving_sample_size, elite_threshold,
-          fix_num=1, fix_den=1, iterate=False, max_fix_phases=1, canon=-1):
+          fix_num=1, fix_den=1, iterate=False, max_fix_phases=1, canon=-1, start0=0):
     """Multi-start SPVAR (Alg. 2) with SA; thr is the original problem's table."""
     thr = _c(thr, np.uint32)
     prm = OrParams(num_starts, fixing_sample_size, solving_sample_size, thr.shape[0], float(elite_threshold),
-                   fix_num, fix_den, 1 if iterate else 0, max_fix_phases, canon)
+                   fix_num, fix_den, 1 if iterate else 0, max_fix_phases, canon, start0)
     P = max_fix_phases + 1
     Smax = max(fixing_sample_size, solving_sample_size)
     n0 = p.n

@@ -446,7 +446,7 @@ int or_solve(int32_t n0, const int32_t *row_ptr0, const int32_t *col0, const int
             int32_t S = fixing ? prm->fixing_sample_size : prm->solving_sample_size;
             if (!fixing && S == 0) break;
             rc = or_sample(n, rp[b], cl[b], vl[b], hh[b], co[b], ncol, prm->num_sweeps, thr, dmax,
-                           0, S, seed, (uint32_t)st, (uint32_t)phase, spins, e, NULL);
+                           0, S, seed, (uint32_t)(prm->start0 + st), (uint32_t)phase, spins, e, NULL);
             if (rc) break;
             int64_t *rec = energies + ((int64_t)st * P + phase) * Smax;
             for (int32_t r = 0; r < S; ++r) rec[r] = e[r] + off;

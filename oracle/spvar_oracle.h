@@ -112,6 +112,7 @@ typedef struct or_params {
     int32_t iterate;               /* 1: repeat SPVAR until no free spin (ISPVAR) */
     int32_t max_fix_phases;        /* cap on SPVAR phases per start (>= 1) */
     int32_t canon;                 /* -1: when every h is 0; 0: never; 1: always */
+    int32_t start0;                /* start st uses counter word start0 + st */
 } or_params;
 
 /* Outputs (caller-allocated, P = max_fix_phases + 1, Smax = max sample size):

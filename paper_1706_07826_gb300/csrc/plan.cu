@@ -252,7 +252,7 @@ int spvar_plan_create(const spvar_problem *const *problems, int32_t nproblems,
         !(p.elite_threshold > 0.0) || !(p.elite_threshold <= 1.0) || !(p.beta0 > 0.0) || !(p.beta1 > 0.0) ||
         p.canon < -1 || p.canon > 1 || (p.form != SPVAR_FORM_BATCHED && p.form != SPVAR_FORM_PLAIN) ||
         p.replicas_per_block < 0 || (p.replicas_per_block % 4) != 0 || p.sweep_kernel < 0 ||
-        p.sweep_kernel > 2 || (p.sweep_block != 0 && p.sweep_block != 128 && p.sweep_block != 256 &&
+        p.sweep_kernel > 2 || p.start_offset < 0 || (p.sweep_block != 0 && p.sweep_block != 128 && p.sweep_block != 256 &&
                                p.sweep_block != 512))
         return SPVAR_EINVAL;
     const int Smax = std::max(p.fixing_sample_size, p.solving_sample_size);
@@ -411,7 +411,7 @@ int spvar_plan_create(const spvar_problem *const *problems, int32_t nproblems,
         S.cur = P->dev;
         S.n0 = H.n;
         S.W0 = ceil_div(n0, 32);
-        S.start = (uint32_t)(s % p.num_starts);
+        S.start = (uint32_t)(p.start_offset + s % p.num_starts);
         S.spins = (uint32_t *)carve(4 * (size_t)Smax * S.W0);
         S.orig[0] = (int32_t *)carve(4 * (size_t)n0);
         S.orig[1] = (int32_t *)carve(4 * (size_t)n0);

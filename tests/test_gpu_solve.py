@@ -142,3 +142,15 @@ def test_chimera_c8_full_size_properties(cuda_lib):
         assert out.best_energy[st] == O.energy(op, out.best_state[st * inst.n:(st + 1) * inst.n])
         assert out.best_energy[st] == min(out.energies[st, 0].min(), out.energies[st, 1].min())
         assert out.nfree[st, 1] == inst.n - int((out.fixed[st * inst.n:(st + 1) * inst.n] != 0).sum())
+
+
+def test_start_offset_shards_reproduce_full_run(cuda_lib):
+    """Two plans over start blocks [0, 3) and [3, 5) equal one plan over [0, 5)."""
+    from paper_1706_07826_gb300 import spvar
+    inst = I.chimera(3, 41)
+    kw = dict(fixing_sample_size=40, solving_sample_size=20, num_sweeps=40, elite_threshold=0.2)
+    full = spvar.solve(gpu_problem(inst), spvar.make_params(num_starts=5, **kw), 99)
+    a = spvar.solve(gpu_problem(inst), spvar.make_params(num_starts=3, start_offset=0, **kw), 99)
+    b = spvar.solve(gpu_problem(inst), spvar.make_params(num_starts=2, start_offset=3, **kw), 99)
+    assert np.array_equal(np.concatenate([a.best_energy, b.best_energy]), full.best_energy)
+    assert np.array_equal(np.concatenate([a.fixed, b.fixed]), full.fixed)
