@@ -278,6 +278,66 @@ int spvar_solve(const spvar_problem *p, const spvar_params *prm, uint64_t seed,
  * phases of samples x sweeps x free spins) and phases executed. */
 int spvar_plan_stats(const spvar_plan *plan, int64_t *attempts, int32_t *phases);
 
+/* ------------------------------------------------------------------ */
+/* Serving: a request loop with continuous batching                      */
+/* ------------------------------------------------------------------ */
+/* Requests (problems) are admitted in arrival order when a request slot is
+ * free and their device workspace fits budget_bytes; each engine step runs
+ * one phase of Alg. 2 for every admitted start of every request (one
+ * persistent launch sequence, CUDA graph), so requests arriving while others
+ * run join at the next phase boundary.  State stays on the device between
+ * steps; results are copied back when a request finishes.  A request's
+ * result is identical whether it ran alone or in any mix (randomness is
+ * keyed by seed, start, phase, sweep, spin and replica only). */
+typedef struct spvar_server spvar_server;
+
+typedef struct spvar_server_config {
+    spvar_params params;    /* Alg. 2 parameters of every request; sweep_kernel = SPVAR_SWEEP_PM1
+                               restricts the server to +-1 couplers (faster sweep) */
+    size_t budget_bytes;    /* device memory for admitted requests' workspaces */
+    int32_t max_n;          /* largest request: spins, CSR entries, degree */
+    int32_t max_nnz;
+    int32_t max_degree;
+    int32_t max_dmax;       /* acceptance table covers flip costs up to this */
+    int32_t energy_scale;   /* shared by all requests */
+    int32_t max_requests;   /* requests in flight at once */
+} spvar_server_config;
+
+typedef struct spvar_request_info {
+    int32_t state;       /* 0 queued, 1 running, 2 done */
+    int32_t n;
+    int64_t best_energy; /* min over starts (done only) */
+    double latency_s;    /* submit -> results on the host (done only) */
+    double queue_s;      /* submit -> admission (admitted only) */
+    int64_t attempts;    /* spin-flip attempts of the request (done only) */
+} spvar_request_info;
+
+/* Allocates the arena (budget_bytes), the slot table and the acceptance
+ * table on the current device and captures the phase graph. */
+int spvar_server_create(const spvar_server_config *cfg, spvar_server **out);
+/* Host CSR problem (validated and laid out here), seed; returns its id.
+ * ELIMIT beyond the configured sizes, EBUDGET if it can never fit. */
+int spvar_server_submit(spvar_server *s, int32_t n, const int32_t *row_ptr, const int32_t *col,
+                        const int32_t *val, const int32_t *h, int64_t offset, uint64_t seed,
+                        int64_t *id);
+/* One engine iteration on the calling thread: admit, one phase, retire.
+ * *active = requests still in flight.  EINVAL while the background engine runs. */
+int spvar_server_step(spvar_server *s, int32_t *active);
+/* Background engine thread (steps while work exists). */
+int spvar_server_start(spvar_server *s);
+int spvar_server_stop(spvar_server *s);
+/* Waits up to timeout_s (0: just query) for a request; ETIMEOUT if not done. */
+int spvar_server_wait(spvar_server *s, int64_t id, double timeout_s, spvar_request_info *info);
+/* Host copies of a finished request's results (layouts as spvar_result with
+ * one problem; any pointer may be NULL). */
+int spvar_server_result(spvar_server *s, int64_t id, int64_t *best_energy, int8_t *best_state,
+                        int8_t *fixed, int64_t *energies, int32_t *counts, int32_t *nfree);
+/* Forgets a finished request's host results. */
+int spvar_server_release(spvar_server *s, int64_t id);
+int spvar_server_stats(spvar_server *s, int64_t *requests_done, int64_t *attempts_done,
+                       int32_t *queued, int32_t *running);
+void spvar_server_destroy(spvar_server *s);
+
 /* Profiling: when on, plan_run waits for every phase and adds up the
  * duration of the sweep kernel (CUDA events recorded on the run's stream
  * around each sweep launch, also inside the captured graph). */

@@ -117,6 +117,125 @@ void prob_carve(DevProb *hdr, void *blob, int cap_n, int cap_nnz, int maxdeg)
     hdr->ell = (uint32_t *)take(4 * (size_t)maxdeg * cap_n);
 }
 
+int host_problem_build(int n, const int32_t *row_ptr, const int32_t *col, const int32_t *val, const int32_t *h,
+                       int64_t offset, int energy_scale, HostProblem &hp)
+{
+    if (n < 0 || energy_scale < 1 || !row_ptr || (n > 0 && !h)) return SPVAR_EINVAL;
+    if (n > SPVAR_MAX_N) return SPVAR_ELIMIT;
+    if (row_ptr[0] != 0) return SPVAR_EINVAL;
+    for (int i = 0; i < n; ++i)
+        if (row_ptr[i + 1] < row_ptr[i]) return SPVAR_EINVAL;
+    const int nnz = row_ptr[n];
+    if (nnz > 0 && (!col || !val)) return SPVAR_EINVAL;
+    int maxdeg = 0;
+    long long total = 0;
+    long long maxrow = 0;
+    for (int i = 0; i < n; ++i) {
+        const int d = row_ptr[i + 1] - row_ptr[i];
+        if (d > SPVAR_MAX_DEGREE) return SPVAR_ELIMIT;
+        maxdeg = std::max(maxdeg, d);
+        long long rowsum = std::llabs((long long)h[i]);
+        total += 2 * std::llabs((long long)h[i]);
+        for (int p = row_ptr[i]; p < row_ptr[i + 1]; ++p) {
+            const int j = col[p];
+            if (j < 0 || j >= n || j == i) return SPVAR_EINVAL;
+            if (p > row_ptr[i] && col[p - 1] >= j) return SPVAR_EINVAL;
+            if (val[p] == 0) return SPVAR_EINVAL;
+            if (val[p] > 32767 || val[p] < -32767) return SPVAR_ELIMIT;
+            // symmetric partner (j, i) with the same value
+            const int32_t *b = col + row_ptr[j], *e = col + row_ptr[j + 1];
+            const int32_t *f = std::lower_bound(b, e, i);
+            if (f == e || *f != i || val[f - col] != val[p]) return SPVAR_EINVAL;
+            rowsum += std::llabs((long long)val[p]);
+            total += std::llabs((long long)val[p]);
+        }
+        maxrow = std::max(maxrow, rowsum);
+        if (total >= (1ll << 31)) return SPVAR_EOVERFLOW;
+    }
+    if (maxrow > 32767) return SPVAR_ELIMIT;  // h' and dmax/2 must fit int16
+
+    const int ncol = colour_classes(n, row_ptr, col, hp.colour);
+    if (ncol > kMaxColours) return SPVAR_ELIMIT;
+    hp.cap_n = std::max(n, 1);
+    hp.cap_nnz = std::max(nnz, 1);
+    hp.md = std::max(maxdeg, 1);
+    DevProb &H = hp.hdr;
+    std::memset(&H, 0, sizeof(H));
+    H.n = n;
+    H.nnz = nnz;
+    H.ncol = ncol;
+    H.maxdeg = hp.md;
+    H.dmax = (int32_t)(2 * maxrow);
+    H.offset = offset;
+    H.scale = energy_scale;
+    H.cap_n = hp.cap_n;
+    H.cap_nnz = hp.cap_nnz;
+    H.hzero = 1;
+    H.pm1 = 1;
+    for (int i = 0; i < n; ++i) if (h[i] != 0) H.hzero = 0;
+    for (int p = 0; p < nnz; ++p) if (val[p] != 1 && val[p] != -1) H.pm1 = 0;
+    H.rho = -1;
+    for (int i = 0, best = -1; i < n; ++i)
+        if (row_ptr[i + 1] - row_ptr[i] > best) { best = row_ptr[i + 1] - row_ptr[i]; H.rho = i; }
+
+    hp.row_ptr.assign(row_ptr, row_ptr + n + 1);
+    hp.col.assign(col, col + nnz);
+    hp.val.assign(val, val + nnz);
+    hp.h.assign(h, h + n);
+    // sweep layout: positions colour class by colour class, index ascending
+    hp.cptr.assign(kMaxColours + 1, 0);
+    hp.idx_of_pos.assign(hp.cap_n, 0);
+    hp.pos_of_idx.assign(hp.cap_n, 0);
+    hp.meta.assign(hp.cap_n, 0);
+    hp.ell.assign((size_t)hp.md * hp.cap_n, 0);
+    for (int i = 0; i < n; ++i) hp.cptr[hp.colour[i] + 1]++;
+    for (int c = 0; c < ncol; ++c) hp.cptr[c + 1] += hp.cptr[c];
+    for (int c = ncol + 1; c <= kMaxColours; ++c) hp.cptr[c] = hp.cptr[ncol];
+    {
+        std::vector<int32_t> fill(hp.cptr.begin(), hp.cptr.end());
+        for (int i = 0; i < n; ++i) {
+            const int pos = fill[hp.colour[i]]++;
+            hp.idx_of_pos[pos] = i;
+            hp.pos_of_idx[i] = pos;
+        }
+    }
+    for (int i = 0; i < n; ++i) {
+        const int pos = hp.pos_of_idx[i];
+        const int deg = row_ptr[i + 1] - row_ptr[i];
+        hp.meta[pos] = ((uint32_t)(h[i] & 0xFFFF) << 16) | (uint32_t)deg;
+        for (int d = 0; d < deg; ++d) {
+            const int p = row_ptr[i] + d;
+            hp.ell[(size_t)d * hp.cap_n + pos] =
+                ((uint32_t)hp.pos_of_idx[col[p]] & 0xFFFFu) | ((uint32_t)(val[p] & 0xFFFF) << 16);
+        }
+    }
+    return SPVAR_OK;
+}
+
+int host_problem_upload(const HostProblem &hp, void *blob, cudaStream_t st, DevProb *hdr_out)
+{
+    DevProb H = hp.hdr;
+    prob_carve(&H, blob, hp.cap_n, hp.cap_nnz, hp.md);
+    const int n = H.n, nnz = H.nnz;
+    bool ok = true;
+    auto up = [&](void *dst, const void *src, size_t bytes) {
+        if (bytes && ok) ok = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st) == cudaSuccess;
+    };
+    *hdr_out = H;
+    up(blob, hdr_out, sizeof(DevProb));
+    up(H.row_ptr, hp.row_ptr.data(), 4 * ((size_t)n + 1));
+    up(H.col, hp.col.data(), 4 * (size_t)nnz);
+    up(H.val, hp.val.data(), 4 * (size_t)nnz);
+    up(H.h, hp.h.data(), 4 * (size_t)n);
+    up(H.colour, hp.colour.data(), 4 * (size_t)n);
+    up(H.cptr, hp.cptr.data(), 4 * hp.cptr.size());
+    up(H.idx_of_pos, hp.idx_of_pos.data(), 4 * (size_t)n);
+    up(H.pos_of_idx, hp.pos_of_idx.data(), 4 * (size_t)n);
+    up(H.meta, hp.meta.data(), 4 * (size_t)n);
+    up(H.ell, hp.ell.data(), 4 * hp.ell.size());
+    return ok ? SPVAR_OK : SPVAR_ECUDA;
+}
+
 }  // namespace spvar
 
 extern "C" {
@@ -189,120 +308,28 @@ int spvar_problem_create(int32_t n, const int32_t *row_ptr, const int32_t *col, 
 {
     if (!out) return SPVAR_EINVAL;
     *out = nullptr;
-    if (n < 0 || energy_scale < 1 || !row_ptr || (n > 0 && !h)) return SPVAR_EINVAL;
-    if (n > SPVAR_MAX_N) return SPVAR_ELIMIT;
-    if (row_ptr[0] != 0) return SPVAR_EINVAL;
-    for (int i = 0; i < n; ++i)
-        if (row_ptr[i + 1] < row_ptr[i]) return SPVAR_EINVAL;
-    const int nnz = row_ptr[n];
-    if (nnz > 0 && (!col || !val)) return SPVAR_EINVAL;
-    int maxdeg = 0;
-    long long total = 0;
-    long long maxrow = 0;
-    for (int i = 0; i < n; ++i) {
-        const int d = row_ptr[i + 1] - row_ptr[i];
-        if (d > SPVAR_MAX_DEGREE) return SPVAR_ELIMIT;
-        maxdeg = std::max(maxdeg, d);
-        long long rowsum = std::llabs((long long)h[i]);
-        total += 2 * std::llabs((long long)h[i]);
-        for (int p = row_ptr[i]; p < row_ptr[i + 1]; ++p) {
-            const int j = col[p];
-            if (j < 0 || j >= n || j == i) return SPVAR_EINVAL;
-            if (p > row_ptr[i] && col[p - 1] >= j) return SPVAR_EINVAL;
-            if (val[p] == 0) return SPVAR_EINVAL;
-            if (val[p] > 32767 || val[p] < -32767) return SPVAR_ELIMIT;
-            // symmetric partner (j, i) with the same value
-            const int32_t *b = col + row_ptr[j], *e = col + row_ptr[j + 1];
-            const int32_t *f = std::lower_bound(b, e, i);
-            if (f == e || *f != i || val[f - col] != val[p]) return SPVAR_EINVAL;
-            rowsum += std::llabs((long long)val[p]);
-            total += std::llabs((long long)val[p]);
-        }
-        maxrow = std::max(maxrow, rowsum);
-        if (total >= (1ll << 31)) return SPVAR_EOVERFLOW;
-    }
-    if (maxrow > 32767) return SPVAR_ELIMIT;  // h' and dmax/2 must fit int16
-
-    std::vector<int32_t> colour;
-    const int ncol = colour_classes(n, row_ptr, col, colour);
-    if (ncol > kMaxColours) return SPVAR_ELIMIT;
-
-    const int cap_n = std::max(n, 1), cap_nnz = std::max(nnz, 1), md = std::max(maxdeg, 1);
+    HostProblem hp;
+    int rc = host_problem_build(n, row_ptr, col, val, h, offset, energy_scale, hp);
+    if (rc != SPVAR_OK) return rc;
     Problem *P = new (std::nothrow) Problem();
     if (!P) return SPVAR_ENOMEM;
     cudaGetDevice(&P->device);
-    P->blob_bytes = prob_blob_bytes(cap_n, cap_nnz, md);
+    P->blob_bytes = prob_blob_bytes(hp.cap_n, hp.cap_nnz, hp.md);
     if (cudaMalloc(&P->blob, P->blob_bytes) != cudaSuccess) {
         delete P;
         cudaGetLastError();
         return SPVAR_ENOMEM;
     }
-    DevProb &H = P->hdr;
-    std::memset(&H, 0, sizeof(H));
-    prob_carve(&H, P->blob, cap_n, cap_nnz, md);
-    P->dev = static_cast<DevProb *>(P->blob);
-    H.n = n;
-    H.nnz = nnz;
-    H.ncol = ncol;
-    H.dmax = (int32_t)(2 * maxrow);
-    H.offset = offset;
-    H.scale = energy_scale;
-    H.hzero = 1;
-    H.pm1 = 1;
-    for (int i = 0; i < n; ++i) if (h[i] != 0) H.hzero = 0;
-    for (int p = 0; p < nnz; ++p) if (val[p] != 1 && val[p] != -1) H.pm1 = 0;
-    H.rho = -1;
-    for (int i = 0, best = -1; i < n; ++i)
-        if (row_ptr[i + 1] - row_ptr[i] > best) { best = row_ptr[i + 1] - row_ptr[i]; H.rho = i; }
-
-    // sweep layout: positions colour class by colour class, index ascending
-    std::vector<int32_t> cptr(kMaxColours + 1, 0), idx_of_pos(cap_n, 0), pos_of_idx(cap_n, 0);
-    std::vector<uint32_t> meta(cap_n, 0), ell((size_t)md * cap_n, 0);
-    for (int i = 0; i < n; ++i) cptr[colour[i] + 1]++;
-    for (int c = 0; c < ncol; ++c) cptr[c + 1] += cptr[c];
-    for (int c = ncol + 1; c <= kMaxColours; ++c) cptr[c] = cptr[ncol];
-    {
-        std::vector<int32_t> fill(cptr.begin(), cptr.end());
-        for (int i = 0; i < n; ++i) {
-            const int pos = fill[colour[i]]++;
-            idx_of_pos[pos] = i;
-            pos_of_idx[i] = pos;
-        }
-    }
-    for (int i = 0; i < n; ++i) {
-        const int pos = pos_of_idx[i];
-        const int deg = row_ptr[i + 1] - row_ptr[i];
-        meta[pos] = ((uint32_t)(h[i] & 0xFFFF) << 16) | (uint32_t)deg;
-        for (int d = 0; d < deg; ++d) {
-            const int p = row_ptr[i] + d;
-            ell[(size_t)d * cap_n + pos] =
-                ((uint32_t)pos_of_idx[col[p]] & 0xFFFFu) | ((uint32_t)(val[p] & 0xFFFF) << 16);
-        }
-    }
-
     cudaStream_t st = as_stream(stream);
-    bool ok = true;
-    auto up = [&](void *dst, const void *src, size_t bytes) {
-        if (bytes && ok) ok = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st) == cudaSuccess;
-    };
-    up(P->dev, &H, sizeof(DevProb));
-    up(H.row_ptr, row_ptr, 4 * ((size_t)n + 1));
-    up(H.col, col, 4 * (size_t)nnz);
-    up(H.val, val, 4 * (size_t)nnz);
-    up(H.h, h, 4 * (size_t)n);
-    up(H.colour, colour.data(), 4 * (size_t)n);
-    up(H.cptr, cptr.data(), 4 * cptr.size());
-    up(H.idx_of_pos, idx_of_pos.data(), 4 * (size_t)n);
-    up(H.pos_of_idx, pos_of_idx.data(), 4 * (size_t)n);
-    up(H.meta, meta.data(), 4 * (size_t)n);
-    up(H.ell, ell.data(), 4 * ell.size());
-    if (ok) ok = cudaStreamSynchronize(st) == cudaSuccess;
-    if (!ok) {
+    rc = host_problem_upload(hp, P->blob, st, &P->hdr);
+    if (rc == SPVAR_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = SPVAR_ECUDA;
+    if (rc != SPVAR_OK) {
         cudaFree(P->blob);
         delete P;
         cudaGetLastError();
-        return SPVAR_ECUDA;
+        return rc;
     }
+    P->dev = static_cast<DevProb *>(P->blob);
     *out = reinterpret_cast<spvar_problem *>(P);
     return SPVAR_OK;
 }

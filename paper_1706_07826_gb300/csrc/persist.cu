@@ -364,6 +364,12 @@ __global__ void k_count_active(const Slot *slots, int nslots, int32_t *nactive)
     if (threadIdx.x == 0) *nactive = s_n;
 }
 
+__global__ void k_gather_modes(const Slot *slots, int nslots, int32_t *modes)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nslots; i += gridDim.x * blockDim.x)
+        modes[i] = slots[i].mode;
+}
+
 size_t elite_smem(int S)
 {
     int N2 = 1;
@@ -372,6 +378,13 @@ size_t elite_smem(int S)
 }
 
 }  // namespace
+
+cudaError_t launch_gather_modes(const Slot *slots, int nslots, int32_t *modes, cudaStream_t st)
+{
+    if (nslots <= 0) return cudaSuccess;
+    k_gather_modes<<<ceil_div(nslots, 256), 256, 0, st>>>(slots, nslots, modes);
+    return cudaGetLastError();
+}
 
 int elite_max_samples() { return SPVAR_MAX_SAMPLES; }
 

@@ -24,6 +24,44 @@
 
 using namespace spvar;
 
+namespace spvar {
+
+cudaError_t engine_phase(const PhaseEngine &E, Slot *slots, int nslots, int T, int grid, cudaStream_t st,
+                         bool count_active, bool capturing)
+{
+    // inside stream capture an event record only becomes a graph node when external
+    auto record = [&](cudaEvent_t ev) {
+        return capturing ? cudaEventRecordWithFlags(ev, st, cudaEventRecordExternal) : cudaEventRecord(ev, st);
+    };
+    SolveConsts C = E.C;
+    C.nslots = nslots;
+    C.Q = E.shape.Q;
+    cudaError_t e = launch_plan(slots, C, E.jobs, E.items, E.ctr + 0, E.ctr + 1, st);
+    if (e != cudaSuccess) return e;
+    SweepLaunch L;
+    std::memset(&L, 0, sizeof(L));
+    L.jobs = E.jobs;
+    L.items = E.items;
+    L.nitems = E.ctr + 0;
+    L.queue = E.ctr + 1;
+    L.thr = E.thr;
+    L.thr_stride = E.thr_stride;
+    L.T = T;
+    L.Q = E.shape.Q;
+    L.stage_ell = E.shape.stage;
+    L.max_n = E.max_n0;
+    L.max_deg = E.max_deg;
+    if (E.ev_sweep[0] && (e = record(E.ev_sweep[0])) != cudaSuccess) return e;
+    e = launch_sweep_shape(L, E.shape, E.pm1, grid, E.sweep_smem, st);
+    if (e != cudaSuccess) return e;
+    if (E.ev_sweep[1] && (e = record(E.ev_sweep[1])) != cudaSuccess) return e;
+    if ((e = launch_elite_slots(slots, C, st)) != cudaSuccess) return e;
+    if ((e = launch_count_slots(slots, C, E.max_n0, st)) != cudaSuccess) return e;
+    return launch_reduce_slots(slots, C, count_active ? E.ctr + 2 : nullptr, st);
+}
+
+}  // namespace spvar
+
 struct spvar_plan {
     int device = 0;
     std::vector<const Problem *> probs;
@@ -98,27 +136,30 @@ int grid_for(const spvar_plan *pl, int items)
     return std::max(1, std::min(items, occ * pl->sms));
 }
 
+PhaseEngine engine_of(const spvar_plan *pl)
+{
+    PhaseEngine E;
+    E.shape = pl->shape;
+    E.sweep_smem = pl->sweep_smem;
+    E.pm1 = pl->pm1;
+    E.max_n0 = pl->max_n0;
+    E.max_deg = pl->max_deg;
+    E.thr_stride = pl->thr_stride;
+    E.thr = pl->d_thr;
+    E.jobs = pl->d_jobs;
+    E.items = pl->d_items;
+    E.ctr = pl->d_ctr;
+    E.ev_sweep[0] = pl->ev_sweep[0];
+    E.ev_sweep[1] = pl->ev_sweep[1];
+    E.C = pl->C;
+    return E;
+}
+
 // One phase of the given slots (all of them in the batched form).
 cudaError_t launch_phase(spvar_plan *pl, Slot *slots, int nslots, int T, int grid, cudaStream_t st,
                          bool count_active, bool capturing = false)
 {
-    // inside stream capture an event record only becomes a graph node when external
-    auto record = [&](cudaEvent_t ev) {
-        return capturing ? cudaEventRecordWithFlags(ev, st, cudaEventRecordExternal) : cudaEventRecord(ev, st);
-    };
-    SolveConsts C = pl->C;
-    C.nslots = nslots;
-    C.Q = pl->shape.Q;
-    cudaError_t e = launch_plan(slots, C, pl->d_jobs, pl->d_items, pl->d_ctr + 0, pl->d_ctr + 1, st);
-    if (e != cudaSuccess) return e;
-    SweepLaunch L = make_launch(pl, T);
-    if ((e = record(pl->ev_sweep[0])) != cudaSuccess) return e;
-    e = launch_sweep_shape(L, pl->shape, pl->pm1, grid, pl->sweep_smem, st);
-    if (e != cudaSuccess) return e;
-    if ((e = record(pl->ev_sweep[1])) != cudaSuccess) return e;
-    if ((e = launch_elite_slots(slots, C, st)) != cudaSuccess) return e;
-    if ((e = launch_count_slots(slots, C, pl->max_n0, st)) != cudaSuccess) return e;
-    return launch_reduce_slots(slots, C, count_active ? pl->d_ctr + 2 : nullptr, st);
+    return engine_phase(engine_of(pl), slots, nslots, T, grid, st, count_active, capturing);
 }
 
 int upload_slots(spvar_plan *pl, const uint64_t *seeds, cudaStream_t st)

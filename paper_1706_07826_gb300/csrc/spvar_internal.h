@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "spvar.h"
 
 namespace spvar {
@@ -44,6 +46,20 @@ struct Problem {
     size_t blob_bytes;
     int device;
 };
+
+// A validated problem with its sweep layout, built on the host.
+struct HostProblem {
+    DevProb hdr;  // scalar fields (pointers unset)
+    int cap_n = 1, cap_nnz = 1, md = 1;
+    std::vector<int32_t> row_ptr, col, val, h, colour, cptr, idx_of_pos, pos_of_idx;
+    std::vector<uint32_t> meta, ell;  // ell: [md][cap_n]
+};
+// Validates a host CSR problem and builds colours and layout (SPVAR_* code).
+int host_problem_build(int n, const int32_t *row_ptr, const int32_t *col, const int32_t *val, const int32_t *h,
+                       int64_t offset, int scale, HostProblem &out);
+// Uploads into a blob of prob_blob_bytes(cap_n, cap_nnz, md) bytes (stream-ordered;
+// the host arrays must stay alive until the stream reaches the copies).
+int host_problem_upload(const HostProblem &hp, void *blob, cudaStream_t st, DevProb *hdr_out);
 
 size_t prob_blob_bytes(int cap_n, int cap_nnz, int maxdeg);
 // Carve a blob into a header with device pointers; the header itself sits at blob offset 0.
@@ -162,6 +178,24 @@ inline int sweep_shape_occupancy(const SweepShape &s, bool pm1, size_t smem)
     return s.kind == 1 ? pm1_max_active_blocks(s.block, s.nslot, s.maxd, smem)
                        : sweep_max_active_blocks(pm1, s.block, smem, s.stage != 0);
 }
+
+// Everything one Multi-start SPVAR phase needs besides the slots.
+struct PhaseEngine {
+    SweepShape shape;
+    size_t sweep_smem;
+    bool pm1;
+    int max_n0, max_deg, thr_stride;
+    const uint32_t *thr;
+    SweepJob *jobs;
+    WorkItem *items;
+    int32_t *ctr;  // [0] items, [1] queue cursor, [2] active slots
+    cudaEvent_t ev_sweep[2];
+    SolveConsts C;
+};
+// plan -> sweep -> elite -> count/fix -> fold/compact for `nslots` slots.
+cudaError_t engine_phase(const PhaseEngine &E, Slot *slots, int nslots, int T, int grid, cudaStream_t st,
+                         bool count_active, bool capturing);
+cudaError_t launch_gather_modes(const Slot *slots, int nslots, int32_t *modes, cudaStream_t st);
 
 // Elite selection of one sample set (standalone form).
 cudaError_t launch_elite_single(const int64_t *energies, int S, int k, int32_t *elite,

@@ -46,6 +46,16 @@ class Params(ctypes.Structure):
                 ("replicas_per_block", i32), ("sweep_kernel", i32), ("sweep_block", i32), ("start_offset", i32)]
 
 
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("params", Params), ("budget_bytes", ctypes.c_size_t), ("max_n", i32), ("max_nnz", i32),
+                ("max_degree", i32), ("max_dmax", i32), ("energy_scale", i32), ("max_requests", i32)]
+
+
+class RequestInfo(ctypes.Structure):
+    _fields_ = [("state", i32), ("n", i32), ("best_energy", i64), ("latency_s", ctypes.c_double),
+                ("queue_s", ctypes.c_double), ("attempts", i64)]
+
+
 class Result(ctypes.Structure):
     _fields_ = [("device", i32), ("energies", vp), ("counts", vp), ("nfree", vp), ("nphases", vp),
                 ("fixed", vp), ("best_energy", vp), ("best_state", vp)]
@@ -91,6 +101,18 @@ def lib():
         L.spvar_plan_sweep_time.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i32)]
         L.spvar_plan_shape.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32),
                                        ctypes.POINTER(i32)]
+        L.spvar_server_create.argtypes = [ctypes.POINTER(ServerConfig), ctypes.POINTER(vp)]
+        L.spvar_server_submit.argtypes = [vp, i32, vp, vp, vp, vp, i64, u64, ctypes.POINTER(i64)]
+        L.spvar_server_step.argtypes = [vp, ctypes.POINTER(i32)]
+        L.spvar_server_start.argtypes = [vp]
+        L.spvar_server_stop.argtypes = [vp]
+        L.spvar_server_wait.argtypes = [vp, i64, ctypes.c_double, ctypes.POINTER(RequestInfo)]
+        L.spvar_server_result.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp]
+        L.spvar_server_release.argtypes = [vp, i64]
+        L.spvar_server_stats.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i32),
+                                         ctypes.POINTER(i32)]
+        L.spvar_server_destroy.argtypes = [vp]
+        L.spvar_server_destroy.restype = None
         _lib = L
     return _lib
 
@@ -401,3 +423,75 @@ def pack_spins(s):
     b = np.zeros((S, W * 32), np.uint32)
     b[:, :n] = (s > 0)
     return (b.reshape(S, W, 32) << np.arange(32, dtype=np.uint32)).sum(axis=2).astype(np.uint32)
+
+
+class Server:
+    """Continuous-batching request loop (spvar_server_*): admission by device
+    memory budget, one Alg. 2 phase per engine step for everything in flight."""
+
+    def __init__(self, params, budget_bytes, max_n, max_nnz, max_degree, max_dmax, energy_scale=1,
+                 max_requests=16):
+        cfg = ServerConfig(params, int(budget_bytes), max_n, max_nnz, max_degree, max_dmax, energy_scale,
+                           max_requests)
+        out = vp()
+        _check(lib().spvar_server_create(ctypes.byref(cfg), ctypes.byref(out)), "spvar_server_create")
+        self.handle = out
+        self.params = params
+        self.P = params.max_fix_phases + 1
+        self.Smax = max(params.fixing_sample_size, params.solving_sample_size)
+        self.sizes = {}
+
+    def submit(self, inst, seed):
+        rp, c, v = csr_from_edges(inst.n, inst.ei, inst.ej, inst.J)
+        hh = _host(inst.h, np.int32)
+        rid = i64(0)
+        _check(lib().spvar_server_submit(self.handle, inst.n, _hp(rp), _hp(c), _hp(v), _hp(hh), int(inst.offset),
+                                         int(seed), ctypes.byref(rid)), "spvar_server_submit")
+        self.sizes[rid.value] = inst.n
+        return rid.value
+
+    def step(self):
+        a = i32(0)
+        _check(lib().spvar_server_step(self.handle, ctypes.byref(a)), "spvar_server_step")
+        return a.value
+
+    def start(self):
+        _check(lib().spvar_server_start(self.handle), "spvar_server_start")
+
+    def stop(self):
+        _check(lib().spvar_server_stop(self.handle), "spvar_server_stop")
+
+    def info(self, rid, timeout=0.0):
+        inf = RequestInfo()
+        rc = lib().spvar_server_wait(self.handle, rid, float(timeout), ctypes.byref(inf))
+        if rc not in (OK, ETIMEOUT):
+            _check(rc, "spvar_server_wait")
+        return inf
+
+    def result(self, rid):
+        """SolveOutput (host arrays) of a finished request."""
+        n, ns = self.sizes[rid], self.params.num_starts
+        o = _alloc_outputs(ns, self.P, self.Smax, n * ns, False)
+        _check(lib().spvar_server_result(self.handle, rid, _hp(o.best_energy), _hp(o.best_state), _hp(o.fixed),
+                                         _hp(o.energies), _hp(o.counts), _hp(o.nfree)), "spvar_server_result")
+        return o
+
+    def release(self, rid):
+        _check(lib().spvar_server_release(self.handle, rid), "spvar_server_release")
+
+    def stats(self):
+        d, a, q, r = i64(0), i64(0), i32(0), i32(0)
+        _check(lib().spvar_server_stats(self.handle, ctypes.byref(d), ctypes.byref(a), ctypes.byref(q),
+                                        ctypes.byref(r)), "spvar_server_stats")
+        return dict(done=d.value, attempts=a.value, queued=q.value, running=r.value)
+
+    def close(self):
+        if self.handle:
+            lib().spvar_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

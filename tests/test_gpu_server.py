@@ -1,0 +1,109 @@
+"""GPU tests of the continuous-batching request loop (spvar_server_*).
+
+Each request's result must be identical whether it ran alone (spvar_solve)
+or inside a mix of requests of different sizes that arrive while others are
+in flight and wait for device memory; one small request is also checked
+against the oracle directly."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1706_07826_gb300 import instances as I
+
+from gpu_cases import gpu_problem, oracle_problem, table
+
+pytestmark = pytest.mark.gpu
+
+KW = dict(num_starts=3, fixing_sample_size=48, solving_sample_size=24, num_sweeps=60, elite_threshold=0.2)
+
+
+def _alone(spvar, inst, seed):
+    return spvar.solve(gpu_problem(inst), spvar.make_params(**KW), seed)
+
+
+def _same(a, b):
+    assert np.array_equal(a.best_energy, b.best_energy)
+    assert np.array_equal(a.fixed, b.fixed)
+    assert np.array_equal(a.best_state, b.best_state)
+    assert np.array_equal(a.counts, b.counts)
+    assert np.array_equal(a.nfree, b.nfree)
+    for s in range(a.counts.shape[0]):
+        for p in range(a.counts.shape[1]):
+            c = a.counts[s, p]
+            assert np.array_equal(a.energies[s, p, :c], b.energies[s, p, :c])
+
+
+def _server(spvar, budget, max_requests=3, pm1=False):
+    prm = spvar.make_params(**KW, sweep_kernel=spvar.SWEEP_PM1 if pm1 else 0)
+    return spvar.Server(prm, budget, max_n=1000, max_nnz=6000, max_degree=6, max_dmax=12, max_requests=max_requests)
+
+
+@pytest.mark.parametrize("pm1", [False, True], ids=["general", "pm1"])
+def test_results_identical_alone_and_in_the_mix(cuda_lib, pm1):
+    spvar = cuda_lib
+    insts = [I.cubic3d(4, 61), I.chimera(4, 62), I.cubic3d(5, 63), I.cubic3d(6, 64), I.chimera(3, 65)]
+    seeds = [101, 102, 103, 104, 105]
+    # budget for about two of these requests at a time: the rest queue for memory
+    srv = _server(spvar, budget=600 << 10, pm1=pm1)
+    ids = [srv.submit(insts[0], seeds[0])]
+    srv.step()                                   # request 0 runs its first phase alone
+    ids += [srv.submit(insts[i], seeds[i]) for i in (1, 2, 3)]
+    saw_queue = srv.stats()["queued"] > 0
+    srv.step()
+    ids.append(srv.submit(insts[4], seeds[4]))
+    steps = 0
+    while srv.step() > 0 or srv.stats()["queued"] > 0:
+        saw_queue |= srv.stats()["queued"] > 0
+        steps += 1
+        assert steps < 100
+    for rid, inst, seed in zip(ids, insts, seeds):
+        info = srv.info(rid)
+        assert info.state == 2 and info.latency_s > 0
+        _same(srv.result(rid), _alone(spvar, inst, seed))
+    assert saw_queue
+    assert srv.stats()["done"] == len(ids)
+    srv.close()
+
+
+def test_server_request_matches_oracle(cuda_lib):
+    spvar = cuda_lib
+    inst = I.cubic3d(3, 70)
+    srv = _server(spvar, budget=4 << 20)
+    rid = srv.submit(inst, 7)
+    while srv.step() > 0:
+        pass
+    out = srv.result(rid)
+    ref = O.solve(oracle_problem(inst), table(inst, KW["num_sweeps"], dmax=12), 7, num_starts=3,
+                  fixing_sample_size=48, solving_sample_size=24, elite_threshold=0.2)
+    assert np.array_equal(out.best_energy, ref.best_e)
+    assert np.array_equal(out.fixed.reshape(3, -1), ref.fixed)
+    srv.close()
+
+
+def test_background_engine_thread(cuda_lib):
+    spvar = cuda_lib
+    insts = [I.cubic3d(4, 80 + i) for i in range(4)]
+    srv = _server(spvar, budget=32 << 20, max_requests=2)
+    srv.start()
+    ids = [srv.submit(inst, 200 + i) for i, inst in enumerate(insts)]
+    for rid in ids:
+        assert srv.info(rid, timeout=60.0).state == 2
+    srv.stop()
+    for i, (rid, inst) in enumerate(zip(ids, insts)):
+        _same(srv.result(rid), _alone(spvar, inst, 200 + i))
+        srv.release(rid)
+    srv.close()
+
+
+def test_server_limits(cuda_lib):
+    spvar = cuda_lib
+    srv = _server(spvar, budget=256 << 10)
+    with pytest.raises(spvar.SpvarError) as e:
+        srv.submit(I.cubic3d(11, 1), 1)          # 1331 spins > max_n
+    assert e.value.code == spvar.ELIMIT
+    with pytest.raises(spvar.SpvarError) as e:
+        srv.submit(I.cubic3d(9, 1), 1)           # fits max_n but never fits the 256 KB budget
+    assert e.value.code == spvar.EBUDGET
+    with pytest.raises(spvar.SpvarError):
+        srv.submit(I.weak_strong(2, 1), 1)       # dmax beyond the table
+    srv.close()
