@@ -219,6 +219,74 @@ def profiled_traffic(kernel_kind):
     return int(vals["dram_bytes_per_launch"])
 
 
+def measure_uneven(spvar, torch, flush):
+    """c4: 64 3D +-J instances, L uniform in 6..12, 2000 samples per phase,
+    one persistent launch per phase for all of them (batched) vs plain."""
+    from paper_1706_07826_gb300 import instances as I
+    insts = I.uneven_batch(64, 6, 12, seed=1400)
+    probs = [spvar.Problem.from_instance(x) for x in insts]
+    out = {}
+    for form, name in ((spvar.FORM_BATCHED, "batched"), (spvar.FORM_PLAIN, "plain")):
+        prm = spvar.make_params(num_starts=1, fixing_sample_size=2000, solving_sample_size=2000, num_sweeps=1000,
+                                elite_threshold=0.1, form=form)
+        plan = spvar.Plan(probs, prm)
+        seeds = [1401 + i for i in range(len(probs))]
+        plan.run(seeds, device=True)
+        torch.cuda.synchronize()
+        flush.add_(1)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        plan.run([x + 7 for x in seeds], device=True)
+        b.record()
+        torch.cuda.synchronize()
+        att, _ = plan.stats()
+        ms = a.elapsed_time(b)
+        out[name] = {"value": att / (ms / 1000.0), "ms": ms, "attempts": att, "sweep_shape": plan.shape()}
+        plan.close()
+    out["speedup_batched_over_plain"] = out["batched"]["value"] / out["plain"]["value"]
+    out["config"] = ("64 3D +-J instances, L uniform in 6..12 (N 216..1728, seed 1400), 1 start each, "
+                     "2000 fixing + 2000 solving samples, 1000 sweeps, elite 0.1")
+    return out
+
+
+def measure_serving(spvar, count=12):
+    """c5: Poisson arrivals of 3D +-J instances, L in 8..20, through the
+    continuous-batching server (background engine): p50/p99 latency and
+    attempts/s.  The rate is 0.7 x the capacity measured on two requests."""
+    from paper_1706_07826_gb300 import instances as I
+    prm = spvar.make_params(num_starts=20, fixing_sample_size=250, solving_sample_size=250, num_sweeps=5000,
+                            elite_threshold=0.2, sweep_kernel=spvar.SWEEP_PM1)
+    srv = spvar.Server(prm, 8 << 30, max_n=8000, max_nnz=48000, max_degree=6, max_dmax=12, max_requests=32)
+    srv.start()
+    cal = [I.cubic3d(14, 1590 + i) for i in range(2)]
+    t0 = time.perf_counter()
+    ids = [srv.submit(x, 1) for x in cal]
+    infos = [srv.info(i, timeout=600.0) for i in ids]
+    dt = time.perf_counter() - t0
+    cap_attempts = sum(i.attempts for i in infos) / dt
+    mean_att = 20 * 500 * 5000 * np.mean([L ** 3 for L in range(8, 21)])
+    rate = 0.7 * cap_attempts / mean_att
+    arrivals, insts = I.poisson_stream(count, rate, 8, 20, seed=1500)
+    t0 = time.perf_counter()
+    ids = []
+    for ta, inst in zip(arrivals, insts):
+        wait = t0 + ta - time.perf_counter()
+        if wait > 0:
+            time.sleep(wait)
+        ids.append(srv.submit(inst, 1501 + len(ids)))
+    infos = [srv.info(i, timeout=1200.0) for i in ids]
+    t_end = time.perf_counter()
+    srv.stop()
+    lat = np.array([i.latency_s for i in infos])
+    att = sum(i.attempts for i in infos)
+    srv.close()
+    return {"value": att / (t_end - t0), "unit": UNIT, "requests": count, "rate_per_s": rate,
+            "latency_p50_s": float(np.percentile(lat, 50)), "latency_p99_s": float(np.percentile(lat, 99)),
+            "queue_p50_s": float(np.median([i.queue_s for i in infos])),
+            "config": "Poisson arrivals (0.7 x measured capacity) of 3D +-J instances, L uniform in 8..20 "
+                      "(N <= 8000), 20 starts x (250 + 250) samples, 5000 sweeps, elite 0.2, budget 8 GB"}
+
+
 def tts99(p, seconds_per_start):
     if p <= 0:
         return None
@@ -315,6 +383,11 @@ def gpu_arm(args, rank, world):
                                              "best_state"))
     e2e_value = sum(e2e_att) / sum(e2e_times) * world
 
+    extra = {}
+    if rank == 0 and world == 1 and not args.no_extra:
+        extra["uneven_batch"] = measure_uneven(spvar, torch, flush)
+        extra["serving"] = measure_serving(spvar)
+
     # roofline of the sweep kernel (integer ALU issue bound)
     mean_deg = 2 * inst.m / inst.n
     ops_per_attempt = PHILOX_OPS_PER_ATTEMPT + mean_deg + ACCEPT_OPS_PER_ATTEMPT
@@ -349,6 +422,7 @@ def gpu_arm(args, rank, world):
         "gpu_launches": K * (1 + 2 * 6),
         "clocks": cs,
     }
+    line.update(extra)
     if cpu:
         line["cpu_baseline"] = cpu
     print(json.dumps(line), flush=True)
@@ -364,6 +438,7 @@ def main():
     ap.add_argument("--ref-replicas", type=int, default=24, help="oracle replicas per core per step (reference arm)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-build", dest="build", action="store_false")
+    ap.add_argument("--no-extra", action="store_true", help="skip the uneven-batch and serving measurements")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

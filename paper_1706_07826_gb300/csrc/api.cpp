@@ -416,11 +416,15 @@ int spvar_sample(const spvar_problem *p, int32_t num_sweeps, const uint32_t *thr
     // shape: the register-resident +-1 kernel when it applies, else the general one
     SweepShape sh{0, (H.n >= 512) ? 256 : 128, Q, 1, 0, 0};
     if (pm1_kernel_eligible(H.pm1 != 0, H.dmax, H.maxdeg)) {
+        const int md = H.maxdeg <= 6 ? 6 : 8;
         for (int blk : {256, 512, 128}) {
             const int ns = pm1_nslot(H.n, Q, blk);
-            const int md = H.maxdeg <= 6 ? 6 : 8;
             if (ns > 0 && pm1_shape_ok(blk, ns, md)) { sh = SweepShape{1, blk, Q, 0, ns, md}; break; }
         }
+        // large problems: the streaming kernel (one quad per CTA)
+        if (sh.kind == 0 && pm1s_shape_ok(512, md, H.n, 1) &&
+            pm1s_smem_bytes(H.n, 1, md) <= (size_t)optin)
+            sh = SweepShape{2, 512, 1, 0, 0, md};
     }
     if (sh.kind == 0 && sweep_shape_smem(sh, H.n, thr_stride, H.maxdeg) > (size_t)optin) sh.stage = 0;
     const size_t smem = sweep_shape_smem(sh, H.n, thr_stride, H.maxdeg);
@@ -443,7 +447,8 @@ int spvar_sample(const spvar_problem *p, int32_t num_sweeps, const uint32_t *thr
     L.stage_ell = sh.stage;
     L.max_n = H.n;
     L.max_deg = H.maxdeg;
-    const int grid = ceil_div(quads, Q);
+    L.Q = sh.Q;
+    const int grid = ceil_div(quads, sh.Q);
     SPVAR_CUDA_TRY(launch_sweep_shape(L, sh, H.pm1 != 0, grid, smem, as_stream(stream)));
     return SPVAR_OK;
 }

@@ -190,6 +190,16 @@ std::vector<SweepShape> candidate_shapes(const spvar_plan *pl, int optin)
                 SweepShape sh{0, blocks[bi], Q, stg, 0, 0};
                 if (sweep_shape_smem(sh, pl->max_n0, pl->thr_stride, pl->max_deg) <= (size_t)optin) out.push_back(sh);
             }
+            if (Q == 1 && pm1_kernel_eligible(pl->pm1, pl->dmax, pl->max_deg)) {
+                const int md = pl->max_deg <= 6 ? 6 : 8;
+                for (int sb : {256, 512, 1024}) {
+                    if (sb != blocks[bi] && !(bi == 2 && sb == 1024)) continue;
+                    SweepShape sh{2, sb, 1, 0, 0, md};
+                    if (pm1s_shape_ok(sb, md, pl->max_n0, 1) &&
+                        sweep_shape_smem(sh, pl->max_n0, pl->thr_stride, pl->max_deg) <= (size_t)optin)
+                        out.push_back(sh);
+                }
+            }
             if (pm1_kernel_eligible(pl->pm1, pl->dmax, pl->max_deg)) {
                 const int ns = pm1_nslot(pl->max_n0, Q, blocks[bi]);
                 const int md = pl->max_deg <= 6 ? 6 : 8;
@@ -293,8 +303,8 @@ int spvar_plan_create(const spvar_problem *const *problems, int32_t nproblems,
         !(p.elite_threshold > 0.0) || !(p.elite_threshold <= 1.0) || !(p.beta0 > 0.0) || !(p.beta1 > 0.0) ||
         p.canon < -1 || p.canon > 1 || (p.form != SPVAR_FORM_BATCHED && p.form != SPVAR_FORM_PLAIN) ||
         p.replicas_per_block < 0 || (p.replicas_per_block % 4) != 0 || p.sweep_kernel < 0 ||
-        p.sweep_kernel > 2 || p.start_offset < 0 || (p.sweep_block != 0 && p.sweep_block != 128 && p.sweep_block != 256 &&
-                               p.sweep_block != 512))
+        p.sweep_kernel > 3 || p.start_offset < 0 || (p.sweep_block != 0 && p.sweep_block != 128 && p.sweep_block != 256 &&
+                               p.sweep_block != 512 && p.sweep_block != 1024))
         return SPVAR_EINVAL;
     const int Smax = std::max(p.fixing_sample_size, p.solving_sample_size);
     if (Smax > SPVAR_MAX_SAMPLES || p.num_sweeps > SPVAR_MAX_SWEEPS ||
@@ -487,8 +497,14 @@ int spvar_plan_create(const spvar_problem *const *problems, int32_t nproblems,
         if (p.sweep_kernel == SPVAR_SWEEP_PM1 || (p.sweep_kernel == SPVAR_SWEEP_AUTO && elig)) {
             const int ns = pm1_nslot(pl->max_n0, Q, blk);
             const int md = pl->max_deg <= 6 ? 6 : 8;
-            if (!elig || ns == 0 || !pm1_shape_ok(blk, ns, md)) { plan_free(pl); return SPVAR_ELIMIT; }
-            sh = SweepShape{1, blk, Q, 0, ns, md};
+            if (!elig) { plan_free(pl); return SPVAR_ELIMIT; }
+            if (ns > 0 && pm1_shape_ok(blk, ns, md)) sh = SweepShape{1, blk, Q, 0, ns, md};
+            else if (pm1s_shape_ok(blk, md, pl->max_n0, Q)) sh = SweepShape{2, blk, Q, 0, 0, md};
+            else { plan_free(pl); return SPVAR_ELIMIT; }
+        } else if (p.sweep_kernel == SPVAR_SWEEP_PM1S) {
+            const int md = pl->max_deg <= 6 ? 6 : 8;
+            if (!elig || !pm1s_shape_ok(blk, md, pl->max_n0, Q)) { plan_free(pl); return SPVAR_ELIMIT; }
+            sh = SweepShape{2, blk, Q, 0, 0, md};
         } else if (sweep_shape_smem(sh, pl->max_n0, pl->thr_stride, pl->max_deg) > (size_t)optin) {
             sh.stage = 0;
         }
@@ -620,7 +636,7 @@ int spvar_plan_shape(const spvar_plan *plan, int32_t *block, int32_t *replicas_p
     if (!plan) return SPVAR_EINVAL;
     if (block) *block = plan->shape.block;
     if (replicas_per_block) *replicas_per_block = 4 * plan->shape.Q;
-    if (staged) *staged = plan->shape.kind == 1 ? 2 : plan->shape.stage;
+    if (staged) *staged = plan->shape.kind == 1 ? 2 : plan->shape.kind == 2 ? 3 : plan->shape.stage;
     if (grid) *grid = plan->sweep_grid;
     return SPVAR_OK;
 }

@@ -430,15 +430,25 @@ int spvar_server_create(const spvar_server_config *cfg, spvar_server **out)
     E.C.P = S->P;
     E.C.Smax = Smax;
     E.C.nslots = S->nslots;
-    const int Q = p.replicas_per_block > 0 ? p.replicas_per_block / 4 : 1;
+    int Q = p.replicas_per_block > 0 ? p.replicas_per_block / 4 : 1;
     const int blk = p.sweep_block ? p.sweep_block : 512;
     E.shape = SweepShape{0, blk, Q, 1, 0, 0};
     if (sweep_shape_smem(E.shape, cfg->max_n, stride, cfg->max_degree) > (size_t)optin) E.shape.stage = 0;
+    // +-1-only servers: the streaming +-1 kernel (one quad per CTA) when it fits
+    const int md = cfg->max_degree <= 6 ? 6 : 8;
+    if ((p.sweep_kernel == SPVAR_SWEEP_PM1 || p.sweep_kernel == SPVAR_SWEEP_PM1S) && cfg->max_degree <= 8 &&
+        cfg->max_dmax <= 254 && pm1s_shape_ok(blk, md, cfg->max_n, 1)) {
+        SweepShape sh{2, blk, 1, 0, 0, md};
+        if (sweep_shape_smem(sh, cfg->max_n, stride, cfg->max_degree) <= (size_t)optin) {
+            E.shape = sh;
+            Q = 1;
+        }
+    }
     E.C.Q = Q;
     E.sweep_smem = sweep_shape_smem(E.shape, cfg->max_n, stride, cfg->max_degree);
     if (E.sweep_smem > (size_t)optin) { server_free(S); return SPVAR_ELIMIT; }
     // +-1-only servers use the byte-wise local field; otherwise general couplers
-    E.pm1 = p.sweep_kernel == SPVAR_SWEEP_PM1;
+    E.pm1 = p.sweep_kernel == SPVAR_SWEEP_PM1 || p.sweep_kernel == SPVAR_SWEEP_PM1S;
     E.max_n0 = cfg->max_n;
     E.max_deg = cfg->max_degree;
     E.thr_stride = stride;

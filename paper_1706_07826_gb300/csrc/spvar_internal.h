@@ -147,9 +147,16 @@ cudaError_t launch_sweep_pm1(const SweepLaunch &L, int block, int nslot, int max
                              cudaStream_t st);
 int pm1_max_active_blocks(int block, int nslot, int maxd, size_t smem);
 
+// Streaming +-1 sweep (sweep_pm1s.cu): one quad per work item.
+bool pm1s_shape_ok(int block, int maxd, int max_n, int Q);
+size_t pm1s_smem_bytes(int max_n, int Q, int maxd);
+cudaError_t launch_sweep_pm1s(const SweepLaunch &L, int block, int maxd, int grid, size_t smem, cudaStream_t st);
+int pm1s_max_active_blocks(int block, int maxd, size_t smem);
+
 // Launch shape of a sweep: kind 0 = general kernel (stage: layout staged in
 // shared memory), kind 1 = register-resident +-1 kernel (nslot items per
-// thread, maxd neighbour registers per item).
+// thread, maxd neighbour registers per item), kind 2 = streaming +-1 kernel
+// (maxd neighbour offsets per spin staged in shared memory, Q = 1).
 struct SweepShape {
     int kind, block, Q, stage, nslot, maxd;
 };
@@ -165,18 +172,22 @@ inline int pm1_nslot(int max_n, int Q, int block)
 }
 inline size_t sweep_shape_smem(const SweepShape &s, int max_n, int thr_stride, int max_deg)
 {
-    return s.kind == 1 ? pm1_smem_bytes(max_n, s.Q) : sweep_smem_bytes(max_n, s.Q, thr_stride, max_deg, s.stage != 0);
+    if (s.kind == 1) return pm1_smem_bytes(max_n, s.Q);
+    if (s.kind == 2) return pm1s_smem_bytes(max_n, s.Q, s.maxd);
+    return sweep_smem_bytes(max_n, s.Q, thr_stride, max_deg, s.stage != 0);
 }
 inline cudaError_t launch_sweep_shape(const SweepLaunch &L, const SweepShape &s, bool pm1, int grid, size_t smem,
                                       cudaStream_t st)
 {
-    return s.kind == 1 ? launch_sweep_pm1(L, s.block, s.nslot, s.maxd, grid, smem, st)
-                       : launch_sweep(L, pm1, s.block, grid, smem, st);
+    if (s.kind == 1) return launch_sweep_pm1(L, s.block, s.nslot, s.maxd, grid, smem, st);
+    if (s.kind == 2) return launch_sweep_pm1s(L, s.block, s.maxd, grid, smem, st);
+    return launch_sweep(L, pm1, s.block, grid, smem, st);
 }
 inline int sweep_shape_occupancy(const SweepShape &s, bool pm1, size_t smem)
 {
-    return s.kind == 1 ? pm1_max_active_blocks(s.block, s.nslot, s.maxd, smem)
-                       : sweep_max_active_blocks(pm1, s.block, smem, s.stage != 0);
+    if (s.kind == 1) return pm1_max_active_blocks(s.block, s.nslot, s.maxd, smem);
+    if (s.kind == 2) return pm1s_max_active_blocks(s.block, s.maxd, smem);
+    return sweep_max_active_blocks(pm1, s.block, smem, s.stage != 0);
 }
 
 // Everything one Multi-start SPVAR phase needs besides the slots.
