@@ -24,12 +24,22 @@ constexpr uint32_t kM0 = 0xD2511F53u, kM1 = 0xCD9E8D57u, kW0 = 0x9E3779B9u, kW1 
 
 template <int MAXD>
 struct SlotRegs {
-    int own;           // word offset of the slot's spin word
-    int nb[MAXD];      // word offsets of the neighbours (inverted copy if J < 0, zero word if padding)
+    uint32_t own;      // byte offset of the slot's spin word in shared memory
+    uint32_t nb[MAXD]; // byte offsets of the neighbours (inverted copy if J < 0, zero word if padding)
     uint32_t c0, c1;   // per byte: bias - deg + h, bias + deg - h
     uint32_t A, L0k, D, H3k, L3;  // Philox rounds 1-3 folded with the slot's fixed counter words
     int colour;        // colour class of the slot, -1 if the slot is empty
 };
+
+// Shared-memory word at a byte offset from the start of the dynamic window.
+__device__ __forceinline__ uint32_t lds_b(const uint32_t *base, uint32_t byte_off)
+{
+    return *reinterpret_cast<const uint32_t *>(reinterpret_cast<const char *>(base) + byte_off);
+}
+__device__ __forceinline__ void sts_b(uint32_t *base, uint32_t byte_off, uint32_t v)
+{
+    *reinterpret_cast<uint32_t *>(reinterpret_cast<char *>(base) + byte_off) = v;
+}
 
 __device__ __forceinline__ void mulhilo(uint32_t m, uint32_t a, uint32_t &hi, uint32_t &lo)
 {
@@ -127,9 +137,9 @@ __device__ void run_item_pm1(const SweepLaunch &L, const SweepJob &job, int quad
     for (int j = 0; j < NSLOT; ++j) {
         const int g = tid + j * B;
         s[j].colour = -1;
-        s[j].own = 2 * S1;
+        s[j].own = 4u * (uint32_t)(2 * S1);
 #pragma unroll
-        for (int d = 0; d < MAXD; ++d) s[j].nb[d] = 2 * S1;
+        for (int d = 0; d < MAXD; ++d) s[j].nb[d] = 4u * (uint32_t)(2 * S1);
         s[j].c0 = s[j].c1 = s[j].A = s[j].L0k = s[j].D = s[j].H3k = s[j].L3 = 0u;
         if (g < total) {
             int c = 0;
@@ -141,12 +151,12 @@ __device__ void run_item_pm1(const SweepLaunch &L, const SweepJob &job, int quad
             const uint32_t meta = P->meta[p];
             const int deg = (int)(meta & 0xFFFFu);
             const int h = (int)meta >> 16;
-            s[j].own = q * n + p;
+            s[j].own = 4u * (uint32_t)(q * n + p);
 #pragma unroll
             for (int d = 0; d < MAXD; ++d) {
                 if (d < deg) {
                     const uint32_t e = P->ell[(size_t)d * cap_n + p];
-                    s[j].nb[d] = ((e >> 31) ? S1 : 0) + q * n + (int)(e & 0xFFFFu);
+                    s[j].nb[d] = 4u * (uint32_t)(((e >> 31) ? S1 : 0) + q * n + (int)(e & 0xFFFFu));
                 }
             }
             s[j].c0 = (uint32_t)(bias - deg + h) * 0x01010101u;
@@ -169,10 +179,10 @@ __device__ void run_item_pm1(const SweepLaunch &L, const SweepJob &job, int quad
 #pragma unroll
             for (int j = 0; j < NSLOT; ++j) {
                 if (s[j].colour == c) {
-                    const uint32_t own = sw[s[j].own];
+                    const uint32_t own = lds_b(sw, s[j].own);
                     uint32_t x = 0;
 #pragma unroll
-                    for (int d = 0; d < MAXD; ++d) x += sw[s[j].nb[d]];
+                    for (int d = 0; d < MAXD; ++d) x += lds_b(sw, s[j].nb[d]);
                     // byte r: number of neighbours with b_j ^ [J_ij < 0] = 1; the
                     // flip-cost index dE/2 + bias is 2x + c0 if b_i = 0, c1 - 2x if b_i = 1
                     const uint32_t m = own * 0xFFu;
@@ -188,8 +198,8 @@ __device__ void run_item_pm1(const SweepLaunch &L, const SweepJob &job, int quad
                         if (uu[r] < th[ir]) flip |= 1u << (8 * r);
                     }
                     const uint32_t nw = own ^ flip;
-                    sw[s[j].own] = nw;
-                    sw[s[j].own + S1] = nw ^ 0x01010101u;
+                    sts_b(sw, s[j].own, nw);
+                    sts_b(sw, s[j].own + 4u * (uint32_t)S1, nw ^ 0x01010101u);
                     // next sweep's words: independent of the spins, so they are computed
                     // here, off the critical path of the following colour class
                     u[j] = philox_slot(s[j], y + 1u, K);
