@@ -171,7 +171,7 @@ def _flush(buf):
     buf.add_(1)
 
 
-def run_form(spvar, torch, plan, K, W, seeds0, flush, profile=False):
+def run_form(spvar, torch, plan, K, W, seeds0, flush, profile=False, nvtx="timed"):
     """W warm-up + K timed plan runs; returns (total ms, attempts list, outs)."""
     stream = torch.cuda.current_stream()
     attempts = []
@@ -185,9 +185,11 @@ def run_form(spvar, torch, plan, K, W, seeds0, flush, profile=False):
     best = []
     for k in range(K):
         _flush(flush)
+        torch.cuda.nvtx.range_push(nvtx)
         evs[k][0].record(stream)
         plan.run(seeds0 + 100 + k, out=out, device=True)
         evs[k][1].record(stream)
+        torch.cuda.nvtx.range_pop()
         if profile:
             ms, n = plan.sweep_time()
             sweep_ms += ms
@@ -235,9 +237,11 @@ def measure_uneven(spvar, torch, flush):
         torch.cuda.synchronize()
         flush.add_(1)
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.nvtx.range_push("c4_" + name)
         a.record()
         plan.run([x + 7 for x in seeds], device=True)
         b.record()
+        torch.cuda.nvtx.range_pop()
         torch.cuda.synchronize()
         att, _ = plan.stats()
         ms = a.elapsed_time(b)
@@ -332,13 +336,13 @@ def gpu_arm(args, rank, world):
 
     barrier()
     with ClockSampler(dev) as clk:
-        tb, att_b, best_b, _, out_b = run_form(spvar, torch, plan_b, K, W, seed_base, flush)
+        tb, att_b, best_b, _, out_b = run_form(spvar, torch, plan_b, K, W, seed_base, flush, nvtx="c2_batched")
     barrier()
     # profiled pass: same runs, sweep kernel timed with events on the launch stream
     _, att_prof, _, (sweep_ms, sweep_n), _ = run_form(spvar, torch, plan_b, max(3, K // 5), 1, seed_base, flush,
                                                        profile=True)
     Kp = max(3, K // 5)
-    tp, att_p, best_p, _, out_p = run_form(spvar, torch, plan_p, Kp, 1, seed_base, flush)
+    tp, att_p, best_p, _, out_p = run_form(spvar, torch, plan_p, Kp, 1, seed_base, flush, nvtx="c2_plain")
     barrier()
 
     t_b = torch.tensor([tb], dtype=torch.float64, device="cuda")

@@ -179,10 +179,16 @@ __device__ void run_item_pm1(const SweepLaunch &L, const SweepJob &job, int quad
 #pragma unroll
             for (int j = 0; j < NSLOT; ++j) {
                 if (s[j].colour == c) {
+                    // loads first; the next sweep's Philox block (independent of the spins)
+                    // is computed while they are in flight
                     const uint32_t own = lds_b(sw, s[j].own);
+                    uint32_t nbw[MAXD];
+#pragma unroll
+                    for (int d = 0; d < MAXD; ++d) nbw[d] = lds_b(sw, s[j].nb[d]);
+                    const uint4 unext = philox_slot(s[j], y + 1u, K);
                     uint32_t x = 0;
 #pragma unroll
-                    for (int d = 0; d < MAXD; ++d) x += lds_b(sw, s[j].nb[d]);
+                    for (int d = 0; d < MAXD; ++d) x += nbw[d];
                     // byte r: number of neighbours with b_j ^ [J_ij < 0] = 1; the
                     // flip-cost index dE/2 + bias is 2x + c0 if b_i = 0, c1 - 2x if b_i = 1
                     const uint32_t m = own * 0xFFu;
@@ -200,9 +206,7 @@ __device__ void run_item_pm1(const SweepLaunch &L, const SweepJob &job, int quad
                     const uint32_t nw = own ^ flip;
                     sts_b(sw, s[j].own, nw);
                     sts_b(sw, s[j].own + 4u * (uint32_t)S1, nw ^ 0x01010101u);
-                    // next sweep's words: independent of the spins, so they are computed
-                    // here, off the critical path of the following colour class
-                    u[j] = philox_slot(s[j], y + 1u, K);
+                    u[j] = unext;
                 }
             }
             __syncthreads();
