@@ -192,7 +192,7 @@ std::vector<SweepShape> candidate_shapes(const spvar_plan *pl, int optin)
             }
             if (Q == 1 && pm1_kernel_eligible(pl->pm1, pl->dmax, pl->max_deg)) {
                 const int md = pl->max_deg <= 6 ? 6 : 8;
-                for (int sb : {256, 512, 1024}) {
+                for (int sb : {128, 256, 512, 1024}) {
                     if (sb != blocks[bi] && !(bi == 2 && sb == 1024)) continue;
                     SweepShape sh{2, sb, 1, 0, 0, md};
                     if (pm1s_shape_ok(sb, md, pl->max_n0, 1) &&

@@ -167,10 +167,12 @@ __global__ void __launch_bounds__(B) k_sweep_pm1s(const SweepLaunch L)
 void *select_s(int block, int maxd)
 {
     if (maxd == 6) {
+        if (block == 128) return reinterpret_cast<void *>(k_sweep_pm1s<128, 6>);
         if (block == 256) return reinterpret_cast<void *>(k_sweep_pm1s<256, 6>);
         if (block == 512) return reinterpret_cast<void *>(k_sweep_pm1s<512, 6>);
         if (block == 1024) return reinterpret_cast<void *>(k_sweep_pm1s<1024, 6>);
     } else if (maxd == 8) {
+        if (block == 128) return reinterpret_cast<void *>(k_sweep_pm1s<128, 8>);
         if (block == 256) return reinterpret_cast<void *>(k_sweep_pm1s<256, 8>);
         if (block == 512) return reinterpret_cast<void *>(k_sweep_pm1s<512, 8>);
         if (block == 1024) return reinterpret_cast<void *>(k_sweep_pm1s<1024, 8>);
