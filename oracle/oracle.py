@@ -32,6 +32,7 @@ class OrParams(ctypes.Structure):
         ("max_fix_phases", ctypes.c_int32),
         ("canon", ctypes.c_int32),
         ("start0", ctypes.c_int32),
+        ("boost", ctypes.c_int32),
     ]
 
 
@@ -68,6 +69,10 @@ def lib():
                                ctypes.POINTER(OrParams), u32p, ctypes.c_int32, ctypes.c_uint64,
                                i64p, i32p, i32p, i32p, i8p, i64p, i8p]
         L.or_solve.restype = ctypes.c_int
+        L.or_components.argtypes = [ctypes.c_int32, i32p, i32p, i32p]
+        L.or_components.restype = ctypes.c_int32
+        L.or_component_boost.argtypes = [ctypes.c_int32, i32p, i32p, i32p, i32p, ctypes.c_int32, i8p, i64p]
+        L.or_component_boost.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -221,6 +226,22 @@ def reduce(p: Csr, fixed, colours=None):
     return red, (co[:m].copy(), colours[1]), oon[:m].copy()
 
 
+def components(p: Csr):
+    """Connected components, numbered by lowest spin index (Sec. II.C)."""
+    c = np.zeros(max(p.n, 1), np.int32)
+    m = lib().or_components(p.n, _p(p.row_ptr, i32p), _p(_c(p.col, np.int32), i32p), _p(c, i32p))
+    return c[:p.n].copy(), int(m)
+
+
+def component_boost(p: Csr, spins, e):
+    """Sec. II.C boosting of a sample; returns (merged spins, merged energies, components)."""
+    spins = _c(spins, np.int8).copy()
+    e = _c(e, np.int64).copy()
+    m = lib().or_component_boost(p.n, _p(p.row_ptr, i32p), _p(_c(p.col, np.int32), i32p),
+                                 _p(_c(p.val, np.int32), i32p), _p(p.h, i32p), len(e), _p(spins, i8p), _p(e, i64p))
+    return spins, e, int(m)
+
+
 @dataclasses.dataclass
 class SolveResult:
     energies: np.ndarray   # [starts, P, Smax]
@@ -233,11 +254,11 @@ class SolveResult:
 
 
 def solve(p: Csr, thr, seed, num_starts, fixing_sample_size, solving_sample_size, elite_threshold,
-          fix_num=1, fix_den=1, iterate=False, max_fix_phases=1, canon=-1, start0=0):
+          fix_num=1, fix_den=1, iterate=False, max_fix_phases=1, canon=-1, start0=0, boost=False):
     """Multi-start SPVAR (Alg. 2) with SA; thr is the original problem's table."""
     thr = _c(thr, np.uint32)
     prm = OrParams(num_starts, fixing_sample_size, solving_sample_size, thr.shape[0], float(elite_threshold),
-                   fix_num, fix_den, 1 if iterate else 0, max_fix_phases, canon, start0)
+                   fix_num, fix_den, 1 if iterate else 0, max_fix_phases, canon, start0, 1 if boost else 0)
     P = max_fix_phases + 1
     Smax = max(fixing_sample_size, solving_sample_size)
     n0 = p.n

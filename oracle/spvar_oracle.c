@@ -379,6 +379,85 @@ int or_reduce(int32_t n, const int32_t *row_ptr, const int32_t *col, const int32
 }
 
 /* ---------------------------------------------------------------------- */
+/* Disconnected-component boosting (Sec. II.C)                              */
+/* ---------------------------------------------------------------------- */
+int32_t or_components(int32_t n, const int32_t *row_ptr, const int32_t *col, int32_t *comp)
+{
+    int32_t *queue = (int32_t *)malloc(sizeof(int32_t) * ((size_t)n + 1));
+    for (int32_t i = 0; i < n; ++i) comp[i] = -1;
+    int32_t m = 0;
+    for (int32_t root = 0; root < n; ++root) {
+        if (comp[root] >= 0) continue;
+        int32_t head = 0, tail = 0;
+        comp[root] = m;
+        queue[tail++] = root;
+        while (head < tail) {
+            int32_t v = queue[head++];
+            for (int32_t p = row_ptr[v]; p < row_ptr[v + 1]; ++p)
+                if (comp[col[p]] < 0) {
+                    comp[col[p]] = m;
+                    queue[tail++] = col[p];
+                }
+        }
+        ++m;
+    }
+    free(queue);
+    return m;
+}
+
+static const int64_t *g_part_e; /* single-threaded oracle: plain qsort context */
+static int32_t g_part_m, g_part_c;
+static int cmp_partial(const void *a, const void *b)
+{
+    int32_t x = *(const int32_t *)a, y = *(const int32_t *)b;
+    int64_t ex = g_part_e[(int64_t)x * g_part_m + g_part_c], ey = g_part_e[(int64_t)y * g_part_m + g_part_c];
+    if (ex != ey) return ex < ey ? -1 : 1;
+    return x < y ? -1 : (x > y ? 1 : 0);
+}
+
+int or_component_boost(int32_t n, const int32_t *row_ptr, const int32_t *col, const int32_t *val,
+                       const int32_t *h, int32_t S, int8_t *spins, int64_t *e)
+{
+    if (n == 0 || S == 0) return 0;
+    int32_t *comp = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    int32_t m = or_components(n, row_ptr, col, comp);
+    /* partial energy of sample r on component c: couplers inside c once, biases of c */
+    int64_t *pe = (int64_t *)calloc((size_t)S * m, sizeof(int64_t));
+    for (int32_t r = 0; r < S; ++r) {
+        const int8_t *s = spins + (int64_t)r * n;
+        for (int32_t i = 0; i < n; ++i) {
+            int64_t v = (int64_t)h[i] * s[i];
+            for (int32_t p = row_ptr[i]; p < row_ptr[i + 1]; ++p)
+                if (col[p] > i) v += (int64_t)val[p] * s[i] * s[col[p]];
+            pe[(int64_t)r * m + comp[i]] += v;
+        }
+    }
+    /* each component's partial samples in (partial energy, sample index) order */
+    int32_t *perm = (int32_t *)malloc(sizeof(int32_t) * (size_t)S * m);
+    int32_t *idx = (int32_t *)malloc(sizeof(int32_t) * (size_t)S);
+    for (int32_t c = 0; c < m; ++c) {
+        for (int32_t r = 0; r < S; ++r) idx[r] = r;
+        g_part_e = pe;
+        g_part_m = m;
+        g_part_c = c;
+        qsort(idx, (size_t)S, sizeof(int32_t), cmp_partial);
+        for (int32_t r = 0; r < S; ++r) perm[(int64_t)c * S + r] = idx[r];
+    }
+    /* merged sample: rank r of every component; energy = sum of the partials */
+    int8_t *out = (int8_t *)malloc((size_t)S * n);
+    for (int32_t r = 0; r < S; ++r) {
+        int64_t E = 0;
+        for (int32_t c = 0; c < m; ++c) E += pe[(int64_t)perm[(int64_t)c * S + r] * m + c];
+        e[r] = E;
+        for (int32_t i = 0; i < n; ++i)
+            out[(int64_t)r * n + i] = spins[(int64_t)perm[(int64_t)comp[i] * S + r] * n + i];
+    }
+    memcpy(spins, out, (size_t)S * n);
+    free(out); free(idx); free(perm); free(pe); free(comp);
+    return m;
+}
+
+/* ---------------------------------------------------------------------- */
 /* Multi-start SPVAR (Alg. 2)                                               */
 /* ---------------------------------------------------------------------- */
 static int all_zero(int32_t n, const int32_t *h)
@@ -448,6 +527,7 @@ int or_solve(int32_t n0, const int32_t *row_ptr0, const int32_t *col0, const int
             rc = or_sample(n, rp[b], cl[b], vl[b], hh[b], co[b], ncol, prm->num_sweeps, thr, dmax,
                            0, S, seed, (uint32_t)(prm->start0 + st), (uint32_t)phase, spins, e, NULL);
             if (rc) break;
+            if (!fixing && prm->boost) or_component_boost(n, rp[b], cl[b], vl[b], hh[b], S, spins, e);
             int64_t *rec = energies + ((int64_t)st * P + phase) * Smax;
             for (int32_t r = 0; r < S; ++r) rec[r] = e[r] + off;
             counts[st * P + phase] = S;

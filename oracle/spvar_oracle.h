@@ -101,6 +101,18 @@ int or_reduce(int32_t n, const int32_t *row_ptr, const int32_t *col, const int32
               int32_t *n_out, int32_t *row_ptr_out, int32_t *col_out, int32_t *val_out,
               int32_t *h_out, int64_t *offset_out, int32_t *colour_out, int32_t *old_of_new);
 
+/* Connected components (Sec. II.C boosting): comp[i] = index of i's
+ * component, components numbered in increasing order of their lowest spin
+ * index.  Returns the number of components. */
+int32_t or_components(int32_t n, const int32_t *row_ptr, const int32_t *col, int32_t *comp);
+
+/* Disconnected-component boosting of one sample (Sec. II.C): partial energy
+ * of every sample on every component, each component's partial samples
+ * sorted by (partial energy, sample index), merged rank by rank.  spins
+ * [S*n] and e [S] (without offset) are replaced by the merged sample. */
+int or_component_boost(int32_t n, const int32_t *row_ptr, const int32_t *col, const int32_t *val,
+                       const int32_t *h, int32_t S, int8_t *spins, int64_t *e);
+
 /* Multi-start SPVAR (Alg. 2) with SA as the sampler. */
 typedef struct or_params {
     int32_t num_starts;
@@ -113,6 +125,7 @@ typedef struct or_params {
     int32_t max_fix_phases;        /* cap on SPVAR phases per start (>= 1) */
     int32_t canon;                 /* -1: when every h is 0; 0: never; 1: always */
     int32_t start0;                /* start st uses counter word start0 + st */
+    int32_t boost;                 /* 1: component boosting of the solving sample (Sec. II.C) */
 } or_params;
 
 /* Outputs (caller-allocated, P = max_fix_phases + 1, Smax = max sample size):

@@ -179,3 +179,85 @@ def test_ispvar_fixes_every_spin():
         ph = r.nphases[st]
         assert np.all(np.diff(r.nfree[st, :ph]) < 0)   # every phase fixes at least one spin
         assert _E(inst, r.best_state[st])[0] == r.best_e[st]
+
+
+def _disconnected():
+    """Three pieces: a 3D L=3 lattice, a Chimera cell, and two isolated biased spins."""
+    a, b = I.cubic3d(3, 14), I.chimera(1, 15)
+    n = a.n + b.n + 2
+    ei = np.concatenate([a.ei, b.ei + a.n])
+    ej = np.concatenate([a.ej, b.ej + a.n])
+    J = np.concatenate([a.J, b.J])
+    h = np.zeros(n, np.int32)
+    h[-2:] = [3, -2]
+    h[:5] = [1, 0, -1, 2, 0]
+    return I.Instance("disconnected", n, ei.astype(np.int32), ej.astype(np.int32), J.astype(np.int32), h)
+
+
+def test_components_against_scipy():
+    import scipy.sparse as sp
+    from scipy.sparse import csgraph
+    inst = _disconnected()
+    p = _csr(inst)
+    comp, m = O.components(p)
+    A = sp.csr_matrix((np.ones(p.nnz), p.col, p.row_ptr), shape=(p.n, p.n))
+    m2, lab = csgraph.connected_components(A, directed=False)
+    assert m == m2 == 4
+    # same partition, numbered by lowest member
+    first = {}
+    for i, l in enumerate(lab):
+        first.setdefault(l, len(first))
+    assert np.array_equal(comp, np.array([first[l] for l in lab]))
+
+
+def test_component_boost_invariants():
+    inst = _disconnected()
+    p = _csr(inst)
+    thr = O.thresholds(O.beta_geometric(20, 0.1, 1.0), O.dmax(p), 1)
+    spins, e, _ = O.sample(p, thr, 40, seed=3)
+    ms, me, m = O.component_boost(p, spins, e)
+    assert m == 4
+    # every merged state is a valid assignment whose energy is the merged energy
+    assert np.array_equal(_E(inst, ms), me)
+    # ranks: non-decreasing energies; the best merged state is at least as good as the best state
+    assert np.all(np.diff(me) >= 0)
+    assert me[0] <= e.min()
+    comp, _ = O.components(p)
+    # rank 0 takes each component's best partial state: its energy is the sum of the minima
+    M = _dense(inst)
+    S64 = spins.astype(np.int64)
+    best_sum = 0
+    for c in range(4):
+        sel = comp == c
+        Mc = M[np.ix_(sel, sel)]
+        part = np.einsum("si,ij,sj->s", S64[:, sel], Mc, S64[:, sel]) + S64[:, sel] @ inst.h[sel].astype(np.int64)
+        best_sum += part.min()
+    assert me[0] == best_sum
+
+
+def test_component_boost_is_a_sort_on_connected_problems():
+    inst = I.chimera(2, 8)
+    p = _csr(inst)
+    thr = O.thresholds(O.beta_geometric(10, 0.1, 1.0), O.dmax(p), 1)
+    spins, e, _ = O.sample(p, thr, 30, seed=4)
+    ms, me, m = O.component_boost(p, spins, e)
+    assert m == 1
+    order = np.lexsort((np.arange(30), e))
+    assert np.array_equal(me, e[order])
+    assert np.array_equal(ms, spins[order])
+
+
+def test_solve_with_boost_only_improves_the_solving_phase():
+    inst = I.cubic3d(4, 31)
+    p = _csr(inst)
+    thr = O.thresholds(O.beta_geometric(40, 0.1, 3.0), O.dmax(p), 1)
+    kw = dict(num_starts=3, fixing_sample_size=64, solving_sample_size=40, elite_threshold=0.1, fix_num=3,
+              fix_den=4)
+    a = O.solve(p, thr, seed=2, **kw)
+    b = O.solve(p, thr, seed=2, boost=True, **kw)
+    for st in range(3):
+        assert np.array_equal(a.energies[st, 0], b.energies[st, 0])          # fixing phase untouched
+        sa, sb = a.energies[st, 1, :40], b.energies[st, 1, :40]
+        assert np.all(np.diff(sb) >= 0) and sb[0] <= sa.min()
+        assert b.best_e[st] <= a.best_e[st]
+        assert _E(inst, b.best_state[st])[0] == b.best_e[st]
