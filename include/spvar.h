@@ -222,6 +222,9 @@ typedef struct spvar_params {
     int32_t sweep_kernel;        /* with replicas_per_block > 0: SPVAR_SWEEP_* */
     int32_t sweep_block;         /* with replicas_per_block > 0: threads per CTA (128/256/512), 0 = 256 */
     int32_t start_offset;        /* start s of a problem uses counter word start_offset + s (sharding) */
+    int32_t component_boost;     /* 1: disconnected-component boosting of the solving sample (Sec. II.C):
+                                    each connected component's partial samples are sorted by partial
+                                    energy and merged rank by rank; recorded energies are the merged ones */
 } spvar_params;
 
 #define SPVAR_SWEEP_AUTO 0    /* register kernel when eligible, else general */

@@ -7,6 +7,7 @@
 // sample (one broadcast word load per warp and row); fold/compact runs one
 // 1024-thread CTA per reduction with block-wide scans, writing the new CSR,
 // the inherited colour classes and the sweep layout of the smaller problem.
+#include <algorithm>
 #include <climits>
 
 #include "persist.cuh"
@@ -364,6 +365,157 @@ __global__ void k_count_active(const Slot *slots, int nslots, int32_t *nactive)
     if (threadIdx.x == 0) *nactive = s_n;
 }
 
+// ------------------------------------------------ component boosting (Sec. II.C)
+// Components of the current problem by min-label propagation with pointer
+// jumping; numbered in increasing order of their lowest spin index.
+__global__ void __launch_bounds__(kBigBlock) k_boost_components(Slot *slots, SolveConsts C)
+{
+    __shared__ int s_warp[32];
+    __shared__ int s_changed;
+    Slot &s = slots[blockIdx.x];
+    if (s.mode != kSolving) return;
+    const DevProb *P = s.cur;
+    const int n = P->n;
+    int32_t *lab = s.comp;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) lab[i] = i;
+    __syncthreads();
+    for (;;) {
+        if (threadIdx.x == 0) s_changed = 0;
+        __syncthreads();
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            int m = lab[i];
+            for (int p = P->row_ptr[i]; p < P->row_ptr[i + 1]; ++p) m = min(m, lab[P->col[p]]);
+            if (m < lab[i]) {
+                atomicMin(&lab[i], m);
+                s_changed = 1;
+            }
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            int l = lab[i];
+            while (lab[l] != l) l = lab[l];
+            lab[i] = l;
+        }
+        __syncthreads();
+        const int ch = s_changed;
+        __syncthreads();
+        if (!ch) break;
+    }
+    // rank of each root (a root is the lowest index of its component)
+    int32_t *rank = s.scratch;
+    int carry = 0;
+    for (int base = 0; base < n; base += blockDim.x) {
+        const int i = base + threadIdx.x;
+        const int f = (i < n && lab[i] == i) ? 1 : 0;
+        int tot;
+        const int ex = block_scan_excl(f, s_warp, &tot);
+        if (f) rank[i] = carry + ex;
+        carry += tot;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) lab[i] = rank[lab[i]];
+    if (threadIdx.x == 0) s.ncomp = carry;
+}
+
+// Twice the partial energy of sample r on every component (one CTA per sample).
+__global__ void __launch_bounds__(256) k_boost_partial(Slot *slots, SolveConsts C)
+{
+    extern __shared__ int s_acc[];
+    Slot &s = slots[blockIdx.y];
+    const int r = blockIdx.x;
+    if (s.mode != kSolving || r >= C.S_solve) return;
+    const DevProb *P = s.cur;
+    const int n = P->n, m = s.ncomp;
+    for (int c = threadIdx.x; c < m; c += blockDim.x) s_acc[c] = 0;
+    __syncthreads();
+    const uint32_t *row = s.spins + (size_t)r * s.W0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const int si = ((row[i >> 5] >> (i & 31)) & 1u) ? 1 : -1;
+        int v = 2 * P->h[i] * si;
+        for (int p = P->row_ptr[i]; p < P->row_ptr[i + 1]; ++p) {
+            const int j = P->col[p];
+            const int sj = ((row[j >> 5] >> (j & 31)) & 1u) ? 1 : -1;
+            v += P->val[p] * si * sj;
+        }
+        atomicAdd(&s_acc[s.comp[i]], v);
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < m; c += blockDim.x) s.part[(size_t)r * s.n0 + c] = s_acc[c];
+}
+
+// Each component's samples ordered by (partial energy, sample index).
+__global__ void __launch_bounds__(kBigBlock) k_boost_sort(Slot *slots, SolveConsts C)
+{
+    extern __shared__ __align__(16) unsigned long long s_key[];
+    Slot &s = slots[blockIdx.y];
+    const int c = blockIdx.x;
+    if (s.mode != kSolving || c >= s.ncomp) return;
+    const int S = C.S_solve;
+    int N2 = 1;
+    while (N2 < S) N2 <<= 1;
+    for (int r = threadIdx.x; r < N2; r += blockDim.x)
+        s_key[r] = (r < S) ? (((unsigned long long)((unsigned)s.part[(size_t)r * s.n0 + c] ^ 0x80000000u) << 32) |
+                              (unsigned)r)
+                           : ~0ull;
+    __syncthreads();
+    for (int size = 2; size <= N2; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int i = threadIdx.x; i < N2; i += blockDim.x) {
+                const int j = i ^ stride;
+                if (j > i) {
+                    const unsigned long long a = s_key[i], b = s_key[j];
+                    if ((a > b) == ((i & size) == 0)) {
+                        s_key[i] = b;
+                        s_key[j] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (int r = threadIdx.x; r < S; r += blockDim.x) s.perm[(size_t)c * C.Smax + r] = (int)(s_key[r] & 0xFFFFFFFFull);
+}
+
+// Rank r of the merged sample: each component's r-th partial state; its
+// energy (with offset) replaces the recorded one.  One CTA per rank.
+__global__ void __launch_bounds__(256) k_boost_merge(Slot *slots, SolveConsts C)
+{
+    __shared__ long long s_e;
+    Slot &s = slots[blockIdx.y];
+    const int r = blockIdx.x;
+    if (s.mode != kSolving || r >= C.S_solve) return;
+    const DevProb *P = s.cur;
+    const int n = P->n, m = s.ncomp;
+    if (threadIdx.x == 0) s_e = 0;
+    __syncthreads();
+    long long e = 0;
+    for (int c = threadIdx.x; c < m; c += blockDim.x) e += s.part[(size_t)s.perm[(size_t)c * C.Smax + r] * s.n0 + c];
+    atomicAdd((unsigned long long *)&s_e, (unsigned long long)e);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int Wn = (n + 31) >> 5;
+    for (int w = warp; w < Wn; w += blockDim.x / 32) {
+        const int i = 32 * w + lane;
+        unsigned b = 0;
+        if (i < n) {
+            const int src = s.perm[(size_t)s.comp[i] * C.Smax + r];
+            b = (s.spins[(size_t)src * s.W0 + w] >> lane) & 1u;
+        }
+        const unsigned bits = __ballot_sync(0xFFFFFFFFu, b);
+        if (lane == 0) s.spins2[(size_t)r * s.W0 + w] = bits;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) s.rec_e[(size_t)s.phase * C.Smax + r] = s_e / 2 + P->offset;
+}
+
+__global__ void __launch_bounds__(256) k_boost_copy(Slot *slots, SolveConsts C)
+{
+    Slot &s = slots[blockIdx.y];
+    const int r = blockIdx.x;
+    if (s.mode != kSolving || r >= C.S_solve) return;
+    const int Wn = (s.cur->n + 31) >> 5;
+    for (int w = threadIdx.x; w < Wn; w += blockDim.x) s.spins[(size_t)r * s.W0 + w] = s.spins2[(size_t)r * s.W0 + w];
+}
+
 __global__ void k_gather_modes(const Slot *slots, int nslots, int32_t *modes)
 {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nslots; i += gridDim.x * blockDim.x)
@@ -378,6 +530,21 @@ size_t elite_smem(int S)
 }
 
 }  // namespace
+
+cudaError_t launch_boost(Slot *slots, const SolveConsts &C, cudaStream_t st)
+{
+    if (!C.boost || C.S_solve <= 0 || C.nslots <= 0) return cudaSuccess;
+    k_boost_components<<<C.nslots, kBigBlock, 0, st>>>(slots, C);
+    const size_t acc = 4 * (size_t)std::max(C.max_n0, 1);
+    cudaFuncSetAttribute(k_boost_partial, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)acc);
+    k_boost_partial<<<dim3(C.S_solve, C.nslots), 256, acc, st>>>(slots, C);
+    const size_t keys = elite_smem(C.S_solve);
+    cudaFuncSetAttribute(k_boost_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)keys);
+    k_boost_sort<<<dim3(std::max(C.max_n0, 1), C.nslots), kBigBlock, keys, st>>>(slots, C);
+    k_boost_merge<<<dim3(C.S_solve, C.nslots), 256, 0, st>>>(slots, C);
+    k_boost_copy<<<dim3(C.S_solve, C.nslots), 256, 0, st>>>(slots, C);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_gather_modes(const Slot *slots, int nslots, int32_t *modes, cudaStream_t st)
 {

@@ -119,13 +119,40 @@ struct Slot {
     int8_t *fixed;             // [n0]
     int32_t *old_of_new;       // [n0]
     int32_t *scratch;          // [2 * n0]
+    // component boosting of the solving sample (Sec. II.C); null when off
+    int32_t *comp;             // [n0] component of each current spin
+    int32_t *part;             // [Smax][n0] twice the partial energy of sample r on component c
+    int32_t *perm;             // [n0][Smax] sample of rank r on component c
+    uint32_t *spins2;          // [Smax][W0] merged sample
+    int32_t ncomp, pad1;
 };
 
 struct SolveConsts {
     int32_t S_fix, S_solve, k_fix, iterate;
     int32_t max_fix, canon, fix_num, fix_den;
     int32_t P, Smax, Q, nslots;
+    int32_t boost, max_n0, pad0, pad1;
 };
+// Bytes of the boosting buffers of one slot (0 when boosting is off).
+inline size_t boost_slot_bytes(int boost, int n0, int Smax, int W0)
+{
+    if (!boost) return 0;
+    auto a = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    return a(4 * (size_t)n0) + 2 * a(4 * (size_t)Smax * n0) + a(4 * (size_t)Smax * W0);
+}
+// Carves the boosting buffers of a slot out of `base` (boost_slot_bytes bytes).
+inline void boost_slot_carve(Slot &s, char *base, int n0, int Smax, int W0)
+{
+    auto a = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    size_t o = 0;
+    s.comp = (int32_t *)(base + o);
+    o += a(4 * (size_t)n0);
+    s.part = (int32_t *)(base + o);
+    o += a(4 * (size_t)Smax * n0);
+    s.perm = (int32_t *)(base + o);
+    o += a(4 * (size_t)Smax * n0);
+    s.spins2 = (uint32_t *)(base + o);
+}
 
 cudaError_t launch_slots_init(Slot *slots, const SolveConsts &C, int max_n0, cudaStream_t st);
 cudaError_t launch_plan(Slot *slots, const SolveConsts &C, SweepJob *jobs, WorkItem *items,
@@ -207,6 +234,8 @@ struct PhaseEngine {
 cudaError_t engine_phase(const PhaseEngine &E, Slot *slots, int nslots, int T, int grid, cudaStream_t st,
                          bool count_active, bool capturing);
 cudaError_t launch_gather_modes(const Slot *slots, int nslots, int32_t *modes, cudaStream_t st);
+// Disconnected-component boosting of every solving-phase slot (Sec. II.C).
+cudaError_t launch_boost(Slot *slots, const SolveConsts &C, cudaStream_t st);
 
 // Elite selection of one sample set (standalone form).
 cudaError_t launch_elite_single(const int64_t *energies, int S, int k, int32_t *elite,

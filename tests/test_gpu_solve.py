@@ -155,3 +155,24 @@ def test_start_offset_shards_reproduce_full_run(cuda_lib):
     b = spvar.solve(gpu_problem(inst), spvar.make_params(num_starts=2, start_offset=3, **kw), 99)
     assert np.array_equal(np.concatenate([a.best_energy, b.best_energy]), full.best_energy)
     assert np.array_equal(np.concatenate([a.fixed, b.fixed]), full.fixed)
+
+
+BCASES = [
+    ("cubic_L4_tau34", lambda: I.cubic3d(4, 31), 40, 3, 64, 40, 0.1, (3, 4)),
+    ("chimera_C4_tau910", lambda: I.chimera(4, 33), 60, 2, 100, 64, 0.1, (9, 10)),
+    ("random_h", lambda: I.random_graph(40, 60, 5, jmax=3, hmax=2), 50, 3, 48, 33, 0.2, (1, 1)),
+    ("random_5_components", lambda: I.random_graph(60, 70, 9, jmax=3, hmax=1), 40, 3, 64, 40, 0.2, (3, 4)),
+]
+
+
+@pytest.mark.parametrize("form", [0, 1], ids=["batched", "plain"])
+@pytest.mark.parametrize("name,make,T,starts,Sf,Ss,elite,tau", BCASES, ids=[c[0] for c in BCASES])
+def test_component_boost_parity(cuda_lib, form, name, make, T, starts, Sf, Ss, elite, tau):
+    """Sec. II.C boosting of the solving sample: identical to the oracle."""
+    from paper_1706_07826_gb300 import spvar
+    inst = make()
+    ref = _oracle_solve(inst, T, 8, num_starts=starts, fixing_sample_size=Sf, solving_sample_size=Ss,
+                        elite_threshold=elite, fix_num=tau[0], fix_den=tau[1], boost=True)
+    prm = spvar.make_params(num_starts=starts, fixing_sample_size=Sf, solving_sample_size=Ss, num_sweeps=T,
+                            elite_threshold=elite, fix_num=tau[0], fix_den=tau[1], form=form, component_boost=True)
+    _check(spvar.solve(gpu_problem(inst), prm, 8), ref, starts, 2, inst.n)
