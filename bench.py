@@ -253,6 +253,41 @@ def measure_uneven(spvar, torch, flush):
     return out
 
 
+def measure_small_configs(spvar, torch):
+    """c1 (3D L=4, ISPVAR until every spin is fixed, 1 start, 256 samples) and
+    c3 (weak-strong Chimera C12 x100, 32 starts, 250 + 250 samples), batched and plain."""
+    from paper_1706_07826_gb300 import instances as I
+    out = {}
+    cases = {
+        "c1_cubic_L4_ispvar": (I.cubic3d(4, 1100), dict(num_starts=1, fixing_sample_size=256, solving_sample_size=0,
+                                                       num_sweeps=1000, elite_threshold=0.1, iterate=True,
+                                                       max_fix_phases=64)),
+        "c3_weak_strong_C12": (I.weak_strong(12, 1300), dict(num_starts=32, fixing_sample_size=250,
+                                                             solving_sample_size=250, num_sweeps=1000,
+                                                             elite_threshold=0.2)),
+    }
+    for name, (inst, kw) in cases.items():
+        prob = spvar.Problem.from_instance(inst)
+        res = {}
+        for form, fname in ((spvar.FORM_BATCHED, "batched"), (spvar.FORM_PLAIN, "plain")):
+            plan = spvar.Plan([prob], spvar.make_params(form=form, **kw))
+            plan.run(1, device=True)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            o = plan.run(2, device=True)
+            b.record()
+            torch.cuda.synchronize()
+            att, phases = plan.stats()
+            ms = a.elapsed_time(b)
+            res[fname] = {"value": att / (ms / 1000.0), "ms": ms, "phases": phases,
+                          "best_energy": int(o.best_energy.min().item()), "sweep_shape": plan.shape()}
+            plan.close()
+        res["speedup_batched_over_plain"] = res["batched"]["value"] / res["plain"]["value"]
+        out[name] = res
+    return out
+
+
 def measure_serving(spvar, count=12):
     """c5: Poisson arrivals of 3D +-J instances, L in 8..20, through the
     continuous-batching server (background engine): p50/p99 latency and
@@ -389,6 +424,7 @@ def gpu_arm(args, rank, world):
 
     extra = {}
     if rank == 0 and world == 1 and not args.no_extra:
+        extra.update(measure_small_configs(spvar, torch))
         extra["uneven_batch"] = measure_uneven(spvar, torch, flush)
         extra["serving"] = measure_serving(spvar)
 
