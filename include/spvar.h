@@ -231,6 +231,7 @@ typedef struct spvar_params {
 #define SPVAR_SWEEP_GENERAL 1 /* general integer-coupler kernel */
 #define SPVAR_SWEEP_PM1 2     /* +-1 kernels (register-resident, else streaming): |J| = 1, degree <= 8, dmax <= 254 */
 #define SPVAR_SWEEP_PM1S 3    /* streaming +-1 kernel (shared-memory neighbour offsets, 4 replicas per CTA) */
+#define SPVAR_SWEEP_PM1W 4    /* warp-per-quad +-1 kernel: replicas_per_block / 4 warps, one quad each */
 
 #define SPVAR_FORM_BATCHED 0 /* every start of every problem in one persistent launch per phase */
 #define SPVAR_FORM_PLAIN 1   /* one start at a time, one launch per kernel and start */

@@ -180,6 +180,15 @@ int upload_slots(spvar_plan *pl, const uint64_t *seeds, cudaStream_t st)
 std::vector<SweepShape> candidate_shapes(const spvar_plan *pl, int optin)
 {
     std::vector<SweepShape> out;
+    if (pm1_kernel_eligible(pl->pm1, pl->dmax, pl->max_deg)) {
+        const int md = pl->max_deg <= 6 ? 6 : 8;
+        for (int w : {2, 4, 8, 16}) {
+            SweepShape sh{4, 32 * w, w, 0, 0, md};
+            if (pm1w_shape_ok(w, md, pl->max_n0) &&
+                sweep_shape_smem(sh, pl->max_n0, pl->thr_stride, pl->max_deg) <= (size_t)optin)
+                out.push_back(sh);
+        }
+    }
     const int blocks[3] = {128, 256, 512};
     const int qs[4] = {1, 2, 4, 8};
     const int quads = ceil_div(pl->C.S_fix, 4);
@@ -304,7 +313,7 @@ int spvar_plan_create(const spvar_problem *const *problems, int32_t nproblems,
         !(p.elite_threshold > 0.0) || !(p.elite_threshold <= 1.0) || !(p.beta0 > 0.0) || !(p.beta1 > 0.0) ||
         p.canon < -1 || p.canon > 1 || (p.form != SPVAR_FORM_BATCHED && p.form != SPVAR_FORM_PLAIN) ||
         p.replicas_per_block < 0 || (p.replicas_per_block % 4) != 0 || p.sweep_kernel < 0 ||
-        p.sweep_kernel > 3 || p.start_offset < 0 || p.component_boost < 0 || p.component_boost > 1 || (p.sweep_block != 0 && p.sweep_block != 128 && p.sweep_block != 256 &&
+        p.sweep_kernel > 4 || p.start_offset < 0 || p.component_boost < 0 || p.component_boost > 1 || (p.sweep_block != 0 && p.sweep_block != 128 && p.sweep_block != 256 &&
                                p.sweep_block != 512 && p.sweep_block != 1024))
         return SPVAR_EINVAL;
     const int Smax = std::max(p.fixing_sample_size, p.solving_sample_size);
@@ -507,6 +516,10 @@ int spvar_plan_create(const spvar_problem *const *problems, int32_t nproblems,
             if (ns > 0 && pm1_shape_ok(blk, ns, md)) sh = SweepShape{1, blk, Q, 0, ns, md};
             else if (pm1s_shape_ok(blk, md, pl->max_n0, Q)) sh = SweepShape{2, blk, Q, 0, 0, md};
             else { plan_free(pl); return SPVAR_ELIMIT; }
+        } else if (p.sweep_kernel == SPVAR_SWEEP_PM1W) {
+            const int md = pl->max_deg <= 6 ? 6 : 8;
+            if (!elig || !pm1w_shape_ok(Q, md, pl->max_n0)) { plan_free(pl); return SPVAR_ELIMIT; }
+            sh = SweepShape{4, 32 * Q, Q, 0, 0, md};
         } else if (p.sweep_kernel == SPVAR_SWEEP_PM1S) {
             const int md = pl->max_deg <= 6 ? 6 : 8;
             if (!elig || !pm1s_shape_ok(blk, md, pl->max_n0, Q)) { plan_free(pl); return SPVAR_ELIMIT; }
@@ -642,7 +655,8 @@ int spvar_plan_shape(const spvar_plan *plan, int32_t *block, int32_t *replicas_p
     if (!plan) return SPVAR_EINVAL;
     if (block) *block = plan->shape.block;
     if (replicas_per_block) *replicas_per_block = 4 * plan->shape.Q;
-    if (staged) *staged = plan->shape.kind == 1 ? 2 : plan->shape.kind == 2 ? 3 : plan->shape.stage;
+    if (staged) *staged = plan->shape.kind == 1 ? 2 : plan->shape.kind == 2 ? 3 : plan->shape.kind == 4 ? 4
+                                                                                                : plan->shape.stage;
     if (grid) *grid = plan->sweep_grid;
     return SPVAR_OK;
 }

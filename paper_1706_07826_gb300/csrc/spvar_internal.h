@@ -180,10 +180,17 @@ size_t pm1s_smem_bytes(int max_n, int Q, int maxd);
 cudaError_t launch_sweep_pm1s(const SweepLaunch &L, int block, int maxd, int grid, size_t smem, cudaStream_t st);
 int pm1s_max_active_blocks(int block, int maxd, size_t smem);
 
+// Warp-per-quad +-1 sweep (sweep_pm1w.cu): WARPS quads per work item.
+bool pm1w_shape_ok(int warps, int maxd, int max_n);
+size_t pm1w_smem_bytes(int max_n, int warps, int maxd);
+cudaError_t launch_sweep_pm1w(const SweepLaunch &L, int warps, int maxd, int grid, size_t smem, cudaStream_t st);
+int pm1w_max_active_blocks(int warps, int maxd, size_t smem);
+
 // Launch shape of a sweep: kind 0 = general kernel (stage: layout staged in
 // shared memory), kind 1 = register-resident +-1 kernel (nslot items per
 // thread, maxd neighbour registers per item), kind 2 = streaming +-1 kernel
-// (maxd neighbour offsets per spin staged in shared memory, Q = 1).
+// (maxd neighbour offsets per spin staged in shared memory, Q = 1), kind 4 =
+// warp-per-quad +-1 kernel (Q = warps = block / 32).
 struct SweepShape {
     int kind, block, Q, stage, nslot, maxd;
 };
@@ -201,6 +208,7 @@ inline size_t sweep_shape_smem(const SweepShape &s, int max_n, int thr_stride, i
 {
     if (s.kind == 1) return pm1_smem_bytes(max_n, s.Q);
     if (s.kind == 2) return pm1s_smem_bytes(max_n, s.Q, s.maxd);
+    if (s.kind == 4) return pm1w_smem_bytes(max_n, s.Q, s.maxd);
     return sweep_smem_bytes(max_n, s.Q, thr_stride, max_deg, s.stage != 0);
 }
 inline cudaError_t launch_sweep_shape(const SweepLaunch &L, const SweepShape &s, bool pm1, int grid, size_t smem,
@@ -208,12 +216,14 @@ inline cudaError_t launch_sweep_shape(const SweepLaunch &L, const SweepShape &s,
 {
     if (s.kind == 1) return launch_sweep_pm1(L, s.block, s.nslot, s.maxd, grid, smem, st);
     if (s.kind == 2) return launch_sweep_pm1s(L, s.block, s.maxd, grid, smem, st);
+    if (s.kind == 4) return launch_sweep_pm1w(L, s.Q, s.maxd, grid, smem, st);
     return launch_sweep(L, pm1, s.block, grid, smem, st);
 }
 inline int sweep_shape_occupancy(const SweepShape &s, bool pm1, size_t smem)
 {
     if (s.kind == 1) return pm1_max_active_blocks(s.block, s.nslot, s.maxd, smem);
     if (s.kind == 2) return pm1s_max_active_blocks(s.block, s.maxd, smem);
+    if (s.kind == 4) return pm1w_max_active_blocks(s.Q, s.maxd, smem);
     return sweep_max_active_blocks(pm1, s.block, smem, s.stage != 0);
 }
 

@@ -65,19 +65,22 @@ __device__ __forceinline__ void init_spins(const DevProb *P, const SweepJob &job
 }
 
 // Final energies (with offset) and bit-packed states of the item's replicas.
-// e2: 4 * nq ints of shared memory.  Contains __syncthreads.
+// Quad q's words start at sw + q * qstride (qstride = n when the quads are
+// packed back to back).  e2: 4 * nq ints of shared memory.  Contains
+// __syncthreads.
 template <bool PM1>
 __device__ __forceinline__ void finish_item(const DevProb *P, const SweepJob &job, int quad0, int nq,
-                                            const uint32_t *sw, int *e2)
+                                            const uint32_t *sw, int *e2, int qstride = -1)
 {
     const int tid = threadIdx.x, B = blockDim.x;
     const int n = P->n;
+    const int qs = qstride < 0 ? n : qstride;
     for (int x = tid; x < 4 * nq; x += B) e2[x] = 0;
     __syncthreads();
     for (int x = tid; x < nq * n; x += B) {
         const int q = x / n, p = x - q * n;
         int c2[4];
-        energy2<PM1>(sw[x], P->meta[p], P->ell, P->cap_n, p, sw + q * n, c2);
+        energy2<PM1>(sw[q * qs + p], P->meta[p], P->ell, P->cap_n, p, sw + q * qs, c2);
 #pragma unroll
         for (int r = 0; r < 4; ++r) atomicAdd(&e2[4 * q + r], c2[r]);
     }
@@ -92,7 +95,7 @@ __device__ __forceinline__ void finish_item(const DevProb *P, const SweepJob &jo
     for (int x = warp; x < nq * Wn; x += B / 32) {
         const int q = x / Wn, w = x - q * Wn;
         const int i = 32 * w + lane;
-        const uint32_t word = (i < n) ? sw[q * n + P->pos_of_idx[i]] : 0u;
+        const uint32_t word = (i < n) ? sw[q * qs + P->pos_of_idx[i]] : 0u;
 #pragma unroll
         for (int rr = 0; rr < 4; ++rr) {
             const uint32_t bits = __ballot_sync(0xFFFFFFFFu, (word >> (8 * rr)) & 1u);

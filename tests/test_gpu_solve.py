@@ -57,7 +57,7 @@ def test_solve_parity(cuda_lib, form, name, make, T, starts, Sf, Ss, elite, iter
 
 
 SHAPES = [(4, 1, 256), (8, 1, 128), (32, 1, 512), (4, 2, 256), (8, 2, 128), (4, 2, 512), (16, 2, 256),
-          (16, 2, 128), (4, 3, 256), (4, 3, 512), (4, 3, 1024)]
+          (16, 2, 128), (4, 3, 256), (4, 3, 512), (4, 3, 1024), (8, 4, 0), (16, 4, 0), (32, 4, 0), (64, 4, 0)]
 
 
 @pytest.mark.parametrize("rpb,kernel,block", SHAPES, ids=["%d-%d-%d" % s for s in SHAPES])
@@ -73,7 +73,7 @@ def test_solve_identical_for_every_sweep_shape(cuda_lib, rpb, kernel, block, mak
     prm = spvar.make_params(num_starts=2, fixing_sample_size=45, solving_sample_size=45, num_sweeps=T,
                             elite_threshold=0.2, replicas_per_block=rpb, sweep_kernel=kernel, sweep_block=block)
     plan = spvar.Plan([gpu_problem(inst)], prm)
-    want = {2: "pm1-register", 3: "pm1-streaming"}.get(kernel, plan.shape()["kernel"])
+    want = {2: "pm1-register", 3: "pm1-streaming", 4: "pm1-warp"}.get(kernel, plan.shape()["kernel"])
     assert plan.shape()["kernel"] == want
     _check(plan.run(seed, device=False), ref, 2, 2, inst.n)
 
