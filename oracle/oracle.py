@@ -33,6 +33,7 @@ class OrParams(ctypes.Structure):
         ("canon", ctypes.c_int32),
         ("start0", ctypes.c_int32),
         ("boost", ctypes.c_int32),
+        ("tree", ctypes.c_int32),
     ]
 
 
@@ -73,6 +74,11 @@ def lib():
         L.or_components.restype = ctypes.c_int32
         L.or_component_boost.argtypes = [ctypes.c_int32, i32p, i32p, i32p, i32p, ctypes.c_int32, i8p, i64p]
         L.or_component_boost.restype = ctypes.c_int
+        L.or_tree.argtypes = [ctypes.c_int32, i32p, i32p, i32p, i32p, i64p, i8p, i32p, i32p, i32p]
+        L.or_tree.restype = ctypes.c_int32
+        L.or_compact.argtypes = [ctypes.c_int32, i32p, i32p, i32p, i32p, ctypes.c_int64, i32p, i8p,
+                                 i32p, i32p, i32p, i32p, i32p, i64p, i32p, i32p]
+        L.or_compact.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -242,6 +248,42 @@ def component_boost(p: Csr, spins, e):
     return spins, e, int(m)
 
 
+def tree(p: Csr):
+    """Sec. II.C tree pre-processing.  Returns (h', offset', code, parent, order)."""
+    h = p.h.copy()
+    off = np.array([p.offset], np.int64)
+    code = np.zeros(max(p.n, 1), np.int8)
+    par = np.zeros(max(p.n, 1), np.int32)
+    order = np.zeros(max(p.n, 1), np.int32)
+    ninf = np.zeros(1, np.int32)
+    lib().or_tree(p.n, _p(p.row_ptr, i32p), _p(_c(p.col, np.int32), i32p), _p(_c(p.val, np.int32), i32p),
+                  _p(h, i32p), _p(off, i64p), _p(code, i8p), _p(par, i32p), _p(order, i32p), _p(ninf, i32p))
+    return h, int(off[0]), code[:p.n].copy(), par[:p.n].copy(), order[:int(ninf[0])].copy()
+
+
+def compact(p: Csr, code, colours=None):
+    """Drop every spin with code != 0 without folding (after the tree step)."""
+    if colours is None:
+        colours = colour(p)
+    c = _c(colours[0], np.int32) if p.n else np.zeros(1, np.int32)
+    code = _c(code, np.int8) if p.n else np.zeros(1, np.int8)
+    n_out = np.zeros(1, np.int32)
+    rp = np.zeros(p.n + 1, np.int32)
+    col = np.zeros(max(p.nnz, 1), np.int32)
+    val = np.zeros(max(p.nnz, 1), np.int32)
+    h = np.zeros(max(p.n, 1), np.int32)
+    off = np.zeros(1, np.int64)
+    co = np.zeros(max(p.n, 1), np.int32)
+    oon = np.zeros(max(p.n, 1), np.int32)
+    lib().or_compact(p.n, _p(p.row_ptr, i32p), _p(_c(p.col, np.int32), i32p), _p(_c(p.val, np.int32), i32p),
+                     _p(p.h, i32p), p.offset, _p(c, i32p), _p(code, i8p), _p(n_out, i32p), _p(rp, i32p),
+                     _p(col, i32p), _p(val, i32p), _p(h, i32p), _p(off, i64p), _p(co, i32p), _p(oon, i32p))
+    m = int(n_out[0])
+    nnz = int(rp[m])
+    red = Csr(m, rp[:m + 1].copy(), col[:nnz].copy(), val[:nnz].copy(), h[:m].copy(), int(off[0]), p.scale)
+    return red, (co[:m].copy(), colours[1]), oon[:m].copy()
+
+
 @dataclasses.dataclass
 class SolveResult:
     energies: np.ndarray   # [starts, P, Smax]
@@ -254,11 +296,12 @@ class SolveResult:
 
 
 def solve(p: Csr, thr, seed, num_starts, fixing_sample_size, solving_sample_size, elite_threshold,
-          fix_num=1, fix_den=1, iterate=False, max_fix_phases=1, canon=-1, start0=0, boost=False):
+          fix_num=1, fix_den=1, iterate=False, max_fix_phases=1, canon=-1, start0=0, boost=False, tree=False):
     """Multi-start SPVAR (Alg. 2) with SA; thr is the original problem's table."""
     thr = _c(thr, np.uint32)
     prm = OrParams(num_starts, fixing_sample_size, solving_sample_size, thr.shape[0], float(elite_threshold),
-                   fix_num, fix_den, 1 if iterate else 0, max_fix_phases, canon, start0, 1 if boost else 0)
+                   fix_num, fix_den, 1 if iterate else 0, max_fix_phases, canon, start0, 1 if boost else 0,
+                   1 if tree else 0)
     P = max_fix_phases + 1
     Smax = max(fixing_sample_size, solving_sample_size)
     n0 = p.n

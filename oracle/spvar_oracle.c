@@ -458,6 +458,111 @@ int or_component_boost(int32_t n, const int32_t *row_ptr, const int32_t *col, co
 }
 
 /* ---------------------------------------------------------------------- */
+/* Tree pre-processing (Sec. II.C)                                          */
+/* ---------------------------------------------------------------------- */
+static int sgn(int64_t x) { return (x > 0) - (x < 0); }
+
+int32_t or_tree(int32_t n, const int32_t *row_ptr, const int32_t *col, const int32_t *val, int32_t *h,
+                int64_t *offset, int8_t *code, int32_t *parent, int32_t *order, int32_t *ninfer)
+{
+    int32_t *deg = (int32_t *)malloc(sizeof(int32_t) * ((size_t)n + 1));
+    int8_t *pick = (int8_t *)malloc((size_t)n + 1);
+    int32_t removed = 0, ni = 0;
+    for (int32_t i = 0; i < n; ++i) { code[i] = 0; parent[i] = -1; }
+    for (;;) {
+        /* active degree of every active spin */
+        for (int32_t i = 0; i < n; ++i) {
+            deg[i] = 0;
+            if (code[i]) continue;
+            for (int32_t p = row_ptr[i]; p < row_ptr[i + 1]; ++p)
+                if (code[col[p]] == 0) deg[i]++;
+        }
+        /* this round's leaves */
+        int32_t any = 0;
+        for (int32_t i = 0; i < n; ++i) {
+            pick[i] = 0;
+            if (code[i] || deg[i] > 1) continue;
+            if (deg[i] == 1) {
+                int32_t j = -1;
+                for (int32_t p = row_ptr[i]; p < row_ptr[i + 1]; ++p)
+                    if (code[col[p]] == 0) j = col[p];
+                if (deg[j] == 1 && i < j) continue; /* isolated coupler: the higher end goes first */
+            }
+            pick[i] = 1;
+            any = 1;
+        }
+        if (!any) break;
+        /* eliminate them simultaneously (updates of a shared neighbour add up) */
+        int32_t *hnew = (int32_t *)malloc(sizeof(int32_t) * ((size_t)n + 1));
+        memcpy(hnew, h, sizeof(int32_t) * (size_t)n);
+        for (int32_t i = 0; i < n; ++i) {
+            if (!pick[i]) continue;
+            if (deg[i] == 0) {
+                int8_t v = h[i] > 0 ? -1 : 1;
+                *offset += (int64_t)h[i] * v;
+                code[i] = v;
+            } else {
+                int32_t j = -1, J = 0;
+                for (int32_t p = row_ptr[i]; p < row_ptr[i + 1]; ++p)
+                    if (code[col[p]] == 0) { j = col[p]; J = val[p]; }
+                if (llabs((long long)J) <= llabs((long long)h[i])) {
+                    int8_t v = (int8_t)(-sgn(h[i]));
+                    *offset += (int64_t)h[i] * v;
+                    hnew[j] += J * v;
+                    code[i] = v;
+                } else {
+                    *offset -= llabs((long long)J);
+                    hnew[j] -= sgn(J) * h[i];
+                    code[i] = 2;
+                    parent[i] = j;
+                    order[ni++] = i;
+                }
+            }
+            removed++;
+        }
+        /* codes of this round were set in index order; active degrees of the next
+           round are recomputed from scratch, so the order does not matter */
+        memcpy(h, hnew, sizeof(int32_t) * (size_t)n);
+        free(hnew);
+    }
+    free(deg);
+    free(pick);
+    if (ninfer) *ninfer = ni;
+    return removed;
+}
+
+int or_compact(int32_t n, const int32_t *row_ptr, const int32_t *col, const int32_t *val,
+               const int32_t *h, int64_t offset, const int32_t *colour, const int8_t *code,
+               int32_t *n_out, int32_t *row_ptr_out, int32_t *col_out, int32_t *val_out,
+               int32_t *h_out, int64_t *offset_out, int32_t *colour_out, int32_t *old_of_new)
+{
+    int32_t *new_of_old = (int32_t *)malloc(sizeof(int32_t) * ((size_t)n + 1));
+    int32_t m = 0;
+    for (int32_t i = 0; i < n; ++i) {
+        new_of_old[i] = code[i] == 0 ? m : -1;
+        if (code[i] == 0) old_of_new[m++] = i;
+    }
+    int32_t nnz = 0;
+    row_ptr_out[0] = 0;
+    for (int32_t a = 0; a < m; ++a) {
+        int32_t i = old_of_new[a];
+        for (int32_t p = row_ptr[i]; p < row_ptr[i + 1]; ++p)
+            if (code[col[p]] == 0) {
+                col_out[nnz] = new_of_old[col[p]];
+                val_out[nnz] = val[p];
+                ++nnz;
+            }
+        h_out[a] = h[i];
+        colour_out[a] = colour[i];
+        row_ptr_out[a + 1] = nnz;
+    }
+    *n_out = m;
+    *offset_out = offset;
+    free(new_of_old);
+    return 0;
+}
+
+/* ---------------------------------------------------------------------- */
 /* Multi-start SPVAR (Alg. 2)                                               */
 /* ---------------------------------------------------------------------- */
 static int all_zero(int32_t n, const int32_t *h)
@@ -501,6 +606,13 @@ int or_solve(int32_t n0, const int32_t *row_ptr0, const int32_t *col0, const int
     int8_t *spins = (int8_t *)malloc((size_t)Smax * (size_t)n0 + 1);
     int64_t *e = (int64_t *)malloc(sizeof(int64_t) * ((size_t)Smax + 1));
     int32_t *elite = (int32_t *)malloc(sizeof(int32_t) * ((size_t)Smax + 1));
+    /* tree pre-processing: codes, parents, and the inference log in original indices */
+    int8_t *tcode = (int8_t *)malloc((size_t)n0 + 1);
+    int32_t *tpar = (int32_t *)malloc(sizeof(int32_t) * ((size_t)n0 + 1));
+    int32_t *tord = (int32_t *)malloc(sizeof(int32_t) * ((size_t)n0 + 1));
+    int32_t *log_child = (int32_t *)malloc(sizeof(int32_t) * ((size_t)n0 + 1));
+    int32_t *log_parent = (int32_t *)malloc(sizeof(int32_t) * ((size_t)n0 + 1));
+    int8_t *log_sigma = (int8_t *)malloc((size_t)n0 + 1);
     int rc = 0;
 
     for (int32_t st = 0; st < prm->num_starts && rc == 0; ++st) {
@@ -518,6 +630,7 @@ int or_solve(int32_t n0, const int32_t *row_ptr0, const int32_t *col0, const int
         memset(fmap, 0, (size_t)n0);
         best_e[st] = INT64_MAX;
         int32_t phase = 0;
+        int32_t nlog = 0;
 
         for (;;) {
             int fixing = phase < prm->max_fix_phases &&
@@ -539,6 +652,9 @@ int or_solve(int32_t n0, const int32_t *row_ptr0, const int32_t *col0, const int
                 best_e[st] = e[elite[0]] + off;
                 for (int32_t i = 0; i < n0; ++i) bstate[i] = fmap[i];
                 for (int32_t a = 0; a < n; ++a) bstate[orig[a]] = spins[(int64_t)elite[0] * n + a];
+                /* inferred spins, latest elimination first: s_child = sigma s_parent */
+                for (int32_t q = nlog - 1; q >= 0; --q)
+                    bstate[log_child[q]] = (int8_t)(log_sigma[q] * bstate[log_parent[q]]);
             }
             ++phase;
             if (!fixing) break;
@@ -564,6 +680,28 @@ int or_solve(int32_t n0, const int32_t *row_ptr0, const int32_t *col0, const int
             n = n2;
             off = off2;
             b = 1 - b;
+            if (prm->tree && n > 0) {
+                int32_t ninf = 0;
+                or_tree(n, rp[b], cl[b], vl[b], hh[b], &off, tcode, tpar, tord, &ninf);
+                for (int32_t a = 0; a < n; ++a)
+                    if (tcode[a] == 1 || tcode[a] == -1) fmap[orig[a]] = tcode[a];
+                for (int32_t q = 0; q < ninf; ++q) {
+                    int32_t a = tord[q], j = tpar[a], J = 0;
+                    for (int32_t p = rp[b][a]; p < rp[b][a + 1]; ++p)
+                        if (cl[b][p] == j) J = vl[b][p];
+                    log_child[nlog] = orig[a];
+                    log_parent[nlog] = orig[j];
+                    log_sigma[nlog] = (int8_t)(J > 0 ? -1 : 1);
+                    ++nlog;
+                }
+                or_compact(n, rp[b], cl[b], vl[b], hh[b], off, co[b], tcode, &n2, rp[1 - b], cl[1 - b],
+                           vl[1 - b], hh[1 - b], &off2, co[1 - b], old_of_new);
+                for (int32_t a = 0; a < n2; ++a) tmp[a] = orig[old_of_new[a]];
+                memcpy(orig, tmp, sizeof(int32_t) * (size_t)n2);
+                n = n2;
+                off = off2;
+                b = 1 - b;
+            }
         }
         nphases[st] = phase;
     }
@@ -571,5 +709,6 @@ int or_solve(int32_t n0, const int32_t *row_ptr0, const int32_t *col0, const int
     for (int b = 0; b < 2; ++b) { free(rp[b]); free(cl[b]); free(vl[b]); free(hh[b]); free(co[b]); }
     free(colour0); free(orig); free(old_of_new); free(tmp); free(cnt); free(fx);
     free(spins); free(e); free(elite);
+    free(tcode); free(tpar); free(tord); free(log_child); free(log_parent); free(log_sigma);
     return rc;
 }

@@ -113,6 +113,27 @@ int32_t or_components(int32_t n, const int32_t *row_ptr, const int32_t *col, int
 int or_component_boost(int32_t n, const int32_t *row_ptr, const int32_t *col, const int32_t *val,
                        const int32_t *h, int32_t S, int8_t *spins, int64_t *e);
 
+/* Tree pre-processing (Sec. II.C), in rounds.  In each round every active
+ * spin of active degree 0, and every spin of active degree 1 except the
+ * lower-index end of an isolated coupler, is eliminated at once:
+ *   degree 0:              fixed to -sign(h) (+1 if h = 0);
+ *   degree 1, |J| <= |h|:  fixed to -sign(h), J v folded into the neighbour;
+ *   degree 1, |J| >  |h|:  inferred s_i = -sign(J) s_j: h_j -= sign(J) h_i,
+ *                          offset -= |J|.
+ * Biases and the constant are updated in place (h [n], *offset); code[i] is
+ * 0 (kept), +1/-1 (fixed to that value) or 2 (inferred from parent[i]);
+ * order[] lists the inferred spins in elimination order.  Returns the number
+ * of eliminated spins; *ninfer gets the number of inferred ones. */
+int32_t or_tree(int32_t n, const int32_t *row_ptr, const int32_t *col, const int32_t *val, int32_t *h,
+                int64_t *offset, int8_t *code, int32_t *parent, int32_t *order, int32_t *ninfer);
+
+/* Drops every spin with code != 0 and its couplers WITHOUT folding (the
+ * tree step has folded already); colours inherited.  Same outputs as or_reduce. */
+int or_compact(int32_t n, const int32_t *row_ptr, const int32_t *col, const int32_t *val,
+               const int32_t *h, int64_t offset, const int32_t *colour, const int8_t *code,
+               int32_t *n_out, int32_t *row_ptr_out, int32_t *col_out, int32_t *val_out,
+               int32_t *h_out, int64_t *offset_out, int32_t *colour_out, int32_t *old_of_new);
+
 /* Multi-start SPVAR (Alg. 2) with SA as the sampler. */
 typedef struct or_params {
     int32_t num_starts;
@@ -126,6 +147,7 @@ typedef struct or_params {
     int32_t canon;                 /* -1: when every h is 0; 0: never; 1: always */
     int32_t start0;                /* start st uses counter word start0 + st */
     int32_t boost;                 /* 1: component boosting of the solving sample (Sec. II.C) */
+    int32_t tree;                  /* 1: tree pre-processing after every SPVAR reduction (Sec. II.C) */
 } or_params;
 
 /* Outputs (caller-allocated, P = max_fix_phases + 1, Smax = max sample size):

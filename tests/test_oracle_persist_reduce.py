@@ -261,3 +261,69 @@ def test_solve_with_boost_only_improves_the_solving_phase():
         assert np.all(np.diff(sb) >= 0) and sb[0] <= sa.min()
         assert b.best_e[st] <= a.best_e[st]
         assert _E(inst, b.best_state[st])[0] == b.best_e[st]
+
+
+def _tree_reconstruct(full_n, free_idx, s_free, code, parent, order, J_of):
+    """Full assignment from a reduced one: fixed codes, free values, inferred last-first."""
+    s = np.zeros(full_n, np.int64)
+    s[code == 1], s[code == -1] = 1, -1
+    s[free_idx] = s_free
+    for i in order[::-1]:
+        s[i] = -np.sign(J_of(i, parent[i])) * s[parent[i]]
+    return s
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3, 4])
+def test_tree_preprocessing_is_exact(seed):
+    """Every reduced assignment lifts to a full one with E_full = E_reduced + offset',
+    and the minimum is preserved (brute force), on sparse problems with trees."""
+    g = np.random.default_rng(seed)
+    n = 12
+    inst = I.random_graph(n, 13 + seed, 100 + seed, jmax=4, hmax=3)
+    if seed == 4:
+        inst.h[:] = 0  # zero bias: only inference and arbitrary degree-0 fixings
+    p = _csr(inst)
+    h2, off2, code, parent, order = O.tree(p)
+    assert len(order) == int((code == 2).sum())
+    p2 = O.Csr(p.n, p.row_ptr, p.col, p.val, h2, off2, p.scale)
+    red, _, oon = O.compact(p2, code)
+    assert red.n == int((code == 0).sum())
+    J = {(int(a), int(b)): int(v) for a, b, v in zip(inst.ei, inst.ej, inst.J)}
+    J_of = lambda i, j: J.get((i, j), J.get((j, i)))
+    allS = np.array(list(itertools.product([-1, 1], repeat=n)), np.int64)
+    e_min = _E(inst, allS).min()
+    if red.n:
+        sub = np.array(list(itertools.product([-1, 1], repeat=red.n)), np.int64)
+        e_red = _E_csr(red, sub)
+    else:
+        sub = np.zeros((1, 0), np.int64)
+        e_red = np.array([red.offset])
+    for k in range(len(sub)):
+        s = _tree_reconstruct(n, oon, sub[k], code, parent, order, J_of)
+        assert _E(inst, s)[0] == e_red[k]
+    assert e_red.min() == e_min
+
+
+def test_tree_eliminates_whole_trees():
+    # a path 0-1-2-3 and a star centred at 4 with leaves 5,6,7: everything goes
+    ei = np.array([0, 1, 2, 4, 4, 4], np.int32)
+    ej = np.array([1, 2, 3, 5, 6, 7], np.int32)
+    inst = I.Instance("forest", 8, ei, ej, np.array([2, -3, 1, 1, -1, 2], np.int32), np.array([1, 0, 0, -1, 0, 0, 0, 0], np.int32))
+    h2, off2, code, parent, order = O.tree(_csr(inst))
+    assert np.all(code != 0)
+    allS = np.array(list(itertools.product([-1, 1], repeat=8)), np.int64)
+    assert off2 == _E(inst, allS).min()
+
+
+def test_solve_with_tree_states_are_consistent():
+    inst = I.random_graph(40, 48, 17, jmax=3, hmax=2)
+    p = _csr(inst)
+    thr = O.thresholds(O.beta_geometric(60, 0.1, 3.0), O.dmax(p), 1)
+    r = O.solve(p, thr, seed=4, num_starts=3, fixing_sample_size=32, solving_sample_size=24,
+                elite_threshold=0.2, tree=True)
+    r0 = O.solve(p, thr, seed=4, num_starts=3, fixing_sample_size=32, solving_sample_size=24,
+                 elite_threshold=0.2)
+    for st in range(3):
+        assert _E(inst, r.best_state[st])[0] == r.best_e[st]
+        assert np.array_equal(r.energies[st, 0], r0.energies[st, 0])   # the first sample is untouched
+        assert r.nfree[st, 1] <= r0.nfree[st, 1]                        # trees only shrink the problem
