@@ -225,6 +225,9 @@ typedef struct spvar_params {
     int32_t component_boost;     /* 1: disconnected-component boosting of the solving sample (Sec. II.C):
                                     each connected component's partial samples are sorted by partial
                                     energy and merged rank by rank; recorded energies are the merged ones */
+    int32_t tree_preprocess;     /* 1: exact tree elimination after every SPVAR reduction (Sec. II.C):
+                                    degree-0/1 spins fixed by their bias or inferred from their neighbour,
+                                    recursively; inferred spins are restored in best_state */
 } spvar_params;
 
 #define SPVAR_SWEEP_AUTO 0    /* register kernel when eligible, else general */

@@ -15,7 +15,7 @@
 namespace spvar {
 
 __device__ void reduce_core(const DevProb *S, DevProb *D, const int8_t *fixed, int32_t *old_of_new,
-                            int32_t *scratch)
+                            int32_t *scratch, bool fold)
 {
     __shared__ int s_warp[32];
     __shared__ unsigned long long s_off;
@@ -59,14 +59,14 @@ __device__ void reduce_core(const DevProb *S, DevProb *D, const int8_t *fixed, i
             const int j = S->col[p];
             const int vj = fixed[j];
             if (vi) {
-                if (vj && j > i) off_part += (long long)S->val[p] * vi * vj;
+                if (fold && vj && j > i) off_part += (long long)S->val[p] * vi * vj;
             } else {
-                if (vj) hf += (long long)S->val[p] * vj;
-                else ++nfree;
+                if (!vj) ++nfree;
+                else if (fold) hf += (long long)S->val[p] * vj;
             }
         }
         if (vi) {
-            off_part += (long long)S->h[i] * vi;
+            if (fold) off_part += (long long)S->h[i] * vi;
         } else {
             const int a = new_of_old[i];
             D->h[a] = (int32_t)hf;
@@ -163,6 +163,97 @@ __device__ void reduce_core(const DevProb *S, DevProb *D, const int8_t *fixed, i
     __syncthreads();
 }
 
+// Tree pre-processing of P in place (Sec. II.C), rounds as in the oracle:
+// every active spin of active degree 0, and of active degree 1 except the
+// lower-index end of an isolated coupler, is eliminated at once.  Writes
+// code[i] (0 kept, +1/-1 fixed, 2 inferred), folds into P->h / P->offset,
+// records fixings in fmap and inferences in the slot's log (original indices
+// through orig).  deg: scratch [n].  One CTA; contains __syncthreads.
+__device__ void tree_core(DevProb *P, int8_t *code, int32_t *scratch, int8_t *fmap, const int32_t *orig,
+                          int32_t *log_child, int32_t *log_parent, int8_t *log_sigma, int32_t *nlog)
+{
+    __shared__ int s_any;
+    __shared__ unsigned long long s_off;
+    __shared__ int s_log;
+    const int n = P->n, tid = threadIdx.x, B = blockDim.x;
+    int32_t *deg = scratch;          // active degree (pass 1)
+    int32_t *nb = scratch + P->cap_n; // this round's pick: -2 none, -1 degree 0, else the neighbour
+    for (int i = tid; i < n; i += B) code[i] = 0;
+    if (tid == 0) {
+        s_off = 0ull;
+        s_log = *nlog;
+    }
+    __syncthreads();
+    for (;;) {
+        // pass 1: active degrees
+        for (int i = tid; i < n; i += B) {
+            int d = 0;
+            if (code[i] == 0)
+                for (int p = P->row_ptr[i]; p < P->row_ptr[i + 1]; ++p) d += code[P->col[p]] == 0;
+            deg[i] = d;
+        }
+        if (tid == 0) s_any = 0;
+        __syncthreads();
+        // pass 2: this round's leaves (codes are not modified in this pass)
+        for (int i = tid; i < n; i += B) {
+            int pick = -2;
+            if (code[i] == 0 && deg[i] == 0) {
+                pick = -1;
+            } else if (code[i] == 0 && deg[i] == 1) {
+                int j = -1;
+                for (int p = P->row_ptr[i]; p < P->row_ptr[i + 1]; ++p)
+                    if (code[P->col[p]] == 0) j = P->col[p];
+                if (!(deg[j] == 1 && i < j)) pick = j;  // isolated coupler: the higher end goes first
+            }
+            nb[i] = pick;
+            if (pick != -2) s_any = 1;
+        }
+        __syncthreads();
+        if (!s_any) break;
+        // pass 3: eliminate; a picked spin's neighbour is never picked, so the
+        // updates of a shared neighbour only add up
+        long long off = 0;
+        for (int i = tid; i < n; i += B) {
+            const int j = nb[i];
+            if (j == -2) continue;
+            const int h = P->h[i];
+            if (j == -1) {
+                const int v = h > 0 ? -1 : 1;
+                off += (long long)h * v;
+                code[i] = (int8_t)v;
+                fmap[orig[i]] = (int8_t)v;
+                continue;
+            }
+            int J = 0;
+            for (int p = P->row_ptr[i]; p < P->row_ptr[i + 1]; ++p)
+                if (P->col[p] == j) J = P->val[p];
+            if (abs(J) <= abs(h)) {
+                const int v = h > 0 ? -1 : 1;
+                off += (long long)h * v;
+                atomicAdd(&P->h[j], J * v);
+                code[i] = (int8_t)v;
+                fmap[orig[i]] = (int8_t)v;
+            } else {
+                const int sJ = J > 0 ? 1 : -1;
+                off -= abs(J);
+                atomicAdd(&P->h[j], -sJ * h);
+                code[i] = 2;
+                const int q = atomicAdd(&s_log, 1);
+                log_child[q] = orig[i];
+                log_parent[q] = orig[j];
+                log_sigma[q] = (int8_t)(-sJ);
+            }
+        }
+        atomicAdd(&s_off, (unsigned long long)off);
+        __syncthreads();
+    }
+    if (tid == 0) {
+        P->offset += (long long)s_off;
+        *nlog = s_log;
+    }
+    __syncthreads();
+}
+
 namespace {
 
 // ---------------------------------------------------------------- standalone
@@ -210,6 +301,7 @@ __global__ void __launch_bounds__(256) k_slots_init(Slot *slots, SolveConsts C)
         s.phase = 0;
         s.fix_done = 0;
         s.nfixed = 0;
+        s.nlog = 0;
         *s.best_e = LLONG_MAX;
         *s.nphases = 0;
     }
@@ -295,6 +387,13 @@ __global__ void __launch_bounds__(kBigBlock) k_elite_slots(Slot *slots, SolveCon
     const uint32_t *row = s.spins + (size_t)rbest * s.W0;
     for (int a = threadIdx.x; a < n; a += blockDim.x)
         s.best_state[orig[a]] = ((row[a >> 5] >> (a & 31)) & 1u) ? 1 : -1;
+    if (C.tree) {
+        // spins removed by tree inference, latest first: s_child = sigma s_parent
+        __syncthreads();
+        if (threadIdx.x == 0)
+            for (int q = s.nlog - 1; q >= 0; --q)
+                s.best_state[s.log_child[q]] = (int8_t)(s.log_sigma[q] * s.best_state[s.log_parent[q]]);
+    }
 }
 
 __global__ void __launch_bounds__(kCountBlock) k_count_slots(Slot *slots, SolveConsts C)
@@ -337,14 +436,29 @@ __global__ void __launch_bounds__(kBigBlock) k_reduce_slots(Slot *slots, SolveCo
     __syncthreads();
     DevProb *D = s.buf[s.next];
     reduce_core(P, D, s.fixed, s.old_of_new, s.scratch);
-    const int m = D->n;
+    int m = D->n;
     int32_t *orig2 = s.orig[s.ocur ^ 1];
     for (int a = threadIdx.x; a < m; a += blockDim.x) orig2[a] = orig[s.old_of_new[a]];
     __syncthreads();
+    DevProb *cur2 = D;
+    int next2 = s.next ^ 1, ocur2 = s.ocur ^ 1;
+    if (C.tree && m > 0) {
+        // exact tree reduction of the new problem (in place), then drop what it removed
+        tree_core(D, s.fixed, s.scratch, s.fmap, orig2, s.log_child, s.log_parent, s.log_sigma, &s.nlog);
+        DevProb *E2 = s.buf[s.next ^ 1];  // the problem sampled this phase is no longer needed
+        reduce_core(D, E2, s.fixed, s.old_of_new, s.scratch, false);
+        m = E2->n;
+        int32_t *orig3 = s.orig[s.ocur];  // the start's map before this phase is no longer needed
+        for (int a = threadIdx.x; a < m; a += blockDim.x) orig3[a] = orig2[s.old_of_new[a]];
+        __syncthreads();
+        cur2 = E2;
+        next2 = s.next;
+        ocur2 = s.ocur;
+    }
     if (threadIdx.x == 0) {
-        s.cur = D;
-        s.next ^= 1;
-        s.ocur ^= 1;
+        s.cur = cur2;
+        s.next = next2;
+        s.ocur = ocur2;
         s.phase += 1;
         s.fix_done += 1;
         *s.nphases = s.phase;

@@ -132,7 +132,9 @@ __device__ __forceinline__ void count_core(const DevProb *P, const uint32_t *spi
 // Fold the fixed spins into h and the offset and compact the free spins into
 // dst (same capacities as src).  old_of_new [n], scratch [2 * cap_n].
 // blockDim.x == kBigBlock, one CTA per reduction.
+// fold = false: spins with fixed[i] != 0 are only dropped (their values were
+// already folded into h and the offset, e.g. by the tree step).
 __device__ void reduce_core(const DevProb *src, DevProb *dst, const int8_t *fixed,
-                            int32_t *old_of_new, int32_t *scratch);
+                            int32_t *old_of_new, int32_t *scratch, bool fold = true);
 
 }  // namespace spvar

@@ -313,7 +313,7 @@ int spvar_plan_create(const spvar_problem *const *problems, int32_t nproblems,
         !(p.elite_threshold > 0.0) || !(p.elite_threshold <= 1.0) || !(p.beta0 > 0.0) || !(p.beta1 > 0.0) ||
         p.canon < -1 || p.canon > 1 || (p.form != SPVAR_FORM_BATCHED && p.form != SPVAR_FORM_PLAIN) ||
         p.replicas_per_block < 0 || (p.replicas_per_block % 4) != 0 || p.sweep_kernel < 0 ||
-        p.sweep_kernel > 4 || p.start_offset < 0 || p.component_boost < 0 || p.component_boost > 1 || (p.sweep_block != 0 && p.sweep_block != 128 && p.sweep_block != 256 &&
+        p.sweep_kernel > 4 || p.start_offset < 0 || p.component_boost < 0 || p.component_boost > 1 || p.tree_preprocess < 0 || p.tree_preprocess > 1 || (p.sweep_block != 0 && p.sweep_block != 128 && p.sweep_block != 256 &&
                                p.sweep_block != 512 && p.sweep_block != 1024))
         return SPVAR_EINVAL;
     const int Smax = std::max(p.fixing_sample_size, p.solving_sample_size);
@@ -363,6 +363,7 @@ int spvar_plan_create(const spvar_problem *const *problems, int32_t nproblems,
     C.nslots = nslots;
     C.boost = p.component_boost;
     C.max_n0 = pl->max_n0;
+    C.tree = p.tree_preprocess;
     pl->iters_max = (p.iterate ? p.max_fix_phases : 1) + (p.solving_sample_size > 0 ? 1 : 0);
 
     // workspace layout
@@ -398,6 +399,7 @@ int spvar_plan_create(const spvar_problem *const *problems, int32_t nproblems,
         b += align256(4 * (size_t)n0);      // old_of_new
         b += align256(8 * (size_t)H.cap_n); // scratch
         b += boost_slot_bytes(p.component_boost, n0, Smax, ceil_div(n0, 32));
+        b += tree_slot_bytes(p.tree_preprocess, n0);
         o_slot[s] = take(b);
     }
     pl->ws_bytes = off;
@@ -486,6 +488,7 @@ int spvar_plan_create(const spvar_problem *const *problems, int32_t nproblems,
         S.scratch = (int32_t *)carve(8 * (size_t)H.cap_n);
         if (p.component_boost)
             boost_slot_carve(S, carve(boost_slot_bytes(1, n0, Smax, S.W0)), n0, Smax, S.W0);
+        if (p.tree_preprocess) tree_slot_carve(S, carve(tree_slot_bytes(1, n0)), n0);
         S.rec_e = pl->d_rec_e + (size_t)s * P_slots * Smax;
         S.rec_count = pl->d_rec_count + (size_t)s * P_slots;
         S.rec_nfree = pl->d_rec_nfree + (size_t)s * P_slots;

@@ -133,6 +133,7 @@ size_t request_bytes(const spvar_server *S, const HostProblem &hp)
            a256(4 * (size_t)n0) + a256(8 * (size_t)n0);
     per += a256(8 * (size_t)S->P * S->Smax) + 2 * a256(4 * (size_t)S->P) + a256(4) + a256(8) + 2 * a256((size_t)n0);
     per += boost_slot_bytes(S->cfg.params.component_boost, n0, S->Smax, ceil_div(n0, 32));
+    per += tree_slot_bytes(S->cfg.params.tree_preprocess, n0);
     return pb + (size_t)S->ns * per;
 }
 
@@ -187,6 +188,7 @@ int place_request(spvar_server *S, Request &R)
         s.best_state = (int8_t *)take((size_t)n0);
         if (S->cfg.params.component_boost)
             boost_slot_carve(s, take(boost_slot_bytes(1, n0, S->Smax, s.W0)), n0, S->Smax, s.W0);
+        if (S->cfg.params.tree_preprocess) tree_slot_carve(s, take(tree_slot_bytes(1, n0)), n0);
         s.mode = kDone;  // activated by the init kernel below
     }
     // the header copies must outlive the asynchronous uploads: synchronise here
@@ -354,7 +356,7 @@ int spvar_server_create(const spvar_server_config *cfg, spvar_server **out)
     if (p.num_starts < 1 || p.fixing_sample_size < 1 || p.solving_sample_size < 0 || p.num_sweeps < 0 ||
         p.max_fix_phases < 1 || p.fix_num <= 0 || p.fix_den <= 0 || p.fix_num > p.fix_den ||
         !(p.elite_threshold > 0.0) || !(p.elite_threshold <= 1.0) || !(p.beta0 > 0.0) || !(p.beta1 > 0.0) ||
-        p.canon < -1 || p.canon > 1 || p.start_offset < 0 || p.component_boost < 0 || p.component_boost > 1 || cfg->max_n < 1 || cfg->max_nnz < 0 ||
+        p.canon < -1 || p.canon > 1 || p.start_offset < 0 || p.component_boost < 0 || p.component_boost > 1 || p.tree_preprocess < 0 || p.tree_preprocess > 1 || cfg->max_n < 1 || cfg->max_nnz < 0 ||
         cfg->max_degree < 1 || cfg->max_dmax < 0 || cfg->energy_scale < 1 || cfg->max_requests < 1 ||
         cfg->budget_bytes == 0)
         return SPVAR_EINVAL;
@@ -435,6 +437,7 @@ int spvar_server_create(const spvar_server_config *cfg, spvar_server **out)
     E.C.nslots = S->nslots;
     E.C.boost = p.component_boost;
     E.C.max_n0 = cfg->max_n;
+    E.C.tree = p.tree_preprocess;
     int Q = p.replicas_per_block > 0 ? p.replicas_per_block / 4 : 1;
     const int blk = p.sweep_block ? p.sweep_block : 512;
     E.shape = SweepShape{0, blk, Q, 1, 0, 0};

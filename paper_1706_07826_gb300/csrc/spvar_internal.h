@@ -124,15 +124,34 @@ struct Slot {
     int32_t *part;             // [Smax][n0] twice the partial energy of sample r on component c
     int32_t *perm;             // [n0][Smax] sample of rank r on component c
     uint32_t *spins2;          // [Smax][W0] merged sample
-    int32_t ncomp, pad1;
+    int32_t ncomp, nlog;
+    // tree pre-processing (Sec. II.C): inferred spins s_child = sigma s_parent, in
+    // elimination order (original indices); null when off
+    int32_t *log_child;        // [n0]
+    int32_t *log_parent;       // [n0]
+    int8_t *log_sigma;         // [n0]
 };
 
 struct SolveConsts {
     int32_t S_fix, S_solve, k_fix, iterate;
     int32_t max_fix, canon, fix_num, fix_den;
     int32_t P, Smax, Q, nslots;
-    int32_t boost, max_n0, pad0, pad1;
+    int32_t boost, max_n0, tree, pad1;
 };
+// Bytes of the tree-inference log of one slot (0 when the tree step is off).
+inline size_t tree_slot_bytes(int tree, int n0)
+{
+    if (!tree) return 0;
+    auto a = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    return 2 * a(4 * (size_t)n0) + a((size_t)n0);
+}
+inline void tree_slot_carve(Slot &s, char *base, int n0)
+{
+    auto a = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    s.log_child = (int32_t *)base;
+    s.log_parent = (int32_t *)(base + a(4 * (size_t)n0));
+    s.log_sigma = (int8_t *)(base + 2 * a(4 * (size_t)n0));
+}
 // Bytes of the boosting buffers of one slot (0 when boosting is off).
 inline size_t boost_slot_bytes(int boost, int n0, int Smax, int W0)
 {

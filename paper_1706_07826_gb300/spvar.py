@@ -44,7 +44,7 @@ class Params(ctypes.Structure):
                 ("elite_threshold", ctypes.c_double), ("fix_num", i32), ("fix_den", i32),
                 ("iterate", i32), ("max_fix_phases", i32), ("canon", i32), ("form", i32),
                 ("replicas_per_block", i32), ("sweep_kernel", i32), ("sweep_block", i32), ("start_offset", i32),
-                ("component_boost", i32)]
+                ("component_boost", i32), ("tree_preprocess", i32)]
 
 
 class ServerConfig(ctypes.Structure):
@@ -299,10 +299,10 @@ def reduce_noalloc(problem, fixed, row_ptr, col, val, h, offset, old_of_new, n_o
 def make_params(num_starts=1, fixing_sample_size=100, solving_sample_size=100, num_sweeps=1000, beta0=0.1,
                 beta1=3.0, elite_threshold=0.1, fix_num=1, fix_den=1, iterate=False, max_fix_phases=1, canon=-1,
                 form=FORM_BATCHED, replicas_per_block=0, sweep_kernel=SWEEP_AUTO, sweep_block=0, start_offset=0,
-                component_boost=False):
+                component_boost=False, tree_preprocess=False):
     return Params(num_starts, fixing_sample_size, solving_sample_size, num_sweeps, beta0, beta1, elite_threshold,
                   fix_num, fix_den, 1 if iterate else 0, max_fix_phases, canon, form, replicas_per_block,
-                  sweep_kernel, sweep_block, start_offset, 1 if component_boost else 0)
+                  sweep_kernel, sweep_block, start_offset, 1 if component_boost else 0, 1 if tree_preprocess else 0)
 
 
 @dataclasses.dataclass

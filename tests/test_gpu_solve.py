@@ -176,3 +176,30 @@ def test_component_boost_parity(cuda_lib, form, name, make, T, starts, Sf, Ss, e
     prm = spvar.make_params(num_starts=starts, fixing_sample_size=Sf, solving_sample_size=Ss, num_sweeps=T,
                             elite_threshold=elite, fix_num=tau[0], fix_den=tau[1], form=form, component_boost=True)
     _check(spvar.solve(gpu_problem(inst), prm, 8), ref, starts, 2, inst.n)
+
+
+TCASES = [
+    ("random_trees", lambda: I.random_graph(40, 48, 17, jmax=3, hmax=2), 60, 3, 32, 24, 0.2, (1, 1), False, 1),
+    ("random_zero_bias", lambda: (lambda x: (setattr(x, "h", np.zeros(x.n, np.int32)), x)[1])(
+        I.random_graph(50, 60, 23, jmax=2, hmax=0)), 50, 2, 40, 20, 0.25, (1, 1), False, 1),
+    ("random_5_components_boost", lambda: I.random_graph(60, 70, 9, jmax=3, hmax=1), 40, 3, 64, 40, 0.2, (3, 4),
+     True, 1),
+    ("cubic_L4_ispvar_tree", lambda: I.cubic3d(4, 32), 60, 2, 64, 0, 0.1, (3, 4), False, 64),
+]
+
+
+@pytest.mark.parametrize("form", [0, 1], ids=["batched", "plain"])
+@pytest.mark.parametrize("name,make,T,starts,Sf,Ss,elite,tau,boost,mf", TCASES, ids=[c[0] for c in TCASES])
+def test_tree_preprocess_parity(cuda_lib, form, name, make, T, starts, Sf, Ss, elite, tau, boost, mf):
+    """Sec. II.C tree pre-processing after SPVAR reductions: identical to the oracle
+    (fix maps, recorded energies, best states with inferred spins restored)."""
+    from paper_1706_07826_gb300 import spvar
+    inst = make()
+    iterate = mf > 1
+    ref = _oracle_solve(inst, T, 6, num_starts=starts, fixing_sample_size=Sf, solving_sample_size=Ss,
+                        elite_threshold=elite, fix_num=tau[0], fix_den=tau[1], boost=boost, tree=True,
+                        iterate=iterate, max_fix_phases=mf)
+    prm = spvar.make_params(num_starts=starts, fixing_sample_size=Sf, solving_sample_size=Ss, num_sweeps=T,
+                            elite_threshold=elite, fix_num=tau[0], fix_den=tau[1], form=form,
+                            component_boost=boost, tree_preprocess=True, iterate=iterate, max_fix_phases=mf)
+    _check(spvar.solve(gpu_problem(inst), prm, 6), ref, starts, mf + 1, inst.n)
