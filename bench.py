@@ -288,6 +288,57 @@ def measure_small_configs(spvar, torch):
     return out
 
 
+def measure_method_variants(spvar, torch):
+    """Sec. III.D-style comparison on a 3D +-J L=10 instance (N = 1000) with the
+    paper's 3D parameters (Table II: elite 0.2, 20 starts, 500 samples per
+    start), 1000 sweeps: plain SA (500 samples per start, no fixing) against
+    Multi-start SPVAR, + component boosting, + tree pre-processing, + both.
+    Success = a start's best energy reaches the best energy any variant found."""
+    from paper_1706_07826_gb300 import instances as I
+    inst = I.cubic3d(10, 1600)
+    prob = spvar.Problem.from_instance(inst)
+    T, starts = 1000, 20
+    beta = spvar.beta_geometric(T, 0.1, 3.0)
+    thr = spvar.thresholds(beta, prob.info().dmax, 1)
+    thr_d = spvar.thresholds_device(thr)
+    out = {}
+    # plain SA: 500 independent samples per start
+    bests, ms_sum, att = [], 0.0, 0
+    for st in range(starts):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        _, e = spvar.sample(prob, thr_d, thr.shape[1], T, 500, 1601, st, 0)
+        b.record()
+        torch.cuda.synchronize()
+        ms_sum += a.elapsed_time(b)
+        att += 500 * inst.n * T
+        bests.append(int(e.min().item()))
+    out["sa"] = {"best": bests, "attempts_per_s": att / (ms_sum / 1000.0)}
+    for name, kw in (("spvar", {}), ("spvar_boost", dict(component_boost=True)),
+                     ("spvar_tree", dict(tree_preprocess=True)),
+                     ("spvar_boost_tree", dict(component_boost=True, tree_preprocess=True))):
+        plan = spvar.Plan([prob], spvar.make_params(num_starts=starts, fixing_sample_size=250, solving_sample_size=250,
+                                                    num_sweeps=T, elite_threshold=0.2, **kw))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        o = plan.run(1601, device=False)
+        b.record()
+        torch.cuda.synchronize()
+        att, _ = plan.stats()
+        out[name] = {"best": [int(x) for x in o.best_energy], "attempts_per_s": att / (a.elapsed_time(b) / 1000.0),
+                     "free_spins_solving_phase_mean": float(np.mean(o.nfree[:, 1]))}
+        plan.close()
+    e_best = min(min(v["best"]) for v in out.values())
+    for v in out.values():
+        v["p_success"] = float(np.mean([x == e_best for x in v["best"]]))
+        v["best_mean"] = float(np.mean(v["best"]))
+        del v["best"]
+    out["e_best_found"] = e_best
+    out["config"] = ("3D +-J L=10 (N=1000, seed 1600), 20 starts x (250 fixing + 250 solving) samples, 1000 sweeps, "
+                     "elite 0.2, fixing threshold 1, reference-spin canonicalisation; SA = 500 samples per start")
+    return out
+
+
 def measure_serving(spvar, count=12):
     """c5: Poisson arrivals of 3D +-J instances, L in 8..20, through the
     continuous-batching server (background engine): p50/p99 latency and
@@ -425,6 +476,7 @@ def gpu_arm(args, rank, world):
     extra = {}
     if rank == 0 and world == 1 and not args.no_extra:
         extra.update(measure_small_configs(spvar, torch))
+        extra["method_variants_3d_L10"] = measure_method_variants(spvar, torch)
         extra["uneven_batch"] = measure_uneven(spvar, torch, flush)
         extra["serving"] = measure_serving(spvar)
 
