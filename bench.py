@@ -289,15 +289,15 @@ def measure_small_configs(spvar, torch):
 
 
 def measure_method_variants(spvar, torch):
-    """Sec. III.D-style comparison on a 3D +-J L=10 instance (N = 1000) with the
-    paper's 3D parameters (Table II: elite 0.2, 20 starts, 500 samples per
-    start), 1000 sweeps: plain SA (500 samples per start, no fixing) against
-    Multi-start SPVAR, + component boosting, + tree pre-processing, + both.
-    Success = a start's best energy reaches the best energy any variant found."""
+    """Sec. III.D-style comparison on a 3D +-J L=10 instance (N = 1000), 20
+    starts x 500 samples per start as in Table II, 5000 sweeps, elite 0.1:
+    plain SA (500 samples per start, no fixing) against Multi-start SPVAR,
+    + component boosting, + tree pre-processing, + both.  Success = a start's
+    best energy reaches the best energy any variant found."""
     from paper_1706_07826_gb300 import instances as I
     inst = I.cubic3d(10, 1600)
     prob = spvar.Problem.from_instance(inst)
-    T, starts = 1000, 20
+    T, starts = 5000, 20
     beta = spvar.beta_geometric(T, 0.1, 3.0)
     thr = spvar.thresholds(beta, prob.info().dmax, 1)
     thr_d = spvar.thresholds_device(thr)
@@ -318,7 +318,7 @@ def measure_method_variants(spvar, torch):
                      ("spvar_tree", dict(tree_preprocess=True)),
                      ("spvar_boost_tree", dict(component_boost=True, tree_preprocess=True))):
         plan = spvar.Plan([prob], spvar.make_params(num_starts=starts, fixing_sample_size=250, solving_sample_size=250,
-                                                    num_sweeps=T, elite_threshold=0.2, **kw))
+                                                    num_sweeps=T, elite_threshold=0.1, **kw))
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record()
         o = plan.run(1601, device=False)
@@ -334,8 +334,8 @@ def measure_method_variants(spvar, torch):
         v["best_mean"] = float(np.mean(v["best"]))
         del v["best"]
     out["e_best_found"] = e_best
-    out["config"] = ("3D +-J L=10 (N=1000, seed 1600), 20 starts x (250 fixing + 250 solving) samples, 1000 sweeps, "
-                     "elite 0.2, fixing threshold 1, reference-spin canonicalisation; SA = 500 samples per start")
+    out["config"] = ("3D +-J L=10 (N=1000, seed 1600), 20 starts x (250 fixing + 250 solving) samples, 5000 sweeps, "
+                     "elite 0.1, fixing threshold 1, reference-spin canonicalisation; SA = 500 samples per start")
     return out
 
 
