@@ -146,6 +146,18 @@ int spvar_sample(const spvar_problem *p, int32_t num_sweeps, const uint32_t *thr
                  int32_t thr_stride, int32_t num_samples, uint64_t seed, uint32_t start,
                  uint32_t phase, uint32_t *spins, int64_t *energies, void *stream);
 
+/* Checkpoint / resume of an anneal: runs sweeps sweep_begin .. sweep_end-1
+ * of the same sample, starting from init_spins (device [num_samples][ceil(n/32)],
+ * the spins a previous range wrote; NULL = the initial state, only with
+ * sweep_begin = 0).  Because every random word is keyed by the absolute sweep
+ * index, any split of [0, T) into consecutive ranges gives exactly the result
+ * of one spvar_sample over T sweeps.  thr must hold rows up to sweep_end - 1;
+ * init_spins must not alias spins.  Errors as spvar_sample, EINVAL for bad ranges. */
+int spvar_sample_range(const spvar_problem *p, int32_t sweep_begin, int32_t sweep_end,
+                       const uint32_t *thr, int32_t thr_stride, int32_t num_samples, uint64_t seed,
+                       uint32_t start, uint32_t phase, const uint32_t *init_spins, uint32_t *spins,
+                       int64_t *energies, void *stream);
+
 /* ------------------------------------------------------------------ */
 /* Persistence (Alg. 1: elite sample, mean value, fixing rule)          */
 /* ------------------------------------------------------------------ */

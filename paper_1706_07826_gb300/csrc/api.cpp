@@ -401,10 +401,22 @@ int spvar_sample(const spvar_problem *p, int32_t num_sweeps, const uint32_t *thr
                  int32_t num_samples, uint64_t seed, uint32_t start, uint32_t phase, uint32_t *spins,
                  int64_t *energies, void *stream)
 {
+    return spvar_sample_range(p, 0, num_sweeps, thr, thr_stride, num_samples, seed, start, phase, nullptr, spins,
+                              energies, stream);
+}
+
+int spvar_sample_range(const spvar_problem *p, int32_t sweep_begin, int32_t sweep_end, const uint32_t *thr,
+                       int32_t thr_stride, int32_t num_samples, uint64_t seed, uint32_t start, uint32_t phase,
+                       const uint32_t *init_spins, uint32_t *spins, int64_t *energies, void *stream)
+{
     if (!p) return SPVAR_EINVAL;
     const Problem *P = reinterpret_cast<const Problem *>(p);
     const DevProb &H = P->hdr;
-    if (num_sweeps < 0 || num_samples < 0 || phase > SPVAR_MAX_PHASE) return SPVAR_EINVAL;
+    const int32_t num_sweeps = sweep_end;
+    if (sweep_begin < 0 || sweep_end < sweep_begin || num_samples < 0 || phase > SPVAR_MAX_PHASE)
+        return SPVAR_EINVAL;
+    if (sweep_begin > 0 && !init_spins) return SPVAR_EINVAL;
+    if (init_spins && init_spins == spins) return SPVAR_EINVAL;  // rows are read while others are written
     if (num_sweeps > SPVAR_MAX_SWEEPS || num_samples > SPVAR_MAX_SAMPLES) return SPVAR_ELIMIT;
     if (num_samples == 0) return SPVAR_OK;
     if ((num_sweeps > 0 && !thr) || thr_stride < H.dmax + 1 || !energies || (H.n > 0 && !spins))
@@ -440,6 +452,8 @@ int spvar_sample(const spvar_problem *p, int32_t num_sweeps, const uint32_t *thr
     L.single.W = ceil_div(std::max(H.n, 0), 32);
     L.single.start = start;
     L.single.phase = phase;
+    L.single.init = init_spins;
+    L.single.t0 = sweep_begin;
     L.thr = thr;
     L.thr_stride = thr_stride;
     L.T = num_sweeps;

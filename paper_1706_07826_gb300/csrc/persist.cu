@@ -331,6 +331,9 @@ __global__ void __launch_bounds__(kBigBlock)
                 j.W = s.W0;
                 j.start = s.start;
                 j.phase = (uint32_t)s.phase;
+                j.init = nullptr;
+                j.t0 = 0;
+                j.pad = 0;
                 jobs[si] = j;
                 groups = ceil_div(ceil_div(S, 4), C.Q);
                 s.rec_count[s.phase] = S;

@@ -73,6 +73,8 @@ struct SweepJob {
     uint64_t seed;
     int32_t S, W;
     uint32_t start, phase;
+    const uint32_t *init;  // [S][W] states to continue from, or null: the initial state
+    int32_t t0, pad;       // first sweep to run (the launch runs sweeps t0 .. T-1)
 };
 
 // A unit of sweep work: quads [quad0, quad0 + nq) of job `job`.

@@ -136,20 +136,15 @@ __device__ void run_item(const SweepLaunch &L, const SweepJob &job, int quad0, i
     for (int c = tid; c <= ncol; c += B) s_cptr[c] = P->cptr[c];
     for (int x = tid; x < 4 * nq; x += B) e2[x] = 0;
 
-    // initial state: s_i = +1 iff the top bit of the word at the init slot is set
-    for (int q = 0; q < nq; ++q) {
-        for (int p = tid; p < n; p += B) {
-            const int i = idx[p];
-            const uint4 r = philox4x32_10(
-                make_uint4((uint32_t)i, phase_hi | kInitSlot, (uint32_t)(quad0 + q), job.start), k0, k1);
-            sw[q * n + p] = (r.x >> 31) | ((r.y >> 31) << 8) | ((r.z >> 31) << 16) | ((r.w >> 31) << 24);
-        }
-    }
-    if (T > 0)
-        for (int d = tid; d < thr_w; d += B) thr_s[d] = L.thr[d];
+    // initial state (s_i = +1 iff the top bit of the word at the init slot is
+    // set), or the state a resumed sample continues from
+    init_spins(P, job, quad0, nq, sw, nullptr);
+    const int t0 = job.t0;
+    if (t0 < T)
+        for (int d = tid; d < thr_w; d += B) thr_s[(t0 & 1) * L.thr_stride + d] = L.thr[(size_t)t0 * L.thr_stride + d];
     __syncthreads();
 
-    for (int t = 0; t < T; ++t) {
+    for (int t = t0; t < T; ++t) {
         const uint32_t *th = thr_s + (t & 1) * L.thr_stride;
         const uint32_t ctr_y = phase_hi | (uint32_t)t;
         for (int c = 0; c < ncol; ++c) {

@@ -45,20 +45,37 @@ __device__ __forceinline__ void energy2(uint32_t own, uint32_t meta, const uint3
     }
 }
 
-// Initial state: s_i = +1 iff the top bit of the replica's word at the
-// initial-state slot is set.  Writes sw[q * n + p] for every quad and
-// position (and, if sw_comp != nullptr, the complemented copy).
+// Word of spin i (position p) for quad q.  A fresh sample starts from
+// s_i = +1 iff the top bit of the replica's random word at the initial-state
+// slot is set; a resumed one (job.init) continues from bit-packed rows
+// (replicas past the sample size read as 0 and are never output).
+__device__ __forceinline__ uint32_t start_word(const DevProb *P, const SweepJob &job, int quad, int p)
+{
+    const uint32_t i = (uint32_t)P->idx_of_pos[p];
+    if (job.init) {
+        uint32_t w = 0;
+#pragma unroll
+        for (int rr = 0; rr < 4; ++rr) {
+            const int r = 4 * quad + rr;
+            if (r < job.S) w |= ((job.init[(size_t)r * job.W + (i >> 5)] >> (i & 31)) & 1u) << (8 * rr);
+        }
+        return w;
+    }
+    const uint32_t k0 = (uint32_t)job.seed, k1 = (uint32_t)(job.seed >> 32);
+    const uint32_t y = (job.phase << kSweepBits) | kInitSlot;
+    const uint4 r = philox4x32_10(make_uint4(i, y, (uint32_t)quad, job.start), k0, k1);
+    return (r.x >> 31) | ((r.y >> 31) << 8) | ((r.z >> 31) << 16) | ((r.w >> 31) << 24);
+}
+
+// Writes sw[q * n + p] for every quad and position (and, if sw_comp !=
+// nullptr, the complemented copy).
 __device__ __forceinline__ void init_spins(const DevProb *P, const SweepJob &job, int quad0, int nq,
                                            uint32_t *sw, uint32_t *sw_comp)
 {
     const int n = P->n;
-    const uint32_t k0 = (uint32_t)job.seed, k1 = (uint32_t)(job.seed >> 32);
-    const uint32_t y = (job.phase << kSweepBits) | kInitSlot;
     for (int x = threadIdx.x; x < nq * n; x += blockDim.x) {
         const int q = x / n, p = x - q * n;
-        const uint4 r = philox4x32_10(make_uint4((uint32_t)P->idx_of_pos[p], y, (uint32_t)(quad0 + q), job.start),
-                                      k0, k1);
-        const uint32_t w = (r.x >> 31) | ((r.y >> 31) << 8) | ((r.z >> 31) << 16) | ((r.w >> 31) << 24);
+        const uint32_t w = start_word(P, job, quad0 + q, p);
         sw[x] = w;
         if (sw_comp) sw_comp[x] = w ^ 0x01010101u;
     }

@@ -124,9 +124,11 @@ __device__ void run_item_pm1(const SweepLaunch &L, const SweepJob &job, int quad
     for (int c = tid; c <= ncol; c += B) s_cptr[c] = P->cptr[c];
     init_spins(P, job, quad0, nq, sw, sw + S1);
     if (tid == 0) sw[2 * S1] = 0u;
-    // row 0 of the thresholds: trow[bias + e] = thr[0][2e], e = 1..bias
-    if (T > 0)
-        for (int e = tid + 1; e <= bias; e += B) trow[bias + e] = L.thr[2 * e];
+    // first row of the thresholds: trow[bias + e] = thr[t0][2e], e = 1..bias
+    const int t0 = job.t0;
+    if (t0 < T)
+        for (int e = tid + 1; e <= bias; e += B)
+            trow[(t0 & 1) * kRowWords + bias + e] = L.thr[(size_t)t0 * L.thr_stride + 2 * e];
     __syncthreads();
 
     SlotRegs<MAXD> s[NSLOT];
@@ -164,10 +166,10 @@ __device__ void run_item_pm1(const SweepLaunch &L, const SweepJob &job, int quad
             philox_setup(s[j], (uint32_t)P->idx_of_pos[p], (uint32_t)(quad0 + q), job.start, k0, k1);
             s[j].colour = c;
         }
-        u[j] = philox_slot(s[j], phase_hi, K);  // sweep 0
+        u[j] = philox_slot(s[j], phase_hi | (uint32_t)t0, K);  // first sweep
     }
 
-    for (int t = 0; t < T; ++t) {
+    for (int t = t0; t < T; ++t) {
         const uint32_t *th = trow + (t & 1) * kRowWords;
         const uint32_t y = phase_hi | (uint32_t)t;
         for (int c = 0; c < ncol; ++c) {

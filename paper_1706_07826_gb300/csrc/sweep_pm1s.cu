@@ -98,8 +98,10 @@ __device__ void run_item_pm1s(const SweepLaunch &L, const SweepJob &job, int qua
         }
         off[x] = o;
     }
-    if (T > 0)
-        for (int e = tid + 1; e <= bias; e += B) trow[bias + e] = L.thr[2 * e];
+    const int t0 = job.t0;
+    if (t0 < T)
+        for (int e = tid + 1; e <= bias; e += B)
+            trow[(t0 & 1) * kRowWordsS + bias + e] = L.thr[(size_t)t0 * L.thr_stride + 2 * e];
     __syncthreads();
 
     Keys10 K;
@@ -112,7 +114,7 @@ __device__ void run_item_pm1s(const SweepLaunch &L, const SweepJob &job, int qua
         }
     }
 
-    for (int t = 0; t < T; ++t) {
+    for (int t = t0; t < T; ++t) {
         const uint32_t *th = trow + (t & 1) * kRowWordsS;
         const uint32_t y = phase_hi | (uint32_t)t;
         for (int c = 0; c < ncol; ++c) {

@@ -124,18 +124,13 @@ __device__ void run_item_pm1w(const SweepLaunch &L, const SweepJob &job, int qua
         uint32_t *sw = regions + warp * region;
         uint32_t *myrows = rows + warp * 2 * kRowW;
         const uint32_t q = (uint32_t)(quad0 + warp);
-        // initial state of this quad
-        {
-            const uint32_t y0 = phase_hi | kInitSlot;
-            for (int p = lane; p < n; p += 32) {
-                const uint4 r =
-                    philox4x32_10(make_uint4((uint32_t)P->idx_of_pos[p], y0, q, job.start), k0, k1);
-                const uint32_t w = (r.x >> 31) | ((r.y >> 31) << 8) | ((r.z >> 31) << 16) | ((r.w >> 31) << 24);
-                sw[p] = w;
-                sw[n + p] = w ^ 0x01010101u;
-            }
-            if (lane == 0) sw[2 * n] = 0u;
+        // initial state of this quad (or the state a resumed sample continues from)
+        for (int p = lane; p < n; p += 32) {
+            const uint32_t w = start_word(P, job, (int)q, p);
+            sw[p] = w;
+            sw[n + p] = w ^ 0x01010101u;
         }
+        if (lane == 0) sw[2 * n] = 0u;
         // quad constants of rounds 1-3
         uint32_t H1, L1;
         mulhilo_w(kM1w, q, H1, L1);
@@ -148,11 +143,13 @@ __device__ void run_item_pm1w(const SweepLaunch &L, const SweepJob &job, int qua
             K1[r - 3] = k1 + (uint32_t)r * kW1w;
         }
         const uint32_t k1_2 = k1 + 2 * kW1w;
-        if (T > 0)
-            for (int e = lane + 1; e <= bias; e += 32) myrows[e - 1] = L.thr[2 * e];
+        const int t0 = job.t0;
+        if (t0 < T)
+            for (int e = lane + 1; e <= bias; e += 32)
+                myrows[(t0 & 1) * kRowW + e - 1] = L.thr[(size_t)t0 * L.thr_stride + 2 * e];
         __syncwarp();
 
-        for (int t = 0; t < T; ++t) {
+        for (int t = t0; t < T; ++t) {
             const uint32_t *th_adj = myrows + (t & 1) * kRowW - (bias + 1);
             const uint32_t y = phase_hi | (uint32_t)t;
             // round-2 product of word 0: the same for every spin of the quad

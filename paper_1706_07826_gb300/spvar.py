@@ -85,6 +85,7 @@ def lib():
         L.spvar_beta_geometric.argtypes = [i32, ctypes.c_double, ctypes.c_double, vp]
         L.spvar_thresholds.argtypes = [i32, vp, i32, i32, vp]
         L.spvar_sample.argtypes = [vp, i32, vp, i32, i32, u64, u32, u32, vp, vp, vp]
+        L.spvar_sample_range.argtypes = [vp, i32, i32, vp, i32, i32, u64, u32, u32, vp, vp, vp, vp]
         L.spvar_persistence.argtypes = [vp, i32, vp, vp, ctypes.c_double, i32, i32, i32, vp, vp, vp, vp,
                                         ctypes.POINTER(i32), vp]
         L.spvar_reduce.argtypes = [vp, vp, vp, vp, ctypes.POINTER(vp)]
@@ -258,6 +259,23 @@ def sample(problem, thr_dev, thr_stride, num_sweeps, num_samples, seed, start=0,
         energies = torch.empty(max(num_samples, 1), dtype=torch.int64, device="cuda")
     _check(lib().spvar_sample(problem.handle, num_sweeps, _dp(thr_dev), thr_stride, num_samples, seed, start,
                               phase, _dp(spins), _dp(energies), _stream(stream)), "spvar_sample")
+    return spins, energies
+
+
+def sample_range(problem, thr_dev, thr_stride, sweep_begin, sweep_end, num_samples, seed, start=0, phase=0,
+                 init=None, spins=None, energies=None, stream=None):
+    """Sweeps [sweep_begin, sweep_end) of a sample, continuing from `init`
+    (bit-packed states of an earlier range; None only for sweep_begin = 0)."""
+    import torch
+    n = problem.n
+    W = (n + 31) // 32
+    if spins is None:
+        spins = torch.empty((max(num_samples, 1), max(W, 1)), dtype=torch.int32, device="cuda")
+    if energies is None:
+        energies = torch.empty(max(num_samples, 1), dtype=torch.int64, device="cuda")
+    _check(lib().spvar_sample_range(problem.handle, sweep_begin, sweep_end, _dp(thr_dev), thr_stride, num_samples,
+                                    seed, start, phase, _dp(init), _dp(spins), _dp(energies), _stream(stream)),
+           "spvar_sample_range")
     return spins, energies
 
 

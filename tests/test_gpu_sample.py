@@ -102,3 +102,50 @@ def test_sample_rejects_short_table(cuda_lib):
     thr = torch.zeros((5, 4), dtype=torch.int32, device="cuda")  # dmax = 12 needs stride 13
     with pytest.raises(spvar.SpvarError):
         spvar.sample(gp, thr, 4, 5, 8, 1)
+
+
+@pytest.mark.parametrize("make,S", [(lambda: I.chimera(4, 1200), 37), (lambda: I.cubic3d(20, 1500), 8),
+                                    (lambda: I.weak_strong(3, 1300), 13), (lambda: I.cubic3d(5, 1101), 21)],
+                         ids=["chimera_register", "cubic_L20_streaming", "weak_strong_general", "cubic_odd"])
+def test_resumed_sample_is_identical(cuda_lib, make, S):
+    """Checkpoint/resume: sweeps [0, 40) + [40, 97) + [97, 150) from saved states
+    equal one uninterrupted 150-sweep sample (and the oracle's)."""
+    import torch
+    from paper_1706_07826_gb300 import spvar
+    inst = make()
+    T = 150
+    thr = table(inst, T)
+    gp = gpu_problem(inst)
+    thr_d = spvar.thresholds_device(thr)
+    full_s, full_e = spvar.sample(gp, thr_d, thr.shape[1], T, S, 99, 2, 1)
+    s1, _ = spvar.sample_range(gp, thr_d, thr.shape[1], 0, 40, S, 99, 2, 1)
+    s2, _ = spvar.sample_range(gp, thr_d, thr.shape[1], 40, 97, S, 99, 2, 1, init=s1)
+    s3, e3 = spvar.sample_range(gp, thr_d, thr.shape[1], 97, T, S, 99, 2, 1, init=s2)
+    torch.cuda.synchronize()
+    assert torch.equal(s3, full_s) and torch.equal(e3, full_e)
+    if inst.n <= 200:
+        o_spins, o_e, _ = O.sample(oracle_problem(inst), thr, S, 99, start=2, phase=1)
+        assert np.array_equal(e3.cpu().numpy()[:S], o_e + inst.offset)
+
+
+def test_resume_edge_cases(cuda_lib):
+    """An empty range returns the saved states with their energies; a range
+    that does not start at sweep 0 needs saved states, which may not alias the
+    output."""
+    import torch
+    from paper_1706_07826_gb300 import spvar
+    inst = I.cubic3d(4, 1102)
+    T, S = 60, 20
+    thr = table(inst, T)
+    gp = gpu_problem(inst)
+    thr_d = spvar.thresholds_device(thr)
+    s, e = spvar.sample(gp, thr_d, thr.shape[1], T, S, 5)
+    s2, e2 = spvar.sample_range(gp, thr_d, thr.shape[1], T, T, S, 5, init=s)
+    torch.cuda.synchronize()
+    assert torch.equal(s2, s) and torch.equal(e2, e)
+    with pytest.raises(spvar.SpvarError):
+        spvar.sample_range(gp, thr_d, thr.shape[1], 10, T, S, 5)
+    with pytest.raises(spvar.SpvarError):
+        spvar.sample_range(gp, thr_d, thr.shape[1], 10, T, S, 5, init=s, spins=s)
+    with pytest.raises(spvar.SpvarError):
+        spvar.sample_range(gp, thr_d, thr.shape[1], 30, 20, S, 5, init=s)
