@@ -330,6 +330,8 @@ int spvar_problem_create(int32_t n, const int32_t *row_ptr, const int32_t *col, 
         return rc;
     }
     P->dev = static_cast<DevProb *>(P->blob);
+    for (int c = 0; c < kMaxColours; ++c)
+        P->csize[c] = c < hp.hdr.ncol ? hp.cptr[c + 1] - hp.cptr[c] : 0;
     *out = reinterpret_cast<spvar_problem *>(P);
     return SPVAR_OK;
 }
@@ -429,10 +431,11 @@ int spvar_sample_range(const spvar_problem *p, int32_t sweep_begin, int32_t swee
     SweepShape sh{0, (H.n >= 512) ? 256 : 128, Q, 1, 0, 0};
     if (pm1_kernel_eligible(H.pm1 != 0, H.dmax, H.maxdeg)) {
         const int md = H.maxdeg <= 6 ? 6 : 8;
-        for (int blk : {256, 512, 128}) {
-            const int ns = pm1_nslot(H.n, Q, blk);
-            if (ns > 0 && pm1_shape_ok(blk, ns, md)) { sh = SweepShape{1, blk, Q, 0, ns, md}; break; }
-        }
+        if (pm1r_kernel_eligible(H.pm1 != 0, H.dmax, H.maxdeg))
+            for (int blk : {256, 512, 128}) {
+                const int ns = pm1_nslot(P, Q, blk);
+                if (ns > 0 && pm1_shape_ok(blk, ns, md)) { sh = SweepShape{1, blk, Q, 0, ns, md}; break; }
+            }
         // large problems: the streaming kernel (one quad per CTA)
         if (sh.kind == 0 && pm1s_shape_ok(512, md, H.n, 1) &&
             pm1s_smem_bytes(H.n, 1, md) <= (size_t)optin)
@@ -526,6 +529,8 @@ int spvar_reduce(const spvar_problem *p, const int8_t *fixed, int32_t *old_of_ne
     DevProb back;
     if (ok) ok = cudaMemcpyAsync(&back, D->dev, sizeof(DevProb), cudaMemcpyDeviceToHost, st) == cudaSuccess;
     if (ok) ok = cudaStreamSynchronize(st) == cudaSuccess;
+    int32_t cptr[kMaxColours + 1] = {0};
+    if (ok) ok = cudaMemcpy(cptr, back.cptr, sizeof(int32_t) * (back.ncol + 1), cudaMemcpyDeviceToHost) == cudaSuccess;
     cudaFree(scratch);
     if (!ok) {
         cudaFree(D->blob);
@@ -534,6 +539,7 @@ int spvar_reduce(const spvar_problem *p, const int8_t *fixed, int32_t *old_of_ne
         return SPVAR_ECUDA;
     }
     D->hdr = back;
+    for (int c = 0; c < kMaxColours; ++c) D->csize[c] = c < back.ncol ? cptr[c + 1] - cptr[c] : 0;
     *out = reinterpret_cast<spvar_problem *>(D);
     return SPVAR_OK;
 }

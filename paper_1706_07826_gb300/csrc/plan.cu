@@ -175,6 +175,18 @@ int upload_slots(spvar_plan *pl, const uint64_t *seeds, cudaStream_t st)
     return SPVAR_OK;
 }
 
+// Register-kernel slot count covering every problem of the plan (0 if none).
+int plan_nslot(const spvar_plan *pl, int Q, int block)
+{
+    int ns = 2;
+    for (const Problem *P : pl->probs) {
+        const int x = pm1_nslot(P, Q, block);
+        if (x == 0) return 0;
+        ns = std::max(ns, x);
+    }
+    return ns;
+}
+
 // Candidate sweep shapes for a plan: the general kernel with and without the
 // staged layout, and (for +-1 problems) the register-resident kernel.
 std::vector<SweepShape> candidate_shapes(const spvar_plan *pl, int optin)
@@ -210,8 +222,8 @@ std::vector<SweepShape> candidate_shapes(const spvar_plan *pl, int optin)
                         out.push_back(sh);
                 }
             }
-            if (pm1_kernel_eligible(pl->pm1, pl->dmax, pl->max_deg)) {
-                const int ns = pm1_nslot(pl->max_n0, Q, blocks[bi]);
+            if (pm1r_kernel_eligible(pl->pm1, pl->dmax, pl->max_deg)) {
+                const int ns = plan_nslot(pl, Q, blocks[bi]);
                 const int md = pl->max_deg <= 6 ? 6 : 8;
                 SweepShape sh{1, blocks[bi], Q, 0, ns, md};
                 if (ns > 0 && pm1_shape_ok(blocks[bi], ns, md) &&
@@ -513,7 +525,7 @@ int spvar_plan_create(const spvar_problem *const *problems, int32_t nproblems,
         const bool elig = pm1_kernel_eligible(pl->pm1, pl->dmax, pl->max_deg);
         SweepShape sh{0, blk, Q, 1, 0, 0};
         if (p.sweep_kernel == SPVAR_SWEEP_PM1 || (p.sweep_kernel == SPVAR_SWEEP_AUTO && elig)) {
-            const int ns = pm1_nslot(pl->max_n0, Q, blk);
+            const int ns = pm1r_kernel_eligible(pl->pm1, pl->dmax, pl->max_deg) ? plan_nslot(pl, Q, blk) : 0;
             const int md = pl->max_deg <= 6 ? 6 : 8;
             if (!elig) { plan_free(pl); return SPVAR_ELIMIT; }
             if (ns > 0 && pm1_shape_ok(blk, ns, md)) sh = SweepShape{1, blk, Q, 0, ns, md};

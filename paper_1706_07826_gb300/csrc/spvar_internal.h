@@ -41,6 +41,7 @@ struct DevProb {
 // Host handle of a problem: the device blob and a host copy of its header.
 struct Problem {
     DevProb hdr;        // host copy (pointers are device pointers)
+    int32_t csize[kMaxColours];  // colour class sizes
     DevProb *dev;       // device copy of the header (inside the blob)
     void *blob;
     size_t blob_bytes;
@@ -215,15 +216,20 @@ int pm1w_max_active_blocks(int warps, int maxd, size_t smem);
 struct SweepShape {
     int kind, block, Q, stage, nslot, maxd;
 };
-// The register kernel applies to +-1 couplers, degree <= 8 and dmax <= 254.
+// The streaming and warp-per-quad kernels apply to +-1 couplers, degree <= 8
+// and dmax <= 254; the register kernel needs dmax <= 30.
 inline bool pm1_kernel_eligible(bool pm1, int dmax, int maxdeg) { return pm1 && dmax <= 254 && maxdeg <= 8; }
-// Smallest slot count (1, 2, 4) covering max_n * Q items with `block` threads, 0 if none.
-inline int pm1_nslot(int max_n, int Q, int block)
+inline bool pm1r_kernel_eligible(bool pm1, int dmax, int maxdeg) { return pm1 && dmax <= 30 && maxdeg <= 8; }
+// Slots per thread the register kernel needs for problem P at Q quads per CTA
+// (every colour class fills whole slots), rounded up to an instantiated count
+// (2..4); 0 if more than 4.  Reductions only shrink classes, so the original
+// problem's count covers all its phases.
+inline int pm1_nslot(const Problem *P, int Q, int block)
 {
-    const long long items = (long long)max_n * Q;
-    for (int ns = 1; ns <= 4; ns <<= 1)
-        if ((long long)ns * block >= items) return ns;
-    return 0;
+    long long need = 0;
+    for (int c = 0; c < P->hdr.ncol; ++c) need += ((long long)P->csize[c] * Q + block - 1) / block;
+    if (need > 4) return 0;
+    return need < 2 ? 2 : (int)need;
 }
 inline size_t sweep_shape_smem(const SweepShape &s, int max_n, int thr_stride, int max_deg)
 {

@@ -2,36 +2,44 @@
 // of Sec. III.A on the paper's +-J spin glasses and Chimera problems).
 //
 // Same dynamics, random words and result as the general sweep kernel, with
-// the per-attempt instruction count cut down:
+// the per-attempt instruction count cut down and moved off the integer ALU
+// pipe (which issues at half the rate of the FMA pipe):
 //  - every thread owns NSLOT fixed (spin, quad) items for the whole anneal;
-//    their neighbour word offsets, SWAR constants and the parts of Philox
-//    rounds 1-3 that do not depend on the sweep index stay in registers;
+//    slot j of every thread belongs to one colour class (a class fills
+//    ceil(size * quads / B) whole slots), so the colour order is the slot
+//    order and the only barriers are the ones between classes;
+//  - each item keeps its neighbour word offsets, its flip-cost constant and
+//    the parts of Philox rounds 1-3 that do not depend on the sweep index in
+//    registers;
 //  - shared memory holds each spin word twice, as is and with every replica
-//    bit inverted, so a J < 0 neighbour is read from the inverted copy and the
-//    local field of four replicas is one byte-wise sum of neighbour words;
-//  - the flip-cost index of the four replicas is formed byte-wise (SWAR) and
-//    looks up a shared row of the threshold table.
-// Eligible when every |J| = 1, degree <= MAXD and dmax <= 254 (the biased
-// index fits a byte).
+//    bit inverted, at a compile-time distance, so a J < 0 neighbour is read
+//    from the inverted copy and the local field of four replicas is one
+//    byte-wise sum of neighbour words;
+//  - the flip-cost index of the four replicas is formed byte-wise (SWAR),
+//    pre-scaled to the byte offset of a 64-bit threshold entry;
+//  - acceptance is one wide multiply-add per replica: the row holds
+//    2^32 - thr (0 where dE <= 0), so u + entry carries into bit 32 exactly
+//    when the move is rejected (u >= thr), and the four carries are the
+//    replicas' reject bits.
+// Eligible when every |J| = 1, degree <= MAXD and dmax <= 30 (so that the
+// scaled index 8 (dE/2 + bias) fits a byte).
 #include "sweep_common.cuh"
 
 namespace spvar {
 
 namespace {
 
-constexpr int kRowWords = 256;  // threshold row indexed by dE/2 + bias, bias <= 127
+constexpr int kRowE = 32;  // 64-bit entries per threshold row: index dE/2 + bias <= 2 * 15
 constexpr uint32_t kM0 = 0xD2511F53u, kM1 = 0xCD9E8D57u, kW0 = 0x9E3779B9u, kW1 = 0xBB67AE85u;
 
 template <int MAXD>
 struct SlotRegs {
-    uint32_t own;      // byte offset of the slot's spin word in shared memory
-    uint32_t nb[MAXD]; // byte offsets of the neighbours (inverted copy if J < 0, zero word if padding)
-    uint32_t c0, c1;   // per byte: bias - deg + h, bias + deg - h
-    uint32_t A, L0k, D, H3k, L3;  // Philox rounds 1-3 folded with the slot's fixed counter words
-    int colour;        // colour class of the slot, -1 if the slot is empty
+    uint32_t own;       // byte offset of the item's spin word (plain copy)
+    uint32_t nb[MAXD];  // byte offsets of the neighbours (inverted copy if J < 0, zero word if padding)
+    uint32_t c0;        // per byte: 8 (bias - deg + h)
+    uint32_t A, L0k, D, H3k, L3;  // Philox rounds 1-3 folded with the item's fixed counter words
 };
 
-// Shared-memory word at a byte offset from the start of the dynamic window.
 __device__ __forceinline__ uint32_t lds_b(const uint32_t *base, uint32_t byte_off)
 {
     return *reinterpret_cast<const uint32_t *>(reinterpret_cast<const char *>(base) + byte_off);
@@ -48,9 +56,25 @@ __device__ __forceinline__ void mulhilo(uint32_t m, uint32_t a, uint32_t &hi, ui
     lo = (uint32_t)p;
 }
 
+// High word of a * b + c (64-bit c); with b = 1 it is the carry of u + entry.
+__device__ __forceinline__ uint32_t mad_wide_hi(uint32_t a, uint32_t b, uint64_t c)
+{
+    uint64_t d;
+    asm("mad.wide.u32 %0, %1, %2, %3;" : "=l"(d) : "r"(a), "r"(b), "l"(c));
+    return (uint32_t)(d >> 32);
+}
+
+// a * b + c on 32 bits.
+__device__ __forceinline__ uint32_t mad_lo(uint32_t a, uint32_t b, uint32_t c)
+{
+    uint32_t d;
+    asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+    return d;
+}
+
 // Counter (i, y, q, s): the sweep word y is the only input that changes
 // between sweeps, so the products of round 1 and parts of rounds 2 and 3 are
-// slot constants.
+// item constants.
 template <int MAXD>
 __device__ __forceinline__ void philox_setup(SlotRegs<MAXD> &s, uint32_t i, uint32_t q, uint32_t start,
                                              uint32_t k0, uint32_t k1)
@@ -102,9 +126,72 @@ __device__ __forceinline__ uint4 philox_slot(const SlotRegs<MAXD> &s, uint32_t y
     return c;
 }
 
-template <int B, int NSLOT, int MAXD>
-__device__ void run_item_pm1(const SweepLaunch &L, const SweepJob &job, int quad0, int nq, uint32_t *smem)
+// Shared memory of one CTA: spin words (plain copy, a dummy word, inverted
+// copy at a fixed distance, its dummy, a zero word) and two threshold rows.
+template <int B, int NSLOT>
+struct Pm1Smem {
+    static constexpr int KW = B * NSLOT + 1;  // words per copy; word KW - 1 is the dummy
+    uint32_t sw[2 * KW + 1];
+    unsigned long long row[2][kRowE];
+    int cptr[kMaxColours + 1];
+};
+
+// One sweep over the slots, reading threshold row PAR.  Slot j is processed
+// by warps with an item in it (bit j of wmask); a barrier precedes slot j
+// when it starts a new colour class (bit j of barmask) and closes the sweep.
+template <int B, int NSLOT, int MAXD, int PAR>
+__device__ __forceinline__ void sweep_once(Pm1Smem<B, NSLOT> &sm, const SlotRegs<MAXD> (&s)[NSLOT], uint32_t y,
+                                           const RoundKeys &K, uint32_t wmask, uint32_t barmask, uint32_t one,
+                                           uint32_t k16, const uint32_t *next_src, int bias)
 {
+    constexpr uint32_t kInv = 4u * (uint32_t)Pm1Smem<B, NSLOT>::KW;  // byte distance to the inverted copy
+    // next sweep's row (its buffer was last read in the previous sweep)
+    if (next_src && (int)threadIdx.x < bias) {
+        const int e = (int)threadIdx.x + 1;
+        sm.row[PAR ^ 1][bias + e] = (1ull << 32) - (unsigned long long)next_src[2 * e];
+    }
+    const char *rowb = reinterpret_cast<const char *>(sm.row[PAR]);
+#pragma unroll
+    for (int j = 0; j < NSLOT; ++j) {
+        if (barmask & (1u << j)) __syncthreads();
+        if (wmask & (1u << j)) {
+            const uint32_t own = lds_b(sm.sw, s[j].own);
+            uint32_t nbw[MAXD];
+#pragma unroll
+            for (int d = 0; d < MAXD; ++d) nbw[d] = lds_b(sm.sw, s[j].nb[d]);
+            const uint4 u = philox_slot(s[j], y, K);
+            uint32_t x = 0;
+#pragma unroll
+            for (int d = 0; d < MAXD; ++d) x += nbw[d];
+            // byte r of x: neighbours with b_j ^ [J_ij < 0] = 1; the flip-cost index
+            // dE/2 + bias is 2x + bias - deg + h if b_i = 0 and its mirror 2 bias - that
+            // if b_i = 1; all scaled by 8 (the byte offset of a 64-bit row entry)
+            const uint32_t a = mad_lo(x, 16u * one, s[j].c0);
+            const uint32_t b = mad_lo(a, 0u - one, k16);
+            const uint32_t m = own * 0xFFu;
+            const uint32_t idx8 = (a & ~m) | (b & m);
+            const uint32_t ur[4] = {u.x, u.y, u.z, u.w};
+            uint32_t rej = 0;
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const uint32_t off = __byte_perm(idx8, 0u, 0x4440u | (uint32_t)r);
+                const unsigned long long ent = *reinterpret_cast<const unsigned long long *>(rowb + off);
+                const uint32_t carry = mad_wide_hi(ur[r], one, ent);
+                rej = r == 0 ? carry : mad_lo(carry, one << (8 * r), rej);
+            }
+            // flip where not rejected
+            const uint32_t inv = own ^ rej;  // = new word with every replica bit inverted
+            sts_b(sm.sw, s[j].own, inv ^ 0x01010101u);
+            sts_b(sm.sw, s[j].own + kInv, inv);
+        }
+    }
+    __syncthreads();
+}
+
+template <int B, int NSLOT, int MAXD>
+__device__ void run_item_pm1(const SweepLaunch &L, const SweepJob &job, int quad0, int nq, Pm1Smem<B, NSLOT> &sm)
+{
+    constexpr int KW = Pm1Smem<B, NSLOT>::KW;
     const int tid = threadIdx.x;
     const DevProb *P = job.prob;
     const int n = P->n;
@@ -114,119 +201,103 @@ __device__ void run_item_pm1(const SweepLaunch &L, const SweepJob &job, int quad
     const uint32_t k0 = (uint32_t)job.seed, k1 = (uint32_t)(job.seed >> 32);
     const uint32_t phase_hi = job.phase << kSweepBits;
     const int T = L.T;
-    const int S1 = nq * n;  // offset of the inverted copy
-
-    uint32_t *sw = smem;                           // [S1] plain, [S1] inverted, [1] zero
-    uint32_t *trow = smem + 2 * L.Q * L.max_n + 4; // 2 threshold rows
-    int *e2 = reinterpret_cast<int *>(trow + 2 * kRowWords);
-    __shared__ int s_cptr[kMaxColours + 1];
-
-    for (int c = tid; c <= ncol; c += B) s_cptr[c] = P->cptr[c];
-    init_spins(P, job, quad0, nq, sw, sw + S1);
-    if (tid == 0) sw[2 * S1] = 0u;
-    // first row of the thresholds: trow[bias + e] = thr[t0][2e], e = 1..bias
     const int t0 = job.t0;
-    if (t0 < T)
-        for (int e = tid + 1; e <= bias; e += B)
-            trow[(t0 & 1) * kRowWords + bias + e] = L.thr[(size_t)t0 * L.thr_stride + 2 * e];
+    // a 1 the compiler cannot fold, so the multiply-adds stay on the FMA pipe
+    const uint32_t one = (uint32_t)(L.thr_stride > 0);
+
+    for (int c = tid; c <= ncol; c += B) sm.cptr[c] = P->cptr[c];
+    init_spins(P, job, quad0, nq, sm.sw, sm.sw + KW);
+    if (tid == 0) {
+        sm.sw[KW - 1] = 0u;
+        sm.sw[2 * KW - 1] = 0u;
+        sm.sw[2 * KW] = 0u;
+    }
+    // threshold rows: entry i = 2^32 - thr[t][2 (i - bias)] for i > bias, 0 (always accept) otherwise
+    for (int i = tid; i < 2 * kRowE; i += B) {
+        const int par = i / kRowE, e = i % kRowE - bias;
+        unsigned long long v = 0;
+        if (e > 0 && e <= bias && par == (t0 & 1) && t0 < T)
+            v = (1ull << 32) - (unsigned long long)L.thr[(size_t)t0 * L.thr_stride + 2 * e];
+        sm.row[par][i % kRowE] = v;
+    }
     __syncthreads();
 
+    // colour-aligned slots
     SlotRegs<MAXD> s[NSLOT];
-    uint4 u[NSLOT];  // random words of each slot for the sweep about to run
+    uint32_t wmask = 0, barmask = 0;
     const RoundKeys K = round_keys(k0, k1);
-    const int total = n * nq;
+    const uint32_t dummy = 4u * (uint32_t)(KW - 1), zero = 4u * (uint32_t)(2 * KW);
 #pragma unroll
     for (int j = 0; j < NSLOT; ++j) {
-        const int g = tid + j * B;
-        s[j].colour = -1;
-        s[j].own = 4u * (uint32_t)(2 * S1);
+        s[j].own = dummy;
 #pragma unroll
-        for (int d = 0; d < MAXD; ++d) s[j].nb[d] = 4u * (uint32_t)(2 * S1);
-        s[j].c0 = s[j].c1 = s[j].A = s[j].L0k = s[j].D = s[j].H3k = s[j].L3 = 0u;
-        if (g < total) {
-            int c = 0;
-            while (s_cptr[c + 1] * nq <= g) ++c;
-            const int nc = s_cptr[c + 1] - s_cptr[c];
-            const int local = g - s_cptr[c] * nq;
-            const int q = local / nc;
-            const int p = s_cptr[c] + (local - q * nc);
-            const uint32_t meta = P->meta[p];
-            const int deg = (int)(meta & 0xFFFFu);
-            const int h = (int)meta >> 16;
-            s[j].own = 4u * (uint32_t)(q * n + p);
-#pragma unroll
-            for (int d = 0; d < MAXD; ++d) {
-                if (d < deg) {
-                    const uint32_t e = P->ell[(size_t)d * cap_n + p];
-                    s[j].nb[d] = 4u * (uint32_t)(((e >> 31) ? S1 : 0) + q * n + (int)(e & 0xFFFFu));
-                }
-            }
-            s[j].c0 = (uint32_t)(bias - deg + h) * 0x01010101u;
-            s[j].c1 = (uint32_t)(bias + deg - h) * 0x01010101u;
-            philox_setup(s[j], (uint32_t)P->idx_of_pos[p], (uint32_t)(quad0 + q), job.start, k0, k1);
-            s[j].colour = c;
+        for (int d = 0; d < MAXD; ++d) s[j].nb[d] = zero;
+        s[j].c0 = (uint32_t)(8 * bias) * 0x01010101u;
+        s[j].A = s[j].L0k = s[j].D = s[j].H3k = s[j].L3 = 0u;
+        // colour class of slot j
+        int c = 0, jb = 0, items = 0;
+        for (; c < ncol; ++c) {
+            items = (sm.cptr[c + 1] - sm.cptr[c]) * nq;
+            const int ns = (items + B - 1) / B;
+            if (j < jb + ns) break;
+            jb += ns;
         }
-        u[j] = philox_slot(s[j], phase_hi | (uint32_t)t0, K);  // first sweep
-    }
-
-    for (int t = t0; t < T; ++t) {
-        const uint32_t *th = trow + (t & 1) * kRowWords;
-        const uint32_t y = phase_hi | (uint32_t)t;
-        for (int c = 0; c < ncol; ++c) {
-            if (c == 0 && t + 1 < T) {
-                uint32_t *nxt = trow + ((t + 1) & 1) * kRowWords;
-                const uint32_t *src = L.thr + (size_t)(t + 1) * L.thr_stride;
-                for (int e = tid + 1; e <= bias; e += B) nxt[bias + e] = src[2 * e];
-            }
+        if (c < ncol) {
+            if (j == jb && j > 0) barmask |= 1u << j;
+            const int local = (j - jb) * B + tid;
+            if ((j - jb) * B + (tid & ~31) < items) wmask |= 1u << j;
+            if (local < items) {
+                const int nc = sm.cptr[c + 1] - sm.cptr[c];
+                const int q = local / nc;
+                const int p = sm.cptr[c] + (local - q * nc);
+                const uint32_t meta = P->meta[p];
+                const int deg = (int)(meta & 0xFFFFu);
+                const int h = (int)meta >> 16;
+                s[j].own = 4u * (uint32_t)(q * n + p);
 #pragma unroll
-            for (int j = 0; j < NSLOT; ++j) {
-                if (s[j].colour == c) {
-                    // loads first; the next sweep's Philox block (independent of the spins)
-                    // is computed while they are in flight
-                    const uint32_t own = lds_b(sw, s[j].own);
-                    uint32_t nbw[MAXD];
-#pragma unroll
-                    for (int d = 0; d < MAXD; ++d) nbw[d] = lds_b(sw, s[j].nb[d]);
-                    const uint4 unext = philox_slot(s[j], y + 1u, K);
-                    uint32_t x = 0;
-#pragma unroll
-                    for (int d = 0; d < MAXD; ++d) x += nbw[d];
-                    // byte r: number of neighbours with b_j ^ [J_ij < 0] = 1; the
-                    // flip-cost index dE/2 + bias is 2x + c0 if b_i = 0, c1 - 2x if b_i = 1
-                    const uint32_t m = own * 0xFFu;
-                    const uint32_t x2 = x + x;
-                    const uint32_t idx4 = ((x2 + s[j].c0) & ~m) | ((s[j].c1 - x2) & m);
-                    // byte r of `always` is 0x80 iff idx_r <= bias (dE <= 0): accepted without a draw
-                    const uint32_t always = ((uint32_t)(bias + 0x80) * 0x01010101u - idx4) & 0x80808080u;
-                    const uint32_t uu[4] = {u[j].x, u[j].y, u[j].z, u[j].w};
-                    uint32_t flip = always >> 7;
-#pragma unroll
-                    for (int r = 0; r < 4; ++r) {
-                        const int ir = (int)((idx4 >> (8 * r)) & 0xFFu);
-                        if (uu[r] < th[ir]) flip |= 1u << (8 * r);
+                for (int d = 0; d < MAXD; ++d) {
+                    if (d < deg) {
+                        const uint32_t e = P->ell[(size_t)d * cap_n + p];
+                        s[j].nb[d] = 4u * (uint32_t)(((e >> 31) ? KW : 0) + q * n + (int)(e & 0xFFFFu));
                     }
-                    const uint32_t nw = own ^ flip;
-                    sts_b(sw, s[j].own, nw);
-                    sts_b(sw, s[j].own + 4u * (uint32_t)S1, nw ^ 0x01010101u);
-                    u[j] = unext;
                 }
+                s[j].c0 = (uint32_t)(8 * (bias - deg + h)) * 0x01010101u;
+                philox_setup(s[j], (uint32_t)P->idx_of_pos[p], (uint32_t)(quad0 + q), job.start, k0, k1);
             }
-            __syncthreads();
         }
     }
-    finish_item<true>(P, job, quad0, nq, sw, e2);
+    const uint32_t k16 = (uint32_t)(16 * bias) * 0x01010101u;
+    const uint32_t *thr = L.thr;
+    const size_t ts = (size_t)L.thr_stride;
+
+    int t = t0;
+    if (t < T && (t & 1)) {
+        sweep_once<B, NSLOT, MAXD, 1>(sm, s, phase_hi | (uint32_t)t, K, wmask, barmask, one, k16,
+                                      t + 1 < T ? thr + (size_t)(t + 1) * ts : nullptr, bias);
+        ++t;
+    }
+    for (; t + 1 < T; t += 2) {
+        sweep_once<B, NSLOT, MAXD, 0>(sm, s, phase_hi | (uint32_t)t, K, wmask, barmask, one, k16,
+                                      thr + (size_t)(t + 1) * ts, bias);
+        sweep_once<B, NSLOT, MAXD, 1>(sm, s, phase_hi | (uint32_t)(t + 1), K, wmask, barmask, one, k16,
+                                      t + 2 < T ? thr + (size_t)(t + 2) * ts : nullptr, bias);
+    }
+    if (t < T)
+        sweep_once<B, NSLOT, MAXD, 0>(sm, s, phase_hi | (uint32_t)t, K, wmask, barmask, one, k16, nullptr, bias);
+    // the inverted copy is dead now: its first 4 nq words hold the energy sums
+    finish_item<true>(P, job, quad0, nq, sm.sw, reinterpret_cast<int *>(sm.sw + KW));
 }
 
 template <int B, int NSLOT, int MAXD>
 __global__ void __launch_bounds__(B) k_sweep_pm1(const SweepLaunch L)
 {
-    extern __shared__ __align__(16) uint32_t smem_pm1[];
+    __shared__ Pm1Smem<B, NSLOT> sm;
     __shared__ int s_item;
     for (int iter = 0;; ++iter) {
         SweepJob job;
         int quad0, nq;
         if (!next_item(L, iter, &s_item, job, quad0, nq)) break;
-        run_item_pm1<B, NSLOT, MAXD>(L, job, quad0, nq, smem_pm1);
+        run_item_pm1<B, NSLOT, MAXD>(L, job, quad0, nq, sm);
         __syncthreads();
     }
 }
@@ -241,12 +312,12 @@ void *select_kernel(int block, int nslot, int maxd)
 {
 #define SPVAR_PM1_CASE(BB, NS, MD) \
     if (block == BB && nslot == NS && maxd == MD) return kernel_ptr<BB, NS, MD>();
-    SPVAR_PM1_CASE(128, 1, 6) SPVAR_PM1_CASE(128, 2, 6) SPVAR_PM1_CASE(128, 4, 6)
-    SPVAR_PM1_CASE(256, 1, 6) SPVAR_PM1_CASE(256, 2, 6) SPVAR_PM1_CASE(256, 4, 6)
-    SPVAR_PM1_CASE(512, 1, 6) SPVAR_PM1_CASE(512, 2, 6)
-    SPVAR_PM1_CASE(128, 1, 8) SPVAR_PM1_CASE(128, 2, 8) SPVAR_PM1_CASE(128, 4, 8)
-    SPVAR_PM1_CASE(256, 1, 8) SPVAR_PM1_CASE(256, 2, 8) SPVAR_PM1_CASE(256, 4, 8)
-    SPVAR_PM1_CASE(512, 1, 8) SPVAR_PM1_CASE(512, 2, 8)
+    SPVAR_PM1_CASE(128, 2, 6) SPVAR_PM1_CASE(128, 3, 6) SPVAR_PM1_CASE(128, 4, 6)
+    SPVAR_PM1_CASE(256, 2, 6) SPVAR_PM1_CASE(256, 3, 6) SPVAR_PM1_CASE(256, 4, 6)
+    SPVAR_PM1_CASE(512, 2, 6)
+    SPVAR_PM1_CASE(128, 2, 8) SPVAR_PM1_CASE(128, 3, 8) SPVAR_PM1_CASE(128, 4, 8)
+    SPVAR_PM1_CASE(256, 2, 8) SPVAR_PM1_CASE(256, 3, 8) SPVAR_PM1_CASE(256, 4, 8)
+    SPVAR_PM1_CASE(512, 2, 8)
 #undef SPVAR_PM1_CASE
     return nullptr;
 }
@@ -255,29 +326,23 @@ void *select_kernel(int block, int nslot, int maxd)
 
 bool pm1_shape_ok(int block, int nslot, int maxd) { return select_kernel(block, nslot, maxd) != nullptr; }
 
-size_t pm1_smem_bytes(int max_n, int Q)
-{
-    return 4 * (2 * (size_t)Q * max_n + 4 + 2 * (size_t)kRowWords + 4 * (size_t)Q);
-}
+size_t pm1_smem_bytes(int, int) { return 0; }  // all shared memory is static
 
-cudaError_t launch_sweep_pm1(const SweepLaunch &L, int block, int nslot, int maxd, int grid, size_t smem,
+cudaError_t launch_sweep_pm1(const SweepLaunch &L, int block, int nslot, int maxd, int grid, size_t,
                              cudaStream_t st)
 {
     void *k = select_kernel(block, nslot, maxd);
     if (!k) return cudaErrorInvalidValue;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
     void *args[] = {const_cast<SweepLaunch *>(&L)};
-    return cudaLaunchKernel(k, dim3(grid), dim3(block), args, smem, st);
+    return cudaLaunchKernel(k, dim3(grid), dim3(block), args, 0, st);
 }
 
-int pm1_max_active_blocks(int block, int nslot, int maxd, size_t smem)
+int pm1_max_active_blocks(int block, int nslot, int maxd, size_t)
 {
     void *k = select_kernel(block, nslot, maxd);
     if (!k) return 0;
-    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int nb = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, block, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, block, 0);
     return nb;
 }
 
