@@ -134,7 +134,9 @@ SweepLaunch make_launch(const spvar_plan *pl, int T)
 int grid_for(const spvar_plan *pl, int items)
 {
     const int occ = std::max(1, sweep_shape_occupancy(pl->shape, pl->pm1, pl->sweep_smem));
-    return std::max(1, std::min(items, occ * pl->sms));
+    const int full = occ * pl->sms;
+    if (!pl->shape.balance || items <= full) return std::max(1, std::min(items, full));
+    return ceil_div(items, ceil_div(items, full));
 }
 
 PhaseEngine engine_of(const spvar_plan *pl)
@@ -256,7 +258,13 @@ void autotune(spvar_plan *pl, cudaStream_t st, int optin)
     cudaEvent_t a, b;
     cudaEventCreate(&a);
     cudaEventCreate(&b);
-    for (const SweepShape &sh : candidate_shapes(pl, optin)) {
+    std::vector<SweepShape> cands;
+    for (SweepShape sh : candidate_shapes(pl, optin)) {
+        cands.push_back(sh);
+        sh.balance = 1;
+        if (pl->prm.form != SPVAR_FORM_PLAIN) cands.push_back(sh);
+    }
+    for (const SweepShape &sh : cands) {
         pl->shape = sh;
         pl->sweep_smem = sweep_shape_smem(sh, pl->max_n0, pl->thr_stride, pl->max_deg);
         if (sweep_shape_occupancy(sh, pl->pm1, pl->sweep_smem) < 1) continue;

@@ -212,9 +212,12 @@ int pm1w_max_active_blocks(int warps, int maxd, size_t smem);
 // shared memory), kind 1 = register-resident +-1 kernel (nslot items per
 // thread, maxd neighbour registers per item), kind 2 = streaming +-1 kernel
 // (maxd neighbour offsets per spin staged in shared memory, Q = 1), kind 4 =
-// warp-per-quad +-1 kernel (Q = warps = block / 32).
+// warp-per-quad +-1 kernel (Q = warps = block / 32).  A persistent grid holds
+// every CTA the SMs can keep resident, or (balance) the fewest CTAs that still
+// need the same number of waves of items, so that no last wave runs nearly empty.
 struct SweepShape {
     int kind, block, Q, stage, nslot, maxd;
+    int balance = 0;  // 1: grid sized so that every CTA runs the same number of items
 };
 // The streaming and warp-per-quad kernels apply to +-1 couplers, degree <= 8
 // and dmax <= 254; the register kernel needs dmax <= 30.

@@ -136,12 +136,13 @@ struct Pm1Smem {
     int cptr[kMaxColours + 1];
 };
 
-// One sweep over the slots, reading threshold row PAR.  Slot j is processed
-// by warps with an item in it (bit j of wmask); a barrier precedes slot j
-// when it starts a new colour class (bit j of barmask) and closes the sweep.
+// One sweep over the slots, reading threshold row PAR.  Every lane runs every
+// slot (lanes without an item anneal the dummy word: no branch per slot); a
+// barrier precedes slot j when it starts a new colour class (bit j of
+// barmask) and closes the sweep.
 template <int B, int NSLOT, int MAXD, int PAR>
 __device__ __forceinline__ void sweep_once(Pm1Smem<B, NSLOT> &sm, const SlotRegs<MAXD> (&s)[NSLOT], uint32_t y,
-                                           const RoundKeys &K, uint32_t wmask, uint32_t barmask, uint32_t one,
+                                           const RoundKeys &K, uint32_t barmask, uint32_t one,
                                            uint32_t k16, const uint32_t *next_src, int bias)
 {
     constexpr uint32_t kInv = 4u * (uint32_t)Pm1Smem<B, NSLOT>::KW;  // byte distance to the inverted copy
@@ -154,7 +155,7 @@ __device__ __forceinline__ void sweep_once(Pm1Smem<B, NSLOT> &sm, const SlotRegs
 #pragma unroll
     for (int j = 0; j < NSLOT; ++j) {
         if (barmask & (1u << j)) __syncthreads();
-        if (wmask & (1u << j)) {
+        {
             const uint32_t own = lds_b(sm.sw, s[j].own);
             uint32_t nbw[MAXD];
 #pragma unroll
@@ -224,7 +225,7 @@ __device__ void run_item_pm1(const SweepLaunch &L, const SweepJob &job, int quad
 
     // colour-aligned slots
     SlotRegs<MAXD> s[NSLOT];
-    uint32_t wmask = 0, barmask = 0;
+    uint32_t barmask = 0;
     const RoundKeys K = round_keys(k0, k1);
     const uint32_t dummy = 4u * (uint32_t)(KW - 1), zero = 4u * (uint32_t)(2 * KW);
 #pragma unroll
@@ -245,7 +246,6 @@ __device__ void run_item_pm1(const SweepLaunch &L, const SweepJob &job, int quad
         if (c < ncol) {
             if (j == jb && j > 0) barmask |= 1u << j;
             const int local = (j - jb) * B + tid;
-            if ((j - jb) * B + (tid & ~31) < items) wmask |= 1u << j;
             if (local < items) {
                 const int nc = sm.cptr[c + 1] - sm.cptr[c];
                 const int q = local / nc;
@@ -272,18 +272,18 @@ __device__ void run_item_pm1(const SweepLaunch &L, const SweepJob &job, int quad
 
     int t = t0;
     if (t < T && (t & 1)) {
-        sweep_once<B, NSLOT, MAXD, 1>(sm, s, phase_hi | (uint32_t)t, K, wmask, barmask, one, k16,
+        sweep_once<B, NSLOT, MAXD, 1>(sm, s, phase_hi | (uint32_t)t, K, barmask, one, k16,
                                       t + 1 < T ? thr + (size_t)(t + 1) * ts : nullptr, bias);
         ++t;
     }
     for (; t + 1 < T; t += 2) {
-        sweep_once<B, NSLOT, MAXD, 0>(sm, s, phase_hi | (uint32_t)t, K, wmask, barmask, one, k16,
+        sweep_once<B, NSLOT, MAXD, 0>(sm, s, phase_hi | (uint32_t)t, K, barmask, one, k16,
                                       thr + (size_t)(t + 1) * ts, bias);
-        sweep_once<B, NSLOT, MAXD, 1>(sm, s, phase_hi | (uint32_t)(t + 1), K, wmask, barmask, one, k16,
+        sweep_once<B, NSLOT, MAXD, 1>(sm, s, phase_hi | (uint32_t)(t + 1), K, barmask, one, k16,
                                       t + 2 < T ? thr + (size_t)(t + 2) * ts : nullptr, bias);
     }
     if (t < T)
-        sweep_once<B, NSLOT, MAXD, 0>(sm, s, phase_hi | (uint32_t)t, K, wmask, barmask, one, k16, nullptr, bias);
+        sweep_once<B, NSLOT, MAXD, 0>(sm, s, phase_hi | (uint32_t)t, K, barmask, one, k16, nullptr, bias);
     // the inverted copy is dead now: its first 4 nq words hold the energy sums
     finish_item<true>(P, job, quad0, nq, sm.sw, reinterpret_cast<int *>(sm.sw + KW));
 }
