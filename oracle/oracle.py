@@ -34,6 +34,10 @@ class OrParams(ctypes.Structure):
         ("start0", ctypes.c_int32),
         ("boost", ctypes.c_int32),
         ("tree", ctypes.c_int32),
+        ("corr_sample_size", ctypes.c_int32),
+        ("corr_num", ctypes.c_int32),
+        ("corr_den", ctypes.c_int32),
+        ("corr_elite_threshold", ctypes.c_double),
     ]
 
 
@@ -296,14 +300,16 @@ class SolveResult:
 
 
 def solve(p: Csr, thr, seed, num_starts, fixing_sample_size, solving_sample_size, elite_threshold,
-          fix_num=1, fix_den=1, iterate=False, max_fix_phases=1, canon=-1, start0=0, boost=False, tree=False):
-    """Multi-start SPVAR (Alg. 2) with SA; thr is the original problem's table."""
+          fix_num=1, fix_den=1, iterate=False, max_fix_phases=1, canon=-1, start0=0, boost=False, tree=False,
+          corr_sample_size=0, corr_elite_threshold=0.2, corr_num=1, corr_den=1):
+    """Multi-start SPVAR (Alg. 2) with SA; thr is the original problem's table.
+    corr_sample_size > 0 adds the correlation-fixing phase for zero-bias problems."""
     thr = _c(thr, np.uint32)
     prm = OrParams(num_starts, fixing_sample_size, solving_sample_size, thr.shape[0], float(elite_threshold),
                    fix_num, fix_den, 1 if iterate else 0, max_fix_phases, canon, start0, 1 if boost else 0,
-                   1 if tree else 0)
-    P = max_fix_phases + 1
-    Smax = max(fixing_sample_size, solving_sample_size)
+                   1 if tree else 0, corr_sample_size, corr_num, corr_den, float(corr_elite_threshold))
+    P = max_fix_phases + 1 + (1 if corr_sample_size > 0 else 0)
+    Smax = max(fixing_sample_size, solving_sample_size, corr_sample_size)
     n0 = p.n
     en = np.zeros((num_starts, P, Smax), np.int64)
     counts = np.zeros((num_starts, P), np.int32)

@@ -578,12 +578,15 @@ int or_solve(int32_t n0, const int32_t *row_ptr0, const int32_t *col0, const int
              int64_t *energies, int32_t *counts, int32_t *nfree, int32_t *nphases,
              int8_t *fixed, int64_t *best_e, int8_t *best_state)
 {
-    const int32_t P = prm->max_fix_phases + 1;
-    const int32_t Smax = prm->fixing_sample_size > prm->solving_sample_size
-                             ? prm->fixing_sample_size : prm->solving_sample_size;
+    const int32_t P = prm->max_fix_phases + 1 + (prm->corr_sample_size > 0 ? 1 : 0);
+    int32_t Smax = prm->fixing_sample_size > prm->solving_sample_size
+                       ? prm->fixing_sample_size : prm->solving_sample_size;
+    if (prm->corr_sample_size > Smax) Smax = prm->corr_sample_size;
     const int64_t nnz0 = row_ptr0[n0];
     if (prm->max_fix_phases < 1 || prm->fix_den <= 0 || prm->fix_num <= 0 ||
-        prm->fix_num > prm->fix_den || prm->fixing_sample_size < 1 || prm->solving_sample_size < 0)
+        prm->fix_num > prm->fix_den || prm->fixing_sample_size < 1 || prm->solving_sample_size < 0 ||
+        prm->corr_sample_size < 0 ||
+        (prm->corr_sample_size > 0 && (prm->corr_den <= 0 || prm->corr_num <= 0 || prm->corr_num > prm->corr_den)))
         return -1;
 
     int32_t *colour0 = (int32_t *)malloc(sizeof(int32_t) * ((size_t)n0 + 1));
@@ -629,13 +632,15 @@ int or_solve(int32_t n0, const int32_t *row_ptr0, const int32_t *col0, const int
         int8_t *bstate = best_state + (int64_t)st * n0;
         memset(fmap, 0, (size_t)n0);
         best_e[st] = INT64_MAX;
-        int32_t phase = 0;
+        int32_t phase = 0;    /* every phase: the RNG phase word and the record slot */
+        int32_t fphase = 0;   /* SPVAR fixing phases done */
         int32_t nlog = 0;
+        /* correlation step first, for a zero-bias problem */
+        int corr = prm->corr_sample_size > 0 && all_zero(n, hh[0]);
 
         for (;;) {
-            int fixing = phase < prm->max_fix_phases &&
-                         (phase == 0 || (prm->iterate && n > 0));
-            int32_t S = fixing ? prm->fixing_sample_size : prm->solving_sample_size;
+            int fixing = corr || (fphase < prm->max_fix_phases && (fphase == 0 || (prm->iterate && n > 0)));
+            int32_t S = corr ? prm->corr_sample_size : fixing ? prm->fixing_sample_size : prm->solving_sample_size;
             if (!fixing && S == 0) break;
             rc = or_sample(n, rp[b], cl[b], vl[b], hh[b], co[b], ncol, prm->num_sweeps, thr, dmax,
                            0, S, seed, (uint32_t)(prm->start0 + st), (uint32_t)phase, spins, e, NULL);
@@ -659,16 +664,26 @@ int or_solve(int32_t n0, const int32_t *row_ptr0, const int32_t *col0, const int
             ++phase;
             if (!fixing) break;
 
-            int32_t k = or_elite_count(prm->elite_threshold, S);
-            int32_t canon = prm->canon < 0 ? all_zero(n, hh[b]) : prm->canon;
-            int32_t nf = or_persistence(n, rp[b], S, spins, e, k, prm->fix_num, prm->fix_den,
-                                        canon, cnt, fx, NULL);
-            if (nf == 0 && prm->iterate && n > 0) {
+            int32_t nf;
+            if (corr) {
+                /* correlation fixing: every elite row multiplied by its value at rho
+                   (so rho itself has mean +1), then the rule with the correlation
+                   threshold: |mean(s_rho s_j)| >= corr_num / corr_den */
+                int32_t k = or_elite_count(prm->corr_elite_threshold, S);
+                nf = or_persistence(n, rp[b], S, spins, e, k, prm->corr_num, prm->corr_den, 1, cnt, fx, NULL);
+            } else {
+                int32_t k = or_elite_count(prm->elite_threshold, S);
+                int32_t canon = prm->canon < 0 ? all_zero(n, hh[b]) : prm->canon;
+                nf = or_persistence(n, rp[b], S, spins, e, k, prm->fix_num, prm->fix_den, canon, cnt, fx, NULL);
+            }
+            if (!corr && nf == 0 && prm->iterate && n > 0) {
                 /* stall rule: fix the lowest-index free spin to its value in
                    the best elite sample, so every SPVAR phase makes progress */
                 or_elite(S, e, 1, elite);
                 fx[0] = spins[(int64_t)elite[0] * n + 0];
             }
+            if (corr) corr = 0;
+            else ++fphase;
             for (int32_t a = 0; a < n; ++a)
                 if (fx[a]) fmap[orig[a]] = fx[a];
             int32_t n2;

@@ -148,9 +148,19 @@ typedef struct or_params {
     int32_t start0;                /* start st uses counter word start0 + st */
     int32_t boost;                 /* 1: component boosting of the solving sample (Sec. II.C) */
     int32_t tree;                  /* 1: tree pre-processing after every SPVAR reduction (Sec. II.C) */
+    /* Correlation fixing (Sec. II.C, Alg. 2 optional step; sample split in the
+     * appendix): for a problem with every h = 0, a first phase samples
+     * corr_sample_size states, takes the corr_elite_threshold elite, fixes the
+     * reference spin rho to +1 and fixes every spin j whose elite correlation
+     * with rho has |mean(s_rho s_j)| >= corr_num / corr_den to sign(mean).
+     * 0 = off; skipped when some h != 0. */
+    int32_t corr_sample_size;
+    int32_t corr_num, corr_den;
+    double corr_elite_threshold;
 } or_params;
 
-/* Outputs (caller-allocated, P = max_fix_phases + 1, Smax = max sample size):
+/* Outputs (caller-allocated, P = max_fix_phases + 1 (+1 with corr_sample_size > 0),
+ * Smax = max sample size):
  *   energies[num_starts][P][Smax]  recorded full-problem energies
  *   counts[num_starts][P]          samples recorded in each phase slot
  *   nfree[num_starts][P]           free spins when that phase sampled
