@@ -240,6 +240,14 @@ typedef struct spvar_params {
     int32_t tree_preprocess;     /* 1: exact tree elimination after every SPVAR reduction (Sec. II.C):
                                     degree-0/1 spins fixed by their bias or inferred from their neighbour,
                                     recursively; inferred spins are restored in best_state */
+    int32_t corr_sample_size;    /* > 0: correlation fixing (Sec. II.C; Alg. 2 optional step) for a
+                                    problem whose every h is 0: a first phase of this many samples; its
+                                    corr_elite_threshold elite fixes the reference spin rho (lowest-index
+                                    spin of maximum degree) to +1 and every spin j with
+                                    |mean(s_rho s_j)| >= corr_num / corr_den to the sign of the mean.
+                                    Skipped for a problem with some h != 0.  0: off */
+    int32_t corr_num, corr_den;  /* correlation threshold corr_num / corr_den (the paper uses 1.0) */
+    double corr_elite_threshold; /* elite fraction of the correlation phase */
 } spvar_params;
 
 #define SPVAR_SWEEP_AUTO 0    /* register kernel when eligible, else general */
@@ -251,7 +259,8 @@ typedef struct spvar_params {
 #define SPVAR_FORM_BATCHED 0 /* every start of every problem in one persistent launch per phase */
 #define SPVAR_FORM_PLAIN 1   /* one start at a time, one launch per kernel and start */
 
-/* Output buffers; P = max_fix_phases + 1 phase slots, Smax = max sample
+/* Output buffers; P = max_fix_phases + 1 phase slots (+1 when
+ * corr_sample_size > 0: the correlation phase is slot 0), Smax = max sample
  * size, n_p = spins of problem p.  Rows are ordered problem-major then
  * start.  Any pointer may be NULL (not written).  device = 1: pointers are
  * device memory written on the stream without synchronising; device = 0:

@@ -582,6 +582,7 @@ int or_solve(int32_t n0, const int32_t *row_ptr0, const int32_t *col0, const int
     int32_t Smax = prm->fixing_sample_size > prm->solving_sample_size
                        ? prm->fixing_sample_size : prm->solving_sample_size;
     if (prm->corr_sample_size > Smax) Smax = prm->corr_sample_size;
+    if (n0 < 0) return -1;
     const int64_t nnz0 = row_ptr0[n0];
     if (prm->max_fix_phases < 1 || prm->fix_den <= 0 || prm->fix_num <= 0 ||
         prm->fix_num > prm->fix_den || prm->fixing_sample_size < 1 || prm->solving_sample_size < 0 ||

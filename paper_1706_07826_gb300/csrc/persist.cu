@@ -297,7 +297,7 @@ __global__ void __launch_bounds__(256) k_slots_init(Slot *slots, SolveConsts C)
         s.cur = s.orig_prob;
         s.next = 0;
         s.ocur = 0;
-        s.mode = kFixing;
+        s.mode = (C.S_corr > 0 && s.orig_prob->hzero) ? kCorr : kFixing;
         s.phase = 0;
         s.fix_done = 0;
         s.nfixed = 0;
@@ -321,7 +321,7 @@ __global__ void __launch_bounds__(kBigBlock)
         if (si < C.nslots) {
             Slot &s = slots[si];
             if (s.mode != kDone) {
-                const int S = (s.mode == kFixing) ? C.S_fix : C.S_solve;
+                const int S = phase_samples(C, s.mode);
                 SweepJob j;
                 j.prob = s.cur;
                 j.spins = s.spins;
@@ -371,8 +371,8 @@ __global__ void __launch_bounds__(kBigBlock) k_elite_slots(Slot *slots, SolveCon
     __shared__ int s_better;
     Slot &s = slots[blockIdx.x];
     if (s.mode == kDone) return;
-    const int S = (s.mode == kFixing) ? C.S_fix : C.S_solve;
-    const int k = (s.mode == kFixing) ? C.k_fix : 1;
+    const int S = phase_samples(C, s.mode);
+    const int k = (s.mode == kFixing) ? C.k_fix : (s.mode == kCorr) ? C.k_corr : 1;
     const int64_t *e = s.rec_e + (size_t)s.phase * C.Smax;
     elite_core(e, S, k, s.elite, s_key);
     const int rbest = s.elite[0];
@@ -402,9 +402,16 @@ __global__ void __launch_bounds__(kBigBlock) k_elite_slots(Slot *slots, SolveCon
 __global__ void __launch_bounds__(kCountBlock) k_count_slots(Slot *slots, SolveConsts C)
 {
     Slot &s = slots[blockIdx.y];
-    if (s.mode != kFixing) return;
+    if (s.mode != kFixing && s.mode != kCorr) return;
     const DevProb *P = s.cur;
     if ((int)(blockIdx.x * blockDim.x) >= P->n) return;
+    if (s.mode == kCorr) {
+        // correlation fixing: elite rows multiplied by their value at rho, then the
+        // rule with the correlation threshold
+        count_core(P, s.spins, s.W0, s.elite, C.k_corr, 1, C.corr_num, C.corr_den, s.counts, s.fixed,
+                   &s.nfixed, s.fmap, s.orig[s.ocur]);
+        return;
+    }
     const int canon = (C.canon < 0) ? P->hzero : C.canon;
     count_core(P, s.spins, s.W0, s.elite, C.k_fix, canon, C.fix_num, C.fix_den, s.counts, s.fixed,
                &s.nfixed, s.fmap, s.orig[s.ocur]);
@@ -428,7 +435,7 @@ __global__ void __launch_bounds__(kBigBlock) k_reduce_slots(Slot *slots, SolveCo
     const DevProb *P = s.cur;
     const int n = P->n;
     const int32_t *orig = s.orig[s.ocur];
-    if (threadIdx.x == 0 && C.iterate && s.nfixed == 0 && n > 0) {
+    if (threadIdx.x == 0 && mode == kFixing && C.iterate && s.nfixed == 0 && n > 0) {
         // nothing fixed: fix the lowest-index spin to its value in the best
         // elite sample so that every SPVAR phase makes progress
         const uint32_t w = s.spins[(size_t)s.elite[0] * s.W0];
@@ -463,10 +470,14 @@ __global__ void __launch_bounds__(kBigBlock) k_reduce_slots(Slot *slots, SolveCo
         s.next = next2;
         s.ocur = ocur2;
         s.phase += 1;
-        s.fix_done += 1;
         *s.nphases = s.phase;
-        if (C.iterate && m > 0 && s.fix_done < C.max_fix) s.mode = kFixing;
-        else s.mode = (C.S_solve > 0) ? kSolving : kDone;
+        if (mode == kCorr) {
+            s.mode = kFixing;  // the SPVAR phases follow the correlation phase
+        } else {
+            s.fix_done += 1;
+            if (C.iterate && m > 0 && s.fix_done < C.max_fix) s.mode = kFixing;
+            else s.mode = (C.S_solve > 0) ? kSolving : kDone;
+        }
     }
 }
 

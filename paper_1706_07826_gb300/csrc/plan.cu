@@ -334,11 +334,12 @@ int spvar_plan_create(const spvar_problem *const *problems, int32_t nproblems,
         p.canon < -1 || p.canon > 1 || (p.form != SPVAR_FORM_BATCHED && p.form != SPVAR_FORM_PLAIN) ||
         p.replicas_per_block < 0 || (p.replicas_per_block % 4) != 0 || p.sweep_kernel < 0 ||
         p.sweep_kernel > 4 || p.start_offset < 0 || p.component_boost < 0 || p.component_boost > 1 || p.tree_preprocess < 0 || p.tree_preprocess > 1 || (p.sweep_block != 0 && p.sweep_block != 128 && p.sweep_block != 256 &&
-                               p.sweep_block != 512 && p.sweep_block != 1024))
+                               p.sweep_block != 512 && p.sweep_block != 1024) ||
+        check_corr_params(p) != SPVAR_OK)
         return SPVAR_EINVAL;
-    const int Smax = std::max(p.fixing_sample_size, p.solving_sample_size);
+    const int Smax = std::max(std::max(p.fixing_sample_size, p.solving_sample_size), p.corr_sample_size);
     if (Smax > SPVAR_MAX_SAMPLES || p.num_sweeps > SPVAR_MAX_SWEEPS ||
-        p.max_fix_phases + 1 > SPVAR_MAX_PHASE)
+        p.max_fix_phases + 2 > SPVAR_MAX_PHASE)
         return SPVAR_ELIMIT;
     spvar_plan *pl = new (std::nothrow) spvar_plan();
     if (!pl) return SPVAR_ENOMEM;
@@ -362,29 +363,15 @@ int spvar_plan_create(const spvar_problem *const *problems, int32_t nproblems,
     pl->T = p.num_sweeps;
     pl->thr_stride = dmax + 1;
     pl->dmax = dmax;
-    const int P_slots = p.max_fix_phases + 1;
     const int nslots = nproblems * p.num_starts;
-    // elite count k = ceil(elite * S), clamped to [1, S]
-    const double x = std::ceil(p.elite_threshold * (double)p.fixing_sample_size);
-    int kfix = (x >= (double)p.fixing_sample_size) ? p.fixing_sample_size : (int)x;
-    kfix = std::max(1, std::min(kfix, p.fixing_sample_size));
     SolveConsts &C = pl->C;
-    C.S_fix = p.fixing_sample_size;
-    C.S_solve = p.solving_sample_size;
-    C.k_fix = kfix;
-    C.iterate = p.iterate ? 1 : 0;
-    C.max_fix = p.max_fix_phases;
-    C.canon = p.canon;
-    C.fix_num = p.fix_num;
-    C.fix_den = p.fix_den;
-    C.P = P_slots;
-    C.Smax = Smax;
+    fill_solve_consts(p, C);
+    const int P_slots = C.P;
     C.Q = 1;
     C.nslots = nslots;
-    C.boost = p.component_boost;
     C.max_n0 = pl->max_n0;
-    C.tree = p.tree_preprocess;
-    pl->iters_max = (p.iterate ? p.max_fix_phases : 1) + (p.solving_sample_size > 0 ? 1 : 0);
+    pl->iters_max = (p.corr_sample_size > 0 ? 1 : 0) + (p.iterate ? p.max_fix_phases : 1) +
+                    (p.solving_sample_size > 0 ? 1 : 0);
 
     // workspace layout
     size_t off = 0;

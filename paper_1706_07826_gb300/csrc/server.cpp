@@ -358,11 +358,11 @@ int spvar_server_create(const spvar_server_config *cfg, spvar_server **out)
         !(p.elite_threshold > 0.0) || !(p.elite_threshold <= 1.0) || !(p.beta0 > 0.0) || !(p.beta1 > 0.0) ||
         p.canon < -1 || p.canon > 1 || p.start_offset < 0 || p.component_boost < 0 || p.component_boost > 1 || p.tree_preprocess < 0 || p.tree_preprocess > 1 || cfg->max_n < 1 || cfg->max_nnz < 0 ||
         cfg->max_degree < 1 || cfg->max_dmax < 0 || cfg->energy_scale < 1 || cfg->max_requests < 1 ||
-        cfg->budget_bytes == 0)
+        cfg->budget_bytes == 0 || check_corr_params(p) != SPVAR_OK)
         return SPVAR_EINVAL;
-    const int Smax = std::max(p.fixing_sample_size, p.solving_sample_size);
+    const int Smax = std::max(std::max(p.fixing_sample_size, p.solving_sample_size), p.corr_sample_size);
     if (cfg->max_n > SPVAR_MAX_N || cfg->max_degree > SPVAR_MAX_DEGREE || Smax > SPVAR_MAX_SAMPLES ||
-        p.num_sweeps > SPVAR_MAX_SWEEPS || p.max_fix_phases + 1 > SPVAR_MAX_PHASE)
+        p.num_sweeps > SPVAR_MAX_SWEEPS || p.max_fix_phases + 2 > SPVAR_MAX_PHASE)
         return SPVAR_ELIMIT;
     spvar_server *S = new (std::nothrow) spvar_server();
     if (!S) return SPVAR_ENOMEM;
@@ -372,7 +372,7 @@ int spvar_server_create(const spvar_server_config *cfg, spvar_server **out)
     int optin = 0;
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, S->device);
     S->ns = p.num_starts;
-    S->P = p.max_fix_phases + 1;
+    S->P = p.max_fix_phases + 1 + (p.corr_sample_size > 0 ? 1 : 0);
     S->Smax = Smax;
     S->nslots = cfg->max_requests * S->ns;
     if (cudaStreamCreateWithFlags(&S->st, cudaStreamNonBlocking) != cudaSuccess ||
@@ -420,24 +420,10 @@ int spvar_server_create(const spvar_server_config *cfg, spvar_server **out)
     if (!ok) { server_free(S); return SPVAR_ECUDA; }
 
     // engine: consts and sweep shape (general kernel; layout staged in shared memory when it fits)
-    const double x = std::ceil(p.elite_threshold * (double)p.fixing_sample_size);
-    int kfix = (x >= (double)p.fixing_sample_size) ? p.fixing_sample_size : (int)x;
-    kfix = std::max(1, std::min(kfix, p.fixing_sample_size));
     PhaseEngine &E = S->E;
-    E.C.S_fix = p.fixing_sample_size;
-    E.C.S_solve = p.solving_sample_size;
-    E.C.k_fix = kfix;
-    E.C.iterate = p.iterate ? 1 : 0;
-    E.C.max_fix = p.max_fix_phases;
-    E.C.canon = p.canon;
-    E.C.fix_num = p.fix_num;
-    E.C.fix_den = p.fix_den;
-    E.C.P = S->P;
-    E.C.Smax = Smax;
+    fill_solve_consts(p, E.C);
     E.C.nslots = S->nslots;
-    E.C.boost = p.component_boost;
     E.C.max_n0 = cfg->max_n;
-    E.C.tree = p.tree_preprocess;
     int Q = p.replicas_per_block > 0 ? p.replicas_per_block / 4 : 1;
     const int blk = p.sweep_block ? p.sweep_block : 512;
     E.shape = SweepShape{0, blk, Q, 1, 0, 0};

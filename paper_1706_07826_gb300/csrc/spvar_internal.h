@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+#include <cmath>
 #include <vector>
 
 #include "spvar.h"
@@ -96,7 +98,7 @@ struct SweepLaunch {
 };
 
 // Per-start state of the multi-start driver (Alg. 2), in device memory.
-enum SlotMode : int32_t { kFixing = 0, kSolving = 1, kDone = 2 };
+enum SlotMode : int32_t { kFixing = 0, kSolving = 1, kDone = 2, kCorr = 3 };
 
 struct Slot {
     const DevProb *orig_prob;  // original problem (read-only, shared by its starts)
@@ -140,7 +142,50 @@ struct SolveConsts {
     int32_t max_fix, canon, fix_num, fix_den;
     int32_t P, Smax, Q, nslots;
     int32_t boost, max_n0, tree, pad1;
+    int32_t S_corr, k_corr, corr_num, corr_den;  // correlation phase (S_corr = 0: off)
 };
+// Samples and elite size of a slot's current phase.
+__host__ __device__ inline int phase_samples(const SolveConsts &C, int mode)
+{
+    return mode == kCorr ? C.S_corr : mode == kFixing ? C.S_fix : C.S_solve;
+}
+// Elite count k = ceil(elite * S), clamped to [1, S].
+inline int elite_count(double elite, int S)
+{
+    const double x = std::ceil(elite * (double)S);
+    const int k = (x >= (double)S) ? S : (int)x;
+    return std::max(1, std::min(k, S));
+}
+// Checks the correlation-step parameters (SPVAR_OK or SPVAR_EINVAL).
+inline int check_corr_params(const spvar_params &p)
+{
+    if (p.corr_sample_size < 0) return SPVAR_EINVAL;
+    if (p.corr_sample_size == 0) return SPVAR_OK;
+    if (p.corr_num <= 0 || p.corr_den <= 0 || p.corr_num > p.corr_den || !(p.corr_elite_threshold > 0.0) ||
+        !(p.corr_elite_threshold <= 1.0))
+        return SPVAR_EINVAL;
+    return SPVAR_OK;
+}
+// Phase-independent constants of the multi-start loop (Alg. 2) from the parameters.
+inline void fill_solve_consts(const spvar_params &p, SolveConsts &C)
+{
+    C.S_fix = p.fixing_sample_size;
+    C.S_solve = p.solving_sample_size;
+    C.k_fix = elite_count(p.elite_threshold, p.fixing_sample_size);
+    C.iterate = p.iterate ? 1 : 0;
+    C.max_fix = p.max_fix_phases;
+    C.canon = p.canon;
+    C.fix_num = p.fix_num;
+    C.fix_den = p.fix_den;
+    C.S_corr = p.corr_sample_size;
+    C.k_corr = p.corr_sample_size > 0 ? elite_count(p.corr_elite_threshold, p.corr_sample_size) : 0;
+    C.corr_num = p.corr_num;
+    C.corr_den = p.corr_den;
+    C.P = p.max_fix_phases + 1 + (p.corr_sample_size > 0 ? 1 : 0);
+    C.Smax = std::max(std::max(p.fixing_sample_size, p.solving_sample_size), p.corr_sample_size);
+    C.boost = p.component_boost;
+    C.tree = p.tree_preprocess;
+}
 // Bytes of the tree-inference log of one slot (0 when the tree step is off).
 inline size_t tree_slot_bytes(int tree, int n0)
 {

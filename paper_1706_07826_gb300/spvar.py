@@ -44,7 +44,8 @@ class Params(ctypes.Structure):
                 ("elite_threshold", ctypes.c_double), ("fix_num", i32), ("fix_den", i32),
                 ("iterate", i32), ("max_fix_phases", i32), ("canon", i32), ("form", i32),
                 ("replicas_per_block", i32), ("sweep_kernel", i32), ("sweep_block", i32), ("start_offset", i32),
-                ("component_boost", i32), ("tree_preprocess", i32)]
+                ("component_boost", i32), ("tree_preprocess", i32), ("corr_sample_size", i32),
+                ("corr_num", i32), ("corr_den", i32), ("corr_elite_threshold", ctypes.c_double)]
 
 
 class ServerConfig(ctypes.Structure):
@@ -317,10 +318,18 @@ def reduce_noalloc(problem, fixed, row_ptr, col, val, h, offset, old_of_new, n_o
 def make_params(num_starts=1, fixing_sample_size=100, solving_sample_size=100, num_sweeps=1000, beta0=0.1,
                 beta1=3.0, elite_threshold=0.1, fix_num=1, fix_den=1, iterate=False, max_fix_phases=1, canon=-1,
                 form=FORM_BATCHED, replicas_per_block=0, sweep_kernel=SWEEP_AUTO, sweep_block=0, start_offset=0,
-                component_boost=False, tree_preprocess=False):
+                component_boost=False, tree_preprocess=False, corr_sample_size=0, corr_elite_threshold=0.2,
+                corr_num=1, corr_den=1):
     return Params(num_starts, fixing_sample_size, solving_sample_size, num_sweeps, beta0, beta1, elite_threshold,
                   fix_num, fix_den, 1 if iterate else 0, max_fix_phases, canon, form, replicas_per_block,
-                  sweep_kernel, sweep_block, start_offset, 1 if component_boost else 0, 1 if tree_preprocess else 0)
+                  sweep_kernel, sweep_block, start_offset, 1 if component_boost else 0, 1 if tree_preprocess else 0,
+                  corr_sample_size, corr_num, corr_den, float(corr_elite_threshold))
+
+
+def phase_slots(params):
+    """Recorded phase slots: the SPVAR phases, the solving phase and, when
+    enabled, the correlation phase."""
+    return params.max_fix_phases + 1 + (1 if params.corr_sample_size > 0 else 0)
 
 
 @dataclasses.dataclass
@@ -364,8 +373,8 @@ class Plan:
                                        ctypes.byref(out)), "spvar_plan_create")
         self.handle = out
         self.nslots = len(self.problems) * params.num_starts
-        self.P = params.max_fix_phases + 1
-        self.Smax = max(params.fixing_sample_size, params.solving_sample_size)
+        self.P = phase_slots(params)
+        self.Smax = max(params.fixing_sample_size, params.solving_sample_size, params.corr_sample_size)
         self.fm_total = sum(p.n for p in self.problems) * params.num_starts
 
     def workspace_bytes(self):
@@ -418,8 +427,8 @@ class Plan:
 def solve(problem, params, seed, device=False, stream=None):
     """One-call Multi-start SPVAR (Alg. 2) of one problem; host outputs by default."""
     nslots = params.num_starts
-    P = params.max_fix_phases + 1
-    Smax = max(params.fixing_sample_size, params.solving_sample_size)
+    P = phase_slots(params)
+    Smax = max(params.fixing_sample_size, params.solving_sample_size, params.corr_sample_size)
     out = _alloc_outputs(nslots, P, Smax, problem.n * nslots, device)
     res = _result_struct(out, device)
     _check(lib().spvar_solve(problem.handle, ctypes.byref(params), int(seed), ctypes.byref(res), _stream(stream)),
@@ -457,8 +466,8 @@ class Server:
         _check(lib().spvar_server_create(ctypes.byref(cfg), ctypes.byref(out)), "spvar_server_create")
         self.handle = out
         self.params = params
-        self.P = params.max_fix_phases + 1
-        self.Smax = max(params.fixing_sample_size, params.solving_sample_size)
+        self.P = phase_slots(params)
+        self.Smax = max(params.fixing_sample_size, params.solving_sample_size, params.corr_sample_size)
         self.sizes = {}
 
     def submit(self, inst, seed):

@@ -206,3 +206,47 @@ def test_tree_preprocess_parity(cuda_lib, form, name, make, T, starts, Sf, Ss, e
                             elite_threshold=elite, fix_num=tau[0], fix_den=tau[1], form=form,
                             component_boost=boost, tree_preprocess=True, iterate=iterate, max_fix_phases=mf)
     _check(spvar.solve(gpu_problem(inst), prm, 6), ref, starts, mf + 1, inst.n)
+
+
+CCASES = [
+    # name, instance, T, starts, S_corr, corr_elite, S_fix, S_solve, elite, iterate, max_fix, tree, boost
+    ("chimera_C4_paper_split", lambda: I.chimera(4, 41), 80, 3, 80, 0.2, 60, 60, 0.2, False, 1, False, False),
+    ("cubic_L4_corr", lambda: I.cubic3d(4, 42), 60, 2, 64, 0.3, 48, 48, 0.2, False, 1, False, False),
+    ("cubic_L5_odd_corr_ispvar", lambda: I.cubic3d(5, 43), 50, 2, 40, 0.25, 32, 16, 0.2, True, 4, False, False),
+    ("random_zero_bias_tree_boost", lambda: I.random_graph(50, 60, 23, jmax=2, hmax=0), 50, 2, 40, 0.3, 30, 24,
+     0.25, False, 1, True, True),
+    ("random_h_skipped", lambda: I.random_graph(30, 70, 3, jmax=3, hmax=2), 40, 2, 50, 0.3, 33, 19, 0.3, False, 1,
+     False, False),
+]
+
+
+@pytest.mark.parametrize("form", [0, 1], ids=["batched", "plain"])
+@pytest.mark.parametrize("name,make,T,starts,Sc,ce,Sf,Ss,elite,iterate,mf,tree,boost", CCASES,
+                         ids=[c[0] for c in CCASES])
+def test_correlation_fixing_parity(cuda_lib, form, name, make, T, starts, Sc, ce, Sf, Ss, elite, iterate, mf, tree,
+                                   boost):
+    """Sec. II.C correlation fixing of zero-bias problems (its own phase, sample
+    size and elite threshold; skipped with bias): identical to the oracle."""
+    from paper_1706_07826_gb300 import spvar
+    inst = make()
+    ref = _oracle_solve(inst, T, 12, num_starts=starts, fixing_sample_size=Sf, solving_sample_size=Ss,
+                        elite_threshold=elite, iterate=iterate, max_fix_phases=mf, tree=tree, boost=boost,
+                        corr_sample_size=Sc, corr_elite_threshold=ce)
+    prm = spvar.make_params(num_starts=starts, fixing_sample_size=Sf, solving_sample_size=Ss, num_sweeps=T,
+                            elite_threshold=elite, iterate=iterate, max_fix_phases=mf, form=form,
+                            tree_preprocess=tree, component_boost=boost, corr_sample_size=Sc,
+                            corr_elite_threshold=ce)
+    out = spvar.solve(gpu_problem(inst), prm, 12)
+    _check(out, ref, starts, mf + 2, inst.n)
+    if not inst.h.any():
+        assert all(int(out.counts[s][0]) == Sc for s in range(starts))
+
+
+def test_correlation_fixing_rejects_bad_parameters(cuda_lib):
+    from paper_1706_07826_gb300 import spvar
+    gp = gpu_problem(I.chimera(2, 3))
+    for kw in (dict(corr_sample_size=-1), dict(corr_sample_size=8, corr_num=2, corr_den=1),
+               dict(corr_sample_size=8, corr_elite_threshold=0.0)):
+        with pytest.raises(spvar.SpvarError):
+            spvar.solve(gp, spvar.make_params(num_starts=1, fixing_sample_size=8, solving_sample_size=8,
+                                              num_sweeps=10, **kw), 1)
