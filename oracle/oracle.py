@@ -17,6 +17,7 @@ i64p = ctypes.POINTER(ctypes.c_int64)
 u32p = ctypes.POINTER(ctypes.c_uint32)
 i8p = ctypes.POINTER(ctypes.c_int8)
 f64p = ctypes.POINTER(ctypes.c_double)
+u64p = ctypes.POINTER(ctypes.c_uint64)
 
 
 class OrParams(ctypes.Structure):
@@ -61,6 +62,13 @@ def lib():
                                 ctypes.c_int32, u32p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64,
                                 ctypes.c_uint32, ctypes.c_uint32, i8p, i64p, i64p]
         L.or_sample.restype = ctypes.c_int
+        L.or_sqa_table.argtypes = [ctypes.c_int32, ctypes.c_int32, f64p, f64p, ctypes.c_int32,
+                                   ctypes.c_int32, u64p]
+        L.or_sqa_sample.argtypes = [ctypes.c_int32, i32p, i32p, i32p, i32p, i32p, ctypes.c_int32,
+                                    ctypes.c_int32, ctypes.c_int32, u64p, ctypes.c_int32, ctypes.c_int32,
+                                    ctypes.c_int32, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, i8p, i64p,
+                                    i32p]
+        L.or_sqa_sample.restype = ctypes.c_int
         L.or_elite_count.argtypes = [ctypes.c_double, ctypes.c_int32]
         L.or_elite_count.restype = ctypes.c_int32
         L.or_elite.argtypes = [ctypes.c_int32, i64p, ctypes.c_int32, i32p]
@@ -187,6 +195,43 @@ def sample(p: Csr, thr, S, seed, start=0, phase=0, colours=None, check_increment
     if rc != 0:
         raise ValueError("or_sample failed: %d" % rc)
     return spins[:S, :p.n].copy(), e[:S].copy(), (int(err[0]) if check_incremental else None)
+
+
+def sqa_table(T, P, beta, gamma, dmax_, scale=1):
+    """SQA acceptance entries [T, 3, 2 (dmax/2) + 1] (uint64; see or_sqa_table).
+    beta and gamma: one value per sweep, or a constant."""
+    beta = _c(np.broadcast_to(np.asarray(beta, np.float64), (max(T, 1),)), np.float64)
+    gamma = _c(np.broadcast_to(np.asarray(gamma, np.float64), (max(T, 1),)), np.float64)
+    W = 2 * (dmax_ // 2) + 1
+    ent = np.zeros((max(T, 1), 3, W), np.uint64)
+    lib().or_sqa_table(T, P, _p(beta, f64p), _p(gamma, f64p), dmax_, scale, _p(ent, u64p))
+    return ent[:T]
+
+
+def gamma_linear(T, gamma0, gamma1):
+    """Transverse field falling linearly from gamma0 to gamma1 (endpoints included)."""
+    if T == 1:
+        return np.array([gamma0], np.float64)
+    return gamma0 + (gamma1 - gamma0) * np.arange(T, dtype=np.float64) / (T - 1)
+
+
+def sqa_sample(p: Csr, ent, P, S, seed, start=0, phase=0, colours=None, r0=0):
+    """SQA samples (lowest-energy slice of each run): (spins int8 [S, n], e [S], slice [S])."""
+    if colours is None:
+        colours = colour(p)
+    c = _c(colours[0], np.int32) if p.n else np.zeros(1, np.int32)
+    ent = _c(ent, np.uint64)
+    T = ent.shape[0]
+    dmax_ = 2 * ((ent.shape[2] - 1) // 2)
+    spins = np.zeros((max(S, 1), max(p.n, 1)), np.int8)
+    e = np.zeros(max(S, 1), np.int64)
+    sl = np.zeros(max(S, 1), np.int32)
+    rc = lib().or_sqa_sample(p.n, _p(p.row_ptr, i32p), _p(_c(p.col, np.int32), i32p), _p(_c(p.val, np.int32), i32p),
+                             _p(p.h, i32p), _p(c, i32p), colours[1], T, P, _p(ent, u64p), dmax_, r0, S, seed,
+                             start, phase, _p(spins, i8p), _p(e, i64p), _p(sl, i32p))
+    if rc != 0:
+        raise ValueError("or_sqa_sample failed: %d" % rc)
+    return spins[:S, :p.n], e[:S], sl[:S]
 
 
 def elite_count(elite, S):

@@ -259,6 +259,97 @@ int or_sample(int32_t n, const int32_t *row_ptr, const int32_t *col, const int32
 }
 
 /* ---------------------------------------------------------------------- */
+/* Simulated quantum annealing (discrete-time path integral)                */
+/* ---------------------------------------------------------------------- */
+void or_sqa_table(int32_t T, int32_t P, const double *beta, const double *gamma, int32_t dmax, int32_t scale,
+                  uint64_t *ent)
+{
+    const int32_t bias = dmax / 2, W = 2 * bias + 1;
+    for (int32_t t = 0; t < T; ++t) {
+        /* slice coupling of this sweep (none for a single slice) */
+        double jp = (P > 1) ? -0.5 * log(tanh(beta[t] * gamma[t] / (double)P)) : 0.0;
+        for (int32_t a = 0; a < 3; ++a) {
+            for (int32_t k = 0; k < W; ++k) {
+                double dA = (2.0 * beta[t] / (double)P) * (double)(k - bias) / (double)scale +
+                            4.0 * jp * (double)(a - 1);
+                double x = floor(ldexp(exp(-dA), 32));
+                uint64_t thr = (x >= 4294967296.0) ? (1ull << 32) : (uint64_t)x;
+                ent[((int64_t)t * 3 + a) * W + k] = (1ull << 32) - thr;
+            }
+        }
+    }
+}
+
+int or_sqa_sample(int32_t n, const int32_t *row_ptr, const int32_t *col, const int32_t *val,
+                  const int32_t *h, const int32_t *colour, int32_t ncol,
+                  int32_t T, int32_t P, const uint64_t *ent, int32_t dmax,
+                  int32_t r0, int32_t S, uint64_t seed, uint32_t start, uint32_t phase,
+                  int8_t *spins, int64_t *e, int32_t *slice)
+{
+    if (T < 0 || (uint32_t)T >= INIT_SLOT || phase >= (1u << 12) || S < 0 || r0 < 0 || P < 1 ||
+        (P > 1 && (P & 1)) || P > 1024 || n >= (1 << 16))
+        return -1;
+    const int32_t bias = dmax / 2, W = 2 * bias + 1;
+    int32_t *order = (int32_t *)malloc(sizeof(int32_t) * ((size_t)n + 1));
+    int32_t *cstart = (int32_t *)malloc(sizeof(int32_t) * ((size_t)ncol + 2));
+    int32_t m = 0;
+    for (int32_t c = 0; c < ncol; ++c) {
+        cstart[c] = m;
+        for (int32_t i = 0; i < n; ++i)
+            if (colour[i] == c) order[m++] = i;
+    }
+    cstart[ncol] = m;
+    int8_t *x = (int8_t *)malloc((size_t)P * (size_t)n + 1); /* x[tau*n + i] */
+    if (m != n) { free(order); free(cstart); free(x); return -1; }
+    int rc = 0;
+    for (int32_t row = 0; row < S && rc == 0; ++row) {
+        const int32_t r = r0 + row;
+        for (int32_t tau = 0; tau < P; ++tau)
+            for (int32_t i = 0; i < n; ++i)
+                x[(int64_t)tau * n + i] =
+                    (rng_word(seed, start, phase, INIT_SLOT, i | (tau << 16), r) >> 31) ? 1 : -1;
+        for (int32_t t = 0; t < T && rc == 0; ++t) {
+            for (int32_t c = 0; c < ncol && rc == 0; ++c) {
+                for (int32_t par = 0; par < (P > 1 ? 2 : 1) && rc == 0; ++par) {
+                    for (int32_t tau = par; tau < P && rc == 0; tau += 2) {
+                        int8_t *s = x + (int64_t)tau * n;
+                        const int8_t *up = x + (int64_t)((tau + 1) % P) * n;
+                        const int8_t *dn = x + (int64_t)((tau + P - 1) % P) * n;
+                        for (int32_t q = cstart[c]; q < cstart[c + 1]; ++q) {
+                            const int32_t i = order[q];
+                            int64_t f = h[i];
+                            for (int32_t p = row_ptr[i]; p < row_ptr[i + 1]; ++p)
+                                f += (int64_t)val[p] * s[col[p]];
+                            const int64_t dE = -2 * (int64_t)s[i] * f;
+                            if (dE > dmax || dE < -dmax) { rc = -2; break; }
+                            const int32_t k = (int32_t)(dE / 2) + bias;
+                            const int32_t a = (P > 1) ? (up[i] == s[i]) + (dn[i] == s[i]) : 1;
+                            const uint64_t en = ent[((int64_t)t * 3 + a) * W + k];
+                            const uint32_t u = rng_word(seed, start, phase, (uint32_t)t, i | (tau << 16), r);
+                            if ((uint64_t)u + en < (1ull << 32)) s[i] = (int8_t)-s[i];
+                        }
+                    }
+                }
+            }
+        }
+        /* the run's sample: its lowest-energy slice */
+        int64_t best = 0;
+        int32_t bt = 0;
+        for (int32_t tau = 0; tau < P; ++tau) {
+            int64_t Et = or_energy(n, row_ptr, col, val, h, x + (int64_t)tau * n);
+            if (tau == 0 || Et < best) { best = Et; bt = tau; }
+        }
+        memcpy(spins + (int64_t)row * n, x + (int64_t)bt * n, (size_t)n);
+        e[row] = best;
+        slice[row] = bt;
+    }
+    free(order);
+    free(cstart);
+    free(x);
+    return rc;
+}
+
+/* ---------------------------------------------------------------------- */
 /* Persistence (Alg. 1)                                                     */
 /* ---------------------------------------------------------------------- */
 int32_t or_elite_count(double elite, int32_t S)

@@ -75,6 +75,35 @@ int or_sample(int32_t n, const int32_t *row_ptr, const int32_t *col, const int32
               int32_t r0, int32_t S, uint64_t seed, uint32_t start, uint32_t phase,
               int8_t *spins, int64_t *e, int64_t *incr_err);
 
+/* ---- Simulated quantum annealing (SQA, Sec. III: discrete-time path-integral
+ * Monte Carlo of the transverse-field Ising model, a second sampler for Alg. 1).
+ * P Trotter slices s^tau (tau = 0..P-1, periodic), weight exp(-A) with
+ *   A(s) = (beta/P) sum_tau E(s^tau)/scale - Jp sum_tau sum_i s_i^tau s_i^(tau+1),
+ *   Jp(t) = -1/2 ln tanh(beta Gamma_t / P);
+ * P = 1 has no slice coupling (classical).  Flipping s_i^tau changes A by
+ *   dA = (2 beta / P) (k - bias) / scale + 4 Jp (a - 1),
+ * k = dE/2 + bias (bias = dmax/2; dE the classical flip cost in slice tau) and
+ * a = number of the two slice neighbours equal to s_i^tau (a = 1 when P = 1).
+ * Metropolis acceptance min(1, exp(-dA)) with a 32-bit uniform u, as a carry:
+ *   ent[(t*3 + a)*W + k] = 2^32 - min(2^32, floor(2^32 exp(-dA)))   (W = 2 bias + 1)
+ * and the move is accepted iff u + ent < 2^32 (ent = 0: always).
+ * beta[T], gamma[T]: inverse temperature and transverse field of each sweep
+ * (quantum annealing: beta constant, gamma falling). */
+void or_sqa_table(int32_t T, int32_t P, const double *beta, const double *gamma, int32_t dmax, int32_t scale,
+                  uint64_t *ent);
+
+/* SQA samples of replicas r0..r0+S-1 (P even, or P = 1).  Random word of
+ * spin i in slice tau: the SA counter with spin word i | tau << 16.  Sweep:
+ * colour classes in order; inside a class the even slices, then the odd
+ * slices; indices ascending.  The sample of a run is its lowest-energy slice
+ * (lowest tau on ties): spins[S][n], e[S] (without offset), slice[S].
+ * Returns 0, -1 on bad arguments, -2 if a flip cost exceeds dmax. */
+int or_sqa_sample(int32_t n, const int32_t *row_ptr, const int32_t *col, const int32_t *val,
+                  const int32_t *h, const int32_t *colour, int32_t ncol,
+                  int32_t T, int32_t P, const uint64_t *ent, int32_t dmax,
+                  int32_t r0, int32_t S, uint64_t seed, uint32_t start, uint32_t phase,
+                  int8_t *spins, int64_t *e, int32_t *slice);
+
 /* Elite sample size k = ceil(elite * S), clamped to [1, S] (Alg. 1). */
 int32_t or_elite_count(double elite, int32_t S);
 
