@@ -159,6 +159,40 @@ int spvar_sample_range(const spvar_problem *p, int32_t sweep_begin, int32_t swee
                        int64_t *energies, void *stream);
 
 /* ------------------------------------------------------------------ */
+/* Simulated quantum annealing: a second sampler for Alg. 1 (Sec. III:  */
+/* discrete-time path-integral Monte Carlo of the transverse-field     */
+/* Ising model)                                                         */
+/* ------------------------------------------------------------------ */
+
+#define SPVAR_SQA_MAX_SLICES 1024
+
+/* Acceptance entries of the path-integral sweep, host -> host.
+ * P Trotter slices (1, or even), beta[T] and gamma[T] the inverse temperature
+ * and transverse field of each sweep.  With bias = dmax / 2, W = 2 bias + 1,
+ * Jp = -1/2 ln tanh(beta gamma / P) (0 when P = 1) and, for flip-cost index
+ * k = dE/2 + bias and a = number of the spin's two slice neighbours equal to
+ * it (a = 1 when P = 1),
+ *   dA = (2 beta / P) (k - bias) / scale + 4 Jp (a - 1),
+ *   ent[(t*3 + a)*W + k] = 2^32 - min(2^32, floor(2^32 exp(-dA)))   (double).
+ * A move is accepted iff u + ent < 2^32 (u the 32-bit uniform).  ent: host
+ * [T][3][W].  EINVAL on a bad P, T, dmax or scale, or gamma <= 0 with P > 1. */
+int spvar_sqa_table(int32_t T, int32_t P, const double *beta, const double *gamma, int32_t dmax,
+                    int32_t energy_scale, uint64_t *ent);
+
+/* num_samples SQA runs of the problem (each returns its lowest-energy slice,
+ * lowest slice index on ties).  ent: device [num_sweeps][3][W] from
+ * spvar_sqa_table for a dmax >= the problem's (W = 2 (dmax/2) + 1).  Counters
+ * as spvar_sample with spin word i | tau << 16 for slice tau; sweep = colour
+ * classes in order, even slices then odd slices inside each.  spins: device
+ * [num_samples][ceil(n/32)]; energies: device [num_samples] (with offset);
+ * slice: device [num_samples] (chosen slice) or NULL.  Asynchronous on stream.
+ * Errors: EINVAL (bad P or table width), ELIMIT (the P slices do not fit in
+ * shared memory), ECUDA. */
+int spvar_sqa_sample(const spvar_problem *p, int32_t num_sweeps, int32_t P, const uint64_t *ent, int32_t W,
+                     int32_t num_samples, uint64_t seed, uint32_t start, uint32_t phase, uint32_t *spins,
+                     int64_t *energies, int32_t *slice, void *stream);
+
+/* ------------------------------------------------------------------ */
 /* Persistence (Alg. 1: elite sample, mean value, fixing rule)          */
 /* ------------------------------------------------------------------ */
 /* k = ceil(elite_threshold * num_samples) (clamped to [1, num_samples])

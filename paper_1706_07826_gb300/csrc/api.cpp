@@ -470,6 +470,68 @@ int spvar_sample_range(const spvar_problem *p, int32_t sweep_begin, int32_t swee
     return SPVAR_OK;
 }
 
+int spvar_sqa_table(int32_t T, int32_t P, const double *beta, const double *gamma, int32_t dmax,
+                    int32_t energy_scale, uint64_t *ent)
+{
+    if (T < 0 || P < 1 || (P > 1 && (P & 1)) || P > SPVAR_SQA_MAX_SLICES || dmax < 0 || energy_scale < 1 ||
+        (T > 0 && (!beta || !gamma || !ent)))
+        return SPVAR_EINVAL;
+    const int32_t bias = dmax / 2, W = 2 * bias + 1;
+    for (int32_t t = 0; t < T; ++t) {
+        if (P > 1 && !(gamma[t] > 0.0)) return SPVAR_EINVAL;
+        // coupling of neighbouring slices in this sweep (none for one slice)
+        const double jp = (P > 1) ? -0.5 * std::log(std::tanh(beta[t] * gamma[t] / (double)P)) : 0.0;
+        for (int32_t a = 0; a < 3; ++a)
+            for (int32_t k = 0; k < W; ++k) {
+                const double dA = (2.0 * beta[t] / (double)P) * (double)(k - bias) / (double)energy_scale +
+                                  4.0 * jp * (double)(a - 1);
+                const double x = std::floor(std::ldexp(std::exp(-dA), 32));
+                const uint64_t thr = (x >= 4294967296.0) ? (1ull << 32) : (uint64_t)x;
+                ent[((size_t)t * 3 + a) * W + k] = (1ull << 32) - thr;
+            }
+    }
+    return SPVAR_OK;
+}
+
+int spvar_sqa_sample(const spvar_problem *p, int32_t num_sweeps, int32_t P, const uint64_t *ent, int32_t W,
+                     int32_t num_samples, uint64_t seed, uint32_t start, uint32_t phase, uint32_t *spins,
+                     int64_t *energies, int32_t *slice, void *stream)
+{
+    if (!p) return SPVAR_EINVAL;
+    const Problem *Pr = reinterpret_cast<const Problem *>(p);
+    const DevProb &H = Pr->hdr;
+    if (num_sweeps < 0 || num_samples < 0 || phase > SPVAR_MAX_PHASE || P < 1 || (P > 1 && (P & 1)) ||
+        P > SPVAR_SQA_MAX_SLICES || W < 1 || (W & 1) == 0 || W - 1 < H.dmax)
+        return SPVAR_EINVAL;
+    if (num_sweeps > SPVAR_MAX_SWEEPS || num_samples > SPVAR_MAX_SAMPLES) return SPVAR_ELIMIT;
+    if (num_samples == 0) return SPVAR_OK;
+    if ((num_sweeps > 0 && !ent) || !energies || (H.n > 0 && !spins)) return SPVAR_EINVAL;
+    const bool pm1 = H.pm1 != 0 && sqa_shape_ok(true, 256, H.n, P, W);
+    if (!sqa_shape_ok(pm1, 256, H.n, P, W)) return SPVAR_ELIMIT;
+    const size_t smem = sqa_smem_bytes(H.n, P, H.maxdeg, pm1);
+    if (smem > (size_t)device_smem_optin()) return SPVAR_ELIMIT;
+    SweepLaunch L;
+    std::memset(&L, 0, sizeof(L));
+    L.single.prob = Pr->dev;
+    L.single.spins = spins;
+    L.single.energies = energies;
+    L.single.seed = seed;
+    L.single.S = num_samples;
+    L.single.W = ceil_div(std::max(H.n, 0), 32);
+    L.single.start = start;
+    L.single.phase = phase;
+    L.T = num_sweeps;
+    L.Q = 1;
+    L.max_n = H.n;
+    L.max_deg = H.maxdeg;
+    L.ent = reinterpret_cast<const unsigned long long *>(ent);
+    L.P = P;
+    L.W = W;
+    L.slice_out = slice;
+    SPVAR_CUDA_TRY(launch_sweep_sqa(L, pm1, 256, ceil_div(num_samples, 4), smem, as_stream(stream)));
+    return SPVAR_OK;
+}
+
 int spvar_persistence(const spvar_problem *p, int32_t num_samples, const uint32_t *spins,
                       const int64_t *energies, double elite_threshold, int32_t fix_num,
                       int32_t fix_den, int32_t canon, int32_t *elite, int32_t *counts,

@@ -95,6 +95,10 @@ struct SweepLaunch {
     int32_t thr_stride, T, Q, stage_ell;
     int32_t max_n;          // largest n of any job (shared-memory carve-up)
     int32_t max_deg;        // largest maxdeg of any job (staged ELL size)
+    // simulated quantum annealing: acceptance entries [T][3][W], Trotter slices, chosen slice per sample
+    const unsigned long long *ent;
+    int32_t P, W;
+    int32_t *slice_out;
 };
 
 // Per-start state of the multi-start driver (Alg. 2), in device memory.
@@ -240,6 +244,14 @@ size_t pm1_smem_bytes(int max_n, int Q);
 cudaError_t launch_sweep_pm1(const SweepLaunch &L, int block, int nslot, int maxd, int grid, size_t smem,
                              cudaStream_t st);
 int pm1_max_active_blocks(int block, int nslot, int maxd, size_t smem);
+
+// Simulated quantum annealing sweep (sweep_sqa.cu): one quad per work item, all
+// Trotter slices in shared memory.
+constexpr int kSqaMaxSlices = 1024;
+bool sqa_shape_ok(bool pm1, int block, int max_n, int P, int W);
+size_t sqa_smem_bytes(int max_n, int P, int maxdeg, bool pm1);
+cudaError_t launch_sweep_sqa(const SweepLaunch &L, bool pm1, int block, int grid, size_t smem, cudaStream_t st);
+int sqa_max_active_blocks(bool pm1, int block, size_t smem);
 
 // Streaming +-1 sweep (sweep_pm1s.cu): one quad per work item.
 bool pm1s_shape_ok(int block, int maxd, int max_n, int Q);

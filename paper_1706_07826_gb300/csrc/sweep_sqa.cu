@@ -1,0 +1,243 @@
+// Simulated quantum annealing sweep: the second sampler for Alg. 1 ("obtain
+// sample"), discrete-time path-integral Monte Carlo of the transverse-field
+// Ising model (the SQA sampler of Sec. III).
+//
+// A run keeps P Trotter slices s^tau (tau = 0..P-1, periodic) of the
+// problem.  Flipping s_i^tau changes the path-integral action by
+//   dA = (2 beta / P) (k - bias) / scale + 4 Jp (a - 1),
+// with k = dE/2 + bias (dE the classical flip cost inside slice tau) and a
+// the number of its two slice neighbours s_i^(tau+-1) equal to s_i^tau
+// (a = 1 for a single slice).  The host tabulates, per sweep, the 64-bit
+// entry 2^32 - min(2^32, floor(2^32 exp(-dA))) for every (a, k); a move is
+// accepted iff u + entry < 2^32 for the replica's uniform word u.
+//
+// One CTA anneals one quad (four independent runs, one byte lane each).  All
+// P slices live in shared memory (and, for +-1 couplers, a copy with every
+// replica bit inverted, so that J < 0 neighbours are read pre-negated and the
+// local field of four replicas is one byte-wise sum).  A sweep visits the
+// colour classes in order and, inside a class, the even slices and then the
+// odd ones: no two spins updated together are coupled in space or in
+// imaginary time, so the parallel sweep equals visiting them one at a time.
+// The random word of spin i in slice tau uses the counter of the SA sweep
+// with spin word i | tau << 16.  A run's sample is its lowest-energy slice.
+#include "sweep_common.cuh"
+
+namespace spvar {
+
+namespace {
+
+// Words of shared memory: spin words (and their inverted copy), 16-bit
+// neighbour offsets (+-1 only), per-slice energy sums and the chosen slices.
+__host__ __device__ inline size_t sqa_words(int max_n, int P, int maxdeg, bool pm1)
+{
+    size_t w = (size_t)P * max_n * (pm1 ? 2 : 1);
+    if (pm1) w += ((size_t)maxdeg * max_n + 1) / 2;
+    return w + 4 * (size_t)P + 4;
+}
+
+template <bool PM1, int B>
+__device__ void run_item_sqa(const SweepLaunch &L, const SweepJob &job, int quad, uint32_t *smem)
+{
+    const int tid = threadIdx.x;
+    const DevProb *pr = job.prob;
+    const int n = pr->n, ncol = pr->ncol, cap_n = pr->cap_n, maxdeg = pr->maxdeg;
+    const int P = L.P, W = L.W, bias = (L.W - 1) / 2;
+    const int T = L.T;
+    const uint32_t k0 = (uint32_t)job.seed, k1 = (uint32_t)(job.seed >> 32);
+    const uint32_t phase_hi = job.phase << kSweepBits;
+    const size_t Pn = (size_t)P * n;
+
+    uint32_t *sw = smem;                                   // [P][n] plain
+    uint32_t *swi = sw + (PM1 ? Pn : 0);                   // [P][n] inverted (+-1 only)
+    uint16_t *off = reinterpret_cast<uint16_t *>(sw + (PM1 ? 2 * Pn : Pn));
+    int *e2 = reinterpret_cast<int *>(sw + (PM1 ? 2 * Pn + ((size_t)maxdeg * n + 1) / 2 : Pn));
+    int *s_best = e2 + 4 * P;
+    __shared__ int s_cptr[kMaxColours + 1];
+
+    for (int c = tid; c <= ncol; c += B) s_cptr[c] = pr->cptr[c];
+    // initial state: top bit of the word at the initial-state slot, per slice
+    for (size_t x = tid; x < Pn; x += B) {
+        const int tau = (int)(x / n), p = (int)(x - (size_t)tau * n);
+        const uint32_t i = (uint32_t)pr->idx_of_pos[p] | ((uint32_t)tau << 16);
+        const uint4 r = philox4x32_10(make_uint4(i, (job.phase << kSweepBits) | kInitSlot, (uint32_t)quad, job.start),
+                                      k0, k1);
+        const uint32_t w = (r.x >> 31) | ((r.y >> 31) << 8) | ((r.z >> 31) << 16) | ((r.w >> 31) << 24);
+        sw[x] = w;
+        if (PM1) swi[x] = w ^ 0x01010101u;
+    }
+    if (PM1) {
+        for (int x = tid; x < maxdeg * n; x += B) {
+            const int d = x / n, p = x - d * n;
+            const uint32_t e = pr->ell[(size_t)d * cap_n + p];
+            off[x] = (uint16_t)(((e >> 31) ? (int)Pn : 0) + (int)(e & 0xFFFFu));
+        }
+    }
+    __syncthreads();
+
+    const int nt = (P > 1) ? P / 2 : 1;  // slices per parity
+    for (int t = 0; t < T; ++t) {
+        const unsigned long long *ent = L.ent + (size_t)t * 3 * W;
+        const uint32_t y = phase_hi | (uint32_t)t;
+        for (int c = 0; c < ncol; ++c) {
+            const int lo = s_cptr[c], nc = s_cptr[c + 1] - lo;
+            for (int par = 0; par < (P > 1 ? 2 : 1); ++par) {
+                for (int it = tid; it < nc * nt; it += B) {
+                    const int tq = it / nc;
+                    const int p = lo + (it - tq * nc);
+                    const int tau = par + 2 * tq;
+                    const size_t base = (size_t)tau * n;
+                    const uint32_t own = sw[base + p];
+                    const uint32_t meta = __ldg(pr->meta + p);
+                    const int deg = (int)(meta & 0xFFFFu);
+                    const int h = (int)meta >> 16;
+                    // a per byte: slice neighbours equal to the spin (1 for a single slice)
+                    uint32_t a4 = 0x01010101u;
+                    if (P > 1) {
+                        const uint32_t up = sw[(size_t)(tau + 1 == P ? 0 : tau + 1) * n + p];
+                        const uint32_t dn = sw[(size_t)(tau == 0 ? P - 1 : tau - 1) * n + p];
+                        a4 = (~(own ^ up) & 0x01010101u) + (~(own ^ dn) & 0x01010101u);
+                    }
+                    int idx[4];
+                    if (PM1) {
+                        // byte r of x: neighbours with b_j ^ [J_ij < 0] = 1; k = 2x + bias - deg + h
+                        // for b_i = 0 and its mirror 2 bias - that for b_i = 1
+                        uint32_t x = 0;
+                        for (int d = 0; d < deg; ++d) x += sw[base + off[d * n + p]];
+                        const uint32_t m = own * 0xFFu;
+                        const uint32_t c0 = (uint32_t)(bias - deg + h) * 0x01010101u;
+                        const uint32_t c1 = (uint32_t)(bias + deg - h) * 0x01010101u;
+                        const uint32_t k4 = ((x + x + c0) & ~m) | ((c1 - x - x) & m);
+                        const uint32_t full = a4 * (uint32_t)W + k4;  // bytes <= 3W - 1 <= 255
+#pragma unroll
+                        for (int r = 0; r < 4; ++r) idx[r] = (int)((full >> (8 * r)) & 0xFFu);
+                    } else {
+                        int acc[4] = {0, 0, 0, 0}, sumJ = 0;
+                        for (int d = 0; d < deg; ++d) {
+                            const uint32_t e = __ldg(pr->ell + (size_t)d * cap_n + p);
+                            const int Jv = (int)e >> 16;
+                            const uint32_t w = sw[base + (e & 0xFFFFu)];
+                            sumJ += Jv;
+#pragma unroll
+                            for (int r = 0; r < 4; ++r) acc[r] += Jv * (int)((w >> (8 * r)) & 1u);
+                        }
+#pragma unroll
+                        for (int r = 0; r < 4; ++r) {
+                            // f = h + sum_j J s_j; k = dE/2 + bias = bias - s f
+                            const int f = h - sumJ + 2 * acc[r];
+                            const int s = 2 * (int)((own >> (8 * r)) & 1u) - 1;
+                            idx[r] = (int)((a4 >> (8 * r)) & 0xFFu) * W + bias - s * f;
+                        }
+                    }
+                    const uint32_t i = (uint32_t)__ldg(pr->idx_of_pos + p) | ((uint32_t)tau << 16);
+                    const uint4 u = philox4x32_10(make_uint4(i, y, (uint32_t)quad, job.start), k0, k1);
+                    const uint32_t ur[4] = {u.x, u.y, u.z, u.w};
+                    uint32_t flip = 0;
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) {
+                        const unsigned long long en = __ldg(ent + idx[r]);
+                        if ((((unsigned long long)ur[r] + en) >> 32) == 0ull) flip |= 1u << (8 * r);
+                    }
+                    const uint32_t nw = own ^ flip;
+                    sw[base + p] = nw;
+                    if (PM1) swi[base + p] = nw ^ 0x01010101u;
+                }
+                __syncthreads();
+            }
+        }
+    }
+
+    // energies of every slice (2E summed per replica), then each run's lowest-energy slice
+    for (int x = tid; x < 4 * P; x += B) e2[x] = 0;
+    __syncthreads();
+    for (size_t x = tid; x < Pn; x += B) {
+        const int tau = (int)(x / n), p = (int)(x - (size_t)tau * n);
+        int c2[4];
+        energy2<PM1>(sw[x], pr->meta[p], pr->ell, cap_n, p, sw + (size_t)tau * n, c2);
+#pragma unroll
+        for (int r = 0; r < 4; ++r) atomicAdd(&e2[4 * tau + r], c2[r]);
+    }
+    __syncthreads();
+    if (tid < 4) {
+        int bt = 0;
+        for (int tau = 1; tau < P; ++tau)
+            if (e2[4 * tau + tid] < e2[4 * bt + tid]) bt = tau;
+        s_best[tid] = bt;
+        const int r = 4 * quad + tid;
+        if (r < job.S) {
+            job.energies[r] = (int64_t)(e2[4 * bt + tid] / 2) + pr->offset;
+            if (L.slice_out) L.slice_out[r] = bt;
+        }
+    }
+    __syncthreads();
+    const int lane = tid & 31, warp = tid >> 5;
+    const int Wn = (n + 31) >> 5;
+    for (int w = warp; w < Wn; w += B / 32) {
+        const int i = 32 * w + lane;
+        const int pos = (i < n) ? pr->pos_of_idx[i] : 0;
+#pragma unroll
+        for (int rr = 0; rr < 4; ++rr) {
+            const uint32_t word = (i < n) ? sw[(size_t)s_best[rr] * n + pos] : 0u;
+            const uint32_t bits = __ballot_sync(0xFFFFFFFFu, (word >> (8 * rr)) & 1u);
+            const int r = 4 * quad + rr;
+            if (lane == 0 && r < job.S) job.spins[(size_t)r * job.W + w] = bits;
+        }
+    }
+}
+
+template <bool PM1, int B>
+__global__ void __launch_bounds__(B) k_sweep_sqa(const SweepLaunch L)
+{
+    extern __shared__ __align__(16) uint32_t smem_sqa[];
+    __shared__ int s_item;
+    for (int iter = 0;; ++iter) {
+        SweepJob job;
+        int quad0, nq;
+        if (!next_item(L, iter, &s_item, job, quad0, nq)) break;
+        run_item_sqa<PM1, B>(L, job, quad0, smem_sqa);
+        __syncthreads();
+    }
+}
+
+void *select_sqa(bool pm1, int block)
+{
+#define SPVAR_SQA_CASE(PM, BB) \
+    if (pm1 == PM && block == BB) return reinterpret_cast<void *>(k_sweep_sqa<PM, BB>);
+    SPVAR_SQA_CASE(true, 128) SPVAR_SQA_CASE(true, 256) SPVAR_SQA_CASE(true, 512)
+    SPVAR_SQA_CASE(false, 128) SPVAR_SQA_CASE(false, 256) SPVAR_SQA_CASE(false, 512)
+#undef SPVAR_SQA_CASE
+    return nullptr;
+}
+
+}  // namespace
+
+bool sqa_shape_ok(bool pm1, int block, int max_n, int P, int W)
+{
+    if (!select_sqa(pm1, block) || P < 1 || (P > 1 && (P & 1)) || P > kSqaMaxSlices) return false;
+    if ((long long)max_n >= (1 << 16)) return false;
+    if (pm1 && ((long long)P * max_n + max_n >= 0xFFFF || 3LL * W - 1 > 255)) return false;
+    return true;
+}
+
+size_t sqa_smem_bytes(int max_n, int P, int maxdeg, bool pm1) { return 4 * sqa_words(max_n, P, maxdeg, pm1); }
+
+cudaError_t launch_sweep_sqa(const SweepLaunch &L, bool pm1, int block, int grid, size_t smem, cudaStream_t st)
+{
+    void *k = select_sqa(pm1, block);
+    if (!k) return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    void *args[] = {const_cast<SweepLaunch *>(&L)};
+    return cudaLaunchKernel(k, dim3(grid), dim3(block), args, smem, st);
+}
+
+int sqa_max_active_blocks(bool pm1, int block, size_t smem)
+{
+    void *k = select_sqa(pm1, block);
+    if (!k) return 0;
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int nb = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, block, smem);
+    return nb;
+}
+
+}  // namespace spvar

@@ -86,6 +86,8 @@ def lib():
         L.spvar_beta_geometric.argtypes = [i32, ctypes.c_double, ctypes.c_double, vp]
         L.spvar_thresholds.argtypes = [i32, vp, i32, i32, vp]
         L.spvar_sample.argtypes = [vp, i32, vp, i32, i32, u64, u32, u32, vp, vp, vp]
+        L.spvar_sqa_table.argtypes = [i32, i32, vp, vp, i32, i32, vp]
+        L.spvar_sqa_sample.argtypes = [vp, i32, i32, vp, i32, i32, u64, u32, u32, vp, vp, vp, vp]
         L.spvar_sample_range.argtypes = [vp, i32, i32, vp, i32, i32, u64, u32, u32, vp, vp, vp, vp]
         L.spvar_persistence.argtypes = [vp, i32, vp, vp, ctypes.c_double, i32, i32, i32, vp, vp, vp, vp,
                                         ctypes.POINTER(i32), vp]
@@ -247,6 +249,30 @@ def thresholds_device(thr):
     return torch.from_numpy(_host(thr, np.uint32).view(np.int32)).cuda()
 
 
+def sqa_table(T, P, beta, gamma, dmax, scale=1):
+    """Host acceptance entries of the SQA sweep, uint64 [T, 3, 2 (dmax/2) + 1];
+    beta and gamma per sweep (or constants)."""
+    beta = np.ascontiguousarray(np.broadcast_to(np.asarray(beta, np.float64), (max(T, 1),)))
+    gamma = np.ascontiguousarray(np.broadcast_to(np.asarray(gamma, np.float64), (max(T, 1),)))
+    W = 2 * (dmax // 2) + 1
+    ent = np.zeros((max(T, 1), 3, max(W, 1)), np.uint64)
+    _check(lib().spvar_sqa_table(T, P, _hp(beta), _hp(gamma), dmax, scale, _hp(ent)), "spvar_sqa_table")
+    return ent[:T]
+
+
+def gamma_linear(T, gamma0, gamma1):
+    """Transverse field falling linearly from gamma0 to gamma1 (endpoints included)."""
+    if T == 1:
+        return np.array([gamma0], np.float64)
+    return gamma0 + (gamma1 - gamma0) * np.arange(T, dtype=np.float64) / (T - 1)
+
+
+def table_device(ent):
+    """Host uint64 SQA table -> CUDA int64 tensor holding the same bits."""
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(ent, np.uint64).view(np.int64)).cuda()
+
+
 # ------------------------------------------------------------------ calls
 def sample(problem, thr_dev, thr_stride, num_sweeps, num_samples, seed, start=0, phase=0,
            spins=None, energies=None, stream=None):
@@ -261,6 +287,20 @@ def sample(problem, thr_dev, thr_stride, num_sweeps, num_samples, seed, start=0,
     _check(lib().spvar_sample(problem.handle, num_sweeps, _dp(thr_dev), thr_stride, num_samples, seed, start,
                               phase, _dp(spins), _dp(energies), _stream(stream)), "spvar_sample")
     return spins, energies
+
+
+def sqa_sample(problem, ent_dev, W, num_sweeps, P, num_samples, seed, start=0, phase=0, stream=None):
+    """SQA sample (second sampler for Alg. 1): each run's lowest-energy Trotter slice.
+    Returns (spins int32 [S, W], energies int64 [S], slice int32 [S])."""
+    import torch
+    n = problem.n
+    Wn = (n + 31) // 32
+    spins = torch.empty((max(num_samples, 1), max(Wn, 1)), dtype=torch.int32, device="cuda")
+    energies = torch.empty(max(num_samples, 1), dtype=torch.int64, device="cuda")
+    sl = torch.empty(max(num_samples, 1), dtype=torch.int32, device="cuda")
+    _check(lib().spvar_sqa_sample(problem.handle, num_sweeps, P, _dp(ent_dev), W, num_samples, seed, start, phase,
+                                  _dp(spins), _dp(energies), _dp(sl), _stream(stream)), "spvar_sqa_sample")
+    return spins, energies, sl
 
 
 def sample_range(problem, thr_dev, thr_stride, sweep_begin, sweep_end, num_samples, seed, start=0, phase=0,

@@ -82,6 +82,23 @@ def test_schedule_and_table_bit_identical_to_oracle(L, T, b0, b1, dmax, scale):
     assert np.array_equal(spvar.thresholds(beta, dmax, scale), O.thresholds(beta, dmax, scale))
 
 
+@pytest.mark.parametrize("T,P,beta,g0,g1,dmax,scale", [(200, 8, 3.0, 3.0, 0.01, 12, 1), (100, 16, 5.0, 2.0, 1e-4, 24, 1),
+                                                      (50, 2, 1.0, 0.5, 0.5, 1400, 100), (30, 1, 2.0, 1.0, 1.0, 12, 1)])
+def test_sqa_table_bit_identical_to_oracle(L, T, P, beta, g0, g1, dmax, scale):
+    from paper_1706_07826_gb300 import spvar
+    gamma = spvar.gamma_linear(T, g0, g1)
+    assert np.array_equal(gamma, O.gamma_linear(T, g0, g1))
+    b = np.full(T, beta)
+    assert np.array_equal(spvar.sqa_table(T, P, b, gamma, dmax, scale), O.sqa_table(T, P, b, gamma, dmax, scale))
+
+
+def test_sqa_table_rejects_bad_input(L):
+    from paper_1706_07826_gb300 import spvar
+    for args in ((10, 3, 1.0, 1.0, 12), (10, 0, 1.0, 1.0, 12), (10, 4, 1.0, 0.0, 12), (10, 4, 1.0, 1.0, -2)):
+        with pytest.raises(spvar.SpvarError):
+            spvar.sqa_table(*args)
+
+
 def _create(L, n, rp, col, val, h, offset=0, scale=1):
     out = ctypes.c_void_p()
     rp, col, val, h = (np.ascontiguousarray(x, np.int32) for x in (rp, col, val, h))

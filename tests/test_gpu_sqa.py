@@ -1,0 +1,96 @@
+"""GPU parity of the second sampler, simulated quantum annealing
+(spvar_sqa_sample, discrete-time path integral, Sec. III), against the
+oracle: returned states, energies and chosen slices identical, bit for bit,
+for +-1 and general couplers, one to sixteen Trotter slices, and sampled
+replicas of a full-size Chimera C8 run."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1706_07826_gb300 import instances as I
+
+from gpu_cases import gpu_problem, oracle_problem, table, with_h
+
+pytestmark = pytest.mark.gpu
+
+CASES = [
+    # name, instance, P, T, S
+    ("cubic_L4_P4", lambda: I.cubic3d(4, 2100), 4, 60, 37),
+    ("cubic_L5_odd_P8", lambda: I.cubic3d(5, 2101), 8, 40, 22),
+    ("chimera_C3_P2", lambda: I.chimera(3, 2102), 2, 50, 16),
+    ("chimera_C2_P16", lambda: I.chimera(2, 2103), 16, 30, 9),
+    ("pm1_with_h_P6", lambda: with_h(I.cubic3d(3, 2104), 4, 3), 6, 40, 13),
+    ("random_general_P4", lambda: I.random_graph(40, 90, 5, jmax=7, hmax=9), 4, 40, 11),
+    ("weak_strong_scaled_P8", lambda: I.weak_strong(2, 2105), 8, 30, 8),
+    ("single_slice", lambda: I.cubic3d(4, 2106), 1, 50, 20),
+]
+
+
+def _gpu(inst, P, ent, S, seed, start, phase):
+    import torch
+    from paper_1706_07826_gb300 import spvar
+    g, e, sl = spvar.sqa_sample(gpu_problem(inst), spvar.table_device(ent), ent.shape[2], ent.shape[0], P, S, seed,
+                                start, phase)
+    torch.cuda.synchronize()
+    return spvar.unpack_spins(g.cpu().numpy()[:S], inst.n), e.cpu().numpy()[:S], sl.cpu().numpy()[:S]
+
+
+@pytest.mark.parametrize("name,make,P,T,S", CASES, ids=[c[0] for c in CASES])
+def test_sqa_parity(cuda_lib, name, make, P, T, S):
+    inst = make()
+    op = oracle_problem(inst)
+    ent = O.sqa_table(T, P, 3.0, O.gamma_linear(T, 3.0, 0.05), O.dmax(op), inst.scale)
+    o_s, o_e, o_sl = O.sqa_sample(op, ent, P, S, 321, start=2, phase=1)
+    g_s, g_e, g_sl = _gpu(inst, P, ent, S, 321, 2, 1)
+    assert np.array_equal(g_e, o_e + inst.offset)
+    assert np.array_equal(g_sl, o_sl)
+    assert np.array_equal(g_s, o_s)
+
+
+def test_single_slice_equals_sa_kernel(cuda_lib):
+    import torch
+    from paper_1706_07826_gb300 import spvar
+    inst = I.chimera(4, 2107)
+    op = oracle_problem(inst)
+    T, S = 80, 24
+    beta = O.beta_geometric(T, 0.1, 3.0)
+    thr = table(inst, T)
+    ent = O.sqa_table(T, 1, beta, 1.0, O.dmax(op), 1)
+    gp = gpu_problem(inst)
+    w1, e1 = spvar.sample(gp, spvar.thresholds_device(thr), thr.shape[1], T, S, 5, 1, 0)
+    torch.cuda.synchronize()
+    s2, e2, sl = _gpu(inst, 1, ent, S, 5, 1, 0)
+    assert np.array_equal(e1.cpu().numpy()[:S], e2) and not sl.any()
+    assert np.array_equal(spvar.unpack_spins(w1.cpu().numpy()[:S], inst.n), s2)
+
+
+def test_chimera_c8_sampled_replicas(cuda_lib):
+    """Chimera C8 (N = 512) with 16 slices, 64 runs; the oracle recomputes
+    sampled runs one by one."""
+    inst = I.chimera(8, 2108)
+    op = oracle_problem(inst)
+    T, P, S = 60, 16, 64
+    ent = O.sqa_table(T, P, 3.0, O.gamma_linear(T, 3.0, 0.05), O.dmax(op), 1)
+    g_s, g_e, g_sl = _gpu(inst, P, ent, S, 99, 0, 0)
+    for r in (0, 5, 31, 63):
+        s, e, sl = O.sqa_sample(op, ent, P, 1, 99, r0=r)
+        assert g_e[r] == e[0] and g_sl[r] == sl[0]
+        assert np.array_equal(g_s[r], s[0])
+
+
+def test_sqa_rejects_bad_arguments(cuda_lib):
+    from paper_1706_07826_gb300 import spvar
+    inst = I.cubic3d(4, 1)
+    op = oracle_problem(inst)
+    ent = O.sqa_table(10, 4, 1.0, 1.0, O.dmax(op), 1)
+    gp = gpu_problem(inst)
+    d = spvar.table_device(ent)
+    with pytest.raises(spvar.SpvarError):
+        spvar.sqa_sample(gp, d, ent.shape[2], 10, 3, 8, 1)            # odd slice count
+    with pytest.raises(spvar.SpvarError):
+        spvar.sqa_sample(gp, d, ent.shape[2] - 2, 10, 4, 8, 1)        # table narrower than the problem's dmax
+    big = I.cubic3d(20, 2)
+    gb = gpu_problem(big)
+    eb = O.sqa_table(2, 1024, 1.0, 1.0, O.dmax(oracle_problem(big)), 1)
+    with pytest.raises(spvar.SpvarError):
+        spvar.sqa_sample(gb, spvar.table_device(eb), eb.shape[2], 2, 1024, 4, 1)  # slices do not fit
