@@ -179,6 +179,10 @@ int spvar_sample_range(const spvar_problem *p, int32_t sweep_begin, int32_t swee
 int spvar_sqa_table(int32_t T, int32_t P, const double *beta, const double *gamma, int32_t dmax,
                     int32_t energy_scale, uint64_t *ent);
 
+/* Linear transverse-field schedule gamma[t] = g0 + (g1 - g0) t / (T - 1)
+ * (gamma[0] = g0 when T = 1), host -> host. */
+int spvar_gamma_linear(int32_t T, double g0, double g1, double *gamma);
+
 /* num_samples SQA runs of the problem (each returns its lowest-energy slice,
  * lowest slice index on ties).  ent: device [num_sweeps][3][W] from
  * spvar_sqa_table for a dmax >= the problem's (W = 2 (dmax/2) + 1).  Counters
@@ -282,7 +286,15 @@ typedef struct spvar_params {
                                     Skipped for a problem with some h != 0.  0: off */
     int32_t corr_num, corr_den;  /* correlation threshold corr_num / corr_den (the paper uses 1.0) */
     double corr_elite_threshold; /* elite fraction of the correlation phase */
+    int32_t sampler;             /* SPVAR_SAMPLER_SA (beta0 -> beta1 anneal) or SPVAR_SAMPLER_SQA */
+    int32_t sqa_slices;          /* SQA: Trotter slices P (1, or even, <= SPVAR_SQA_MAX_SLICES) */
+    double sqa_beta;             /* SQA: inverse temperature, constant over the anneal */
+    double sqa_gamma0, sqa_gamma1; /* SQA: transverse field, linear from gamma0 to gamma1 (both > 0) */
 } spvar_params;
+
+#define SPVAR_SAMPLER_SA 0  /* simulated annealing (Sec. III.A) */
+#define SPVAR_SAMPLER_SQA 1 /* simulated quantum annealing: discrete-time path integral (Sec. III);
+                               the sample of a run is its lowest-energy Trotter slice */
 
 #define SPVAR_SWEEP_AUTO 0    /* register kernel when eligible, else general */
 #define SPVAR_SWEEP_GENERAL 1 /* general integer-coupler kernel */

@@ -39,6 +39,12 @@ class OrParams(ctypes.Structure):
         ("corr_num", ctypes.c_int32),
         ("corr_den", ctypes.c_int32),
         ("corr_elite_threshold", ctypes.c_double),
+        ("sampler", ctypes.c_int32),
+        ("sqa_slices", ctypes.c_int32),
+        ("sqa_beta", ctypes.c_double),
+        ("sqa_gamma0", ctypes.c_double),
+        ("sqa_gamma1", ctypes.c_double),
+        ("energy_scale", ctypes.c_int32),
     ]
 
 
@@ -69,6 +75,7 @@ def lib():
                                     ctypes.c_int32, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, i8p, i64p,
                                     i32p]
         L.or_sqa_sample.restype = ctypes.c_int
+        L.or_gamma_linear.argtypes = [ctypes.c_int32, ctypes.c_double, ctypes.c_double, f64p]
         L.or_elite_count.argtypes = [ctypes.c_double, ctypes.c_int32]
         L.or_elite_count.restype = ctypes.c_int32
         L.or_elite.argtypes = [ctypes.c_int32, i64p, ctypes.c_int32, i32p]
@@ -210,9 +217,9 @@ def sqa_table(T, P, beta, gamma, dmax_, scale=1):
 
 def gamma_linear(T, gamma0, gamma1):
     """Transverse field falling linearly from gamma0 to gamma1 (endpoints included)."""
-    if T == 1:
-        return np.array([gamma0], np.float64)
-    return gamma0 + (gamma1 - gamma0) * np.arange(T, dtype=np.float64) / (T - 1)
+    g = np.zeros(max(T, 1), np.float64)
+    lib().or_gamma_linear(T, float(gamma0), float(gamma1), _p(g, f64p))
+    return g[:T]
 
 
 def sqa_sample(p: Csr, ent, P, S, seed, start=0, phase=0, colours=None, r0=0):
@@ -346,13 +353,16 @@ class SolveResult:
 
 def solve(p: Csr, thr, seed, num_starts, fixing_sample_size, solving_sample_size, elite_threshold,
           fix_num=1, fix_den=1, iterate=False, max_fix_phases=1, canon=-1, start0=0, boost=False, tree=False,
-          corr_sample_size=0, corr_elite_threshold=0.2, corr_num=1, corr_den=1):
-    """Multi-start SPVAR (Alg. 2) with SA; thr is the original problem's table.
-    corr_sample_size > 0 adds the correlation-fixing phase for zero-bias problems."""
+          corr_sample_size=0, corr_elite_threshold=0.2, corr_num=1, corr_den=1, sampler=0, sqa_slices=16,
+          sqa_beta=3.0, sqa_gamma0=3.0, sqa_gamma1=0.01):
+    """Multi-start SPVAR (Alg. 2); thr is the original problem's SA table (its
+    length sets the sweeps).  corr_sample_size > 0 adds the correlation-fixing
+    phase for zero-bias problems; sampler = 1 samples every phase with SQA."""
     thr = _c(thr, np.uint32)
     prm = OrParams(num_starts, fixing_sample_size, solving_sample_size, thr.shape[0], float(elite_threshold),
                    fix_num, fix_den, 1 if iterate else 0, max_fix_phases, canon, start0, 1 if boost else 0,
-                   1 if tree else 0, corr_sample_size, corr_num, corr_den, float(corr_elite_threshold))
+                   1 if tree else 0, corr_sample_size, corr_num, corr_den, float(corr_elite_threshold), sampler,
+                   sqa_slices, float(sqa_beta), float(sqa_gamma0), float(sqa_gamma1), p.scale)
     P = max_fix_phases + 1 + (1 if corr_sample_size > 0 else 0)
     Smax = max(fixing_sample_size, solving_sample_size, corr_sample_size)
     n0 = p.n

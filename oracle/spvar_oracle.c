@@ -280,6 +280,11 @@ void or_sqa_table(int32_t T, int32_t P, const double *beta, const double *gamma,
     }
 }
 
+void or_gamma_linear(int32_t T, double g0, double g1, double *gamma)
+{
+    for (int32_t t = 0; t < T; ++t) gamma[t] = (T == 1) ? g0 : g0 + (g1 - g0) * (double)t / (double)(T - 1);
+}
+
 int or_sqa_sample(int32_t n, const int32_t *row_ptr, const int32_t *col, const int32_t *val,
                   const int32_t *h, const int32_t *colour, int32_t ncol,
                   int32_t T, int32_t P, const uint64_t *ent, int32_t dmax,
@@ -709,6 +714,21 @@ int or_solve(int32_t n0, const int32_t *row_ptr0, const int32_t *col0, const int
     int32_t *log_parent = (int32_t *)malloc(sizeof(int32_t) * ((size_t)n0 + 1));
     int8_t *log_sigma = (int8_t *)malloc((size_t)n0 + 1);
     int rc = 0;
+    /* SQA: its acceptance table for the original problem, and the chosen slices */
+    uint64_t *ent = NULL;
+    int32_t *slice = NULL;
+    if (prm->sampler == 1) {
+        const int32_t T = prm->num_sweeps, W = 2 * (dmax / 2) + 1;
+        double *bt = (double *)malloc(sizeof(double) * ((size_t)T + 1));
+        double *gt = (double *)malloc(sizeof(double) * ((size_t)T + 1));
+        for (int32_t t = 0; t < T; ++t) bt[t] = prm->sqa_beta;
+        or_gamma_linear(T, prm->sqa_gamma0, prm->sqa_gamma1, gt);
+        ent = (uint64_t *)malloc(sizeof(uint64_t) * ((size_t)T * 3 * W + 1));
+        or_sqa_table(T, prm->sqa_slices, bt, gt, dmax, prm->energy_scale > 0 ? prm->energy_scale : 1, ent);
+        free(bt);
+        free(gt);
+        slice = (int32_t *)malloc(sizeof(int32_t) * ((size_t)Smax + 1));
+    }
 
     for (int32_t st = 0; st < prm->num_starts && rc == 0; ++st) {
         int b = 0;
@@ -734,8 +754,13 @@ int or_solve(int32_t n0, const int32_t *row_ptr0, const int32_t *col0, const int
             int fixing = corr || (fphase < prm->max_fix_phases && (fphase == 0 || (prm->iterate && n > 0)));
             int32_t S = corr ? prm->corr_sample_size : fixing ? prm->fixing_sample_size : prm->solving_sample_size;
             if (!fixing && S == 0) break;
-            rc = or_sample(n, rp[b], cl[b], vl[b], hh[b], co[b], ncol, prm->num_sweeps, thr, dmax,
-                           0, S, seed, (uint32_t)(prm->start0 + st), (uint32_t)phase, spins, e, NULL);
+            if (prm->sampler == 1)
+                rc = or_sqa_sample(n, rp[b], cl[b], vl[b], hh[b], co[b], ncol, prm->num_sweeps, prm->sqa_slices,
+                                   ent, dmax, 0, S, seed, (uint32_t)(prm->start0 + st), (uint32_t)phase, spins, e,
+                                   slice);
+            else
+                rc = or_sample(n, rp[b], cl[b], vl[b], hh[b], co[b], ncol, prm->num_sweeps, thr, dmax,
+                               0, S, seed, (uint32_t)(prm->start0 + st), (uint32_t)phase, spins, e, NULL);
             if (rc) break;
             if (!fixing && prm->boost) or_component_boost(n, rp[b], cl[b], vl[b], hh[b], S, spins, e);
             int64_t *rec = energies + ((int64_t)st * P + phase) * Smax;
@@ -817,5 +842,6 @@ int or_solve(int32_t n0, const int32_t *row_ptr0, const int32_t *col0, const int
     free(colour0); free(orig); free(old_of_new); free(tmp); free(cnt); free(fx);
     free(spins); free(e); free(elite);
     free(tcode); free(tpar); free(tord); free(log_child); free(log_parent); free(log_sigma);
+    free(ent); free(slice);
     return rc;
 }

@@ -186,7 +186,16 @@ typedef struct or_params {
     int32_t corr_sample_size;
     int32_t corr_num, corr_den;
     double corr_elite_threshold;
+    /* Sampler of every phase: 0 = SA with the table thr; 1 = SQA with
+     * sqa_slices slices, constant sqa_beta and a transverse field linear from
+     * sqa_gamma0 to sqa_gamma1 over the sweeps (or_gamma_linear). */
+    int32_t sampler, sqa_slices;
+    double sqa_beta, sqa_gamma0, sqa_gamma1;
+    int32_t energy_scale;          /* the problem's scale (SQA table; >= 1) */
 } or_params;
+
+/* gamma[t] = g0 + (g1 - g0) t / (T - 1); gamma[0] = g0 when T = 1. */
+void or_gamma_linear(int32_t T, double g0, double g1, double *gamma);
 
 /* Outputs (caller-allocated, P = max_fix_phases + 1 (+1 with corr_sample_size > 0),
  * Smax = max sample size):

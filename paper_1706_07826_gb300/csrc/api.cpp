@@ -493,6 +493,13 @@ int spvar_sqa_table(int32_t T, int32_t P, const double *beta, const double *gamm
     return SPVAR_OK;
 }
 
+int spvar_gamma_linear(int32_t T, double g0, double g1, double *gamma)
+{
+    if (T < 0 || (T > 0 && !gamma)) return SPVAR_EINVAL;
+    for (int32_t t = 0; t < T; ++t) gamma[t] = (T == 1) ? g0 : g0 + (g1 - g0) * (double)t / (double)(T - 1);
+    return SPVAR_OK;
+}
+
 int spvar_sqa_sample(const spvar_problem *p, int32_t num_sweeps, int32_t P, const uint64_t *ent, int32_t W,
                      int32_t num_samples, uint64_t seed, uint32_t start, uint32_t phase, uint32_t *spins,
                      int64_t *energies, int32_t *slice, void *stream)

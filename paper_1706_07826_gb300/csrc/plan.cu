@@ -51,6 +51,9 @@ cudaError_t engine_phase(const PhaseEngine &E, Slot *slots, int nslots, int T, i
     L.stage_ell = E.shape.stage;
     L.max_n = E.max_n0;
     L.max_deg = E.max_deg;
+    L.ent = E.ent;
+    L.P = E.P;
+    L.W = E.W;
     if (E.ev_sweep[0] && (e = record(E.ev_sweep[0])) != cudaSuccess) return e;
     e = launch_sweep_shape(L, E.shape, E.pm1, grid, E.sweep_smem, st);
     if (e != cudaSuccess) return e;
@@ -77,6 +80,8 @@ struct spvar_plan {
     std::vector<Slot> h_slots;
     Slot *h_slots_pinned = nullptr;
     uint32_t *d_thr = nullptr;
+    unsigned long long *d_ent = nullptr;  // SQA acceptance entries
+    int sqa_P = 0, sqa_W = 0;             // SQA slices and table width (0: SA)
     SweepJob *d_jobs = nullptr;
     WorkItem *d_items = nullptr;
     int32_t *d_ctr = nullptr;       // [0] nitems, [1] queue, [2] nactive
@@ -103,11 +108,11 @@ inline cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct TuneKey {
-    int max_n, max_deg, pm1, S, nslots, form, thr_stride;
+    int max_n, max_deg, pm1, S, nslots, form, thr_stride, sqa_P;
     bool operator<(const TuneKey &o) const
     {
-        return std::tie(max_n, max_deg, pm1, S, nslots, form, thr_stride) <
-               std::tie(o.max_n, o.max_deg, o.pm1, o.S, o.nslots, o.form, o.thr_stride);
+        return std::tie(max_n, max_deg, pm1, S, nslots, form, thr_stride, sqa_P) <
+               std::tie(o.max_n, o.max_deg, o.pm1, o.S, o.nslots, o.form, o.thr_stride, o.sqa_P);
     }
 };
 std::map<TuneKey, SweepShape> g_tune_cache;
@@ -128,6 +133,9 @@ SweepLaunch make_launch(const spvar_plan *pl, int T)
     L.stage_ell = pl->shape.stage;
     L.max_n = pl->max_n0;
     L.max_deg = pl->max_deg;
+    L.ent = pl->d_ent;
+    L.P = pl->sqa_P;
+    L.W = pl->sqa_W;
     return L;
 }
 
@@ -149,6 +157,9 @@ PhaseEngine engine_of(const spvar_plan *pl)
     E.max_deg = pl->max_deg;
     E.thr_stride = pl->thr_stride;
     E.thr = pl->d_thr;
+    E.ent = pl->d_ent;
+    E.P = pl->sqa_P;
+    E.W = pl->sqa_W;
     E.jobs = pl->d_jobs;
     E.items = pl->d_items;
     E.ctr = pl->d_ctr;
@@ -191,9 +202,28 @@ int plan_nslot(const spvar_plan *pl, int Q, int block)
 
 // Candidate sweep shapes for a plan: the general kernel with and without the
 // staged layout, and (for +-1 problems) the register-resident kernel.
+// SQA sweep shape for a block size, or kind -1 if the slices do not fit.
+SweepShape sqa_shape(const spvar_plan *pl, int block, int optin)
+{
+    const bool pm1 = pl->pm1 && sqa_shape_ok(true, block, pl->max_n0, pl->sqa_P, pl->sqa_W);
+    SweepShape sh{5, block, 1, pm1 ? 1 : 0, 0, 0};
+    sh.slices = pl->sqa_P;
+    if (!sqa_shape_ok(pm1, block, pl->max_n0, pl->sqa_P, pl->sqa_W) ||
+        sweep_shape_smem(sh, pl->max_n0, pl->thr_stride, pl->max_deg) > (size_t)optin)
+        sh.kind = -1;
+    return sh;
+}
+
 std::vector<SweepShape> candidate_shapes(const spvar_plan *pl, int optin)
 {
     std::vector<SweepShape> out;
+    if (pl->sqa_P > 0) {
+        for (int b : {128, 256, 512}) {
+            const SweepShape sh = sqa_shape(pl, b, optin);
+            if (sh.kind == 5) out.push_back(sh);
+        }
+        return out;
+    }
     if (pm1_kernel_eligible(pl->pm1, pl->dmax, pl->max_deg)) {
         const int md = pl->max_deg <= 6 ? 6 : 8;
         for (int w : {2, 4, 8, 16}) {
@@ -241,7 +271,7 @@ std::vector<SweepShape> candidate_shapes(const spvar_plan *pl, int optin)
 void autotune(spvar_plan *pl, cudaStream_t st, int optin)
 {
     const TuneKey key{pl->max_n0, pl->max_deg, pl->pm1 ? 1 : 0, pl->C.S_fix, pl->C.nslots,
-                      pl->prm.form, pl->thr_stride};
+                      pl->prm.form, pl->thr_stride, pl->sqa_P};
     {
         std::lock_guard<std::mutex> g(g_tune_mu);
         auto it = g_tune_cache.find(key);
@@ -335,7 +365,7 @@ int spvar_plan_create(const spvar_problem *const *problems, int32_t nproblems,
         p.replicas_per_block < 0 || (p.replicas_per_block % 4) != 0 || p.sweep_kernel < 0 ||
         p.sweep_kernel > 4 || p.start_offset < 0 || p.component_boost < 0 || p.component_boost > 1 || p.tree_preprocess < 0 || p.tree_preprocess > 1 || (p.sweep_block != 0 && p.sweep_block != 128 && p.sweep_block != 256 &&
                                p.sweep_block != 512 && p.sweep_block != 1024) ||
-        check_corr_params(p) != SPVAR_OK)
+        check_corr_params(p) != SPVAR_OK || check_sampler_params(p) != SPVAR_OK)
         return SPVAR_EINVAL;
     const int Smax = std::max(std::max(p.fixing_sample_size, p.solving_sample_size), p.corr_sample_size);
     if (Smax > SPVAR_MAX_SAMPLES || p.num_sweeps > SPVAR_MAX_SWEEPS ||
@@ -363,6 +393,10 @@ int spvar_plan_create(const spvar_problem *const *problems, int32_t nproblems,
     pl->T = p.num_sweeps;
     pl->thr_stride = dmax + 1;
     pl->dmax = dmax;
+    if (p.sampler == SPVAR_SAMPLER_SQA) {
+        pl->sqa_P = p.sqa_slices;
+        pl->sqa_W = 2 * (dmax / 2) + 1;
+    }
     const int nslots = nproblems * p.num_starts;
     SolveConsts &C = pl->C;
     fill_solve_consts(p, C);
@@ -382,6 +416,7 @@ int spvar_plan_create(const spvar_problem *const *problems, int32_t nproblems,
     const size_t o_items = take(sizeof(WorkItem) * max_items);
     const size_t o_ctr = take(16);
     const size_t o_thr = take(4 * (size_t)std::max(pl->T, 1) * pl->thr_stride);
+    const size_t o_ent = take(pl->sqa_P > 0 ? 8 * (size_t)std::max(pl->T, 1) * 3 * pl->sqa_W : 0);
     const size_t o_rec = take(8 * (size_t)nslots * P_slots * Smax);
     const size_t o_rc = take(4 * (size_t)nslots * P_slots);
     const size_t o_rn = take(4 * (size_t)nslots * P_slots);
@@ -429,6 +464,7 @@ int spvar_plan_create(const spvar_problem *const *problems, int32_t nproblems,
     pl->d_items = (WorkItem *)(w + o_items);
     pl->d_ctr = (int32_t *)(w + o_ctr);
     pl->d_thr = (uint32_t *)(w + o_thr);
+    if (pl->sqa_P > 0) pl->d_ent = (unsigned long long *)(w + o_ent);
     pl->d_rec_e = (int64_t *)(w + o_rec);
     pl->d_rec_count = (int32_t *)(w + o_rc);
     pl->d_rec_nfree = (int32_t *)(w + o_rn);
@@ -446,7 +482,19 @@ int spvar_plan_create(const spvar_problem *const *problems, int32_t nproblems,
             spvar_beta_geometric(pl->T, p.beta0, p.beta1, beta.data());
             spvar_thresholds(pl->T, beta.data(), dmax, scale, thr.data());
         }
+        std::vector<uint64_t> ent;
+        if (pl->sqa_P > 0) {
+            // SQA: constant beta, linear transverse field
+            ent.assign((size_t)std::max(pl->T, 1) * 3 * pl->sqa_W, 0ull);
+            std::vector<double> sb(std::max(pl->T, 1), p.sqa_beta), sg(std::max(pl->T, 1));
+            if (pl->T > 0) {
+                spvar_gamma_linear(pl->T, p.sqa_gamma0, p.sqa_gamma1, sg.data());
+                spvar_sqa_table(pl->T, pl->sqa_P, sb.data(), sg.data(), dmax, scale, ent.data());
+            }
+        }
         if (cudaMemcpyAsync(pl->d_thr, thr.data(), 4 * thr.size(), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+            (pl->sqa_P > 0 &&
+             cudaMemcpyAsync(pl->d_ent, ent.data(), 8 * ent.size(), cudaMemcpyHostToDevice, st) != cudaSuccess) ||
             cudaStreamSynchronize(st) != cudaSuccess) {
             cudaGetLastError();
             plan_free(pl);
@@ -519,7 +567,11 @@ int spvar_plan_create(const spvar_problem *const *problems, int32_t nproblems,
         const int blk = p.sweep_block ? p.sweep_block : 256;
         const bool elig = pm1_kernel_eligible(pl->pm1, pl->dmax, pl->max_deg);
         SweepShape sh{0, blk, Q, 1, 0, 0};
-        if (p.sweep_kernel == SPVAR_SWEEP_PM1 || (p.sweep_kernel == SPVAR_SWEEP_AUTO && elig)) {
+        if (pl->sqa_P > 0) {
+            // SQA: one quad per CTA
+            sh = sqa_shape(pl, blk, optin);
+            if (Q != 1 || sh.kind != 5) { plan_free(pl); return SPVAR_ELIMIT; }
+        } else if (p.sweep_kernel == SPVAR_SWEEP_PM1 || (p.sweep_kernel == SPVAR_SWEEP_AUTO && elig)) {
             const int ns = pm1r_kernel_eligible(pl->pm1, pl->dmax, pl->max_deg) ? plan_nslot(pl, Q, blk) : 0;
             const int md = pl->max_deg <= 6 ? 6 : 8;
             if (!elig) { plan_free(pl); return SPVAR_ELIMIT; }
@@ -682,8 +734,9 @@ int spvar_plan_stats(const spvar_plan *plan, int64_t *attempts, int32_t *phases)
         return SPVAR_ECUDA;
     int64_t a = 0;
     int32_t ph = 0;
+    const int64_t per = (int64_t)pl->T * (pl->sqa_P > 0 ? pl->sqa_P : 1);  // SQA: every slice is swept
     for (size_t i = 0; i < n; ++i) {
-        a += (int64_t)cnt[i] * nf[i] * pl->T;
+        a += (int64_t)cnt[i] * nf[i] * per;
         if (cnt[i] > 0) ++ph;
     }
     if (attempts) *attempts = a;

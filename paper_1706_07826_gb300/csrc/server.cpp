@@ -358,7 +358,7 @@ int spvar_server_create(const spvar_server_config *cfg, spvar_server **out)
         !(p.elite_threshold > 0.0) || !(p.elite_threshold <= 1.0) || !(p.beta0 > 0.0) || !(p.beta1 > 0.0) ||
         p.canon < -1 || p.canon > 1 || p.start_offset < 0 || p.component_boost < 0 || p.component_boost > 1 || p.tree_preprocess < 0 || p.tree_preprocess > 1 || cfg->max_n < 1 || cfg->max_nnz < 0 ||
         cfg->max_degree < 1 || cfg->max_dmax < 0 || cfg->energy_scale < 1 || cfg->max_requests < 1 ||
-        cfg->budget_bytes == 0 || check_corr_params(p) != SPVAR_OK)
+        cfg->budget_bytes == 0 || check_corr_params(p) != SPVAR_OK || p.sampler != SPVAR_SAMPLER_SA)
         return SPVAR_EINVAL;
     const int Smax = std::max(std::max(p.fixing_sample_size, p.solving_sample_size), p.corr_sample_size);
     if (cfg->max_n > SPVAR_MAX_N || cfg->max_degree > SPVAR_MAX_DEGREE || Smax > SPVAR_MAX_SAMPLES ||

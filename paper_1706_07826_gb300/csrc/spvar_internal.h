@@ -170,6 +170,16 @@ inline int check_corr_params(const spvar_params &p)
         return SPVAR_EINVAL;
     return SPVAR_OK;
 }
+// Checks the sampler choice (SPVAR_OK or SPVAR_EINVAL).
+inline int check_sampler_params(const spvar_params &p)
+{
+    if (p.sampler == SPVAR_SAMPLER_SA) return SPVAR_OK;
+    if (p.sampler != SPVAR_SAMPLER_SQA) return SPVAR_EINVAL;
+    if (p.sqa_slices < 1 || (p.sqa_slices > 1 && (p.sqa_slices & 1)) || p.sqa_slices > SPVAR_SQA_MAX_SLICES ||
+        !(p.sqa_beta > 0.0) || !(p.sqa_gamma0 > 0.0) || !(p.sqa_gamma1 > 0.0))
+        return SPVAR_EINVAL;
+    return SPVAR_OK;
+}
 // Phase-independent constants of the multi-start loop (Alg. 2) from the parameters.
 inline void fill_solve_consts(const spvar_params &p, SolveConsts &C)
 {
@@ -269,12 +279,14 @@ int pm1w_max_active_blocks(int warps, int maxd, size_t smem);
 // shared memory), kind 1 = register-resident +-1 kernel (nslot items per
 // thread, maxd neighbour registers per item), kind 2 = streaming +-1 kernel
 // (maxd neighbour offsets per spin staged in shared memory, Q = 1), kind 4 =
-// warp-per-quad +-1 kernel (Q = warps = block / 32).  A persistent grid holds
+// warp-per-quad +-1 kernel (Q = warps = block / 32), kind 5 = simulated
+// quantum annealing (Q = 1).  A persistent grid holds
 // every CTA the SMs can keep resident, or (balance) the fewest CTAs that still
 // need the same number of waves of items, so that no last wave runs nearly empty.
 struct SweepShape {
     int kind, block, Q, stage, nslot, maxd;
     int balance = 0;  // 1: grid sized so that every CTA runs the same number of items
+    int slices = 0;   // kind 5 (SQA): Trotter slices; stage = 1 selects the +-1 SWAR path
 };
 // The streaming and warp-per-quad kernels apply to +-1 couplers, degree <= 8
 // and dmax <= 254; the register kernel needs dmax <= 30.
@@ -293,6 +305,7 @@ inline int pm1_nslot(const Problem *P, int Q, int block)
 }
 inline size_t sweep_shape_smem(const SweepShape &s, int max_n, int thr_stride, int max_deg)
 {
+    if (s.kind == 5) return sqa_smem_bytes(max_n, s.slices, max_deg, s.stage != 0);
     if (s.kind == 1) return pm1_smem_bytes(max_n, s.Q);
     if (s.kind == 2) return pm1s_smem_bytes(max_n, s.Q, s.maxd);
     if (s.kind == 4) return pm1w_smem_bytes(max_n, s.Q, s.maxd);
@@ -301,6 +314,7 @@ inline size_t sweep_shape_smem(const SweepShape &s, int max_n, int thr_stride, i
 inline cudaError_t launch_sweep_shape(const SweepLaunch &L, const SweepShape &s, bool pm1, int grid, size_t smem,
                                       cudaStream_t st)
 {
+    if (s.kind == 5) return launch_sweep_sqa(L, s.stage != 0, s.block, grid, smem, st);
     if (s.kind == 1) return launch_sweep_pm1(L, s.block, s.nslot, s.maxd, grid, smem, st);
     if (s.kind == 2) return launch_sweep_pm1s(L, s.block, s.maxd, grid, smem, st);
     if (s.kind == 4) return launch_sweep_pm1w(L, s.Q, s.maxd, grid, smem, st);
@@ -308,6 +322,7 @@ inline cudaError_t launch_sweep_shape(const SweepLaunch &L, const SweepShape &s,
 }
 inline int sweep_shape_occupancy(const SweepShape &s, bool pm1, size_t smem)
 {
+    if (s.kind == 5) return sqa_max_active_blocks(s.stage != 0, s.block, smem);
     if (s.kind == 1) return pm1_max_active_blocks(s.block, s.nslot, s.maxd, smem);
     if (s.kind == 2) return pm1s_max_active_blocks(s.block, s.maxd, smem);
     if (s.kind == 4) return pm1w_max_active_blocks(s.Q, s.maxd, smem);
@@ -321,6 +336,8 @@ struct PhaseEngine {
     bool pm1;
     int max_n0, max_deg, thr_stride;
     const uint32_t *thr;
+    const unsigned long long *ent;  // SQA acceptance entries (null for SA)
+    int P, W;
     SweepJob *jobs;
     WorkItem *items;
     int32_t *ctr;  // [0] items, [1] queue cursor, [2] active slots

@@ -17,6 +17,7 @@ LIB_PATH = os.path.join(HERE, "libspvar.so")
 OK, EINVAL, EOVERFLOW, ENOMEM, EBUDGET, ETIMEOUT, ECUDA, ELIMIT = 0, -1, -2, -3, -4, -5, -6, -7
 FORM_BATCHED, FORM_PLAIN = 0, 1
 SWEEP_AUTO, SWEEP_GENERAL, SWEEP_PM1, SWEEP_PM1S, SWEEP_PM1W = 0, 1, 2, 3, 4
+SAMPLER_SA, SAMPLER_SQA = 0, 1
 MAX_N, MAX_DEGREE, MAX_SWEEPS, MAX_PHASE, MAX_SAMPLES = 32768, 32, 1048574, 4095, 16384
 NOALLOC_MAX_N = 16384
 
@@ -45,7 +46,9 @@ class Params(ctypes.Structure):
                 ("iterate", i32), ("max_fix_phases", i32), ("canon", i32), ("form", i32),
                 ("replicas_per_block", i32), ("sweep_kernel", i32), ("sweep_block", i32), ("start_offset", i32),
                 ("component_boost", i32), ("tree_preprocess", i32), ("corr_sample_size", i32),
-                ("corr_num", i32), ("corr_den", i32), ("corr_elite_threshold", ctypes.c_double)]
+                ("corr_num", i32), ("corr_den", i32), ("corr_elite_threshold", ctypes.c_double),
+                ("sampler", i32), ("sqa_slices", i32), ("sqa_beta", ctypes.c_double), ("sqa_gamma0", ctypes.c_double),
+                ("sqa_gamma1", ctypes.c_double)]
 
 
 class ServerConfig(ctypes.Structure):
@@ -87,6 +90,7 @@ def lib():
         L.spvar_thresholds.argtypes = [i32, vp, i32, i32, vp]
         L.spvar_sample.argtypes = [vp, i32, vp, i32, i32, u64, u32, u32, vp, vp, vp]
         L.spvar_sqa_table.argtypes = [i32, i32, vp, vp, i32, i32, vp]
+        L.spvar_gamma_linear.argtypes = [i32, ctypes.c_double, ctypes.c_double, vp]
         L.spvar_sqa_sample.argtypes = [vp, i32, i32, vp, i32, i32, u64, u32, u32, vp, vp, vp, vp]
         L.spvar_sample_range.argtypes = [vp, i32, i32, vp, i32, i32, u64, u32, u32, vp, vp, vp, vp]
         L.spvar_persistence.argtypes = [vp, i32, vp, vp, ctypes.c_double, i32, i32, i32, vp, vp, vp, vp,
@@ -262,9 +266,9 @@ def sqa_table(T, P, beta, gamma, dmax, scale=1):
 
 def gamma_linear(T, gamma0, gamma1):
     """Transverse field falling linearly from gamma0 to gamma1 (endpoints included)."""
-    if T == 1:
-        return np.array([gamma0], np.float64)
-    return gamma0 + (gamma1 - gamma0) * np.arange(T, dtype=np.float64) / (T - 1)
+    g = np.zeros(max(T, 1), np.float64)
+    _check(lib().spvar_gamma_linear(T, float(gamma0), float(gamma1), _hp(g)), "spvar_gamma_linear")
+    return g[:T]
 
 
 def table_device(ent):
@@ -359,11 +363,12 @@ def make_params(num_starts=1, fixing_sample_size=100, solving_sample_size=100, n
                 beta1=3.0, elite_threshold=0.1, fix_num=1, fix_den=1, iterate=False, max_fix_phases=1, canon=-1,
                 form=FORM_BATCHED, replicas_per_block=0, sweep_kernel=SWEEP_AUTO, sweep_block=0, start_offset=0,
                 component_boost=False, tree_preprocess=False, corr_sample_size=0, corr_elite_threshold=0.2,
-                corr_num=1, corr_den=1):
+                corr_num=1, corr_den=1, sampler=0, sqa_slices=16, sqa_beta=3.0, sqa_gamma0=3.0, sqa_gamma1=0.01):
     return Params(num_starts, fixing_sample_size, solving_sample_size, num_sweeps, beta0, beta1, elite_threshold,
                   fix_num, fix_den, 1 if iterate else 0, max_fix_phases, canon, form, replicas_per_block,
                   sweep_kernel, sweep_block, start_offset, 1 if component_boost else 0, 1 if tree_preprocess else 0,
-                  corr_sample_size, corr_num, corr_den, float(corr_elite_threshold))
+                  corr_sample_size, corr_num, corr_den, float(corr_elite_threshold), sampler, sqa_slices,
+                  float(sqa_beta), float(sqa_gamma0), float(sqa_gamma1))
 
 
 def phase_slots(params):

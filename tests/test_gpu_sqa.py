@@ -94,3 +94,52 @@ def test_sqa_rejects_bad_arguments(cuda_lib):
     eb = O.sqa_table(2, 1024, 1.0, 1.0, O.dmax(oracle_problem(big)), 1)
     with pytest.raises(spvar.SpvarError):
         spvar.sqa_sample(gb, spvar.table_device(eb), eb.shape[2], 2, 1024, 4, 1)  # slices do not fit
+
+
+SOLVE = [
+    # name, instance, P, T, starts, S_fix, S_solve, elite, extra
+    ("chimera_C3_P4", lambda: I.chimera(3, 2110), 4, 40, 3, 40, 24, 0.2, {}),
+    ("cubic_L4_P8_ispvar", lambda: I.cubic3d(4, 2111), 8, 30, 2, 32, 0, 0.1, dict(iterate=True, max_fix_phases=6)),
+    ("random_h_P2_tree_boost", lambda: I.random_graph(40, 60, 7, jmax=3, hmax=2), 2, 40, 2, 32, 20, 0.25,
+     dict(tree=True, boost=True)),
+    ("weak_strong_P8_corr_skip", lambda: I.weak_strong(2, 2112), 8, 30, 2, 24, 16, 0.2, dict(corr_sample_size=16)),
+    ("cubic_L4_P4_corr", lambda: I.cubic3d(4, 2113), 4, 30, 2, 24, 16, 0.2, dict(corr_sample_size=20)),
+]
+
+
+@pytest.mark.parametrize("form", [0, 1], ids=["batched", "plain"])
+@pytest.mark.parametrize("name,make,P,T,starts,Sf,Ss,elite,extra", SOLVE, ids=[c[0] for c in SOLVE])
+def test_solve_with_sqa_parity(cuda_lib, form, name, make, P, T, starts, Sf, Ss, elite, extra):
+    """Alg. 2 with the SQA sampler in every phase: identical to the oracle."""
+    from paper_1706_07826_gb300 import spvar
+    inst = make()
+    op = oracle_problem(inst)
+    okw = dict(extra)
+    gkw = {{"tree": "tree_preprocess", "boost": "component_boost"}.get(k, k): v for k, v in extra.items()}
+    sq = dict(sqa_slices=P, sqa_beta=3.0, sqa_gamma0=2.5, sqa_gamma1=0.05)
+    ref = O.solve(op, table(inst, T), 31, num_starts=starts, fixing_sample_size=Sf, solving_sample_size=Ss,
+                  elite_threshold=elite, sampler=1, **sq, **okw)
+    prm = spvar.make_params(num_starts=starts, fixing_sample_size=Sf, solving_sample_size=Ss, num_sweeps=T,
+                            elite_threshold=elite, form=form, sampler=spvar.SAMPLER_SQA, **sq, **gkw)
+    out = spvar.solve(gpu_problem(inst), prm, 31)
+    for s in range(starts):
+        assert int(out.nphases[s]) == ref.nphases[s]
+        assert np.array_equal(np.asarray(out.counts[s]), ref.counts[s])
+        assert np.array_equal(np.asarray(out.nfree[s]), ref.nfree[s])
+        for ph in range(ref.nphases[s]):
+            c = ref.counts[s, ph]
+            assert np.array_equal(np.asarray(out.energies[s, ph, :c]), ref.energies[s, ph, :c]), (s, ph)
+        assert int(out.best_energy[s]) == ref.best_e[s]
+        n = inst.n
+        assert np.array_equal(np.asarray(out.fixed[s * n:(s + 1) * n]), ref.fixed[s])
+        assert np.array_equal(np.asarray(out.best_state[s * n:(s + 1) * n]), ref.best_state[s])
+
+
+def test_sqa_sampler_parameters_validated(cuda_lib):
+    from paper_1706_07826_gb300 import spvar
+    gp = gpu_problem(I.chimera(2, 3))
+    for kw in (dict(sampler=2), dict(sampler=1, sqa_slices=3), dict(sampler=1, sqa_gamma1=0.0),
+               dict(sampler=1, sqa_beta=-1.0)):
+        with pytest.raises(spvar.SpvarError):
+            spvar.solve(gp, spvar.make_params(num_starts=1, fixing_sample_size=8, solving_sample_size=8,
+                                              num_sweeps=10, **kw), 1)

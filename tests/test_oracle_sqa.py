@@ -133,3 +133,32 @@ def test_odd_slice_count_rejected():
     ent = O.sqa_table(3, 3, 1.0, 1.0, O.dmax(p), 1)
     with pytest.raises(ValueError):
         O.sqa_sample(p, ent, 3, 4, 1)
+
+
+def test_solve_with_one_slice_equals_constant_temperature_sa():
+    """Alg. 2 with the SQA sampler at P = 1 and inverse temperature beta is
+    Alg. 2 with SA at the constant schedule beta0 = beta1 = beta."""
+    inst = I.random_graph(18, 40, 11, jmax=3, hmax=2)
+    p = _csr(inst)
+    T, beta = 60, 1.7
+    thr = O.thresholds(O.beta_geometric(T, beta, beta), O.dmax(p), 1)
+    kw = dict(num_starts=3, fixing_sample_size=20, solving_sample_size=12, elite_threshold=0.25)
+    a = O.solve(p, thr, 5, **kw)
+    b = O.solve(p, thr, 5, sampler=1, sqa_slices=1, sqa_beta=beta, sqa_gamma0=1.0, sqa_gamma1=0.5, **kw)
+    for f in ("energies", "counts", "nfree", "nphases", "fixed", "best_e", "best_state"):
+        assert np.array_equal(getattr(a, f), getattr(b, f)), f
+
+
+def test_solve_with_sqa_records_valid_energies():
+    inst = I.random_graph(14, 30, 13, jmax=3, hmax=1)
+    p = _csr(inst)
+    T = 80
+    thr = O.thresholds(O.beta_geometric(T, 0.1, 3.0), O.dmax(p), 1)
+    r = O.solve(p, thr, 6, num_starts=2, fixing_sample_size=16, solving_sample_size=8, elite_threshold=0.25,
+                sampler=1, sqa_slices=4, sqa_beta=3.0, sqa_gamma0=2.0, sqa_gamma1=0.05)
+    allS = np.array(list(itertools.product((-1, 1), repeat=inst.n)), np.int64)
+    e0 = _E(inst, allS).min()
+    for st in range(2):
+        rec = np.concatenate([r.energies[st, ph, :r.counts[st, ph]] for ph in range(r.nphases[st])])
+        assert rec.min() >= e0 and r.best_e[st] == rec.min()
+        assert _E(inst, r.best_state[st])[0] == r.best_e[st]
