@@ -40,6 +40,7 @@ L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
 SMS, LANES_PER_SM = 152, 128  # GB300: 152 SMs x 4 SMSPs x 32 lanes issue one int op per lane per clock
 PHILOX_OPS_PER_ATTEMPT = 15  # 10 rounds x (2 wide multiplies + 2 three-input xors + 2 key adds) / 4 replicas
 ACCEPT_OPS_PER_ATTEMPT = 3   # dE, dE <= 0 test, threshold compare
+ALU_PEAK_TOPS = SMS * LANES_PER_SM * 2070e6 / 1e12  # at the maximum SM clock
 
 
 def _instance():
@@ -251,6 +252,55 @@ def measure_uneven(spvar, torch, flush):
     out["config"] = ("64 3D +-J instances, L uniform in 6..12 (N 216..1728, seed 1400), 1 start each, "
                      "2000 fixing + 2000 solving samples, 1000 sweeps, elite 0.1")
     return out
+
+
+def measure_sqa(spvar, torch, flush):
+    """Second sampler (simulated quantum annealing, discrete-time path integral):
+    Multi-start SPVAR on Chimera C8 with SQA in every phase, 10 starts x
+    (500 fixing + 500 solving) runs, 16 Trotter slices, 1000 sweeps, beta 3,
+    transverse field 3 -> 0.01.  An attempt is one spin-slice update; the
+    roofline is the SQA sweep kernel's against the integer issue peak."""
+    from paper_1706_07826_gb300 import instances as I
+    inst = I.chimera(8, 1100)
+    prob = spvar.Problem.from_instance(inst)
+    P = 16
+    prm = spvar.make_params(num_starts=10, fixing_sample_size=500, solving_sample_size=500, num_sweeps=1000,
+                            elite_threshold=0.1, sampler=spvar.SAMPLER_SQA, sqa_slices=P, sqa_beta=3.0,
+                            sqa_gamma0=3.0, sqa_gamma1=0.01)
+    plan = spvar.Plan([prob], prm)
+    plan.run([2299], device=True)
+    torch.cuda.synchronize()
+    ms_tot, att_tot, best = 0.0, 0, []
+    for k in range(3):
+        flush.add_(1)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.nvtx.range_push("sqa_c8")
+        a.record()
+        o = plan.run([2300 + k], device=True)
+        b.record()
+        torch.cuda.nvtx.range_pop()
+        torch.cuda.synchronize()
+        ms_tot += a.elapsed_time(b)
+        att, _ = plan.stats()
+        att_tot += att
+        best.append(int(o.best_energy.min().item()))
+    # kernel time of the sweeps (a separate, profiled run: it waits for every phase)
+    plan.set_profiling(True)
+    plan.run([2303], device=True)
+    sweep_ms, sweep_n = plan.sweep_time()
+    att_prof, _ = plan.stats()
+    shape = plan.shape()
+    plan.close()
+    ops = PHILOX_OPS_PER_ATTEMPT + 2 * inst.m / inst.n + 2 + ACCEPT_OPS_PER_ATTEMPT  # + two slice neighbours
+    achieved = (att_prof / max(sweep_n, 1)) * ops / (sweep_ms / max(sweep_n, 1) / 1000.0) / 1e12
+    return {"value": att_tot / (ms_tot / 1000.0), "unit": "spin-slice update attempts/s", "ms_per_step": ms_tot / 3,
+            "best_energy": min(best), "sweep_shape": shape,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": ALU_PEAK_TOPS, "unit": "Tops/s",
+                         "frac": achieved / ALU_PEAK_TOPS, "ops_per_attempt": ops,
+                         "ms_per_launch": sweep_ms / max(sweep_n, 1)},
+            "config": "Chimera C8 +-J (N=512, seed 1100), 10 starts x (500 fixing + 500 solving) SQA runs, "
+                      "16 Trotter slices, 1000 sweeps, beta 3.0, transverse field 3.0 -> 0.01 linear, elite 0.1"}
 
 
 def measure_small_configs(spvar, torch):
@@ -488,6 +538,7 @@ def gpu_arm(args, rank, world):
         extra["method_variants_3d_L10"] = measure_method_variants(spvar, torch)
         extra["uneven_batch"] = measure_uneven(spvar, torch, flush)
         extra["serving"] = measure_serving(spvar)
+        extra["sqa_chimera_c8"] = measure_sqa(spvar, torch, flush)
 
     # roofline of the sweep kernel (integer ALU issue bound)
     mean_deg = 2 * inst.m / inst.n
