@@ -425,7 +425,9 @@ int spvar_plan_sweep_time(const spvar_plan *plan, double *total_ms, int32_t *lau
 /* The sweep launch shape the plan chose (autotuned or requested): threads
  * per CTA, replicas per CTA, kernel (0: general kernel reading its layout
  * from global memory, 1: general kernel with the layout staged in shared
- * memory, 2: register-resident +-1 kernel), persistent grid size. */
+ * memory, 2: register-resident +-1 kernel, 3: streaming +-1 kernel, 4:
+ * warp-per-quad +-1 kernel, 5: simulated quantum annealing kernel), persistent
+ * grid size. */
 int spvar_plan_shape(const spvar_plan *plan, int32_t *block, int32_t *replicas_per_block,
                      int32_t *staged, int32_t *grid);
 

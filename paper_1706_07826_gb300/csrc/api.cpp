@@ -513,9 +513,9 @@ int spvar_sqa_sample(const spvar_problem *p, int32_t num_sweeps, int32_t P, cons
     if (num_sweeps > SPVAR_MAX_SWEEPS || num_samples > SPVAR_MAX_SAMPLES) return SPVAR_ELIMIT;
     if (num_samples == 0) return SPVAR_OK;
     if ((num_sweeps > 0 && !ent) || !energies || (H.n > 0 && !spins)) return SPVAR_EINVAL;
-    const bool pm1 = H.pm1 != 0 && sqa_shape_ok(true, 256, H.n, P, W);
-    if (!sqa_shape_ok(pm1, 256, H.n, P, W)) return SPVAR_ELIMIT;
-    const size_t smem = sqa_smem_bytes(H.n, P, H.maxdeg, pm1);
+    const bool pm1 = H.pm1 != 0 && sqa_shape_ok(true, 256, H.n, H.maxdeg, P, W);
+    if (!sqa_shape_ok(pm1, 256, H.n, H.maxdeg, P, W)) return SPVAR_ELIMIT;
+    const size_t smem = sqa_smem_bytes(H.n, P, H.maxdeg, W, pm1);
     if (smem > (size_t)device_smem_optin()) return SPVAR_ELIMIT;
     SweepLaunch L;
     std::memset(&L, 0, sizeof(L));

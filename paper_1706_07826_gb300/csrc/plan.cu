@@ -205,10 +205,10 @@ int plan_nslot(const spvar_plan *pl, int Q, int block)
 // SQA sweep shape for a block size, or kind -1 if the slices do not fit.
 SweepShape sqa_shape(const spvar_plan *pl, int block, int optin)
 {
-    const bool pm1 = pl->pm1 && sqa_shape_ok(true, block, pl->max_n0, pl->sqa_P, pl->sqa_W);
-    SweepShape sh{5, block, 1, pm1 ? 1 : 0, 0, 0};
+    const bool pm1 = pl->pm1 && sqa_shape_ok(true, block, pl->max_n0, pl->max_deg, pl->sqa_P, pl->sqa_W);
+    SweepShape sh{5, block, 1, pm1 ? 1 : 0, pl->sqa_W, pl->max_deg};
     sh.slices = pl->sqa_P;
-    if (!sqa_shape_ok(pm1, block, pl->max_n0, pl->sqa_P, pl->sqa_W) ||
+    if (!sqa_shape_ok(pm1, block, pl->max_n0, pl->max_deg, pl->sqa_P, pl->sqa_W) ||
         sweep_shape_smem(sh, pl->max_n0, pl->thr_stride, pl->max_deg) > (size_t)optin)
         sh.kind = -1;
     return sh;
@@ -717,8 +717,10 @@ int spvar_plan_shape(const spvar_plan *plan, int32_t *block, int32_t *replicas_p
     if (!plan) return SPVAR_EINVAL;
     if (block) *block = plan->shape.block;
     if (replicas_per_block) *replicas_per_block = 4 * plan->shape.Q;
-    if (staged) *staged = plan->shape.kind == 1 ? 2 : plan->shape.kind == 2 ? 3 : plan->shape.kind == 4 ? 4
-                                                                                                : plan->shape.stage;
+    if (staged) {
+        const int k = plan->shape.kind;
+        *staged = k == 1 ? 2 : k == 2 ? 3 : k == 4 ? 4 : k == 5 ? 5 : plan->shape.stage;
+    }
     if (grid) *grid = plan->sweep_grid;
     return SPVAR_OK;
 }

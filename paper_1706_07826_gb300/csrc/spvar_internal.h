@@ -258,10 +258,10 @@ int pm1_max_active_blocks(int block, int nslot, int maxd, size_t smem);
 // Simulated quantum annealing sweep (sweep_sqa.cu): one quad per work item, all
 // Trotter slices in shared memory.
 constexpr int kSqaMaxSlices = 1024;
-bool sqa_shape_ok(bool pm1, int block, int max_n, int P, int W);
-size_t sqa_smem_bytes(int max_n, int P, int maxdeg, bool pm1);
+bool sqa_shape_ok(bool pm1, int block, int max_n, int max_deg, int P, int W);
+size_t sqa_smem_bytes(int max_n, int P, int maxdeg, int W, bool pm1);
 cudaError_t launch_sweep_sqa(const SweepLaunch &L, bool pm1, int block, int grid, size_t smem, cudaStream_t st);
-int sqa_max_active_blocks(bool pm1, int block, size_t smem);
+int sqa_max_active_blocks(bool pm1, int block, int max_deg, size_t smem);
 
 // Streaming +-1 sweep (sweep_pm1s.cu): one quad per work item.
 bool pm1s_shape_ok(int block, int maxd, int max_n, int Q);
@@ -286,7 +286,8 @@ int pm1w_max_active_blocks(int warps, int maxd, size_t smem);
 struct SweepShape {
     int kind, block, Q, stage, nslot, maxd;
     int balance = 0;  // 1: grid sized so that every CTA runs the same number of items
-    int slices = 0;   // kind 5 (SQA): Trotter slices; stage = 1 selects the +-1 SWAR path
+    int slices = 0;   // kind 5 (SQA): Trotter slices; stage = 1 selects the +-1 SWAR path, nslot holds
+                      // the acceptance-table width W and maxd the largest degree
 };
 // The streaming and warp-per-quad kernels apply to +-1 couplers, degree <= 8
 // and dmax <= 254; the register kernel needs dmax <= 30.
@@ -305,7 +306,7 @@ inline int pm1_nslot(const Problem *P, int Q, int block)
 }
 inline size_t sweep_shape_smem(const SweepShape &s, int max_n, int thr_stride, int max_deg)
 {
-    if (s.kind == 5) return sqa_smem_bytes(max_n, s.slices, max_deg, s.stage != 0);
+    if (s.kind == 5) return sqa_smem_bytes(max_n, s.slices, max_deg, s.nslot, s.stage != 0);
     if (s.kind == 1) return pm1_smem_bytes(max_n, s.Q);
     if (s.kind == 2) return pm1s_smem_bytes(max_n, s.Q, s.maxd);
     if (s.kind == 4) return pm1w_smem_bytes(max_n, s.Q, s.maxd);
@@ -322,7 +323,7 @@ inline cudaError_t launch_sweep_shape(const SweepLaunch &L, const SweepShape &s,
 }
 inline int sweep_shape_occupancy(const SweepShape &s, bool pm1, size_t smem)
 {
-    if (s.kind == 5) return sqa_max_active_blocks(s.stage != 0, s.block, smem);
+    if (s.kind == 5) return sqa_max_active_blocks(s.stage != 0, s.block, s.maxd, smem);
     if (s.kind == 1) return pm1_max_active_blocks(s.block, s.nslot, s.maxd, smem);
     if (s.kind == 2) return pm1s_max_active_blocks(s.block, s.maxd, smem);
     if (s.kind == 4) return pm1w_max_active_blocks(s.Q, s.maxd, smem);

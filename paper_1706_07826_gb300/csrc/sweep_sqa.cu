@@ -26,16 +26,22 @@ namespace spvar {
 
 namespace {
 
-// Words of shared memory: spin words (and their inverted copy), 16-bit
-// neighbour offsets (+-1 only), per-slice energy sums and the chosen slices.
-__host__ __device__ inline size_t sqa_words(int max_n, int P, int maxdeg, bool pm1)
+// Shared memory of one CTA, in 32-bit words: the two 64-bit acceptance rows
+// (current and next sweep), spin words [P][n + 1] (word n of every slice is
+// zero: the target of missing neighbours), for +-1 couplers their inverted
+// copy [P][n + 1], per-spin meta and index, 16-bit neighbour offsets, per-slice
+// energy sums and the chosen slices.
+__host__ __device__ inline size_t sqa_words(int max_n, int P, int maxdeg, int W, bool pm1)
 {
-    size_t w = (size_t)P * max_n * (pm1 ? 2 : 1);
-    if (pm1) w += ((size_t)maxdeg * max_n + 1) / 2;
+    const size_t slice = (size_t)max_n + 1;
+    size_t w = 2 * 2 * 3 * (size_t)W;  // two rows of 3W 64-bit entries
+    w += (size_t)P * slice * (pm1 ? 2 : 1);
+    w += 2 * (size_t)max_n;
+    if (pm1) w += ((size_t)(maxdeg <= 6 ? 6 : 8) * max_n + 1) / 2;  // the kernel's unrolled degree
     return w + 4 * (size_t)P + 4;
 }
 
-template <bool PM1, int B>
+template <bool PM1, int B, int MAXD>
 __device__ void run_item_sqa(const SweepLaunch &L, const SweepJob &job, int quad, uint32_t *smem)
 {
     const int tid = threadIdx.x;
@@ -45,56 +51,81 @@ __device__ void run_item_sqa(const SweepLaunch &L, const SweepJob &job, int quad
     const int T = L.T;
     const uint32_t k0 = (uint32_t)job.seed, k1 = (uint32_t)(job.seed >> 32);
     const uint32_t phase_hi = job.phase << kSweepBits;
-    const size_t Pn = (size_t)P * n;
+    const int ns = n + 1;                 // words per slice
+    const size_t Pn = (size_t)P * ns;
 
-    uint32_t *sw = smem;                                   // [P][n] plain
-    uint32_t *swi = sw + (PM1 ? Pn : 0);                   // [P][n] inverted (+-1 only)
-    uint16_t *off = reinterpret_cast<uint16_t *>(sw + (PM1 ? 2 * Pn : Pn));
-    int *e2 = reinterpret_cast<int *>(sw + (PM1 ? 2 * Pn + ((size_t)maxdeg * n + 1) / 2 : Pn));
+    unsigned long long *rows = reinterpret_cast<unsigned long long *>(smem);  // [2][3W]
+    uint32_t *sw = smem + 2 * 2 * 3 * (size_t)W;                            // [P][n + 1] plain
+    uint32_t *swi = sw + (PM1 ? Pn : 0);                                     // [P][n + 1] inverted
+    uint32_t *meta_s = sw + (PM1 ? 2 * Pn : Pn);                             // [n]
+    uint32_t *idx_s = meta_s + n;                                            // [n]
+    uint16_t *off = reinterpret_cast<uint16_t *>(idx_s + n);                 // [MAXD][n] (+-1)
+    int *e2 = reinterpret_cast<int *>(idx_s + n + (PM1 ? ((size_t)MAXD * n + 1) / 2 : 0));
     int *s_best = e2 + 4 * P;
     __shared__ int s_cptr[kMaxColours + 1];
 
     for (int c = tid; c <= ncol; c += B) s_cptr[c] = pr->cptr[c];
+    for (int p = tid; p < n; p += B) {
+        meta_s[p] = pr->meta[p];
+        idx_s[p] = (uint32_t)pr->idx_of_pos[p];
+    }
     // initial state: top bit of the word at the initial-state slot, per slice
     for (size_t x = tid; x < Pn; x += B) {
-        const int tau = (int)(x / n), p = (int)(x - (size_t)tau * n);
-        const uint32_t i = (uint32_t)pr->idx_of_pos[p] | ((uint32_t)tau << 16);
-        const uint4 r = philox4x32_10(make_uint4(i, (job.phase << kSweepBits) | kInitSlot, (uint32_t)quad, job.start),
-                                      k0, k1);
-        const uint32_t w = (r.x >> 31) | ((r.y >> 31) << 8) | ((r.z >> 31) << 16) | ((r.w >> 31) << 24);
+        const int tau = (int)(x / ns), p = (int)(x - (size_t)tau * ns);
+        uint32_t w = 0u;
+        if (p < n) {
+            const uint32_t i = (uint32_t)pr->idx_of_pos[p] | ((uint32_t)tau << 16);
+            const uint4 r = philox4x32_10(
+                make_uint4(i, (job.phase << kSweepBits) | kInitSlot, (uint32_t)quad, job.start), k0, k1);
+            w = (r.x >> 31) | ((r.y >> 31) << 8) | ((r.z >> 31) << 16) | ((r.w >> 31) << 24);
+            if (PM1) swi[x] = w ^ 0x01010101u;
+        } else if (PM1) {
+            swi[x] = 0u;
+        }
         sw[x] = w;
-        if (PM1) swi[x] = w ^ 0x01010101u;
     }
     if (PM1) {
-        for (int x = tid; x < maxdeg * n; x += B) {
+        for (int x = tid; x < MAXD * n; x += B) {
             const int d = x / n, p = x - d * n;
-            const uint32_t e = pr->ell[(size_t)d * cap_n + p];
-            off[x] = (uint16_t)(((e >> 31) ? (int)Pn : 0) + (int)(e & 0xFFFFu));
+            uint16_t o = (uint16_t)n;  // missing neighbour: the slice's zero word
+            if (d < maxdeg) {
+                const uint32_t e = pr->ell[(size_t)d * cap_n + p];
+                if (d < (int)(pr->meta[p] & 0xFFFFu)) o = (uint16_t)(((e >> 31) ? (int)Pn : 0) + (int)(e & 0xFFFFu));
+            }
+            off[x] = o;
         }
     }
+    if (T > 0)
+        for (int x = tid; x < 3 * W; x += B) rows[x] = L.ent[x];
     __syncthreads();
 
     const int nt = (P > 1) ? P / 2 : 1;  // slices per parity
     for (int t = 0; t < T; ++t) {
-        const unsigned long long *ent = L.ent + (size_t)t * 3 * W;
+        const unsigned long long *ent = rows + (t & 1) * 3 * W;
+        if (t + 1 < T)
+            for (int x = tid; x < 3 * W; x += B) rows[((t + 1) & 1) * 3 * W + x] = L.ent[(size_t)(t + 1) * 3 * W + x];
         const uint32_t y = phase_hi | (uint32_t)t;
         for (int c = 0; c < ncol; ++c) {
             const int lo = s_cptr[c], nc = s_cptr[c + 1] - lo;
+            if (nc == 0) continue;
+            // items (slice pair index tq, position k), k fastest, walked without divisions
+            const int dq = B / nc, dk = B - dq * nc;
+            const int q0 = tid / nc, kk0 = tid - q0 * nc;
             for (int par = 0; par < (P > 1 ? 2 : 1); ++par) {
-                for (int it = tid; it < nc * nt; it += B) {
-                    const int tq = it / nc;
-                    const int p = lo + (it - tq * nc);
+                int tq = q0, k = kk0;
+                while (tq < nt) {
+                    const int p = lo + k;
                     const int tau = par + 2 * tq;
-                    const size_t base = (size_t)tau * n;
-                    const uint32_t own = sw[base + p];
-                    const uint32_t meta = __ldg(pr->meta + p);
+                    const uint32_t *s = sw + (size_t)tau * ns;
+                    const uint32_t own = s[p];
+                    const uint32_t meta = meta_s[p];
                     const int deg = (int)(meta & 0xFFFFu);
                     const int h = (int)meta >> 16;
                     // a per byte: slice neighbours equal to the spin (1 for a single slice)
                     uint32_t a4 = 0x01010101u;
                     if (P > 1) {
-                        const uint32_t up = sw[(size_t)(tau + 1 == P ? 0 : tau + 1) * n + p];
-                        const uint32_t dn = sw[(size_t)(tau == 0 ? P - 1 : tau - 1) * n + p];
+                        const uint32_t up = sw[(size_t)(tau + 1 == P ? 0 : tau + 1) * ns + p];
+                        const uint32_t dn = sw[(size_t)(tau == 0 ? P - 1 : tau - 1) * ns + p];
                         a4 = (~(own ^ up) & 0x01010101u) + (~(own ^ dn) & 0x01010101u);
                     }
                     int idx[4];
@@ -102,20 +133,21 @@ __device__ void run_item_sqa(const SweepLaunch &L, const SweepJob &job, int quad
                         // byte r of x: neighbours with b_j ^ [J_ij < 0] = 1; k = 2x + bias - deg + h
                         // for b_i = 0 and its mirror 2 bias - that for b_i = 1
                         uint32_t x = 0;
-                        for (int d = 0; d < deg; ++d) x += sw[base + off[d * n + p]];
+#pragma unroll
+                        for (int d = 0; d < MAXD; ++d) x += s[off[d * n + p]];
                         const uint32_t m = own * 0xFFu;
                         const uint32_t c0 = (uint32_t)(bias - deg + h) * 0x01010101u;
                         const uint32_t c1 = (uint32_t)(bias + deg - h) * 0x01010101u;
                         const uint32_t k4 = ((x + x + c0) & ~m) | ((c1 - x - x) & m);
                         const uint32_t full = a4 * (uint32_t)W + k4;  // bytes <= 3W - 1 <= 255
 #pragma unroll
-                        for (int r = 0; r < 4; ++r) idx[r] = (int)((full >> (8 * r)) & 0xFFu);
+                        for (int r = 0; r < 4; ++r) idx[r] = (int)__byte_perm(full, 0u, 0x4440u | (uint32_t)r);
                     } else {
                         int acc[4] = {0, 0, 0, 0}, sumJ = 0;
                         for (int d = 0; d < deg; ++d) {
                             const uint32_t e = __ldg(pr->ell + (size_t)d * cap_n + p);
                             const int Jv = (int)e >> 16;
-                            const uint32_t w = sw[base + (e & 0xFFFFu)];
+                            const uint32_t w = s[e & 0xFFFFu];
                             sumJ += Jv;
 #pragma unroll
                             for (int r = 0; r < 4; ++r) acc[r] += Jv * (int)((w >> (8 * r)) & 1u);
@@ -124,22 +156,23 @@ __device__ void run_item_sqa(const SweepLaunch &L, const SweepJob &job, int quad
                         for (int r = 0; r < 4; ++r) {
                             // f = h + sum_j J s_j; k = dE/2 + bias = bias - s f
                             const int f = h - sumJ + 2 * acc[r];
-                            const int s = 2 * (int)((own >> (8 * r)) & 1u) - 1;
-                            idx[r] = (int)((a4 >> (8 * r)) & 0xFFu) * W + bias - s * f;
+                            const int sg = 2 * (int)((own >> (8 * r)) & 1u) - 1;
+                            idx[r] = (int)((a4 >> (8 * r)) & 0xFFu) * W + bias - sg * f;
                         }
                     }
-                    const uint32_t i = (uint32_t)__ldg(pr->idx_of_pos + p) | ((uint32_t)tau << 16);
+                    const uint32_t i = idx_s[p] | ((uint32_t)tau << 16);
                     const uint4 u = philox4x32_10(make_uint4(i, y, (uint32_t)quad, job.start), k0, k1);
                     const uint32_t ur[4] = {u.x, u.y, u.z, u.w};
                     uint32_t flip = 0;
 #pragma unroll
-                    for (int r = 0; r < 4; ++r) {
-                        const unsigned long long en = __ldg(ent + idx[r]);
-                        if ((((unsigned long long)ur[r] + en) >> 32) == 0ull) flip |= 1u << (8 * r);
-                    }
+                    for (int r = 0; r < 4; ++r)
+                        if ((((unsigned long long)ur[r] + ent[idx[r]]) >> 32) == 0ull) flip |= 1u << (8 * r);
                     const uint32_t nw = own ^ flip;
-                    sw[base + p] = nw;
-                    if (PM1) swi[base + p] = nw ^ 0x01010101u;
+                    sw[(size_t)tau * ns + p] = nw;
+                    if (PM1) swi[(size_t)tau * ns + p] = nw ^ 0x01010101u;
+                    tq += dq;
+                    k += dk;
+                    if (k >= nc) { k -= nc; ++tq; }
                 }
                 __syncthreads();
             }
@@ -149,10 +182,11 @@ __device__ void run_item_sqa(const SweepLaunch &L, const SweepJob &job, int quad
     // energies of every slice (2E summed per replica), then each run's lowest-energy slice
     for (int x = tid; x < 4 * P; x += B) e2[x] = 0;
     __syncthreads();
-    for (size_t x = tid; x < Pn; x += B) {
+    for (size_t x = tid; x < (size_t)P * n; x += B) {
         const int tau = (int)(x / n), p = (int)(x - (size_t)tau * n);
+        const uint32_t *s = sw + (size_t)tau * ns;
         int c2[4];
-        energy2<PM1>(sw[x], pr->meta[p], pr->ell, cap_n, p, sw + (size_t)tau * n, c2);
+        energy2<PM1>(s[p], meta_s[p], pr->ell, cap_n, p, s, c2);
 #pragma unroll
         for (int r = 0; r < 4; ++r) atomicAdd(&e2[4 * tau + r], c2[r]);
     }
@@ -176,7 +210,7 @@ __device__ void run_item_sqa(const SweepLaunch &L, const SweepJob &job, int quad
         const int pos = (i < n) ? pr->pos_of_idx[i] : 0;
 #pragma unroll
         for (int rr = 0; rr < 4; ++rr) {
-            const uint32_t word = (i < n) ? sw[(size_t)s_best[rr] * n + pos] : 0u;
+            const uint32_t word = (i < n) ? sw[(size_t)s_best[rr] * ns + pos] : 0u;
             const uint32_t bits = __ballot_sync(0xFFFFFFFFu, (word >> (8 * rr)) & 1u);
             const int r = 4 * quad + rr;
             if (lane == 0 && r < job.S) job.spins[(size_t)r * job.W + w] = bits;
@@ -184,7 +218,7 @@ __device__ void run_item_sqa(const SweepLaunch &L, const SweepJob &job, int quad
     }
 }
 
-template <bool PM1, int B>
+template <bool PM1, int B, int MAXD>
 __global__ void __launch_bounds__(B) k_sweep_sqa(const SweepLaunch L)
 {
     extern __shared__ __align__(16) uint32_t smem_sqa[];
@@ -193,36 +227,45 @@ __global__ void __launch_bounds__(B) k_sweep_sqa(const SweepLaunch L)
         SweepJob job;
         int quad0, nq;
         if (!next_item(L, iter, &s_item, job, quad0, nq)) break;
-        run_item_sqa<PM1, B>(L, job, quad0, smem_sqa);
+        run_item_sqa<PM1, B, MAXD>(L, job, quad0, smem_sqa);
         __syncthreads();
     }
 }
 
-void *select_sqa(bool pm1, int block)
+// +-1 couplers: neighbour loop unrolled to MAXD (6 or 8); general couplers: MAXD unused.
+void *select_sqa(bool pm1, int block, int maxdeg)
 {
-#define SPVAR_SQA_CASE(PM, BB) \
-    if (pm1 == PM && block == BB) return reinterpret_cast<void *>(k_sweep_sqa<PM, BB>);
-    SPVAR_SQA_CASE(true, 128) SPVAR_SQA_CASE(true, 256) SPVAR_SQA_CASE(true, 512)
-    SPVAR_SQA_CASE(false, 128) SPVAR_SQA_CASE(false, 256) SPVAR_SQA_CASE(false, 512)
+#define SPVAR_SQA_CASE(PM, BB, MD) \
+    if (pm1 == PM && block == BB) return reinterpret_cast<void *>(k_sweep_sqa<PM, BB, MD>);
+    if (pm1 && maxdeg <= 6) {
+        SPVAR_SQA_CASE(true, 128, 6) SPVAR_SQA_CASE(true, 256, 6) SPVAR_SQA_CASE(true, 512, 6)
+    } else if (pm1 && maxdeg <= 8) {
+        SPVAR_SQA_CASE(true, 128, 8) SPVAR_SQA_CASE(true, 256, 8) SPVAR_SQA_CASE(true, 512, 8)
+    } else if (!pm1) {
+        SPVAR_SQA_CASE(false, 128, 0) SPVAR_SQA_CASE(false, 256, 0) SPVAR_SQA_CASE(false, 512, 0)
+    }
 #undef SPVAR_SQA_CASE
     return nullptr;
 }
 
 }  // namespace
 
-bool sqa_shape_ok(bool pm1, int block, int max_n, int P, int W)
+bool sqa_shape_ok(bool pm1, int block, int max_n, int max_deg, int P, int W)
 {
-    if (!select_sqa(pm1, block) || P < 1 || (P > 1 && (P & 1)) || P > kSqaMaxSlices) return false;
-    if ((long long)max_n >= (1 << 16)) return false;
-    if (pm1 && ((long long)P * max_n + max_n >= 0xFFFF || 3LL * W - 1 > 255)) return false;
+    if (!select_sqa(pm1, block, max_deg) || P < 1 || (P > 1 && (P & 1)) || P > kSqaMaxSlices) return false;
+    if ((long long)max_n >= (1 << 16) - 1) return false;
+    if (pm1 && ((long long)P * (max_n + 1) + max_n >= 0xFFFF || 3LL * W - 1 > 255)) return false;
     return true;
 }
 
-size_t sqa_smem_bytes(int max_n, int P, int maxdeg, bool pm1) { return 4 * sqa_words(max_n, P, maxdeg, pm1); }
+size_t sqa_smem_bytes(int max_n, int P, int maxdeg, int W, bool pm1)
+{
+    return 4 * sqa_words(max_n, P, maxdeg, W, pm1);
+}
 
 cudaError_t launch_sweep_sqa(const SweepLaunch &L, bool pm1, int block, int grid, size_t smem, cudaStream_t st)
 {
-    void *k = select_sqa(pm1, block);
+    void *k = select_sqa(pm1, block, L.max_deg);
     if (!k) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -230,9 +273,9 @@ cudaError_t launch_sweep_sqa(const SweepLaunch &L, bool pm1, int block, int grid
     return cudaLaunchKernel(k, dim3(grid), dim3(block), args, smem, st);
 }
 
-int sqa_max_active_blocks(bool pm1, int block, size_t smem)
+int sqa_max_active_blocks(bool pm1, int block, int max_deg, size_t smem)
 {
-    void *k = select_sqa(pm1, block);
+    void *k = select_sqa(pm1, block, max_deg);
     if (!k) return 0;
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int nb = 0;
