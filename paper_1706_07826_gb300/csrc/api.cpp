@@ -174,6 +174,10 @@ int host_problem_build(int n, const int32_t *row_ptr, const int32_t *col, const 
     H.pm1 = 1;
     for (int i = 0; i < n; ++i) if (h[i] != 0) H.hzero = 0;
     for (int p = 0; p < nnz; ++p) if (val[p] != 1 && val[p] != -1) H.pm1 = 0;
+    H.ujs = 1;
+    for (int i = 0; i < n && H.ujs; ++i)
+        for (int p = row_ptr[i] + 1; p < row_ptr[i + 1]; ++p)
+            if (std::abs(val[p]) != std::abs(val[row_ptr[i]])) { H.ujs = 0; break; }
     H.rho = -1;
     for (int i = 0, best = -1; i < n; ++i)
         if (row_ptr[i + 1] - row_ptr[i] > best) { best = row_ptr[i + 1] - row_ptr[i]; H.rho = i; }
@@ -434,12 +438,25 @@ int spvar_sample_range(const spvar_problem *p, int32_t sweep_begin, int32_t swee
         if (pm1r_kernel_eligible(H.pm1 != 0, H.dmax, H.maxdeg))
             for (int blk : {256, 512, 128}) {
                 const int ns = pm1_nslot(P, Q, blk);
-                if (ns > 0 && pm1_shape_ok(blk, ns, md)) { sh = SweepShape{1, blk, Q, 0, ns, md}; break; }
+                if (ns > 0 && pm1_shape_ok(blk, ns, md, false)) { sh = SweepShape{1, blk, Q, 0, ns, md}; break; }
             }
         // large problems: the streaming kernel (one quad per CTA)
         if (sh.kind == 0 && pm1s_shape_ok(512, md, H.n, 1) &&
             pm1s_smem_bytes(H.n, 1, md) <= (size_t)optin)
             sh = SweepShape{2, 512, 1, 0, 0, md};
+    }
+    if (sh.kind == 0 && ujr_kernel_eligible(H.ujs != 0, H.dmax, H.maxdeg)) {
+        // one coupler magnitude per spin: the register kernel's 16-bit-lane variant
+        const int md = H.maxdeg <= 6 ? 6 : 8;
+        for (int blk : {256, 512, 1024}) {
+            const int ns = pm1_nslot(P, Q, blk);
+            const SweepShape c{1, blk, Q, 1, ns, md};
+            if (ns > 0 && pm1_shape_ok(blk, ns, md, true) &&
+                sweep_shape_smem(c, H.n, thr_stride, H.maxdeg) <= (size_t)optin) {
+                sh = c;
+                break;
+            }
+        }
     }
     if (sh.kind == 0 && sweep_shape_smem(sh, H.n, thr_stride, H.maxdeg) > (size_t)optin) sh.stage = 0;
     const size_t smem = sweep_shape_smem(sh, H.n, thr_stride, H.maxdeg);

@@ -156,6 +156,7 @@ __device__ void reduce_core(const DevProb *S, DevProb *D, const int8_t *fixed, i
         D->dmax = S->dmax;
         D->hzero = s_hnz ? 0 : 1;
         D->pm1 = S->pm1;
+        D->ujs = S->ujs;
         D->rho = (m > 0) ? (0x7FFFFFFF - (int)(s_rho_key & 0xFFFFFFFFll)) : -1;
         D->offset = S->offset + (long long)s_off;
         D->scale = S->scale;

@@ -74,6 +74,8 @@ struct spvar_plan {
     SolveConsts C{};
     int T = 0, thr_stride = 1, max_n0 = 0, max_deg = 1, iters_max = 1;
     bool pm1 = true;
+    bool ujs = true;      // every problem has one coupler magnitude per spin
+    uint64_t sig = 0;     // structure signature of the problems (autotune cache key)
     void *ws = nullptr;
     size_t ws_bytes = 0;
     Slot *d_slots = nullptr;
@@ -109,10 +111,11 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct TuneKey {
     int max_n, max_deg, pm1, S, nslots, form, thr_stride, sqa_P;
+    uint64_t sig;
     bool operator<(const TuneKey &o) const
     {
-        return std::tie(max_n, max_deg, pm1, S, nslots, form, thr_stride, sqa_P) <
-               std::tie(o.max_n, o.max_deg, o.pm1, o.S, o.nslots, o.form, o.thr_stride, o.sqa_P);
+        return std::tie(max_n, max_deg, pm1, S, nslots, form, thr_stride, sqa_P, sig) <
+               std::tie(o.max_n, o.max_deg, o.pm1, o.S, o.nslots, o.form, o.thr_stride, o.sqa_P, o.sig);
     }
 };
 std::map<TuneKey, SweepShape> g_tune_cache;
@@ -258,11 +261,25 @@ std::vector<SweepShape> candidate_shapes(const spvar_plan *pl, int optin)
                 const int ns = plan_nslot(pl, Q, blocks[bi]);
                 const int md = pl->max_deg <= 6 ? 6 : 8;
                 SweepShape sh{1, blocks[bi], Q, 0, ns, md};
-                if (ns > 0 && pm1_shape_ok(blocks[bi], ns, md) &&
+                if (ns > 0 && pm1_shape_ok(blocks[bi], ns, md, false) &&
                     sweep_shape_smem(sh, pl->max_n0, pl->thr_stride, pl->max_deg) <= (size_t)optin)
                     out.push_back(sh);
             }
         }
+    if (!pm1r_kernel_eligible(pl->pm1, pl->dmax, pl->max_deg) && ujr_kernel_eligible(pl->ujs, pl->dmax, pl->max_deg)) {
+        // one coupler magnitude per spin: the register kernel's 16-bit-lane variant
+        const int md = pl->max_deg <= 6 ? 6 : 8;
+        for (int blk : {256, 512, 1024})
+            for (int Q : {1, 2, 4}) {
+                if (Q > 1 && quads < Q) continue;
+                int ns = plan_nslot(pl, Q, blk);
+                if (ns == 3) ns = 4;
+                SweepShape sh{1, blk, Q, 1, ns, md};
+                if (ns > 0 && pm1_shape_ok(blk, ns, md, true) &&
+                    sweep_shape_smem(sh, pl->max_n0, pl->thr_stride, pl->max_deg) <= (size_t)optin)
+                    out.push_back(sh);
+            }
+    }
     return out;
 }
 
@@ -271,7 +288,7 @@ std::vector<SweepShape> candidate_shapes(const spvar_plan *pl, int optin)
 void autotune(spvar_plan *pl, cudaStream_t st, int optin)
 {
     const TuneKey key{pl->max_n0, pl->max_deg, pl->pm1 ? 1 : 0, pl->C.S_fix, pl->C.nslots,
-                      pl->prm.form, pl->thr_stride, pl->sqa_P};
+                      pl->prm.form, pl->thr_stride, pl->sqa_P, pl->sig};
     {
         std::lock_guard<std::mutex> g(g_tune_mu);
         auto it = g_tune_cache.find(key);
@@ -389,6 +406,13 @@ int spvar_plan_create(const spvar_problem *const *problems, int32_t nproblems,
         pl->max_n0 = std::max(pl->max_n0, P->hdr.n);
         pl->max_deg = std::max(pl->max_deg, P->hdr.maxdeg);
         if (!P->hdr.pm1) pl->pm1 = false;
+        if (!P->hdr.ujs) pl->ujs = false;
+        // colour classes, coupler kind and dmax decide which shapes are valid
+        auto mix = [&](uint64_t v) { pl->sig = (pl->sig ^ v) * 1099511628211ull; };
+        mix((uint64_t)P->hdr.ncol);
+        for (int c = 0; c < P->hdr.ncol; ++c) mix((uint64_t)P->csize[c]);
+        mix((uint64_t)P->hdr.pm1 << 1 | (uint64_t)P->hdr.ujs);
+        mix((uint64_t)P->hdr.dmax);
     }
     pl->T = p.num_sweeps;
     pl->thr_stride = dmax + 1;
@@ -572,12 +596,25 @@ int spvar_plan_create(const spvar_problem *const *problems, int32_t nproblems,
             sh = sqa_shape(pl, blk, optin);
             if (Q != 1 || sh.kind != 5) { plan_free(pl); return SPVAR_ELIMIT; }
         } else if (p.sweep_kernel == SPVAR_SWEEP_PM1 || (p.sweep_kernel == SPVAR_SWEEP_AUTO && elig)) {
-            const int ns = pm1r_kernel_eligible(pl->pm1, pl->dmax, pl->max_deg) ? plan_nslot(pl, Q, blk) : 0;
             const int md = pl->max_deg <= 6 ? 6 : 8;
-            if (!elig) { plan_free(pl); return SPVAR_ELIMIT; }
-            if (ns > 0 && pm1_shape_ok(blk, ns, md)) sh = SweepShape{1, blk, Q, 0, ns, md};
-            else if (pm1s_shape_ok(blk, md, pl->max_n0, Q)) sh = SweepShape{2, blk, Q, 0, 0, md};
-            else { plan_free(pl); return SPVAR_ELIMIT; }
+            if (elig) {
+                const int ns = pm1r_kernel_eligible(pl->pm1, pl->dmax, pl->max_deg) ? plan_nslot(pl, Q, blk) : 0;
+                if (ns > 0 && pm1_shape_ok(blk, ns, md, false)) sh = SweepShape{1, blk, Q, 0, ns, md};
+                else if (pm1s_shape_ok(blk, md, pl->max_n0, Q)) sh = SweepShape{2, blk, Q, 0, 0, md};
+                else { plan_free(pl); return SPVAR_ELIMIT; }
+            } else if (ujr_kernel_eligible(pl->ujs, pl->dmax, pl->max_deg)) {
+                // one coupler magnitude per spin: the register kernel's 16-bit-lane variant
+                int ns = plan_nslot(pl, Q, blk);
+                if (ns == 3) ns = 4;
+                const SweepShape c{1, blk, Q, 1, ns, md};
+                if (ns > 0 && pm1_shape_ok(blk, ns, md, true) &&
+                    sweep_shape_smem(c, pl->max_n0, pl->thr_stride, pl->max_deg) <= (size_t)optin)
+                    sh = c;
+                else { plan_free(pl); return SPVAR_ELIMIT; }
+            } else {
+                plan_free(pl);
+                return SPVAR_ELIMIT;
+            }
         } else if (p.sweep_kernel == SPVAR_SWEEP_PM1W) {
             const int md = pl->max_deg <= 6 ? 6 : 8;
             if (!elig || !pm1w_shape_ok(Q, md, pl->max_n0)) { plan_free(pl); return SPVAR_ELIMIT; }

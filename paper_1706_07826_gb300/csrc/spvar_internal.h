@@ -27,7 +27,8 @@ struct DevProb {
     int32_t n, nnz, ncol, maxdeg;  // maxdeg: ELL rows (an upper bound on every row length)
     int32_t dmax, hzero, pm1, rho; // rho: lowest-index spin of maximum degree (-1 if n == 0)
     int64_t offset;
-    int32_t cap_n, cap_nnz, scale, pad0;
+    int32_t cap_n, cap_nnz, scale;
+    int32_t ujs;         // 1: the couplers of every spin share one magnitude
     int32_t *row_ptr;    // [cap_n + 1]
     int32_t *col;        // [cap_nnz]
     int32_t *val;        // [cap_nnz]
@@ -249,11 +250,11 @@ cudaError_t launch_sweep(const SweepLaunch &L, bool pm1, int block, int grid, si
 int sweep_max_active_blocks(bool pm1, int block, size_t smem, bool stage_ell);
 
 // Register-resident +-1 sweep (sweep_pm1.cu).
-bool pm1_shape_ok(int block, int nslot, int maxd);
-size_t pm1_smem_bytes(int max_n, int Q);
-cudaError_t launch_sweep_pm1(const SweepLaunch &L, int block, int nslot, int maxd, int grid, size_t smem,
+bool pm1_shape_ok(int block, int nslot, int maxd, bool scaled);
+size_t pm1_smem_bytes(bool scaled, int thr_stride);
+cudaError_t launch_sweep_pm1(const SweepLaunch &L, int block, int nslot, int maxd, bool scaled, int grid, size_t smem,
                              cudaStream_t st);
-int pm1_max_active_blocks(int block, int nslot, int maxd, size_t smem);
+int pm1_max_active_blocks(int block, int nslot, int maxd, bool scaled, size_t smem);
 
 // Simulated quantum annealing sweep (sweep_sqa.cu): one quad per work item, all
 // Trotter slices in shared memory.
@@ -276,8 +277,9 @@ cudaError_t launch_sweep_pm1w(const SweepLaunch &L, int warps, int maxd, int gri
 int pm1w_max_active_blocks(int warps, int maxd, size_t smem);
 
 // Launch shape of a sweep: kind 0 = general kernel (stage: layout staged in
-// shared memory), kind 1 = register-resident +-1 kernel (nslot items per
-// thread, maxd neighbour registers per item), kind 2 = streaming +-1 kernel
+// shared memory), kind 1 = register-resident kernel (nslot items per thread,
+// maxd neighbour registers per item; stage = 1: the 16-bit-lane variant for
+// one coupler magnitude per spin), kind 2 = streaming +-1 kernel
 // (maxd neighbour offsets per spin staged in shared memory, Q = 1), kind 4 =
 // warp-per-quad +-1 kernel (Q = warps = block / 32), kind 5 = simulated
 // quantum annealing (Q = 1).  A persistent grid holds
@@ -293,6 +295,8 @@ struct SweepShape {
 // and dmax <= 254; the register kernel needs dmax <= 30.
 inline bool pm1_kernel_eligible(bool pm1, int dmax, int maxdeg) { return pm1 && dmax <= 254 && maxdeg <= 8; }
 inline bool pm1r_kernel_eligible(bool pm1, int dmax, int maxdeg) { return pm1 && dmax <= 30 && maxdeg <= 8; }
+// The register kernel's 16-bit-lane variant: one coupler magnitude per spin, dmax <= 4094.
+inline bool ujr_kernel_eligible(bool ujs, int dmax, int maxdeg) { return ujs && dmax <= 4094 && maxdeg <= 8; }
 // Slots per thread the register kernel needs for problem P at Q quads per CTA
 // (every colour class fills whole slots), rounded up to an instantiated count
 // (2..4); 0 if more than 4.  Reductions only shrink classes, so the original
@@ -307,7 +311,7 @@ inline int pm1_nslot(const Problem *P, int Q, int block)
 inline size_t sweep_shape_smem(const SweepShape &s, int max_n, int thr_stride, int max_deg)
 {
     if (s.kind == 5) return sqa_smem_bytes(max_n, s.slices, max_deg, s.nslot, s.stage != 0);
-    if (s.kind == 1) return pm1_smem_bytes(max_n, s.Q);
+    if (s.kind == 1) return pm1_smem_bytes(s.stage != 0, thr_stride);
     if (s.kind == 2) return pm1s_smem_bytes(max_n, s.Q, s.maxd);
     if (s.kind == 4) return pm1w_smem_bytes(max_n, s.Q, s.maxd);
     return sweep_smem_bytes(max_n, s.Q, thr_stride, max_deg, s.stage != 0);
@@ -316,7 +320,7 @@ inline cudaError_t launch_sweep_shape(const SweepLaunch &L, const SweepShape &s,
                                       cudaStream_t st)
 {
     if (s.kind == 5) return launch_sweep_sqa(L, s.stage != 0, s.block, grid, smem, st);
-    if (s.kind == 1) return launch_sweep_pm1(L, s.block, s.nslot, s.maxd, grid, smem, st);
+    if (s.kind == 1) return launch_sweep_pm1(L, s.block, s.nslot, s.maxd, s.stage != 0, grid, smem, st);
     if (s.kind == 2) return launch_sweep_pm1s(L, s.block, s.maxd, grid, smem, st);
     if (s.kind == 4) return launch_sweep_pm1w(L, s.Q, s.maxd, grid, smem, st);
     return launch_sweep(L, pm1, s.block, grid, smem, st);
@@ -324,7 +328,7 @@ inline cudaError_t launch_sweep_shape(const SweepLaunch &L, const SweepShape &s,
 inline int sweep_shape_occupancy(const SweepShape &s, bool pm1, size_t smem)
 {
     if (s.kind == 5) return sqa_max_active_blocks(s.stage != 0, s.block, s.maxd, smem);
-    if (s.kind == 1) return pm1_max_active_blocks(s.block, s.nslot, s.maxd, smem);
+    if (s.kind == 1) return pm1_max_active_blocks(s.block, s.nslot, s.maxd, s.stage != 0, smem);
     if (s.kind == 2) return pm1s_max_active_blocks(s.block, s.maxd, smem);
     if (s.kind == 4) return pm1w_max_active_blocks(s.Q, s.maxd, smem);
     return sweep_max_active_blocks(pm1, s.block, smem, s.stage != 0);

@@ -23,6 +23,13 @@
 //    replicas' reject bits.
 // Eligible when every |J| = 1, degree <= MAXD and dmax <= 30 (so that the
 // scaled index 8 (dE/2 + bias) fits a byte).
+//
+// SCALED variant, for couplers whose magnitude is one value J0_i per spin
+// (weak-strong cluster problems: every |J| = 100): the byte-wise neighbour sum
+// is the same, the local field is h + J0 (2x - deg), and the flip-cost index
+// 16 (dE/2 + bias) of two replicas at a time is formed in 16-bit lanes; the
+// two acceptance rows (2 dmax + 2 entries) are interleaved in dynamic shared
+// memory.  Needs dmax <= 4094.
 #include "sweep_common.cuh"
 
 namespace spvar {
@@ -36,7 +43,8 @@ template <int MAXD>
 struct SlotRegs {
     uint32_t own;       // byte offset of the item's spin word (plain copy)
     uint32_t nb[MAXD];  // byte offsets of the neighbours (inverted copy if J < 0, zero word if padding)
-    uint32_t c0;        // per byte: 8 (bias - deg + h)
+    uint32_t c0;        // per byte: 8 (bias - deg + h); SCALED: per 16-bit lane 16 (bias + h - J0 deg)
+    uint32_t tj;        // SCALED: 32 J0
     uint32_t A, L0k, D, H3k, L3;  // Philox rounds 1-3 folded with the item's fixed counter words
 };
 
@@ -140,18 +148,24 @@ struct Pm1Smem {
 // slot (lanes without an item anneal the dummy word: no branch per slot); a
 // barrier precedes slot j when it starts a new colour class (bit j of
 // barmask) and closes the sweep.
-template <int B, int NSLOT, int MAXD, int PAR>
-__device__ __forceinline__ void sweep_once(Pm1Smem<B, NSLOT> &sm, const SlotRegs<MAXD> (&s)[NSLOT], uint32_t y,
+template <int B, int NSLOT, int MAXD, bool SCALED, int PAR>
+__device__ __forceinline__ void sweep_once(Pm1Smem<B, NSLOT> &sm, unsigned long long *drow,
+                                           const SlotRegs<MAXD> (&s)[NSLOT], uint32_t y,
                                            const RoundKeys &K, uint32_t barmask, uint32_t one,
                                            uint32_t k16, const uint32_t *next_src, int bias)
 {
     constexpr uint32_t kInv = 4u * (uint32_t)Pm1Smem<B, NSLOT>::KW;  // byte distance to the inverted copy
     // next sweep's row (its buffer was last read in the previous sweep)
-    if (next_src && (int)threadIdx.x < bias) {
+    if (SCALED) {
+        if (next_src)
+            for (int e = (int)threadIdx.x + 1; e <= bias; e += B)
+                drow[2 * (bias + e) + (PAR ^ 1)] = (1ull << 32) - (unsigned long long)next_src[2 * e];
+    } else if (next_src && (int)threadIdx.x < bias) {
         const int e = (int)threadIdx.x + 1;
         sm.row[PAR ^ 1][bias + e] = (1ull << 32) - (unsigned long long)next_src[2 * e];
     }
-    const char *rowb = reinterpret_cast<const char *>(sm.row[PAR]);
+    const char *rowb = SCALED ? reinterpret_cast<const char *>(drow) + 8 * PAR
+                              : reinterpret_cast<const char *>(sm.row[PAR]);
 #pragma unroll
     for (int j = 0; j < NSLOT; ++j) {
         if (barmask & (1u << j)) __syncthreads();
@@ -164,19 +178,37 @@ __device__ __forceinline__ void sweep_once(Pm1Smem<B, NSLOT> &sm, const SlotRegs
             uint32_t x = 0;
 #pragma unroll
             for (int d = 0; d < MAXD; ++d) x += nbw[d];
-            // byte r of x: neighbours with b_j ^ [J_ij < 0] = 1; the flip-cost index
-            // dE/2 + bias is 2x + bias - deg + h if b_i = 0 and its mirror 2 bias - that
-            // if b_i = 1; all scaled by 8 (the byte offset of a 64-bit row entry)
-            const uint32_t a = mad_lo(x, 16u * one, s[j].c0);
-            const uint32_t b = mad_lo(a, 0u - one, k16);
-            const uint32_t m = own * 0xFFu;
-            const uint32_t idx8 = (a & ~m) | (b & m);
+            // byte r of x: neighbours with b_j ^ [J_ij < 0] = 1
+            uint32_t off[4];
+            if (SCALED) {
+                // replicas (0, 2) and (1, 3) in 16-bit lanes: 16 (dE/2 + bias) is
+                // 16 (bias + h - J0 deg) + 32 J0 x for b_i = 0 and 32 bias minus that for b_i = 1
+                const uint32_t xl = __byte_perm(x, 0u, 0x4240u), xh = __byte_perm(x, 0u, 0x4341u);
+                const uint32_t ml = __byte_perm(own, 0u, 0x4240u) * 0xFFFFu;
+                const uint32_t mh = __byte_perm(own, 0u, 0x4341u) * 0xFFFFu;
+                const uint32_t al = mad_lo(xl, s[j].tj, s[j].c0), ah = mad_lo(xh, s[j].tj, s[j].c0);
+                const uint32_t bl = mad_lo(al, 0u - one, k16), bh = mad_lo(ah, 0u - one, k16);
+                const uint32_t kl = (al & ~ml) | (bl & ml), kh = (ah & ~mh) | (bh & mh);
+                off[0] = kl & 0xFFFFu;
+                off[1] = kh & 0xFFFFu;
+                off[2] = kl >> 16;
+                off[3] = kh >> 16;
+            } else {
+                // the flip-cost index dE/2 + bias is 2x + bias - deg + h if b_i = 0 and its
+                // mirror 2 bias - that if b_i = 1; all scaled by 8 (the byte offset of a
+                // 64-bit row entry)
+                const uint32_t a = mad_lo(x, 16u * one, s[j].c0);
+                const uint32_t b = mad_lo(a, 0u - one, k16);
+                const uint32_t m = own * 0xFFu;
+                const uint32_t idx8 = (a & ~m) | (b & m);
+#pragma unroll
+                for (int r = 0; r < 4; ++r) off[r] = __byte_perm(idx8, 0u, 0x4440u | (uint32_t)r);
+            }
             const uint32_t ur[4] = {u.x, u.y, u.z, u.w};
             uint32_t rej = 0;
 #pragma unroll
             for (int r = 0; r < 4; ++r) {
-                const uint32_t off = __byte_perm(idx8, 0u, 0x4440u | (uint32_t)r);
-                const unsigned long long ent = *reinterpret_cast<const unsigned long long *>(rowb + off);
+                const unsigned long long ent = *reinterpret_cast<const unsigned long long *>(rowb + off[r]);
                 const uint32_t carry = mad_wide_hi(ur[r], one, ent);
                 rej = r == 0 ? carry : mad_lo(carry, one << (8 * r), rej);
             }
@@ -189,8 +221,9 @@ __device__ __forceinline__ void sweep_once(Pm1Smem<B, NSLOT> &sm, const SlotRegs
     __syncthreads();
 }
 
-template <int B, int NSLOT, int MAXD>
-__device__ void run_item_pm1(const SweepLaunch &L, const SweepJob &job, int quad0, int nq, Pm1Smem<B, NSLOT> &sm)
+template <int B, int NSLOT, int MAXD, bool SCALED>
+__device__ void run_item_pm1(const SweepLaunch &L, const SweepJob &job, int quad0, int nq, Pm1Smem<B, NSLOT> &sm,
+                             unsigned long long *drow)
 {
     constexpr int KW = Pm1Smem<B, NSLOT>::KW;
     const int tid = threadIdx.x;
@@ -214,12 +247,23 @@ __device__ void run_item_pm1(const SweepLaunch &L, const SweepJob &job, int quad
         sm.sw[2 * KW] = 0u;
     }
     // threshold rows: entry i = 2^32 - thr[t][2 (i - bias)] for i > bias, 0 (always accept) otherwise
-    for (int i = tid; i < 2 * kRowE; i += B) {
-        const int par = i / kRowE, e = i % kRowE - bias;
-        unsigned long long v = 0;
-        if (e > 0 && e <= bias && par == (t0 & 1) && t0 < T)
-            v = (1ull << 32) - (unsigned long long)L.thr[(size_t)t0 * L.thr_stride + 2 * e];
-        sm.row[par][i % kRowE] = v;
+    if (SCALED) {
+        // two rows interleaved: entry i of row par at 2 i + par
+        for (int x = tid; x < 2 * (2 * bias + 1); x += B) {
+            const int par = x & 1, e = (x >> 1) - bias;
+            unsigned long long v = 0;
+            if (e > 0 && par == (t0 & 1) && t0 < T)
+                v = (1ull << 32) - (unsigned long long)L.thr[(size_t)t0 * L.thr_stride + 2 * e];
+            drow[x] = v;
+        }
+    } else {
+        for (int i = tid; i < 2 * kRowE; i += B) {
+            const int par = i / kRowE, e = i % kRowE - bias;
+            unsigned long long v = 0;
+            if (e > 0 && e <= bias && par == (t0 & 1) && t0 < T)
+                v = (1ull << 32) - (unsigned long long)L.thr[(size_t)t0 * L.thr_stride + 2 * e];
+            sm.row[par][i % kRowE] = v;
+        }
     }
     __syncthreads();
 
@@ -233,7 +277,8 @@ __device__ void run_item_pm1(const SweepLaunch &L, const SweepJob &job, int quad
         s[j].own = dummy;
 #pragma unroll
         for (int d = 0; d < MAXD; ++d) s[j].nb[d] = zero;
-        s[j].c0 = (uint32_t)(8 * bias) * 0x01010101u;
+        s[j].c0 = SCALED ? (uint32_t)(16 * bias) * 0x00010001u : (uint32_t)(8 * bias) * 0x01010101u;
+        s[j].tj = 0u;
         s[j].A = s[j].L0k = s[j].D = s[j].H3k = s[j].L3 = 0u;
         // colour class of slot j
         int c = 0, jb = 0, items = 0;
@@ -261,88 +306,107 @@ __device__ void run_item_pm1(const SweepLaunch &L, const SweepJob &job, int quad
                         s[j].nb[d] = 4u * (uint32_t)(((e >> 31) ? KW : 0) + q * n + (int)(e & 0xFFFFu));
                     }
                 }
-                s[j].c0 = (uint32_t)(8 * (bias - deg + h)) * 0x01010101u;
+                if (SCALED) {
+                    // one coupler magnitude J0 per spin
+                    const int J0 = deg > 0 ? abs((int)P->ell[p] >> 16) : 0;
+                    s[j].c0 = (uint32_t)(16 * (bias + h - J0 * deg)) * 0x00010001u;
+                    s[j].tj = (uint32_t)(32 * J0);
+                } else {
+                    s[j].c0 = (uint32_t)(8 * (bias - deg + h)) * 0x01010101u;
+                }
                 philox_setup(s[j], (uint32_t)P->idx_of_pos[p], (uint32_t)(quad0 + q), job.start, k0, k1);
             }
         }
     }
-    const uint32_t k16 = (uint32_t)(16 * bias) * 0x01010101u;
+    const uint32_t k16 = SCALED ? (uint32_t)(32 * bias) * 0x00010001u : (uint32_t)(16 * bias) * 0x01010101u;
     const uint32_t *thr = L.thr;
     const size_t ts = (size_t)L.thr_stride;
 
     int t = t0;
     if (t < T && (t & 1)) {
-        sweep_once<B, NSLOT, MAXD, 1>(sm, s, phase_hi | (uint32_t)t, K, barmask, one, k16,
+        sweep_once<B, NSLOT, MAXD, SCALED, 1>(sm, drow, s, phase_hi | (uint32_t)t, K, barmask, one, k16,
                                       t + 1 < T ? thr + (size_t)(t + 1) * ts : nullptr, bias);
         ++t;
     }
     for (; t + 1 < T; t += 2) {
-        sweep_once<B, NSLOT, MAXD, 0>(sm, s, phase_hi | (uint32_t)t, K, barmask, one, k16,
+        sweep_once<B, NSLOT, MAXD, SCALED, 0>(sm, drow, s, phase_hi | (uint32_t)t, K, barmask, one, k16,
                                       thr + (size_t)(t + 1) * ts, bias);
-        sweep_once<B, NSLOT, MAXD, 1>(sm, s, phase_hi | (uint32_t)(t + 1), K, barmask, one, k16,
+        sweep_once<B, NSLOT, MAXD, SCALED, 1>(sm, drow, s, phase_hi | (uint32_t)(t + 1), K, barmask, one, k16,
                                       t + 2 < T ? thr + (size_t)(t + 2) * ts : nullptr, bias);
     }
     if (t < T)
-        sweep_once<B, NSLOT, MAXD, 0>(sm, s, phase_hi | (uint32_t)t, K, barmask, one, k16, nullptr, bias);
+        sweep_once<B, NSLOT, MAXD, SCALED, 0>(sm, drow, s, phase_hi | (uint32_t)t, K, barmask, one, k16, nullptr, bias);
     // the inverted copy is dead now: its first 4 nq words hold the energy sums
     finish_item<true>(P, job, quad0, nq, sm.sw, reinterpret_cast<int *>(sm.sw + KW));
 }
 
-template <int B, int NSLOT, int MAXD>
+template <int B, int NSLOT, int MAXD, bool SCALED>
 __global__ void __launch_bounds__(B) k_sweep_pm1(const SweepLaunch L)
 {
     __shared__ Pm1Smem<B, NSLOT> sm;
+    extern __shared__ __align__(16) unsigned long long drow_pm1[];  // SCALED: the two acceptance rows
     __shared__ int s_item;
     for (int iter = 0;; ++iter) {
         SweepJob job;
         int quad0, nq;
         if (!next_item(L, iter, &s_item, job, quad0, nq)) break;
-        run_item_pm1<B, NSLOT, MAXD>(L, job, quad0, nq, sm);
+        run_item_pm1<B, NSLOT, MAXD, SCALED>(L, job, quad0, nq, sm, drow_pm1);
         __syncthreads();
     }
 }
 
-template <int B, int NSLOT, int MAXD>
+template <int B, int NSLOT, int MAXD, bool SCALED>
 void *kernel_ptr()
 {
-    return reinterpret_cast<void *>(k_sweep_pm1<B, NSLOT, MAXD>);
+    return reinterpret_cast<void *>(k_sweep_pm1<B, NSLOT, MAXD, SCALED>);
 }
 
-void *select_kernel(int block, int nslot, int maxd)
+void *select_kernel(int block, int nslot, int maxd, bool scaled)
 {
 #define SPVAR_PM1_CASE(BB, NS, MD) \
-    if (block == BB && nslot == NS && maxd == MD) return kernel_ptr<BB, NS, MD>();
+    if (!scaled && block == BB && nslot == NS && maxd == MD) return kernel_ptr<BB, NS, MD, false>();
+#define SPVAR_UJ_CASE(BB, NS, MD) \
+    if (scaled && block == BB && nslot == NS && maxd == MD) return kernel_ptr<BB, NS, MD, true>();
     SPVAR_PM1_CASE(128, 2, 6) SPVAR_PM1_CASE(128, 3, 6) SPVAR_PM1_CASE(128, 4, 6)
     SPVAR_PM1_CASE(256, 2, 6) SPVAR_PM1_CASE(256, 3, 6) SPVAR_PM1_CASE(256, 4, 6)
-    SPVAR_PM1_CASE(512, 2, 6)
+    SPVAR_PM1_CASE(512, 2, 6) SPVAR_PM1_CASE(1024, 2, 6)
     SPVAR_PM1_CASE(128, 2, 8) SPVAR_PM1_CASE(128, 3, 8) SPVAR_PM1_CASE(128, 4, 8)
     SPVAR_PM1_CASE(256, 2, 8) SPVAR_PM1_CASE(256, 3, 8) SPVAR_PM1_CASE(256, 4, 8)
-    SPVAR_PM1_CASE(512, 2, 8)
+    SPVAR_PM1_CASE(512, 2, 8) SPVAR_PM1_CASE(1024, 2, 8)
+    SPVAR_UJ_CASE(256, 2, 6) SPVAR_UJ_CASE(256, 4, 6) SPVAR_UJ_CASE(512, 2, 6) SPVAR_UJ_CASE(1024, 2, 6)
+    SPVAR_UJ_CASE(256, 2, 8) SPVAR_UJ_CASE(256, 4, 8) SPVAR_UJ_CASE(512, 2, 8) SPVAR_UJ_CASE(1024, 2, 8)
 #undef SPVAR_PM1_CASE
+#undef SPVAR_UJ_CASE
     return nullptr;
 }
 
 }  // namespace
 
-bool pm1_shape_ok(int block, int nslot, int maxd) { return select_kernel(block, nslot, maxd) != nullptr; }
+bool pm1_shape_ok(int block, int nslot, int maxd, bool scaled) { return select_kernel(block, nslot, maxd, scaled) != nullptr; }
 
-size_t pm1_smem_bytes(int, int) { return 0; }  // all shared memory is static
+// SCALED: two interleaved rows of thr_stride (= dmax + 1 >= 2 bias + 1) 64-bit entries.
+size_t pm1_smem_bytes(bool scaled, int thr_stride) { return scaled ? 2 * 8 * (size_t)thr_stride : 0; }
 
-cudaError_t launch_sweep_pm1(const SweepLaunch &L, int block, int nslot, int maxd, int grid, size_t,
-                             cudaStream_t st)
+cudaError_t launch_sweep_pm1(const SweepLaunch &L, int block, int nslot, int maxd, bool scaled, int grid,
+                             size_t smem, cudaStream_t st)
 {
-    void *k = select_kernel(block, nslot, maxd);
+    void *k = select_kernel(block, nslot, maxd, scaled);
     if (!k) return cudaErrorInvalidValue;
+    if (scaled) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
     void *args[] = {const_cast<SweepLaunch *>(&L)};
-    return cudaLaunchKernel(k, dim3(grid), dim3(block), args, 0, st);
+    return cudaLaunchKernel(k, dim3(grid), dim3(block), args, scaled ? smem : 0, st);
 }
 
-int pm1_max_active_blocks(int block, int nslot, int maxd, size_t)
+int pm1_max_active_blocks(int block, int nslot, int maxd, bool scaled, size_t smem)
 {
-    void *k = select_kernel(block, nslot, maxd);
+    void *k = select_kernel(block, nslot, maxd, scaled);
     if (!k) return 0;
+    if (scaled) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int nb = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, block, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, block, scaled ? smem : 0);
     return nb;
 }
 

@@ -17,6 +17,8 @@ CASES = [
     ("weak_strong_C3", lambda: I.weak_strong(3, 1300), 22, 120),
     ("random_general", lambda: I.random_graph(40, 90, 5, jmax=7, hmax=9), 13, 100),
     ("pm1_with_h", lambda: with_h(I.cubic3d(3, 8), 4, 3), 9, 80),
+    ("pm1_big_h", lambda: with_h(I.cubic3d(4, 9), 3, 20), 17, 80),
+    ("weak_strong_C6", lambda: I.weak_strong(6, 1301), 41, 100),
     ("isolated", isolated_spins, 11, 40),
     ("single_spin", single_spin, 5, 20),
     ("empty", empty, 4, 10),

@@ -8,7 +8,7 @@ import pytest
 from oracle import oracle as O
 from paper_1706_07826_gb300 import instances as I
 
-from gpu_cases import gpu_problem, oracle_problem, table
+from gpu_cases import gpu_problem, oracle_problem, table, with_h
 
 pytestmark = pytest.mark.gpu
 
@@ -82,11 +82,36 @@ def test_solve_identical_for_every_sweep_shape(cuda_lib, rpb, kernel, block, mak
 
 
 def test_register_kernel_rejects_general_couplers(cuda_lib):
+    """Couplers of several magnitudes at one spin have no register-kernel form."""
     from paper_1706_07826_gb300 import spvar
     prm = spvar.make_params(num_starts=1, fixing_sample_size=8, solving_sample_size=8, num_sweeps=4,
                             replicas_per_block=4, sweep_kernel=spvar.SWEEP_PM1)
     with pytest.raises(spvar.SpvarError):
-        spvar.Plan([gpu_problem(I.weak_strong(2, 1))], prm)
+        spvar.Plan([gpu_problem(I.random_graph(30, 60, 2, jmax=5, hmax=3))], prm)
+
+
+UJ_SHAPES = [(4, 256), (8, 256), (16, 256), (4, 512), (4, 1024), (8, 1024)]
+
+
+@pytest.mark.parametrize("rpb,block", UJ_SHAPES, ids=["%d-%d" % s for s in UJ_SHAPES])
+@pytest.mark.parametrize("make", [lambda: I.weak_strong(2, 61), lambda: with_h(I.cubic3d(4, 62), 5, 20)],
+                         ids=["weak_strong_x100", "pm1_big_h"])
+def test_register_kernel_one_magnitude_per_spin(cuda_lib, rpb, block, make):
+    """The register kernel's 16-bit-lane variant (one coupler magnitude per
+    spin: weak-strong problems, +-1 problems with large biases): identical to
+    the oracle for several launch shapes."""
+    from paper_1706_07826_gb300 import spvar
+    inst = make()
+    T, seed = 50, 19
+    ref = _oracle_solve(inst, T, seed, num_starts=2, fixing_sample_size=45, solving_sample_size=45,
+                        elite_threshold=0.2)
+    prm = spvar.make_params(num_starts=2, fixing_sample_size=45, solving_sample_size=45, num_sweeps=T,
+                            elite_threshold=0.2, replicas_per_block=rpb, sweep_kernel=spvar.SWEEP_PM1,
+                            sweep_block=block)
+    plan = spvar.Plan([gpu_problem(inst)], prm)
+    assert plan.shape()["kernel"] == "pm1-register"
+    _check(plan.run([seed], device=False), ref, 2, 2, inst.n)
+    plan.close()
 
 
 def test_profiling_reports_sweep_time(cuda_lib):
