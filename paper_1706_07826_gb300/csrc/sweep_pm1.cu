@@ -337,7 +337,7 @@ __device__ void run_item_pm1(const SweepLaunch &L, const SweepJob &job, int quad
     if (t < T)
         sweep_once<B, NSLOT, MAXD, SCALED, 0>(sm, drow, s, phase_hi | (uint32_t)t, K, barmask, one, k16, nullptr, bias);
     // the inverted copy is dead now: its first 4 nq words hold the energy sums
-    finish_item<true>(P, job, quad0, nq, sm.sw, reinterpret_cast<int *>(sm.sw + KW));
+    finish_item<!SCALED>(P, job, quad0, nq, sm.sw, reinterpret_cast<int *>(sm.sw + KW));  // general J for SCALED
 }
 
 template <int B, int NSLOT, int MAXD, bool SCALED>
