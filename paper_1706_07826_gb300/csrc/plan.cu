@@ -597,24 +597,18 @@ int spvar_plan_create(const spvar_problem *const *problems, int32_t nproblems,
             if (Q != 1 || sh.kind != 5) { plan_free(pl); return SPVAR_ELIMIT; }
         } else if (p.sweep_kernel == SPVAR_SWEEP_PM1 || (p.sweep_kernel == SPVAR_SWEEP_AUTO && elig)) {
             const int md = pl->max_deg <= 6 ? 6 : 8;
-            if (elig) {
-                const int ns = pm1r_kernel_eligible(pl->pm1, pl->dmax, pl->max_deg) ? plan_nslot(pl, Q, blk) : 0;
-                if (ns > 0 && pm1_shape_ok(blk, ns, md, false)) sh = SweepShape{1, blk, Q, 0, ns, md};
-                else if (pm1s_shape_ok(blk, md, pl->max_n0, Q)) sh = SweepShape{2, blk, Q, 0, 0, md};
-                else { plan_free(pl); return SPVAR_ELIMIT; }
-            } else if (ujr_kernel_eligible(pl->ujs, pl->dmax, pl->max_deg)) {
-                // one coupler magnitude per spin: the register kernel's 16-bit-lane variant
-                int ns = plan_nslot(pl, Q, blk);
-                if (ns == 3) ns = 4;
-                const SweepShape c{1, blk, Q, 1, ns, md};
-                if (ns > 0 && pm1_shape_ok(blk, ns, md, true) &&
-                    sweep_shape_smem(c, pl->max_n0, pl->thr_stride, pl->max_deg) <= (size_t)optin)
-                    sh = c;
-                else { plan_free(pl); return SPVAR_ELIMIT; }
-            } else {
-                plan_free(pl);
-                return SPVAR_ELIMIT;
-            }
+            // byte-lane register kernel, else (one coupler magnitude per spin) its
+            // 16-bit-lane variant, else the streaming +-1 kernel
+            const int ns = pm1r_kernel_eligible(pl->pm1, pl->dmax, pl->max_deg) ? plan_nslot(pl, Q, blk) : 0;
+            int nsu = ujr_kernel_eligible(pl->ujs, pl->dmax, pl->max_deg) ? plan_nslot(pl, Q, blk) : 0;
+            if (nsu == 3) nsu = 4;
+            const SweepShape cu{1, blk, Q, 1, nsu, md};
+            if (ns > 0 && pm1_shape_ok(blk, ns, md, false)) sh = SweepShape{1, blk, Q, 0, ns, md};
+            else if (nsu > 0 && pm1_shape_ok(blk, nsu, md, true) &&
+                     sweep_shape_smem(cu, pl->max_n0, pl->thr_stride, pl->max_deg) <= (size_t)optin)
+                sh = cu;
+            else if (elig && pm1s_shape_ok(blk, md, pl->max_n0, Q)) sh = SweepShape{2, blk, Q, 0, 0, md};
+            else { plan_free(pl); return SPVAR_ELIMIT; }
         } else if (p.sweep_kernel == SPVAR_SWEEP_PM1W) {
             const int md = pl->max_deg <= 6 ? 6 : 8;
             if (!elig || !pm1w_shape_ok(Q, md, pl->max_n0)) { plan_free(pl); return SPVAR_ELIMIT; }
