@@ -319,16 +319,20 @@ void autotune(spvar_plan *pl, cudaStream_t st, int optin)
         SolveConsts C = pl->C;
         C.nslots = nslots;
         C.Q = sh.Q;
-        launch_slots_init(pl->d_slots, C, pl->max_n0, st);
+        pl->C.Q = sh.Q;
         const int items = nslots * ceil_div(ceil_div(pl->C.Smax, 4), sh.Q);
         const int grid = (pl->prm.form == SPVAR_FORM_PLAIN) ? items : grid_for(pl, items);
-        SweepLaunch L = make_launch(pl, Tt);
+        // a short run of the plan's phases (fixing, and solving on the problems it
+        // reduced), so that shapes that suit the full problem but not the reduced
+        // ones are not picked
+        const int phases = std::min(pl->iters_max, 4);
         float ms = 1e30f;
         bool ok = true;
         for (int rep = 0; rep < 2 && ok; ++rep) {
-            launch_plan(pl->d_slots, C, pl->d_jobs, pl->d_items, pl->d_ctr, pl->d_ctr + 1, st);
+            ok = launch_slots_init(pl->d_slots, C, pl->max_n0, st) == cudaSuccess;
             cudaEventRecord(a, st);
-            ok = launch_sweep_shape(L, sh, pl->pm1, grid, pl->sweep_smem, st) == cudaSuccess;
+            for (int it = 0; it < phases && ok; ++it)
+                ok = launch_phase(pl, pl->d_slots, nslots, Tt, grid, st, false) == cudaSuccess;
             cudaEventRecord(b, st);
             if (!ok || cudaEventSynchronize(b) != cudaSuccess) { ok = false; break; }
             float m = 0.f;
