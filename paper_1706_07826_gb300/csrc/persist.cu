@@ -308,8 +308,31 @@ __global__ void __launch_bounds__(256) k_slots_init(Slot *slots, SolveConsts C)
     }
 }
 
-// Builds this phase's sweep jobs and work items (one item = Q quads of one
-// start) for every start that is not done, and resets the queue cursor.
+// Quads per work item of a start whose current problem is P: C.Q, or for the
+// register kernel the most that its slots hold (every colour class fills
+// ceil(size * q / block) whole slots; at most block * nslot / 4 quads so that
+// the per-item energy sums fit).
+__device__ __forceinline__ int item_quads(const DevProb *P, const SolveConsts &C)
+{
+    if (C.fit_block <= 0) return C.Q;
+    const int ncol = P->ncol;
+    auto need = [&](int q) {
+        int s = 0;
+        for (int c = 0; c < ncol; ++c) s += ceil_div((P->cptr[c + 1] - P->cptr[c]) * q, C.fit_block);
+        return s;
+    };
+    int lo = 1, hi = max(1, (C.fit_block * C.fit_nslot + 1) / 4);
+    if (need(lo) > C.fit_nslot) return 1;  // cannot happen for a shape the host chose
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) / 2;
+        if (need(mid) <= C.fit_nslot) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Builds this phase's sweep jobs and work items (one item = item_quads quads
+// of one start) for every start that is not done, and resets the queue cursor.
 __global__ void __launch_bounds__(kBigBlock)
     k_plan(Slot *slots, SolveConsts C, SweepJob *jobs, WorkItem *items, int32_t *nitems,
            int32_t *queue)
@@ -336,7 +359,7 @@ __global__ void __launch_bounds__(kBigBlock)
                 j.t0 = 0;
                 j.pad = 0;
                 jobs[si] = j;
-                groups = ceil_div(ceil_div(S, 4), C.Q);
+                groups = ceil_div(ceil_div(S, 4), item_quads(s.cur, C));
                 s.rec_count[s.phase] = S;
                 s.rec_nfree[s.phase] = s.cur->n;
                 s.nfixed = 0;
@@ -347,11 +370,12 @@ __global__ void __launch_bounds__(kBigBlock)
         if (groups > 0) {
             const int S = jobs[si].S;
             const int nquads = ceil_div(S, 4);
+            const int qn = item_quads(slots[si].cur, C);
             for (int g = 0; g < groups; ++g) {
                 WorkItem w;
                 w.job = si;
-                w.quad0 = g * C.Q;
-                w.nq = min(C.Q, nquads - g * C.Q);
+                w.quad0 = g * qn;
+                w.nq = min(qn, nquads - g * qn);
                 w.pad = 0;
                 items[carry + ex + g] = w;
             }
