@@ -308,20 +308,22 @@ __global__ void __launch_bounds__(256) k_slots_init(Slot *slots, SolveConsts C)
     }
 }
 
-// Quads per work item of a start whose current problem is P: C.Q, or for the
-// register kernel the most that its slots hold (every colour class fills
-// ceil(size * q / block) whole slots; at most block * nslot / 4 quads so that
-// the per-item energy sums fit).
-__device__ __forceinline__ int item_quads(const DevProb *P, const SolveConsts &C)
+// Quads per work item of a start whose current problem is P and who runs
+// nquads quads: C.Q, or for the register kernel the most that its slots hold
+// (every colour class fills ceil(size * q / block) whole slots; at most
+// block * nslot / 4 quads so that the per-item energy sums fit), but no more
+// than leaves about two items per CTA of the launch (starts of similar size).
+__device__ __forceinline__ int item_quads(const DevProb *P, const SolveConsts &C, int nquads)
 {
     if (C.fit_block <= 0) return C.Q;
+    const int cap = max(1, (int)(((long long)nquads * C.nslots) / (2ll * max(C.grid, 1))));
     const int ncol = P->ncol;
     auto need = [&](int q) {
         int s = 0;
         for (int c = 0; c < ncol; ++c) s += ceil_div((P->cptr[c + 1] - P->cptr[c]) * q, C.fit_block);
         return s;
     };
-    int lo = 1, hi = max(1, (C.fit_block * C.fit_nslot + 1) / 4);
+    int lo = 1, hi = max(1, min(cap, (C.fit_block * C.fit_nslot + 1) / 4));
     if (need(lo) > C.fit_nslot) return 1;  // cannot happen for a shape the host chose
     while (lo < hi) {
         const int mid = (lo + hi + 1) / 2;
@@ -359,7 +361,7 @@ __global__ void __launch_bounds__(kBigBlock)
                 j.t0 = 0;
                 j.pad = 0;
                 jobs[si] = j;
-                groups = ceil_div(ceil_div(S, 4), item_quads(s.cur, C));
+                groups = ceil_div(ceil_div(S, 4), item_quads(s.cur, C, ceil_div(S, 4)));
                 s.rec_count[s.phase] = S;
                 s.rec_nfree[s.phase] = s.cur->n;
                 s.nfixed = 0;
@@ -370,7 +372,7 @@ __global__ void __launch_bounds__(kBigBlock)
         if (groups > 0) {
             const int S = jobs[si].S;
             const int nquads = ceil_div(S, 4);
-            const int qn = item_quads(slots[si].cur, C);
+            const int qn = item_quads(slots[si].cur, C, nquads);
             for (int g = 0; g < groups; ++g) {
                 WorkItem w;
                 w.job = si;

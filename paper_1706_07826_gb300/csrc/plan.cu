@@ -38,6 +38,7 @@ cudaError_t engine_phase(const PhaseEngine &E, Slot *slots, int nslots, int T, i
     C.Q = E.shape.Q;
     C.fit_block = E.shape.kind == 1 ? E.shape.block : 0;
     C.fit_nslot = E.shape.kind == 1 ? E.shape.nslot : 0;
+    C.grid = grid;
     cudaError_t e = launch_plan(slots, C, E.jobs, E.items, E.ctr + 0, E.ctr + 1, st);
     if (e != cudaSuccess) return e;
     SweepLaunch L;

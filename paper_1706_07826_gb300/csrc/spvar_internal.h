@@ -150,7 +150,7 @@ struct SolveConsts {
     int32_t S_corr, k_corr, corr_num, corr_den;  // correlation phase (S_corr = 0: off)
     // register kernel: work items take as many quads as the slots hold (block
     // threads x nslot items per thread, colour classes in whole slots); 0: Q quads
-    int32_t fit_block, fit_nslot, pad2, pad3;
+    int32_t fit_block, fit_nslot, grid, pad3;  // grid: CTAs of the sweep launch
 };
 // Samples and elite size of a slot's current phase.
 __host__ __device__ inline int phase_samples(const SolveConsts &C, int mode)
