@@ -232,12 +232,13 @@ std::vector<SweepShape> candidate_shapes(const spvar_plan *pl, int optin)
     }
     if (pm1_kernel_eligible(pl->pm1, pl->dmax, pl->max_deg)) {
         const int md = pl->max_deg <= 6 ? 6 : 8;
-        for (int w : {2, 4, 8, 16}) {
-            SweepShape sh{4, 32 * w, w, 0, 0, md};
-            if (pm1w_shape_ok(w, md, pl->max_n0) &&
-                sweep_shape_smem(sh, pl->max_n0, pl->thr_stride, pl->max_deg) <= (size_t)optin)
-                out.push_back(sh);
-        }
+        for (int w : {2, 4, 8, 16})
+            for (int K : {2, 4}) {
+                SweepShape sh{4, 32 * w, w, 0, K, md};
+                if (pm1w_shape_ok(w, md, pl->max_n0, K) &&
+                    sweep_shape_smem(sh, pl->max_n0, pl->thr_stride, pl->max_deg) <= (size_t)optin)
+                    out.push_back(sh);
+            }
     }
     const int blocks[3] = {128, 256, 512};
     const int qs[4] = {1, 2, 4, 8};
@@ -618,8 +619,8 @@ int spvar_plan_create(const spvar_problem *const *problems, int32_t nproblems,
             else { plan_free(pl); return SPVAR_ELIMIT; }
         } else if (p.sweep_kernel == SPVAR_SWEEP_PM1W) {
             const int md = pl->max_deg <= 6 ? 6 : 8;
-            if (!elig || !pm1w_shape_ok(Q, md, pl->max_n0)) { plan_free(pl); return SPVAR_ELIMIT; }
-            sh = SweepShape{4, 32 * Q, Q, 0, 0, md};
+            if (!elig || !pm1w_shape_ok(Q, md, pl->max_n0, 4)) { plan_free(pl); return SPVAR_ELIMIT; }
+            sh = SweepShape{4, 32 * Q, Q, 0, 4, md};
         } else if (p.sweep_kernel == SPVAR_SWEEP_PM1S) {
             const int md = pl->max_deg <= 6 ? 6 : 8;
             if (!elig || !pm1s_shape_ok(blk, md, pl->max_n0, Q)) { plan_free(pl); return SPVAR_ELIMIT; }

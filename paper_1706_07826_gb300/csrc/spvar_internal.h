@@ -274,17 +274,19 @@ cudaError_t launch_sweep_pm1s(const SweepLaunch &L, int block, int maxd, int gri
 int pm1s_max_active_blocks(int block, int maxd, size_t smem);
 
 // Warp-per-quad +-1 sweep (sweep_pm1w.cu): WARPS quads per work item.
-bool pm1w_shape_ok(int warps, int maxd, int max_n);
+bool pm1w_shape_ok(int warps, int maxd, int max_n, int K);
 size_t pm1w_smem_bytes(int max_n, int warps, int maxd);
-cudaError_t launch_sweep_pm1w(const SweepLaunch &L, int warps, int maxd, int grid, size_t smem, cudaStream_t st);
-int pm1w_max_active_blocks(int warps, int maxd, size_t smem);
+cudaError_t launch_sweep_pm1w(const SweepLaunch &L, int warps, int maxd, int K, int grid, size_t smem,
+                              cudaStream_t st);
+int pm1w_max_active_blocks(int warps, int maxd, int K, size_t smem);
 
 // Launch shape of a sweep: kind 0 = general kernel (stage: layout staged in
 // shared memory), kind 1 = register-resident kernel (nslot items per thread,
 // maxd neighbour registers per item; stage = 1: the 16-bit-lane variant for
 // one coupler magnitude per spin), kind 2 = streaming +-1 kernel
 // (maxd neighbour offsets per spin staged in shared memory, Q = 1), kind 4 =
-// warp-per-quad +-1 kernel (Q = warps = block / 32), kind 5 = simulated
+// warp-per-quad +-1 kernel (Q = warps = block / 32; nslot = spins in flight per lane,
+// 2 or 4), kind 5 = simulated
 // quantum annealing (Q = 1).  A persistent grid holds
 // every CTA the SMs can keep resident, or (balance) the fewest CTAs that still
 // need the same number of waves of items, so that no last wave runs nearly empty.
@@ -325,7 +327,7 @@ inline cudaError_t launch_sweep_shape(const SweepLaunch &L, const SweepShape &s,
     if (s.kind == 5) return launch_sweep_sqa(L, s.stage != 0, s.block, grid, smem, st);
     if (s.kind == 1) return launch_sweep_pm1(L, s.block, s.nslot, s.maxd, s.stage != 0, grid, smem, st);
     if (s.kind == 2) return launch_sweep_pm1s(L, s.block, s.maxd, grid, smem, st);
-    if (s.kind == 4) return launch_sweep_pm1w(L, s.Q, s.maxd, grid, smem, st);
+    if (s.kind == 4) return launch_sweep_pm1w(L, s.Q, s.maxd, s.nslot ? s.nslot : 2, grid, smem, st);
     return launch_sweep(L, pm1, s.block, grid, smem, st);
 }
 inline int sweep_shape_occupancy(const SweepShape &s, bool pm1, size_t smem)
@@ -333,7 +335,7 @@ inline int sweep_shape_occupancy(const SweepShape &s, bool pm1, size_t smem)
     if (s.kind == 5) return sqa_max_active_blocks(s.stage != 0, s.block, s.maxd, smem);
     if (s.kind == 1) return pm1_max_active_blocks(s.block, s.nslot, s.maxd, s.stage != 0, smem);
     if (s.kind == 2) return pm1s_max_active_blocks(s.block, s.maxd, smem);
-    if (s.kind == 4) return pm1w_max_active_blocks(s.Q, s.maxd, smem);
+    if (s.kind == 4) return pm1w_max_active_blocks(s.Q, s.maxd, s.nslot ? s.nslot : 2, smem);
     return sweep_max_active_blocks(pm1, s.block, smem, s.stage != 0);
 }
 

@@ -6,7 +6,7 @@
 // quad w alone, in its own region of shared memory (spin words as is, spin
 // words with every replica bit inverted, a zero word).  A colour class is
 // therefore closed by __syncwarp, not by a CTA barrier, and each lane walks
-// many spins of the class, two at a time.  What every quad needs is staged
+// many spins of the class, K (2 or 4) at a time.  What every quad needs is staged
 // once per CTA: each spin's (h, degree), its neighbour word offsets (16-bit,
 // J < 0 neighbours pointing into the inverted copy, missing neighbours at the
 // zero word) and the parts of Philox rounds 1-3 that depend only on the spin
@@ -68,7 +68,7 @@ __device__ __forceinline__ uint32_t update_spin(uint32_t *sw, const uint16_t *of
     return own ^ flip;
 }
 
-template <int WARPS, int MAXD>
+template <int WARPS, int MAXD, int K>
 __device__ void run_item_pm1w(const SweepLaunch &L, const SweepJob &job, int quad0, int nq, uint32_t *smem)
 {
     constexpr int B = 32 * WARPS;
@@ -163,13 +163,18 @@ __device__ void run_item_pm1w(const SweepLaunch &L, const SweepJob &job, int qua
                     for (int e = lane + 1; e <= bias; e += 32) nxt[e - 1] = src[2 * e];
                 }
                 const int lo = s_cptr[c], hi = s_cptr[c + 1];
-                for (int p1 = lo + lane; p1 < hi; p1 += 64) {
-                    const bool has2 = p1 + 32 < hi;
-                    const int p2 = has2 ? p1 + 32 : p1;
-                    uint4 u[2];
-                    const int pp[2] = {p1, p2};
+                for (int p1 = lo + lane; p1 < hi; p1 += 32 * K) {
+                    // K spins of the class per lane, all loads and Philox blocks before any store
+                    int pp[K];
+                    bool valid[K];
 #pragma unroll
-                    for (int k = 0; k < 2; ++k) {
+                    for (int k = 0; k < K; ++k) {
+                        valid[k] = p1 + 32 * k < hi;
+                        pp[k] = valid[k] ? p1 + 32 * k : p1;
+                    }
+                    uint4 u[K];
+#pragma unroll
+                    for (int k = 0; k < K; ++k) {
                         const int p = pp[k];
                         uint32_t h3, l3, HH, LL;
                         mulhilo_w(kM1w, hh ^ l0k_s[p], h3, l3);        // round 2, word 2
@@ -184,14 +189,16 @@ __device__ void run_item_pm1w(const SweepLaunch &L, const SweepJob &job, int qua
                         }
                         u[k] = cc;
                     }
-                    const uint32_t w1 = update_spin<MAXD>(sw, off, n, p1, meta_s[p1], bias, u[0], th_adj);
-                    const uint32_t w2 = update_spin<MAXD>(sw, off, n, p2, meta_s[p2], bias, u[1], th_adj);
-                    sw[p1] = w1;
-                    sw[n + p1] = w1 ^ 0x01010101u;
-                    if (has2) {
-                        sw[p2] = w2;
-                        sw[n + p2] = w2 ^ 0x01010101u;
-                    }
+                    uint32_t w[K];
+#pragma unroll
+                    for (int k = 0; k < K; ++k)
+                        w[k] = update_spin<MAXD>(sw, off, n, pp[k], meta_s[pp[k]], bias, u[k], th_adj);
+#pragma unroll
+                    for (int k = 0; k < K; ++k)
+                        if (valid[k]) {
+                            sw[pp[k]] = w[k];
+                            sw[n + pp[k]] = w[k] ^ 0x01010101u;
+                        }
                 }
                 __syncwarp();
             }
@@ -201,7 +208,7 @@ __device__ void run_item_pm1w(const SweepLaunch &L, const SweepJob &job, int qua
     finish_item<true>(P, job, quad0, nq, regions, e2, region);
 }
 
-template <int WARPS, int MAXD>
+template <int WARPS, int MAXD, int K>
 __global__ void __launch_bounds__(32 * WARPS) k_sweep_pm1w(const SweepLaunch L)
 {
     extern __shared__ __align__(16) uint32_t smem_pm1w[];
@@ -210,30 +217,37 @@ __global__ void __launch_bounds__(32 * WARPS) k_sweep_pm1w(const SweepLaunch L)
         SweepJob job;
         int quad0, nq;
         if (!next_item(L, iter, &s_item, job, quad0, nq)) break;
-        run_item_pm1w<WARPS, MAXD>(L, job, quad0, nq, smem_pm1w);
+        run_item_pm1w<WARPS, MAXD, K>(L, job, quad0, nq, smem_pm1w);
         __syncthreads();
     }
 }
 
-void *select_w(int warps, int maxd)
+// K: spins in flight per lane (2 or 4).
+void *select_w(int warps, int maxd, int K)
 {
-#define SPVAR_W_CASE(W, MD) \
-    if (warps == W && maxd == MD) return reinterpret_cast<void *>(k_sweep_pm1w<W, MD>);
-    SPVAR_W_CASE(2, 6) SPVAR_W_CASE(4, 6) SPVAR_W_CASE(8, 6) SPVAR_W_CASE(16, 6)
-    SPVAR_W_CASE(2, 8) SPVAR_W_CASE(4, 8) SPVAR_W_CASE(8, 8) SPVAR_W_CASE(16, 8)
+#define SPVAR_W_CASE(W, MD, KK) \
+    if (warps == W && maxd == MD && K == KK) return reinterpret_cast<void *>(k_sweep_pm1w<W, MD, KK>);
+    SPVAR_W_CASE(2, 6, 2) SPVAR_W_CASE(4, 6, 2) SPVAR_W_CASE(8, 6, 2) SPVAR_W_CASE(16, 6, 2)
+    SPVAR_W_CASE(2, 8, 2) SPVAR_W_CASE(4, 8, 2) SPVAR_W_CASE(8, 8, 2) SPVAR_W_CASE(16, 8, 2)
+    SPVAR_W_CASE(2, 6, 4) SPVAR_W_CASE(4, 6, 4) SPVAR_W_CASE(8, 6, 4) SPVAR_W_CASE(16, 6, 4)
+    SPVAR_W_CASE(2, 8, 4) SPVAR_W_CASE(4, 8, 4) SPVAR_W_CASE(8, 8, 4) SPVAR_W_CASE(16, 8, 4)
 #undef SPVAR_W_CASE
     return nullptr;
 }
 
 }  // namespace
 
-bool pm1w_shape_ok(int warps, int maxd, int max_n) { return select_w(warps, maxd) && 2LL * max_n + 1 <= 0xFFFF; }
+bool pm1w_shape_ok(int warps, int maxd, int max_n, int K)
+{
+    return select_w(warps, maxd, K) && 2LL * max_n + 1 <= 0xFFFF;
+}
 
 size_t pm1w_smem_bytes(int max_n, int warps, int maxd) { return 4 * pm1w_words(max_n, warps, maxd); }
 
-cudaError_t launch_sweep_pm1w(const SweepLaunch &L, int warps, int maxd, int grid, size_t smem, cudaStream_t st)
+cudaError_t launch_sweep_pm1w(const SweepLaunch &L, int warps, int maxd, int K, int grid, size_t smem,
+                              cudaStream_t st)
 {
-    void *k = select_w(warps, maxd);
+    void *k = select_w(warps, maxd, K);
     if (!k) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -241,9 +255,9 @@ cudaError_t launch_sweep_pm1w(const SweepLaunch &L, int warps, int maxd, int gri
     return cudaLaunchKernel(k, dim3(grid), dim3(32 * warps), args, smem, st);
 }
 
-int pm1w_max_active_blocks(int warps, int maxd, size_t smem)
+int pm1w_max_active_blocks(int warps, int maxd, int K, size_t smem)
 {
-    void *k = select_w(warps, maxd);
+    void *k = select_w(warps, maxd, K);
     if (!k) return 0;
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int nb = 0;

@@ -41,6 +41,36 @@ __host__ __device__ inline size_t sqa_words(int max_n, int P, int maxdeg, int W,
     return w + 4 * (size_t)P + 4;
 }
 
+constexpr uint32_t kM0q = 0xD2511F53u, kM1q = 0xCD9E8D57u, kW0q = 0x9E3779B9u, kW1q = 0xBB67AE85u;
+
+__device__ __forceinline__ void mulhilo_q(uint32_t m, uint32_t a, uint32_t &hi, uint32_t &lo)
+{
+    const uint64_t p = (uint64_t)m * a;
+    hi = (uint32_t)(p >> 32);
+    lo = (uint32_t)p;
+}
+
+// Philox4x32-10 of counter (w0, y, quad, start) with the products that do not
+// depend on w0 hoisted: (H1, L1) = M1 * quad (round 1, per CTA) and
+// (HA, LA) = M0 * (H1 ^ y ^ k0) (round 2, per sweep).  Kr0/Kr1: keys of rounds 3..10.
+__device__ __forceinline__ uint4 philox_sqa(uint32_t w0, uint32_t start, uint32_t k1, uint32_t L1, uint32_t HA,
+                                            uint32_t LA, uint32_t k0w, uint32_t k1w, const uint32_t (&Kr0)[8],
+                                            const uint32_t (&Kr1)[8])
+{
+    uint32_t h0, l0, hb, lb;
+    mulhilo_q(kM0q, w0, h0, l0);                       // round 1, word 0
+    mulhilo_q(kM1q, h0 ^ start ^ k1, hb, lb);          // round 2, word 2
+    uint4 c = make_uint4(hb ^ L1 ^ k0w, lb, HA ^ l0 ^ k1w, LA);
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+        uint32_t a, b, e, f;
+        mulhilo_q(kM0q, c.x, a, b);
+        mulhilo_q(kM1q, c.z, e, f);
+        c = make_uint4(e ^ c.y ^ Kr0[r], f, a ^ c.w ^ Kr1[r], b);
+    }
+    return c;
+}
+
 template <bool PM1, int B, int MAXD>
 __device__ void run_item_sqa(const SweepLaunch &L, const SweepJob &job, int quad, uint32_t *smem)
 {
@@ -99,12 +129,25 @@ __device__ void run_item_sqa(const SweepLaunch &L, const SweepJob &job, int quad
         for (int x = tid; x < 3 * W; x += B) rows[x] = L.ent[x];
     __syncthreads();
 
+    // Philox parts fixed for this quad
+    uint32_t H1, L1;
+    mulhilo_q(kM1q, (uint32_t)quad, H1, L1);
+    const uint32_t k0w = k0 + kW0q, k1w = k1 + kW1q;
+    uint32_t Kr0[8], Kr1[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+        Kr0[r] = k0 + (uint32_t)(r + 2) * kW0q;
+        Kr1[r] = k1 + (uint32_t)(r + 2) * kW1q;
+    }
+
     const int nt = (P > 1) ? P / 2 : 1;  // slices per parity
     for (int t = 0; t < T; ++t) {
         const unsigned long long *ent = rows + (t & 1) * 3 * W;
         if (t + 1 < T)
             for (int x = tid; x < 3 * W; x += B) rows[((t + 1) & 1) * 3 * W + x] = L.ent[(size_t)(t + 1) * 3 * W + x];
         const uint32_t y = phase_hi | (uint32_t)t;
+        uint32_t HA, LA;  // round 2, word 0: fixed for this quad and sweep
+        mulhilo_q(kM0q, H1 ^ y ^ k0, HA, LA);
         for (int c = 0; c < ncol; ++c) {
             const int lo = s_cptr[c], nc = s_cptr[c + 1] - lo;
             if (nc == 0) continue;
@@ -161,7 +204,7 @@ __device__ void run_item_sqa(const SweepLaunch &L, const SweepJob &job, int quad
                         }
                     }
                     const uint32_t i = idx_s[p] | ((uint32_t)tau << 16);
-                    const uint4 u = philox4x32_10(make_uint4(i, y, (uint32_t)quad, job.start), k0, k1);
+                    const uint4 u = philox_sqa(i, job.start, k1, L1, HA, LA, k0w, k1w, Kr0, Kr1);
                     const uint32_t ur[4] = {u.x, u.y, u.z, u.w};
                     uint32_t flip = 0;
 #pragma unroll
