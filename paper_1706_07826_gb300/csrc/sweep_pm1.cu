@@ -17,10 +17,10 @@
 //    byte-wise sum of neighbour words;
 //  - the flip-cost index of the four replicas is formed byte-wise (SWAR),
 //    pre-scaled to the byte offset of a 64-bit threshold entry;
-//  - acceptance is one wide multiply-add per replica: the row holds
-//    2^32 - thr (0 where dE <= 0), so u + entry carries into bit 32 exactly
-//    when the move is rejected (u >= thr), and the four carries are the
-//    replicas' reject bits.
+//  - acceptance is one 64-bit add per replica: the row holds 2^32 - thr (0
+//    where dE <= 0), so u + entry carries into bit 32 exactly when the move
+//    is rejected (u >= thr), and the four carries are the replicas' reject
+//    bits (no compare, select or "always accept" mask).
 // Eligible when every |J| = 1, degree <= MAXD and dmax <= 30 (so that the
 // scaled index 8 (dE/2 + bias) fits a byte).
 //
@@ -62,14 +62,6 @@ __device__ __forceinline__ void mulhilo(uint32_t m, uint32_t a, uint32_t &hi, ui
     const uint64_t p = (uint64_t)m * a;
     hi = (uint32_t)(p >> 32);
     lo = (uint32_t)p;
-}
-
-// High word of a * b + c (64-bit c); with b = 1 it is the carry of u + entry.
-__device__ __forceinline__ uint32_t mad_wide_hi(uint32_t a, uint32_t b, uint64_t c)
-{
-    uint64_t d;
-    asm("mad.wide.u32 %0, %1, %2, %3;" : "=l"(d) : "r"(a), "r"(b), "l"(c));
-    return (uint32_t)(d >> 32);
 }
 
 // a * b + c on 32 bits.
@@ -209,7 +201,9 @@ __device__ __forceinline__ void sweep_once(Pm1Smem<B, NSLOT> &sm, unsigned long 
 #pragma unroll
             for (int r = 0; r < 4; ++r) {
                 const unsigned long long ent = *reinterpret_cast<const unsigned long long *>(rowb + off[r]);
-                const uint32_t carry = mad_wide_hi(ur[r], one, ent);
+                // carry of u + entry: a 64-bit add, on the integer pipe (the multiply
+                // pipe is busy with Philox)
+                const uint32_t carry = (uint32_t)(((unsigned long long)ur[r] + ent) >> 32);
                 rej = r == 0 ? carry : mad_lo(carry, one << (8 * r), rej);
             }
             // flip where not rejected
