@@ -303,6 +303,60 @@ def measure_sqa(spvar, torch, flush):
                       "16 Trotter slices, 1000 sweeps, beta 3.0, transverse field 3.0 -> 0.01 linear, elite 0.1"}
 
 
+def _hbm_peak_gbs():
+    """Measured copy bandwidth of this GPU pool (GB/s), or the recipe's fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def measure_persistence_scaled(spvar, torch):
+    """The persistence pass (elite, counts and fixing, fold and compact) at a
+    scale where HBM matters: 64 3D +-J problems of N = 8000 in one plan, 2000
+    samples per phase, one launch per kernel for all of them.  Algorithmic
+    bytes per problem: energies 8S, elite rows k ceil(N/32) 4, counts and fixes
+    5N, the CSR and layout read (4(N+1) + 8 nnz + 13N) and the reduced one
+    written (28N' + 12 nnz'), and the solving phase's energies 8S."""
+    from paper_1706_07826_gb300 import instances as I
+    insts = [I.cubic3d(20, 1700 + i) for i in range(64)]
+    probs = [spvar.Problem.from_instance(x) for x in insts]
+    S, T = 2000, 20
+    prm = spvar.make_params(num_starts=1, fixing_sample_size=S, solving_sample_size=S, num_sweeps=T,
+                            elite_threshold=0.1)
+    plan = spvar.Plan(probs, prm)
+    seeds = [1800 + i for i in range(64)]
+    plan.run(seeds, device=True)
+    torch.cuda.synchronize()
+    plan.set_profiling(True)
+    out = plan.run([x + 1 for x in seeds], device=False)
+    post_ms = plan.post_time()
+    sweep_ms, _ = plan.sweep_time()
+    plan.close()
+    k = int(np.ceil(0.1 * S))
+    total = 0
+    off = 0
+    for i, x in enumerate(insts):
+        n, nnz = x.n, 2 * x.m
+        fixed = np.asarray(out.fixed[off:off + n])
+        off += n
+        free = fixed == 0
+        n2 = int(free.sum())
+        nnz2 = 2 * int(np.sum(free[x.ei] & free[x.ej]))
+        total += 8 * S + k * ((n + 31) // 32) * 4 + 5 * n
+        total += 4 * (n + 1) + 8 * nnz + 13 * n + 28 * n2 + 12 * nnz2
+        total += 8 * S
+    peak, kind = _hbm_peak_gbs()
+    gbs = total / (post_ms / 1000.0) / 1e9
+    return {"bound": "hbm", "achieved": gbs, "peak": peak, "peak_kind": kind, "unit": "GB/s", "frac": gbs / peak,
+            "bytes": total, "post_ms": post_ms, "sweep_ms": sweep_ms,
+            "note": "one launch per kernel for all 64 problems and both phases; a fold/compact is one CTA per "
+                    "problem, so 64 SMs stream the CSRs",
+            "config": "64 3D +-J L=20 problems (N=8000, 24000 couplers each, seeds 1700..1763), 1 start each, "
+                      "2000 + 2000 samples, 20 sweeps (short anneal: the pass does not depend on it), elite 0.1"}
+
+
 def measure_small_configs(spvar, torch):
     """c1 (3D L=4, ISPVAR until every spin is fixed, 1 start, 256 samples) and
     c3 (weak-strong Chimera C12 x100, 32 starts, 250 + 250 samples), batched and plain."""
@@ -539,6 +593,7 @@ def gpu_arm(args, rank, world):
         extra["uneven_batch"] = measure_uneven(spvar, torch, flush)
         extra["serving"] = measure_serving(spvar)
         extra["sqa_chimera_c8"] = measure_sqa(spvar, torch, flush)
+        extra["persistence_pass_scaled"] = measure_persistence_scaled(spvar, torch)
 
     # roofline of the sweep kernel (integer ALU issue bound)
     mean_deg = 2 * inst.m / inst.n

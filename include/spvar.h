@@ -424,6 +424,11 @@ int spvar_plan_set_profiling(spvar_plan *plan, int32_t on);
  * profiled plan_run. */
 int spvar_plan_sweep_time(const spvar_plan *plan, double *total_ms, int32_t *launches);
 
+/* Sum of the persistence-pass durations (ms) of the last profiled plan_run:
+ * from the end of each sweep launch to the end of the phase's fold/compact
+ * (boosting, elite, counts and fixing, fold and compact kernels). */
+int spvar_plan_post_time(const spvar_plan *plan, double *total_ms);
+
 /* The sweep launch shape the plan chose (autotuned or requested): threads
  * per CTA, replicas per CTA, kernel (0: general kernel reading its layout
  * from global memory, 1: general kernel with the layout staged in shared

@@ -64,7 +64,10 @@ cudaError_t engine_phase(const PhaseEngine &E, Slot *slots, int nslots, int T, i
     if ((e = launch_boost(slots, C, st)) != cudaSuccess) return e;
     if ((e = launch_elite_slots(slots, C, st)) != cudaSuccess) return e;
     if ((e = launch_count_slots(slots, C, E.max_n0, st)) != cudaSuccess) return e;
-    return launch_reduce_slots(slots, C, count_active ? E.ctr + 2 : nullptr, st);
+    if ((e = launch_reduce_slots(slots, C, count_active ? E.ctr + 2 : nullptr, st)) != cudaSuccess) return e;
+    // end of the persistence pass (boosting, elite, counts and fixing, fold/compact)
+    if (E.ev_post && (e = record(E.ev_post)) != cudaSuccess) return e;
+    return cudaSuccess;
 }
 
 }  // namespace spvar
@@ -102,6 +105,8 @@ struct spvar_plan {
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t graph = nullptr;
     cudaEvent_t ev_sweep[2] = {nullptr, nullptr};  // recorded around every sweep launch
+    cudaEvent_t ev_post = nullptr;                 // end of each phase's persistence pass
+    double post_ms = 0.0;
     int profiling = 0;
     double sweep_ms = 0.0;
     int32_t sweep_launches = 0;
@@ -171,6 +176,7 @@ PhaseEngine engine_of(const spvar_plan *pl)
     E.ctr = pl->d_ctr;
     E.ev_sweep[0] = pl->ev_sweep[0];
     E.ev_sweep[1] = pl->ev_sweep[1];
+    E.ev_post = pl->ev_post;
     E.C = pl->C;
     return E;
 }
@@ -365,6 +371,7 @@ void plan_free(spvar_plan *pl)
     if (pl->graph) cudaGraphExecDestroy(pl->graph);
     for (int i = 0; i < 2; ++i)
         if (pl->ev_sweep[i]) cudaEventDestroy(pl->ev_sweep[i]);
+    if (pl->ev_post) cudaEventDestroy(pl->ev_post);
     if (pl->cap_stream) cudaStreamDestroy(pl->cap_stream);
     if (pl->ws) cudaFree(pl->ws);
     if (pl->h_slots_pinned) cudaFreeHost(pl->h_slots_pinned);
@@ -485,7 +492,8 @@ int spvar_plan_create(const spvar_problem *const *problems, int32_t nproblems,
         plan_free(pl);
         return SPVAR_ENOMEM;
     }
-    if (cudaEventCreate(&pl->ev_sweep[0]) != cudaSuccess || cudaEventCreate(&pl->ev_sweep[1]) != cudaSuccess) {
+    if (cudaEventCreate(&pl->ev_sweep[0]) != cudaSuccess || cudaEventCreate(&pl->ev_sweep[1]) != cudaSuccess ||
+        cudaEventCreate(&pl->ev_post) != cudaSuccess) {
         cudaGetLastError();
         plan_free(pl);
         return SPVAR_ECUDA;
@@ -675,6 +683,7 @@ int spvar_plan_run(spvar_plan *pl, const uint64_t *seeds, const spvar_result *re
     SPVAR_CUDA_TRY(launch_slots_init(pl->d_slots, pl->C, pl->max_n0, st));
     const bool iterate = pl->prm.iterate != 0;
     pl->sweep_ms = 0.0;
+    pl->post_ms = 0.0;
     pl->sweep_launches = 0;
     // profiling: wait for each phase and add up the sweep kernel's event time
     auto profile_phase = [&]() -> int {
@@ -684,6 +693,9 @@ int spvar_plan_run(spvar_plan *pl, const uint64_t *seeds, const spvar_result *re
         SPVAR_CUDA_TRY(cudaEventElapsedTime(&ms, pl->ev_sweep[0], pl->ev_sweep[1]));
         pl->sweep_ms += ms;
         pl->sweep_launches += 1;
+        SPVAR_CUDA_TRY(cudaEventSynchronize(pl->ev_post));
+        SPVAR_CUDA_TRY(cudaEventElapsedTime(&ms, pl->ev_sweep[1], pl->ev_post));
+        pl->post_ms += ms;
         return SPVAR_OK;
     };
     if (pl->prm.form == SPVAR_FORM_BATCHED) {
@@ -747,6 +759,13 @@ int spvar_plan_sweep_time(const spvar_plan *plan, double *total_ms, int32_t *lau
     if (!plan) return SPVAR_EINVAL;
     if (total_ms) *total_ms = plan->sweep_ms;
     if (launches) *launches = plan->sweep_launches;
+    return SPVAR_OK;
+}
+
+int spvar_plan_post_time(const spvar_plan *plan, double *total_ms)
+{
+    if (!plan) return SPVAR_EINVAL;
+    if (total_ms) *total_ms = plan->post_ms;
     return SPVAR_OK;
 }
 

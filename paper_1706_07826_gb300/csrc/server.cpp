@@ -451,6 +451,7 @@ int spvar_server_create(const spvar_server_config *cfg, spvar_server **out)
     E.items = (WorkItem *)(w + o_items);
     E.ctr = (int32_t *)(w + o_ctr);
     E.ev_sweep[0] = E.ev_sweep[1] = nullptr;
+    E.ev_post = nullptr;
     const int occ = std::max(1, sweep_shape_occupancy(E.shape, E.pm1, E.sweep_smem));
     S->grid = occ * S->sms;
     // capture one phase over the whole slot table

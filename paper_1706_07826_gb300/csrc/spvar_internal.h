@@ -352,6 +352,7 @@ struct PhaseEngine {
     WorkItem *items;
     int32_t *ctr;  // [0] items, [1] queue cursor, [2] active slots
     cudaEvent_t ev_sweep[2];
+    cudaEvent_t ev_post;  // recorded after each phase's persistence pass (null: none)
     SolveConsts C;
 };
 // plan -> sweep -> elite -> count/fix -> fold/compact for `nslots` slots.

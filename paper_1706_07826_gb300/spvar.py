@@ -450,6 +450,12 @@ class Plan:
         _check(lib().spvar_plan_sweep_time(self.handle, ctypes.byref(ms), ctypes.byref(n)), "spvar_plan_sweep_time")
         return ms.value, n.value
 
+    def post_time(self):
+        """Persistence-pass time (ms) of the last profiled run."""
+        ms = ctypes.c_double(0)
+        _check(lib().spvar_plan_post_time(self.handle, ctypes.byref(ms)), "spvar_plan_post_time")
+        return ms.value
+
     def shape(self):
         b, r, s, g = i32(0), i32(0), i32(0), i32(0)
         _check(lib().spvar_plan_shape(self.handle, ctypes.byref(b), ctypes.byref(r), ctypes.byref(s), ctypes.byref(g)),
