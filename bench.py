@@ -603,6 +603,10 @@ def gpu_arm(args, rank, world):
     achieved = att_per_launch * ops_per_attempt / (ms_per_launch / 1000.0) / 1e12
     cs = clk.summary()
     peak = SMS * LANES_PER_SM * 2070e6 / 1e12
+    att_per_start = value / world * (tb / 1000.0 / K) / 10  # attempts of one start (both phases)
+    if cpu:
+        cpu["per_core"] = cpu["value"] / cpu["cores"]
+        cpu["tts99_s"] = tts99(p, att_per_start / cpu["value"])  # all cores, starts run one after another
     shape = plan_b.shape()
     if rank != 0:
         return
@@ -617,7 +621,11 @@ def gpu_arm(args, rank, world):
                   "speedup_batched_over_plain": value / world / plain_value},
         "tts99": {"p_success_per_start": p, "e_best_known": int(e_known), "e_known_kind": "best found by the runs "
                   "of this benchmark (not proved optimal)", "batched_s": tts_b, "plain_s": tts_p,
-                  "starts_measured": len(hit)},
+                  "starts_measured": len(hit),
+                  # the same starts at the integer issue peak (the pass and the copies are ~0.4 %)
+                  "roofline_s": tts99(p, att_per_start * ops_per_attempt / (peak * 1e12)),
+                  "roofline_frac": (tts99(p, att_per_start * ops_per_attempt / (peak * 1e12)) / tts_b)
+                  if tts_b else None},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                 "api": "spvar_problem_create + spvar_solve (host buffers, plan built per call)",
                 "ms_per_step": 1000 * statistics.mean(e2e_times)},
