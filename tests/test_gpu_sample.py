@@ -107,8 +107,10 @@ def test_sample_rejects_short_table(cuda_lib):
 
 
 @pytest.mark.parametrize("make,S", [(lambda: I.chimera(4, 1200), 37), (lambda: I.cubic3d(20, 1500), 8),
-                                    (lambda: I.weak_strong(3, 1300), 13), (lambda: I.cubic3d(5, 1101), 21)],
-                         ids=["chimera_register", "cubic_L20_streaming", "weak_strong_general", "cubic_odd"])
+                                    (lambda: I.weak_strong(3, 1300), 13), (lambda: I.cubic3d(5, 1101), 21),
+                                    (lambda: I.random_graph(40, 90, 5, jmax=7, hmax=9), 11)],
+                         ids=["chimera_register", "cubic_L20_streaming", "weak_strong_register_16bit", "cubic_odd",
+                              "random_general"])
 def test_resumed_sample_is_identical(cuda_lib, make, S):
     """Checkpoint/resume: sweeps [0, 40) + [40, 97) + [97, 150) from saved states
     equal one uninterrupted 150-sweep sample (and the oracle's)."""
