@@ -207,20 +207,30 @@ def run_form(spvar, torch, plan, K, W, seeds0, flush, profile=False, nvtx="timed
 def profiled_traffic(kernel_kind):
     """DRAM bytes per launch of the sweep kernel from the committed ncu
     summary, or None when the kernel's source changed since the capture."""
-    import hashlib
     path = os.path.join(ROOT, "profiles", "k_sweep_pm1_chimera_c8.md")
     if kernel_kind != "pm1-register" or not os.path.exists(path):
         return None
     text = open(path).read()
     vals = dict(l.split(": ", 1) for l in text.splitlines()
                 if l.startswith(("dram_bytes_per_launch:", "kernel_source_sha256_16:")))
-    h = hashlib.sha256()
-    for f in ("sweep_pm1.cu", "sweep_common.cuh", "philox.cuh", "spvar_internal.h"):
-        h.update(open(os.path.join(ROOT, "paper_1706_07826_gb300", "csrc", f), "rb").read())
-    if vals.get("kernel_source_sha256_16") != h.hexdigest()[:16]:
+    if vals.get("kernel_source_sha256_16") != kernel_source_hash():
         return None
     return int(vals["dram_bytes_per_launch"])
 
+
+def kernel_source_hash():
+    """Hash of what the register sweep kernel is compiled from: its own sources
+    and the device structs it reads (not the host-side parts of the header)."""
+    import hashlib
+    csrc = os.path.join(ROOT, "paper_1706_07826_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in ("sweep_pm1.cu", "sweep_common.cuh", "philox.cuh"):
+        h.update(open(os.path.join(csrc, f), "rb").read())
+    text = open(os.path.join(csrc, "spvar_internal.h")).read()
+    for name in ("DevProb", "SweepJob", "WorkItem", "SweepLaunch"):
+        start = text.index("struct %s {" % name)
+        h.update(text[start:text.index("};", start) + 2].encode())
+    return h.hexdigest()[:16]
 
 def measure_uneven(spvar, torch, flush):
     """c4: 64 3D +-J instances, L uniform in 6..12, 2000 samples per phase,
