@@ -92,7 +92,7 @@ struct spvar_plan {
     int sqa_P = 0, sqa_W = 0;             // SQA slices and table width (0: SA)
     SweepJob *d_jobs = nullptr;
     WorkItem *d_items = nullptr;
-    int32_t *d_ctr = nullptr;       // [0] nitems, [1] queue, [2] nactive
+    int32_t *d_ctr = nullptr;       // [0] nitems, [1] queue, [2] nactive, [3] phases run by the loop graph
     int32_t *h_nactive = nullptr;   // pinned
     int64_t *d_rec_e = nullptr;
     int32_t *d_rec_count = nullptr, *d_rec_nfree = nullptr, *d_nphases = nullptr;
@@ -103,7 +103,8 @@ struct spvar_plan {
     int sweep_grid = 1, sms = 1, dmax = 0;
     size_t sweep_smem = 0;
     cudaStream_t cap_stream = nullptr;
-    cudaGraphExec_t graph = nullptr;
+    cudaGraphExec_t graph = nullptr;       // one batched phase
+    cudaGraphExec_t graph_loop = nullptr;  // every phase of a run: a device-side while loop over `graph`'s body
     cudaEvent_t ev_sweep[2] = {nullptr, nullptr};  // recorded around every sweep launch
     cudaEvent_t ev_post = nullptr;                 // end of each phase's persistence pass
     double post_ms = 0.0;
@@ -181,11 +182,64 @@ PhaseEngine engine_of(const spvar_plan *pl)
     return E;
 }
 
-// One phase of the given slots (all of them in the batched form).
+// One phase of the given slots (all of them in the batched form).  timed =
+// false leaves out the event records (a conditional graph body takes none).
 cudaError_t launch_phase(spvar_plan *pl, Slot *slots, int nslots, int T, int grid, cudaStream_t st,
-                         bool count_active, bool capturing = false)
+                         bool count_active, bool capturing = false, bool timed = true)
 {
-    return engine_phase(engine_of(pl), slots, nslots, T, grid, st, count_active, capturing);
+    PhaseEngine E = engine_of(pl);
+    if (!timed) E.ev_sweep[0] = E.ev_sweep[1] = E.ev_post = nullptr;
+    return engine_phase(E, slots, nslots, T, grid, st, count_active, capturing);
+}
+
+// Loop condition of the whole-run graph: run another phase while phases
+// remain and (ISPVAR) some start is still active.
+__global__ void k_loop_cond(cudaGraphConditionalHandle h, int32_t *ctr, int iters_max, int iterate)
+{
+    const int it = ++ctr[3];
+    const bool more = it < iters_max && (!iterate || ctr[2] > 0);
+    cudaGraphSetConditional(h, more ? 1u : 0u);
+}
+
+// Captures every phase of a batched run as one graph: a conditional while
+// node whose body is one phase followed by k_loop_cond, so the whole Alg. 2
+// loop (ISPVAR included) runs without the host.  Returns false if the graph
+// could not be built (the per-phase graph is used then).
+bool build_loop_graph(spvar_plan *pl, int nslots)
+{
+    cudaGraph_t g = nullptr;
+    if (cudaGraphCreate(&g, 0) != cudaSuccess) return false;
+    bool ok = true;
+    cudaGraphConditionalHandle h;
+    ok = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault) == cudaSuccess;
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    if (ok) ok = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp) == cudaSuccess;
+    if (ok) {
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        ok = cudaStreamBeginCaptureToGraph(pl->cap_stream, body, nullptr, nullptr, 0,
+                                           cudaStreamCaptureModeRelaxed) == cudaSuccess;
+        if (ok) {
+            cudaError_t e = launch_phase(pl, pl->d_slots, nslots, pl->T, pl->sweep_grid, pl->cap_stream, true, true,
+                                         false);
+            if (e == cudaSuccess) {
+                k_loop_cond<<<1, 1, 0, pl->cap_stream>>>(h, pl->d_ctr, pl->iters_max, pl->prm.iterate ? 1 : 0);
+                e = cudaGetLastError();
+            }
+            cudaGraph_t out = nullptr;
+            const cudaError_t e2 = cudaStreamEndCapture(pl->cap_stream, &out);
+            ok = e == cudaSuccess && e2 == cudaSuccess;
+        }
+    }
+    if (ok) ok = cudaGraphInstantiate(&pl->graph_loop, g, 0) == cudaSuccess;
+    if (!ok) pl->graph_loop = nullptr;
+    cudaGraphDestroy(g);
+    cudaGetLastError();
+    return ok;
 }
 
 int upload_slots(spvar_plan *pl, const uint64_t *seeds, cudaStream_t st)
@@ -369,6 +423,7 @@ void plan_free(spvar_plan *pl)
 {
     if (!pl) return;
     if (pl->graph) cudaGraphExecDestroy(pl->graph);
+    if (pl->graph_loop) cudaGraphExecDestroy(pl->graph_loop);
     for (int i = 0; i < 2; ++i)
         if (pl->ev_sweep[i]) cudaEventDestroy(pl->ev_sweep[i]);
     if (pl->ev_post) cudaEventDestroy(pl->ev_post);
@@ -665,6 +720,7 @@ int spvar_plan_create(const spvar_problem *const *problems, int32_t nproblems,
                 if (g) cudaGraphDestroy(g);
             }
             cudaGetLastError();
+            build_loop_graph(pl, nslots);
         }
     }
     *out = pl;
@@ -698,7 +754,11 @@ int spvar_plan_run(spvar_plan *pl, const uint64_t *seeds, const spvar_result *re
         pl->post_ms += ms;
         return SPVAR_OK;
     };
-    if (pl->prm.form == SPVAR_FORM_BATCHED) {
+    if (pl->prm.form == SPVAR_FORM_BATCHED && pl->graph_loop && !pl->profiling) {
+        // the whole run on the device: phases loop inside the graph
+        SPVAR_CUDA_TRY(cudaMemsetAsync(pl->d_ctr + 3, 0, sizeof(int32_t), st));
+        SPVAR_CUDA_TRY(cudaGraphLaunch(pl->graph_loop, st));
+    } else if (pl->prm.form == SPVAR_FORM_BATCHED) {
         for (int it = 0; it < pl->iters_max; ++it) {
             if (pl->graph) {
                 SPVAR_CUDA_TRY(cudaGraphLaunch(pl->graph, st));
