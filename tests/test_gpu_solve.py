@@ -122,7 +122,26 @@ def test_profiling_reports_sweep_time(cuda_lib):
     plan.set_profiling(True)
     plan.run(5, device=False)
     ms, n = plan.sweep_time()
-    assert n == 2 and ms > 0
+    assert n == 2 and ms > 0 and plan.post_time() > 0
+
+
+@pytest.mark.parametrize("iterate", [False, True], ids=["spvar", "ispvar"])
+def test_loop_graph_equals_phase_by_phase(cuda_lib, iterate):
+    """A batched run as one graph launch (device-side phase loop) gives the same
+    results as phase-by-phase launches with the host in between (profiled)."""
+    from paper_1706_07826_gb300 import spvar
+    inst = I.cubic3d(4, 77)
+    prm = spvar.make_params(num_starts=3, fixing_sample_size=48, solving_sample_size=0 if iterate else 24,
+                            num_sweeps=30, elite_threshold=0.2, iterate=iterate, max_fix_phases=32 if iterate else 1)
+    plan = spvar.Plan([gpu_problem(inst)], prm)
+    a = plan.run(9, device=False)
+    plan.set_profiling(True)
+    b = plan.run(9, device=False)
+    for f in ("energies", "counts", "nfree", "nphases", "fixed", "best_energy", "best_state"):
+        assert np.array_equal(np.asarray(getattr(a, f)), np.asarray(getattr(b, f))), f
+    ref = _oracle_solve(inst, 30, 9, num_starts=3, fixing_sample_size=48, solving_sample_size=0 if iterate else 24,
+                        elite_threshold=0.2, iterate=iterate, max_fix_phases=32 if iterate else 1)
+    _check(a, ref, 3, (32 if iterate else 1) + 1, inst.n)
 
 
 def test_uneven_problems_in_one_plan(cuda_lib):
