@@ -151,85 +151,71 @@ __device__ void run_item_sqa(const SweepLaunch &L, const SweepJob &job, int quad
         for (int c = 0; c < ncol; ++c) {
             const int lo = s_cptr[c], nc = s_cptr[c + 1] - lo;
             if (nc == 0) continue;
-            // work units (spin k of the class, chunk ch of ks slices of one parity), k fastest,
-            // about one per thread, walked without divisions; a unit loads its spin's data once
-            const int chunks_want = max(1, B / nc);
-            const int ks = (nt + chunks_want - 1) / chunks_want;
-            const int nch = (nt + ks - 1) / ks;
+            // items (slice pair index tq, position k), k fastest, walked without divisions
             const int dq = B / nc, dk = B - dq * nc;
             const int q0 = tid / nc, kk0 = tid - q0 * nc;
             for (int par = 0; par < (P > 1 ? 2 : 1); ++par) {
-                int ch = q0, k = kk0;
-                while (ch < nch) {
+                int tq = q0, k = kk0;
+                while (tq < nt) {
                     const int p = lo + k;
+                    const int tau = par + 2 * tq;
+                    const uint32_t *s = sw + (size_t)tau * ns;
+                    const uint32_t own = s[p];
                     const uint32_t meta = meta_s[p];
                     const int deg = (int)(meta & 0xFFFFu);
                     const int h = (int)meta >> 16;
-                    const uint32_t ibase = idx_s[p];
-                    uint32_t offs[PM1 ? MAXD : 1];
-                    uint32_t c0 = 0, c1 = 0;
+                    // a per byte: slice neighbours equal to the spin (1 for a single slice)
+                    uint32_t a4 = 0x01010101u;
+                    if (P > 1) {
+                        const uint32_t up = sw[(size_t)(tau + 1 == P ? 0 : tau + 1) * ns + p];
+                        const uint32_t dn = sw[(size_t)(tau == 0 ? P - 1 : tau - 1) * ns + p];
+                        a4 = (~(own ^ up) & 0x01010101u) + (~(own ^ dn) & 0x01010101u);
+                    }
+                    int idx[4];
                     if (PM1) {
+                        // byte r of x: neighbours with b_j ^ [J_ij < 0] = 1; k = 2x + bias - deg + h
+                        // for b_i = 0 and its mirror 2 bias - that for b_i = 1
+                        uint32_t x = 0;
 #pragma unroll
-                        for (int d = 0; d < MAXD; ++d) offs[d] = off[d * n + p];
-                        c0 = (uint32_t)(bias - deg + h) * 0x01010101u;
-                        c1 = (uint32_t)(bias + deg - h) * 0x01010101u;
-                    }
-                    const int tq1 = min(nt, (ch + 1) * ks);
-                    for (int tq = ch * ks; tq < tq1; ++tq) {
-                        const int tau = par + 2 * tq;
-                        const uint32_t *s = sw + (size_t)tau * ns;
-                        const uint32_t own = s[p];
-                        // a per byte: slice neighbours equal to the spin (1 for a single slice)
-                        uint32_t a4 = 0x01010101u;
-                        if (P > 1) {
-                            const uint32_t up = sw[(size_t)(tau + 1 == P ? 0 : tau + 1) * ns + p];
-                            const uint32_t dn = sw[(size_t)(tau == 0 ? P - 1 : tau - 1) * ns + p];
-                            a4 = (~(own ^ up) & 0x01010101u) + (~(own ^ dn) & 0x01010101u);
+                        for (int d = 0; d < MAXD; ++d) x += s[off[d * n + p]];
+                        const uint32_t m = own * 0xFFu;
+                        const uint32_t c0 = (uint32_t)(bias - deg + h) * 0x01010101u;
+                        const uint32_t c1 = (uint32_t)(bias + deg - h) * 0x01010101u;
+                        const uint32_t k4 = ((x + x + c0) & ~m) | ((c1 - x - x) & m);
+                        const uint32_t full = a4 * (uint32_t)W + k4;  // bytes <= 3W - 1 <= 255
+#pragma unroll
+                        for (int r = 0; r < 4; ++r) idx[r] = (int)__byte_perm(full, 0u, 0x4440u | (uint32_t)r);
+                    } else {
+                        int acc[4] = {0, 0, 0, 0}, sumJ = 0;
+                        for (int d = 0; d < deg; ++d) {
+                            const uint32_t e = __ldg(pr->ell + (size_t)d * cap_n + p);
+                            const int Jv = (int)e >> 16;
+                            const uint32_t w = s[e & 0xFFFFu];
+                            sumJ += Jv;
+#pragma unroll
+                            for (int r = 0; r < 4; ++r) acc[r] += Jv * (int)((w >> (8 * r)) & 1u);
                         }
-                        int idx[4];
-                        if (PM1) {
-                            // byte r of x: neighbours with b_j ^ [J_ij < 0] = 1; k = 2x + bias - deg + h
-                            // for b_i = 0 and its mirror 2 bias - that for b_i = 1
-                            uint32_t x = 0;
 #pragma unroll
-                            for (int d = 0; d < MAXD; ++d) x += s[offs[d]];
-                            const uint32_t m = own * 0xFFu;
-                            const uint32_t k4 = ((x + x + c0) & ~m) | ((c1 - x - x) & m);
-                            const uint32_t full = a4 * (uint32_t)W + k4;  // bytes <= 3W - 1 <= 255
-#pragma unroll
-                            for (int r = 0; r < 4; ++r) idx[r] = (int)__byte_perm(full, 0u, 0x4440u | (uint32_t)r);
-                        } else {
-                            int acc[4] = {0, 0, 0, 0}, sumJ = 0;
-                            for (int d = 0; d < deg; ++d) {
-                                const uint32_t e = __ldg(pr->ell + (size_t)d * cap_n + p);
-                                const int Jv = (int)e >> 16;
-                                const uint32_t w = s[e & 0xFFFFu];
-                                sumJ += Jv;
-#pragma unroll
-                                for (int r = 0; r < 4; ++r) acc[r] += Jv * (int)((w >> (8 * r)) & 1u);
-                            }
-#pragma unroll
-                            for (int r = 0; r < 4; ++r) {
-                                // f = h + sum_j J s_j; k = dE/2 + bias = bias - s f
-                                const int f = h - sumJ + 2 * acc[r];
-                                const int sg = 2 * (int)((own >> (8 * r)) & 1u) - 1;
-                                idx[r] = (int)((a4 >> (8 * r)) & 0xFFu) * W + bias - sg * f;
-                            }
+                        for (int r = 0; r < 4; ++r) {
+                            // f = h + sum_j J s_j; k = dE/2 + bias = bias - s f
+                            const int f = h - sumJ + 2 * acc[r];
+                            const int sg = 2 * (int)((own >> (8 * r)) & 1u) - 1;
+                            idx[r] = (int)((a4 >> (8 * r)) & 0xFFu) * W + bias - sg * f;
                         }
-                        const uint32_t i = ibase | ((uint32_t)tau << 16);
-                        const uint4 u = philox_sqa(i, job.start, k1, L1, HA, LA, k0w, k1w, Kr0, Kr1);
-                        const uint32_t ur[4] = {u.x, u.y, u.z, u.w};
-                        uint32_t flip = 0;
-#pragma unroll
-                        for (int r = 0; r < 4; ++r)
-                            if ((((unsigned long long)ur[r] + ent[idx[r]]) >> 32) == 0ull) flip |= 1u << (8 * r);
-                        const uint32_t nw = own ^ flip;
-                        sw[(size_t)tau * ns + p] = nw;
-                        if (PM1) swi[(size_t)tau * ns + p] = nw ^ 0x01010101u;
                     }
-                    ch += dq;
+                    const uint32_t i = idx_s[p] | ((uint32_t)tau << 16);
+                    const uint4 u = philox_sqa(i, job.start, k1, L1, HA, LA, k0w, k1w, Kr0, Kr1);
+                    const uint32_t ur[4] = {u.x, u.y, u.z, u.w};
+                    uint32_t flip = 0;
+#pragma unroll
+                    for (int r = 0; r < 4; ++r)
+                        if ((((unsigned long long)ur[r] + ent[idx[r]]) >> 32) == 0ull) flip |= 1u << (8 * r);
+                    const uint32_t nw = own ^ flip;
+                    sw[(size_t)tau * ns + p] = nw;
+                    if (PM1) swi[(size_t)tau * ns + p] = nw ^ 0x01010101u;
+                    tq += dq;
                     k += dk;
-                    if (k >= nc) { k -= nc; ++ch; }
+                    if (k >= nc) { k -= nc; ++tq; }
                 }
                 __syncthreads();
             }
