@@ -270,7 +270,7 @@ typedef struct spvar_params {
     int32_t form;                /* SPVAR_FORM_BATCHED or SPVAR_FORM_PLAIN */
     int32_t replicas_per_block;  /* 0: autotune the sweep shape; else a multiple of 4 */
     int32_t sweep_kernel;        /* with replicas_per_block > 0: SPVAR_SWEEP_* */
-    int32_t sweep_block;         /* with replicas_per_block > 0: threads per CTA (128/256/512), 0 = 256 */
+    int32_t sweep_block;         /* with replicas_per_block > 0: threads per CTA (128/256/512/1024), 0 = 256 */
     int32_t start_offset;        /* start s of a problem uses counter word start_offset + s (sharding) */
     int32_t component_boost;     /* 1: disconnected-component boosting of the solving sample (Sec. II.C):
                                     each connected component's partial samples are sorted by partial
@@ -303,6 +303,11 @@ typedef struct spvar_params {
                                  streaming +-1 kernel (|J| = 1, dmax <= 254) */
 #define SPVAR_SWEEP_PM1S 3    /* streaming +-1 kernel (shared-memory neighbour offsets, 4 replicas per CTA) */
 #define SPVAR_SWEEP_PM1W 4    /* warp-per-quad +-1 kernel: replicas_per_block / 4 warps, one quad each */
+/* With the SQA sampler (replicas_per_block = 4): AUTO and PM1 take the register
+ * form for +-1 couplers when it applies (two or more slices, at most 4 colour
+ * classes, none larger than sweep_block; blocks 256/512/1024), else the item
+ * walk (blocks 128/256/512); PM1S the item walk; GENERAL the general path; PM1W
+ * is rejected (SPVAR_ELIMIT). */
 
 #define SPVAR_FORM_BATCHED 0 /* every start of every problem in one persistent launch per phase */
 #define SPVAR_FORM_PLAIN 1   /* one start at a time, one launch per kernel and start */
@@ -433,8 +438,10 @@ int spvar_plan_post_time(const spvar_plan *plan, double *total_ms);
  * per CTA, replicas per CTA, kernel (0: general kernel reading its layout
  * from global memory, 1: general kernel with the layout staged in shared
  * memory, 2: register-resident +-1 kernel, 3: streaming +-1 kernel, 4:
- * warp-per-quad +-1 kernel, 5: simulated quantum annealing kernel), persistent
- * grid size. */
+ * warp-per-quad +-1 kernel, 5: simulated quantum annealing kernel walking
+ * (spin, slice) items, 6: simulated quantum annealing kernel in register form:
+ * each thread keeps one spin of every colour class in registers and sweeps a
+ * fixed set of its slices), persistent grid size. */
 int spvar_plan_shape(const spvar_plan *plan, int32_t *block, int32_t *replicas_per_block,
                      int32_t *staged, int32_t *grid);
 

@@ -530,10 +530,28 @@ int spvar_sqa_sample(const spvar_problem *p, int32_t num_sweeps, int32_t P, cons
     if (num_sweeps > SPVAR_MAX_SWEEPS || num_samples > SPVAR_MAX_SAMPLES) return SPVAR_ELIMIT;
     if (num_samples == 0) return SPVAR_OK;
     if ((num_sweeps > 0 && !ent) || !energies || (H.n > 0 && !spins)) return SPVAR_EINVAL;
-    const bool pm1 = H.pm1 != 0 && sqa_shape_ok(true, 256, H.n, H.maxdeg, P, W);
-    if (!sqa_shape_ok(pm1, 256, H.n, H.maxdeg, P, W)) return SPVAR_ELIMIT;
-    const size_t smem = sqa_smem_bytes(H.n, P, H.maxdeg, W, pm1);
-    if (smem > (size_t)device_smem_optin()) return SPVAR_ELIMIT;
+    // +-1 couplers: the register form when every colour class fits a block of 512 (else 1024)
+    // threads, else the item walk; general couplers: the general path
+    int max_class = 0;
+    for (int c = 0; c < H.ncol && c < kMaxColours; ++c) max_class = std::max(max_class, Pr->csize[c]);
+    const int optin = device_smem_optin();
+    int variant = 0, block = 256, ncls = 0;
+    if (H.pm1 != 0) {
+        for (int b : {512, 1024}) {
+            ncls = sqa_reg_ncls(H.ncol, max_class, b, P);
+            if (ncls > 0 && sqa_shape_ok(2, b, H.n, H.maxdeg, P, W, ncls) &&
+                sqa_smem_bytes(H.n, P, H.maxdeg, W, true) <= (size_t)optin) {
+                variant = 2;
+                block = b;
+                break;
+            }
+        }
+        if (variant == 0 && sqa_shape_ok(1, 256, H.n, H.maxdeg, P, W)) variant = 1;
+    }
+    if (variant != 2) ncls = 0;
+    if (!sqa_shape_ok(variant, block, H.n, H.maxdeg, P, W, ncls)) return SPVAR_ELIMIT;
+    const size_t smem = sqa_smem_bytes(H.n, P, H.maxdeg, W, variant != 0);
+    if (smem > (size_t)optin) return SPVAR_ELIMIT;
     SweepLaunch L;
     std::memset(&L, 0, sizeof(L));
     L.single.prob = Pr->dev;
@@ -552,7 +570,7 @@ int spvar_sqa_sample(const spvar_problem *p, int32_t num_sweeps, int32_t P, cons
     L.P = P;
     L.W = W;
     L.slice_out = slice;
-    SPVAR_CUDA_TRY(launch_sweep_sqa(L, pm1, 256, ceil_div(num_samples, 4), smem, as_stream(stream)));
+    SPVAR_CUDA_TRY(launch_sweep_sqa(L, variant, block, ncls, ceil_div(num_samples, 4), smem, as_stream(stream)));
     return SPVAR_OK;
 }
 

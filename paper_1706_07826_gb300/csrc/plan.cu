@@ -79,6 +79,7 @@ struct spvar_plan {
     spvar_params prm{};
     SolveConsts C{};
     int T = 0, thr_stride = 1, max_n0 = 0, max_deg = 1, iters_max = 1;
+    int ncol_max = 0, class_max = 0;  // most colour classes and largest class of any problem
     bool pm1 = true;
     bool ujs = true;      // every problem has one coupler magnitude per spin
     uint64_t sig = 0;     // structure signature of the problems (autotune cache key)
@@ -268,15 +269,17 @@ int plan_nslot(const spvar_plan *pl, int Q, int block)
 
 // Candidate sweep shapes for a plan: the general kernel with and without the
 // staged layout, and (for +-1 problems) the register-resident kernel.
-// SQA sweep shape for a block size, or kind -1 if the slices do not fit.
-SweepShape sqa_shape(const spvar_plan *pl, int block, int optin)
+// SQA sweep shape of a variant (0 general, 1 +-1 walk, 2 +-1 register form)
+// and block size, or kind -1 if it does not apply or the slices do not fit.
+SweepShape sqa_shape(const spvar_plan *pl, int block, int optin, int variant)
 {
-    const bool pm1 = pl->pm1 && sqa_shape_ok(true, block, pl->max_n0, pl->max_deg, pl->sqa_P, pl->sqa_W);
-    SweepShape sh{5, block, 1, pm1 ? 1 : 0, pl->sqa_W, pl->max_deg};
+    SweepShape sh{5, block, 1, variant, pl->sqa_W, pl->max_deg};
     sh.slices = pl->sqa_P;
-    if (!sqa_shape_ok(pm1, block, pl->max_n0, pl->max_deg, pl->sqa_P, pl->sqa_W) ||
-        sweep_shape_smem(sh, pl->max_n0, pl->thr_stride, pl->max_deg) > (size_t)optin)
-        sh.kind = -1;
+    sh.ncls = variant == 2 ? sqa_reg_ncls(pl->ncol_max, pl->class_max, block, pl->sqa_P) : 0;
+    const bool ok = (variant == 0 || pl->pm1) && (variant != 2 || sh.ncls > 0) &&
+                    sqa_shape_ok(variant, block, pl->max_n0, pl->max_deg, pl->sqa_P, pl->sqa_W, sh.ncls) &&
+                    sweep_shape_smem(sh, pl->max_n0, pl->thr_stride, pl->max_deg) <= (size_t)optin;
+    if (!ok) sh.kind = -1;
     return sh;
 }
 
@@ -285,7 +288,11 @@ std::vector<SweepShape> candidate_shapes(const spvar_plan *pl, int optin)
     std::vector<SweepShape> out;
     if (pl->sqa_P > 0) {
         for (int b : {128, 256, 512}) {
-            const SweepShape sh = sqa_shape(pl, b, optin);
+            const SweepShape sh = sqa_shape(pl, b, optin, pl->pm1 ? 1 : 0);
+            if (sh.kind == 5) out.push_back(sh);
+        }
+        for (int b : {256, 512, 1024}) {
+            const SweepShape sh = sqa_shape(pl, b, optin, 2);
             if (sh.kind == 5) out.push_back(sh);
         }
         return out;
@@ -475,6 +482,8 @@ int spvar_plan_create(const spvar_problem *const *problems, int32_t nproblems,
         dmax = std::max(dmax, P->hdr.dmax);
         pl->max_n0 = std::max(pl->max_n0, P->hdr.n);
         pl->max_deg = std::max(pl->max_deg, P->hdr.maxdeg);
+        pl->ncol_max = std::max(pl->ncol_max, P->hdr.ncol);
+        for (int c = 0; c < P->hdr.ncol && c < kMaxColours; ++c) pl->class_max = std::max(pl->class_max, P->csize[c]);
         if (!P->hdr.pm1) pl->pm1 = false;
         if (!P->hdr.ujs) pl->ujs = false;
         // colour classes, coupler kind and dmax decide which shapes are valid
@@ -663,8 +672,16 @@ int spvar_plan_create(const spvar_problem *const *problems, int32_t nproblems,
         const bool elig = pm1_kernel_eligible(pl->pm1, pl->dmax, pl->max_deg);
         SweepShape sh{0, blk, Q, 1, 0, 0};
         if (pl->sqa_P > 0) {
-            // SQA: one quad per CTA
-            sh = sqa_shape(pl, blk, optin);
+            // SQA: one quad per CTA; the register form (else the walk) for +-1 couplers unless the
+            // walk or the general path is asked for
+            if (p.sweep_kernel == SPVAR_SWEEP_GENERAL) sh = sqa_shape(pl, blk, optin, 0);
+            else if (p.sweep_kernel == SPVAR_SWEEP_PM1S) sh = sqa_shape(pl, blk, optin, 1);
+            else if (p.sweep_kernel == SPVAR_SWEEP_PM1W) sh.kind = -1;
+            else if (!pl->pm1) sh = sqa_shape(pl, blk, optin, 0);
+            else {
+                sh = sqa_shape(pl, blk, optin, 2);
+                if (sh.kind != 5) sh = sqa_shape(pl, blk, optin, 1);
+            }
             if (Q != 1 || sh.kind != 5) { plan_free(pl); return SPVAR_ELIMIT; }
         } else if (p.sweep_kernel == SPVAR_SWEEP_PM1 || (p.sweep_kernel == SPVAR_SWEEP_AUTO && elig)) {
             const int md = pl->max_deg <= 6 ? 6 : 8;
@@ -837,7 +854,7 @@ int spvar_plan_shape(const spvar_plan *plan, int32_t *block, int32_t *replicas_p
     if (replicas_per_block) *replicas_per_block = 4 * plan->shape.Q;
     if (staged) {
         const int k = plan->shape.kind;
-        *staged = k == 1 ? 2 : k == 2 ? 3 : k == 4 ? 4 : k == 5 ? 5 : plan->shape.stage;
+        *staged = k == 1 ? 2 : k == 2 ? 3 : k == 4 ? 4 : k == 5 ? (plan->shape.stage == 2 ? 6 : 5) : plan->shape.stage;
     }
     if (grid) *grid = plan->sweep_grid;
     return SPVAR_OK;

@@ -71,7 +71,71 @@ __device__ __forceinline__ uint4 philox_sqa(uint32_t w0, uint32_t start, uint32_
     return c;
 }
 
-template <bool PM1, int B, int MAXD>
+__device__ __forceinline__ uint32_t lds_q(const uint32_t *base, uint32_t byte_off)
+{
+    return *reinterpret_cast<const uint32_t *>(reinterpret_cast<const char *>(base) + byte_off);
+}
+__device__ __forceinline__ void sts_q(uint32_t *base, uint32_t byte_off, uint32_t v)
+{
+    *reinterpret_cast<uint32_t *>(reinterpret_cast<char *>(base) + byte_off) = v;
+}
+
+// Register-resident form, +-1 couplers: the thread's spin of one colour class
+// (its word offsets, flip-cost constant and spin word of the counter held in
+// registers) in slices PAR + 2 (g + G m), m = 0, 1, ...  Byte offsets:
+// `own4` of the spin and `o4` of its neighbours inside a slice (the inverted
+// copy folded in for J < 0; the slice's zero word for a missing neighbour),
+// `ns4` per slice, `inv4` to the inverted copy.
+template <int PAR, int MAXD>
+__device__ __forceinline__ void sqa_reg_pass(uint32_t *sw, const unsigned long long *ent, int g, int G, int P,
+                                             uint32_t own4, const uint32_t (&o4)[MAXD], uint32_t c0, uint32_t ib,
+                                             uint32_t ns4, uint32_t inv4, uint32_t k2, uint32_t W, uint32_t start,
+                                             uint32_t k1, uint32_t L1, uint32_t HA, uint32_t LA, uint32_t k0w,
+                                             uint32_t k1w, const uint32_t (&Kr0)[8], const uint32_t (&Kr1)[8])
+{
+    constexpr uint32_t M = 0x01010101u;
+    if (g < 0) return;
+    const uint32_t wrap4 = (uint32_t)(P - 1) * ns4;
+    const uint32_t step = 2u * (uint32_t)G * ns4, istep = (2u * (uint32_t)G) << 16;
+    int tau = PAR + 2 * g;
+    uint32_t base = (uint32_t)tau * ns4;
+    uint32_t iw = ib | ((uint32_t)tau << 16);
+    for (; tau < P; tau += 2 * G, base += step, iw += istep) {
+        const uint32_t oa = base + own4;
+        const uint32_t own = lds_q(sw, oa);
+        // slice neighbours; only the first even slice (down) and the last odd one (up) wrap
+        uint32_t ua = oa + ns4, da = oa - ns4;
+        if (PAR == 0) {
+            if (tau == 0) da = oa + wrap4;
+        } else {
+            if (tau == P - 1) ua = oa - wrap4;
+        }
+        const uint32_t up = lds_q(sw, ua), dn = lds_q(sw, da);
+        uint32_t x = 0;
+#pragma unroll
+        for (int d = 0; d < MAXD; ++d) x += lds_q(sw, base + o4[d]);
+        const uint32_t a4 = (~(own ^ up) & M) + (~(own ^ dn) & M);
+        // k = dE/2 + bias per byte: 2x + bias - deg + h for b_i = 0, its mirror 2 bias - that for b_i = 1
+        const uint32_t a = x + x + c0;
+        const uint32_t b = k2 - a;
+        const uint32_t m = own * 0xFFu;
+        const uint32_t full = a4 * W + ((a & ~m) | (b & m));  // entry a W + k per byte, <= 3W - 1 <= 255
+        const uint4 u = philox_sqa(iw, start, k1, L1, HA, LA, k0w, k1w, Kr0, Kr1);
+        const uint32_t ur[4] = {u.x, u.y, u.z, u.w};
+        uint32_t rej = 0;
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            // u + entry carries into bit 32 exactly when the move is rejected
+            const uint32_t e = __byte_perm(full, 0u, 0x4440u | (uint32_t)r);
+            rej |= (uint32_t)(((unsigned long long)ur[r] + ent[e]) >> 32) << (8 * r);
+        }
+        const uint32_t nw = own ^ rej ^ M;  // flip where not rejected
+        sts_q(sw, oa, nw);
+        sts_q(sw, oa + inv4, nw ^ M);
+    }
+}
+
+template <bool PM1, int B, int MAXD, int NC>
 __device__ void run_item_sqa(const SweepLaunch &L, const SweepJob &job, int quad, uint32_t *smem)
 {
     const int tid = threadIdx.x;
@@ -141,6 +205,62 @@ __device__ void run_item_sqa(const SweepLaunch &L, const SweepJob &job, int quad
     }
 
     const int nt = (P > 1) ? P / 2 : 1;  // slices per parity
+    // register form: +-1 couplers, two or more slices, at most NC colour classes of at most B spins
+    bool reg = NC > 0 && PM1 && P > 1 && ncol <= NC;
+    for (int c = 0; reg && c < ncol; ++c) reg = s_cptr[c + 1] - s_cptr[c] <= B;
+    if constexpr (PM1 && NC > 0) {
+      if (reg) {
+        constexpr int NCR = NC;
+        // class j: units (spin k, slice group g) = thread k + g nc, g < G = min(nt, B / nc)
+        uint32_t own4[NCR], o4[NCR][MAXD], c0[NCR], ib[NCR];
+        int g[NCR], G[NCR];
+#pragma unroll
+        for (int j = 0; j < NCR; ++j) {
+            g[j] = -1;
+            G[j] = 1;
+            own4[j] = c0[j] = ib[j] = 0u;
+#pragma unroll
+            for (int d = 0; d < MAXD; ++d) o4[j][d] = 0u;
+            if (j < ncol) {
+                const int lo = s_cptr[j], nc = s_cptr[j + 1] - lo;
+                if (nc > 0) {
+                    G[j] = min(nt, B / nc);
+                    if (tid < nc * G[j]) {
+                        const int gq = tid / nc, p = lo + (tid - gq * nc);
+                        const uint32_t meta = meta_s[p];
+                        g[j] = gq;
+                        own4[j] = 4u * (uint32_t)p;
+#pragma unroll
+                        for (int d = 0; d < MAXD; ++d) o4[j][d] = 4u * (uint32_t)off[d * n + p];
+                        c0[j] = (uint32_t)(bias - (int)(meta & 0xFFFFu) + ((int)meta >> 16)) * 0x01010101u;
+                        ib[j] = idx_s[p];
+                    }
+                }
+            }
+        }
+        const uint32_t ns4 = 4u * (uint32_t)ns, inv4 = 4u * (uint32_t)Pn;
+        const uint32_t k2 = (uint32_t)(2 * bias) * 0x01010101u;
+        for (int t = 0; t < T; ++t) {
+            const unsigned long long *ent = rows + (t & 1) * 3 * W;
+            if (t + 1 < T)
+                for (int x = tid; x < 3 * W; x += B) rows[((t + 1) & 1) * 3 * W + x] = L.ent[(size_t)(t + 1) * 3 * W + x];
+            uint32_t HA, LA;
+            mulhilo_q(kM0q, H1 ^ (phase_hi | (uint32_t)t) ^ k0, HA, LA);
+#pragma unroll
+            for (int j = 0; j < NCR; ++j) {
+                if (j < ncol) {
+                    sqa_reg_pass<0, MAXD>(sw, ent, g[j], G[j], P, own4[j], o4[j], c0[j], ib[j], ns4, inv4, k2,
+                                          (uint32_t)W, job.start, k1, L1, HA, LA, k0w, k1w, Kr0, Kr1);
+                    __syncthreads();
+                    sqa_reg_pass<1, MAXD>(sw, ent, g[j], G[j], P, own4[j], o4[j], c0[j], ib[j], ns4, inv4, k2,
+                                          (uint32_t)W, job.start, k1, L1, HA, LA, k0w, k1w, Kr0, Kr1);
+                    __syncthreads();
+                }
+            }
+        }
+      }
+    }
+    if (!reg)
     for (int t = 0; t < T; ++t) {
         const unsigned long long *ent = rows + (t & 1) * 3 * W;
         if (t + 1 < T)
@@ -261,7 +381,9 @@ __device__ void run_item_sqa(const SweepLaunch &L, const SweepJob &job, int quad
     }
 }
 
-template <bool PM1, int B, int MAXD>
+// NC > 0: register form for problems of at most NC colour classes of at most
+// B spins (+-1 couplers, two or more slices); other items take the walk.
+template <bool PM1, int B, int MAXD, int NC>
 __global__ void __launch_bounds__(B) k_sweep_sqa(const SweepLaunch L)
 {
     extern __shared__ __align__(16) uint32_t smem_sqa[];
@@ -270,22 +392,32 @@ __global__ void __launch_bounds__(B) k_sweep_sqa(const SweepLaunch L)
         SweepJob job;
         int quad0, nq;
         if (!next_item(L, iter, &s_item, job, quad0, nq)) break;
-        run_item_sqa<PM1, B, MAXD>(L, job, quad0, smem_sqa);
+        run_item_sqa<PM1, B, MAXD, NC>(L, job, quad0, smem_sqa);
         __syncthreads();
     }
 }
 
-// +-1 couplers: neighbour loop unrolled to MAXD (6 or 8); general couplers: MAXD unused.
-void *select_sqa(bool pm1, int block, int maxdeg)
+// variant 0: general couplers (MAXD unused); 1: +-1 couplers, item walk; 2: +-1
+// couplers, register form with ncls colour-class slots (2 or 4).  +-1: neighbour
+// loop unrolled to MAXD (6 or 8).
+void *select_sqa(int variant, int block, int maxdeg, int ncls)
 {
-#define SPVAR_SQA_CASE(PM, BB, MD) \
-    if (pm1 == PM && block == BB) return reinterpret_cast<void *>(k_sweep_sqa<PM, BB, MD>);
-    if (pm1 && maxdeg <= 6) {
-        SPVAR_SQA_CASE(true, 128, 6) SPVAR_SQA_CASE(true, 256, 6) SPVAR_SQA_CASE(true, 512, 6)
-    } else if (pm1 && maxdeg <= 8) {
-        SPVAR_SQA_CASE(true, 128, 8) SPVAR_SQA_CASE(true, 256, 8) SPVAR_SQA_CASE(true, 512, 8)
-    } else if (!pm1) {
-        SPVAR_SQA_CASE(false, 128, 0) SPVAR_SQA_CASE(false, 256, 0) SPVAR_SQA_CASE(false, 512, 0)
+#define SPVAR_SQA_CASE(PM, BB, MD, NCC) \
+    if (block == BB) return reinterpret_cast<void *>(k_sweep_sqa<PM, BB, MD, NCC>);
+    if (variant == 0) {
+        SPVAR_SQA_CASE(false, 128, 0, 0) SPVAR_SQA_CASE(false, 256, 0, 0) SPVAR_SQA_CASE(false, 512, 0, 0)
+    } else if (variant == 1 && maxdeg <= 6) {
+        SPVAR_SQA_CASE(true, 128, 6, 0) SPVAR_SQA_CASE(true, 256, 6, 0) SPVAR_SQA_CASE(true, 512, 6, 0)
+    } else if (variant == 1 && maxdeg <= 8) {
+        SPVAR_SQA_CASE(true, 128, 8, 0) SPVAR_SQA_CASE(true, 256, 8, 0) SPVAR_SQA_CASE(true, 512, 8, 0)
+    } else if (variant == 2 && ncls == 2 && maxdeg <= 6) {
+        SPVAR_SQA_CASE(true, 256, 6, 2) SPVAR_SQA_CASE(true, 512, 6, 2) SPVAR_SQA_CASE(true, 1024, 6, 2)
+    } else if (variant == 2 && ncls == 2 && maxdeg <= 8) {
+        SPVAR_SQA_CASE(true, 256, 8, 2) SPVAR_SQA_CASE(true, 512, 8, 2) SPVAR_SQA_CASE(true, 1024, 8, 2)
+    } else if (variant == 2 && ncls == 4 && maxdeg <= 6) {
+        SPVAR_SQA_CASE(true, 256, 6, 4) SPVAR_SQA_CASE(true, 512, 6, 4) SPVAR_SQA_CASE(true, 1024, 6, 4)
+    } else if (variant == 2 && ncls == 4 && maxdeg <= 8) {
+        SPVAR_SQA_CASE(true, 256, 8, 4) SPVAR_SQA_CASE(true, 512, 8, 4) SPVAR_SQA_CASE(true, 1024, 8, 4)
     }
 #undef SPVAR_SQA_CASE
     return nullptr;
@@ -293,11 +425,12 @@ void *select_sqa(bool pm1, int block, int maxdeg)
 
 }  // namespace
 
-bool sqa_shape_ok(bool pm1, int block, int max_n, int max_deg, int P, int W)
+bool sqa_shape_ok(int variant, int block, int max_n, int max_deg, int P, int W, int ncls)
 {
-    if (!select_sqa(pm1, block, max_deg) || P < 1 || (P > 1 && (P & 1)) || P > kSqaMaxSlices) return false;
+    if (!select_sqa(variant, block, max_deg, ncls) || P < 1 || (P > 1 && (P & 1)) || P > kSqaMaxSlices) return false;
+    if (variant == 2 && P < 2) return false;
     if ((long long)max_n >= (1 << 16) - 1) return false;
-    if (pm1 && ((long long)P * (max_n + 1) + max_n >= 0xFFFF || 3LL * W - 1 > 255)) return false;
+    if (variant != 0 && ((long long)P * (max_n + 1) + max_n >= 0xFFFF || 3LL * W - 1 > 255)) return false;
     return true;
 }
 
@@ -306,9 +439,10 @@ size_t sqa_smem_bytes(int max_n, int P, int maxdeg, int W, bool pm1)
     return 4 * sqa_words(max_n, P, maxdeg, W, pm1);
 }
 
-cudaError_t launch_sweep_sqa(const SweepLaunch &L, bool pm1, int block, int grid, size_t smem, cudaStream_t st)
+cudaError_t launch_sweep_sqa(const SweepLaunch &L, int variant, int block, int ncls, int grid, size_t smem,
+                             cudaStream_t st)
 {
-    void *k = select_sqa(pm1, block, L.max_deg);
+    void *k = select_sqa(variant, block, L.max_deg, ncls);
     if (!k) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -316,9 +450,9 @@ cudaError_t launch_sweep_sqa(const SweepLaunch &L, bool pm1, int block, int grid
     return cudaLaunchKernel(k, dim3(grid), dim3(block), args, smem, st);
 }
 
-int sqa_max_active_blocks(bool pm1, int block, int max_deg, size_t smem)
+int sqa_max_active_blocks(int variant, int block, int max_deg, int ncls, size_t smem)
 {
-    void *k = select_sqa(pm1, block, max_deg);
+    void *k = select_sqa(variant, block, max_deg, ncls);
     if (!k) return 0;
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int nb = 0;

@@ -461,7 +461,7 @@ class Plan:
         _check(lib().spvar_plan_shape(self.handle, ctypes.byref(b), ctypes.byref(r), ctypes.byref(s), ctypes.byref(g)),
                "spvar_plan_shape")
         return dict(block=b.value, replicas_per_block=r.value, kernel=("general", "general-staged", "pm1-register", "pm1-streaming", "pm1-warp",
-                                                                 "sqa")[s.value],
+                                                                 "sqa", "sqa-register")[s.value],
                     grid=g.value)
 
     def close(self):

@@ -143,3 +143,83 @@ def test_sqa_sampler_parameters_validated(cuda_lib):
         with pytest.raises(spvar.SpvarError):
             spvar.solve(gp, spvar.make_params(num_starts=1, fixing_sample_size=8, solving_sample_size=8,
                                               num_sweeps=10, **kw), 1)
+
+
+REQUESTED = [
+    # kernel, block, expected shape name
+    ("PM1S", 128, "sqa"),
+    ("PM1S", 512, "sqa"),
+    ("PM1", 256, "sqa-register"),
+    ("PM1", 512, "sqa-register"),
+    ("PM1", 1024, "sqa-register"),
+    ("GENERAL", 256, "sqa"),
+]
+REQ_CASES = [
+    ("chimera_C3_P4", lambda: I.chimera(3, 2120), 4, 30, 3, 24, 16, 0.2, {}),
+    ("cubic_L5_odd_3col_P8_h", lambda: with_h(I.cubic3d(5, 2121), 3, 5), 8, 20, 2, 16, 8, 0.25, {}),
+    ("cubic_L4_P2_ispvar", lambda: I.cubic3d(4, 2122), 2, 20, 2, 16, 0, 0.2, dict(iterate=True, max_fix_phases=4)),
+]
+
+
+@pytest.mark.parametrize("kernel,block,shape", REQUESTED, ids=["%s_%d" % r[:2] for r in REQUESTED])
+@pytest.mark.parametrize("name,make,P,T,starts,Sf,Ss,elite,extra", REQ_CASES, ids=[c[0] for c in REQ_CASES])
+def test_solve_with_sqa_requested_kernel(cuda_lib, kernel, block, shape, name, make, P, T, starts, Sf, Ss, elite,
+                                         extra):
+    """Every SQA sweep variant (item walk, register form at 256/512/1024
+    threads, general path), requested explicitly: Alg. 2 identical to the
+    oracle in every phase."""
+    from paper_1706_07826_gb300 import spvar
+    inst = make()
+    op = oracle_problem(inst)
+    sq = dict(sqa_slices=P, sqa_beta=3.0, sqa_gamma0=2.5, sqa_gamma1=0.05)
+    ref = O.solve(op, table(inst, T), 41, num_starts=starts, fixing_sample_size=Sf, solving_sample_size=Ss,
+                  elite_threshold=elite, sampler=1, **sq, **extra)
+    prm = spvar.make_params(num_starts=starts, fixing_sample_size=Sf, solving_sample_size=Ss, num_sweeps=T,
+                            elite_threshold=elite, sampler=spvar.SAMPLER_SQA, replicas_per_block=4,
+                            sweep_kernel=getattr(spvar, "SWEEP_" + kernel), sweep_block=block, **sq, **extra)
+    plan = spvar.Plan([gpu_problem(inst)], prm)
+    assert plan.shape()["kernel"] == shape and plan.shape()["block"] == block
+    out = plan.run([41], device=False)
+    plan.close()
+    for s in range(starts):
+        assert int(out.nphases[s]) == ref.nphases[s]
+        assert np.array_equal(np.asarray(out.counts[s]), ref.counts[s])
+        for ph in range(ref.nphases[s]):
+            c = ref.counts[s, ph]
+            assert np.array_equal(np.asarray(out.energies[s, ph, :c]), ref.energies[s, ph, :c]), (s, ph)
+        n = inst.n
+        assert int(out.best_energy[s]) == ref.best_e[s]
+        assert np.array_equal(np.asarray(out.fixed[s * n:(s + 1) * n]), ref.fixed[s])
+        assert np.array_equal(np.asarray(out.best_state[s * n:(s + 1) * n]), ref.best_state[s])
+
+
+def test_sqa_register_form_rejections(cuda_lib):
+    """The register form needs every colour class to fit the block; the warp
+    kernel has no SQA form."""
+    from paper_1706_07826_gb300 import spvar
+    gp = gpu_problem(I.cubic3d(10, 2123))  # two classes of 500 spins
+    base = dict(num_starts=1, fixing_sample_size=8, solving_sample_size=8, num_sweeps=10, sampler=spvar.SAMPLER_SQA,
+                sqa_slices=4, sqa_beta=3.0, sqa_gamma0=2.0, sqa_gamma1=0.1, replicas_per_block=4)
+    # 256 threads: falls back to the item walk
+    plan = spvar.Plan([gp], spvar.make_params(sweep_kernel=spvar.SWEEP_PM1, sweep_block=256, **base))
+    assert plan.shape()["kernel"] == "sqa"
+    plan.close()
+    plan = spvar.Plan([gp], spvar.make_params(sweep_kernel=spvar.SWEEP_PM1, sweep_block=512, **base))
+    assert plan.shape()["kernel"] == "sqa-register"
+    plan.close()
+    with pytest.raises(spvar.SpvarError):
+        spvar.Plan([gp], spvar.make_params(sweep_kernel=spvar.SWEEP_PM1W, sweep_block=256, **base))
+
+
+def test_cubic_L12_sampled_replicas_block_1024(cuda_lib):
+    """3D L = 12 (N = 1728, two colour classes of 864 spins: the register form
+    at 1024 threads), 4 slices, 40 runs; sampled runs recomputed by the oracle."""
+    inst = I.cubic3d(12, 2124)
+    op = oracle_problem(inst)
+    T, P, S = 30, 4, 40
+    ent = O.sqa_table(T, P, 3.0, O.gamma_linear(T, 3.0, 0.05), O.dmax(op), 1)
+    g_s, g_e, g_sl = _gpu(inst, P, ent, S, 77, 1, 2)
+    for r in (0, 13, 39):
+        s, e, sl = O.sqa_sample(op, ent, P, 1, 77, start=1, phase=2, r0=r)
+        assert g_e[r] == e[0] + inst.offset and g_sl[r] == sl[0]
+        assert np.array_equal(g_s[r], s[0])
