@@ -570,7 +570,7 @@ int spvar_sqa_sample(const spvar_problem *p, int32_t num_sweeps, int32_t P, cons
     L.P = P;
     L.W = W;
     L.slice_out = slice;
-    SPVAR_CUDA_TRY(launch_sweep_sqa(L, variant, block, ncls, ceil_div(num_samples, 4), smem, as_stream(stream)));
+    SPVAR_CUDA_TRY(launch_sweep_sqa(L, variant, block, ncls, false, ceil_div(num_samples, 4), smem, as_stream(stream)));
     return SPVAR_OK;
 }
 

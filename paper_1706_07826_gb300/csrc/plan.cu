@@ -91,6 +91,7 @@ struct spvar_plan {
     uint32_t *d_thr = nullptr;
     unsigned long long *d_ent = nullptr;  // SQA acceptance entries
     int sqa_P = 0, sqa_W = 0;             // SQA slices and table width (0: SA)
+    bool sqa_ent32 = false;               // SQA: no acceptance entry is 2^32 (32-bit entries suffice)
     SweepJob *d_jobs = nullptr;
     WorkItem *d_items = nullptr;
     int32_t *d_ctr = nullptr;       // [0] nitems, [1] queue, [2] nactive, [3] phases run by the loop graph
@@ -276,6 +277,7 @@ SweepShape sqa_shape(const spvar_plan *pl, int block, int optin, int variant)
     SweepShape sh{5, block, 1, variant, pl->sqa_W, pl->max_deg};
     sh.slices = pl->sqa_P;
     sh.ncls = variant == 2 ? sqa_reg_ncls(pl->ncol_max, pl->class_max, block, pl->sqa_P) : 0;
+    sh.ent32 = variant == 2 && pl->sqa_ent32 ? 1 : 0;
     const bool ok = (variant == 0 || pl->pm1) && (variant != 2 || sh.ncls > 0) &&
                     sqa_shape_ok(variant, block, pl->max_n0, pl->max_deg, pl->sqa_P, pl->sqa_W, sh.ncls) &&
                     sweep_shape_smem(sh, pl->max_n0, pl->thr_stride, pl->max_deg) <= (size_t)optin;
@@ -595,6 +597,7 @@ int spvar_plan_create(const spvar_problem *const *problems, int32_t nproblems,
                 spvar_gamma_linear(pl->T, p.sqa_gamma0, p.sqa_gamma1, sg.data());
                 spvar_sqa_table(pl->T, pl->sqa_P, sb.data(), sg.data(), dmax, scale, ent.data());
             }
+            pl->sqa_ent32 = std::all_of(ent.begin(), ent.end(), [](uint64_t v) { return (v >> 32) == 0; });
         }
         if (cudaMemcpyAsync(pl->d_thr, thr.data(), 4 * thr.size(), cudaMemcpyHostToDevice, st) != cudaSuccess ||
             (pl->sqa_P > 0 &&

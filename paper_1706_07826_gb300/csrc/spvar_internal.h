@@ -266,9 +266,9 @@ int pm1_max_active_blocks(int block, int nslot, int maxd, bool scaled, size_t sm
 constexpr int kSqaMaxSlices = 1024;
 bool sqa_shape_ok(int variant, int block, int max_n, int max_deg, int P, int W, int ncls = 0);
 size_t sqa_smem_bytes(int max_n, int P, int maxdeg, int W, bool pm1);
-cudaError_t launch_sweep_sqa(const SweepLaunch &L, int variant, int block, int ncls, int grid, size_t smem,
-                             cudaStream_t st);
-int sqa_max_active_blocks(int variant, int block, int max_deg, int ncls, size_t smem);
+cudaError_t launch_sweep_sqa(const SweepLaunch &L, int variant, int block, int ncls, bool ent32, int grid,
+                             size_t smem, cudaStream_t st);
+int sqa_max_active_blocks(int variant, int block, int max_deg, int ncls, bool ent32, size_t smem);
 // The register form holds one spin of every colour class per thread: two or
 // more slices, at most 4 classes, none larger than the block.  Colour-class
 // slots it needs (2 or 4), 0 if it does not apply.
@@ -307,6 +307,7 @@ struct SweepShape {
     int slices = 0;   // kind 5 (SQA): Trotter slices; stage = the variant (0 general, 1 +-1 walk,
                       // 2 +-1 register form), nslot the acceptance-table width W, maxd the largest degree
     int ncls = 0;     // kind 5, variant 2: colour-class slots per thread (2 or 4)
+    int ent32 = 0;    // kind 5, variant 2: 32-bit acceptance entries (no entry of the table is 2^32)
 };
 // The streaming and warp-per-quad kernels apply to +-1 couplers, degree <= 8
 // and dmax <= 254; the register kernel needs dmax <= 30.
@@ -336,7 +337,7 @@ inline size_t sweep_shape_smem(const SweepShape &s, int max_n, int thr_stride, i
 inline cudaError_t launch_sweep_shape(const SweepLaunch &L, const SweepShape &s, bool pm1, int grid, size_t smem,
                                       cudaStream_t st)
 {
-    if (s.kind == 5) return launch_sweep_sqa(L, s.stage, s.block, s.ncls, grid, smem, st);
+    if (s.kind == 5) return launch_sweep_sqa(L, s.stage, s.block, s.ncls, s.ent32 != 0, grid, smem, st);
     if (s.kind == 1) return launch_sweep_pm1(L, s.block, s.nslot, s.maxd, s.stage != 0, grid, smem, st);
     if (s.kind == 2) return launch_sweep_pm1s(L, s.block, s.maxd, grid, smem, st);
     if (s.kind == 4) return launch_sweep_pm1w(L, s.Q, s.maxd, s.nslot ? s.nslot : 2, grid, smem, st);
@@ -344,7 +345,7 @@ inline cudaError_t launch_sweep_shape(const SweepLaunch &L, const SweepShape &s,
 }
 inline int sweep_shape_occupancy(const SweepShape &s, bool pm1, size_t smem)
 {
-    if (s.kind == 5) return sqa_max_active_blocks(s.stage, s.block, s.maxd, s.ncls, smem);
+    if (s.kind == 5) return sqa_max_active_blocks(s.stage, s.block, s.maxd, s.ncls, s.ent32 != 0, smem);
     if (s.kind == 1) return pm1_max_active_blocks(s.block, s.nslot, s.maxd, s.stage != 0, smem);
     if (s.kind == 2) return pm1s_max_active_blocks(s.block, s.maxd, smem);
     if (s.kind == 4) return pm1w_max_active_blocks(s.Q, s.maxd, s.nslot ? s.nslot : 2, smem);

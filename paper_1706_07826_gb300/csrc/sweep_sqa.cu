@@ -86,56 +86,104 @@ __device__ __forceinline__ void sts_q(uint32_t *base, uint32_t byte_off, uint32_
 // `own4` of the spin and `o4` of its neighbours inside a slice (the inverted
 // copy folded in for J < 0; the slice's zero word for a missing neighbour),
 // `ns4` per slice, `inv4` to the inverted copy.
-template <int PAR, int MAXD>
-__device__ __forceinline__ void sqa_reg_pass(uint32_t *sw, const unsigned long long *ent, int g, int G, int P,
-                                             uint32_t own4, const uint32_t (&o4)[MAXD], uint32_t c0, uint32_t ib,
-                                             uint32_t ns4, uint32_t inv4, uint32_t k2, uint32_t W, uint32_t start,
-                                             uint32_t k1, uint32_t L1, uint32_t HA, uint32_t LA, uint32_t k0w,
-                                             uint32_t k1w, const uint32_t (&Kr0)[8], const uint32_t (&Kr1)[8])
+struct SqaRegConsts {
+    uint32_t ns4, inv4, wrap4, k2, W, start, k1, L1, HA, LA, k0w, k1w;
+};
+
+// U independent items (slices tau[u] of one parity, so none reads a word
+// another writes): every load first, then the flip costs, the random words
+// and the acceptance of all of them, then the stores.  `chain`: the items are
+// consecutive slices of the thread's sequence (tau, tau + 2, ...), so the
+// down neighbour of one is the up neighbour of the one before (`prev_up`,
+// valid when `have`).  E32: acceptance entries are 32-bit (no entry of the
+// table is 2^32, i.e. every flip has a nonzero acceptance probability).
+template <int PAR, int MAXD, int U, bool E32>
+__device__ __forceinline__ void sqa_reg_items(uint32_t *sw, const void *entv, int P, const int (&tau)[U],
+                                              const uint32_t (&base)[U], const uint32_t (&iw)[U], uint32_t own4,
+                                              const uint32_t (&o4)[MAXD], uint32_t c0, const SqaRegConsts &K,
+                                              const uint32_t (&Kr0)[8], const uint32_t (&Kr1)[8], bool chain,
+                                              bool have, uint32_t &prev_up)
 {
     constexpr uint32_t M = 0x01010101u;
-    if (g < 0) return;
-    const uint32_t wrap4 = (uint32_t)(P - 1) * ns4;
-    const uint32_t step = 2u * (uint32_t)G * ns4, istep = (2u * (uint32_t)G) << 16;
-    int tau = PAR + 2 * g;
-    uint32_t base = (uint32_t)tau * ns4;
-    uint32_t iw = ib | ((uint32_t)tau << 16);
-    for (; tau < P; tau += 2 * G, base += step, iw += istep) {
-        const uint32_t oa = base + own4;
-        const uint32_t own = lds_q(sw, oa);
-        // slice neighbours; only the first even slice (down) and the last odd one (up) wrap
-        uint32_t ua = oa + ns4, da = oa - ns4;
-        if (PAR == 0) {
-            if (tau == 0) da = oa + wrap4;
-        } else {
-            if (tau == P - 1) ua = oa - wrap4;
-        }
-        const uint32_t up = lds_q(sw, ua), dn = lds_q(sw, da);
-        uint32_t x = 0;
+    uint32_t oa[U], own[U], up[U], dn[U], x[U];
 #pragma unroll
-        for (int d = 0; d < MAXD; ++d) x += lds_q(sw, base + o4[d]);
-        const uint32_t a4 = (~(own ^ up) & M) + (~(own ^ dn) & M);
+    for (int u = 0; u < U; ++u) {
+        oa[u] = base[u] + own4;
+        own[u] = lds_q(sw, oa[u]);
+        // slice neighbours; only the first even slice (down) and the last odd one (up) wrap
+        uint32_t ua = oa[u] + K.ns4, da = oa[u] - K.ns4;
+        if (PAR == 0) {
+            if (tau[u] == 0) da = oa[u] + K.wrap4;
+        } else {
+            if (tau[u] == P - 1) ua = oa[u] - K.wrap4;
+        }
+        up[u] = lds_q(sw, ua);
+        if (chain && (u > 0 || have)) dn[u] = u > 0 ? up[u - 1] : prev_up;
+        else dn[u] = lds_q(sw, da);
+        x[u] = 0;
+#pragma unroll
+        for (int d = 0; d < MAXD; ++d) x[u] += lds_q(sw, base[u] + o4[d]);
+    }
+    prev_up = up[U - 1];
+    uint32_t nw[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        const uint32_t a4 = (~(own[u] ^ up[u]) & M) + (~(own[u] ^ dn[u]) & M);
         // k = dE/2 + bias per byte: 2x + bias - deg + h for b_i = 0, its mirror 2 bias - that for b_i = 1
-        const uint32_t a = x + x + c0;
-        const uint32_t b = k2 - a;
-        const uint32_t m = own * 0xFFu;
-        const uint32_t full = a4 * W + ((a & ~m) | (b & m));  // entry a W + k per byte, <= 3W - 1 <= 255
-        const uint4 u = philox_sqa(iw, start, k1, L1, HA, LA, k0w, k1w, Kr0, Kr1);
-        const uint32_t ur[4] = {u.x, u.y, u.z, u.w};
+        const uint32_t a = x[u] + x[u] + c0;
+        const uint32_t b = K.k2 - a;
+        const uint32_t m = own[u] * 0xFFu;
+        const uint32_t full = a4 * K.W + ((a & ~m) | (b & m));  // entry a W + k per byte, <= 3W - 1 <= 255
+        const uint4 r4 = philox_sqa(iw[u], K.start, K.k1, K.L1, K.HA, K.LA, K.k0w, K.k1w, Kr0, Kr1);
+        const uint32_t ur[4] = {r4.x, r4.y, r4.z, r4.w};
         uint32_t rej = 0;
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
             // u + entry carries into bit 32 exactly when the move is rejected
             const uint32_t e = __byte_perm(full, 0u, 0x4440u | (uint32_t)r);
-            rej |= (uint32_t)(((unsigned long long)ur[r] + ent[e]) >> 32) << (8 * r);
+            const unsigned long long v = E32 ? (unsigned long long)static_cast<const uint32_t *>(entv)[e]
+                                             : static_cast<const unsigned long long *>(entv)[e];
+            rej |= (uint32_t)(((unsigned long long)ur[r] + v) >> 32) << (8 * r);
         }
-        const uint32_t nw = own ^ rej ^ M;  // flip where not rejected
-        sts_q(sw, oa, nw);
-        sts_q(sw, oa + inv4, nw ^ M);
+        nw[u] = own[u] ^ rej ^ M;  // flip where not rejected
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        sts_q(sw, oa[u], nw[u]);
+        sts_q(sw, oa[u] + K.inv4, nw[u] ^ M);
     }
 }
 
-template <bool PM1, int B, int MAXD, int NC>
+// One parity pass of one colour-class slot: slices two at a time.
+template <int PAR, int MAXD, bool E32>
+__device__ __forceinline__ void sqa_reg_pass(uint32_t *sw, const void *ent, int g, int G, int P, uint32_t own4,
+                                             const uint32_t (&o4)[MAXD], uint32_t c0, uint32_t ib,
+                                             const SqaRegConsts &K, const uint32_t (&Kr0)[8],
+                                             const uint32_t (&Kr1)[8])
+{
+    if (g < 0) return;
+    const int dt = 2 * G;
+    const bool chain = G == 1;
+    const uint32_t step = (uint32_t)dt * K.ns4, istep = (uint32_t)dt << 16;
+    int tau = PAR + 2 * g;
+    uint32_t base = (uint32_t)tau * K.ns4;
+    uint32_t iw = ib | ((uint32_t)tau << 16);
+    uint32_t prev_up = 0u;
+    bool have = false;
+    for (; tau + dt < P; tau += 2 * dt, base += 2 * step, iw += 2 * istep) {
+        const int t2[2] = {tau, tau + dt};
+        const uint32_t b2[2] = {base, base + step}, i2[2] = {iw, iw + istep};
+        sqa_reg_items<PAR, MAXD, 2, E32>(sw, ent, P, t2, b2, i2, own4, o4, c0, K, Kr0, Kr1, chain, have, prev_up);
+        have = true;
+    }
+    if (tau < P) {
+        const int t1[1] = {tau};
+        const uint32_t b1[1] = {base}, i1[1] = {iw};
+        sqa_reg_items<PAR, MAXD, 1, E32>(sw, ent, P, t1, b1, i1, own4, o4, c0, K, Kr0, Kr1, chain, have, prev_up);
+    }
+}
+
+template <bool PM1, int B, int MAXD, int NC, bool E32>
 __device__ void run_item_sqa(const SweepLaunch &L, const SweepJob &job, int quad, uint32_t *smem)
 {
     const int tid = threadIdx.x;
@@ -238,22 +286,41 @@ __device__ void run_item_sqa(const SweepLaunch &L, const SweepJob &job, int quad
                 }
             }
         }
-        const uint32_t ns4 = 4u * (uint32_t)ns, inv4 = 4u * (uint32_t)Pn;
-        const uint32_t k2 = (uint32_t)(2 * bias) * 0x01010101u;
+        SqaRegConsts K;
+        K.ns4 = 4u * (uint32_t)ns;
+        K.inv4 = 4u * (uint32_t)Pn;
+        K.wrap4 = (uint32_t)(P - 1) * K.ns4;
+        K.k2 = (uint32_t)(2 * bias) * 0x01010101u;
+        K.W = (uint32_t)W;
+        K.start = job.start;
+        K.k1 = k1;
+        K.L1 = L1;
+        K.k0w = k0w;
+        K.k1w = k1w;
+        // E32: the rows as 32-bit entries (low words) in the same space
+        uint32_t *rows32 = reinterpret_cast<uint32_t *>(rows);
+        if (E32) {
+            __syncthreads();  // every thread has read the 64-bit row 0
+            for (int x = tid; x < 3 * W; x += B) rows32[x] = (uint32_t)L.ent[x];
+            __syncthreads();
+        }
         for (int t = 0; t < T; ++t) {
-            const unsigned long long *ent = rows + (t & 1) * 3 * W;
-            if (t + 1 < T)
-                for (int x = tid; x < 3 * W; x += B) rows[((t + 1) & 1) * 3 * W + x] = L.ent[(size_t)(t + 1) * 3 * W + x];
-            uint32_t HA, LA;
-            mulhilo_q(kM0q, H1 ^ (phase_hi | (uint32_t)t) ^ k0, HA, LA);
+            const void *ent = E32 ? static_cast<const void *>(rows32 + (t & 1) * 3 * W)
+                                  : static_cast<const void *>(rows + (t & 1) * 3 * W);
+            if (t + 1 < T) {
+                const unsigned long long *src = L.ent + (size_t)(t + 1) * 3 * W;
+                if (E32)
+                    for (int x = tid; x < 3 * W; x += B) rows32[((t + 1) & 1) * 3 * W + x] = (uint32_t)src[x];
+                else
+                    for (int x = tid; x < 3 * W; x += B) rows[((t + 1) & 1) * 3 * W + x] = src[x];
+            }
+            mulhilo_q(kM0q, H1 ^ (phase_hi | (uint32_t)t) ^ k0, K.HA, K.LA);
 #pragma unroll
             for (int j = 0; j < NCR; ++j) {
                 if (j < ncol) {
-                    sqa_reg_pass<0, MAXD>(sw, ent, g[j], G[j], P, own4[j], o4[j], c0[j], ib[j], ns4, inv4, k2,
-                                          (uint32_t)W, job.start, k1, L1, HA, LA, k0w, k1w, Kr0, Kr1);
+                    sqa_reg_pass<0, MAXD, E32>(sw, ent, g[j], G[j], P, own4[j], o4[j], c0[j], ib[j], K, Kr0, Kr1);
                     __syncthreads();
-                    sqa_reg_pass<1, MAXD>(sw, ent, g[j], G[j], P, own4[j], o4[j], c0[j], ib[j], ns4, inv4, k2,
-                                          (uint32_t)W, job.start, k1, L1, HA, LA, k0w, k1w, Kr0, Kr1);
+                    sqa_reg_pass<1, MAXD, E32>(sw, ent, g[j], G[j], P, own4[j], o4[j], c0[j], ib[j], K, Kr0, Kr1);
                     __syncthreads();
                 }
             }
@@ -383,8 +450,8 @@ __device__ void run_item_sqa(const SweepLaunch &L, const SweepJob &job, int quad
 
 // NC > 0: register form for problems of at most NC colour classes of at most
 // B spins (+-1 couplers, two or more slices); other items take the walk.
-template <bool PM1, int B, int MAXD, int NC>
-__global__ void __launch_bounds__(B) k_sweep_sqa(const SweepLaunch L)
+template <bool PM1, int B, int MAXD, int NC, bool E32>
+__global__ void __launch_bounds__(B, (NC > 0 && B == 256) ? 2 : 1) k_sweep_sqa(const SweepLaunch L)
 {
     extern __shared__ __align__(16) uint32_t smem_sqa[];
     __shared__ int s_item;
@@ -392,33 +459,41 @@ __global__ void __launch_bounds__(B) k_sweep_sqa(const SweepLaunch L)
         SweepJob job;
         int quad0, nq;
         if (!next_item(L, iter, &s_item, job, quad0, nq)) break;
-        run_item_sqa<PM1, B, MAXD, NC>(L, job, quad0, smem_sqa);
+        run_item_sqa<PM1, B, MAXD, NC, E32>(L, job, quad0, smem_sqa);
         __syncthreads();
     }
 }
 
 // variant 0: general couplers (MAXD unused); 1: +-1 couplers, item walk; 2: +-1
-// couplers, register form with ncls colour-class slots (2 or 4).  +-1: neighbour
-// loop unrolled to MAXD (6 or 8).
-void *select_sqa(int variant, int block, int maxdeg, int ncls)
+// couplers, register form with ncls colour-class slots (2 or 4) and, with
+// ent32, 32-bit acceptance entries.  +-1: neighbour loop unrolled to MAXD (6 or 8).
+void *select_sqa(int variant, int block, int maxdeg, int ncls, bool ent32)
 {
-#define SPVAR_SQA_CASE(PM, BB, MD, NCC) \
-    if (block == BB) return reinterpret_cast<void *>(k_sweep_sqa<PM, BB, MD, NCC>);
+#define SPVAR_SQA_CASE(PM, BB, MD, NCC, E) \
+    if (block == BB) return reinterpret_cast<void *>(k_sweep_sqa<PM, BB, MD, NCC, E>);
+#define SPVAR_SQA_REG(MD, NCC, E) \
+    SPVAR_SQA_CASE(true, 256, MD, NCC, E) SPVAR_SQA_CASE(true, 512, MD, NCC, E) SPVAR_SQA_CASE(true, 1024, MD, NCC, E)
     if (variant == 0) {
-        SPVAR_SQA_CASE(false, 128, 0, 0) SPVAR_SQA_CASE(false, 256, 0, 0) SPVAR_SQA_CASE(false, 512, 0, 0)
+        SPVAR_SQA_CASE(false, 128, 0, 0, false) SPVAR_SQA_CASE(false, 256, 0, 0, false)
+        SPVAR_SQA_CASE(false, 512, 0, 0, false)
     } else if (variant == 1 && maxdeg <= 6) {
-        SPVAR_SQA_CASE(true, 128, 6, 0) SPVAR_SQA_CASE(true, 256, 6, 0) SPVAR_SQA_CASE(true, 512, 6, 0)
+        SPVAR_SQA_CASE(true, 128, 6, 0, false) SPVAR_SQA_CASE(true, 256, 6, 0, false)
+        SPVAR_SQA_CASE(true, 512, 6, 0, false)
     } else if (variant == 1 && maxdeg <= 8) {
-        SPVAR_SQA_CASE(true, 128, 8, 0) SPVAR_SQA_CASE(true, 256, 8, 0) SPVAR_SQA_CASE(true, 512, 8, 0)
-    } else if (variant == 2 && ncls == 2 && maxdeg <= 6) {
-        SPVAR_SQA_CASE(true, 256, 6, 2) SPVAR_SQA_CASE(true, 512, 6, 2) SPVAR_SQA_CASE(true, 1024, 6, 2)
-    } else if (variant == 2 && ncls == 2 && maxdeg <= 8) {
-        SPVAR_SQA_CASE(true, 256, 8, 2) SPVAR_SQA_CASE(true, 512, 8, 2) SPVAR_SQA_CASE(true, 1024, 8, 2)
-    } else if (variant == 2 && ncls == 4 && maxdeg <= 6) {
-        SPVAR_SQA_CASE(true, 256, 6, 4) SPVAR_SQA_CASE(true, 512, 6, 4) SPVAR_SQA_CASE(true, 1024, 6, 4)
-    } else if (variant == 2 && ncls == 4 && maxdeg <= 8) {
-        SPVAR_SQA_CASE(true, 256, 8, 4) SPVAR_SQA_CASE(true, 512, 8, 4) SPVAR_SQA_CASE(true, 1024, 8, 4)
+        SPVAR_SQA_CASE(true, 128, 8, 0, false) SPVAR_SQA_CASE(true, 256, 8, 0, false)
+        SPVAR_SQA_CASE(true, 512, 8, 0, false)
+    } else if (variant == 2) {
+        const int md = maxdeg <= 6 ? 6 : maxdeg <= 8 ? 8 : 0;
+        if (md == 6 && ncls == 2 && !ent32) { SPVAR_SQA_REG(6, 2, false) }
+        if (md == 6 && ncls == 2 && ent32) { SPVAR_SQA_REG(6, 2, true) }
+        if (md == 6 && ncls == 4 && !ent32) { SPVAR_SQA_REG(6, 4, false) }
+        if (md == 6 && ncls == 4 && ent32) { SPVAR_SQA_REG(6, 4, true) }
+        if (md == 8 && ncls == 2 && !ent32) { SPVAR_SQA_REG(8, 2, false) }
+        if (md == 8 && ncls == 2 && ent32) { SPVAR_SQA_REG(8, 2, true) }
+        if (md == 8 && ncls == 4 && !ent32) { SPVAR_SQA_REG(8, 4, false) }
+        if (md == 8 && ncls == 4 && ent32) { SPVAR_SQA_REG(8, 4, true) }
     }
+#undef SPVAR_SQA_REG
 #undef SPVAR_SQA_CASE
     return nullptr;
 }
@@ -427,7 +502,7 @@ void *select_sqa(int variant, int block, int maxdeg, int ncls)
 
 bool sqa_shape_ok(int variant, int block, int max_n, int max_deg, int P, int W, int ncls)
 {
-    if (!select_sqa(variant, block, max_deg, ncls) || P < 1 || (P > 1 && (P & 1)) || P > kSqaMaxSlices) return false;
+    if (!select_sqa(variant, block, max_deg, ncls, false) || P < 1 || (P > 1 && (P & 1)) || P > kSqaMaxSlices) return false;
     if (variant == 2 && P < 2) return false;
     if ((long long)max_n >= (1 << 16) - 1) return false;
     if (variant != 0 && ((long long)P * (max_n + 1) + max_n >= 0xFFFF || 3LL * W - 1 > 255)) return false;
@@ -439,10 +514,10 @@ size_t sqa_smem_bytes(int max_n, int P, int maxdeg, int W, bool pm1)
     return 4 * sqa_words(max_n, P, maxdeg, W, pm1);
 }
 
-cudaError_t launch_sweep_sqa(const SweepLaunch &L, int variant, int block, int ncls, int grid, size_t smem,
-                             cudaStream_t st)
+cudaError_t launch_sweep_sqa(const SweepLaunch &L, int variant, int block, int ncls, bool ent32, int grid,
+                             size_t smem, cudaStream_t st)
 {
-    void *k = select_sqa(variant, block, L.max_deg, ncls);
+    void *k = select_sqa(variant, block, L.max_deg, ncls, ent32);
     if (!k) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -450,9 +525,9 @@ cudaError_t launch_sweep_sqa(const SweepLaunch &L, int variant, int block, int n
     return cudaLaunchKernel(k, dim3(grid), dim3(block), args, smem, st);
 }
 
-int sqa_max_active_blocks(int variant, int block, int max_deg, int ncls, size_t smem)
+int sqa_max_active_blocks(int variant, int block, int max_deg, int ncls, bool ent32, size_t smem)
 {
-    void *k = select_sqa(variant, block, max_deg, ncls);
+    void *k = select_sqa(variant, block, max_deg, ncls, ent32);
     if (!k) return 0;
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int nb = 0;

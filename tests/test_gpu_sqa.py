@@ -223,3 +223,29 @@ def test_cubic_L12_sampled_replicas_block_1024(cuda_lib):
         s, e, sl = O.sqa_sample(op, ent, P, 1, 77, start=1, phase=2, r0=r)
         assert g_e[r] == e[0] + inst.offset and g_sl[r] == sl[0]
         assert np.array_equal(g_s[r], s[0])
+
+
+def test_sqa_register_form_with_never_accept_entries(cuda_lib):
+    """A transverse field that ends near zero makes the slice coupling so
+    strong that some moves are never accepted (entry 2^32): the register form
+    then keeps 64-bit entries, and Alg. 2 stays identical to the oracle."""
+    from paper_1706_07826_gb300 import spvar
+    inst = I.chimera(3, 2125)
+    op = oracle_problem(inst)
+    T, P = 30, 8
+    sq = dict(sqa_slices=P, sqa_beta=3.0, sqa_gamma0=2.0, sqa_gamma1=1e-7)
+    ent = O.sqa_table(T, P, 3.0, O.gamma_linear(T, 2.0, 1e-7), O.dmax(op), 1)
+    assert (ent == 1 << 32).any()
+    kw = dict(num_starts=2, fixing_sample_size=24, solving_sample_size=16, elite_threshold=0.2)
+    ref = O.solve(op, table(inst, T), 43, sampler=1, **sq, **kw)
+    prm = spvar.make_params(num_sweeps=T, sampler=spvar.SAMPLER_SQA, replicas_per_block=4,
+                            sweep_kernel=spvar.SWEEP_PM1, sweep_block=256, **sq, **kw)
+    plan = spvar.Plan([gpu_problem(inst)], prm)
+    assert plan.shape()["kernel"] == "sqa-register"
+    out = plan.run([43], device=False)
+    plan.close()
+    for s in range(2):
+        for ph in range(ref.nphases[s]):
+            c = ref.counts[s, ph]
+            assert np.array_equal(np.asarray(out.energies[s, ph, :c]), ref.energies[s, ph, :c]), (s, ph)
+        assert np.array_equal(np.asarray(out.best_state[s * inst.n:(s + 1) * inst.n]), ref.best_state[s])
