@@ -356,8 +356,9 @@ std::vector<SweepShape> candidate_shapes(const spvar_plan *pl, int optin)
     return out;
 }
 
-// Times the plan's first phase (a short anneal) for every candidate shape and
-// keeps the fastest; results are cached per problem/plan geometry.
+// Times a short run of the plan's phases (at most 4, at most 48 sweeps each)
+// for every candidate shape and keeps the fastest; results are cached per
+// problem/plan geometry.
 void autotune(spvar_plan *pl, cudaStream_t st, int optin)
 {
     const TuneKey key{pl->max_n0, pl->max_deg, pl->pm1 ? 1 : 0, pl->C.S_fix, pl->C.nslots,
@@ -367,6 +368,8 @@ void autotune(spvar_plan *pl, cudaStream_t st, int optin)
         auto it = g_tune_cache.find(key);
         if (it != g_tune_cache.end()) {
             pl->shape = it->second;
+            // 32-bit acceptance entries are a property of this plan's table, not of the geometry
+            if (pl->shape.kind == 5 && pl->shape.stage == 2) pl->shape.ent32 = pl->sqa_ent32 ? 1 : 0;
             pl->sweep_smem = sweep_shape_smem(pl->shape, pl->max_n0, pl->thr_stride, pl->max_deg);
             return;
         }

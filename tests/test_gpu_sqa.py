@@ -249,3 +249,24 @@ def test_sqa_register_form_with_never_accept_entries(cuda_lib):
             c = ref.counts[s, ph]
             assert np.array_equal(np.asarray(out.energies[s, ph, :c]), ref.energies[s, ph, :c]), (s, ph)
         assert np.array_equal(np.asarray(out.best_state[s * inst.n:(s + 1) * inst.n]), ref.best_state[s])
+
+
+def test_sqa_autotune_cache_keeps_each_tables_entry_width(cuda_lib):
+    """Two autotuned plans of the same geometry share the tuned shape, but the
+    second one's table has never-accept entries: it must not inherit 32-bit
+    entries from the first."""
+    from paper_1706_07826_gb300 import spvar
+    inst = I.chimera(3, 2126)
+    op = oracle_problem(inst)
+    T, P = 30, 8
+    kw = dict(num_starts=2, fixing_sample_size=24, solving_sample_size=16, elite_threshold=0.2)
+    for g1 in (0.05, 1e-7):
+        sq = dict(sqa_slices=P, sqa_beta=3.0, sqa_gamma0=2.0, sqa_gamma1=g1)
+        plan = spvar.Plan([gpu_problem(inst)], spvar.make_params(num_sweeps=T, sampler=spvar.SAMPLER_SQA, **sq, **kw))
+        out = plan.run([44], device=False)
+        plan.close()
+        ref = O.solve(op, table(inst, T), 44, sampler=1, **sq, **kw)
+        for s in range(2):
+            for ph in range(ref.nphases[s]):
+                c = ref.counts[s, ph]
+                assert np.array_equal(np.asarray(out.energies[s, ph, :c]), ref.energies[s, ph, :c]), (g1, s, ph)
