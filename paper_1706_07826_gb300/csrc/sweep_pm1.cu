@@ -109,11 +109,11 @@ __device__ __forceinline__ RoundKeys round_keys(uint32_t k0, uint32_t k1)
     return K;
 }
 
+// (h, l): the round-2 product of word 0, M0 (A ^ y).
 template <int MAXD>
-__device__ __forceinline__ uint4 philox_slot(const SlotRegs<MAXD> &s, uint32_t y, const RoundKeys &K)
+__device__ __forceinline__ uint4 philox_slot_hl(const SlotRegs<MAXD> &s, uint32_t h, uint32_t l, const RoundKeys &K)
 {
-    uint32_t h, l, h2, l2;
-    mulhilo(kM0, s.A ^ y, h, l);          // round 2: word 0 product
+    uint32_t h2, l2;
     mulhilo(kM1, h ^ s.L0k, h2, l2);      // round 3: word 2 product
     uint4 c = make_uint4(h2 ^ s.D, l2, s.H3k ^ l, s.L3);
 #pragma unroll
@@ -124,6 +124,14 @@ __device__ __forceinline__ uint4 philox_slot(const SlotRegs<MAXD> &s, uint32_t y
         c = make_uint4(e ^ c.y ^ K.k0[r - 3], f, a ^ c.w ^ K.k1[r - 3], b);
     }
     return c;
+}
+
+template <int MAXD>
+__device__ __forceinline__ uint4 philox_slot(const SlotRegs<MAXD> &s, uint32_t y, const RoundKeys &K)
+{
+    uint32_t h, l;
+    mulhilo(kM0, s.A ^ y, h, l);          // round 2: word 0 product
+    return philox_slot_hl(s, h, l, K);
 }
 
 // Shared memory of one CTA: spin words (plain copy, a dummy word, inverted
@@ -140,12 +148,16 @@ struct Pm1Smem {
 // slot (lanes without an item anneal the dummy word: no branch per slot); a
 // barrier precedes slot j when it starts a new colour class (bit j of
 // barmask) and closes the sweep.
-template <int B, int NSLOT, int MAXD, bool SCALED, int PAR>
+// ONEQ: every item of the CTA is of one quad (word A of every slot is A0), so
+// the round-2 product of word 0 is computed once per sweep, not per slot.
+template <int B, int NSLOT, int MAXD, bool SCALED, int PAR, bool ONEQ>
 __device__ __forceinline__ void sweep_once(Pm1Smem<B, NSLOT> &sm, unsigned long long *drow,
                                            const SlotRegs<MAXD> (&s)[NSLOT], uint32_t y,
                                            const RoundKeys &K, uint32_t barmask, uint32_t one,
-                                           uint32_t k16, const uint32_t *next_src, int bias)
+                                           uint32_t k16, const uint32_t *next_src, int bias, uint32_t A0)
 {
+    uint32_t hA = 0u, lA = 0u;
+    if (ONEQ) mulhilo(kM0, A0 ^ y, hA, lA);
     constexpr uint32_t kInv = 4u * (uint32_t)Pm1Smem<B, NSLOT>::KW;  // byte distance to the inverted copy
     // next sweep's row (its buffer was last read in the previous sweep)
     if (SCALED) {
@@ -166,7 +178,7 @@ __device__ __forceinline__ void sweep_once(Pm1Smem<B, NSLOT> &sm, unsigned long 
             uint32_t nbw[MAXD];
 #pragma unroll
             for (int d = 0; d < MAXD; ++d) nbw[d] = lds_b(sm.sw, s[j].nb[d]);
-            const uint4 u = philox_slot(s[j], y, K);
+            const uint4 u = ONEQ ? philox_slot_hl(s[j], hA, lA, K) : philox_slot(s[j], y, K);
             uint32_t x = 0;
 #pragma unroll
             for (int d = 0; d < MAXD; ++d) x += nbw[d];
@@ -213,6 +225,29 @@ __device__ __forceinline__ void sweep_once(Pm1Smem<B, NSLOT> &sm, unsigned long 
         }
     }
     __syncthreads();
+}
+
+// Sweeps t0 .. T - 1, two per step (the rows alternate).
+template <int B, int NSLOT, int MAXD, bool SCALED, bool ONEQ>
+__device__ __forceinline__ void sweeps(Pm1Smem<B, NSLOT> &sm, unsigned long long *drow, const SlotRegs<MAXD> (&s)[NSLOT],
+                                       int t0, int T, uint32_t phase_hi, const RoundKeys &K, uint32_t barmask,
+                                       uint32_t one, uint32_t k16, const uint32_t *thr, size_t ts, int bias, uint32_t A0)
+{
+    int t = t0;
+    if (t < T && (t & 1)) {
+        sweep_once<B, NSLOT, MAXD, SCALED, 1, ONEQ>(sm, drow, s, phase_hi | (uint32_t)t, K, barmask, one, k16,
+                                                    t + 1 < T ? thr + (size_t)(t + 1) * ts : nullptr, bias, A0);
+        ++t;
+    }
+    for (; t + 1 < T; t += 2) {
+        sweep_once<B, NSLOT, MAXD, SCALED, 0, ONEQ>(sm, drow, s, phase_hi | (uint32_t)t, K, barmask, one, k16,
+                                                    thr + (size_t)(t + 1) * ts, bias, A0);
+        sweep_once<B, NSLOT, MAXD, SCALED, 1, ONEQ>(sm, drow, s, phase_hi | (uint32_t)(t + 1), K, barmask, one,
+                                                    k16, t + 2 < T ? thr + (size_t)(t + 2) * ts : nullptr, bias, A0);
+    }
+    if (t < T)
+        sweep_once<B, NSLOT, MAXD, SCALED, 0, ONEQ>(sm, drow, s, phase_hi | (uint32_t)t, K, barmask, one, k16,
+                                                    nullptr, bias, A0);
 }
 
 template <int B, int NSLOT, int MAXD, bool SCALED>
@@ -316,20 +351,15 @@ __device__ void run_item_pm1(const SweepLaunch &L, const SweepJob &job, int quad
     const uint32_t *thr = L.thr;
     const size_t ts = (size_t)L.thr_stride;
 
-    int t = t0;
-    if (t < T && (t & 1)) {
-        sweep_once<B, NSLOT, MAXD, SCALED, 1>(sm, drow, s, phase_hi | (uint32_t)t, K, barmask, one, k16,
-                                      t + 1 < T ? thr + (size_t)(t + 1) * ts : nullptr, bias);
-        ++t;
+    if (nq == 1) {
+        uint32_t H1, L1;
+        mulhilo(kM1, (uint32_t)quad0, H1, L1);
+        sweeps<B, NSLOT, MAXD, SCALED, true>(sm, drow, s, t0, T, phase_hi, K, barmask, one, k16, thr, ts, bias,
+                                             H1 ^ k0);
+    } else {
+        sweeps<B, NSLOT, MAXD, SCALED, false>(sm, drow, s, t0, T, phase_hi, K, barmask, one, k16, thr, ts, bias,
+                                              0u);
     }
-    for (; t + 1 < T; t += 2) {
-        sweep_once<B, NSLOT, MAXD, SCALED, 0>(sm, drow, s, phase_hi | (uint32_t)t, K, barmask, one, k16,
-                                      thr + (size_t)(t + 1) * ts, bias);
-        sweep_once<B, NSLOT, MAXD, SCALED, 1>(sm, drow, s, phase_hi | (uint32_t)(t + 1), K, barmask, one, k16,
-                                      t + 2 < T ? thr + (size_t)(t + 2) * ts : nullptr, bias);
-    }
-    if (t < T)
-        sweep_once<B, NSLOT, MAXD, SCALED, 0>(sm, drow, s, phase_hi | (uint32_t)t, K, barmask, one, k16, nullptr, bias);
     // the inverted copy is dead now: its first 4 nq words hold the energy sums
     finish_item<!SCALED>(P, job, quad0, nq, sm.sw, reinterpret_cast<int *>(sm.sw + KW));  // general J for SCALED
 }
