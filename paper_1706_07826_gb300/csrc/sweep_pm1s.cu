@@ -26,14 +26,21 @@ struct Keys10 {
     uint32_t k0[10], k1[10];
 };
 
-__device__ __forceinline__ uint4 philox_keys(uint4 c, const Keys10 &K)
+// Philox4x32-10 of counter (i, y, quad, start) with the quad's products
+// hoisted: L1k = lo(M1 quad) ^ key0 of round 2 (per CTA item), (HA, LA) = M0 (hi(M1 quad) ^ y ^ key0)
+// (round 2, word 0: per sweep); zs = start ^ key1 of round 1.
+__device__ __forceinline__ uint4 philox_quad(uint32_t i, uint32_t zs, uint32_t L1k, uint32_t HA, uint32_t LA,
+                                             const Keys10 &K)
 {
+    const uint64_t p0 = (uint64_t)0xD2511F53u * i;                          // round 1, word 0
+    const uint64_t p1 = (uint64_t)0xCD9E8D57u * ((uint32_t)(p0 >> 32) ^ zs);  // round 2, word 2
+    uint4 c = make_uint4((uint32_t)(p1 >> 32) ^ L1k, (uint32_t)p1, HA ^ (uint32_t)p0 ^ K.k1[1], LA);
 #pragma unroll
-    for (int r = 0; r < 10; ++r) {
-        const uint64_t p0 = (uint64_t)0xD2511F53u * c.x;
-        const uint64_t p1 = (uint64_t)0xCD9E8D57u * c.z;
-        c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ K.k0[r], (uint32_t)p1, (uint32_t)(p0 >> 32) ^ c.w ^ K.k1[r],
-                       (uint32_t)p0);
+    for (int r = 2; r < 10; ++r) {
+        const uint64_t q0 = (uint64_t)0xD2511F53u * c.x;
+        const uint64_t q1 = (uint64_t)0xCD9E8D57u * c.z;
+        c = make_uint4((uint32_t)(q1 >> 32) ^ c.y ^ K.k0[r], (uint32_t)q1, (uint32_t)(q0 >> 32) ^ c.w ^ K.k1[r],
+                       (uint32_t)q0);
     }
     return c;
 }
@@ -114,9 +121,14 @@ __device__ void run_item_pm1s(const SweepLaunch &L, const SweepJob &job, int qua
         }
     }
 
+    // the quad's Philox products: round 1 word 2 per item, round 2 word 0 per sweep
+    const uint64_t pq = (uint64_t)0xCD9E8D57u * (uint32_t)quad0;
+    const uint32_t H1 = (uint32_t)(pq >> 32), L1k = (uint32_t)pq ^ K.k0[1], zs = job.start ^ K.k1[0];
     for (int t = t0; t < T; ++t) {
         const uint32_t *th = trow + (t & 1) * kRowWordsS;
         const uint32_t y = phase_hi | (uint32_t)t;
+        const uint64_t pa = (uint64_t)0xD2511F53u * (H1 ^ y ^ K.k0[0]);
+        const uint32_t HA = (uint32_t)(pa >> 32), LA = (uint32_t)pa;
         for (int c = 0; c < ncol; ++c) {
             if (c == 0 && t + 1 < T) {
                 uint32_t *nxt = trow + ((t + 1) & 1) * kRowWordsS;
@@ -125,15 +137,14 @@ __device__ void run_item_pm1s(const SweepLaunch &L, const SweepJob &job, int qua
             }
             const int lo = s_cptr[c];
             const int hi = s_cptr[c + 1];
-            const uint32_t quad = (uint32_t)quad0;
             // two spins per iteration: loads and Philox of both before either store
             for (int p1 = lo + tid; p1 < hi; p1 += 2 * B) {
                 const bool has2 = p1 + B < hi;
                 const int p2 = has2 ? p1 + B : p1;
                 const uint32_t meta1 = __ldg(P->meta + p1), meta2 = __ldg(P->meta + p2);
                 const uint32_t i1 = (uint32_t)__ldg(P->idx_of_pos + p1), i2 = (uint32_t)__ldg(P->idx_of_pos + p2);
-                const uint4 u1 = philox_keys(make_uint4(i1, y, quad, job.start), K);
-                const uint4 u2 = philox_keys(make_uint4(i2, y, quad, job.start), K);
+                const uint4 u1 = philox_quad(i1, zs, L1k, HA, LA, K);
+                const uint4 u2 = philox_quad(i2, zs, L1k, HA, LA, K);
                 const uint32_t own1 = sw[p1], own2 = sw[p2];
                 const uint32_t f1 = flip_item<MAXD>(sw, off, n, p1, own1, meta1, bias, u1, th);
                 const uint32_t f2 = flip_item<MAXD>(sw, off, n, p2, own2, meta2, bias, u2, th);
