@@ -303,11 +303,14 @@ typedef struct spvar_params {
                                  streaming +-1 kernel (|J| = 1, dmax <= 254) */
 #define SPVAR_SWEEP_PM1S 3    /* streaming +-1 kernel (shared-memory neighbour offsets, 4 replicas per CTA) */
 #define SPVAR_SWEEP_PM1W 4    /* warp-per-quad +-1 kernel: replicas_per_block / 4 warps, one quad each */
+#define SPVAR_SWEEP_PM1Q 5    /* quad-group +-1 kernel (|J| = 1, degree <= 8, dmax <= 30): work items of
+                                 replicas_per_block / 4 quads of the largest problem (more quads of smaller
+                                 ones, at most 64), spin words alone in shared memory */
 /* With the SQA sampler (replicas_per_block = 4): AUTO and PM1 take the register
  * form for +-1 couplers when it applies (two or more slices, at most 4 colour
  * classes, none larger than sweep_block; blocks 256/512/1024), else the item
  * walk (blocks 128/256/512); PM1S the item walk; GENERAL the general path; PM1W
- * is rejected (SPVAR_ELIMIT). */
+ * and PM1Q are rejected (SPVAR_ELIMIT). */
 
 #define SPVAR_FORM_BATCHED 0 /* every start of every problem in one persistent launch per phase */
 #define SPVAR_FORM_PLAIN 1   /* one start at a time, one launch per kernel and start */
@@ -441,7 +444,7 @@ int spvar_plan_post_time(const spvar_plan *plan, double *total_ms);
  * warp-per-quad +-1 kernel, 5: simulated quantum annealing kernel walking
  * (spin, slice) items, 6: simulated quantum annealing kernel in register form:
  * each thread keeps one spin of every colour class in registers and sweeps a
- * fixed set of its slices), persistent grid size. */
+ * fixed set of its slices, 7: quad-group +-1 kernel), persistent grid size. */
 int spvar_plan_shape(const spvar_plan *plan, int32_t *block, int32_t *replicas_per_block,
                      int32_t *staged, int32_t *grid);
 

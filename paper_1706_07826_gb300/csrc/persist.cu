@@ -309,14 +309,20 @@ __global__ void __launch_bounds__(256) k_slots_init(Slot *slots, SolveConsts C)
 }
 
 // Quads per work item of a start whose current problem is P and who runs
-// nquads quads: C.Q, or for the register kernel the most that its slots hold
+// nquads quads: C.Q; for the quad-group kernel the most that the launch's
+// shared memory holds; for the register kernel the most that its slots hold
 // (every colour class fills ceil(size * q / block) whole slots; at most
 // block * nslot / 4 quads so that the per-item energy sums fit), but no more
 // than leaves about two items per CTA of the launch (starts of similar size).
 __device__ __forceinline__ int item_quads(const DevProb *P, const SolveConsts &C, int nquads)
 {
-    if (C.fit_block <= 0) return C.Q;
     const int cap = max(1, (int)(((long long)nquads * C.nslots) / (2ll * max(C.grid, 1))));
+    if (C.fit_words > 0) {
+        // quad-group kernel: as many quads as the launch's spin words hold, at most 64
+        const int fit = C.fit_words / (2 * (P->n + 1));
+        return max(1, min(min(fit, 64), cap));
+    }
+    if (C.fit_block <= 0) return C.Q;
     const int ncol = P->ncol;
     auto need = [&](int q) {
         int s = 0;

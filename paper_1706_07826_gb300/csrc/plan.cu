@@ -38,6 +38,7 @@ cudaError_t engine_phase(const PhaseEngine &E, Slot *slots, int nslots, int T, i
     C.Q = E.shape.Q;
     C.fit_block = E.shape.kind == 1 ? E.shape.block : 0;
     C.fit_nslot = E.shape.kind == 1 ? E.shape.nslot : 0;
+    C.fit_words = E.shape.kind == 6 ? 2 * E.shape.Q * (E.max_n0 + 1) : 0;
     C.grid = grid;
     cudaError_t e = launch_plan(slots, C, E.jobs, E.items, E.ctr + 0, E.ctr + 1, st);
     if (e != cudaSuccess) return e;
@@ -309,6 +310,17 @@ std::vector<SweepShape> candidate_shapes(const spvar_plan *pl, int optin)
                     out.push_back(sh);
             }
     }
+    if (pm1r_kernel_eligible(pl->pm1, pl->dmax, pl->max_deg)) {
+        // quad-group kernel: Q quads of the largest problem per item (more for smaller ones)
+        const int md = pl->max_deg <= 6 ? 6 : 8;
+        for (int b : {128, 256, 512})
+            for (int Q : {1, 2, 4, 8}) {
+                SweepShape sh{6, b, Q, 0, 0, md};
+                if (pm1q_shape_ok(b, md, pl->max_n0, Q) &&
+                    sweep_shape_smem(sh, pl->max_n0, pl->thr_stride, pl->max_deg) <= (size_t)optin)
+                    out.push_back(sh);
+            }
+    }
     const int blocks[3] = {128, 256, 512};
     const int qs[4] = {1, 2, 4, 8};
     const int quads = ceil_div(pl->C.S_fix, 4);
@@ -462,7 +474,7 @@ int spvar_plan_create(const spvar_problem *const *problems, int32_t nproblems,
         !(p.elite_threshold > 0.0) || !(p.elite_threshold <= 1.0) || !(p.beta0 > 0.0) || !(p.beta1 > 0.0) ||
         p.canon < -1 || p.canon > 1 || (p.form != SPVAR_FORM_BATCHED && p.form != SPVAR_FORM_PLAIN) ||
         p.replicas_per_block < 0 || (p.replicas_per_block % 4) != 0 || p.sweep_kernel < 0 ||
-        p.sweep_kernel > 4 || p.start_offset < 0 || p.component_boost < 0 || p.component_boost > 1 || p.tree_preprocess < 0 || p.tree_preprocess > 1 || (p.sweep_block != 0 && p.sweep_block != 128 && p.sweep_block != 256 &&
+        p.sweep_kernel > 5 || p.start_offset < 0 || p.component_boost < 0 || p.component_boost > 1 || p.tree_preprocess < 0 || p.tree_preprocess > 1 || (p.sweep_block != 0 && p.sweep_block != 128 && p.sweep_block != 256 &&
                                p.sweep_block != 512 && p.sweep_block != 1024) ||
         check_corr_params(p) != SPVAR_OK || check_sampler_params(p) != SPVAR_OK)
         return SPVAR_EINVAL;
@@ -682,7 +694,7 @@ int spvar_plan_create(const spvar_problem *const *problems, int32_t nproblems,
             // walk or the general path is asked for
             if (p.sweep_kernel == SPVAR_SWEEP_GENERAL) sh = sqa_shape(pl, blk, optin, 0);
             else if (p.sweep_kernel == SPVAR_SWEEP_PM1S) sh = sqa_shape(pl, blk, optin, 1);
-            else if (p.sweep_kernel == SPVAR_SWEEP_PM1W) sh.kind = -1;
+            else if (p.sweep_kernel == SPVAR_SWEEP_PM1W || p.sweep_kernel == SPVAR_SWEEP_PM1Q) sh.kind = -1;
             else if (!pl->pm1) sh = sqa_shape(pl, blk, optin, 0);
             else {
                 sh = sqa_shape(pl, blk, optin, 2);
@@ -703,6 +715,13 @@ int spvar_plan_create(const spvar_problem *const *problems, int32_t nproblems,
                 sh = cu;
             else if (elig && pm1s_shape_ok(blk, md, pl->max_n0, Q)) sh = SweepShape{2, blk, Q, 0, 0, md};
             else { plan_free(pl); return SPVAR_ELIMIT; }
+        } else if (p.sweep_kernel == SPVAR_SWEEP_PM1Q) {
+            const int md = pl->max_deg <= 6 ? 6 : 8;
+            if (!pm1r_kernel_eligible(pl->pm1, pl->dmax, pl->max_deg) || !pm1q_shape_ok(blk, md, pl->max_n0, Q)) {
+                plan_free(pl);
+                return SPVAR_ELIMIT;
+            }
+            sh = SweepShape{6, blk, Q, 0, 0, md};
         } else if (p.sweep_kernel == SPVAR_SWEEP_PM1W) {
             const int md = pl->max_deg <= 6 ? 6 : 8;
             if (!elig || !pm1w_shape_ok(Q, md, pl->max_n0, 4)) { plan_free(pl); return SPVAR_ELIMIT; }
@@ -860,7 +879,8 @@ int spvar_plan_shape(const spvar_plan *plan, int32_t *block, int32_t *replicas_p
     if (replicas_per_block) *replicas_per_block = 4 * plan->shape.Q;
     if (staged) {
         const int k = plan->shape.kind;
-        *staged = k == 1 ? 2 : k == 2 ? 3 : k == 4 ? 4 : k == 5 ? (plan->shape.stage == 2 ? 6 : 5) : plan->shape.stage;
+        *staged = k == 1 ? 2 : k == 2 ? 3 : k == 4 ? 4 : k == 5 ? (plan->shape.stage == 2 ? 6 : 5) : k == 6 ? 7
+                                                                                                 : plan->shape.stage;
     }
     if (grid) *grid = plan->sweep_grid;
     return SPVAR_OK;

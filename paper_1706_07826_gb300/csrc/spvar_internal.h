@@ -150,7 +150,8 @@ struct SolveConsts {
     int32_t S_corr, k_corr, corr_num, corr_den;  // correlation phase (S_corr = 0: off)
     // register kernel: work items take as many quads as the slots hold (block
     // threads x nslot items per thread, colour classes in whole slots); 0: Q quads
-    int32_t fit_block, fit_nslot, grid, pad3;  // grid: CTAs of the sweep launch
+    int32_t fit_block, fit_nslot, grid;  // grid: CTAs of the sweep launch
+    int32_t fit_words;                   // quad-group kernel: spin words of the launch's shared memory
 };
 // Samples and elite size of a slot's current phase.
 __host__ __device__ inline int phase_samples(const SolveConsts &C, int mode)
@@ -278,6 +279,13 @@ inline int sqa_reg_ncls(int ncol, int max_class, int block, int P)
     return ncol <= 2 ? 2 : 4;
 }
 
+// Quad-group +-1 sweep (sweep_pm1q.cu): up to 64 quads of one problem per work
+// item, spin words only in shared memory (2 (n + 1) words per quad).
+bool pm1q_shape_ok(int block, int maxd, int max_n, int Q);
+size_t pm1q_smem_bytes(int max_n, int Q);
+cudaError_t launch_sweep_pm1q(const SweepLaunch &L, int block, int maxd, int grid, size_t smem, cudaStream_t st);
+int pm1q_max_active_blocks(int block, int maxd, size_t smem);
+
 // Streaming +-1 sweep (sweep_pm1s.cu): one quad per work item.
 bool pm1s_shape_ok(int block, int maxd, int max_n, int Q);
 size_t pm1s_smem_bytes(int max_n, int Q, int maxd);
@@ -332,6 +340,7 @@ inline size_t sweep_shape_smem(const SweepShape &s, int max_n, int thr_stride, i
     if (s.kind == 1) return pm1_smem_bytes(s.stage != 0, thr_stride);
     if (s.kind == 2) return pm1s_smem_bytes(max_n, s.Q, s.maxd);
     if (s.kind == 4) return pm1w_smem_bytes(max_n, s.Q, s.maxd);
+    if (s.kind == 6) return pm1q_smem_bytes(max_n, s.Q);
     return sweep_smem_bytes(max_n, s.Q, thr_stride, max_deg, s.stage != 0);
 }
 inline cudaError_t launch_sweep_shape(const SweepLaunch &L, const SweepShape &s, bool pm1, int grid, size_t smem,
@@ -341,6 +350,7 @@ inline cudaError_t launch_sweep_shape(const SweepLaunch &L, const SweepShape &s,
     if (s.kind == 1) return launch_sweep_pm1(L, s.block, s.nslot, s.maxd, s.stage != 0, grid, smem, st);
     if (s.kind == 2) return launch_sweep_pm1s(L, s.block, s.maxd, grid, smem, st);
     if (s.kind == 4) return launch_sweep_pm1w(L, s.Q, s.maxd, s.nslot ? s.nslot : 2, grid, smem, st);
+    if (s.kind == 6) return launch_sweep_pm1q(L, s.block, s.maxd, grid, smem, st);
     return launch_sweep(L, pm1, s.block, grid, smem, st);
 }
 inline int sweep_shape_occupancy(const SweepShape &s, bool pm1, size_t smem)
@@ -349,6 +359,7 @@ inline int sweep_shape_occupancy(const SweepShape &s, bool pm1, size_t smem)
     if (s.kind == 1) return pm1_max_active_blocks(s.block, s.nslot, s.maxd, s.stage != 0, smem);
     if (s.kind == 2) return pm1s_max_active_blocks(s.block, s.maxd, smem);
     if (s.kind == 4) return pm1w_max_active_blocks(s.Q, s.maxd, s.nslot ? s.nslot : 2, smem);
+    if (s.kind == 6) return pm1q_max_active_blocks(s.block, s.maxd, smem);
     return sweep_max_active_blocks(pm1, s.block, smem, s.stage != 0);
 }
 

@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(HERE, "libspvar.so")
 
 OK, EINVAL, EOVERFLOW, ENOMEM, EBUDGET, ETIMEOUT, ECUDA, ELIMIT = 0, -1, -2, -3, -4, -5, -6, -7
 FORM_BATCHED, FORM_PLAIN = 0, 1
-SWEEP_AUTO, SWEEP_GENERAL, SWEEP_PM1, SWEEP_PM1S, SWEEP_PM1W = 0, 1, 2, 3, 4
+SWEEP_AUTO, SWEEP_GENERAL, SWEEP_PM1, SWEEP_PM1S, SWEEP_PM1W, SWEEP_PM1Q = 0, 1, 2, 3, 4, 5
 SAMPLER_SA, SAMPLER_SQA = 0, 1
 MAX_N, MAX_DEGREE, MAX_SWEEPS, MAX_PHASE, MAX_SAMPLES = 32768, 32, 1048574, 4095, 16384
 NOALLOC_MAX_N = 16384
@@ -461,7 +461,7 @@ class Plan:
         _check(lib().spvar_plan_shape(self.handle, ctypes.byref(b), ctypes.byref(r), ctypes.byref(s), ctypes.byref(g)),
                "spvar_plan_shape")
         return dict(block=b.value, replicas_per_block=r.value, kernel=("general", "general-staged", "pm1-register", "pm1-streaming", "pm1-warp",
-                                                                 "sqa", "sqa-register")[s.value],
+                                                                 "sqa", "sqa-register", "pm1-quads")[s.value],
                     grid=g.value)
 
     def close(self):

@@ -57,15 +57,16 @@ def test_solve_parity(cuda_lib, form, name, make, T, starts, Sf, Ss, elite, iter
 
 
 SHAPES = [(4, 1, 256), (8, 1, 128), (32, 1, 512), (4, 2, 256), (8, 2, 128), (4, 2, 512), (16, 2, 256),
-          (12, 2, 128), (4, 3, 256), (4, 3, 512), (4, 3, 1024), (8, 4, 0), (16, 4, 0), (32, 4, 0), (64, 4, 0)]
+          (12, 2, 128), (4, 3, 256), (4, 3, 512), (4, 3, 1024), (8, 4, 0), (16, 4, 0), (32, 4, 0), (64, 4, 0),
+          (4, 5, 128), (8, 5, 256), (32, 5, 512), (16, 5, 128)]
 
 
 @pytest.mark.parametrize("rpb,kernel,block", SHAPES, ids=["%d-%d-%d" % s for s in SHAPES])
 @pytest.mark.parametrize("make", [lambda: I.chimera(3, 9), lambda: I.cubic3d(5, 19)], ids=["chimera", "cubic_odd"])
 def test_solve_identical_for_every_sweep_shape(cuda_lib, rpb, kernel, block, make):
-    """General, register-resident, streaming and warp-per-quad kernels, several
-    replicas per CTA and block sizes (2 to 4 register slots per thread): all
-    identical."""
+    """General, register-resident, streaming, warp-per-quad and quad-group
+    kernels, several replicas per CTA and block sizes (2 to 4 register slots
+    per thread): all identical."""
     from paper_1706_07826_gb300 import spvar
     inst = make()
     T, seed = 50, 17
@@ -74,11 +75,36 @@ def test_solve_identical_for_every_sweep_shape(cuda_lib, rpb, kernel, block, mak
     prm = spvar.make_params(num_starts=2, fixing_sample_size=45, solving_sample_size=45, num_sweeps=T,
                             elite_threshold=0.2, replicas_per_block=rpb, sweep_kernel=kernel, sweep_block=block)
     plan = spvar.Plan([gpu_problem(inst)], prm)
-    want = {2: "pm1-register", 3: "pm1-streaming", 4: "pm1-warp"}.get(kernel, plan.shape()["kernel"])
+    want = {2: "pm1-register", 3: "pm1-streaming", 4: "pm1-warp", 5: "pm1-quads"}.get(kernel,
+                                                                                     plan.shape()["kernel"])
     if kernel == 2 and block == 512 and inst.n == 125:
         want = "pm1-streaming"  # four colour classes need four slots; 512-thread CTAs have two
     assert plan.shape()["kernel"] == want
     _check(plan.run(seed, device=False), ref, 2, 2, inst.n)
+
+
+def test_quad_group_kernel_uneven_problems(cuda_lib):
+    """The quad-group kernel with problems of four sizes in one plan: its shared
+    memory holds two quads of the largest, so smaller problems run more quads
+    per work item (up to 15 here); all identical to the oracle."""
+    from paper_1706_07826_gb300 import spvar
+    insts = [I.cubic3d(L, 1500 + L) for L in (3, 6, 5, 4)]
+    T, starts, Sf, Ss = 40, 2, 120, 60
+    dmax = max(O.dmax(oracle_problem(i)) for i in insts)
+    seeds = [21, 22, 23, 24]
+    plan = spvar.Plan([gpu_problem(i) for i in insts],
+                      spvar.make_params(num_starts=starts, fixing_sample_size=Sf, solving_sample_size=Ss,
+                                        num_sweeps=T, elite_threshold=0.1, replicas_per_block=8,
+                                        sweep_kernel=spvar.SWEEP_PM1Q, sweep_block=128))
+    assert plan.shape()["kernel"] == "pm1-quads"
+    out = plan.run(seeds, device=False)
+    plan.close()
+    fm0 = 0
+    for pi, inst in enumerate(insts):
+        ref = O.solve(oracle_problem(inst), table(inst, T, dmax=dmax), seeds[pi], num_starts=starts,
+                      fixing_sample_size=Sf, solving_sample_size=Ss, elite_threshold=0.1)
+        _check(out, ref, starts, 2, inst.n, slot0=pi * starts, fm0=fm0)
+        fm0 += starts * inst.n
 
 
 def test_register_kernel_rejects_general_couplers(cuda_lib):
