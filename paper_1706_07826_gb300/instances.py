@@ -112,6 +112,28 @@ def weak_strong(M, seed, h_strong=-100, h_weak=44, j_intra=-100, j_inter=100, sc
     return Instance(name or "weak_strong_C%d_s%d" % (M, seed), n, ei, ej, J, h, scale=scale)
 
 
+def chimera_u10(M, seed, name=None):
+    """Reduced-degeneracy Chimera C_M problem (the U_10 class of Sec. III.C):
+    couplers uniform in {-10, ..., 10} without 0, biases uniform in {-10, ..., 10},
+    stored with scale 10 (so that |J| <= 1 in problem units)."""
+    g = _rng(seed)
+    ei, ej, _ = chimera_edges(M)
+    J = (g.integers(1, 11, size=len(ei)) * (g.integers(0, 2, size=len(ei)) * 2 - 1)).astype(np.int32)
+    h = g.integers(-10, 11, size=8 * M * M).astype(np.int32)
+    return Instance(name or "chimera_u10_C%d_s%d" % (M, seed), 8 * M * M, ei, ej, J, h, scale=10)
+
+
+def weak_strong_pair(h_strong=-100, h_weak=44, j=-100, scale=100):
+    """The two-cluster weak-strong toy (Sec. III.B): two Chimera unit cells,
+    ferromagnetic inside and between them (the four inter-cell couplers), the
+    first cell strong, the second weak, stored x scale."""
+    ei, ej, kind = chimera_edges(2)
+    keep = (ei < 16) & (ej < 16)
+    ei, ej = ei[keep].astype(np.int32), ej[keep].astype(np.int32)
+    h = np.array([h_strong] * 8 + [h_weak] * 8, np.int32)
+    return Instance("weak_strong_pair", 16, ei, ej, np.full(len(ei), j, np.int32), h, scale=scale)
+
+
 def random_graph(n, m, seed, jmax=3, hmax=2, name=None):
     """Small random sparse problem: m distinct pairs, J in [-jmax, jmax] \\ {0},
     h uniform in [-hmax, hmax].  Used for brute-force checks (n <= 20)."""
