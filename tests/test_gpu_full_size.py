@@ -10,7 +10,9 @@ replicas one by one, or a whole start where that takes seconds.
   start of an L = 6 problem and sampled phase-0 replicas of the largest and
   of odd-L (three-colour) problems;
 - SQA on Chimera C8 (N = 512), 16 slices, 10 starts x (500 + 500) runs, 1000
-  sweeps: sampled phase-0 runs (recorded energies).
+  sweeps: sampled phase-0 runs (recorded energies);
+- reduced-degeneracy Chimera C8 with biases (U_10, Sec. III.C) on the
+  general-coupler kernel: one whole start and sampled replicas.
 """
 import numpy as np
 import pytest
@@ -92,3 +94,30 @@ def test_sqa_chimera_c8_full_size(cuda_lib):
     for st, r in ((0, 0), (4, 311), (9, 499)):
         _, e, _ = O.sqa_sample(op, ent, P, 1, seed, start=st, phase=0, r0=r)
         assert out.energies[st, 0, r] == e[0] + inst.offset, (st, r)
+
+
+def test_u10_chimera_c8_general_couplers(cuda_lib):
+    """Reduced-degeneracy Chimera C8 with biases (the U_10 class of Sec. III.C:
+    couplers of ten magnitudes, so the general-coupler kernel): an autotuned
+    plan of 4 starts x (100 + 100) samples at 1000 sweeps equals the oracle on
+    one whole start; sampled phase-0 replicas of the others match one by one."""
+    from paper_1706_07826_gb300 import spvar
+    inst = I.chimera_u10(8, 2500)
+    T, seed, starts = 1000, 8, 4
+    kw = dict(fixing_sample_size=100, solving_sample_size=100, elite_threshold=0.1)
+    plan = spvar.Plan([gpu_problem(inst)], spvar.make_params(num_starts=starts, num_sweeps=T, **kw))
+    assert plan.shape()["kernel"] in ("general", "general-staged")
+    out = plan.run(seed, device=False)
+    plan.close()
+    op = oracle_problem(inst)
+    thr = table(inst, T)
+    st = 2
+    ref = O.solve(op, thr, seed, num_starts=1, start0=st, **kw)
+    for ph in range(ref.nphases[0]):
+        c = ref.counts[0, ph]
+        assert np.array_equal(np.asarray(out.energies[st, ph, :c]), ref.energies[0, ph, :c]), ph
+    n = inst.n
+    assert np.array_equal(np.asarray(out.best_state[st * n:(st + 1) * n]), ref.best_state[0])
+    for s, r in ((0, 0), (1, 57), (3, 99)):
+        _, e, _ = O.sample(op, thr, 1, seed, start=s, phase=0, r0=r)
+        assert out.energies[s, 0, r] == e[0] + inst.offset, (s, r)
