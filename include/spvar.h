@@ -299,8 +299,8 @@ typedef struct spvar_params {
 #define SPVAR_SWEEP_AUTO 0    /* register kernel when eligible, else general */
 #define SPVAR_SWEEP_GENERAL 1 /* general integer-coupler kernel */
 #define SPVAR_SWEEP_PM1 2     /* register-resident kernel (degree <= 8; |J| = 1 and dmax <= 30 in byte lanes, or
-                                 one coupler magnitude per spin and dmax <= 4094 in 16-bit lanes), else the
-                                 streaming +-1 kernel (|J| = 1, dmax <= 254) */
+                                 one coupler magnitude per spin, or every |J| <= 15, with dmax <= 4094 in
+                                 16-bit lanes), else the streaming +-1 kernel (|J| = 1, dmax <= 254) */
 #define SPVAR_SWEEP_PM1S 3    /* streaming +-1 kernel (shared-memory neighbour offsets, 4 replicas per CTA) */
 #define SPVAR_SWEEP_PM1W 4    /* warp-per-quad +-1 kernel: replicas_per_block / 4 warps, one quad each */
 #define SPVAR_SWEEP_PM1Q 5    /* quad-group +-1 kernel (|J| = 1, degree <= 8, dmax <= 30): work items of

@@ -336,6 +336,7 @@ int spvar_problem_create(int32_t n, const int32_t *row_ptr, const int32_t *col, 
     P->dev = static_cast<DevProb *>(P->blob);
     for (int c = 0; c < kMaxColours; ++c)
         P->csize[c] = c < hp.hdr.ncol ? hp.cptr[c + 1] - hp.cptr[c] : 0;
+    for (size_t k = 0; k < hp.val.size(); ++k) P->jabs_max = std::max(P->jabs_max, std::abs(hp.val[k]));
     *out = reinterpret_cast<spvar_problem *>(P);
     return SPVAR_OK;
 }
@@ -438,20 +439,25 @@ int spvar_sample_range(const spvar_problem *p, int32_t sweep_begin, int32_t swee
         if (pm1r_kernel_eligible(H.pm1 != 0, H.dmax, H.maxdeg))
             for (int blk : {256, 512, 128}) {
                 const int ns = pm1_nslot(P, Q, blk);
-                if (ns > 0 && pm1_shape_ok(blk, ns, md, false)) { sh = SweepShape{1, blk, Q, 0, ns, md}; break; }
+                if (ns > 0 && pm1_shape_ok(blk, ns, md, 0)) { sh = SweepShape{1, blk, Q, 0, ns, md}; break; }
             }
         // large problems: the streaming kernel (one quad per CTA)
         if (sh.kind == 0 && pm1s_shape_ok(512, md, H.n, 1) &&
             pm1s_smem_bytes(H.n, 1, md) <= (size_t)optin)
             sh = SweepShape{2, 512, 1, 0, 0, md};
     }
-    if (sh.kind == 0 && ujr_kernel_eligible(H.ujs != 0, H.dmax, H.maxdeg)) {
-        // one coupler magnitude per spin: the register kernel's 16-bit-lane variant
+    const int mode16 = ujr_kernel_eligible(H.ujs != 0, H.dmax, H.maxdeg)          ? 1
+                       : sir_kernel_eligible(P->jabs_max, H.dmax, H.maxdeg) ? 2
+                                                                             : 0;
+    if (sh.kind == 0 && mode16 != 0) {
+        // one coupler magnitude per spin, or small integer couplers: the register
+        // kernel's 16-bit-lane variants
         const int md = H.maxdeg <= 6 ? 6 : 8;
         for (int blk : {256, 512, 1024}) {
-            const int ns = pm1_nslot(P, Q, blk);
-            const SweepShape c{1, blk, Q, 1, ns, md};
-            if (ns > 0 && pm1_shape_ok(blk, ns, md, true) &&
+            int ns = pm1_nslot(P, Q, blk);
+            if (ns == 3) ns = 4;
+            const SweepShape c{1, blk, Q, mode16, ns, md};
+            if (ns > 0 && pm1_shape_ok(blk, ns, md, mode16) &&
                 sweep_shape_smem(c, H.n, thr_stride, H.maxdeg) <= (size_t)optin) {
                 sh = c;
                 break;
@@ -643,6 +649,7 @@ int spvar_reduce(const spvar_problem *p, const int8_t *fixed, int32_t *old_of_ne
         return SPVAR_ECUDA;
     }
     D->hdr = back;
+    D->jabs_max = S->jabs_max;  // the reduced couplers are a subset
     for (int c = 0; c < kMaxColours; ++c) D->csize[c] = c < back.ncol ? cptr[c + 1] - cptr[c] : 0;
     *out = reinterpret_cast<spvar_problem *>(D);
     return SPVAR_OK;

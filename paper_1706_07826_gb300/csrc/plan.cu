@@ -81,6 +81,7 @@ struct spvar_plan {
     SolveConsts C{};
     int T = 0, thr_stride = 1, max_n0 = 0, max_deg = 1, iters_max = 1;
     int ncol_max = 0, class_max = 0;  // most colour classes and largest class of any problem
+    int jabs_max = 0;                 // largest coupler magnitude of any problem
     bool pm1 = true;
     bool ujs = true;      // every problem has one coupler magnitude per spin
     uint64_t sig = 0;     // structure signature of the problems (autotune cache key)
@@ -346,21 +347,26 @@ std::vector<SweepShape> candidate_shapes(const spvar_plan *pl, int optin)
                 const int ns = plan_nslot(pl, Q, blocks[bi]);
                 const int md = pl->max_deg <= 6 ? 6 : 8;
                 SweepShape sh{1, blocks[bi], Q, 0, ns, md};
-                if (ns > 0 && pm1_shape_ok(blocks[bi], ns, md, false) &&
+                if (ns > 0 && pm1_shape_ok(blocks[bi], ns, md, 0) &&
                     sweep_shape_smem(sh, pl->max_n0, pl->thr_stride, pl->max_deg) <= (size_t)optin)
                     out.push_back(sh);
             }
         }
-    if (!pm1r_kernel_eligible(pl->pm1, pl->dmax, pl->max_deg) && ujr_kernel_eligible(pl->ujs, pl->dmax, pl->max_deg)) {
-        // one coupler magnitude per spin: the register kernel's 16-bit-lane variant
+    const int mode16 = pm1r_kernel_eligible(pl->pm1, pl->dmax, pl->max_deg)          ? 0
+                       : ujr_kernel_eligible(pl->ujs, pl->dmax, pl->max_deg)       ? 1
+                       : sir_kernel_eligible(pl->jabs_max, pl->dmax, pl->max_deg) ? 2
+                                                                                   : 0;
+    if (mode16 != 0) {
+        // one coupler magnitude per spin, or small integer couplers: the register
+        // kernel's 16-bit-lane variants
         const int md = pl->max_deg <= 6 ? 6 : 8;
         for (int blk : {256, 512, 1024})
             for (int Q : {1, 2, 4}) {
                 if (Q > 1 && quads < Q) continue;
                 int ns = plan_nslot(pl, Q, blk);
                 if (ns == 3) ns = 4;
-                SweepShape sh{1, blk, Q, 1, ns, md};
-                if (ns > 0 && pm1_shape_ok(blk, ns, md, true) &&
+                SweepShape sh{1, blk, Q, mode16, ns, md};
+                if (ns > 0 && pm1_shape_ok(blk, ns, md, mode16) &&
                     sweep_shape_smem(sh, pl->max_n0, pl->thr_stride, pl->max_deg) <= (size_t)optin)
                     out.push_back(sh);
             }
@@ -503,11 +509,13 @@ int spvar_plan_create(const spvar_problem *const *problems, int32_t nproblems,
         for (int c = 0; c < P->hdr.ncol && c < kMaxColours; ++c) pl->class_max = std::max(pl->class_max, P->csize[c]);
         if (!P->hdr.pm1) pl->pm1 = false;
         if (!P->hdr.ujs) pl->ujs = false;
+        pl->jabs_max = std::max(pl->jabs_max, P->jabs_max);
         // colour classes, coupler kind and dmax decide which shapes are valid
         auto mix = [&](uint64_t v) { pl->sig = (pl->sig ^ v) * 1099511628211ull; };
         mix((uint64_t)P->hdr.ncol);
         for (int c = 0; c < P->hdr.ncol; ++c) mix((uint64_t)P->csize[c]);
         mix((uint64_t)P->hdr.pm1 << 1 | (uint64_t)P->hdr.ujs);
+        mix((uint64_t)P->jabs_max);
         mix((uint64_t)P->hdr.dmax);
     }
     pl->T = p.num_sweeps;
@@ -706,11 +714,14 @@ int spvar_plan_create(const spvar_problem *const *problems, int32_t nproblems,
             // byte-lane register kernel, else (one coupler magnitude per spin) its
             // 16-bit-lane variant, else the streaming +-1 kernel
             const int ns = pm1r_kernel_eligible(pl->pm1, pl->dmax, pl->max_deg) ? plan_nslot(pl, Q, blk) : 0;
-            int nsu = ujr_kernel_eligible(pl->ujs, pl->dmax, pl->max_deg) ? plan_nslot(pl, Q, blk) : 0;
+            const int mu = ujr_kernel_eligible(pl->ujs, pl->dmax, pl->max_deg)          ? 1
+                           : sir_kernel_eligible(pl->jabs_max, pl->dmax, pl->max_deg) ? 2
+                                                                                       : 0;
+            int nsu = mu ? plan_nslot(pl, Q, blk) : 0;
             if (nsu == 3) nsu = 4;
-            const SweepShape cu{1, blk, Q, 1, nsu, md};
-            if (ns > 0 && pm1_shape_ok(blk, ns, md, false)) sh = SweepShape{1, blk, Q, 0, ns, md};
-            else if (nsu > 0 && pm1_shape_ok(blk, nsu, md, true) &&
+            const SweepShape cu{1, blk, Q, mu, nsu, md};
+            if (ns > 0 && pm1_shape_ok(blk, ns, md, 0)) sh = SweepShape{1, blk, Q, 0, ns, md};
+            else if (nsu > 0 && pm1_shape_ok(blk, nsu, md, mu) &&
                      sweep_shape_smem(cu, pl->max_n0, pl->thr_stride, pl->max_deg) <= (size_t)optin)
                 sh = cu;
             else if (elig && pm1s_shape_ok(blk, md, pl->max_n0, Q)) sh = SweepShape{2, blk, Q, 0, 0, md};

@@ -45,6 +45,7 @@ struct DevProb {
 struct Problem {
     DevProb hdr;        // host copy (pointers are device pointers)
     int32_t csize[kMaxColours];  // colour class sizes
+    int32_t jabs_max = 0;        // largest coupler magnitude
     DevProb *dev;       // device copy of the header (inside the blob)
     void *blob;
     size_t blob_bytes;
@@ -254,11 +255,14 @@ cudaError_t launch_sweep(const SweepLaunch &L, bool pm1, int block, int grid, si
 int sweep_max_active_blocks(bool pm1, int block, size_t smem, bool stage_ell);
 
 // Register-resident +-1 sweep (sweep_pm1.cu).
-bool pm1_shape_ok(int block, int nslot, int maxd, bool scaled);
+// mode 0: +-1 couplers in byte lanes; 1: one coupler magnitude per spin, 16-bit
+// lanes; 2: small integer couplers (|J| <= 15), weighted byte-wise neighbour
+// sum, 16-bit lanes.
+bool pm1_shape_ok(int block, int nslot, int maxd, int mode);
 size_t pm1_smem_bytes(bool scaled, int thr_stride);
-cudaError_t launch_sweep_pm1(const SweepLaunch &L, int block, int nslot, int maxd, bool scaled, int grid, size_t smem,
+cudaError_t launch_sweep_pm1(const SweepLaunch &L, int block, int nslot, int maxd, int mode, int grid, size_t smem,
                              cudaStream_t st);
-int pm1_max_active_blocks(int block, int nslot, int maxd, bool scaled, size_t smem);
+int pm1_max_active_blocks(int block, int nslot, int maxd, int mode, size_t smem);
 
 // Simulated quantum annealing sweep (sweep_sqa.cu): one quad per work item, all
 // Trotter slices in shared memory.
@@ -302,7 +306,8 @@ int pm1w_max_active_blocks(int warps, int maxd, int K, size_t smem);
 // Launch shape of a sweep: kind 0 = general kernel (stage: layout staged in
 // shared memory), kind 1 = register-resident kernel (nslot items per thread,
 // maxd neighbour registers per item; stage = 1: the 16-bit-lane variant for
-// one coupler magnitude per spin), kind 2 = streaming +-1 kernel
+// one coupler magnitude per spin, stage = 2: its variant for small integer
+// couplers), kind 2 = streaming +-1 kernel
 // (maxd neighbour offsets per spin staged in shared memory, Q = 1), kind 4 =
 // warp-per-quad +-1 kernel (Q = warps = block / 32; nslot = spins in flight per lane,
 // 2 or 4), kind 5 = simulated
@@ -323,6 +328,11 @@ inline bool pm1_kernel_eligible(bool pm1, int dmax, int maxdeg) { return pm1 && 
 inline bool pm1r_kernel_eligible(bool pm1, int dmax, int maxdeg) { return pm1 && dmax <= 30 && maxdeg <= 8; }
 // The register kernel's 16-bit-lane variant: one coupler magnitude per spin, dmax <= 4094.
 inline bool ujr_kernel_eligible(bool ujs, int dmax, int maxdeg) { return ujs && dmax <= 4094 && maxdeg <= 8; }
+// Its small-integer variant: every |J| <= 15 (four bits per neighbour), dmax <= 4094.
+inline bool sir_kernel_eligible(int jabs_max, int dmax, int maxdeg)
+{
+    return jabs_max >= 1 && jabs_max <= 15 && dmax <= 4094 && maxdeg <= 8;
+}
 // Slots per thread the register kernel needs for problem P at Q quads per CTA
 // (every colour class fills whole slots), rounded up to an instantiated count
 // (2..4); 0 if more than 4.  Reductions only shrink classes, so the original
@@ -347,7 +357,7 @@ inline cudaError_t launch_sweep_shape(const SweepLaunch &L, const SweepShape &s,
                                       cudaStream_t st)
 {
     if (s.kind == 5) return launch_sweep_sqa(L, s.stage, s.block, s.ncls, s.ent32 != 0, grid, smem, st);
-    if (s.kind == 1) return launch_sweep_pm1(L, s.block, s.nslot, s.maxd, s.stage != 0, grid, smem, st);
+    if (s.kind == 1) return launch_sweep_pm1(L, s.block, s.nslot, s.maxd, s.stage, grid, smem, st);
     if (s.kind == 2) return launch_sweep_pm1s(L, s.block, s.maxd, grid, smem, st);
     if (s.kind == 4) return launch_sweep_pm1w(L, s.Q, s.maxd, s.nslot ? s.nslot : 2, grid, smem, st);
     if (s.kind == 6) return launch_sweep_pm1q(L, s.block, s.maxd, grid, smem, st);
@@ -356,7 +366,7 @@ inline cudaError_t launch_sweep_shape(const SweepLaunch &L, const SweepShape &s,
 inline int sweep_shape_occupancy(const SweepShape &s, bool pm1, size_t smem)
 {
     if (s.kind == 5) return sqa_max_active_blocks(s.stage, s.block, s.maxd, s.ncls, s.ent32 != 0, smem);
-    if (s.kind == 1) return pm1_max_active_blocks(s.block, s.nslot, s.maxd, s.stage != 0, smem);
+    if (s.kind == 1) return pm1_max_active_blocks(s.block, s.nslot, s.maxd, s.stage, smem);
     if (s.kind == 2) return pm1s_max_active_blocks(s.block, s.maxd, smem);
     if (s.kind == 4) return pm1w_max_active_blocks(s.Q, s.maxd, s.nslot ? s.nslot : 2, smem);
     if (s.kind == 6) return pm1q_max_active_blocks(s.block, s.maxd, smem);

@@ -29,7 +29,11 @@
 // is the same, the local field is h + J0 (2x - deg), and the flip-cost index
 // 16 (dE/2 + bias) of two replicas at a time is formed in 16-bit lanes; the
 // two acceptance rows (2 dmax + 2 entries) are interleaved in dynamic shared
-// memory.  Needs dmax <= 4094.
+// memory.  Needs dmax <= 4094.  With SI (small integer couplers, every
+// |J| <= 15: the reduced-degeneracy problems of Sec. III.C) the byte-wise sum
+// is weighted, X = sum_j |J_ij| b'_j <= 120 per byte with the magnitudes packed
+// four bits per neighbour in one register, and the local field is
+// h + 2 X - sum_j |J_ij|.
 #include "sweep_common.cuh"
 
 namespace spvar {
@@ -44,7 +48,8 @@ struct SlotRegs {
     uint32_t own;       // byte offset of the item's spin word (plain copy)
     uint32_t nb[MAXD];  // byte offsets of the neighbours (inverted copy if J < 0, zero word if padding)
     uint32_t c0;        // per byte: 8 (bias - deg + h); SCALED: per 16-bit lane 16 (bias + h - J0 deg)
-    uint32_t tj;        // SCALED: 32 J0
+    uint32_t tj;        // SCALED: 32 J0 (SI: 32)
+    uint32_t jp;        // SI: |J| of neighbour d in bits 4d .. 4d + 3
     uint32_t A, L0k, D, H3k, L3;  // Philox rounds 1-3 folded with the item's fixed counter words
 };
 
@@ -150,7 +155,7 @@ struct Pm1Smem {
 // barmask) and closes the sweep.
 // ONEQ: every item of the CTA is of one quad (word A of every slot is A0), so
 // the round-2 product of word 0 is computed once per sweep, not per slot.
-template <int B, int NSLOT, int MAXD, bool SCALED, int PAR, bool ONEQ>
+template <int B, int NSLOT, int MAXD, bool SCALED, bool SI, int PAR, bool ONEQ>
 __device__ __forceinline__ void sweep_once(Pm1Smem<B, NSLOT> &sm, unsigned long long *drow,
                                            const SlotRegs<MAXD> (&s)[NSLOT], uint32_t y,
                                            const RoundKeys &K, uint32_t barmask, uint32_t one,
@@ -181,7 +186,7 @@ __device__ __forceinline__ void sweep_once(Pm1Smem<B, NSLOT> &sm, unsigned long 
             const uint4 u = ONEQ ? philox_slot_hl(s[j], hA, lA, K) : philox_slot(s[j], y, K);
             uint32_t x = 0;
 #pragma unroll
-            for (int d = 0; d < MAXD; ++d) x += nbw[d];
+            for (int d = 0; d < MAXD; ++d) x = SI ? mad_lo(nbw[d], (s[j].jp >> (4 * d)) & 15u, x) : x + nbw[d];
             // byte r of x: neighbours with b_j ^ [J_ij < 0] = 1
             uint32_t off[4];
             if (SCALED) {
@@ -228,29 +233,29 @@ __device__ __forceinline__ void sweep_once(Pm1Smem<B, NSLOT> &sm, unsigned long 
 }
 
 // Sweeps t0 .. T - 1, two per step (the rows alternate).
-template <int B, int NSLOT, int MAXD, bool SCALED, bool ONEQ>
+template <int B, int NSLOT, int MAXD, bool SCALED, bool SI, bool ONEQ>
 __device__ __forceinline__ void sweeps(Pm1Smem<B, NSLOT> &sm, unsigned long long *drow, const SlotRegs<MAXD> (&s)[NSLOT],
                                        int t0, int T, uint32_t phase_hi, const RoundKeys &K, uint32_t barmask,
                                        uint32_t one, uint32_t k16, const uint32_t *thr, size_t ts, int bias, uint32_t A0)
 {
     int t = t0;
     if (t < T && (t & 1)) {
-        sweep_once<B, NSLOT, MAXD, SCALED, 1, ONEQ>(sm, drow, s, phase_hi | (uint32_t)t, K, barmask, one, k16,
+        sweep_once<B, NSLOT, MAXD, SCALED, SI, 1, ONEQ>(sm, drow, s, phase_hi | (uint32_t)t, K, barmask, one, k16,
                                                     t + 1 < T ? thr + (size_t)(t + 1) * ts : nullptr, bias, A0);
         ++t;
     }
     for (; t + 1 < T; t += 2) {
-        sweep_once<B, NSLOT, MAXD, SCALED, 0, ONEQ>(sm, drow, s, phase_hi | (uint32_t)t, K, barmask, one, k16,
+        sweep_once<B, NSLOT, MAXD, SCALED, SI, 0, ONEQ>(sm, drow, s, phase_hi | (uint32_t)t, K, barmask, one, k16,
                                                     thr + (size_t)(t + 1) * ts, bias, A0);
-        sweep_once<B, NSLOT, MAXD, SCALED, 1, ONEQ>(sm, drow, s, phase_hi | (uint32_t)(t + 1), K, barmask, one,
+        sweep_once<B, NSLOT, MAXD, SCALED, SI, 1, ONEQ>(sm, drow, s, phase_hi | (uint32_t)(t + 1), K, barmask, one,
                                                     k16, t + 2 < T ? thr + (size_t)(t + 2) * ts : nullptr, bias, A0);
     }
     if (t < T)
-        sweep_once<B, NSLOT, MAXD, SCALED, 0, ONEQ>(sm, drow, s, phase_hi | (uint32_t)t, K, barmask, one, k16,
+        sweep_once<B, NSLOT, MAXD, SCALED, SI, 0, ONEQ>(sm, drow, s, phase_hi | (uint32_t)t, K, barmask, one, k16,
                                                     nullptr, bias, A0);
 }
 
-template <int B, int NSLOT, int MAXD, bool SCALED>
+template <int B, int NSLOT, int MAXD, bool SCALED, bool SI>
 __device__ void run_item_pm1(const SweepLaunch &L, const SweepJob &job, int quad0, int nq, Pm1Smem<B, NSLOT> &sm,
                              unsigned long long *drow)
 {
@@ -308,6 +313,7 @@ __device__ void run_item_pm1(const SweepLaunch &L, const SweepJob &job, int quad
         for (int d = 0; d < MAXD; ++d) s[j].nb[d] = zero;
         s[j].c0 = SCALED ? (uint32_t)(16 * bias) * 0x00010001u : (uint32_t)(8 * bias) * 0x01010101u;
         s[j].tj = 0u;
+        s[j].jp = 0u;
         s[j].A = s[j].L0k = s[j].D = s[j].H3k = s[j].L3 = 0u;
         // colour class of slot j
         int c = 0, jb = 0, items = 0;
@@ -335,7 +341,17 @@ __device__ void run_item_pm1(const SweepLaunch &L, const SweepJob &job, int quad
                         s[j].nb[d] = 4u * (uint32_t)(((e >> 31) ? KW : 0) + q * n + (int)(e & 0xFFFFu));
                     }
                 }
-                if (SCALED) {
+                if (SI) {
+                    // small integer couplers: magnitudes packed four bits per neighbour
+                    int sumj = 0;
+                    for (int d = 0; d < deg && d < MAXD; ++d) {
+                        const uint32_t a = (uint32_t)abs((int)P->ell[(size_t)d * cap_n + p] >> 16);
+                        s[j].jp |= a << (4 * d);
+                        sumj += (int)a;
+                    }
+                    s[j].c0 = (uint32_t)(16 * (bias + h - sumj)) * 0x00010001u;
+                    s[j].tj = 32u;
+                } else if (SCALED) {
                     // one coupler magnitude J0 per spin
                     const int J0 = deg > 0 ? abs((int)P->ell[p] >> 16) : 0;
                     s[j].c0 = (uint32_t)(16 * (bias + h - J0 * deg)) * 0x00010001u;
@@ -354,17 +370,17 @@ __device__ void run_item_pm1(const SweepLaunch &L, const SweepJob &job, int quad
     if (nq == 1) {
         uint32_t H1, L1;
         mulhilo(kM1, (uint32_t)quad0, H1, L1);
-        sweeps<B, NSLOT, MAXD, SCALED, true>(sm, drow, s, t0, T, phase_hi, K, barmask, one, k16, thr, ts, bias,
+        sweeps<B, NSLOT, MAXD, SCALED, SI, true>(sm, drow, s, t0, T, phase_hi, K, barmask, one, k16, thr, ts, bias,
                                              H1 ^ k0);
     } else {
-        sweeps<B, NSLOT, MAXD, SCALED, false>(sm, drow, s, t0, T, phase_hi, K, barmask, one, k16, thr, ts, bias,
+        sweeps<B, NSLOT, MAXD, SCALED, SI, false>(sm, drow, s, t0, T, phase_hi, K, barmask, one, k16, thr, ts, bias,
                                               0u);
     }
     // the inverted copy is dead now: its first 4 nq words hold the energy sums
     finish_item<!SCALED>(P, job, quad0, nq, sm.sw, reinterpret_cast<int *>(sm.sw + KW));  // general J for SCALED
 }
 
-template <int B, int NSLOT, int MAXD, bool SCALED>
+template <int B, int NSLOT, int MAXD, bool SCALED, bool SI>
 __global__ void __launch_bounds__(B) k_sweep_pm1(const SweepLaunch L)
 {
     __shared__ Pm1Smem<B, NSLOT> sm;
@@ -374,23 +390,25 @@ __global__ void __launch_bounds__(B) k_sweep_pm1(const SweepLaunch L)
         SweepJob job;
         int quad0, nq;
         if (!next_item(L, iter, &s_item, job, quad0, nq)) break;
-        run_item_pm1<B, NSLOT, MAXD, SCALED>(L, job, quad0, nq, sm, drow_pm1);
+        run_item_pm1<B, NSLOT, MAXD, SCALED, SI>(L, job, quad0, nq, sm, drow_pm1);
         __syncthreads();
     }
 }
 
-template <int B, int NSLOT, int MAXD, bool SCALED>
+template <int B, int NSLOT, int MAXD, bool SCALED, bool SI>
 void *kernel_ptr()
 {
-    return reinterpret_cast<void *>(k_sweep_pm1<B, NSLOT, MAXD, SCALED>);
+    return reinterpret_cast<void *>(k_sweep_pm1<B, NSLOT, MAXD, SCALED, SI>);
 }
 
-void *select_kernel(int block, int nslot, int maxd, bool scaled)
+void *select_kernel(int block, int nslot, int maxd, int mode)
 {
 #define SPVAR_PM1_CASE(BB, NS, MD) \
-    if (!scaled && block == BB && nslot == NS && maxd == MD) return kernel_ptr<BB, NS, MD, false>();
+    if (mode == 0 && block == BB && nslot == NS && maxd == MD) return kernel_ptr<BB, NS, MD, false, false>();
 #define SPVAR_UJ_CASE(BB, NS, MD) \
-    if (scaled && block == BB && nslot == NS && maxd == MD) return kernel_ptr<BB, NS, MD, true>();
+    if (mode == 1 && block == BB && nslot == NS && maxd == MD) return kernel_ptr<BB, NS, MD, true, false>();
+#define SPVAR_SI_CASE(BB, NS, MD) \
+    if (mode == 2 && block == BB && nslot == NS && maxd == MD) return kernel_ptr<BB, NS, MD, true, true>();
     SPVAR_PM1_CASE(128, 2, 6) SPVAR_PM1_CASE(128, 3, 6) SPVAR_PM1_CASE(128, 4, 6)
     SPVAR_PM1_CASE(256, 2, 6) SPVAR_PM1_CASE(256, 3, 6) SPVAR_PM1_CASE(256, 4, 6)
     SPVAR_PM1_CASE(512, 2, 6) SPVAR_PM1_CASE(1024, 2, 6)
@@ -399,22 +417,28 @@ void *select_kernel(int block, int nslot, int maxd, bool scaled)
     SPVAR_PM1_CASE(512, 2, 8) SPVAR_PM1_CASE(1024, 2, 8)
     SPVAR_UJ_CASE(256, 2, 6) SPVAR_UJ_CASE(256, 4, 6) SPVAR_UJ_CASE(512, 2, 6) SPVAR_UJ_CASE(1024, 2, 6)
     SPVAR_UJ_CASE(256, 2, 8) SPVAR_UJ_CASE(256, 4, 8) SPVAR_UJ_CASE(512, 2, 8) SPVAR_UJ_CASE(1024, 2, 8)
+    SPVAR_SI_CASE(128, 4, 6) SPVAR_SI_CASE(256, 2, 6) SPVAR_SI_CASE(256, 4, 6) SPVAR_SI_CASE(512, 2, 6)
+    SPVAR_SI_CASE(1024, 2, 6)
+    SPVAR_SI_CASE(128, 4, 8) SPVAR_SI_CASE(256, 2, 8) SPVAR_SI_CASE(256, 4, 8) SPVAR_SI_CASE(512, 2, 8)
+    SPVAR_SI_CASE(1024, 2, 8)
 #undef SPVAR_PM1_CASE
 #undef SPVAR_UJ_CASE
+#undef SPVAR_SI_CASE
     return nullptr;
 }
 
 }  // namespace
 
-bool pm1_shape_ok(int block, int nslot, int maxd, bool scaled) { return select_kernel(block, nslot, maxd, scaled) != nullptr; }
+bool pm1_shape_ok(int block, int nslot, int maxd, int mode) { return select_kernel(block, nslot, maxd, mode) != nullptr; }
 
 // SCALED: two interleaved rows of thr_stride (= dmax + 1 >= 2 bias + 1) 64-bit entries.
 size_t pm1_smem_bytes(bool scaled, int thr_stride) { return scaled ? 2 * 8 * (size_t)thr_stride : 0; }
 
-cudaError_t launch_sweep_pm1(const SweepLaunch &L, int block, int nslot, int maxd, bool scaled, int grid,
+cudaError_t launch_sweep_pm1(const SweepLaunch &L, int block, int nslot, int maxd, int mode, int grid,
                              size_t smem, cudaStream_t st)
 {
-    void *k = select_kernel(block, nslot, maxd, scaled);
+    const bool scaled = mode != 0;
+    void *k = select_kernel(block, nslot, maxd, mode);
     if (!k) return cudaErrorInvalidValue;
     if (scaled) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -424,9 +448,10 @@ cudaError_t launch_sweep_pm1(const SweepLaunch &L, int block, int nslot, int max
     return cudaLaunchKernel(k, dim3(grid), dim3(block), args, scaled ? smem : 0, st);
 }
 
-int pm1_max_active_blocks(int block, int nslot, int maxd, bool scaled, size_t smem)
+int pm1_max_active_blocks(int block, int nslot, int maxd, int mode, size_t smem)
 {
-    void *k = select_kernel(block, nslot, maxd, scaled);
+    const bool scaled = mode != 0;
+    void *k = select_kernel(block, nslot, maxd, mode);
     if (!k) return 0;
     if (scaled) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int nb = 0;

@@ -19,6 +19,8 @@ CASES = [
     ("pm1_with_h", lambda: with_h(I.cubic3d(3, 8), 4, 3), 9, 80),
     ("pm1_big_h", lambda: with_h(I.cubic3d(4, 9), 3, 20), 17, 80),
     ("weak_strong_C6", lambda: I.weak_strong(6, 1301), 41, 100),
+    ("u10_chimera_C4", lambda: I.chimera_u10(4, 1400), 37, 120),
+    ("u10_chimera_C8", lambda: I.chimera_u10(8, 1401), 64, 100),
     ("isolated", isolated_spins, 11, 40),
     ("single_spin", single_spin, 5, 20),
     ("empty", empty, 4, 10),

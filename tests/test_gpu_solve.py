@@ -120,12 +120,14 @@ UJ_SHAPES = [(4, 256), (8, 256), (16, 256), (4, 512), (4, 1024), (8, 1024)]
 
 
 @pytest.mark.parametrize("rpb,block", UJ_SHAPES, ids=["%d-%d" % s for s in UJ_SHAPES])
-@pytest.mark.parametrize("make", [lambda: I.weak_strong(2, 61), lambda: with_h(I.cubic3d(4, 62), 5, 20)],
-                         ids=["weak_strong_x100", "pm1_big_h"])
+@pytest.mark.parametrize("make", [lambda: I.weak_strong(2, 61), lambda: with_h(I.cubic3d(4, 62), 5, 20),
+                                  lambda: I.chimera_u10(3, 63), lambda: I.chimera_u10(4, 64)],
+                         ids=["weak_strong_x100", "pm1_big_h", "u10_C3", "u10_C4"])
 def test_register_kernel_one_magnitude_per_spin(cuda_lib, rpb, block, make):
-    """The register kernel's 16-bit-lane variant (one coupler magnitude per
-    spin: weak-strong problems, +-1 problems with large biases): identical to
-    the oracle for several launch shapes."""
+    """The register kernel's 16-bit-lane variants (one coupler magnitude per
+    spin: weak-strong problems, +-1 problems with large biases; small integer
+    couplers: U_10 Chimera problems): identical to the oracle for several
+    launch shapes."""
     from paper_1706_07826_gb300 import spvar
     inst = make()
     T, seed = 50, 19
