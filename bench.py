@@ -349,6 +349,54 @@ def _hbm_peak_gbs():
         return 6800.0, "fallback"
 
 
+def measure_u10(spvar, torch, flush):
+    """Reduced-degeneracy Chimera C8 with biases (the U_10 class of Sec. III.C:
+    couplers in {-10..10} without 0, biases in {-10..10}) with c2's parameters:
+    10 starts x (1000 + 1000) samples, 1000 sweeps, elite 0.1.  Also the mean
+    fraction of variables the fixing phase removes (the paper reports more
+    than 80 % on this class)."""
+    from paper_1706_07826_gb300 import instances as I
+    inst = I.chimera_u10(8, 2500)
+    prob = spvar.Problem.from_instance(inst)
+    prm = spvar.make_params(num_starts=10, fixing_sample_size=1000, solving_sample_size=1000, num_sweeps=1000,
+                            elite_threshold=0.1)
+    plan = spvar.Plan([prob], prm)
+    plan.run([2599], device=True)
+    torch.cuda.synchronize()
+    ms_tot, att_tot, fixed = 0.0, 0, []
+    for k in range(3):
+        flush.add_(1)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.nvtx.range_push("u10_c8")
+        a.record()
+        o = plan.run([2600 + k], device=True)
+        b.record()
+        torch.cuda.nvtx.range_pop()
+        torch.cuda.synchronize()
+        ms_tot += a.elapsed_time(b)
+        att, _ = plan.stats()
+        att_tot += att
+        fixed += [1.0 - x / inst.n for x in o.nfree[:, 1].cpu().tolist()]
+    plan.set_profiling(True)
+    torch.cuda.nvtx.range_push("u10_c8_profiled")
+    plan.run([2603], device=True)
+    torch.cuda.nvtx.range_pop()
+    sweep_ms, sweep_n = plan.sweep_time()
+    att_prof, _ = plan.stats()
+    shape = plan.shape()
+    plan.close()
+    ops = PHILOX_OPS_PER_ATTEMPT + 2 * inst.m / inst.n + ACCEPT_OPS_PER_ATTEMPT
+    achieved = att_prof * ops / (sweep_ms / 1000.0) / 1e12
+    return {"value": att_tot / (ms_tot / 1000.0), "unit": UNIT, "ms_per_step": ms_tot / 3, "sweep_shape": shape,
+            "fixed_fraction_mean": float(np.mean(fixed)),
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": ALU_PEAK_TOPS, "unit": "Tops/s",
+                         "frac": achieved / ALU_PEAK_TOPS, "ops_per_attempt": ops,
+                         "ms_per_launch": sweep_ms / max(sweep_n, 1)},
+            "config": "Chimera C8 U_10 couplers and biases (N=512, seed 2500), 10 starts x (1000 fixing + 1000 "
+                      "solving) samples, 1000 sweeps, beta 0.1->3.0 geometric (couplers /10), elite 0.1"}
+
+
 def measure_persistence_scaled(spvar, torch):
     """The persistence pass (elite, counts and fixing, fold and compact) at a
     scale where HBM matters: 64 3D +-J problems of N = 8000 in one plan, 2000
@@ -630,6 +678,7 @@ def gpu_arm(args, rank, world):
         extra["uneven_batch"] = measure_uneven(spvar, torch, flush)
         extra["serving"] = measure_serving(spvar)
         extra["sqa_chimera_c8"] = measure_sqa(spvar, torch, flush)
+        extra["u10_chimera_c8"] = measure_u10(spvar, torch, flush)
         extra["persistence_pass_scaled"] = measure_persistence_scaled(spvar, torch)
 
     # roofline of the sweep kernel (integer ALU issue bound)
