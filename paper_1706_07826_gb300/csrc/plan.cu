@@ -360,7 +360,7 @@ std::vector<SweepShape> candidate_shapes(const spvar_plan *pl, int optin)
         // one coupler magnitude per spin, or small integer couplers: the register
         // kernel's 16-bit-lane variants
         const int md = pl->max_deg <= 6 ? 6 : 8;
-        for (int blk : {256, 512, 1024})
+        for (int blk : {128, 256, 512, 1024})
             for (int Q : {1, 2, 4}) {
                 if (Q > 1 && quads < Q) continue;
                 int ns = plan_nslot(pl, Q, blk);
