@@ -309,8 +309,10 @@ typedef struct spvar_params {
 /* With the SQA sampler (replicas_per_block = 4): AUTO and PM1 take the register
  * form for +-1 couplers when it applies (two or more slices, at most 4 colour
  * classes, none larger than sweep_block; blocks 256/512/1024), else the item
- * walk (blocks 128/256/512); PM1S the item walk; GENERAL the general path; PM1W
- * and PM1Q are rejected (SPVAR_ELIMIT). */
+ * walk (blocks 128/256/512); PM1 on small integer couplers (every |J| <= 15,
+ * degree <= 8, dmax <= 254) takes their register form (block 256) when it
+ * applies, else the general path; PM1S the item walk; GENERAL the general path;
+ * PM1W and PM1Q are rejected (SPVAR_ELIMIT). */
 
 #define SPVAR_FORM_BATCHED 0 /* every start of every problem in one persistent launch per phase */
 #define SPVAR_FORM_PLAIN 1   /* one start at a time, one launch per kernel and start */

@@ -553,8 +553,16 @@ int spvar_sqa_sample(const spvar_problem *p, int32_t num_sweeps, int32_t P, cons
             }
         }
         if (variant == 0 && sqa_shape_ok(1, 256, H.n, H.maxdeg, P, W)) variant = 1;
+    } else if (sqa_si_eligible(Pr->jabs_max, H.dmax, H.maxdeg)) {
+        // small integer couplers: their register form (256 threads) when every class fits
+        ncls = sqa_reg_ncls(H.ncol, max_class, 256, P);
+        if (ncls > 0 && sqa_shape_ok(3, 256, H.n, H.maxdeg, P, W, ncls) &&
+            sqa_smem_bytes(H.n, P, H.maxdeg, W, true) <= (size_t)optin) {
+            variant = 3;
+            block = 256;
+        }
     }
-    if (variant != 2) ncls = 0;
+    if (variant < 2) ncls = 0;
     if (!sqa_shape_ok(variant, block, H.n, H.maxdeg, P, W, ncls)) return SPVAR_ELIMIT;
     const size_t smem = sqa_smem_bytes(H.n, P, H.maxdeg, W, variant != 0);
     if (smem > (size_t)optin) return SPVAR_ELIMIT;

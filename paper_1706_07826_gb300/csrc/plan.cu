@@ -278,9 +278,11 @@ SweepShape sqa_shape(const spvar_plan *pl, int block, int optin, int variant)
 {
     SweepShape sh{5, block, 1, variant, pl->sqa_W, pl->max_deg};
     sh.slices = pl->sqa_P;
-    sh.ncls = variant == 2 ? sqa_reg_ncls(pl->ncol_max, pl->class_max, block, pl->sqa_P) : 0;
-    sh.ent32 = variant == 2 && pl->sqa_ent32 ? 1 : 0;
-    const bool ok = (variant == 0 || pl->pm1) && (variant != 2 || sh.ncls > 0) &&
+    sh.ncls = variant >= 2 ? sqa_reg_ncls(pl->ncol_max, pl->class_max, block, pl->sqa_P) : 0;
+    sh.ent32 = variant >= 2 && pl->sqa_ent32 ? 1 : 0;
+    const bool kind_ok = variant == 0 || (variant == 3 ? sqa_si_eligible(pl->jabs_max, pl->dmax, pl->max_deg)
+                                                       : pl->pm1);
+    const bool ok = kind_ok && (variant < 2 || sh.ncls > 0) &&
                     sqa_shape_ok(variant, block, pl->max_n0, pl->max_deg, pl->sqa_P, pl->sqa_W, sh.ncls) &&
                     sweep_shape_smem(sh, pl->max_n0, pl->thr_stride, pl->max_deg) <= (size_t)optin;
     if (!ok) sh.kind = -1;
@@ -297,6 +299,10 @@ std::vector<SweepShape> candidate_shapes(const spvar_plan *pl, int optin)
         }
         for (int b : {256, 512, 1024}) {
             const SweepShape sh = sqa_shape(pl, b, optin, 2);
+            if (sh.kind == 5) out.push_back(sh);
+        }
+        if (!pl->pm1) {
+            const SweepShape sh = sqa_shape(pl, 256, optin, 3);
             if (sh.kind == 5) out.push_back(sh);
         }
         return out;
@@ -387,7 +393,7 @@ void autotune(spvar_plan *pl, cudaStream_t st, int optin)
         if (it != g_tune_cache.end()) {
             pl->shape = it->second;
             // 32-bit acceptance entries are a property of this plan's table, not of the geometry
-            if (pl->shape.kind == 5 && pl->shape.stage == 2) pl->shape.ent32 = pl->sqa_ent32 ? 1 : 0;
+            if (pl->shape.kind == 5 && pl->shape.stage >= 2) pl->shape.ent32 = pl->sqa_ent32 ? 1 : 0;
             pl->sweep_smem = sweep_shape_smem(pl->shape, pl->max_n0, pl->thr_stride, pl->max_deg);
             return;
         }
@@ -703,7 +709,10 @@ int spvar_plan_create(const spvar_problem *const *problems, int32_t nproblems,
             if (p.sweep_kernel == SPVAR_SWEEP_GENERAL) sh = sqa_shape(pl, blk, optin, 0);
             else if (p.sweep_kernel == SPVAR_SWEEP_PM1S) sh = sqa_shape(pl, blk, optin, 1);
             else if (p.sweep_kernel == SPVAR_SWEEP_PM1W || p.sweep_kernel == SPVAR_SWEEP_PM1Q) sh.kind = -1;
-            else if (!pl->pm1) sh = sqa_shape(pl, blk, optin, 0);
+            else if (!pl->pm1) {
+                if (p.sweep_kernel == SPVAR_SWEEP_PM1) sh = sqa_shape(pl, blk, optin, 3);
+                if (sh.kind != 5) sh = sqa_shape(pl, blk, optin, 0);
+            }
             else {
                 sh = sqa_shape(pl, blk, optin, 2);
                 if (sh.kind != 5) sh = sqa_shape(pl, blk, optin, 1);
@@ -890,7 +899,7 @@ int spvar_plan_shape(const spvar_plan *plan, int32_t *block, int32_t *replicas_p
     if (replicas_per_block) *replicas_per_block = 4 * plan->shape.Q;
     if (staged) {
         const int k = plan->shape.kind;
-        *staged = k == 1 ? 2 : k == 2 ? 3 : k == 4 ? 4 : k == 5 ? (plan->shape.stage == 2 ? 6 : 5) : k == 6 ? 7
+        *staged = k == 1 ? 2 : k == 2 ? 3 : k == 4 ? 4 : k == 5 ? (plan->shape.stage >= 2 ? 6 : 5) : k == 6 ? 7
                                                                                                  : plan->shape.stage;
     }
     if (grid) *grid = plan->sweep_grid;

@@ -267,7 +267,8 @@ int pm1_max_active_blocks(int block, int nslot, int maxd, int mode, size_t smem)
 // Simulated quantum annealing sweep (sweep_sqa.cu): one quad per work item, all
 // Trotter slices in shared memory.
 // Variants: 0 general couplers, 1 +-1 couplers (item walk), 2 +-1 couplers in
-// register form (ncls = 2 or 4 colour-class slots per thread).
+// register form (ncls = 2 or 4 colour-class slots per thread), 3 small integer
+// couplers (|J| <= 15, dmax <= 254) in register form.
 constexpr int kSqaMaxSlices = 1024;
 bool sqa_shape_ok(int variant, int block, int max_n, int max_deg, int P, int W, int ncls = 0);
 size_t sqa_smem_bytes(int max_n, int P, int maxdeg, int W, bool pm1);
@@ -277,6 +278,10 @@ int sqa_max_active_blocks(int variant, int block, int max_deg, int ncls, bool en
 // The register form holds one spin of every colour class per thread: two or
 // more slices, at most 4 classes, none larger than the block.  Colour-class
 // slots it needs (2 or 4), 0 if it does not apply.
+inline bool sqa_si_eligible(int jabs_max, int dmax, int maxdeg)
+{
+    return jabs_max >= 1 && jabs_max <= 15 && dmax <= 254 && maxdeg <= 8;
+}
 inline int sqa_reg_ncls(int ncol, int max_class, int block, int P)
 {
     if (P < 2 || ncol > 4 || max_class > block) return 0;

@@ -71,6 +71,13 @@ __device__ __forceinline__ uint4 philox_sqa(uint32_t w0, uint32_t start, uint32_
     return c;
 }
 
+// a * b + c on 32 bits, on the FMA pipe.
+__device__ __forceinline__ uint32_t madq(uint32_t a, uint32_t b, uint32_t c)
+{
+    uint32_t d;
+    asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+    return d;
+}
 __device__ __forceinline__ uint32_t lds_q(const uint32_t *base, uint32_t byte_off)
 {
     return *reinterpret_cast<const uint32_t *>(reinterpret_cast<const char *>(base) + byte_off);
@@ -97,12 +104,15 @@ struct SqaRegConsts {
 // down neighbour of one is the up neighbour of the one before (`prev_up`,
 // valid when `have`).  E32: acceptance entries are 32-bit (no entry of the
 // table is 2^32, i.e. every flip has a nonzero acceptance probability).
-template <int PAR, int MAXD, int U, bool E32>
+// SI: small integer couplers (|J| <= 15; jp holds |J| of neighbour d in bits
+// 4d .. 4d + 3): the byte-wise neighbour sum is weighted, X = sum |J| b', and
+// the entry index a W + k is formed per replica (it may exceed a byte).
+template <int PAR, int MAXD, int U, bool E32, bool SI>
 __device__ __forceinline__ void sqa_reg_items(uint32_t *sw, const void *entv, int P, const int (&tau)[U],
                                               const uint32_t (&base)[U], const uint32_t (&iw)[U], uint32_t own4,
-                                              const uint32_t (&o4)[MAXD], uint32_t c0, const SqaRegConsts &K,
-                                              const uint32_t (&Kr0)[8], const uint32_t (&Kr1)[8], bool chain,
-                                              bool have, uint32_t &prev_up)
+                                              const uint32_t (&o4)[MAXD], uint32_t c0, uint32_t jp,
+                                              const SqaRegConsts &K, const uint32_t (&Kr0)[8],
+                                              const uint32_t (&Kr1)[8], bool chain, bool have, uint32_t &prev_up)
 {
     constexpr uint32_t M = 0x01010101u;
     uint32_t oa[U], own[U], up[U], dn[U], x[U];
@@ -122,7 +132,10 @@ __device__ __forceinline__ void sqa_reg_items(uint32_t *sw, const void *entv, in
         else dn[u] = lds_q(sw, da);
         x[u] = 0;
 #pragma unroll
-        for (int d = 0; d < MAXD; ++d) x[u] += lds_q(sw, base[u] + o4[d]);
+        for (int d = 0; d < MAXD; ++d) {
+            const uint32_t w = lds_q(sw, base[u] + o4[d]);
+            x[u] = SI ? madq(w, (jp >> (4 * d)) & 15u, x[u]) : x[u] + w;
+        }
     }
     prev_up = up[U - 1];
     uint32_t nw[U];
@@ -133,14 +146,17 @@ __device__ __forceinline__ void sqa_reg_items(uint32_t *sw, const void *entv, in
         const uint32_t a = x[u] + x[u] + c0;
         const uint32_t b = K.k2 - a;
         const uint32_t m = own[u] * 0xFFu;
-        const uint32_t full = a4 * K.W + ((a & ~m) | (b & m));  // entry a W + k per byte, <= 3W - 1 <= 255
+        const uint32_t kk = (a & ~m) | (b & m);
+        const uint32_t full = SI ? 0u : a4 * K.W + kk;  // entry a W + k per byte, <= 3W - 1 <= 255
         const uint4 r4 = philox_sqa(iw[u], K.start, K.k1, K.L1, K.HA, K.LA, K.k0w, K.k1w, Kr0, Kr1);
         const uint32_t ur[4] = {r4.x, r4.y, r4.z, r4.w};
         uint32_t rej = 0;
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
             // u + entry carries into bit 32 exactly when the move is rejected
-            const uint32_t e = __byte_perm(full, 0u, 0x4440u | (uint32_t)r);
+            const uint32_t sel = 0x4440u | (uint32_t)r;
+            const uint32_t e = SI ? madq(__byte_perm(a4, 0u, sel), K.W, __byte_perm(kk, 0u, sel))
+                                  : __byte_perm(full, 0u, sel);
             const unsigned long long v = E32 ? (unsigned long long)static_cast<const uint32_t *>(entv)[e]
                                              : static_cast<const unsigned long long *>(entv)[e];
             rej |= (uint32_t)(((unsigned long long)ur[r] + v) >> 32) << (8 * r);
@@ -155,9 +171,9 @@ __device__ __forceinline__ void sqa_reg_items(uint32_t *sw, const void *entv, in
 }
 
 // One parity pass of one colour-class slot: slices two at a time.
-template <int PAR, int MAXD, bool E32>
+template <int PAR, int MAXD, bool E32, bool SI>
 __device__ __forceinline__ void sqa_reg_pass(uint32_t *sw, const void *ent, int g, int G, int P, uint32_t own4,
-                                             const uint32_t (&o4)[MAXD], uint32_t c0, uint32_t ib,
+                                             const uint32_t (&o4)[MAXD], uint32_t c0, uint32_t jp, uint32_t ib,
                                              const SqaRegConsts &K, const uint32_t (&Kr0)[8],
                                              const uint32_t (&Kr1)[8])
 {
@@ -173,17 +189,19 @@ __device__ __forceinline__ void sqa_reg_pass(uint32_t *sw, const void *ent, int 
     for (; tau + dt < P; tau += 2 * dt, base += 2 * step, iw += 2 * istep) {
         const int t2[2] = {tau, tau + dt};
         const uint32_t b2[2] = {base, base + step}, i2[2] = {iw, iw + istep};
-        sqa_reg_items<PAR, MAXD, 2, E32>(sw, ent, P, t2, b2, i2, own4, o4, c0, K, Kr0, Kr1, chain, have, prev_up);
+        sqa_reg_items<PAR, MAXD, 2, E32, SI>(sw, ent, P, t2, b2, i2, own4, o4, c0, jp, K, Kr0, Kr1, chain, have,
+                                             prev_up);
         have = true;
     }
     if (tau < P) {
         const int t1[1] = {tau};
         const uint32_t b1[1] = {base}, i1[1] = {iw};
-        sqa_reg_items<PAR, MAXD, 1, E32>(sw, ent, P, t1, b1, i1, own4, o4, c0, K, Kr0, Kr1, chain, have, prev_up);
+        sqa_reg_items<PAR, MAXD, 1, E32, SI>(sw, ent, P, t1, b1, i1, own4, o4, c0, jp, K, Kr0, Kr1, chain, have,
+                                             prev_up);
     }
 }
 
-template <bool PM1, int B, int MAXD, int NC, bool E32>
+template <bool PM1, int B, int MAXD, int NC, bool E32, bool SI>
 __device__ void run_item_sqa(const SweepLaunch &L, const SweepJob &job, int quad, uint32_t *smem)
 {
     const int tid = threadIdx.x;
@@ -260,13 +278,13 @@ __device__ void run_item_sqa(const SweepLaunch &L, const SweepJob &job, int quad
       if (reg) {
         constexpr int NCR = NC;
         // class j: units (spin k, slice group g) = thread k + g nc, g < G = min(nt, B / nc)
-        uint32_t own4[NCR], o4[NCR][MAXD], c0[NCR], ib[NCR];
+        uint32_t own4[NCR], o4[NCR][MAXD], c0[NCR], ib[NCR], jp[NCR];
         int g[NCR], G[NCR];
 #pragma unroll
         for (int j = 0; j < NCR; ++j) {
             g[j] = -1;
             G[j] = 1;
-            own4[j] = c0[j] = ib[j] = 0u;
+            own4[j] = c0[j] = ib[j] = jp[j] = 0u;
 #pragma unroll
             for (int d = 0; d < MAXD; ++d) o4[j][d] = 0u;
             if (j < ncol) {
@@ -280,7 +298,17 @@ __device__ void run_item_sqa(const SweepLaunch &L, const SweepJob &job, int quad
                         own4[j] = 4u * (uint32_t)p;
 #pragma unroll
                         for (int d = 0; d < MAXD; ++d) o4[j][d] = 4u * (uint32_t)off[d * n + p];
-                        c0[j] = (uint32_t)(bias - (int)(meta & 0xFFFFu) + ((int)meta >> 16)) * 0x01010101u;
+                        // bias - sum_j |J_ij| + h per byte (every |J| = 1: bias - deg + h)
+                        int sumj = (int)(meta & 0xFFFFu);
+                        if (SI) {
+                            sumj = 0;
+                            for (int d = 0; d < (int)(meta & 0xFFFFu) && d < MAXD; ++d) {
+                                const uint32_t aj = (uint32_t)abs((int)pr->ell[(size_t)d * cap_n + p] >> 16);
+                                jp[j] |= aj << (4 * d);
+                                sumj += (int)aj;
+                            }
+                        }
+                        c0[j] = (uint32_t)(bias - sumj + ((int)meta >> 16)) * 0x01010101u;
                         ib[j] = idx_s[p];
                     }
                 }
@@ -318,9 +346,11 @@ __device__ void run_item_sqa(const SweepLaunch &L, const SweepJob &job, int quad
 #pragma unroll
             for (int j = 0; j < NCR; ++j) {
                 if (j < ncol) {
-                    sqa_reg_pass<0, MAXD, E32>(sw, ent, g[j], G[j], P, own4[j], o4[j], c0[j], ib[j], K, Kr0, Kr1);
+                    sqa_reg_pass<0, MAXD, E32, SI>(sw, ent, g[j], G[j], P, own4[j], o4[j], c0[j], jp[j], ib[j], K, Kr0,
+                                                   Kr1);
                     __syncthreads();
-                    sqa_reg_pass<1, MAXD, E32>(sw, ent, g[j], G[j], P, own4[j], o4[j], c0[j], ib[j], K, Kr0, Kr1);
+                    sqa_reg_pass<1, MAXD, E32, SI>(sw, ent, g[j], G[j], P, own4[j], o4[j], c0[j], jp[j], ib[j], K, Kr0,
+                                                   Kr1);
                     __syncthreads();
                 }
             }
@@ -359,7 +389,7 @@ __device__ void run_item_sqa(const SweepLaunch &L, const SweepJob &job, int quad
                         a4 = (~(own ^ up) & 0x01010101u) + (~(own ^ dn) & 0x01010101u);
                     }
                     int idx[4];
-                    if (PM1) {
+                    if (PM1 && !SI) {
                         // byte r of x: neighbours with b_j ^ [J_ij < 0] = 1; k = 2x + bias - deg + h
                         // for b_i = 0 and its mirror 2 bias - that for b_i = 1
                         uint32_t x = 0;
@@ -416,7 +446,7 @@ __device__ void run_item_sqa(const SweepLaunch &L, const SweepJob &job, int quad
         const int tau = (int)(x / n), p = (int)(x - (size_t)tau * n);
         const uint32_t *s = sw + (size_t)tau * ns;
         int c2[4];
-        energy2<PM1>(s[p], meta_s[p], pr->ell, cap_n, p, s, c2);
+        energy2<PM1 && !SI>(s[p], meta_s[p], pr->ell, cap_n, p, s, c2);
 #pragma unroll
         for (int r = 0; r < 4; ++r) atomicAdd(&e2[4 * tau + r], c2[r]);
     }
@@ -450,7 +480,7 @@ __device__ void run_item_sqa(const SweepLaunch &L, const SweepJob &job, int quad
 
 // NC > 0: register form for problems of at most NC colour classes of at most
 // B spins (+-1 couplers, two or more slices); other items take the walk.
-template <bool PM1, int B, int MAXD, int NC, bool E32>
+template <bool PM1, int B, int MAXD, int NC, bool E32, bool SI>
 __global__ void __launch_bounds__(B, (NC > 0 && B == 256) ? 2 : 1) k_sweep_sqa(const SweepLaunch L)
 {
     extern __shared__ __align__(16) uint32_t smem_sqa[];
@@ -459,31 +489,35 @@ __global__ void __launch_bounds__(B, (NC > 0 && B == 256) ? 2 : 1) k_sweep_sqa(c
         SweepJob job;
         int quad0, nq;
         if (!next_item(L, iter, &s_item, job, quad0, nq)) break;
-        run_item_sqa<PM1, B, MAXD, NC, E32>(L, job, quad0, smem_sqa);
+        run_item_sqa<PM1, B, MAXD, NC, E32, SI>(L, job, quad0, smem_sqa);
         __syncthreads();
     }
 }
 
 // variant 0: general couplers (MAXD unused); 1: +-1 couplers, item walk; 2: +-1
 // couplers, register form with ncls colour-class slots (2 or 4) and, with
-// ent32, 32-bit acceptance entries.  +-1: neighbour loop unrolled to MAXD (6 or 8).
+// ent32, 32-bit acceptance entries; 3: the register form for small integer
+// couplers (|J| <= 15; block 256).  +-1 and small integers: neighbour
+// loop unrolled to MAXD (6 or 8).
 void *select_sqa(int variant, int block, int maxdeg, int ncls, bool ent32)
 {
-#define SPVAR_SQA_CASE(PM, BB, MD, NCC, E) \
-    if (block == BB) return reinterpret_cast<void *>(k_sweep_sqa<PM, BB, MD, NCC, E>);
-#define SPVAR_SQA_REG(MD, NCC, E) \
-    SPVAR_SQA_CASE(true, 256, MD, NCC, E) SPVAR_SQA_CASE(true, 512, MD, NCC, E) SPVAR_SQA_CASE(true, 1024, MD, NCC, E)
+#define SPVAR_SQA_CASE(PM, BB, MD, NCC, E, S) \
+    if (block == BB) return reinterpret_cast<void *>(k_sweep_sqa<PM, BB, MD, NCC, E, S>);
+#define SPVAR_SQA_REG(MD, NCC, E)                                                    \
+    SPVAR_SQA_CASE(true, 256, MD, NCC, E, false) SPVAR_SQA_CASE(true, 512, MD, NCC, E, false) \
+        SPVAR_SQA_CASE(true, 1024, MD, NCC, E, false)
+#define SPVAR_SQA_SI(MD, NCC, E) SPVAR_SQA_CASE(true, 256, MD, NCC, E, true)
+    const int md = maxdeg <= 6 ? 6 : maxdeg <= 8 ? 8 : 0;
     if (variant == 0) {
-        SPVAR_SQA_CASE(false, 128, 0, 0, false) SPVAR_SQA_CASE(false, 256, 0, 0, false)
-        SPVAR_SQA_CASE(false, 512, 0, 0, false)
-    } else if (variant == 1 && maxdeg <= 6) {
-        SPVAR_SQA_CASE(true, 128, 6, 0, false) SPVAR_SQA_CASE(true, 256, 6, 0, false)
-        SPVAR_SQA_CASE(true, 512, 6, 0, false)
-    } else if (variant == 1 && maxdeg <= 8) {
-        SPVAR_SQA_CASE(true, 128, 8, 0, false) SPVAR_SQA_CASE(true, 256, 8, 0, false)
-        SPVAR_SQA_CASE(true, 512, 8, 0, false)
+        SPVAR_SQA_CASE(false, 128, 0, 0, false, false) SPVAR_SQA_CASE(false, 256, 0, 0, false, false)
+        SPVAR_SQA_CASE(false, 512, 0, 0, false, false)
+    } else if (variant == 1 && md == 6) {
+        SPVAR_SQA_CASE(true, 128, 6, 0, false, false) SPVAR_SQA_CASE(true, 256, 6, 0, false, false)
+        SPVAR_SQA_CASE(true, 512, 6, 0, false, false)
+    } else if (variant == 1 && md == 8) {
+        SPVAR_SQA_CASE(true, 128, 8, 0, false, false) SPVAR_SQA_CASE(true, 256, 8, 0, false, false)
+        SPVAR_SQA_CASE(true, 512, 8, 0, false, false)
     } else if (variant == 2) {
-        const int md = maxdeg <= 6 ? 6 : maxdeg <= 8 ? 8 : 0;
         if (md == 6 && ncls == 2 && !ent32) { SPVAR_SQA_REG(6, 2, false) }
         if (md == 6 && ncls == 2 && ent32) { SPVAR_SQA_REG(6, 2, true) }
         if (md == 6 && ncls == 4 && !ent32) { SPVAR_SQA_REG(6, 4, false) }
@@ -492,7 +526,17 @@ void *select_sqa(int variant, int block, int maxdeg, int ncls, bool ent32)
         if (md == 8 && ncls == 2 && ent32) { SPVAR_SQA_REG(8, 2, true) }
         if (md == 8 && ncls == 4 && !ent32) { SPVAR_SQA_REG(8, 4, false) }
         if (md == 8 && ncls == 4 && ent32) { SPVAR_SQA_REG(8, 4, true) }
+    } else if (variant == 3) {
+        if (md == 6 && ncls == 2 && !ent32) { SPVAR_SQA_SI(6, 2, false) }
+        if (md == 6 && ncls == 2 && ent32) { SPVAR_SQA_SI(6, 2, true) }
+        if (md == 6 && ncls == 4 && !ent32) { SPVAR_SQA_SI(6, 4, false) }
+        if (md == 6 && ncls == 4 && ent32) { SPVAR_SQA_SI(6, 4, true) }
+        if (md == 8 && ncls == 2 && !ent32) { SPVAR_SQA_SI(8, 2, false) }
+        if (md == 8 && ncls == 2 && ent32) { SPVAR_SQA_SI(8, 2, true) }
+        if (md == 8 && ncls == 4 && !ent32) { SPVAR_SQA_SI(8, 4, false) }
+        if (md == 8 && ncls == 4 && ent32) { SPVAR_SQA_SI(8, 4, true) }
     }
+#undef SPVAR_SQA_SI
 #undef SPVAR_SQA_REG
 #undef SPVAR_SQA_CASE
     return nullptr;
@@ -503,9 +547,12 @@ void *select_sqa(int variant, int block, int maxdeg, int ncls, bool ent32)
 bool sqa_shape_ok(int variant, int block, int max_n, int max_deg, int P, int W, int ncls)
 {
     if (!select_sqa(variant, block, max_deg, ncls, false) || P < 1 || (P > 1 && (P & 1)) || P > kSqaMaxSlices) return false;
-    if (variant == 2 && P < 2) return false;
+    if (variant >= 2 && P < 2) return false;
     if ((long long)max_n >= (1 << 16) - 1) return false;
-    if (variant != 0 && ((long long)P * (max_n + 1) + max_n >= 0xFFFF || 3LL * W - 1 > 255)) return false;
+    if (variant != 0 && (long long)P * (max_n + 1) + max_n >= 0xFFFF) return false;
+    // byte lanes: the entry index a W + k (+-1), or k alone (small integers)
+    if ((variant == 1 || variant == 2) && 3LL * W - 1 > 255) return false;
+    if (variant == 3 && W > 255) return false;
     return true;
 }
 

@@ -121,3 +121,23 @@ def test_u10_chimera_c8_small_integer_couplers(cuda_lib):
     for s, r in ((0, 0), (1, 57), (3, 99)):
         _, e, _ = O.sample(op, thr, 1, seed, start=s, phase=0, r0=r)
         assert out.energies[s, 0, r] == e[0] + inst.offset, (s, r)
+
+
+def test_sqa_u10_chimera_c8_full_size(cuda_lib):
+    """SQA on a U_10 Chimera C8 problem with biases (16 slices, 1000 sweeps,
+    10 starts x (500 + 500) runs, autotuned): sampled phase-0 runs match the
+    oracle one by one."""
+    from paper_1706_07826_gb300 import spvar
+    inst = I.chimera_u10(8, 2500)
+    T, P, seed, starts = 1000, 16, 2400, 10
+    prm = spvar.make_params(num_starts=starts, fixing_sample_size=500, solving_sample_size=500, num_sweeps=T,
+                            elite_threshold=0.1, sampler=spvar.SAMPLER_SQA, sqa_slices=P, sqa_beta=3.0,
+                            sqa_gamma0=3.0, sqa_gamma1=0.01)
+    plan = spvar.Plan([gpu_problem(inst)], prm)
+    out = plan.run([seed], device=False)
+    plan.close()
+    op = oracle_problem(inst)
+    ent = O.sqa_table(T, P, 3.0, O.gamma_linear(T, 3.0, 0.01), O.dmax(op), inst.scale)
+    for st, r in ((0, 0), (5, 250), (9, 499)):
+        _, e, _ = O.sqa_sample(op, ent, P, 1, seed, start=st, phase=0, r0=r)
+        assert out.energies[st, 0, r] == e[0] + inst.offset, (st, r)

@@ -22,6 +22,8 @@ CASES = [
     ("pm1_with_h_P6", lambda: with_h(I.cubic3d(3, 2104), 4, 3), 6, 40, 13),
     ("random_general_P4", lambda: I.random_graph(40, 90, 5, jmax=7, hmax=9), 4, 40, 11),
     ("weak_strong_scaled_P8", lambda: I.weak_strong(2, 2105), 8, 30, 8),
+    ("u10_C3_P4", lambda: I.chimera_u10(3, 2130), 4, 40, 16),
+    ("u10_C4_P8", lambda: I.chimera_u10(4, 2131), 8, 30, 12),
     ("single_slice", lambda: I.cubic3d(4, 2106), 1, 50, 20),
 ]
 
@@ -270,3 +272,32 @@ def test_sqa_autotune_cache_keeps_each_tables_entry_width(cuda_lib):
             for ph in range(ref.nphases[s]):
                 c = ref.counts[s, ph]
                 assert np.array_equal(np.asarray(out.energies[s, ph, :c]), ref.energies[s, ph, :c]), (g1, s, ph)
+
+
+@pytest.mark.parametrize("kernel,block,shape", [("PM1", 256, "sqa-register"), ("GENERAL", 256, "sqa"),
+                                                ("GENERAL", 512, "sqa")], ids=["si_register", "general_256",
+                                                                              "general_512"])
+@pytest.mark.parametrize("make,P", [(lambda: I.chimera_u10(3, 2132), 4), (lambda: I.chimera_u10(4, 2133), 8)],
+                         ids=["u10_C3_P4", "u10_C4_P8"])
+def test_solve_with_sqa_small_integer_couplers(cuda_lib, kernel, block, shape, make, P):
+    """SQA on U_10 Chimera problems (couplers of ten magnitudes): the register
+    form for small integer couplers and the general path, requested
+    explicitly, are identical to the oracle in every phase."""
+    from paper_1706_07826_gb300 import spvar
+    inst = make()
+    op = oracle_problem(inst)
+    T, starts = 30, 2
+    sq = dict(sqa_slices=P, sqa_beta=3.0, sqa_gamma0=2.5, sqa_gamma1=0.05)
+    kw = dict(num_starts=starts, fixing_sample_size=24, solving_sample_size=16, elite_threshold=0.2)
+    ref = O.solve(op, table(inst, T), 45, sampler=1, **sq, **kw)
+    prm = spvar.make_params(num_sweeps=T, sampler=spvar.SAMPLER_SQA, replicas_per_block=4,
+                            sweep_kernel=getattr(spvar, "SWEEP_" + kernel), sweep_block=block, **sq, **kw)
+    plan = spvar.Plan([gpu_problem(inst)], prm)
+    assert plan.shape()["kernel"] == shape
+    out = plan.run([45], device=False)
+    plan.close()
+    for s in range(starts):
+        for ph in range(ref.nphases[s]):
+            c = ref.counts[s, ph]
+            assert np.array_equal(np.asarray(out.energies[s, ph, :c]), ref.energies[s, ph, :c]), (s, ph)
+        assert np.array_equal(np.asarray(out.best_state[s * inst.n:(s + 1) * inst.n]), ref.best_state[s])
