@@ -76,6 +76,13 @@ def lib():
                                     i32p]
         L.or_sqa_sample.restype = ctypes.c_int
         L.or_gamma_linear.argtypes = [ctypes.c_int32, ctypes.c_double, ctypes.c_double, f64p]
+        L.or_icm_move.argtypes = [ctypes.c_int32, i32p, i32p, i8p, i8p, ctypes.c_int32]
+        L.or_icm_move.restype = ctypes.c_int32
+        L.or_pticm_sample.argtypes = [ctypes.c_int32, i32p, i32p, i32p, i32p, i32p, ctypes.c_int32,
+                                      ctypes.c_int32, ctypes.c_int32, u32p, ctypes.c_int32, u32p, ctypes.c_int32,
+                                      ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                      ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, i8p, i64p, i32p, i8p, i64p]
+        L.or_pticm_sample.restype = ctypes.c_int
         L.or_elite_count.argtypes = [ctypes.c_double, ctypes.c_int32]
         L.or_elite_count.restype = ctypes.c_int32
         L.or_elite.argtypes = [ctypes.c_int32, i64p, ctypes.c_int32, i32p]
@@ -239,6 +246,64 @@ def sqa_sample(p: Csr, ent, P, S, seed, start=0, phase=0, colours=None, r0=0):
     if rc != 0:
         raise ValueError("or_sqa_sample failed: %d" % rc)
     return spins[:S, :p.n], e[:S], sl[:S]
+
+
+def icm_move(p: Csr, a, b, seed_spin):
+    """Houdayer's cluster move between replicas a and b (int8 +-1 [n]) seeded at
+    seed_spin: returns (a', b', cluster size)."""
+    a = _c(a, np.int8).copy()
+    b = _c(b, np.int8).copy()
+    size = lib().or_icm_move(p.n, _p(p.row_ptr, i32p), _p(_c(p.col, np.int32), i32p), _p(a, i8p), _p(b, i8p),
+                             int(seed_spin))
+    if size < 0:
+        raise ValueError("seed spin outside the set where the replicas differ")
+    return a, b, int(size)
+
+
+def energy_range(p: Csr):
+    """An upper bound of max E - min E: 2 (sum_{i<j} |J_ij| + sum_i |h_i|)."""
+    return int(np.abs(_c(p.val, np.int64)).sum() + 2 * np.abs(p.h.astype(np.int64)).sum())
+
+
+def pticm_sample(p: Csr, betas, T, K=10, seed=0, start=0, phase=0, icm_from=None, keep_from=None, exchange=True,
+                 icm=True, colours=None):
+    """PTICM (Sec. III.D) with the paper's sample: the K lowest-energy distinct
+    states seen at each replica of the lower half of the temperatures.  betas:
+    R ascending inverse temperatures (problem units).  Returns dict with kept
+    [2(R - keep_from), K, n], kept_e, nkept, final [2R, n], final_e (energies
+    without offset)."""
+    betas = np.asarray(betas, np.float64)
+    R = len(betas)
+    icm_from = R // 2 if icm_from is None else icm_from
+    keep_from = R // 2 if keep_from is None else keep_from
+    if colours is None:
+        colours = colour(p)
+    c = _c(colours[0], np.int32) if p.n else np.zeros(1, np.int32)
+    dm = dmax(p)
+    thr = np.zeros((R, dm + 1), np.uint32)
+    lib().or_thresholds(R, _p(_c(betas, np.float64), f64p), dm, p.scale, _p(thr, u32p))
+    dx = max(energy_range(p), 1)
+    xthr = np.zeros((max(R - 1, 1), dx + 1), np.uint32)
+    if R > 1:
+        db = _c(np.diff(betas), np.float64)
+        lib().or_thresholds(R - 1, _p(db, f64p), dx, p.scale, _p(xthr, u32p))
+    ntr = 2 * (R - keep_from)
+    n1 = max(p.n, 1)
+    kept = np.zeros((max(ntr, 1), K, n1), np.int8)
+    kept_e = np.zeros((max(ntr, 1), K), np.int64)
+    nkept = np.zeros(max(ntr, 1), np.int32)
+    final = np.zeros((2 * R, n1), np.int8)
+    final_e = np.zeros(2 * R, np.int64)
+    flags = (1 if exchange else 0) | (2 if icm else 0)
+    rc = lib().or_pticm_sample(p.n, _p(p.row_ptr, i32p), _p(_c(p.col, np.int32), i32p),
+                               _p(_c(p.val, np.int32), i32p), _p(p.h, i32p), _p(c, i32p), colours[1], R, T,
+                               _p(thr, u32p), dm, _p(xthr, u32p), dx, icm_from, keep_from, K, flags, seed, start,
+                               phase, _p(kept, i8p), _p(kept_e, i64p), _p(nkept, i32p), _p(final, i8p),
+                               _p(final_e, i64p))
+    if rc != 0:
+        raise ValueError("or_pticm_sample failed: %d" % rc)
+    return dict(kept=kept[:ntr, :, :p.n], kept_e=kept_e[:ntr], nkept=nkept[:ntr], final=final[:, :p.n],
+                final_e=final_e)
 
 
 def elite_count(elite, S):

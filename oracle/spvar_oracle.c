@@ -357,6 +357,172 @@ int or_sqa_sample(int32_t n, const int32_t *row_ptr, const int32_t *col, const i
 /* ---------------------------------------------------------------------- */
 /* Persistence (Alg. 1)                                                     */
 /* ---------------------------------------------------------------------- */
+/* ---------------------------------------------------------------------- */
+/* Parallel tempering with isoenergetic cluster moves                       */
+/* ---------------------------------------------------------------------- */
+
+int32_t or_icm_move(int32_t n, const int32_t *row_ptr, const int32_t *col, int8_t *a, int8_t *b,
+                    int32_t seed_spin)
+{
+    if (seed_spin < 0 || seed_spin >= n || a[seed_spin] == b[seed_spin]) return -1;
+    /* breadth-first search over couplers between spins where the replicas differ */
+    int32_t *queue = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    int8_t *in = (int8_t *)calloc((size_t)n, 1);
+    int32_t head = 0, tail = 0;
+    queue[tail++] = seed_spin;
+    in[seed_spin] = 1;
+    while (head < tail) {
+        const int32_t i = queue[head++];
+        for (int32_t p = row_ptr[i]; p < row_ptr[i + 1]; ++p) {
+            const int32_t j = col[p];
+            if (!in[j] && a[j] != b[j]) {
+                in[j] = 1;
+                queue[tail++] = j;
+            }
+        }
+    }
+    for (int32_t q = 0; q < tail; ++q) {
+        a[queue[q]] = (int8_t)-a[queue[q]];
+        b[queue[q]] = (int8_t)-b[queue[q]];
+    }
+    free(in);
+    free(queue);
+    return tail;
+}
+
+static uint32_t rng_word0(uint64_t seed, uint32_t w0, uint32_t phase, uint32_t t, uint32_t start)
+{
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t ctr[4] = {w0, (phase << SWEEP_BITS) + t, 0u, start};
+    uint32_t out[4];
+    or_philox4x32_10(ctr, key, out);
+    return out[0];
+}
+
+/* Offers state s (energy E) to a list of at most K distinct states ordered by
+ * (energy, first sight). */
+static void keep_offer(int32_t n, int32_t K, int8_t *list, int64_t *le, int32_t *cnt, const int8_t *s, int64_t E)
+{
+    if (*cnt == K && E >= le[K - 1]) return;
+    for (int32_t q = 0; q < *cnt; ++q)
+        if (le[q] == E && memcmp(list + (int64_t)q * n, s, (size_t)n) == 0) return;
+    int32_t pos = *cnt;
+    while (pos > 0 && le[pos - 1] > E) --pos; /* after every listed state of energy <= E */
+    const int32_t last = *cnt < K ? *cnt : K - 1;
+    for (int32_t q = last; q > pos; --q) {
+        memcpy(list + (int64_t)q * n, list + (int64_t)(q - 1) * n, (size_t)n);
+        le[q] = le[q - 1];
+    }
+    memcpy(list + (int64_t)pos * n, s, (size_t)n);
+    le[pos] = E;
+    if (*cnt < K) ++*cnt;
+}
+
+int or_pticm_sample(int32_t n, const int32_t *row_ptr, const int32_t *col, const int32_t *val,
+                    const int32_t *h, const int32_t *colour, int32_t ncol,
+                    int32_t R, int32_t T, const uint32_t *thr, int32_t dmax, const uint32_t *xthr, int32_t dx,
+                    int32_t icm_from, int32_t keep_from, int32_t K, int32_t flags,
+                    uint64_t seed, uint32_t start, uint32_t phase,
+                    int8_t *kept, int64_t *kept_e, int32_t *nkept, int8_t *final, int64_t *final_e)
+{
+    if (n < 0 || R < 1 || T < 0 || (uint32_t)T >= INIT_SLOT || phase >= (1u << 12) || K < 1 ||
+        keep_from < 0 || keep_from > R || icm_from < 0 || n >= 0xFFFF || R > 0x7FFF)
+        return -1;
+    int32_t *order = (int32_t *)malloc(sizeof(int32_t) * ((size_t)n + 1));
+    int32_t m = 0;
+    for (int32_t c = 0; c < ncol; ++c)
+        for (int32_t i = 0; i < n; ++i)
+            if (colour[i] == c) order[m++] = i;
+    if (m != n) { free(order); return -1; }
+    const int32_t NR = 2 * R;
+    int8_t *s = final; /* the replicas' current states, [2R][n] */
+    int64_t *E = final_e;
+    for (int32_t r = 0; r < NR; ++r) {
+        for (int32_t i = 0; i < n; ++i)
+            s[(int64_t)r * n + i] = (rng_word(seed, start, phase, INIT_SLOT, i, r) >> 31) ? 1 : -1;
+        E[r] = or_energy(n, row_ptr, col, val, h, s + (int64_t)r * n);
+    }
+    const int32_t ntr = 2 * (R - keep_from);
+    for (int32_t q = 0; q < ntr; ++q) nkept[q] = 0;
+    int8_t *tmp = (int8_t *)malloc((size_t)n + 1);
+    int rc = 0;
+    for (int32_t t = 0; t < T && rc == 0; ++t) {
+        /* 1. Metropolis sweep of every replica at its temperature */
+        for (int32_t r = 0; r < NR && rc == 0; ++r) {
+            const uint32_t *row = thr + (int64_t)(r / 2) * (dmax + 1);
+            int8_t *x = s + (int64_t)r * n;
+            for (int32_t q = 0; q < n; ++q) {
+                const int32_t i = order[q];
+                int64_t f = h[i];
+                for (int32_t p = row_ptr[i]; p < row_ptr[i + 1]; ++p) f += (int64_t)val[p] * x[col[p]];
+                const int64_t dE = -2 * (int64_t)x[i] * f;
+                const uint32_t u = rng_word(seed, start, phase, (uint32_t)t, i, r);
+                int accept;
+                if (dE <= 0) {
+                    accept = 1;
+                } else {
+                    if (dE > dmax) { rc = -2; break; }
+                    accept = u < row[dE];
+                }
+                if (accept) {
+                    x[i] = (int8_t)-x[i];
+                    E[r] += dE;
+                }
+            }
+        }
+        if (rc) break;
+        /* 2. isoenergetic cluster moves at the lower temperatures */
+        if (flags & 2)
+            for (int32_t k = icm_from; k < R; ++k) {
+                int8_t *a = s + (int64_t)(2 * k) * n, *b = s + (int64_t)(2 * k + 1) * n;
+                int32_t nd = 0;
+                for (int32_t i = 0; i < n; ++i) nd += a[i] != b[i];
+                if (nd == 0) continue;
+                const uint32_t u = rng_word0(seed, 0xFFFF0000u | (uint32_t)k, phase, (uint32_t)t, start);
+                const int32_t pick = (int32_t)(((uint64_t)u * (uint64_t)nd) >> 32);
+                int32_t seen = 0, seed_spin = -1;
+                for (int32_t i = 0; i < n && seed_spin < 0; ++i)
+                    if (a[i] != b[i] && seen++ == pick) seed_spin = i;
+                or_icm_move(n, row_ptr, col, a, b, seed_spin);
+                E[2 * k] = or_energy(n, row_ptr, col, val, h, a);
+                E[2 * k + 1] = or_energy(n, row_ptr, col, val, h, b);
+            }
+        /* 3. replica exchange between neighbouring temperatures */
+        if (flags & 1)
+            for (int32_t k = t & 1; k + 1 < R && rc == 0; k += 2)
+                for (int32_t c = 0; c < 2; ++c) {
+                    const int32_t lo = 2 * k + c, hi = 2 * (k + 1) + c;
+                    const int64_t d = E[lo] - E[hi];
+                    const uint32_t u = rng_word0(seed, 0xFFFE0000u | (uint32_t)lo, phase, (uint32_t)t, start);
+                    int accept;
+                    if (d <= 0) {
+                        accept = 1;
+                    } else {
+                        if (d > dx) { rc = -2; break; }
+                        accept = u < xthr[(int64_t)k * (dx + 1) + d];
+                    }
+                    if (accept) {
+                        memcpy(tmp, s + (int64_t)lo * n, (size_t)n);
+                        memcpy(s + (int64_t)lo * n, s + (int64_t)hi * n, (size_t)n);
+                        memcpy(s + (int64_t)hi * n, tmp, (size_t)n);
+                        const int64_t ex = E[lo];
+                        E[lo] = E[hi];
+                        E[hi] = ex;
+                    }
+                }
+        /* 4. the lowest distinct states seen at the tracked replicas */
+        for (int32_t k = keep_from; k < R; ++k)
+            for (int32_t c = 0; c < 2; ++c) {
+                const int32_t q = 2 * (k - keep_from) + c;
+                keep_offer(n, K, kept + (int64_t)q * K * n, kept_e + (int64_t)q * K, nkept + q,
+                           s + (int64_t)(2 * k + c) * n, E[2 * k + c]);
+            }
+    }
+    free(tmp);
+    free(order);
+    return rc;
+}
+
 int32_t or_elite_count(double elite, int32_t S)
 {
     double x = ceil(elite * (double)S);

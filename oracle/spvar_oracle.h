@@ -1,7 +1,9 @@
 /*
  * spvar_oracle.h -- plain, slow, single-threaded C restatement of the
  * sample-persistence variable reduction method (SPVAR, Alg. 1; Multi-start
- * SPVAR, Alg. 2, Sec. II.A-II.C) with simulated annealing as the sampler.
+ * SPVAR, Alg. 2, Sec. II.A-II.C) with simulated annealing as the sampler, and
+ * the paper's other samplers of Sec. III: simulated quantum annealing and
+ * parallel tempering with isoenergetic cluster moves (PTICM).
  *
  * TEST INFRASTRUCTURE ONLY.  This oracle exists so that tests, the
  * smoke check and the CPU baseline leg of the benchmark can check and time
@@ -103,6 +105,47 @@ int or_sqa_sample(int32_t n, const int32_t *row_ptr, const int32_t *col, const i
                   int32_t T, int32_t P, const uint64_t *ent, int32_t dmax,
                   int32_t r0, int32_t S, uint64_t seed, uint32_t start, uint32_t phase,
                   int8_t *spins, int64_t *e, int32_t *slice);
+
+/* Isoenergetic cluster move between two replicas a and b of one temperature
+ * (the cluster step of PTICM, Sec. III.D; Houdayer's move): D = the spins
+ * where a and b differ; the cluster is the connected component of `seed_spin`
+ * (which must be in D) in the graph of couplers restricted to D; both
+ * replicas flip on it, which leaves E(a) + E(b) unchanged.  Returns the
+ * cluster size, or -1 if seed_spin is out of range or not in D. */
+int32_t or_icm_move(int32_t n, const int32_t *row_ptr, const int32_t *col, int8_t *a, int8_t *b,
+                    int32_t seed_spin);
+
+/* Parallel tempering with isoenergetic cluster moves (PTICM, Sec. III.D) as a
+ * sampler of Alg. 1.  R inverse temperatures beta_0 < ... < beta_{R-1}, two
+ * replicas per temperature (replica r = 2k + c, copy c of temperature k),
+ * all started from the initial-state words of or_sample.  Each of T sweeps:
+ *   1. a Metropolis sweep of every replica at its temperature: thr[k][dE]
+ *      (or_thresholds of beta_k), random word of spin i of replica r as in
+ *      or_sample with sweep t;
+ *   2. if flags & 2, for every k >= icm_from with D non-empty, or_icm_move
+ *      on the two copies, seeded at element floor(u |D| / 2^32) of D in index
+ *      order, u = word 0 of Philox((0xFFFF0000 | k, phase 2^20 + t, 0, start));
+ *   3. if flags & 1, replica exchange between temperatures k and k + 1 for
+ *      every k = t (mod 2), copy 0 then copy 1: with d = E(k, c) - E(k+1, c),
+ *      accepted iff d <= 0 or u < xthr[k][d] (xthr = or_thresholds of
+ *      beta_{k+1} - beta_k over d = 1 .. dx), u = word 0 of
+ *      Philox((0xFFFE0000 | (2k + c), phase 2^20 + t, 0, start)); accepted
+ *      exchanges swap the two replicas' states and energies;
+ *   4. for every temperature k >= keep_from and copy c, the current state is
+ *      offered to that replica's list of the K lowest-energy distinct states
+ *      seen (ordered by energy, then by first sight; a state already listed
+ *      is not listed again; a full list takes a state only if its energy is
+ *      below the list's highest, which then leaves).
+ * Outputs: kept[2 (R - keep_from)][K][n], kept_e[..][K] (without offset),
+ * nkept[2 (R - keep_from)] (replica order k = keep_from.., copy 0 then 1),
+ * and the final states final[2R][n], final_e[2R].  Returns 0, -1 on bad
+ * arguments, -2 if a flip cost exceeds dmax or an energy gap exceeds dx. */
+int or_pticm_sample(int32_t n, const int32_t *row_ptr, const int32_t *col, const int32_t *val,
+                    const int32_t *h, const int32_t *colour, int32_t ncol,
+                    int32_t R, int32_t T, const uint32_t *thr, int32_t dmax, const uint32_t *xthr, int32_t dx,
+                    int32_t icm_from, int32_t keep_from, int32_t K, int32_t flags,
+                    uint64_t seed, uint32_t start, uint32_t phase,
+                    int8_t *kept, int64_t *kept_e, int32_t *nkept, int8_t *final, int64_t *final_e);
 
 /* Elite sample size k = ceil(elite * S), clamped to [1, S] (Alg. 1). */
 int32_t or_elite_count(double elite, int32_t S);
