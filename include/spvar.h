@@ -197,6 +197,45 @@ int spvar_sqa_sample(const spvar_problem *p, int32_t num_sweeps, int32_t P, cons
                      int64_t *energies, int32_t *slice, void *stream);
 
 /* ------------------------------------------------------------------ */
+/* Third sampler: parallel tempering with isoenergetic cluster moves     */
+/* (PTICM, Sec. III.D), with the paper's sample rule                     */
+/* ------------------------------------------------------------------ */
+
+#define SPVAR_PTICM_MAX_KEEP 64
+
+/* num_runs independent PTICM runs of the problem (run j uses start word
+ * start0 + j), one CTA each.  R inverse temperatures beta_0 < ... < beta_{R-1}
+ * with two replicas each (replica r = 2k + c), initial states from the
+ * initial-state words of spvar_sample (replica r = sample r).  Each of
+ * num_sweeps sweeps: (1) a Metropolis sweep of every replica at its
+ * temperature, thr: device [R][thr_stride] from spvar_thresholds of the betas
+ * (thr_stride >= dmax + 1), random words as spvar_sample; (2) if flags & 2,
+ * Houdayer's move at every temperature k >= icm_from whose two replicas
+ * differ: the seed is element floor(u |D| / 2^32) of the differing set D in
+ * index order (u: word 0 of Philox((0xFFFF0000 | k, phase 2^20 + t, 0,
+ * start))), the cluster its connected component among the couplers inside
+ * D, and both replicas flip on it; (3) if flags & 1, replica exchange between
+ * temperatures k and k + 1 for k = t (mod 2), each copy: with
+ * d = E(k) - E(k+1), accepted iff d <= 0 or u < xthr[k][d] (xthr: device
+ * [R-1][dx+1] from spvar_thresholds of beta_{k+1} - beta_k, dx >= the range
+ * max E - min E; u: word 0 of Philox((0xFFFE0000 | (2k + c), phase 2^20 + t,
+ * 0, start))); (4) every replica of temperature k >= keep_from offers its
+ * state to its list of the K lowest-energy distinct states seen (ordered by
+ * energy, then first sight; a full list takes a state only below its highest
+ * energy).  Outputs (device): kept [num_runs][2 (R - keep_from)][K][ceil(n/32)]
+ * bit-packed in index order, kept_e [..][K] (with offset), nkept [num_runs][2
+ * (R - keep_from)] (zeroed here), final_states [num_runs][2R][ceil(n/32)],
+ * final_e [num_runs][2R] (with offset).  Asynchronous on stream.  Errors:
+ * EINVAL (bad sizes or flags, missing buffers), ELIMIT (R > 64, K >
+ * SPVAR_PTICM_MAX_KEEP, n > 2048, or the replicas do not fit in shared
+ * memory), ECUDA. */
+int spvar_pticm_sample(const spvar_problem *p, int32_t R, int32_t num_sweeps, const uint32_t *thr,
+                       int32_t thr_stride, const uint32_t *xthr, int32_t dx, int32_t icm_from, int32_t keep_from,
+                       int32_t K, int32_t flags, int32_t num_runs, uint64_t seed, uint32_t start0, uint32_t phase,
+                       uint32_t *kept, int64_t *kept_e, int32_t *nkept, uint32_t *final_states, int64_t *final_e,
+                       void *stream);
+
+/* ------------------------------------------------------------------ */
 /* Persistence (Alg. 1: elite sample, mean value, fixing rule)          */
 /* ------------------------------------------------------------------ */
 /* k = ceil(elite_threshold * num_samples) (clamped to [1, num_samples])

@@ -588,6 +588,34 @@ int spvar_sqa_sample(const spvar_problem *p, int32_t num_sweeps, int32_t P, cons
     return SPVAR_OK;
 }
 
+int spvar_pticm_sample(const spvar_problem *p, int32_t R, int32_t num_sweeps, const uint32_t *thr,
+                       int32_t thr_stride, const uint32_t *xthr, int32_t dx, int32_t icm_from, int32_t keep_from,
+                       int32_t K, int32_t flags, int32_t num_runs, uint64_t seed, uint32_t start0, uint32_t phase,
+                       uint32_t *kept, int64_t *kept_e, int32_t *nkept, uint32_t *final_states, int64_t *final_e,
+                       void *stream)
+{
+    if (!p) return SPVAR_EINVAL;
+    const Problem *Pr = reinterpret_cast<const Problem *>(p);
+    const DevProb &H = Pr->hdr;
+    if (R < 1 || num_sweeps < 0 || icm_from < 0 || icm_from > R || keep_from < 0 || keep_from > R || K < 1 ||
+        flags < 0 || flags > 3 || num_runs < 0 || phase > SPVAR_MAX_PHASE || thr_stride < H.dmax + 1 ||
+        ((flags & 1) && R > 1 && (dx < 1 || !xthr)))
+        return SPVAR_EINVAL;
+    if (R > pticm_max_r() || K > SPVAR_PTICM_MAX_KEEP || num_sweeps > SPVAR_MAX_SWEEPS || H.n > pticm_max_n())
+        return SPVAR_ELIMIT;
+    if (num_runs == 0) return SPVAR_OK;
+    if ((num_sweeps > 0 && !thr) || !final_e || !nkept || !kept_e || (H.n > 0 && (!final_states || !kept)))
+        return SPVAR_EINVAL;
+    const size_t smem = pticm_smem_bytes(H.n, R, icm_from, H.dmax);
+    if (smem > (size_t)device_smem_optin()) return SPVAR_ELIMIT;
+    cudaStream_t st = as_stream(stream);
+    const size_t ntr = 2 * (size_t)(R - keep_from);
+    if (ntr > 0) SPVAR_CUDA_TRY(cudaMemsetAsync(nkept, 0, sizeof(int32_t) * ntr * (size_t)num_runs, st));
+    SPVAR_CUDA_TRY(launch_pticm(Pr->dev, thr, thr_stride, xthr, dx, R, num_sweeps, icm_from, keep_from, K, flags, seed,
+                                start0, phase, num_runs, smem, kept, kept_e, nkept, final_states, final_e, st));
+    return SPVAR_OK;
+}
+
 int spvar_persistence(const spvar_problem *p, int32_t num_samples, const uint32_t *spins,
                       const int64_t *energies, double elite_threshold, int32_t fix_num,
                       int32_t fix_den, int32_t canon, int32_t *elite, int32_t *counts,

@@ -295,6 +295,16 @@ size_t pm1q_smem_bytes(int max_n, int Q);
 cudaError_t launch_sweep_pm1q(const SweepLaunch &L, int block, int maxd, int grid, size_t smem, cudaStream_t st);
 int pm1q_max_active_blocks(int block, int maxd, size_t smem);
 
+// PTICM sampler (sweep_pticm.cu): one CTA per run, every replica's spins in
+// shared memory.
+size_t pticm_smem_bytes(int n, int R, int icm_from, int dmax);
+int pticm_max_r();
+int pticm_max_n();
+cudaError_t launch_pticm(const DevProb *prob, const uint32_t *thr, int thr_stride, const uint32_t *xthr, int dx,
+                         int R, int T, int icm_from, int keep_from, int K, int flags, uint64_t seed,
+                         uint32_t start0, uint32_t phase, int runs, size_t smem, uint32_t *kept, int64_t *kept_e,
+                         int32_t *nkept, uint32_t *final_bits, int64_t *final_e, cudaStream_t st);
+
 // Streaming +-1 sweep (sweep_pm1s.cu): one quad per work item.
 bool pm1s_shape_ok(int block, int maxd, int max_n, int Q);
 size_t pm1s_smem_bytes(int max_n, int Q, int maxd);

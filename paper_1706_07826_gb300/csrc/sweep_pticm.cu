@@ -1,0 +1,354 @@
+// Parallel tempering with isoenergetic cluster moves (PTICM, Sec. III.D) as
+// a sampler of Alg. 1, with the paper's sample: the K lowest-energy distinct
+// states seen at each replica of the lower half of the temperatures.
+//
+// One CTA runs one PTICM run (start = start0 + blockIdx.x).  R inverse
+// temperatures, two replicas (copies) each, replica r = 2k + c; every replica's
+// spins live in shared memory as bytes (0/1) by position.  A sweep:
+//   1. a Metropolis sweep of every replica at its temperature: items
+//      (quad, spin) of one colour class at a time, one Philox block per item
+//      for its four replicas (the counter and word of the SA sweep), the
+//      thresholds of temperature k = r / 2 staged in shared memory;
+//   2. Houdayer's cluster move at every temperature k >= icm_from whose
+//      copies differ somewhere: a warp finds the seed (element
+//      floor(u |D| / 2^32) of the differing set D in index order) with
+//      ballots, then the clusters of all those temperatures grow together,
+//      one neighbour ring per round, until a round adds nothing (at most n
+//      rounds), and both copies flip on them;
+//   3. replica exchange between temperatures k and k + 1 for k = t (mod 2):
+//      the pairs are disjoint, so every decision is taken at once from the
+//      replicas' energies and an integer threshold table, and accepted pairs
+//      swap their states;
+//   4. a warp per tracked replica offers its state, bit-packed in index
+//      order, to the replica's list of the K lowest distinct states seen.
+// Every wait is a __syncthreads reached by the whole CTA.
+#include "sweep_common.cuh"
+
+namespace spvar {
+
+namespace {
+
+constexpr int kPtMaxR = 64;     // most temperatures
+constexpr int kPtWarpWords = 64;  // packed words of one state a warp keeps (n <= 2048)
+
+struct PticmArgs {
+    const DevProb *prob;
+    const uint32_t *thr;   // [R][thr_stride]: Metropolis thresholds of each temperature
+    const uint32_t *xthr;  // [R - 1][dx + 1]: exchange thresholds
+    int32_t R, T, thr_stride, dx, icm_from, keep_from, K, flags;
+    uint64_t seed;
+    uint32_t start0, phase;
+    uint32_t *kept;        // [runs][ntr][K][W] bit-packed, index order
+    int64_t *kept_e;       // [runs][ntr][K] (with offset)
+    int32_t *nkept;        // [runs][ntr]
+    uint32_t *final_bits;  // [runs][2R][W]
+    int64_t *final_e;      // [runs][2R] (with offset)
+};
+
+__device__ __forceinline__ uint32_t word0(uint32_t w0, uint32_t y, uint32_t start, uint32_t k0, uint32_t k1)
+{
+    return philox4x32_10(make_uint4(w0, y, 0u, start), k0, k1).x;
+}
+
+// 2E of every replica into E[r] (without offset).  Contains __syncthreads.
+template <int B>
+__device__ void replica_energies(const DevProb *P, const uint8_t *s8, int NR, int *E2, int *E)
+{
+    const int tid = threadIdx.x, n = P->n, cap_n = P->cap_n;
+    for (int r = tid; r < NR; r += B) E2[r] = 0;
+    __syncthreads();
+    for (int x = tid; x < NR * n; x += B) {
+        const int r = x / n, p = x - r * n;
+        const uint8_t *s = s8 + (size_t)r * n;
+        const uint32_t meta = P->meta[p];
+        const int deg = (int)(meta & 0xFFFFu);
+        int f = 2 * ((int)meta >> 16);
+        for (int d = 0; d < deg; ++d) {
+            const uint32_t e = P->ell[(size_t)d * cap_n + p];
+            f += ((int)e >> 16) * (2 * (int)s[e & 0xFFFFu] - 1);
+        }
+        atomicAdd(&E2[r], (2 * (int)s[p] - 1) * f);
+    }
+    __syncthreads();
+    for (int r = tid; r < NR; r += B) E[r] = E2[r] / 2;
+    __syncthreads();
+}
+
+template <int B>
+__global__ void __launch_bounds__(B) k_pticm(const PticmArgs A)
+{
+    extern __shared__ __align__(16) unsigned char smem_pt[];
+    __shared__ int sE[2 * kPtMaxR], sE2[2 * kPtMaxR], sCnt[kPtMaxR], sSeed[kPtMaxR], sAcc[kPtMaxR];
+    __shared__ int sFlag[3];
+    __shared__ int s_cptr[kMaxColours + 1];
+    __shared__ uint32_t sPack[B / 32][kPtWarpWords];
+
+    const DevProb *P = A.prob;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int n = P->n, ncol = P->ncol, cap_n = P->cap_n, dmax = P->dmax;
+    const int R = A.R, NR = 2 * R, T = A.T;
+    const int nic = R - A.icm_from;            // temperatures with cluster moves
+    const int ntr = 2 * (R - A.keep_from);     // tracked replicas
+    const int W = (n + 31) >> 5;
+    const int run = blockIdx.x;
+    const uint32_t start = A.start0 + (uint32_t)run;
+    const uint32_t k0 = (uint32_t)A.seed, k1 = (uint32_t)(A.seed >> 32);
+    const uint32_t phase_hi = A.phase << kSweepBits;
+
+    uint8_t *s8 = smem_pt;                                         // [2R][n]
+    uint8_t *cl = s8 + (size_t)NR * n;                             // [nic][n]
+    uint32_t *thr_s = reinterpret_cast<uint32_t *>(smem_pt + (((size_t)NR * n + (size_t)nic * n + 15) & ~(size_t)15));
+
+    for (int c = tid; c <= ncol; c += B) s_cptr[c] = P->cptr[c];
+    for (int x = tid; x < R * (dmax + 1); x += B) {
+        const int k = x / (dmax + 1), d = x - k * (dmax + 1);
+        thr_s[x] = A.thr[(size_t)k * A.thr_stride + d];
+    }
+    // initial states: the SA initial-state words of replica r
+    for (int x = tid; x < NR * n; x += B) {
+        const int r = x / n, p = x - r * n;
+        const uint4 w = philox4x32_10(
+            make_uint4((uint32_t)P->idx_of_pos[p], phase_hi | kInitSlot, (uint32_t)(r >> 2), start), k0, k1);
+        const uint32_t u = (r & 3) == 0 ? w.x : (r & 3) == 1 ? w.y : (r & 3) == 2 ? w.z : w.w;
+        s8[x] = (uint8_t)(u >> 31);
+    }
+    __syncthreads();
+    replica_energies<B>(P, s8, NR, sE2, sE);
+
+    const int nq = (NR + 3) >> 2;
+    for (int t = 0; t < T; ++t) {
+        const uint32_t y = phase_hi | (uint32_t)t;
+        // 1. Metropolis sweep of every replica, colour class by colour class
+        for (int c = 0; c < ncol; ++c) {
+            const int lo = s_cptr[c], nc = s_cptr[c + 1] - lo;
+            for (int x = tid; x < nq * nc; x += B) {
+                const int q = x / nc, p = lo + (x - q * nc);
+                const uint4 w = philox4x32_10(make_uint4((uint32_t)P->idx_of_pos[p], y, (uint32_t)q, start), k0, k1);
+                const uint32_t uu[4] = {w.x, w.y, w.z, w.w};
+                const uint32_t meta = P->meta[p];
+                const int deg = (int)(meta & 0xFFFFu), h = (int)meta >> 16;
+#pragma unroll
+                for (int rr = 0; rr < 4; ++rr) {
+                    const int r = 4 * q + rr;
+                    if (r >= NR) break;
+                    uint8_t *s = s8 + (size_t)r * n;
+                    int f = h;
+                    for (int d = 0; d < deg; ++d) {
+                        const uint32_t e = P->ell[(size_t)d * cap_n + p];
+                        f += ((int)e >> 16) * (2 * (int)s[e & 0xFFFFu] - 1);
+                    }
+                    const int dE = -2 * (2 * (int)s[p] - 1) * f;
+                    const bool accept =
+                        dE <= 0 || uu[rr] < thr_s[(size_t)(r >> 1) * (dmax + 1) + min(dE, dmax)];
+                    if (accept) {
+                        s[p] ^= 1u;
+                        atomicAdd(&sE[r], dE);
+                    }
+                }
+            }
+            __syncthreads();
+        }
+        // 2. cluster moves at the lower temperatures
+        if ((A.flags & 2) && nic > 0) {
+            for (int k = tid; k < nic; k += B) sCnt[k] = 0;
+            __syncthreads();
+            for (int x = tid; x < nic * n; x += B) {
+                const int kk = x / n, p = x - kk * n, k = A.icm_from + kk;
+                if (s8[(size_t)(2 * k) * n + p] != s8[(size_t)(2 * k + 1) * n + p]) atomicAdd(&sCnt[kk], 1);
+            }
+            __syncthreads();
+            // seeds: element floor(u |D| / 2^32) of D in index order, one warp per temperature
+            for (int kk = warp; kk < nic; kk += B / 32) {
+                const int k = A.icm_from + kk, cnt = sCnt[kk];
+                int seedpos = -1;
+                if (cnt > 0) {
+                    const uint32_t u = word0(0xFFFF0000u | (uint32_t)k, y, start, k0, k1);
+                    const int pick = (int)(((uint64_t)u * (uint64_t)cnt) >> 32);
+                    int seen = 0;
+                    for (int base = 0; base < n && seedpos < 0; base += 32) {
+                        const int i = base + lane;
+                        int pos = -1;
+                        bool dif = false;
+                        if (i < n) {
+                            pos = P->pos_of_idx[i];
+                            dif = s8[(size_t)(2 * k) * n + pos] != s8[(size_t)(2 * k + 1) * n + pos];
+                        }
+                        const uint32_t bal = __ballot_sync(0xFFFFFFFFu, dif);
+                        const int c = __popc(bal);
+                        if (pick < seen + c) {
+                            // the (pick - seen)-th set lane
+                            const int want = pick - seen;
+                            const bool mine = dif && __popc(bal & ((1u << lane) - 1u)) == want;
+                            const uint32_t who = __ballot_sync(0xFFFFFFFFu, mine);
+                            seedpos = __shfl_sync(0xFFFFFFFFu, pos, __ffs(who) - 1);
+                        }
+                        seen += c;
+                    }
+                }
+                if (lane == 0) sSeed[kk] = seedpos;
+            }
+            __syncthreads();
+            for (int x = tid; x < nic * n; x += B) {
+                const int kk = x / n, p = x - kk * n;
+                cl[x] = (uint8_t)(p == sSeed[kk]);
+            }
+            if (tid < 3) sFlag[tid] = 0;
+            __syncthreads();
+            // grow every cluster by one neighbour ring per round (in place) until a round adds nothing
+            for (int it = 0; it < n; ++it) {
+                if (tid == 0) sFlag[(it + 1) % 3] = 0;
+                for (int x = tid; x < nic * n; x += B) {
+                    const int kk = x / n, p = x - kk * n, k = A.icm_from + kk;
+                    if (cl[x] || sSeed[kk] < 0) continue;
+                    if (s8[(size_t)(2 * k) * n + p] == s8[(size_t)(2 * k + 1) * n + p]) continue;
+                    const int deg = (int)(P->meta[p] & 0xFFFFu);
+                    for (int d = 0; d < deg; ++d) {
+                        const int j = (int)(P->ell[(size_t)d * cap_n + p] & 0xFFFFu);
+                        if (cl[(size_t)kk * n + j]) {
+                            cl[x] = 1;
+                            sFlag[it % 3] = 1;
+                            break;
+                        }
+                    }
+                }
+                __syncthreads();
+                if (!sFlag[it % 3]) break;
+            }
+            for (int x = tid; x < nic * n; x += B) {
+                if (!cl[x]) continue;
+                const int kk = x / n, p = x - kk * n, k = A.icm_from + kk;
+                s8[(size_t)(2 * k) * n + p] ^= 1u;
+                s8[(size_t)(2 * k + 1) * n + p] ^= 1u;
+            }
+            __syncthreads();
+            replica_energies<B>(P, s8, NR, sE2, sE);
+        }
+        // 3. replica exchange between temperatures k and k + 1, k = t (mod 2)
+        if (A.flags & 1) {
+            const int npair = (R - 1 - (t & 1) + 1) / 2;  // k = (t & 1), (t & 1) + 2, ... < R - 1
+            for (int z = tid; z < 2 * max(npair, 0); z += B) {
+                const int k = (t & 1) + 2 * (z >> 1), c = z & 1;
+                const int lo = 2 * k + c, hi = lo + 2;
+                const int d = sE[lo] - sE[hi];
+                const uint32_t u = word0(0xFFFE0000u | (uint32_t)lo, y, start, k0, k1);
+                sAcc[z] = d <= 0 || u < A.xthr[(size_t)k * (A.dx + 1) + min(d, A.dx)];
+            }
+            __syncthreads();
+            for (int x = tid; x < 2 * max(npair, 0) * n; x += B) {
+                const int z = x / n, p = x - z * n;
+                if (!sAcc[z]) continue;
+                const int lo = 2 * ((t & 1) + 2 * (z >> 1)) + (z & 1), hi = lo + 2;
+                const uint8_t a = s8[(size_t)lo * n + p];
+                s8[(size_t)lo * n + p] = s8[(size_t)hi * n + p];
+                s8[(size_t)hi * n + p] = a;
+            }
+            __syncthreads();
+            for (int z = tid; z < 2 * max(npair, 0); z += B) {
+                if (!sAcc[z]) continue;
+                const int lo = 2 * ((t & 1) + 2 * (z >> 1)) + (z & 1), hi = lo + 2;
+                const int e = sE[lo];
+                sE[lo] = sE[hi];
+                sE[hi] = e;
+            }
+            __syncthreads();
+        }
+        // 4. each tracked replica's list of the K lowest distinct states seen
+        for (int q = warp; q < ntr; q += B / 32) {
+            const int r = 2 * (A.keep_from + q / 2) + (q & 1);
+            const int64_t E = (int64_t)sE[r] + P->offset;
+            const size_t base = (size_t)run * ntr + q;
+            int32_t *cntp = A.nkept + base;
+            int64_t *le = A.kept_e + base * A.K;
+            uint32_t *lst = A.kept + base * A.K * W;
+            const int cnt = *cntp;
+            if (cnt == A.K && E >= le[A.K - 1]) continue;
+            // the state, bit-packed in index order
+            for (int w = 0; w < W; ++w) {
+                const int i = 32 * w + lane;
+                const bool b = i < n && s8[(size_t)r * n + P->pos_of_idx[i]];
+                const uint32_t bits = __ballot_sync(0xFFFFFFFFu, b);
+                if (lane == 0) sPack[warp][w] = bits;
+            }
+            __syncwarp();
+            bool dup = false;
+            for (int j = 0; j < cnt && !dup; ++j) {
+                if (le[j] != E) continue;
+                bool diff = false;
+                for (int w = lane; w < W; w += 32) diff |= lst[(size_t)j * W + w] != sPack[warp][w];
+                dup = !__any_sync(0xFFFFFFFFu, diff);
+            }
+            if (dup) continue;
+            int pos = cnt;
+            while (pos > 0 && le[pos - 1] > E) --pos;
+            const int last = cnt < A.K ? cnt : A.K - 1;
+            for (int j = last; j > pos; --j) {
+                for (int w = lane; w < W; w += 32) lst[(size_t)j * W + w] = lst[(size_t)(j - 1) * W + w];
+                __syncwarp();
+                if (lane == 0) le[j] = le[j - 1];
+                __syncwarp();
+            }
+            for (int w = lane; w < W; w += 32) lst[(size_t)pos * W + w] = sPack[warp][w];
+            if (lane == 0) {
+                le[pos] = E;
+                if (cnt < A.K) *cntp = cnt + 1;
+            }
+            __syncwarp();
+        }
+        __syncthreads();
+    }
+    // final states and energies of every replica
+    for (int r = warp; r < NR; r += B / 32) {
+        for (int w = 0; w < W; ++w) {
+            const int i = 32 * w + lane;
+            const bool b = i < n && s8[(size_t)r * n + P->pos_of_idx[i]];
+            const uint32_t bits = __ballot_sync(0xFFFFFFFFu, b);
+            if (lane == 0) A.final_bits[((size_t)run * NR + r) * W + w] = bits;
+        }
+        if (lane == 0) A.final_e[(size_t)run * NR + r] = (int64_t)sE[r] + P->offset;
+    }
+}
+
+}  // namespace
+
+size_t pticm_smem_bytes(int n, int R, int icm_from, int dmax)
+{
+    const size_t spins = (2 * (size_t)R * n + (size_t)(R - icm_from) * n + 15) & ~(size_t)15;
+    return spins + 4 * (size_t)R * ((size_t)dmax + 1);
+}
+
+int pticm_max_r() { return kPtMaxR; }
+int pticm_max_n() { return 32 * kPtWarpWords; }
+
+cudaError_t launch_pticm(const DevProb *prob, const uint32_t *thr, int thr_stride, const uint32_t *xthr, int dx,
+                         int R, int T, int icm_from, int keep_from, int K, int flags, uint64_t seed,
+                         uint32_t start0, uint32_t phase, int runs, size_t smem, uint32_t *kept, int64_t *kept_e,
+                         int32_t *nkept, uint32_t *final_bits, int64_t *final_e, cudaStream_t st)
+{
+    PticmArgs A;
+    A.prob = prob;
+    A.thr = thr;
+    A.xthr = xthr;
+    A.R = R;
+    A.T = T;
+    A.thr_stride = thr_stride;
+    A.dx = dx;
+    A.icm_from = icm_from;
+    A.keep_from = keep_from;
+    A.K = K;
+    A.flags = flags;
+    A.seed = seed;
+    A.start0 = start0;
+    A.phase = phase;
+    A.kept = kept;
+    A.kept_e = kept_e;
+    A.nkept = nkept;
+    A.final_bits = final_bits;
+    A.final_e = final_e;
+    void *k = reinterpret_cast<void *>(k_pticm<256>);
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    void *args[] = {&A};
+    return cudaLaunchKernel(k, dim3(runs), dim3(256), args, smem, st);
+}
+
+}  // namespace spvar

@@ -92,6 +92,8 @@ def lib():
         L.spvar_sqa_table.argtypes = [i32, i32, vp, vp, i32, i32, vp]
         L.spvar_gamma_linear.argtypes = [i32, ctypes.c_double, ctypes.c_double, vp]
         L.spvar_sqa_sample.argtypes = [vp, i32, i32, vp, i32, i32, u64, u32, u32, vp, vp, vp, vp]
+        L.spvar_pticm_sample.argtypes = [vp, i32, i32, vp, i32, vp, i32, i32, i32, i32, i32, i32, u64, u32, u32,
+                                         vp, vp, vp, vp, vp, vp]
         L.spvar_sample_range.argtypes = [vp, i32, i32, vp, i32, i32, u64, u32, u32, vp, vp, vp, vp]
         L.spvar_persistence.argtypes = [vp, i32, vp, vp, ctypes.c_double, i32, i32, i32, vp, vp, vp, vp,
                                         ctypes.POINTER(i32), vp]
@@ -305,6 +307,45 @@ def sqa_sample(problem, ent_dev, W, num_sweeps, P, num_samples, seed, start=0, p
     _check(lib().spvar_sqa_sample(problem.handle, num_sweeps, P, _dp(ent_dev), W, num_samples, seed, start, phase,
                                   _dp(spins), _dp(energies), _dp(sl), _stream(stream)), "spvar_sqa_sample")
     return spins, energies, sl
+
+
+def energy_range(inst):
+    """An upper bound of max E - min E of an instance: 2 (sum |J| + sum |h|)."""
+    return int(2 * (np.abs(np.asarray(inst.J, np.int64)).sum() + np.abs(np.asarray(inst.h, np.int64)).sum()))
+
+
+def pticm_sample(problem, betas, num_sweeps, dx, K=10, num_runs=1, seed=0, start0=0, phase=0, icm_from=None,
+                 keep_from=None, exchange=True, icm=True, stream=None):
+    """PTICM runs (third sampler for Alg. 1, Sec. III.D): R = len(betas)
+    ascending inverse temperatures, two replicas each; the sample of a run is
+    the K lowest distinct states seen at each replica of temperatures
+    >= keep_from (default R / 2).  dx >= max E - min E (energy_range).
+    Returns dict of device tensors: kept int32 [runs, ntr, K, W], kept_e,
+    nkept, final_states int32 [runs, 2R, W], final_e."""
+    import torch
+    betas = _host(betas, np.float64)
+    R = len(betas)
+    icm_from = R // 2 if icm_from is None else icm_from
+    keep_from = R // 2 if keep_from is None else keep_from
+    info = problem.info()
+    dm, scale = info.dmax, info.energy_scale
+    thr = thresholds_device(thresholds(betas, dm, scale))
+    xthr = thresholds_device(thresholds(np.diff(betas) if R > 1 else np.zeros(1), dx, scale))
+    n = problem.n
+    Wn = max((n + 31) // 32, 1)
+    ntr = 2 * (R - keep_from)
+    runs1 = max(num_runs, 1)
+    kept = torch.zeros((runs1, max(ntr, 1), K, Wn), dtype=torch.int32, device="cuda")
+    kept_e = torch.zeros((runs1, max(ntr, 1), K), dtype=torch.int64, device="cuda")
+    nkept = torch.zeros((runs1, max(ntr, 1)), dtype=torch.int32, device="cuda")
+    final = torch.zeros((runs1, 2 * R, Wn), dtype=torch.int32, device="cuda")
+    final_e = torch.zeros((runs1, 2 * R), dtype=torch.int64, device="cuda")
+    flags = (1 if exchange else 0) | (2 if icm else 0)
+    _check(lib().spvar_pticm_sample(problem.handle, R, num_sweeps, _dp(thr), dm + 1, _dp(xthr), dx, icm_from,
+                                    keep_from, K, flags, num_runs, seed, start0, phase, _dp(kept), _dp(kept_e),
+                                    _dp(nkept), _dp(final), _dp(final_e), _stream(stream)), "spvar_pticm_sample")
+    return dict(kept=kept[:, :ntr], kept_e=kept_e[:, :ntr], nkept=nkept[:, :ntr], final_states=final,
+                final_e=final_e)
 
 
 def sample_range(problem, thr_dev, thr_stride, sweep_begin, sweep_end, num_samples, seed, start=0, phase=0,

@@ -1,0 +1,63 @@
+"""GPU parity of the third sampler, PTICM (parallel tempering with
+isoenergetic cluster moves, Sec. III.D; spvar_pticm_sample), against the
+oracle: every run's kept lists (states, energies, counts) and every replica's
+final state and energy identical, bit for bit, for +-1, integer and U_10
+couplers, odd and even temperature counts, and with exchanges or cluster
+moves switched off."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1706_07826_gb300 import instances as I
+
+from gpu_cases import gpu_problem, oracle_problem, with_h
+
+pytestmark = pytest.mark.gpu
+
+CASES = [
+    # name, instance, betas, sweeps, runs, options
+    ("random_h_R6", lambda: I.random_graph(20, 40, 3, jmax=3, hmax=2), np.geomspace(0.2, 2.5, 6), 40, 3, {}),
+    ("chimera_C3_R8", lambda: I.chimera(3, 2140), np.geomspace(0.2, 3.0, 8), 30, 2, {}),
+    ("cubic_L4_R4", lambda: I.cubic3d(4, 2141), np.geomspace(0.3, 3.0, 4), 30, 2, {}),
+    ("cubic_L5_odd_h_R5", lambda: with_h(I.cubic3d(5, 2143), 6, 2), np.geomspace(0.3, 2.0, 5), 25, 2, {}),
+    ("u10_C3_R8", lambda: I.chimera_u10(3, 2142), np.geomspace(0.2, 3.0, 8), 30, 2, {}),
+    ("no_exchange", lambda: I.random_graph(16, 30, 7, jmax=2, hmax=1), np.geomspace(0.3, 2.0, 4), 30, 2,
+     dict(exchange=False)),
+    ("no_icm_keep_all", lambda: I.chimera(2, 2144), np.geomspace(0.3, 2.0, 6), 30, 2,
+     dict(icm=False, keep_from=0)),
+    ("icm_all_keep_top", lambda: I.random_graph(18, 36, 9, jmax=3, hmax=2), np.geomspace(0.2, 2.5, 6), 30, 1,
+     dict(icm_from=0, keep_from=5)),
+    ("one_temperature", lambda: I.random_graph(12, 20, 11, jmax=2, hmax=2), np.array([1.3]), 40, 2, {}),
+]
+
+
+@pytest.mark.parametrize("name,make,betas,T,runs,opt", CASES, ids=[c[0] for c in CASES])
+def test_pticm_parity(cuda_lib, name, make, betas, T, runs, opt):
+    import torch
+    from paper_1706_07826_gb300 import spvar
+    inst = make()
+    op = oracle_problem(inst)
+    g = spvar.pticm_sample(gpu_problem(inst), betas, T, spvar.energy_range(inst), K=10, num_runs=runs, seed=77,
+                           start0=5, phase=1, **opt)
+    torch.cuda.synchronize()
+    g = {k: v.cpu().numpy() for k, v in g.items()}
+    for run in range(runs):
+        ref = O.pticm_sample(op, betas, T, K=10, seed=77, start=5 + run, phase=1, **opt)
+        assert np.array_equal(g["nkept"][run], ref["nkept"]), run
+        for q, nk in enumerate(ref["nkept"]):
+            assert np.array_equal(g["kept_e"][run, q, :nk], ref["kept_e"][q, :nk] + inst.offset), (run, q)
+            states = spvar.unpack_spins(g["kept"][run, q, :nk], inst.n)
+            assert np.array_equal(states, ref["kept"][q, :nk]), (run, q)
+        assert np.array_equal(spvar.unpack_spins(g["final_states"][run], inst.n), ref["final"]), run
+        assert np.array_equal(g["final_e"][run], ref["final_e"] + inst.offset), run
+
+
+def test_pticm_limits(cuda_lib):
+    from paper_1706_07826_gb300 import spvar
+    small = I.random_graph(10, 15, 1, jmax=2, hmax=1)
+    gp = gpu_problem(small)
+    with pytest.raises(spvar.SpvarError):
+        spvar.pticm_sample(gp, np.geomspace(0.1, 3.0, 65), 2, spvar.energy_range(small))   # more than 64 temperatures
+    big = I.cubic3d(13, 3)  # N = 2197 > 2048
+    with pytest.raises(spvar.SpvarError):
+        spvar.pticm_sample(gpu_problem(big), np.geomspace(0.1, 3.0, 4), 2, spvar.energy_range(big))
