@@ -397,6 +397,37 @@ def measure_u10(spvar, torch, flush):
                       "solving) samples, 1000 sweeps, beta 0.1->3.0 geometric (couplers /10), elite 0.1"}
 
 
+def measure_pticm(spvar, torch, flush):
+    """PTICM (Sec. III.D) on a 3D +-J L=10 problem (N = 1000): 304 independent
+    runs (two per SM), 32 inverse temperatures geometric 0.2 -> 3.0, two
+    replicas each, cluster moves and kept lists (K = 10) in the lower half,
+    1000 sweeps.  Attempts count the Metropolis proposals of every replica."""
+    from paper_1706_07826_gb300 import instances as I
+    inst = I.cubic3d(10, 1600)
+    prob = spvar.Problem.from_instance(inst)
+    betas = np.geomspace(0.2, 3.0, 32)
+    T, runs = 1000, 304
+    dx = spvar.energy_range(inst)
+    spvar.pticm_sample(prob, betas, 20, dx, K=10, num_runs=runs, seed=3)
+    torch.cuda.synchronize()
+    flush.add_(1)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("pticm_3d_L10")
+    a.record()
+    out = spvar.pticm_sample(prob, betas, T, dx, K=10, num_runs=runs, seed=4)
+    b.record()
+    torch.cuda.nvtx.range_pop()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b)
+    att = runs * 2 * len(betas) * inst.n * T
+    return {"value": att / (ms / 1000.0), "unit": UNIT, "ms": ms, "runs": runs,
+            "best_kept_energy": int(out["kept_e"][:, :, 0].min().item()),
+            "config": "3D +-J L=10 (N=1000, seed 1600), 304 runs, 32 temperatures (beta 0.2 -> 3.0 geometric) x 2 "
+                      "replicas, Houdayer cluster moves and 10 kept states per replica in the lower half, 1000 "
+                      "sweeps"}
+
+
 def measure_persistence_scaled(spvar, torch):
     """The persistence pass (elite, counts and fixing, fold and compact) at a
     scale where HBM matters: 64 3D +-J problems of N = 8000 in one plan, 2000
@@ -679,6 +710,7 @@ def gpu_arm(args, rank, world):
         extra["serving"] = measure_serving(spvar)
         extra["sqa_chimera_c8"] = measure_sqa(spvar, torch, flush)
         extra["u10_chimera_c8"] = measure_u10(spvar, torch, flush)
+        extra["pticm_3d_L10"] = measure_pticm(spvar, torch, flush)
         extra["persistence_pass_scaled"] = measure_persistence_scaled(spvar, torch)
 
     # roofline of the sweep kernel (integer ALU issue bound)
