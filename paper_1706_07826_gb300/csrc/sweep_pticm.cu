@@ -12,9 +12,8 @@
 //   2. Houdayer's cluster move at every temperature k >= icm_from whose
 //      copies differ somewhere: a warp finds the seed (element
 //      floor(u |D| / 2^32) of the differing set D in index order) with
-//      ballots, then the clusters of all those temperatures grow together,
-//      one neighbour ring per round, until a round adds nothing (at most n
-//      rounds), and both copies flip on them;
+//      ballots, then grows its cluster by breadth-first search from a queue
+//      in shared memory, and both copies flip on the clusters;
 //   3. replica exchange between temperatures k and k + 1 for k = t (mod 2):
 //      the pairs are disjoint, so every decision is taken at once from the
 //      replicas' energies and an integer threshold table, and accepted pairs
@@ -50,27 +49,29 @@ __device__ __forceinline__ uint32_t word0(uint32_t w0, uint32_t y, uint32_t star
     return philox4x32_10(make_uint4(w0, y, 0u, start), k0, k1).x;
 }
 
-// 2E of every replica into E[r] (without offset).  Contains __syncthreads.
+// Energies (without offset) of replicas r0 .. NR - 1 into E[r]: one warp per
+// replica sums s_i (2 h_i + sum_j J_ij s_j) = 2E over its spins.  Contains
+// __syncthreads.
 template <int B>
-__device__ void replica_energies(const DevProb *P, const uint8_t *s8, int NR, int *E2, int *E)
+__device__ void replica_energies(const DevProb *P, const uint8_t *s8, int r0, int NR, int *E)
 {
-    const int tid = threadIdx.x, n = P->n, cap_n = P->cap_n;
-    for (int r = tid; r < NR; r += B) E2[r] = 0;
-    __syncthreads();
-    for (int x = tid; x < NR * n; x += B) {
-        const int r = x / n, p = x - r * n;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, n = P->n, cap_n = P->cap_n;
+    for (int r = r0 + warp; r < NR; r += B / 32) {
         const uint8_t *s = s8 + (size_t)r * n;
-        const uint32_t meta = P->meta[p];
-        const int deg = (int)(meta & 0xFFFFu);
-        int f = 2 * ((int)meta >> 16);
-        for (int d = 0; d < deg; ++d) {
-            const uint32_t e = P->ell[(size_t)d * cap_n + p];
-            f += ((int)e >> 16) * (2 * (int)s[e & 0xFFFFu] - 1);
+        int acc = 0;
+        for (int p = lane; p < n; p += 32) {
+            const uint32_t meta = P->meta[p];
+            const int deg = (int)(meta & 0xFFFFu);
+            int f = 2 * ((int)meta >> 16);
+            for (int d = 0; d < deg; ++d) {
+                const uint32_t e = P->ell[(size_t)d * cap_n + p];
+                f += ((int)e >> 16) * (2 * (int)s[e & 0xFFFFu] - 1);
+            }
+            acc += (2 * (int)s[p] - 1) * f;
         }
-        atomicAdd(&E2[r], (2 * (int)s[p] - 1) * f);
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
+        if (lane == 0) E[r] = acc / 2;
     }
-    __syncthreads();
-    for (int r = tid; r < NR; r += B) E[r] = E2[r] / 2;
     __syncthreads();
 }
 
@@ -78,8 +79,7 @@ template <int B>
 __global__ void __launch_bounds__(B) k_pticm(const PticmArgs A)
 {
     extern __shared__ __align__(16) unsigned char smem_pt[];
-    __shared__ int sE[2 * kPtMaxR], sE2[2 * kPtMaxR], sCnt[kPtMaxR], sSeed[kPtMaxR], sAcc[kPtMaxR];
-    __shared__ int sFlag[3];
+    __shared__ int sE[2 * kPtMaxR], sCnt[kPtMaxR], sSeed[kPtMaxR], sAcc[kPtMaxR];
     __shared__ int s_cptr[kMaxColours + 1];
     __shared__ uint32_t sPack[B / 32][kPtWarpWords];
 
@@ -98,6 +98,7 @@ __global__ void __launch_bounds__(B) k_pticm(const PticmArgs A)
     uint8_t *s8 = smem_pt;                                         // [2R][n]
     uint8_t *cl = s8 + (size_t)NR * n;                             // [nic][n]
     uint32_t *thr_s = reinterpret_cast<uint32_t *>(smem_pt + (((size_t)NR * n + (size_t)nic * n + 15) & ~(size_t)15));
+    uint16_t *queue = reinterpret_cast<uint16_t *>(thr_s + (size_t)R * (dmax + 1));  // [B / 32][n]
 
     for (int c = tid; c <= ncol; c += B) s_cptr[c] = P->cptr[c];
     for (int x = tid; x < R * (dmax + 1); x += B) {
@@ -113,7 +114,7 @@ __global__ void __launch_bounds__(B) k_pticm(const PticmArgs A)
         s8[x] = (uint8_t)(u >> 31);
     }
     __syncthreads();
-    replica_energies<B>(P, s8, NR, sE2, sE);
+    replica_energies<B>(P, s8, 0, NR, sE);
 
     const int nq = (NR + 3) >> 2;
     for (int t = 0; t < T; ++t) {
@@ -150,11 +151,16 @@ __global__ void __launch_bounds__(B) k_pticm(const PticmArgs A)
         }
         // 2. cluster moves at the lower temperatures
         if ((A.flags & 2) && nic > 0) {
-            for (int k = tid; k < nic; k += B) sCnt[k] = 0;
-            __syncthreads();
-            for (int x = tid; x < nic * n; x += B) {
-                const int kk = x / n, p = x - kk * n, k = A.icm_from + kk;
-                if (s8[(size_t)(2 * k) * n + p] != s8[(size_t)(2 * k + 1) * n + p]) atomicAdd(&sCnt[kk], 1);
+            // |D| per temperature: one warp each
+            for (int kk = warp; kk < nic; kk += B / 32) {
+                const int k = A.icm_from + kk;
+                int cnt = 0;
+                for (int base = 0; base < n; base += 32) {
+                    const int p = base + lane;
+                    cnt += __popc(__ballot_sync(0xFFFFFFFFu, p < n && s8[(size_t)(2 * k) * n + p] !=
+                                                                        s8[(size_t)(2 * k + 1) * n + p]));
+                }
+                if (lane == 0) sCnt[kk] = cnt;
             }
             __syncthreads();
             // seeds: element floor(u |D| / 2^32) of D in index order, one warp per temperature
@@ -188,32 +194,51 @@ __global__ void __launch_bounds__(B) k_pticm(const PticmArgs A)
                 if (lane == 0) sSeed[kk] = seedpos;
             }
             __syncthreads();
-            for (int x = tid; x < nic * n; x += B) {
-                const int kk = x / n, p = x - kk * n;
-                cl[x] = (uint8_t)(p == sSeed[kk]);
-            }
-            if (tid < 3) sFlag[tid] = 0;
+            for (int x = tid; x < nic * n; x += B) cl[x] = 0;
             __syncthreads();
-            // grow every cluster by one neighbour ring per round (in place) until a round adds nothing
-            for (int it = 0; it < n; ++it) {
-                if (tid == 0) sFlag[(it + 1) % 3] = 0;
-                for (int x = tid; x < nic * n; x += B) {
-                    const int kk = x / n, p = x - kk * n, k = A.icm_from + kk;
-                    if (cl[x] || sSeed[kk] < 0) continue;
-                    if (s8[(size_t)(2 * k) * n + p] == s8[(size_t)(2 * k + 1) * n + p]) continue;
-                    const int deg = (int)(P->meta[p] & 0xFFFFu);
-                    for (int d = 0; d < deg; ++d) {
-                        const int j = (int)(P->ell[(size_t)d * cap_n + p] & 0xFFFFu);
-                        if (cl[(size_t)kk * n + j]) {
-                            cl[x] = 1;
-                            sFlag[it % 3] = 1;
-                            break;
-                        }
-                    }
+            // each cluster by breadth-first search, one warp per temperature: a step expands up to 32 queued
+            // spins, neighbour slot by neighbour slot; a spin found by several lanes in one slot is queued
+            // once (match), and it is marked before the next slot looks, so the queue never exceeds n
+            for (int kk = warp; kk < nic; kk += B / 32) {
+                const int seedpos = sSeed[kk];
+                if (seedpos < 0) continue;
+                const int k = A.icm_from + kk;
+                const uint8_t *sa = s8 + (size_t)(2 * k) * n, *sb = s8 + (size_t)(2 * k + 1) * n;
+                uint8_t *c = cl + (size_t)kk * n;
+                uint16_t *qu = queue + (size_t)warp * n;
+                if (lane == 0) {
+                    qu[0] = (uint16_t)seedpos;
+                    c[seedpos] = 1;
                 }
-                __syncthreads();
-                if (!sFlag[it % 3]) break;
+                __syncwarp();
+                int head = 0, tail = 1;
+                while (head < tail) {
+                    const int take = min(32, tail - head);
+                    const int v = lane < take ? (int)qu[head + lane] : -1;
+                    const int deg = v >= 0 ? (int)(P->meta[v] & 0xFFFFu) : 0;
+                    int maxdeg = deg;
+                    for (int o = 16; o > 0; o >>= 1) maxdeg = max(maxdeg, __shfl_xor_sync(0xFFFFFFFFu, maxdeg, o));
+                    for (int d = 0; d < maxdeg; ++d) {
+                        int j = -1;
+                        if (d < deg) {
+                            const int cand = (int)(P->ell[(size_t)d * cap_n + v] & 0xFFFFu);
+                            if (sa[cand] != sb[cand] && !c[cand]) j = cand;
+                        }
+                        // one lane per distinct new spin
+                        const uint32_t same = __match_any_sync(0xFFFFFFFFu, j);
+                        const bool first = j >= 0 && (__ffs(same) - 1) == lane;
+                        const uint32_t add = __ballot_sync(0xFFFFFFFFu, first);
+                        if (first) {
+                            qu[tail + __popc(add & ((1u << lane) - 1u))] = (uint16_t)j;
+                            c[j] = 1;
+                        }
+                        tail += __popc(add);
+                        __syncwarp();
+                    }
+                    head += take;
+                }
             }
+            __syncthreads();
             for (int x = tid; x < nic * n; x += B) {
                 if (!cl[x]) continue;
                 const int kk = x / n, p = x - kk * n, k = A.icm_from + kk;
@@ -221,7 +246,7 @@ __global__ void __launch_bounds__(B) k_pticm(const PticmArgs A)
                 s8[(size_t)(2 * k + 1) * n + p] ^= 1u;
             }
             __syncthreads();
-            replica_energies<B>(P, s8, NR, sE2, sE);
+            replica_energies<B>(P, s8, 2 * A.icm_from, NR, sE);  // the replicas the cluster moves touched
         }
         // 3. replica exchange between temperatures k and k + 1, k = t (mod 2)
         if (A.flags & 1) {
@@ -313,7 +338,7 @@ __global__ void __launch_bounds__(B) k_pticm(const PticmArgs A)
 size_t pticm_smem_bytes(int n, int R, int icm_from, int dmax)
 {
     const size_t spins = (2 * (size_t)R * n + (size_t)(R - icm_from) * n + 15) & ~(size_t)15;
-    return spins + 4 * (size_t)R * ((size_t)dmax + 1);
+    return spins + 4 * (size_t)R * ((size_t)dmax + 1) + 2 * (size_t)(256 / 32) * n;  // + one queue per warp
 }
 
 int pticm_max_r() { return kPtMaxR; }
