@@ -79,7 +79,7 @@ template <int B>
 __global__ void __launch_bounds__(B) k_pticm(const PticmArgs A)
 {
     extern __shared__ __align__(16) unsigned char smem_pt[];
-    __shared__ int sE[2 * kPtMaxR], sCnt[kPtMaxR], sSeed[kPtMaxR], sAcc[kPtMaxR];
+    __shared__ int sE[2 * kPtMaxR], sAcc[kPtMaxR];
     __shared__ int s_cptr[kMaxColours + 1];
     __shared__ uint32_t sPack[B / 32][kPtWarpWords];
 
@@ -117,112 +117,137 @@ __global__ void __launch_bounds__(B) k_pticm(const PticmArgs A)
     replica_energies<B>(P, s8, 0, NR, sE);
 
     const int nq = (NR + 3) >> 2;
+    constexpr int NW = B / 32;
+    // Metropolis work split: with at least as many quads (four replicas) as warps a warp owns whole quads for
+    // a sweep and walks the colour classes under warp synchronisation only; with fewer, gq warps share a
+    // quad and a CTA barrier separates the classes
+    const int gq = nq >= NW ? 1 : NW / nq;
+    const int mslot = warp / gq, msub = warp - mslot * gq, nslots = NW / gq;
+    if (A.flags & 2)
+        for (int x = tid; x < nic * n; x += B) cl[x] = 0;  // cluster marks; each search clears its own
     for (int t = 0; t < T; ++t) {
         const uint32_t y = phase_hi | (uint32_t)t;
         // 1. Metropolis sweep of every replica, colour class by colour class
-        for (int c = 0; c < ncol; ++c) {
-            const int lo = s_cptr[c], nc = s_cptr[c + 1] - lo;
-            for (int x = tid; x < nq * nc; x += B) {
-                const int q = x / nc, p = lo + (x - q * nc);
-                const uint4 w = philox4x32_10(make_uint4((uint32_t)P->idx_of_pos[p], y, (uint32_t)q, start), k0, k1);
-                const uint32_t uu[4] = {w.x, w.y, w.z, w.w};
-                const uint32_t meta = P->meta[p];
-                const int deg = (int)(meta & 0xFFFFu), h = (int)meta >> 16;
+        for (int q0 = 0; q0 < nq; q0 += nslots) {
+            const int q = q0 + mslot;
+            const bool mine = mslot < nslots && q < nq;
+            const int nr = min(4, NR - 4 * q);
+            uint8_t *sq = s8 + (size_t)(4 * q) * n;
+            int acc[4] = {0, 0, 0, 0};
+            for (int c = 0; c < ncol; ++c) {
+                if (mine) {
+                    const int hi = s_cptr[c + 1];
+                    for (int p = s_cptr[c] + 32 * msub + lane; p < hi; p += 32 * gq) {
+                        const uint4 w =
+                            philox4x32_10(make_uint4((uint32_t)P->idx_of_pos[p], y, (uint32_t)q, start), k0, k1);
+                        const uint32_t uu[4] = {w.x, w.y, w.z, w.w};
+                        const uint32_t meta = P->meta[p];
+                        const int deg = (int)(meta & 0xFFFFu), h = (int)meta >> 16;
+                        int f[4] = {h, h, h, h};
+                        for (int d = 0; d < deg; ++d) {
+                            const uint32_t e = P->ell[(size_t)d * cap_n + p];
+                            const int j = (int)(e & 0xFFFFu), Jv = (int)e >> 16;
 #pragma unroll
-                for (int rr = 0; rr < 4; ++rr) {
-                    const int r = 4 * q + rr;
-                    if (r >= NR) break;
-                    uint8_t *s = s8 + (size_t)r * n;
-                    int f = h;
-                    for (int d = 0; d < deg; ++d) {
-                        const uint32_t e = P->ell[(size_t)d * cap_n + p];
-                        f += ((int)e >> 16) * (2 * (int)s[e & 0xFFFFu] - 1);
-                    }
-                    const int dE = -2 * (2 * (int)s[p] - 1) * f;
-                    const bool accept =
-                        dE <= 0 || uu[rr] < thr_s[(size_t)(r >> 1) * (dmax + 1) + min(dE, dmax)];
-                    if (accept) {
-                        s[p] ^= 1u;
-                        atomicAdd(&sE[r], dE);
+                            for (int rr = 0; rr < 4; ++rr)
+                                if (rr < nr) f[rr] += Jv * (2 * (int)sq[(size_t)rr * n + j] - 1);
+                        }
+#pragma unroll
+                        for (int rr = 0; rr < 4; ++rr) {
+                            if (rr >= nr) break;
+                            const int r = 4 * q + rr;
+                            const int dE = -2 * (2 * (int)sq[(size_t)rr * n + p] - 1) * f[rr];
+                            const bool accept =
+                                dE <= 0 || uu[rr] < thr_s[(size_t)(r >> 1) * (dmax + 1) + min(dE, dmax)];
+                            if (accept) {
+                                sq[(size_t)rr * n + p] ^= 1u;
+                                acc[rr] += dE;
+                            }
+                        }
                     }
                 }
+                if (gq > 1)
+                    __syncthreads();
+                else
+                    __syncwarp();
             }
-            __syncthreads();
+            if (mine) {
+#pragma unroll
+                for (int rr = 0; rr < 4; ++rr) {
+                    int v = acc[rr];
+                    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+                    if (lane == 0 && rr < nr) atomicAdd(&sE[4 * q + rr], v);
+                }
+            }
         }
-        // 2. cluster moves at the lower temperatures
+        __syncthreads();
+        // 2. cluster moves at the lower temperatures, one warp per temperature: |D|, the seed (element
+        //    floor(u |D| / 2^32) of D in index order), then the cluster by breadth-first search.  A step
+        //    expands up to 32 queued spins, neighbour slot by neighbour slot; a spin found by several lanes in
+        //    one slot is queued once (match) and marked before the next slot looks, so the queue never exceeds
+        //    n.  Expanded spins flip in both copies (membership of D is unchanged by that), and the copies'
+        //    energies change by -+2 (sum over the cluster of h_i a_i plus J_ij a_i a_j over couplers leaving it):
+        //    every neighbour outside the cluster lies outside D
         if ((A.flags & 2) && nic > 0) {
-            // |D| per temperature: one warp each
-            for (int kk = warp; kk < nic; kk += B / 32) {
+            for (int kk = warp; kk < nic; kk += NW) {
                 const int k = A.icm_from + kk;
+                uint8_t *sa = s8 + (size_t)(2 * k) * n, *sb = sa + n;
                 int cnt = 0;
                 for (int base = 0; base < n; base += 32) {
                     const int p = base + lane;
-                    cnt += __popc(__ballot_sync(0xFFFFFFFFu, p < n && s8[(size_t)(2 * k) * n + p] !=
-                                                                        s8[(size_t)(2 * k + 1) * n + p]));
+                    cnt += __popc(__ballot_sync(0xFFFFFFFFu, p < n && sa[p] != sb[p]));
                 }
-                if (lane == 0) sCnt[kk] = cnt;
-            }
-            __syncthreads();
-            // seeds: element floor(u |D| / 2^32) of D in index order, one warp per temperature
-            for (int kk = warp; kk < nic; kk += B / 32) {
-                const int k = A.icm_from + kk, cnt = sCnt[kk];
-                int seedpos = -1;
-                if (cnt > 0) {
-                    const uint32_t u = word0(0xFFFF0000u | (uint32_t)k, y, start, k0, k1);
-                    const int pick = (int)(((uint64_t)u * (uint64_t)cnt) >> 32);
-                    int seen = 0;
-                    for (int base = 0; base < n && seedpos < 0; base += 32) {
-                        const int i = base + lane;
-                        int pos = -1;
-                        bool dif = false;
-                        if (i < n) {
-                            pos = P->pos_of_idx[i];
-                            dif = s8[(size_t)(2 * k) * n + pos] != s8[(size_t)(2 * k + 1) * n + pos];
-                        }
-                        const uint32_t bal = __ballot_sync(0xFFFFFFFFu, dif);
-                        const int c = __popc(bal);
-                        if (pick < seen + c) {
-                            // the (pick - seen)-th set lane
-                            const int want = pick - seen;
-                            const bool mine = dif && __popc(bal & ((1u << lane) - 1u)) == want;
-                            const uint32_t who = __ballot_sync(0xFFFFFFFFu, mine);
-                            seedpos = __shfl_sync(0xFFFFFFFFu, pos, __ffs(who) - 1);
-                        }
-                        seen += c;
+                if (cnt == 0) continue;
+                const uint32_t u = word0(0xFFFF0000u | (uint32_t)k, y, start, k0, k1);
+                const int pick = (int)(((uint64_t)u * (uint64_t)cnt) >> 32);
+                int seedpos = -1, seen = 0;
+                for (int base = 0; base < n && seedpos < 0; base += 32) {
+                    const int i = base + lane;
+                    int pos = -1;
+                    bool dif = false;
+                    if (i < n) {
+                        pos = P->pos_of_idx[i];
+                        dif = sa[pos] != sb[pos];
                     }
+                    const uint32_t bal = __ballot_sync(0xFFFFFFFFu, dif);
+                    const int c = __popc(bal);
+                    if (pick < seen + c) {
+                        // the (pick - seen)-th set lane
+                        const bool hit = dif && __popc(bal & ((1u << lane) - 1u)) == pick - seen;
+                        seedpos = __shfl_sync(0xFFFFFFFFu, pos, __ffs(__ballot_sync(0xFFFFFFFFu, hit)) - 1);
+                    }
+                    seen += c;
                 }
-                if (lane == 0) sSeed[kk] = seedpos;
-            }
-            __syncthreads();
-            for (int x = tid; x < nic * n; x += B) cl[x] = 0;
-            __syncthreads();
-            // each cluster by breadth-first search, one warp per temperature: a step expands up to 32 queued
-            // spins, neighbour slot by neighbour slot; a spin found by several lanes in one slot is queued
-            // once (match), and it is marked before the next slot looks, so the queue never exceeds n
-            for (int kk = warp; kk < nic; kk += B / 32) {
-                const int seedpos = sSeed[kk];
-                if (seedpos < 0) continue;
-                const int k = A.icm_from + kk;
-                const uint8_t *sa = s8 + (size_t)(2 * k) * n, *sb = s8 + (size_t)(2 * k + 1) * n;
-                uint8_t *c = cl + (size_t)kk * n;
+                uint8_t *mk = cl + (size_t)kk * n;
                 uint16_t *qu = queue + (size_t)warp * n;
                 if (lane == 0) {
                     qu[0] = (uint16_t)seedpos;
-                    c[seedpos] = 1;
+                    mk[seedpos] = 1;
                 }
                 __syncwarp();
-                int head = 0, tail = 1;
+                int head = 0, tail = 1, bsum = 0;
                 while (head < tail) {
                     const int take = min(32, tail - head);
                     const int v = lane < take ? (int)qu[head + lane] : -1;
-                    const int deg = v >= 0 ? (int)(P->meta[v] & 0xFFFFu) : 0;
+                    int deg = 0, av = 0;
+                    if (v >= 0) {
+                        const uint32_t meta = P->meta[v];
+                        deg = (int)(meta & 0xFFFFu);
+                        av = 2 * (int)sa[v] - 1;
+                        bsum += ((int)meta >> 16) * av;
+                    }
                     int maxdeg = deg;
                     for (int o = 16; o > 0; o >>= 1) maxdeg = max(maxdeg, __shfl_xor_sync(0xFFFFFFFFu, maxdeg, o));
                     for (int d = 0; d < maxdeg; ++d) {
                         int j = -1;
                         if (d < deg) {
-                            const int cand = (int)(P->ell[(size_t)d * cap_n + v] & 0xFFFFu);
-                            if (sa[cand] != sb[cand] && !c[cand]) j = cand;
+                            const uint32_t e = P->ell[(size_t)d * cap_n + v];
+                            const int cand = (int)(e & 0xFFFFu);
+                            const int ac = sa[cand];
+                            if (ac != sb[cand]) {
+                                if (!mk[cand]) j = cand;
+                            } else {
+                                bsum += ((int)e >> 16) * av * (2 * ac - 1);
+                            }
                         }
                         // one lane per distinct new spin
                         const uint32_t same = __match_any_sync(0xFFFFFFFFu, j);
@@ -230,23 +255,27 @@ __global__ void __launch_bounds__(B) k_pticm(const PticmArgs A)
                         const uint32_t add = __ballot_sync(0xFFFFFFFFu, first);
                         if (first) {
                             qu[tail + __popc(add & ((1u << lane) - 1u))] = (uint16_t)j;
-                            c[j] = 1;
+                            mk[j] = 1;
                         }
                         tail += __popc(add);
                         __syncwarp();
                     }
+                    if (v >= 0) {
+                        sa[v] ^= 1u;
+                        sb[v] ^= 1u;
+                    }
+                    __syncwarp();
                     head += take;
                 }
+                for (int o = 16; o > 0; o >>= 1) bsum += __shfl_xor_sync(0xFFFFFFFFu, bsum, o);
+                if (lane == 0) {
+                    sE[2 * k] -= 2 * bsum;
+                    sE[2 * k + 1] += 2 * bsum;
+                }
+                for (int i = lane; i < tail; i += 32) mk[qu[i]] = 0;
+                __syncwarp();
             }
             __syncthreads();
-            for (int x = tid; x < nic * n; x += B) {
-                if (!cl[x]) continue;
-                const int kk = x / n, p = x - kk * n, k = A.icm_from + kk;
-                s8[(size_t)(2 * k) * n + p] ^= 1u;
-                s8[(size_t)(2 * k + 1) * n + p] ^= 1u;
-            }
-            __syncthreads();
-            replica_energies<B>(P, s8, 2 * A.icm_from, NR, sE);  // the replicas the cluster moves touched
         }
         // 3. replica exchange between temperatures k and k + 1, k = t (mod 2)
         if (A.flags & 1) {

@@ -12,7 +12,9 @@ replicas one by one, or a whole start where that takes seconds.
 - SQA on Chimera C8 (N = 512), 16 slices, 10 starts x (500 + 500) runs, 1000
   sweeps: sampled phase-0 runs (recorded energies);
 - reduced-degeneracy Chimera C8 with biases (U_10, Sec. III.C): one whole
-  start and sampled replicas.
+  start and sampled replicas;
+- PTICM (Sec. III.D) on 3D +-J L = 10, 304 runs x 32 temperatures x 2
+  replicas, 1000 sweeps: two whole runs (kept lists, final states).
 """
 import numpy as np
 import pytest
@@ -141,3 +143,26 @@ def test_sqa_u10_chimera_c8_full_size(cuda_lib):
     for st, r in ((0, 0), (5, 250), (9, 499)):
         _, e, _ = O.sqa_sample(op, ent, P, 1, seed, start=st, phase=0, r0=r)
         assert out.energies[st, 0, r] == e[0] + inst.offset, (st, r)
+
+
+def test_pticm_3d_l10_full_size(cuda_lib):
+    """The PTICM benchmark launch (304 runs, 32 temperatures geometric 0.2 ->
+    3.0, cluster moves and kept lists in the lower half, 1000 sweeps): the
+    first and the last run equal the oracle bit for bit."""
+    import torch
+    from paper_1706_07826_gb300 import spvar
+    inst = I.cubic3d(10, 1600)
+    betas = np.geomspace(0.2, 3.0, 32)
+    T, runs = 1000, 304
+    g = spvar.pticm_sample(gpu_problem(inst), betas, T, spvar.energy_range(inst), K=10, num_runs=runs, seed=4)
+    torch.cuda.synchronize()
+    g = {k: v.cpu().numpy() for k, v in g.items()}
+    op = oracle_problem(inst)
+    for run in (0, runs - 1):
+        ref = O.pticm_sample(op, betas, T, K=10, seed=4, start=run)
+        assert np.array_equal(g["nkept"][run], ref["nkept"]), run
+        for q, nk in enumerate(ref["nkept"]):
+            assert np.array_equal(g["kept_e"][run, q, :nk], ref["kept_e"][q, :nk] + inst.offset), (run, q)
+            assert np.array_equal(spvar.unpack_spins(g["kept"][run, q, :nk], inst.n), ref["kept"][q, :nk]), (run, q)
+        assert np.array_equal(spvar.unpack_spins(g["final_states"][run], inst.n), ref["final"]), run
+        assert np.array_equal(g["final_e"][run], ref["final_e"] + inst.offset), run

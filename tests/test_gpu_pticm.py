@@ -28,6 +28,10 @@ CASES = [
     ("icm_all_keep_top", lambda: I.random_graph(18, 36, 9, jmax=3, hmax=2), np.geomspace(0.2, 2.5, 6), 30, 1,
      dict(icm_from=0, keep_from=5)),
     ("one_temperature", lambda: I.random_graph(12, 20, 11, jmax=2, hmax=2), np.array([1.3]), 40, 2, {}),
+    # at least as many replica quads as warps: each warp owns whole quads for a sweep
+    ("chimera_C3_R16", lambda: I.chimera(3, 2145), np.geomspace(0.2, 3.0, 16), 20, 2, {}),
+    ("random_h_R19_uneven_quads", lambda: I.random_graph(24, 50, 13, jmax=3, hmax=2), np.geomspace(0.2, 3.0, 19),
+     20, 2, {}),
 ]
 
 
