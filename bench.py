@@ -408,7 +408,9 @@ def measure_pticm(spvar, torch, flush):
     betas = np.geomspace(0.2, 3.0, 32)
     T, runs = 1000, 304
     dx = spvar.energy_range(inst)
+    torch.cuda.nvtx.range_push("pticm_3d_L10_short")  # the warm-up launch, 20 sweeps: the case profiles capture
     spvar.pticm_sample(prob, betas, 20, dx, K=10, num_runs=runs, seed=3)
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     flush.add_(1)
     torch.cuda.synchronize()

@@ -5,22 +5,27 @@
 // One CTA runs one PTICM run (start = start0 + blockIdx.x).  R inverse
 // temperatures, two replicas (copies) each, replica r = 2k + c; every replica's
 // spins live in shared memory as bytes (0/1) by position.  A sweep:
-//   1. a Metropolis sweep of every replica at its temperature: items
-//      (quad, spin) of one colour class at a time, one Philox block per item
-//      for its four replicas (the counter and word of the SA sweep), the
-//      thresholds of temperature k = r / 2 staged in shared memory;
+//   1. a Metropolis sweep of every replica at its temperature: a warp takes a
+//      quad of replicas (one Philox block per spin gives their four words, the
+//      counter and word of the SA sweep) through the colour classes; with at
+//      least as many quads as warps it owns the quad for the whole sweep and
+//      only warp synchronisation separates the classes, otherwise several
+//      warps share a quad between CTA barriers.  Energy changes add up in
+//      registers and reach the replica energies once per sweep;
 //   2. Houdayer's cluster move at every temperature k >= icm_from whose
-//      copies differ somewhere: a warp finds the seed (element
-//      floor(u |D| / 2^32) of the differing set D in index order) with
-//      ballots, then grows its cluster by breadth-first search from a queue
-//      in shared memory, and both copies flip on the clusters;
+//      copies differ somewhere, one warp per temperature: |D| and the seed
+//      (element floor(u |D| / 2^32) of the differing set D in index order) by
+//      ballots, then the cluster by breadth-first search from a queue in
+//      shared memory; expanded spins flip in both copies, and the copies'
+//      energies change by the boundary sum of the cluster (the couplers that
+//      leave it end outside D), so no energy pass follows;
 //   3. replica exchange between temperatures k and k + 1 for k = t (mod 2):
 //      the pairs are disjoint, so every decision is taken at once from the
 //      replicas' energies and an integer threshold table, and accepted pairs
 //      swap their states;
 //   4. a warp per tracked replica offers its state, bit-packed in index
 //      order, to the replica's list of the K lowest distinct states seen.
-// Every wait is a __syncthreads reached by the whole CTA.
+// Every wait is a CTA or warp barrier that all of its threads reach.
 #include "sweep_common.cuh"
 
 namespace spvar {
