@@ -227,8 +227,9 @@ int spvar_sqa_sample(const spvar_problem *p, int32_t num_sweeps, int32_t P, cons
  * (R - keep_from)] (zeroed here), final_states [num_runs][2R][ceil(n/32)],
  * final_e [num_runs][2R] (with offset).  Asynchronous on stream.  Errors:
  * EINVAL (bad sizes or flags, missing buffers), ELIMIT (R > 64, K >
- * SPVAR_PTICM_MAX_KEEP, n > 2048, or the replicas do not fit in shared
- * memory), ECUDA. */
+ * SPVAR_PTICM_MAX_KEEP, n > 2048, or the 2Rn + 4R(dmax + 1) + 32n bytes of
+ * replicas, thresholds and search queues exceed the shared memory of one
+ * CTA), ECUDA. */
 int spvar_pticm_sample(const spvar_problem *p, int32_t R, int32_t num_sweeps, const uint32_t *thr,
                        int32_t thr_stride, const uint32_t *xthr, int32_t dx, int32_t icm_from, int32_t keep_from,
                        int32_t K, int32_t flags, int32_t num_runs, uint64_t seed, uint32_t start0, uint32_t phase,

@@ -606,7 +606,7 @@ int spvar_pticm_sample(const spvar_problem *p, int32_t R, int32_t num_sweeps, co
     if (num_runs == 0) return SPVAR_OK;
     if ((num_sweeps > 0 && !thr) || !final_e || !nkept || !kept_e || (H.n > 0 && (!final_states || !kept)))
         return SPVAR_EINVAL;
-    const size_t smem = pticm_smem_bytes(H.n, R, icm_from, H.dmax);
+    const size_t smem = pticm_smem_bytes(H.n, R, H.dmax);
     if (smem > (size_t)device_smem_optin()) return SPVAR_ELIMIT;
     cudaStream_t st = as_stream(stream);
     const size_t ntr = 2 * (size_t)(R - keep_from);

@@ -297,7 +297,7 @@ int pm1q_max_active_blocks(int block, int maxd, size_t smem);
 
 // PTICM sampler (sweep_pticm.cu): one CTA per run, every replica's spins in
 // shared memory.
-size_t pticm_smem_bytes(int n, int R, int icm_from, int dmax);
+size_t pticm_smem_bytes(int n, int R, int dmax);
 int pticm_max_r();
 int pticm_max_n();
 cudaError_t launch_pticm(const DevProb *prob, const uint32_t *thr, int thr_stride, const uint32_t *xthr, int dx,

@@ -4,7 +4,8 @@
 //
 // One CTA runs one PTICM run (start = start0 + blockIdx.x).  R inverse
 // temperatures, two replicas (copies) each, replica r = 2k + c; every replica's
-// spins live in shared memory as bytes (0/1) by position.  A sweep:
+// spins live in shared memory as bytes by position (bit 0 the spin; bit 1 of
+// copy 0 marks cluster members during a cluster move).  A sweep:
 //   1. a Metropolis sweep of every replica at its temperature: a warp takes a
 //      quad of replicas (one Philox block per spin gives their four words, the
 //      counter and word of the SA sweep) through the colour classes; with at
@@ -33,6 +34,7 @@ namespace spvar {
 namespace {
 
 constexpr int kPtMaxR = 64;     // most temperatures
+constexpr int kPtBlock = 512;   // threads per run: two runs (32 warps) per SM when shared memory allows
 constexpr int kPtWarpWords = 64;  // packed words of one state a warp keeps (n <= 2048)
 
 struct PticmArgs {
@@ -81,7 +83,7 @@ __device__ void replica_energies(const DevProb *P, const uint8_t *s8, int r0, in
 }
 
 template <int B>
-__global__ void __launch_bounds__(B) k_pticm(const PticmArgs A)
+__global__ void __launch_bounds__(B, 2) k_pticm(const PticmArgs A)
 {
     extern __shared__ __align__(16) unsigned char smem_pt[];
     __shared__ int sE[2 * kPtMaxR], sAcc[kPtMaxR];
@@ -101,8 +103,7 @@ __global__ void __launch_bounds__(B) k_pticm(const PticmArgs A)
     const uint32_t phase_hi = A.phase << kSweepBits;
 
     uint8_t *s8 = smem_pt;                                         // [2R][n]
-    uint8_t *cl = s8 + (size_t)NR * n;                             // [nic][n]
-    uint32_t *thr_s = reinterpret_cast<uint32_t *>(smem_pt + (((size_t)NR * n + (size_t)nic * n + 15) & ~(size_t)15));
+    uint32_t *thr_s = reinterpret_cast<uint32_t *>(smem_pt + (((size_t)NR * n + 15) & ~(size_t)15));
     uint16_t *queue = reinterpret_cast<uint16_t *>(thr_s + (size_t)R * (dmax + 1));  // [B / 32][n]
 
     for (int c = tid; c <= ncol; c += B) s_cptr[c] = P->cptr[c];
@@ -128,8 +129,6 @@ __global__ void __launch_bounds__(B) k_pticm(const PticmArgs A)
     // quad and a CTA barrier separates the classes
     const int gq = nq >= NW ? 1 : NW / nq;
     const int mslot = warp / gq, msub = warp - mslot * gq, nslots = NW / gq;
-    if (A.flags & 2)
-        for (int x = tid; x < nic * n; x += B) cl[x] = 0;  // cluster marks; each search clears its own
     for (int t = 0; t < T; ++t) {
         const uint32_t y = phase_hi | (uint32_t)t;
         // 1. Metropolis sweep of every replica, colour class by colour class
@@ -199,7 +198,7 @@ __global__ void __launch_bounds__(B) k_pticm(const PticmArgs A)
                 int cnt = 0;
                 for (int base = 0; base < n; base += 32) {
                     const int p = base + lane;
-                    cnt += __popc(__ballot_sync(0xFFFFFFFFu, p < n && sa[p] != sb[p]));
+                    cnt += __popc(__ballot_sync(0xFFFFFFFFu, p < n && ((sa[p] ^ sb[p]) & 1)));
                 }
                 if (cnt == 0) continue;
                 const uint32_t u = word0(0xFFFF0000u | (uint32_t)k, y, start, k0, k1);
@@ -211,7 +210,7 @@ __global__ void __launch_bounds__(B) k_pticm(const PticmArgs A)
                     bool dif = false;
                     if (i < n) {
                         pos = P->pos_of_idx[i];
-                        dif = sa[pos] != sb[pos];
+                        dif = (sa[pos] ^ sb[pos]) & 1;
                     }
                     const uint32_t bal = __ballot_sync(0xFFFFFFFFu, dif);
                     const int c = __popc(bal);
@@ -222,11 +221,10 @@ __global__ void __launch_bounds__(B) k_pticm(const PticmArgs A)
                     }
                     seen += c;
                 }
-                uint8_t *mk = cl + (size_t)kk * n;
                 uint16_t *qu = queue + (size_t)warp * n;
                 if (lane == 0) {
                     qu[0] = (uint16_t)seedpos;
-                    mk[seedpos] = 1;
+                    sa[seedpos] |= 2u;
                 }
                 __syncwarp();
                 int head = 0, tail = 1, bsum = 0;
@@ -237,7 +235,7 @@ __global__ void __launch_bounds__(B) k_pticm(const PticmArgs A)
                     if (v >= 0) {
                         const uint32_t meta = P->meta[v];
                         deg = (int)(meta & 0xFFFFu);
-                        av = 2 * (int)sa[v] - 1;
+                        av = 2 * (int)(sa[v] & 1u) - 1;
                         bsum += ((int)meta >> 16) * av;
                     }
                     int maxdeg = deg;
@@ -248,10 +246,10 @@ __global__ void __launch_bounds__(B) k_pticm(const PticmArgs A)
                             const uint32_t e = P->ell[(size_t)d * cap_n + v];
                             const int cand = (int)(e & 0xFFFFu);
                             const int ac = sa[cand];
-                            if (ac != sb[cand]) {
-                                if (!mk[cand]) j = cand;
+                            if ((ac ^ sb[cand]) & 1) {
+                                if (!(ac & 2)) j = cand;
                             } else {
-                                bsum += ((int)e >> 16) * av * (2 * ac - 1);
+                                bsum += ((int)e >> 16) * av * (2 * (ac & 1) - 1);
                             }
                         }
                         // one lane per distinct new spin
@@ -260,7 +258,7 @@ __global__ void __launch_bounds__(B) k_pticm(const PticmArgs A)
                         const uint32_t add = __ballot_sync(0xFFFFFFFFu, first);
                         if (first) {
                             qu[tail + __popc(add & ((1u << lane) - 1u))] = (uint16_t)j;
-                            mk[j] = 1;
+                            sa[j] |= 2u;
                         }
                         tail += __popc(add);
                         __syncwarp();
@@ -277,7 +275,7 @@ __global__ void __launch_bounds__(B) k_pticm(const PticmArgs A)
                     sE[2 * k] -= 2 * bsum;
                     sE[2 * k + 1] += 2 * bsum;
                 }
-                for (int i = lane; i < tail; i += 32) mk[qu[i]] = 0;
+                for (int i = lane; i < tail; i += 32) sa[qu[i]] &= 1u;
                 __syncwarp();
             }
             __syncthreads();
@@ -369,10 +367,10 @@ __global__ void __launch_bounds__(B) k_pticm(const PticmArgs A)
 
 }  // namespace
 
-size_t pticm_smem_bytes(int n, int R, int icm_from, int dmax)
+size_t pticm_smem_bytes(int n, int R, int dmax)
 {
-    const size_t spins = (2 * (size_t)R * n + (size_t)(R - icm_from) * n + 15) & ~(size_t)15;
-    return spins + 4 * (size_t)R * ((size_t)dmax + 1) + 2 * (size_t)(256 / 32) * n;  // + one queue per warp
+    const size_t spins = (2 * (size_t)R * n + 15) & ~(size_t)15;
+    return spins + 4 * (size_t)R * ((size_t)dmax + 1) + 2 * (size_t)(kPtBlock / 32) * n;  // + one queue per warp
 }
 
 int pticm_max_r() { return kPtMaxR; }
@@ -403,11 +401,11 @@ cudaError_t launch_pticm(const DevProb *prob, const uint32_t *thr, int thr_strid
     A.nkept = nkept;
     A.final_bits = final_bits;
     A.final_e = final_e;
-    void *k = reinterpret_cast<void *>(k_pticm<256>);
+    void *k = reinterpret_cast<void *>(k_pticm<kPtBlock>);
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     void *args[] = {&A};
-    return cudaLaunchKernel(k, dim3(runs), dim3(256), args, smem, st);
+    return cudaLaunchKernel(k, dim3(runs), dim3(kPtBlock), args, smem, st);
 }
 
 }  // namespace spvar

@@ -65,3 +65,6 @@ def test_pticm_limits(cuda_lib):
     big = I.cubic3d(13, 3)  # N = 2197 > 2048
     with pytest.raises(spvar.SpvarError):
         spvar.pticm_sample(gpu_problem(big), np.geomspace(0.1, 3.0, 4), 2, spvar.energy_range(big))
+    mid = I.cubic3d(12, 5)  # N = 1728: 64 temperatures of replicas and queues need more than one CTA's shared memory
+    with pytest.raises(spvar.SpvarError):
+        spvar.pticm_sample(gpu_problem(mid), np.geomspace(0.1, 3.0, 64), 2, spvar.energy_range(mid))
