@@ -6,8 +6,8 @@ seen at each replica of the lower half of the temperatures).
   constant temperature, bit for bit (same random words and decisions);
 - the cluster move is Houdayer's: the flipped set equals the connected
   component of the seed among the spins where the two replicas differ
-  (scipy), both replicas flip on it, and the pair's total energy is
-  unchanged;
+  (scipy), both replicas flip on it, the pair's total energy is unchanged,
+  and each copy's energy moves by -+2 times the cluster's boundary sum;
 - the whole chain (Metropolis, cluster moves, exchanges) leaves each
   temperature's Boltzmann distribution in place: chi-square of the final
   states of many independent runs against enumeration, at both temperatures;
@@ -78,6 +78,18 @@ def test_cluster_move_is_houdayers():
         assert np.array_equal(np.flatnonzero(b2 != b), cluster)
         assert np.array_equal(a2[cluster], b[cluster]) and np.array_equal(b2[cluster], a[cluster])
         assert _E(inst, a2)[0] + _E(inst, b2)[0] == _E(inst, a)[0] + _E(inst, b)[0]
+        # each copy's change is -+2 (sum over the cluster of h_i a_i and of J_ij a_i a_j over the couplers
+        # leaving it): every such coupler ends outside D, where the copies agree
+        inC = np.zeros(inst.n, bool)
+        inC[cluster] = True
+        ai = a.astype(np.int64)
+        bnd = int((inst.h[cluster] * ai[cluster]).sum())
+        for i, j, w in zip(inst.ei, inst.ej, inst.J):
+            if inC[i] != inC[j]:
+                assert a[i] == b[i] and not inC[i] or a[j] == b[j] and not inC[j]
+                bnd += int(w) * int(ai[i]) * int(ai[j])
+        assert _E(inst, a2)[0] - _E(inst, a)[0] == -2 * bnd
+        assert _E(inst, b2)[0] - _E(inst, b)[0] == 2 * bnd
     with pytest.raises(ValueError):
         same = np.ones(inst.n, np.int8)
         O.icm_move(p, same, same, 0)
