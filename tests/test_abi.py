@@ -126,3 +126,21 @@ def test_problem_create_validation_errors(L):
     # bad scale / negative n
     assert _create(L, 2, [0, 1, 2], [1, 0], [1, 1], [0, 0], scale=0) == -1
     assert _create(L, -1, [0], [], [], []) == -1
+
+
+def test_problem_create_without_device_reports_enomem(L):
+    """A valid problem passes host validation; with no CUDA device the device
+    allocation fails and the call returns SPVAR_ENOMEM with no handle (the
+    allocation-failure path, reached without a GPU)."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    inst = I.cubic3d(3, 1)
+    from paper_1706_07826_gb300 import spvar
+    rp, col, val = spvar.csr_from_edges(inst.n, inst.ei, inst.ej, inst.J)
+    out = ctypes.c_void_p(1234)
+    h = np.zeros(inst.n, np.int32)
+    rc = L.spvar_problem_create(inst.n, _ptr(np.ascontiguousarray(rp, np.int32)),
+                                _ptr(np.ascontiguousarray(col, np.int32)), _ptr(np.ascontiguousarray(val, np.int32)),
+                                _ptr(h), 0, 1, None, ctypes.byref(out))
+    assert rc == -3 and not out.value
