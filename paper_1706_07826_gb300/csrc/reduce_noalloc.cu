@@ -153,7 +153,12 @@ extern "C" int spvar_reduce_noalloc(const spvar_problem *p, const int8_t *fixed,
     int32_t *scratch = nullptr;
     const int rc = scratch_address(&scratch);
     if (rc != SPVAR_OK) return rc;
-    k_reduce_csr<<<1, kBigBlock, 0, reinterpret_cast<cudaStream_t>(stream)>>>(
-        S->dev, fixed, row_ptr, col, val, h, offset, old_of_new, n_out, scratch);
-    return cudaGetLastError() == cudaSuccess ? SPVAR_OK : SPVAR_ECUDA;
+    // launched through cudaLaunchKernel so that its own status is checked, not an
+    // earlier error left pending on this thread by unrelated work
+    const DevProb *src = S->dev;
+    void *args[] = {(void *)&src, (void *)&fixed, (void *)&row_ptr, (void *)&col, (void *)&val, (void *)&h,
+                    (void *)&offset, (void *)&old_of_new, (void *)&n_out, (void *)&scratch};
+    const cudaError_t e = cudaLaunchKernel(reinterpret_cast<const void *>(k_reduce_csr), dim3(1), dim3(kBigBlock),
+                                           args, 0, reinterpret_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? SPVAR_OK : SPVAR_ECUDA;
 }
