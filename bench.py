@@ -1,14 +1,24 @@
 """Benchmark: SA spin-flip attempts/s and SPVAR TTS99 of Multi-start SPVAR
-(Alg. 2) on a Chimera C8 +-J problem (N = 512, 1472 couplers, h = 0):
-10 starts x (1000 fixing + 1000 solving) samples, 1000 sweeps, geometric
-beta 0.1 -> 3.0, elite 10 %, fixing threshold 1.
+(Alg. 2), batched against plain form, on one GB300.
 
-One step = one full Multi-start SPVAR run (every start: sample, elite,
-persistence, fold/compact, solving sample) through the C-ABI library.
-``value`` is attempts/s of the batched (persistent + CUDA graph) form with the
-problem resident on the device; the plain one-launch-per-start form is timed
-beside it; ``e2e`` goes through spvar_problem_create + spvar_solve with host
-buffers.  ``--impl reference`` times the oracle on the host cores instead.
+The headline workload is a Chimera C8 +-J problem (N = 512, 1472 couplers,
+h = 0): 10 starts x (1000 fixing + 1000 solving) samples, 1000 sweeps,
+geometric beta 0.1 -> 3.0, elite 10 %, fixing threshold 1.  One step = one
+full Multi-start SPVAR run (every start: sample, elite, persistence,
+fold/compact, solving sample) through the C-ABI library.  ``value`` is
+attempts/s of the batched form (persistent sweep + CUDA graph) with the
+problem resident on the device; ``plain`` is the one-launch-per-start form;
+``e2e`` goes through spvar_problem_create + spvar_solve with host buffers.
+
+Every sweep kernel's roofline divides its algorithmic integer operations per
+second by the measured issue ceiling of this GPU (spvar_measure_issue_rate:
+lop3 and mad.lo chains on both integer pipes), and the wide-multiply ceiling
+(mul.wide chains) bounds the Philox part.  TTS99 (Sec. III.A R99 in wall time)
+is measured on a 3D +-J L = 12 problem at 1000 sweeps, where the per-start
+success rate lies strictly between 0 and 1, against a best-known energy from
+independent long runs (PTICM at 10^4 sweeps and SA at 2 x 10^4 sweeps), for
+SA alone, SPVAR batched, SPVAR plain and the oracle solving on the host cores.
+``--impl reference`` times the oracle on the host cores instead.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
@@ -29,18 +39,28 @@ sys.path.insert(0, ROOT)
 
 METRIC = "SA spin-flip attempts/s (SPVAR TTS99 beside it), batched vs plain form"
 UNIT = "spin-flip attempts/s"
-WORKLOAD = dict(workload="Chimera C8 +-J (N=512, 1472 couplers, h=0, instance seed 1200); Multi-start SPVAR: "
-                         "10 starts x (1000 fixing + 1000 solving) samples, 1000 sweeps, beta 0.1->3.0 geometric, "
-                         "elite 0.1, fixing threshold 1.0, zero-bias reference-spin canonicalisation",
-                instance="chimera(M=8, seed=1200)", num_starts=10, fixing_sample_size=1000,
-                solving_sample_size=1000, num_sweeps=1000, beta0=0.1, beta1=3.0, elite_threshold=0.1)
+WORKLOAD = dict(workload="Chimera C8 +-J N=512 h=0 (seed 1200): 10 starts x (1000+1000) samples, 1000 sweeps, "
+                         "beta 0.1->3, elite 0.1")
 INSTANCE_SEED = 1200
 RUN_SEED0 = 42
 L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
-SMS, LANES_PER_SM = 152, 128  # GB300: 152 SMs x 4 SMSPs x 32 lanes issue one int op per lane per clock
 PHILOX_OPS_PER_ATTEMPT = 15  # 10 rounds x (2 wide multiplies + 2 three-input xors + 2 key adds) / 4 replicas
 ACCEPT_OPS_PER_ATTEMPT = 3   # dE, dE <= 0 test, threshold compare
-ALU_PEAK_TOPS = SMS * LANES_PER_SM * 2070e6 / 1e12  # at the maximum SM clock
+WIDE_PER_ATTEMPT = 15 / 4    # wide multiplies per attempt left after the kernels hoist the item-constant ones
+# TTS99 workload: 3D +-J L = 12 (one of the uneven batch's sizes), Table II's sample split
+TTS_L, TTS_SEED, TTS_T, TTS_STARTS, TTS_S, TTS_ELITE = 12, 1612, 1000, 200, 250, 0.2
+TTS_RUN_SEED = 1700
+
+
+def r4(x):
+    """Four significant digits (keeps the line short enough for the driver's tail)."""
+    if isinstance(x, float):
+        return float("%.4g" % x) if math.isfinite(x) else None
+    if isinstance(x, dict):
+        return {k: r4(v) for k, v in x.items()}
+    if isinstance(x, (list, tuple)):
+        return [r4(v) for v in x]
+    return x
 
 
 def _instance():
@@ -119,6 +139,20 @@ def _oracle_worker(args):
     return time.perf_counter() - t0
 
 
+def _oracle_solve_worker(start):
+    """One Multi-start SPVAR start of the TTS99 workload, solved by the oracle."""
+    sys.path.insert(0, ROOT)
+    from oracle import oracle as O
+    from paper_1706_07826_gb300 import instances as I
+    inst = I.cubic3d(TTS_L, TTS_SEED)
+    p = O.csr_from_edges(inst.n, inst.ei, inst.ej, inst.J, inst.h)
+    thr = O.thresholds(O.beta_geometric(TTS_T, 0.1, 3.0), O.dmax(p), 1)
+    t0 = time.perf_counter()
+    r = O.solve(p, thr, TTS_RUN_SEED, num_starts=1, start0=start, fixing_sample_size=TTS_S,
+                solving_sample_size=TTS_S, elite_threshold=TTS_ELITE)
+    return time.perf_counter() - t0, int(r.best_e[0])
+
+
 def cpu_oracle_rate(replicas_per_core, cores=None, pool=None):
     """Oracle SA sample of the workload's first phase, replicas split across
     the host cores (one process each).  Returns (attempts/s, cores, seconds)."""
@@ -137,6 +171,14 @@ def cpu_oracle_rate(replicas_per_core, cores=None, pool=None):
             pool.join()
     attempts = cores * replicas_per_core * 512 * 1000
     return attempts / dt, cores, dt
+
+
+def cpu_oracle_tts(pool, cores):
+    """The oracle solving one TTS99 start per host core at once: wall time and
+    each start's best energy."""
+    t0 = time.perf_counter()
+    res = pool.map(_oracle_solve_worker, list(range(cores)))
+    return time.perf_counter() - t0, [b for _, b in res]
 
 
 def reference_arm(args, rank, world):
@@ -168,8 +210,34 @@ def reference_arm(args, rank, world):
 
 
 # ------------------------------------------------------------ GPU arm
-def _flush(buf):
-    buf.add_(1)
+class Peaks:
+    """Measured integer issue ceilings of this GPU (thread-level ops/s)."""
+
+    def __init__(self, spvar):
+        self.rate = {}
+        for form in range(6):
+            self.rate[form], _ = spvar.measure_issue_rate(form, 20000)
+        self.issue = self.rate[3]  # lop3 + mad.lo on alternate chains: both integer pipes busy
+        self.wide = self.rate[4]
+
+    def roof(self, attempts, sweep_ms, ops_per_attempt):
+        """Roofline of a sweep kernel from its attempts and event-timed duration."""
+        if not sweep_ms or sweep_ms <= 0:
+            return None
+        aps = attempts / (sweep_ms / 1000.0)
+        achieved = aps * ops_per_attempt / 1e12
+        wide_cap = self.wide / WIDE_PER_ATTEMPT
+        return {"bound": "alu", "achieved": achieved, "peak": self.issue / 1e12, "unit": "Tops/s",
+                "frac": achieved * 1e12 / self.issue, "ops_per_attempt": ops_per_attempt,
+                "wide_mul_cap": wide_cap, "wide_frac": aps / wide_cap}
+
+    def summary(self):
+        from paper_1706_07826_gb300 import spvar
+        return {spvar.ISSUE_FORMS[f]: self.rate[f] for f in range(6)}
+
+
+def ops_per_attempt(inst, extra=0.0):
+    return PHILOX_OPS_PER_ATTEMPT + 2.0 * inst.m / max(inst.n, 1) + ACCEPT_OPS_PER_ATTEMPT + extra
 
 
 def run_form(spvar, torch, plan, K, W, seeds0, flush, profile=False, nvtx="c2"):
@@ -185,7 +253,7 @@ def run_form(spvar, torch, plan, K, W, seeds0, flush, profile=False, nvtx="c2"):
     out = plan.alloc_outputs(True)
     best = []
     for k in range(K):
-        _flush(flush)
+        flush.add_(1)
         torch.cuda.nvtx.range_push(nvtx)
         evs[k][0].record(stream)
         plan.run(seeds0 + 100 + k, out=out, device=True)
@@ -232,176 +300,125 @@ def kernel_source_hash():
         h.update(text[start:text.index("};", start) + 2].encode())
     return h.hexdigest()[:16]
 
-def measure_uneven(spvar, torch, flush):
-    """c4: 64 3D +-J instances, L uniform in 6..12, 2000 samples per phase,
-    one persistent launch per phase for all of them (batched) vs plain."""
-    from paper_1706_07826_gb300 import instances as I
-    insts = I.uneven_batch(64, 6, 12, seed=1400)
-    probs = [spvar.Problem.from_instance(x) for x in insts]
-    out, best = {}, {}
-    for form, name in ((spvar.FORM_BATCHED, "batched"), (spvar.FORM_PLAIN, "plain")):
-        prm = spvar.make_params(num_starts=1, fixing_sample_size=2000, solving_sample_size=2000, num_sweeps=1000,
-                                elite_threshold=0.1, form=form)
-        plan = spvar.Plan(probs, prm)
-        seeds = [1401 + i for i in range(len(probs))]
-        o0 = plan.run(seeds, device=True)
-        torch.cuda.synchronize()
-        best0 = o0.best_energy.cpu().numpy()
-        flush.add_(1)
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.nvtx.range_push("c4_" + name)
-        a.record()
-        o = plan.run([x + 7 for x in seeds], device=True)
-        b.record()
-        torch.cuda.nvtx.range_pop()
-        torch.cuda.synchronize()
-        best[name] = (best0, o.best_energy.cpu().numpy())
-        att, _ = plan.stats()
-        ms = a.elapsed_time(b)
-        out[name] = {"value": att / (ms / 1000.0), "ms": ms, "attempts": att, "sweep_shape": plan.shape()}
-        if name == "batched":
-            # kernel time of the sweeps (a separate, profiled run of the same seeds: it waits for every phase)
-            plan.set_profiling(True)
-            torch.cuda.nvtx.range_push("c4_batched_profiled")
-            plan.run([x + 7 for x in seeds], device=True)
-            torch.cuda.nvtx.range_pop()
-            sweep_ms, sweep_n = plan.sweep_time()
-            att_prof, _ = plan.stats()
-            plan.set_profiling(False)
-            mean_deg = sum(x.m for x in insts) * 2.0 / sum(x.n for x in insts)
-            ops = PHILOX_OPS_PER_ATTEMPT + mean_deg + ACCEPT_OPS_PER_ATTEMPT
-            achieved = att_prof * ops / (sweep_ms / 1000.0) / 1e12
-            out[name]["roofline"] = {"bound": "alu", "achieved": achieved, "peak": ALU_PEAK_TOPS, "unit": "Tops/s",
-                                     "frac": achieved / ALU_PEAK_TOPS, "ops_per_attempt": ops,
-                                     "sweep_launches": sweep_n, "sweep_ms": sweep_ms}
+
+def timed_plan(spvar, torch, plan, seeds, flush, name):
+    """One untimed run, one timed run (CUDA events), one profiled run (sweep
+    kernel time); returns (attempts/s, ms, attempts, sweep ms, launches, out)."""
+    plan.run([s + 7919 for s in seeds], device=True)
+    torch.cuda.synchronize()
+    flush.add_(1)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push(name)
+    a.record()
+    out = plan.run(seeds, device=True)
+    b.record()
+    torch.cuda.nvtx.range_pop()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b)
+    att, _ = plan.stats()
+    plan.set_profiling(True)
+    torch.cuda.nvtx.range_push(name + "_profiled")
+    plan.run(seeds, device=True)
+    torch.cuda.nvtx.range_pop()
+    sweep_ms, sweep_n = plan.sweep_time()
+    plan.set_profiling(False)
+    return att / (ms / 1000.0), ms, att, sweep_ms, sweep_n, out
+
+
+def measure_config(spvar, torch, flush, peaks, probs, insts, kw, seeds, name, plain=True):
+    """Batched (and plain) form of one configuration with the batched sweep
+    kernel's roofline."""
+    res = {}
+    for form, fname in ((spvar.FORM_BATCHED, "batched"), (spvar.FORM_PLAIN, "plain")):
+        if fname == "plain" and not plain:
+            continue
+        plan = spvar.Plan(probs, spvar.make_params(form=form, **kw))
+        aps, ms, att, sweep_ms, sweep_n, out = timed_plan(spvar, torch, plan, seeds, flush, name + "_" + fname)
+        if fname == "batched":
+            res["value"] = aps
+            mean_deg_ops = sum(ops_per_attempt(x) * x.n for x in insts) / sum(x.n for x in insts)
+            roof = peaks.roof(att, sweep_ms, mean_deg_ops)
+            if roof:
+                res["frac"] = roof["frac"]
+                res["wide_frac"] = roof["wide_frac"]
+            res["kernel"] = plan.shape()["kernel"]
+        else:
+            res["plain"] = aps
+            res["speedup"] = res["value"] / aps
         plan.close()
-    out["speedup_batched_over_plain"] = out["batched"]["value"] / out["plain"]["value"]
-    # success metrics (Sec. III.A) over the 64 problems of the timed run, against the best energy of
-    # it and of the untimed run with other seeds (both forms give the same results for the same seeds)
-    from paper_1706_07826_gb300 import metrics as MT
-    first, timed = best["batched"]
-    known = np.minimum(first, timed)
-    out["fraction_solved"] = MT.fraction_solved(timed, known)
-    out["median_residual_pct"] = float(np.median(MT.residual(timed, known)))
-    out["e_known_kind"] = "best energy of two independent runs (not proved optimal)"
-    out["config"] = ("64 3D +-J instances, L uniform in 6..12 (N 216..1728, seed 1400), 1 start each, "
-                     "2000 fixing + 2000 solving samples, 1000 sweeps, elite 0.1")
+    return res
+
+
+def measure_c1_c3(spvar, torch, flush, peaks):
+    """c1 (3D L=4, ISPVAR until every spin is fixed, 1 start, 256 samples,
+    1000 sweeps) and c3 (weak-strong Chimera C12 x100, 32 starts, 250 + 250
+    samples), batched and plain."""
+    from paper_1706_07826_gb300 import instances as I
+    out = {}
+    c1 = I.cubic3d(4, 1100)
+    r = measure_config(spvar, torch, flush, peaks, [spvar.Problem.from_instance(c1)], [c1],
+                       dict(num_starts=1, fixing_sample_size=256, solving_sample_size=0, num_sweeps=1000,
+                            elite_threshold=0.1, iterate=True, max_fix_phases=64), [2], "c1")
+    out["c1"] = r
+    c3 = I.weak_strong(12, 1300)
+    r = measure_config(spvar, torch, flush, peaks, [spvar.Problem.from_instance(c3)], [c3],
+                       dict(num_starts=32, fixing_sample_size=250, solving_sample_size=250, num_sweeps=1000,
+                            elite_threshold=0.2), [2], "c3")
+    out["c3"] = r
     return out
 
 
-def measure_sqa(spvar, torch, flush):
-    """Second sampler (simulated quantum annealing, discrete-time path integral):
-    Multi-start SPVAR on Chimera C8 with SQA in every phase, 10 starts x
-    (500 fixing + 500 solving) runs, 16 Trotter slices, 1000 sweeps, beta 3,
-    transverse field 3 -> 0.01.  An attempt is one spin-slice update; the
-    roofline is the SQA sweep kernel's against the integer issue peak."""
+def measure_uneven(spvar, torch, flush, peaks):
+    """c4: 64 3D +-J instances, L uniform in 6..12, 2000 + 2000 samples, 1000
+    sweeps, one persistent launch per phase for all of them (batched) vs plain."""
+    from paper_1706_07826_gb300 import instances as I
+    insts = I.uneven_batch(64, 6, 12, seed=1400)
+    probs = [spvar.Problem.from_instance(x) for x in insts]
+    seeds = [1401 + i for i in range(len(insts))]
+    return measure_config(spvar, torch, flush, peaks, probs, insts,
+                          dict(num_starts=1, fixing_sample_size=2000, solving_sample_size=2000, num_sweeps=1000,
+                               elite_threshold=0.1), seeds, "c4")
+
+
+def measure_sweeps_per_launch(spvar, torch, flush, peaks):
+    """The autotuner's sweeps-per-launch axis, measured on the headline
+    workload: one sweep launch per phase against four (each resuming from the
+    states the previous one wrote)."""
+    inst = _instance()
+    prob = spvar.Problem.from_instance(inst)
+    out = {}
+    for spl, name in ((1000, "one"), (250, "four")):
+        prm = _params(spvar.FORM_BATCHED)
+        prm.sweeps_per_launch = spl
+        plan = spvar.Plan([prob], prm)
+        aps, ms, att, sweep_ms, sweep_n, _ = timed_plan(spvar, torch, plan, [77], flush, "spl_" + name)
+        out[name] = aps
+        plan.close()
+    return out
+
+
+def measure_sqa(spvar, torch, flush, peaks):
+    """Second sampler (SQA, discrete-time path integral): Multi-start SPVAR on
+    Chimera C8 with SQA in every phase, 10 starts x (500 + 500) runs, 16 Trotter
+    slices, 1000 sweeps, beta 3, transverse field 3 -> 0.01.  An attempt is one
+    spin-slice update (two slice neighbours added to the local field)."""
     from paper_1706_07826_gb300 import instances as I
     inst = I.chimera(8, 1100)
     prob = spvar.Problem.from_instance(inst)
-    P = 16
     prm = spvar.make_params(num_starts=10, fixing_sample_size=500, solving_sample_size=500, num_sweeps=1000,
-                            elite_threshold=0.1, sampler=spvar.SAMPLER_SQA, sqa_slices=P, sqa_beta=3.0,
+                            elite_threshold=0.1, sampler=spvar.SAMPLER_SQA, sqa_slices=16, sqa_beta=3.0,
                             sqa_gamma0=3.0, sqa_gamma1=0.01)
     plan = spvar.Plan([prob], prm)
-    plan.run([2299], device=True)
-    torch.cuda.synchronize()
-    ms_tot, att_tot, best = 0.0, 0, []
-    for k in range(3):
-        flush.add_(1)
-        torch.cuda.synchronize()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.nvtx.range_push("sqa_c8")
-        a.record()
-        o = plan.run([2300 + k], device=True)
-        b.record()
-        torch.cuda.nvtx.range_pop()
-        torch.cuda.synchronize()
-        ms_tot += a.elapsed_time(b)
-        att, _ = plan.stats()
-        att_tot += att
-        best.append(int(o.best_energy.min().item()))
-    # kernel time of the sweeps (a separate, profiled run: it waits for every phase)
-    plan.set_profiling(True)
-    torch.cuda.nvtx.range_push("sqa_c8_profiled")
-    plan.run([2303], device=True)
-    torch.cuda.nvtx.range_pop()
-    sweep_ms, sweep_n = plan.sweep_time()
-    att_prof, _ = plan.stats()
-    shape = plan.shape()
+    aps, ms, att, sweep_ms, sweep_n, out = timed_plan(spvar, torch, plan, [2300], flush, "sqa_c8")
     plan.close()
-    ops = PHILOX_OPS_PER_ATTEMPT + 2 * inst.m / inst.n + 2 + ACCEPT_OPS_PER_ATTEMPT  # + two slice neighbours
-    achieved = (att_prof / max(sweep_n, 1)) * ops / (sweep_ms / max(sweep_n, 1) / 1000.0) / 1e12
-    return {"value": att_tot / (ms_tot / 1000.0), "unit": "spin-slice update attempts/s", "ms_per_step": ms_tot / 3,
-            "best_energy": min(best), "sweep_shape": shape,
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": ALU_PEAK_TOPS, "unit": "Tops/s",
-                         "frac": achieved / ALU_PEAK_TOPS, "ops_per_attempt": ops,
-                         "ms_per_launch": sweep_ms / max(sweep_n, 1)},
-            "config": "Chimera C8 +-J (N=512, seed 1100), 10 starts x (500 fixing + 500 solving) SQA runs, "
-                      "16 Trotter slices, 1000 sweeps, beta 3.0, transverse field 3.0 -> 0.01 linear, elite 0.1"}
-
-
-def _hbm_peak_gbs():
-    """Measured copy bandwidth of this GPU pool (GB/s), or the recipe's fallback."""
-    try:
-        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-            return float(json.load(f)["hbm_gbs"]), "measured"
-    except (OSError, KeyError, ValueError):
-        return 6800.0, "fallback"
-
-
-def measure_u10(spvar, torch, flush):
-    """Reduced-degeneracy Chimera C8 with biases (the U_10 class of Sec. III.C:
-    couplers in {-10..10} without 0, biases in {-10..10}) with c2's parameters:
-    10 starts x (1000 + 1000) samples, 1000 sweeps, elite 0.1.  Also the mean
-    fraction of variables the fixing phase removes (the paper reports more
-    than 80 % on this class)."""
-    from paper_1706_07826_gb300 import instances as I
-    inst = I.chimera_u10(8, 2500)
-    prob = spvar.Problem.from_instance(inst)
-    prm = spvar.make_params(num_starts=10, fixing_sample_size=1000, solving_sample_size=1000, num_sweeps=1000,
-                            elite_threshold=0.1)
-    plan = spvar.Plan([prob], prm)
-    plan.run([2599], device=True)
-    torch.cuda.synchronize()
-    ms_tot, att_tot, fixed = 0.0, 0, []
-    for k in range(3):
-        flush.add_(1)
-        torch.cuda.synchronize()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.nvtx.range_push("u10_c8")
-        a.record()
-        o = plan.run([2600 + k], device=True)
-        b.record()
-        torch.cuda.nvtx.range_pop()
-        torch.cuda.synchronize()
-        ms_tot += a.elapsed_time(b)
-        att, _ = plan.stats()
-        att_tot += att
-        fixed += [1.0 - x / inst.n for x in o.nfree[:, 1].cpu().tolist()]
-    plan.set_profiling(True)
-    torch.cuda.nvtx.range_push("u10_c8_profiled")
-    plan.run([2603], device=True)
-    torch.cuda.nvtx.range_pop()
-    sweep_ms, sweep_n = plan.sweep_time()
-    att_prof, _ = plan.stats()
-    shape = plan.shape()
-    plan.close()
-    ops = PHILOX_OPS_PER_ATTEMPT + 2 * inst.m / inst.n + ACCEPT_OPS_PER_ATTEMPT
-    achieved = att_prof * ops / (sweep_ms / 1000.0) / 1e12
-    return {"value": att_tot / (ms_tot / 1000.0), "unit": UNIT, "ms_per_step": ms_tot / 3, "sweep_shape": shape,
-            "fixed_fraction_mean": float(np.mean(fixed)),
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": ALU_PEAK_TOPS, "unit": "Tops/s",
-                         "frac": achieved / ALU_PEAK_TOPS, "ops_per_attempt": ops,
-                         "ms_per_launch": sweep_ms / max(sweep_n, 1)},
-            "config": "Chimera C8 U_10 couplers and biases (N=512, seed 2500), 10 starts x (1000 fixing + 1000 "
-                      "solving) samples, 1000 sweeps, beta 0.1->3.0 geometric (couplers /10), elite 0.1"}
+    roof = peaks.roof(att, sweep_ms, ops_per_attempt(inst, 2.0))
+    return {"value": aps, "frac": roof["frac"] if roof else None, "best": int(out.best_energy.min().item())}
 
 
 def measure_pticm(spvar, torch, flush):
-    """PTICM (Sec. III.D) on a 3D +-J L=10 problem (N = 1000): 304 independent
-    runs (two per SM), 32 inverse temperatures geometric 0.2 -> 3.0, two
-    replicas each, cluster moves and kept lists (K = 10) in the lower half,
-    1000 sweeps.  Attempts count the Metropolis proposals of every replica."""
+    """PTICM (Sec. III.D) on a 3D +-J L=10 problem: 304 independent runs, 32
+    inverse temperatures geometric 0.2 -> 3.0, two replicas each, cluster
+    moves and kept lists (K = 10) in the lower half, 1000 sweeps."""
     from paper_1706_07826_gb300 import instances as I
     inst = I.cubic3d(10, 1600)
     prob = spvar.Problem.from_instance(inst)
@@ -423,11 +440,16 @@ def measure_pticm(spvar, torch, flush):
     torch.cuda.synchronize()
     ms = a.elapsed_time(b)
     att = runs * 2 * len(betas) * inst.n * T
-    return {"value": att / (ms / 1000.0), "unit": UNIT, "ms": ms, "runs": runs,
-            "best_kept_energy": int(out["kept_e"][:, :, 0].min().item()),
-            "config": "3D +-J L=10 (N=1000, seed 1600), 304 runs, 32 temperatures (beta 0.2 -> 3.0 geometric) x 2 "
-                      "replicas, Houdayer cluster moves and 10 kept states per replica in the lower half, 1000 "
-                      "sweeps"}
+    return {"value": att / (ms / 1000.0), "best": int(out["kept_e"][:, :, 0].min().item())}
+
+
+def _hbm_peak_gbs():
+    """Measured copy bandwidth of this GPU pool (GB/s), or the recipe's fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
 
 
 def measure_persistence_scaled(spvar, torch):
@@ -450,7 +472,6 @@ def measure_persistence_scaled(spvar, torch):
     plan.set_profiling(True)
     out = plan.run([x + 1 for x in seeds], device=False)
     post_ms = plan.post_time()
-    sweep_ms, _ = plan.sweep_time()
     plan.close()
     k = int(np.ceil(0.1 * S))
     total = 0
@@ -467,117 +488,19 @@ def measure_persistence_scaled(spvar, torch):
         total += 8 * S
     peak, kind = _hbm_peak_gbs()
     gbs = total / (post_ms / 1000.0) / 1e9
-    return {"bound": "hbm", "achieved": gbs, "peak": peak, "peak_kind": kind, "unit": "GB/s", "frac": gbs / peak,
-            "bytes": total, "post_ms": post_ms, "sweep_ms": sweep_ms,
-            "note": "one launch per kernel for all 64 problems and both phases; a fold/compact is one CTA per "
-                    "problem, so 64 SMs stream the CSRs",
-            "config": "64 3D +-J L=20 problems (N=8000, 24000 couplers each, seeds 1700..1763), 1 start each, "
-                      "2000 + 2000 samples, 20 sweeps (short anneal: the pass does not depend on it), elite 0.1"}
+    return {"gbs": gbs, "frac": gbs / peak, "peak": kind, "bytes": total, "ms": post_ms}
 
 
-def measure_small_configs(spvar, torch):
-    """c1 (3D L=4, ISPVAR until every spin is fixed, 1 start, 256 samples) and
-    c3 (weak-strong Chimera C12 x100, 32 starts, 250 + 250 samples), batched and plain."""
-    from paper_1706_07826_gb300 import instances as I
-    out = {}
-    cases = {
-        "c1_cubic_L4_ispvar": (I.cubic3d(4, 1100), dict(num_starts=1, fixing_sample_size=256, solving_sample_size=0,
-                                                       num_sweeps=1000, elite_threshold=0.1, iterate=True,
-                                                       max_fix_phases=64)),
-        "c3_weak_strong_C12": (I.weak_strong(12, 1300), dict(num_starts=32, fixing_sample_size=250,
-                                                             solving_sample_size=250, num_sweeps=1000,
-                                                             elite_threshold=0.2)),
-    }
-    for name, (inst, kw) in cases.items():
-        prob = spvar.Problem.from_instance(inst)
-        res = {}
-        for form, fname in ((spvar.FORM_BATCHED, "batched"), (spvar.FORM_PLAIN, "plain")):
-            plan = spvar.Plan([prob], spvar.make_params(form=form, **kw))
-            plan.run(1, device=True)
-            torch.cuda.synchronize()
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record()
-            o = plan.run(2, device=True)
-            b.record()
-            torch.cuda.synchronize()
-            att, phases = plan.stats()
-            ms = a.elapsed_time(b)
-            res[fname] = {"value": att / (ms / 1000.0), "ms": ms, "phases": phases,
-                          "best_energy": int(o.best_energy.min().item()), "sweep_shape": plan.shape()}
-            plan.close()
-        res["speedup_batched_over_plain"] = res["batched"]["value"] / res["plain"]["value"]
-        out[name] = res
-    return out
-
-
-def measure_method_variants(spvar, torch):
-    """Sec. III.D-style comparison on a 3D +-J L=10 instance (N = 1000), 20
-    starts x 500 samples per start as in Table II, 5000 sweeps, elite 0.1:
-    plain SA (500 samples per start, no fixing) against Multi-start SPVAR,
-    + component boosting, + tree pre-processing, + both, and the paper's
-    zero-bias split with the correlation step.  Success = a start's best
-    energy reaches the best energy any variant found."""
-    from paper_1706_07826_gb300 import instances as I
-    inst = I.cubic3d(10, 1600)
-    prob = spvar.Problem.from_instance(inst)
-    T, starts = 5000, 20
-    beta = spvar.beta_geometric(T, 0.1, 3.0)
-    thr = spvar.thresholds(beta, prob.info().dmax, 1)
-    thr_d = spvar.thresholds_device(thr)
-    out = {}
-    # plain SA: 500 independent samples per start
-    bests, ms_sum, att = [], 0.0, 0
-    for st in range(starts):
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record()
-        _, e = spvar.sample(prob, thr_d, thr.shape[1], T, 500, 1601, st, 0)
-        b.record()
-        torch.cuda.synchronize()
-        ms_sum += a.elapsed_time(b)
-        att += 500 * inst.n * T
-        bests.append(int(e.min().item()))
-    out["sa"] = {"best": bests, "attempts_per_s": att / (ms_sum / 1000.0)}
-    base = dict(fixing_sample_size=250, solving_sample_size=250, elite_threshold=0.1)
-    # the paper's zero-bias setting: 40 % of 500 samples for the correlation step, the rest halved;
-    # elite 0.2 and correlation elite 0.3 (its 3D spin-glass parameters)
-    paper = dict(corr_sample_size=200, corr_elite_threshold=0.3, fixing_sample_size=150, solving_sample_size=150,
-                 elite_threshold=0.2)
-    for name, kw in (("spvar", base), ("spvar_boost", dict(base, component_boost=True)),
-                     ("spvar_tree", dict(base, tree_preprocess=True)),
-                     ("spvar_boost_tree", dict(base, component_boost=True, tree_preprocess=True)),
-                     ("spvar_corr_paper_split", paper)):
-        plan = spvar.Plan([prob], spvar.make_params(num_starts=starts, num_sweeps=T, **kw))
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record()
-        o = plan.run(1601, device=False)
-        b.record()
-        torch.cuda.synchronize()
-        att, _ = plan.stats()
-        last = np.asarray(o.nphases) - 1
-        out[name] = {"best": [int(x) for x in o.best_energy], "attempts_per_s": att / (a.elapsed_time(b) / 1000.0),
-                     "free_spins_solving_phase_mean": float(np.mean(o.nfree[np.arange(starts), last]))}
-        plan.close()
-    e_best = min(min(v["best"]) for v in out.values())
-    for v in out.values():
-        v["p_success"] = float(np.mean([x == e_best for x in v["best"]]))
-        v["best_mean"] = float(np.mean(v["best"]))
-        del v["best"]
-    out["e_best_found"] = e_best
-    out["config"] = ("3D +-J L=10 (N=1000, seed 1600), 20 starts x (250 fixing + 250 solving) samples, 5000 sweeps, "
-                     "elite 0.1, fixing threshold 1, reference-spin canonicalisation; spvar_corr_paper_split = "
-                     "200 correlation (elite 0.3) + 150 fixing (elite 0.2) + 150 solving samples; "
-                     "SA = 500 samples per start")
-    return out
-
-
-def measure_serving(spvar, count=12):
+def measure_serving(spvar, peaks, count=12):
     """c5: Poisson arrivals of 3D +-J instances, L in 8..20, through the
-    continuous-batching server (background engine): p50/p99 latency and
-    attempts/s.  The rate is 0.7 x the capacity measured on two requests."""
+    continuous-batching server (background engine, 500-sweep steps): p50/p99
+    latency, attempts/s and the sweep kernel's roofline.  The arrival rate is
+    0.7 x the capacity measured on two saturating requests."""
     from paper_1706_07826_gb300 import instances as I
     prm = spvar.make_params(num_starts=20, fixing_sample_size=250, solving_sample_size=250, num_sweeps=5000,
                             elite_threshold=0.2, sweep_kernel=spvar.SWEEP_PM1)
-    srv = spvar.Server(prm, 8 << 30, max_n=8000, max_nnz=48000, max_degree=6, max_dmax=12, max_requests=32)
+    srv = spvar.Server(prm, 8 << 30, max_n=8000, max_nnz=48000, max_degree=6, max_dmax=12, max_requests=32,
+                       sweeps_per_step=500)
     srv.start()
     cal = [I.cubic3d(14, 1590 + i) for i in range(2)]
     t0 = time.perf_counter()
@@ -588,6 +511,7 @@ def measure_serving(spvar, count=12):
     mean_att = 20 * 500 * 5000 * np.mean([L ** 3 for L in range(8, 21)])
     rate = 0.7 * cap_attempts / mean_att
     arrivals, insts = I.poisson_stream(count, rate, 8, 20, seed=1500)
+    ms0, _ = srv.sweep_time()
     t0 = time.perf_counter()
     ids = []
     for ta, inst in zip(arrivals, insts):
@@ -598,21 +522,85 @@ def measure_serving(spvar, count=12):
     infos = [srv.info(i, timeout=1200.0) for i in ids]
     t_end = time.perf_counter()
     srv.stop()
+    ms1, _ = srv.sweep_time()
     lat = np.array([i.latency_s for i in infos])
     att = sum(i.attempts for i in infos)
     srv.close()
-    return {"value": att / (t_end - t0), "unit": UNIT, "requests": count, "rate_per_s": rate,
-            "latency_p50_s": float(np.percentile(lat, 50)), "latency_p99_s": float(np.percentile(lat, 99)),
-            "queue_p50_s": float(np.median([i.queue_s for i in infos])),
-            "config": "Poisson arrivals (0.7 x measured capacity) of 3D +-J instances, L uniform in 8..20 "
-                      "(N <= 8000), 20 starts x (250 + 250) samples, 5000 sweeps, elite 0.2, budget 8 GB"}
+    ops = sum(ops_per_attempt(x) * x.n for x in insts) / sum(x.n for x in insts)
+    roof = peaks.roof(att, ms1 - ms0, ops)
+    return {"value": att / (t_end - t0), "capacity": cap_attempts, "rate": rate,
+            "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+            "frac": roof["frac"] if roof else None}
 
 
-def tts99(p, seconds_per_start):
-    if p <= 0:
-        return None
-    starts = 1.0 if p >= 1 else math.log(0.01) / math.log(1 - p)
-    return starts * seconds_per_start
+def measure_tts99(spvar, torch, flush, peaks, oracle_tts):
+    """TTS99 (Sec. III.A: R99 in wall time) on 3D +-J L = 12 (N = 1728) at
+    1000 sweeps, 200 starts x (250 + 250) samples, elite 0.2, where the
+    per-start success rate is strictly between 0 and 1.  E_known = the lowest
+    energy of independent long runs (PTICM, 152 runs at 10^4 sweeps; SA, 4000
+    samples at 2 x 10^4 sweeps): best known, not proved.  SA alone draws 500
+    samples per start (the same sample budget).  Each form's p comes from its
+    own starts (plain: other seeds)."""
+    from paper_1706_07826_gb300 import instances as I
+    from paper_1706_07826_gb300 import metrics as MT
+    inst = I.cubic3d(TTS_L, TTS_SEED)
+    prob = spvar.Problem.from_instance(inst)
+    dmax = prob.info().dmax
+    # independent best-known energy
+    pt = spvar.pticm_sample(prob, np.geomspace(0.2, 3.0, 32), 10000, spvar.energy_range(inst), K=10, num_runs=152,
+                            seed=77)
+    thr_l = spvar.thresholds(spvar.beta_geometric(20000, 0.1, 3.0), dmax, 1)
+    _, e_l = spvar.sample(prob, spvar.thresholds_device(thr_l), thr_l.shape[1], 20000, 4000, 99, 0, 0)
+    torch.cuda.synchronize()
+    e_known = min(int(pt["kept_e"][:, :, 0].min().item()), int(e_l.min().item()))
+    out = {"e_known": e_known}
+    att_start = 2 * TTS_S * TTS_T * inst.n  # upper bound: the solving phase anneals the reduced problem
+    # SA alone: 500 samples per start
+    thr = spvar.thresholds(spvar.beta_geometric(TTS_T, 0.1, 3.0), dmax, 1)
+    thr_d = spvar.thresholds_device(thr)
+    spvar.sample(prob, thr_d, thr.shape[1], TTS_T, 2 * TTS_S, 5, 0, 0)
+    torch.cuda.synchronize()
+    flush.add_(1)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    es = [spvar.sample(prob, thr_d, thr.shape[1], TTS_T, 2 * TTS_S, TTS_RUN_SEED, st, 0)[1]
+          for st in range(TTS_STARTS)]
+    b.record()
+    torch.cuda.synchronize()
+    best_sa = [int(e.min().item()) for e in es]
+    p = MT.fraction_solved(best_sa, e_known)
+    s99 = MT.starts99(p)
+    sec = a.elapsed_time(b) / 1000.0 / TTS_STARTS
+    out["sa"] = {"p": p, "s": s99 * sec if s99 else None}
+    best_b = None
+    for form, name, seed in ((spvar.FORM_BATCHED, "batched", TTS_RUN_SEED), (spvar.FORM_PLAIN, "plain",
+                                                                              TTS_RUN_SEED + 1)):
+        plan = spvar.Plan([prob], spvar.make_params(num_starts=TTS_STARTS, fixing_sample_size=TTS_S,
+                                                    solving_sample_size=TTS_S, num_sweeps=TTS_T,
+                                                    elite_threshold=TTS_ELITE, form=form))
+        aps, ms, att, sweep_ms, sweep_n, o = timed_plan(spvar, torch, plan, [seed], flush, "tts_" + name)
+        plan.close()
+        best = o.best_energy.cpu().numpy()
+        p = MT.fraction_solved(best, e_known)
+        s99 = MT.starts99(p)
+        sec = ms / 1000.0 / TTS_STARTS
+        out[name] = {"p": p, "s": s99 * sec if s99 else None}
+        if name == "batched":
+            best_b = best
+            att_start = att / TTS_STARTS
+            p_b = p
+            if s99:
+                # the same starts at the measured issue ceiling (sweep only)
+                out["roof_s"] = s99 * att_start * ops_per_attempt(inst) / peaks.issue
+                out["roof_frac"] = out["roof_s"] / out[name]["s"]
+    if oracle_tts:
+        wall, best_o = oracle_tts
+        n = len(best_o)
+        s99 = MT.starts99(p_b)
+        # the oracle computes exactly what the GPU does: its starts' results equal the batched run's
+        out["oracle"] = {"s": s99 * wall / n if s99 else None, "cores": n,
+                         "same_as_gpu": bool(np.array_equal(np.asarray(best_o), best_b[:n]))}
+    return out
 
 
 def gpu_arm(args, rank, world):
@@ -622,20 +610,28 @@ def gpu_arm(args, rank, world):
     if args.build:
         B.build()
     dev = int(os.environ.get("LOCAL_RANK", "0"))
+
+    cpu, oracle_tts = None, None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        # before any GPU work: spawned oracle processes on the host cores
+        R = args.cpu_replicas
+        cores = os.cpu_count() or 1
+        pool = mp.get_context("spawn").Pool(cores)
+        pool.map(_oracle_worker, [(0, 1)] * cores)
+        rate, cores, dt = cpu_oracle_rate(R, cores, pool)
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": "headline phase 0: %d replicas x 512 spins x 1000 sweeps, %d per core, %.1f s"
+                         % (cores * R, R, dt)}
+        if not args.no_extra:
+            oracle_tts = cpu_oracle_tts(pool, cores)
+        pool.close()
+        pool.join()
+
     torch.cuda.set_device(dev)
     dist = None
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", dev))
-
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        # before any GPU work: spawned oracle processes on the host cores
-        R = args.cpu_replicas
-        rate, cores, dt = cpu_oracle_rate(R)
-        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": "oracle SA sample of the first phase (start 0, phase 0): %d replicas x 512 spins x 1000 "
-                         "sweeps (%d per core, one process per core, %.1f s wall)" % (cores * R, R, dt)}
 
     inst = _instance()
     seed_base = RUN_SEED0
@@ -643,6 +639,8 @@ def gpu_arm(args, rank, world):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
     K, W = args.steps, args.warmup
 
+    with ClockSampler(dev) as clk_peak:
+        peaks = Peaks(spvar)
     plan_b = spvar.Plan([prob], _params(spvar.FORM_BATCHED, rank))
     plan_p = spvar.Plan([prob], _params(spvar.FORM_PLAIN, rank))
 
@@ -656,9 +654,9 @@ def gpu_arm(args, rank, world):
         tb, att_b, best_b, _, out_b = run_form(spvar, torch, plan_b, K, W, seed_base, flush, nvtx="c2_batched")
     barrier()
     # profiled pass: same runs, sweep kernel timed with events on the launch stream
-    _, att_prof, _, (sweep_ms, sweep_n), _ = run_form(spvar, torch, plan_b, max(3, K // 5), 1, seed_base, flush,
-                                                       profile=True, nvtx="c2_batched_profiled")
     Kp = max(3, K // 5)
+    _, att_prof, _, (sweep_ms, sweep_n), _ = run_form(spvar, torch, plan_b, Kp, 1, seed_base, flush, profile=True,
+                                                       nvtx="c2_batched_profiled")
     tp, att_p, best_p, _, out_p = run_form(spvar, torch, plan_p, Kp, 1, seed_base, flush, nvtx="c2_plain")
     barrier()
 
@@ -669,28 +667,16 @@ def gpu_arm(args, rank, world):
         dist.all_reduce(n_b, op=dist.ReduceOp.SUM)
     value = n_b.item() / (t_b.item() / 1000.0)
     plain_value = sum(att_p) / (tp / 1000.0)
-
-    # TTS99 (Sec. III.A R99 with wall time): p = fraction of starts whose
-    # recorded energies reach the best energy known for the instance
-    from paper_1706_07826_gb300 import distributed as D
-    local_best = out_b.best_energy.cpu().numpy()
     if dist:
-        e_glob, all_best = D.combine_best(local_best, device=torch.device("cuda", dev))
-        e_known = min(e_glob, min(best_p))
-    else:
-        all_best = local_best
-        e_known = min(min(best_b), min(best_p))
-    hit = list(all_best <= e_known)
-    p = D.success_rate(all_best, e_known)
-    tts_b = tts99(p, tb / 1000.0 / K / 10)
-    tts_p = tts99(p, tp / 1000.0 / Kp / 10)
+        from paper_1706_07826_gb300 import distributed as D
+        D.combine_best(out_b.best_energy.cpu().numpy(), device=torch.device("cuda", dev))
 
     # e2e through the public API with host buffers
     rp, col, val = spvar.csr_from_edges(inst.n, inst.ei, inst.ej, inst.J)
     prm = _params(spvar.FORM_BATCHED, rank)
     h2d = rp.nbytes + col.nbytes + val.nbytes + inst.h.nbytes + 1000 * 13 * 4
     e2e_times, e2e_att = [], []
-    for k in range(max(3, K // 5) + 1):
+    for k in range(Kp + 1):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         pr = spvar.Problem.create(inst.n, rp, col, val, inst.h)
@@ -706,62 +692,47 @@ def gpu_arm(args, rank, world):
 
     extra = {}
     if rank == 0 and world == 1 and not args.no_extra:
-        extra.update(measure_small_configs(spvar, torch))
-        extra["method_variants_3d_L10"] = measure_method_variants(spvar, torch)
-        extra["uneven_batch"] = measure_uneven(spvar, torch, flush)
-        extra["serving"] = measure_serving(spvar)
-        extra["sqa_chimera_c8"] = measure_sqa(spvar, torch, flush)
-        extra["u10_chimera_c8"] = measure_u10(spvar, torch, flush)
-        extra["pticm_3d_L10"] = measure_pticm(spvar, torch, flush)
-        extra["persistence_pass_scaled"] = measure_persistence_scaled(spvar, torch)
+        extra["tts99"] = measure_tts99(spvar, torch, flush, peaks, oracle_tts)
+        extra.update(measure_c1_c3(spvar, torch, flush, peaks))
+        extra["c4"] = measure_uneven(spvar, torch, flush, peaks)
+        extra["c5"] = measure_serving(spvar, peaks)
+        extra["sqa"] = measure_sqa(spvar, torch, flush, peaks)
+        extra["pticm"] = measure_pticm(spvar, torch, flush)
+        extra["persist"] = measure_persistence_scaled(spvar, torch)
+        extra["spl"] = measure_sweeps_per_launch(spvar, torch, flush, peaks)
 
-    # roofline of the sweep kernel (integer ALU issue bound)
-    mean_deg = 2 * inst.m / inst.n
-    ops_per_attempt = PHILOX_OPS_PER_ATTEMPT + mean_deg + ACCEPT_OPS_PER_ATTEMPT
+    # roofline of the headline sweep kernel (integer issue bound)
+    opa = ops_per_attempt(inst)
     att_per_launch = sum(att_prof) / max(sweep_n, 1)
     ms_per_launch = sweep_ms / max(sweep_n, 1)
-    achieved = att_per_launch * ops_per_attempt / (ms_per_launch / 1000.0) / 1e12
+    roof = peaks.roof(att_per_launch, ms_per_launch, opa)
+    shape = plan_b.shape()
     cs = clk.summary()
-    peak = SMS * LANES_PER_SM * 2070e6 / 1e12
-    att_per_start = value / world * (tb / 1000.0 / K) / 10  # attempts of one start (both phases)
     if cpu:
         cpu["per_core"] = cpu["value"] / cpu["cores"]
-        cpu["tts99_s"] = tts99(p, att_per_start / cpu["value"])  # all cores, starts run one after another
-    shape = plan_b.shape()
     if rank != 0:
         return
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
         "ms_per_step": tb / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "int32", "data": "synthetic",
-        "config": dict(WORKLOAD, form="batched (persistent sweep + CUDA graph per phase)",
-                       l2="256 MB buffer written between timed steps", parallelism="starts sharded per rank"
-                       if world > 1 else "single GPU", sweep_shape=shape),
-        "plain": {"value": plain_value, "unit": UNIT, "ms_per_step": tp / Kp, "steps": Kp,
-                  "speedup_batched_over_plain": value / world / plain_value},
-        "tts99": {"p_success_per_start": p, "e_best_known": int(e_known), "e_known_kind": "best found by the runs "
-                  "of this benchmark (not proved optimal)", "batched_s": tts_b, "plain_s": tts_p,
-                  "starts_measured": len(hit),
-                  # the same starts at the integer issue peak (the pass and the copies are ~0.4 %)
-                  "roofline_s": tts99(p, att_per_start * ops_per_attempt / (peak * 1e12)),
-                  "roofline_frac": (tts99(p, att_per_start * ops_per_attempt / (peak * 1e12)) / tts_b)
-                  if tts_b else None},
+        "config": dict(WORKLOAD, form="batched", l2="256 MB written between steps",
+                       parallelism="starts sharded per rank" if world > 1 else "single GPU", sweep_shape=shape),
+        "roofline": dict(roof, traffic=profiled_traffic(shape["kernel"]), kernel="k_sweep_pm1",
+                         ms_per_launch=ms_per_launch, peak_kind="measured issue probe"),
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-                "api": "spvar_problem_create + spvar_solve (host buffers, plan built per call)",
-                "ms_per_step": 1000 * statistics.mean(e2e_times)},
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
-                     "traffic": profiled_traffic(shape["kernel"]), "kernel": "k_sweep (SA colour-class sweep)",
-                     "ops_per_attempt": ops_per_attempt, "attempts_per_launch": att_per_launch,
-                     "ms_per_launch": ms_per_launch,
-                     "peak_note": "152 SMs x 128 int32 lanes x 2070 MHz (one warp instruction per SMSP per clock)"},
-        # per run: slot init, then per phase (2) the six phase kernels and the loop-condition kernel
-        "gpu_launches": K * (1 + 2 * (6 + 1)),
+                "api": "problem_create+solve", "ms_per_step": 1000 * statistics.mean(e2e_times)},
+        # per run: slot init, then per sweep launch of each of the two phases the six phase kernels
+        # (plan, sweep, elite, count/fix, fold/compact, active count) and the loop-condition kernel
+        "gpu_launches": K * (1 + 2 * -(-1000 // max(shape["sweeps_per_launch"], 1)) * (6 + 1)),
         "clocks": cs,
+        "plain": {"value": plain_value, "speedup": value / world / plain_value},
+        "peaks": dict(peaks.summary(), sm_mhz=clk_peak.summary()["sm_mhz"]),
     }
     line.update(extra)
     if cpu:
         line["cpu_baseline"] = cpu
-    print(json.dumps(line), flush=True)
+    print(json.dumps(r4(line), separators=(",", ":")), flush=True)
 
 
 def main():
@@ -774,7 +745,7 @@ def main():
     ap.add_argument("--ref-replicas", type=int, default=24, help="oracle replicas per core per step (reference arm)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-build", dest="build", action="store_false")
-    ap.add_argument("--no-extra", action="store_true", help="skip the uneven-batch and serving measurements")
+    ap.add_argument("--no-extra", action="store_true", help="only the headline workload")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -38,6 +38,23 @@
  *    seed, counter (spin, phase * 2^20 + sweep, replica / 4, start), word
  *    replica % 4.  Results therefore depend only on the logical coordinates,
  *    never on launch shape, batching or scheduling.
+ *
+ * How these calls differ from a plain host-side statement of Alg. 1
+ * -----------------------------------------------------------------
+ *  - Samples are not library objects: spvar_sample writes spins and energies
+ *    into device buffers the caller owns (e.g. torch tensors), so a phase
+ *    allocates nothing and its output feeds spvar_persistence directly.
+ *  - The acceptance table is a required device input, built once by
+ *    spvar_thresholds from the beta schedule and reused by every call and
+ *    start: the table (not beta) is what both this library and a checker
+ *    evaluate, so results are bit-exact, and no call hides a host-to-device
+ *    copy of a table per sample.
+ *  - spvar_persistence writes the counts, the fixings and the number fixed to
+ *    device memory and does not synchronise, so sample -> persistence ->
+ *    reduction chain on the stream; only the elite size returns to the host.
+ *  - spvar_reduce synchronises once, to learn the size of the new problem.
+ *  - Problem sizes and the constant term are read through
+ *    spvar_problem_get_info rather than one accessor each.
  */
 #ifndef SPVAR_H
 #define SPVAR_H
@@ -330,6 +347,12 @@ typedef struct spvar_params {
     int32_t sqa_slices;          /* SQA: Trotter slices P (1, or even, <= SPVAR_SQA_MAX_SLICES) */
     double sqa_beta;             /* SQA: inverse temperature, constant over the anneal */
     double sqa_gamma0, sqa_gamma1; /* SQA: transverse field, linear from gamma0 to gamma1 (both > 0) */
+    int32_t sweeps_per_launch;   /* SA: sweeps of a phase's anneal per sweep launch; a phase then takes
+                                    ceil(num_sweeps / sweeps_per_launch) launches, each resuming from the
+                                    states the previous one wrote (results are identical: every random
+                                    word is keyed by the absolute sweep).  0: the autotuner chooses
+                                    between one launch per phase and four when replicas_per_block is 0,
+                                    else one launch per phase.  Must be 0 with the SQA sampler */
 } spvar_params;
 
 #define SPVAR_SAMPLER_SA 0  /* simulated annealing (Sec. III.A) */
@@ -405,6 +428,10 @@ int spvar_solve(const spvar_problem *p, const spvar_params *prm, uint64_t seed,
  * phases of samples x sweeps x free spins) and phases executed. */
 int spvar_plan_stats(const spvar_plan *plan, int64_t *attempts, int32_t *phases);
 
+/* Sweeps per sweep launch the plan uses (requested, or chosen by the
+ * autotuner); num_sweeps when a phase is one launch. */
+int spvar_plan_sweeps_per_launch(const spvar_plan *plan, int32_t *sweeps);
+
 /* ------------------------------------------------------------------ */
 /* Serving: a request loop with continuous batching                      */
 /* ------------------------------------------------------------------ */
@@ -428,6 +455,9 @@ typedef struct spvar_server_config {
     int32_t max_dmax;       /* acceptance table covers flip costs up to this */
     int32_t energy_scale;   /* shared by all requests */
     int32_t max_requests;   /* requests in flight at once */
+    int32_t sweeps_per_step; /* sweeps of every in-flight anneal per engine step (0: a whole phase).  A
+                                request that arrives is admitted at the next step, so smaller steps
+                                shorten its wait; results do not depend on it */
 } spvar_server_config;
 
 typedef struct spvar_request_info {
@@ -463,6 +493,9 @@ int spvar_server_result(spvar_server *s, int64_t id, int64_t *best_energy, int8_
 int spvar_server_release(spvar_server *s, int64_t id);
 int spvar_server_stats(spvar_server *s, int64_t *requests_done, int64_t *attempts_done,
                        int32_t *queued, int32_t *running);
+/* Sum of the sweep launches' durations (ms; CUDA events recorded around the
+ * sweep of every engine step) and the number of steps timed, since creation. */
+int spvar_server_sweep_time(spvar_server *s, double *total_ms, int64_t *launches);
 void spvar_server_destroy(spvar_server *s);
 
 /* Profiling: when on, plan_run waits for every phase and adds up the
@@ -489,6 +522,26 @@ int spvar_plan_post_time(const spvar_plan *plan, double *total_ms);
  * fixed set of its slices, 7: quad-group +-1 kernel), persistent grid size. */
 int spvar_plan_shape(const spvar_plan *plan, int32_t *block, int32_t *replicas_per_block,
                      int32_t *staged, int32_t *grid);
+
+/* ------------------------------------------------------------------ */
+/* Measurement: integer issue ceilings of the current GPU               */
+/* ------------------------------------------------------------------ */
+/* The paper has no counterpart: these probes give the measured ceilings that
+ * the sweep kernels' rooflines divide by (the sweep is bound by 32-bit integer
+ * instruction issue, not by memory).  One launch of `iters` iterations on
+ * every CTA the SMs keep resident (256 threads each), each thread running 16
+ * independent register chains of one instruction form:
+ *   form 0  three-input logic (lop3)           form 1  three-input add
+ *   form 2  32-bit multiply-add (mad.lo)       form 3  forms 0 and 2 alternating
+ *   form 4  32x32->64 multiply (mul.wide) whose halves one lop3 folds
+ *   form 5  whole Philox4x32-10 blocks
+ * ops_per_s: thread-level operations per second of the timed launch (forms
+ * 0-3 count every instruction of the form, form 4 the wide multiplies, form 5
+ * the Philox blocks), timed with CUDA events on `stream` after one untimed
+ * launch of iters/8 iterations; ms (may be NULL): the timed launch.
+ * Synchronises the stream.  Errors: EINVAL (form outside 0-5, iters < 1, NULL
+ * ops_per_s), ECUDA. */
+int spvar_measure_issue_rate(int32_t form, int32_t iters, double *ops_per_s, double *ms, void *stream);
 
 #ifdef __cplusplus
 }

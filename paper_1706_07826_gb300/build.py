@@ -14,7 +14,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OBJDIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libspvar.so")
-SOURCES = ["api.cpp", "sweep.cu", "sweep_pm1.cu", "sweep_pm1s.cu", "sweep_pm1w.cu", "sweep_pm1q.cu", "sweep_pticm.cu", "sweep_sqa.cu", "persist.cu", "plan.cu", "reduce_noalloc.cu", "server.cpp"]
+SOURCES = ["api.cpp", "sweep.cu", "sweep_pm1.cu", "sweep_pm1s.cu", "sweep_pm1w.cu", "sweep_pm1q.cu", "sweep_pticm.cu", "sweep_sqa.cu", "persist.cu", "plan.cu", "reduce_noalloc.cu", "server.cpp", "peak.cu"]
 HEADERS = ["spvar_internal.h", "philox.cuh", "persist.cuh", "sweep_common.cuh"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 

@@ -303,6 +303,7 @@ __global__ void __launch_bounds__(256) k_slots_init(Slot *slots, SolveConsts C)
         s.fix_done = 0;
         s.nfixed = 0;
         s.nlog = 0;
+        s.tsw = 0;
         *s.best_e = LLONG_MAX;
         *s.nphases = 0;
     }
@@ -354,6 +355,10 @@ __global__ void __launch_bounds__(kBigBlock)
             Slot &s = slots[si];
             if (s.mode != kDone) {
                 const int S = phase_samples(C, s.mode);
+                // this launch's sweep range; a later chunk resumes from the states the
+                // previous one wrote (every work item reads its own rows before it writes them)
+                const int t0 = s.tsw;
+                const int t1 = C.chunk > 0 ? min(C.T, t0 + C.chunk) : C.T;
                 SweepJob j;
                 j.prob = s.cur;
                 j.spins = s.spins;
@@ -363,14 +368,17 @@ __global__ void __launch_bounds__(kBigBlock)
                 j.W = s.W0;
                 j.start = s.start;
                 j.phase = (uint32_t)s.phase;
-                j.init = nullptr;
-                j.t0 = 0;
-                j.pad = 0;
+                j.init = t0 > 0 ? s.spins : nullptr;
+                j.t0 = t0;
+                j.t1 = t1;
                 jobs[si] = j;
                 groups = ceil_div(ceil_div(S, 4), item_quads(s.cur, C, ceil_div(S, 4)));
-                s.rec_count[s.phase] = S;
-                s.rec_nfree[s.phase] = s.cur->n;
-                s.nfixed = 0;
+                if (t0 == 0) {
+                    s.rec_count[s.phase] = S;
+                    s.rec_nfree[s.phase] = s.cur->n;
+                    s.nfixed = 0;
+                }
+                s.tsw = t1;
             }
         }
         int tot;
@@ -403,7 +411,7 @@ __global__ void __launch_bounds__(kBigBlock) k_elite_slots(Slot *slots, SolveCon
     extern __shared__ __align__(16) unsigned long long s_key[];
     __shared__ int s_better;
     Slot &s = slots[blockIdx.x];
-    if (s.mode == kDone) return;
+    if (s.mode == kDone || !sample_complete(s, C)) return;
     const int S = phase_samples(C, s.mode);
     const int k = (s.mode == kFixing) ? C.k_fix : (s.mode == kCorr) ? C.k_corr : 1;
     const int64_t *e = s.rec_e + (size_t)s.phase * C.Smax;
@@ -435,7 +443,7 @@ __global__ void __launch_bounds__(kBigBlock) k_elite_slots(Slot *slots, SolveCon
 __global__ void __launch_bounds__(kCountBlock) k_count_slots(Slot *slots, SolveConsts C)
 {
     Slot &s = slots[blockIdx.y];
-    if (s.mode != kFixing && s.mode != kCorr) return;
+    if ((s.mode != kFixing && s.mode != kCorr) || !sample_complete(s, C)) return;
     const DevProb *P = s.cur;
     if ((int)(blockIdx.x * blockDim.x) >= P->n) return;
     if (s.mode == kCorr) {
@@ -455,13 +463,14 @@ __global__ void __launch_bounds__(kBigBlock) k_reduce_slots(Slot *slots, SolveCo
 {
     Slot &s = slots[blockIdx.x];
     const int mode = s.mode;
-    if (mode == kDone) return;
+    if (mode == kDone || !sample_complete(s, C)) return;
+    __syncthreads();  // every thread has read the slot's state before thread 0 moves it on
     if (mode == kSolving) {
-        __syncthreads();
         if (threadIdx.x == 0) {
             s.phase += 1;
             *s.nphases = s.phase;
             s.mode = kDone;
+            s.tsw = 0;
         }
         return;
     }
@@ -503,6 +512,7 @@ __global__ void __launch_bounds__(kBigBlock) k_reduce_slots(Slot *slots, SolveCo
         s.next = next2;
         s.ocur = ocur2;
         s.phase += 1;
+        s.tsw = 0;
         *s.nphases = s.phase;
         if (mode == kCorr) {
             s.mode = kFixing;  // the SPVAR phases follow the correlation phase
@@ -512,6 +522,317 @@ __global__ void __launch_bounds__(kBigBlock) k_reduce_slots(Slot *slots, SolveCo
             else s.mode = (C.S_solve > 0) ? kSolving : kDone;
         }
     }
+}
+
+// ------------------------------------------- multi-CTA fold/compact (Alg. 1)
+// Alg. 1's update of J and h for every slot whose fixing (or correlation)
+// phase sample is complete, spread over chunks of kFoldChunk spins so that all
+// SMs stream the CSRs:
+//   k_fold_prep    stall rule (ISPVAR) and the zeroed energy accumulator;
+//   k_fold_count   per spin: folded bias, free-free row length, energy of the
+//                  fixed spins; per chunk: the totals k_fold_index offsets by;
+//   k_fold_index   new indices, h', row pointers, inherited colours and sweep
+//                  positions (each chunk adds the totals of the chunks before
+//                  it), and the new header (chunk 0);
+//   k_fold_fill    CSR columns and values and the ELL layout of the free spins;
+//   k_fold_finish  phase transitions and the count of active slots.
+// The result is the one reduce_core computes: free spins keep their order,
+// couplers between free spins keep theirs, colour classes are inherited.
+constexpr int kFoldBlock = 256;
+constexpr int kFoldPer = kFoldChunk / kFoldBlock;
+
+__device__ __forceinline__ bool fold_active(const Slot &s, const SolveConsts &C)
+{
+    return (s.mode == kFixing || s.mode == kCorr) && sample_complete(s, C);
+}
+
+__global__ void __launch_bounds__(32) k_fold_prep(Slot *slots, SolveConsts C)
+{
+    Slot &s = slots[blockIdx.x];
+    if (!fold_active(s, C) || threadIdx.x != 0) return;
+    const DevProb *P = s.cur;
+    int32_t *tab = s.scratch + fold_table_offset(P->cap_n);
+    *reinterpret_cast<unsigned long long *>(tab + kFoldMaxChunks * kFoldStride) = 0ull;
+    if (s.mode == kFixing && C.iterate && s.nfixed == 0 && P->n > 0) {
+        // nothing fixed: fix the lowest-index spin to its value in the best
+        // elite sample so that every SPVAR phase makes progress
+        const uint32_t w = s.spins[(size_t)s.elite[0] * s.W0];
+        const int8_t v = (w & 1u) ? 1 : -1;
+        s.fixed[0] = v;
+        s.fmap[s.orig[s.ocur][0]] = v;
+    }
+}
+
+__global__ void __launch_bounds__(kFoldBlock) k_fold_count(Slot *slots, SolveConsts C)
+{
+    __shared__ int s_cls[kMaxColours];
+    __shared__ int s_free, s_nnz, s_hnz;
+    __shared__ unsigned long long s_key, s_off;
+    Slot &s = slots[blockIdx.y];
+    if (!fold_active(s, C)) return;
+    const DevProb *P = s.cur;
+    const int n = P->n, cap = P->cap_n, tid = threadIdx.x;
+    const int i0 = blockIdx.x * kFoldChunk;
+    if (i0 >= n) return;
+    for (int c = tid; c < kMaxColours; c += kFoldBlock) s_cls[c] = 0;
+    if (tid == 0) {
+        s_free = s_nnz = s_hnz = 0;
+        s_key = 0ull;
+        s_off = 0ull;
+    }
+    __syncthreads();
+    int32_t *rowcnt = s.scratch + cap, *hfold = s.scratch + 2 * cap;
+    const int8_t *fx = s.fixed;
+    long long off = 0;
+    int nfree = 0, nnz = 0, hnz = 0;
+    unsigned long long key = 0ull;
+#pragma unroll
+    for (int k = 0; k < kFoldPer; ++k) {
+        const int i = i0 + k * kFoldBlock + tid;
+        if (i >= n) break;
+        const int vi = fx[i];
+        long long hf = P->h[i];
+        int nf = 0;
+        const int p1 = P->row_ptr[i + 1];
+        for (int p = P->row_ptr[i]; p < p1; ++p) {
+            const int j = P->col[p];
+            const int vj = fx[j];
+            if (vi) {
+                if (vj && j > i) off += (long long)P->val[p] * vi * vj;
+            } else if (vj) {
+                hf += (long long)P->val[p] * vj;
+            } else {
+                ++nf;
+            }
+        }
+        if (vi) {
+            off += (long long)P->h[i] * vi;
+        } else {
+            hfold[i] = (int32_t)hf;
+            rowcnt[i] = nf;
+            ++nfree;
+            nnz += nf;
+            hnz |= hf != 0;
+            atomicAdd(&s_cls[P->colour[i]], 1);
+            // reference spin of the new problem: largest degree, lowest index
+            key = max(key, ((unsigned long long)nf << 32) | (unsigned long long)(0x7FFFFFFF - i));
+        }
+    }
+    atomicAdd(&s_free, nfree);
+    atomicAdd(&s_nnz, nnz);
+    if (hnz) atomicOr(&s_hnz, 1);
+    atomicMax(&s_key, key);
+    atomicAdd(&s_off, (unsigned long long)off);
+    __syncthreads();
+    int32_t *tab = s.scratch + fold_table_offset(cap);
+    int32_t *e = tab + blockIdx.x * kFoldStride;
+    if (tid == 0) {
+        e[0] = s_free;
+        e[1] = s_nnz;
+        e[2] = s_hnz;
+        e[3] = (int32_t)(s_key >> 32);
+        e[4] = (int32_t)(s_key & 0xFFFFFFFFull);
+        atomicAdd(reinterpret_cast<unsigned long long *>(tab + kFoldMaxChunks * kFoldStride), s_off);
+    }
+    for (int c = tid; c < P->ncol; c += kFoldBlock) e[6 + c] = s_cls[c];
+}
+
+__global__ void __launch_bounds__(kFoldBlock) k_fold_index(Slot *slots, SolveConsts C)
+{
+    __shared__ int s_warp[32];
+    __shared__ int s_base_cls[kMaxColours], s_tot_cls[kMaxColours], s_cptr[kMaxColours + 1];
+    __shared__ int s_base[2], s_tot[2], s_hnz;
+    Slot &s = slots[blockIdx.y];
+    if (!fold_active(s, C)) return;
+    const DevProb *P = s.cur;
+    DevProb *D = s.buf[s.next];
+    const int n = P->n, cap = P->cap_n, ncol = P->ncol, tid = threadIdx.x;
+    const int chunk = blockIdx.x, i0 = chunk * kFoldChunk;
+    if (chunk > 0 && i0 >= n) return;  // chunk 0 writes the header, even for n = 0
+    const int nch = (n + kFoldChunk - 1) / kFoldChunk;
+    const int32_t *tab = s.scratch + fold_table_offset(cap);
+    // offsets of this chunk (totals of the chunks before it) and the totals of all
+    if (tid < ncol) {
+        int b = 0, t = 0;
+        for (int q = 0; q < nch; ++q) {
+            const int v = tab[q * kFoldStride + 6 + tid];
+            b += q < chunk ? v : 0;
+            t += v;
+        }
+        s_base_cls[tid] = b;
+        s_tot_cls[tid] = t;
+    } else if (tid >= 64 && tid < 66) {
+        const int f = tid - 64;
+        int b = 0, t = 0;
+        for (int q = 0; q < nch; ++q) {
+            const int v = tab[q * kFoldStride + f];
+            b += q < chunk ? v : 0;
+            t += v;
+        }
+        s_base[f] = b;
+        s_tot[f] = t;
+    } else if (tid == 96) {
+        int h = 0;
+        for (int q = 0; q < nch; ++q) h |= tab[q * kFoldStride + 2];
+        s_hnz = h;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        int c0 = 0;
+        for (int c = 0; c < ncol; ++c) {
+            s_cptr[c] = c0;
+            c0 += s_tot_cls[c];
+        }
+        s_cptr[ncol] = c0;
+    }
+    __syncthreads();
+    if (chunk == 0 && tid <= ncol) D->cptr[tid] = s_cptr[tid];
+    if (chunk == 0 && tid == 0) {
+        const int m = s_tot[0], nnz2 = s_tot[1];
+        D->n = m;
+        D->nnz = nnz2;
+        D->ncol = ncol;
+        D->maxdeg = P->maxdeg;
+        D->dmax = P->dmax;
+        D->hzero = s_hnz ? 0 : 1;
+        D->pm1 = P->pm1;
+        D->ujs = P->ujs;
+        D->scale = P->scale;
+        D->offset = P->offset +
+                    (long long)*reinterpret_cast<const unsigned long long *>(tab + kFoldMaxChunks * kFoldStride);
+        D->row_ptr[m] = nnz2;
+    }
+    if (i0 >= n) return;
+    const int8_t *fx = s.fixed;
+    int32_t *nofo = s.scratch;
+    const int32_t *rowcnt = s.scratch + cap, *hfold = s.scratch + 2 * cap;
+    const int32_t *orig = s.orig[s.ocur];
+    int32_t *orig2 = s.orig[s.ocur ^ 1];
+    int carry_free = s_base[0], carry_nnz = s_base[1];
+    for (int k = 0; k < kFoldPer; ++k) {
+        if (i0 + k * kFoldBlock >= n) break;  // uniform over the block
+        const int i = i0 + k * kFoldBlock + tid;
+        const bool valid = i < n;
+        const bool f = valid && fx[i] == 0;
+        const int rc = f ? rowcnt[i] : 0;
+        const int col = f ? P->colour[i] : -1;
+        int tf, tr;
+        const int exf = block_scan_excl(f ? 1 : 0, s_warp, &tf);
+        const int exr = block_scan_excl(rc, s_warp, &tr);
+        // rank among this step's free spins of the same colour class
+        int rank = 0;
+        for (int c = 0; c < ncol; ++c) {
+            int tc;
+            // the scan ends with a barrier, so s_base_cls[c] is settled here
+            const int exc = block_scan_excl(col == c ? 1 : 0, s_warp, &tc);
+            if (col == c) rank = s_base_cls[c] + exc;
+            __syncthreads();  // every thread has read the class offset before it advances
+            if (tid == 0) s_base_cls[c] += tc;
+        }
+        if (valid) nofo[i] = f ? carry_free + exf : -1;
+        if (f) {
+            const int a = carry_free + exf;
+            const int h = hfold[i];
+            const int pos = s_cptr[col] + rank;
+            s.old_of_new[a] = i;
+            orig2[a] = orig[i];
+            D->h[a] = h;
+            D->colour[a] = col;
+            D->row_ptr[a] = carry_nnz + exr;
+            D->pos_of_idx[a] = pos;
+            D->idx_of_pos[pos] = a;
+            D->meta[pos] = ((uint32_t)(h & 0xFFFF) << 16) | (uint32_t)rc;
+        }
+        carry_free += tf;
+        carry_nnz += tr;
+    }
+}
+
+__global__ void __launch_bounds__(kFoldBlock) k_fold_fill(Slot *slots, SolveConsts C)
+{
+    Slot &s = slots[blockIdx.y];
+    if (!fold_active(s, C)) return;
+    const DevProb *P = s.cur;
+    DevProb *D = s.buf[s.next];
+    const int n = P->n, cap = P->cap_n, tid = threadIdx.x;
+    const int i0 = blockIdx.x * kFoldChunk;
+    const int32_t *nofo = s.scratch;
+    if (blockIdx.x == 0 && tid == 0) {
+        // the reference spin: the chunks' candidates, largest degree then lowest index
+        const int32_t *tab = s.scratch + fold_table_offset(cap);
+        unsigned long long best = 0ull;
+        bool any = false;
+        for (int q = 0; q * kFoldChunk < n; ++q) {
+            const int32_t *e = tab + q * kFoldStride;
+            if (e[0] == 0) continue;
+            const unsigned long long k = ((unsigned long long)(uint32_t)e[3] << 32) | (uint32_t)e[4];
+            best = max(best, k);
+            any = true;
+        }
+        D->rho = any ? nofo[0x7FFFFFFF - (int)(best & 0xFFFFFFFFull)] : -1;
+    }
+    if (i0 >= n) return;
+    const int8_t *fx = s.fixed;
+#pragma unroll
+    for (int k = 0; k < kFoldPer; ++k) {
+        const int i = i0 + k * kFoldBlock + tid;
+        if (i >= n) break;
+        if (fx[i] != 0) continue;
+        const int a = nofo[i];
+        int q = D->row_ptr[a];
+        const int pos = D->pos_of_idx[a];
+        int d = 0;
+        const int p1 = P->row_ptr[i + 1];
+        for (int p = P->row_ptr[i]; p < p1; ++p) {
+            const int j = P->col[p];
+            if (fx[j] != 0) continue;
+            const int b = nofo[j];
+            const int J = P->val[p];
+            D->col[q] = b;
+            D->val[q] = J;
+            D->ell[(size_t)d * cap + pos] = ((uint32_t)D->pos_of_idx[b] & 0xFFFFu) | ((uint32_t)(J & 0xFFFF) << 16);
+            ++q;
+            ++d;
+        }
+    }
+}
+
+// Phase transitions after the multi-CTA fold/compact, then the active count.
+__global__ void __launch_bounds__(256) k_fold_finish(Slot *slots, SolveConsts C, int32_t *nactive)
+{
+    __shared__ int s_n;
+    if (threadIdx.x == 0) s_n = 0;
+    __syncthreads();
+    int act = 0;
+    for (int si = threadIdx.x; si < C.nslots; si += blockDim.x) {
+        Slot &s = slots[si];
+        const int mode = s.mode;
+        if (mode != kDone && sample_complete(s, C)) {
+            if (mode == kSolving) {
+                s.mode = kDone;
+            } else {
+                DevProb *D = s.buf[s.next];
+                const int m = D->n;
+                s.cur = D;
+                s.next ^= 1;
+                s.ocur ^= 1;
+                if (mode == kCorr) {
+                    s.mode = kFixing;  // the SPVAR phases follow the correlation phase
+                } else {
+                    s.fix_done += 1;
+                    if (C.iterate && m > 0 && s.fix_done < C.max_fix) s.mode = kFixing;
+                    else s.mode = (C.S_solve > 0) ? kSolving : kDone;
+                }
+            }
+            s.phase += 1;
+            s.tsw = 0;
+            *s.nphases = s.phase;
+        }
+        act += s.mode != kDone;
+    }
+    atomicAdd(&s_n, act);
+    __syncthreads();
+    if (threadIdx.x == 0 && nactive) *nactive = s_n;
 }
 
 __global__ void k_count_active(const Slot *slots, int nslots, int32_t *nactive)
@@ -534,7 +855,7 @@ __global__ void __launch_bounds__(kBigBlock) k_boost_components(Slot *slots, Sol
     __shared__ int s_warp[32];
     __shared__ int s_changed;
     Slot &s = slots[blockIdx.x];
-    if (s.mode != kSolving) return;
+    if (s.mode != kSolving || !sample_complete(s, C)) return;
     const DevProb *P = s.cur;
     const int n = P->n;
     int32_t *lab = s.comp;
@@ -584,7 +905,7 @@ __global__ void __launch_bounds__(256) k_boost_partial(Slot *slots, SolveConsts 
     extern __shared__ int s_acc[];
     Slot &s = slots[blockIdx.y];
     const int r = blockIdx.x;
-    if (s.mode != kSolving || r >= C.S_solve) return;
+    if (s.mode != kSolving || !sample_complete(s, C) || r >= C.S_solve) return;
     const DevProb *P = s.cur;
     const int n = P->n, m = s.ncomp;
     for (int c = threadIdx.x; c < m; c += blockDim.x) s_acc[c] = 0;
@@ -610,7 +931,7 @@ __global__ void __launch_bounds__(kBigBlock) k_boost_sort(Slot *slots, SolveCons
     extern __shared__ __align__(16) unsigned long long s_key[];
     Slot &s = slots[blockIdx.y];
     const int c = blockIdx.x;
-    if (s.mode != kSolving || c >= s.ncomp) return;
+    if (s.mode != kSolving || !sample_complete(s, C) || c >= s.ncomp) return;
     const int S = C.S_solve;
     int N2 = 1;
     while (N2 < S) N2 <<= 1;
@@ -644,7 +965,7 @@ __global__ void __launch_bounds__(256) k_boost_merge(Slot *slots, SolveConsts C)
     __shared__ long long s_e;
     Slot &s = slots[blockIdx.y];
     const int r = blockIdx.x;
-    if (s.mode != kSolving || r >= C.S_solve) return;
+    if (s.mode != kSolving || !sample_complete(s, C) || r >= C.S_solve) return;
     const DevProb *P = s.cur;
     const int n = P->n, m = s.ncomp;
     if (threadIdx.x == 0) s_e = 0;
@@ -672,7 +993,7 @@ __global__ void __launch_bounds__(256) k_boost_copy(Slot *slots, SolveConsts C)
 {
     Slot &s = slots[blockIdx.y];
     const int r = blockIdx.x;
-    if (s.mode != kSolving || r >= C.S_solve) return;
+    if (s.mode != kSolving || !sample_complete(s, C) || r >= C.S_solve) return;
     const int Wn = (s.cur->n + 31) >> 5;
     for (int w = threadIdx.x; w < Wn; w += blockDim.x) s.spins[(size_t)r * s.W0 + w] = s.spins2[(size_t)r * s.W0 + w];
 }
@@ -770,6 +1091,18 @@ cudaError_t launch_count_slots(Slot *slots, const SolveConsts &C, int max_n0, cu
     if (max_n0 <= 0) return cudaSuccess;
     dim3 grid(ceil_div(max_n0, kCountBlock), C.nslots);
     k_count_slots<<<grid, kCountBlock, 0, st>>>(slots, C);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fold_slots(Slot *slots, const SolveConsts &C, int max_n0, int32_t *nactive, cudaStream_t st)
+{
+    if (C.nslots <= 0) return cudaSuccess;
+    const dim3 grid(std::max(1, ceil_div(max_n0, kFoldChunk)), C.nslots);
+    k_fold_prep<<<C.nslots, 32, 0, st>>>(slots, C);
+    k_fold_count<<<grid, kFoldBlock, 0, st>>>(slots, C);
+    k_fold_index<<<grid, kFoldBlock, 0, st>>>(slots, C);
+    k_fold_fill<<<grid, kFoldBlock, 0, st>>>(slots, C);
+    k_fold_finish<<<1, 256, 0, st>>>(slots, C, nactive);
     return cudaGetLastError();
 }
 

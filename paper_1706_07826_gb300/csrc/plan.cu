@@ -40,6 +40,7 @@ cudaError_t engine_phase(const PhaseEngine &E, Slot *slots, int nslots, int T, i
     C.fit_nslot = E.shape.kind == 1 ? E.shape.nslot : 0;
     C.fit_words = E.shape.kind == 6 ? 2 * E.shape.Q * (E.max_n0 + 1) : 0;
     C.grid = grid;
+    C.T = T;
     cudaError_t e = launch_plan(slots, C, E.jobs, E.items, E.ctr + 0, E.ctr + 1, st);
     if (e != cudaSuccess) return e;
     SweepLaunch L;
@@ -65,7 +66,10 @@ cudaError_t engine_phase(const PhaseEngine &E, Slot *slots, int nslots, int T, i
     if ((e = launch_boost(slots, C, st)) != cudaSuccess) return e;
     if ((e = launch_elite_slots(slots, C, st)) != cudaSuccess) return e;
     if ((e = launch_count_slots(slots, C, E.max_n0, st)) != cudaSuccess) return e;
-    if ((e = launch_reduce_slots(slots, C, count_active ? E.ctr + 2 : nullptr, st)) != cudaSuccess) return e;
+    // fold/compact: spread over chunks of spins, or one CTA per start when the tree step follows
+    e = C.tree ? launch_reduce_slots(slots, C, count_active ? E.ctr + 2 : nullptr, st)
+               : launch_fold_slots(slots, C, E.max_n0, count_active ? E.ctr + 2 : nullptr, st);
+    if (e != cudaSuccess) return e;
     // end of the persistence pass (boosting, elite, counts and fixing, fold/compact)
     if (E.ev_post && (e = record(E.ev_post)) != cudaSuccess) return e;
     return cudaSuccess;
@@ -196,6 +200,9 @@ cudaError_t launch_phase(spvar_plan *pl, Slot *slots, int nslots, int T, int gri
     return engine_phase(E, slots, nslots, T, grid, st, count_active, capturing);
 }
 
+// Sweep launches of a whole run: every phase takes launches_per_phase launches.
+int plan_steps(const spvar_plan *pl) { return pl->iters_max * launches_per_phase(pl->T, pl->C.chunk); }
+
 // Loop condition of the whole-run graph: run another phase while phases
 // remain and (ISPVAR) some start is still active.
 __global__ void k_loop_cond(cudaGraphConditionalHandle h, int32_t *ctr, int iters_max, int iterate)
@@ -231,7 +238,7 @@ bool build_loop_graph(spvar_plan *pl, int nslots)
             cudaError_t e = launch_phase(pl, pl->d_slots, nslots, pl->T, pl->sweep_grid, pl->cap_stream, true, true,
                                          false);
             if (e == cudaSuccess) {
-                k_loop_cond<<<1, 1, 0, pl->cap_stream>>>(h, pl->d_ctr, pl->iters_max, pl->prm.iterate ? 1 : 0);
+                k_loop_cond<<<1, 1, 0, pl->cap_stream>>>(h, pl->d_ctr, plan_steps(pl), pl->prm.iterate ? 1 : 0);
                 e = cudaGetLastError();
             }
             cudaGraph_t out = nullptr;
@@ -411,27 +418,27 @@ void autotune(spvar_plan *pl, cudaStream_t st, int optin)
         sh.balance = 1;
         if (pl->prm.form != SPVAR_FORM_PLAIN) cands.push_back(sh);
     }
-    for (const SweepShape &sh : cands) {
+    // a short run of the plan's phases (fixing, and solving on the problems it
+    // reduced), so that shapes that suit the full problem but not the reduced
+    // ones are not picked; chunk_t > 0 splits every phase into sweep launches
+    auto trial = [&](const SweepShape &sh, int chunk_t) -> float {
         pl->shape = sh;
         pl->sweep_smem = sweep_shape_smem(sh, pl->max_n0, pl->thr_stride, pl->max_deg);
-        if (sweep_shape_occupancy(sh, pl->pm1, pl->sweep_smem) < 1) continue;
+        if (sweep_shape_occupancy(sh, pl->pm1, pl->sweep_smem) < 1) return 1e30f;
         const int nslots = (pl->prm.form == SPVAR_FORM_PLAIN) ? 1 : pl->C.nslots;
+        pl->C.Q = sh.Q;
+        pl->C.chunk = chunk_t;
         SolveConsts C = pl->C;
         C.nslots = nslots;
-        C.Q = sh.Q;
-        pl->C.Q = sh.Q;
         const int items = nslots * ceil_div(ceil_div(pl->C.Smax, 4), sh.Q);
         const int grid = (pl->prm.form == SPVAR_FORM_PLAIN) ? items : grid_for(pl, items);
-        // a short run of the plan's phases (fixing, and solving on the problems it
-        // reduced), so that shapes that suit the full problem but not the reduced
-        // ones are not picked
-        const int phases = std::min(pl->iters_max, 4);
+        const int launches = std::min(pl->iters_max, 4) * launches_per_phase(Tt, chunk_t);
         float ms = 1e30f;
         bool ok = true;
         for (int rep = 0; rep < 2 && ok; ++rep) {
             ok = launch_slots_init(pl->d_slots, C, pl->max_n0, st) == cudaSuccess;
             cudaEventRecord(a, st);
-            for (int it = 0; it < phases && ok; ++it)
+            for (int it = 0; it < launches && ok; ++it)
                 ok = launch_phase(pl, pl->d_slots, nslots, Tt, grid, st, false) == cudaSuccess;
             cudaEventRecord(b, st);
             if (!ok || cudaEventSynchronize(b) != cudaSuccess) { ok = false; break; }
@@ -439,12 +446,23 @@ void autotune(spvar_plan *pl, cudaStream_t st, int optin)
             cudaEventElapsedTime(&m, a, b);
             ms = std::min(ms, m);  // the first repetition includes one-time setup
         }
-        if (!ok) { cudaGetLastError(); continue; }
+        pl->C.chunk = 0;
+        if (!ok) { cudaGetLastError(); return 1e30f; }
+        return ms;
+    };
+    for (const SweepShape &sh : cands) {
+        const float ms = trial(sh, 0);
         if (ms < best) {
             best = ms;
             pick = sh;
             found = true;
         }
+    }
+    // sweeps per launch: the whole phase in one launch against four launches per
+    // phase (each resumes from the states the previous one wrote)
+    if (found && pl->sqa_P == 0 && Tt >= 8) {
+        const float ms4 = trial(pick, ceil_div(Tt, 4));
+        if (ms4 < best) pick.lpp = 4;
     }
     cudaEventDestroy(a);
     cudaEventDestroy(b);
@@ -488,7 +506,8 @@ int spvar_plan_create(const spvar_problem *const *problems, int32_t nproblems,
         p.replicas_per_block < 0 || (p.replicas_per_block % 4) != 0 || p.sweep_kernel < 0 ||
         p.sweep_kernel > 5 || p.start_offset < 0 || p.component_boost < 0 || p.component_boost > 1 || p.tree_preprocess < 0 || p.tree_preprocess > 1 || (p.sweep_block != 0 && p.sweep_block != 128 && p.sweep_block != 256 &&
                                p.sweep_block != 512 && p.sweep_block != 1024) ||
-        check_corr_params(p) != SPVAR_OK || check_sampler_params(p) != SPVAR_OK)
+        check_corr_params(p) != SPVAR_OK || check_sampler_params(p) != SPVAR_OK || p.sweeps_per_launch < 0 ||
+        (p.sampler != SPVAR_SAMPLER_SA && p.sweeps_per_launch != 0))
         return SPVAR_EINVAL;
     const int Smax = std::max(std::max(p.fixing_sample_size, p.solving_sample_size), p.corr_sample_size);
     if (Smax > SPVAR_MAX_SAMPLES || p.num_sweeps > SPVAR_MAX_SWEEPS ||
@@ -573,7 +592,7 @@ int spvar_plan_create(const spvar_problem *const *problems, int32_t nproblems,
         b += align256(4 * (size_t)n0);      // counts
         b += align256((size_t)n0);          // fixed
         b += align256(4 * (size_t)n0);      // old_of_new
-        b += align256(8 * (size_t)H.cap_n); // scratch
+        b += align256(4 * slot_scratch_ints(H.cap_n)); // scratch
         b += boost_slot_bytes(p.component_boost, n0, Smax, ceil_div(n0, 32));
         b += tree_slot_bytes(p.tree_preprocess, n0);
         o_slot[s] = take(b);
@@ -676,7 +695,7 @@ int spvar_plan_create(const spvar_problem *const *problems, int32_t nproblems,
         S.counts = (int32_t *)carve(4 * (size_t)n0);
         S.fixed = (int8_t *)carve((size_t)n0);
         S.old_of_new = (int32_t *)carve(4 * (size_t)n0);
-        S.scratch = (int32_t *)carve(8 * (size_t)H.cap_n);
+        S.scratch = (int32_t *)carve(4 * slot_scratch_ints(H.cap_n));
         if (p.component_boost)
             boost_slot_carve(S, carve(boost_slot_bytes(1, n0, Smax, S.W0)), n0, Smax, S.W0);
         if (p.tree_preprocess) tree_slot_carve(S, carve(tree_slot_bytes(1, n0)), n0);
@@ -761,6 +780,10 @@ int spvar_plan_create(const spvar_problem *const *problems, int32_t nproblems,
         if (pl->sweep_smem > (size_t)optin) { plan_free(pl); return SPVAR_ELIMIT; }
     }
     pl->C.Q = pl->shape.Q;
+    // sweeps per launch: requested, else the autotuner's choice (one launch per phase by default)
+    if (p.sweeps_per_launch > 0) pl->C.chunk = p.sweeps_per_launch < pl->T ? p.sweeps_per_launch : 0;
+    else if (p.replicas_per_block == 0 && pl->shape.lpp > 1) pl->C.chunk = ceil_div(std::max(pl->T, 1), pl->shape.lpp);
+    else pl->C.chunk = 0;
     const int items = nslots * ceil_div(ceil_div(Smax, 4), pl->shape.Q);
     pl->sweep_grid = grid_for(pl, items);
 
@@ -821,7 +844,8 @@ int spvar_plan_run(spvar_plan *pl, const uint64_t *seeds, const spvar_result *re
         SPVAR_CUDA_TRY(cudaMemsetAsync(pl->d_ctr + 3, 0, sizeof(int32_t), st));
         SPVAR_CUDA_TRY(cudaGraphLaunch(pl->graph_loop, st));
     } else if (pl->prm.form == SPVAR_FORM_BATCHED) {
-        for (int it = 0; it < pl->iters_max; ++it) {
+        const int steps = plan_steps(pl);
+        for (int it = 0; it < steps; ++it) {
             if (pl->graph) {
                 SPVAR_CUDA_TRY(cudaGraphLaunch(pl->graph, st));
             } else {
@@ -830,18 +854,19 @@ int spvar_plan_run(spvar_plan *pl, const uint64_t *seeds, const spvar_result *re
                                                cudaMemcpyDeviceToHost, st));
             }
             if ((rc = profile_phase()) != SPVAR_OK) return rc;
-            if (iterate && it + 1 < pl->iters_max) {
+            if (iterate && it + 1 < steps) {
                 SPVAR_CUDA_TRY(cudaStreamSynchronize(st));
                 if (*pl->h_nactive == 0) break;
             }
         }
     } else {
         const int grid = ceil_div(ceil_div(pl->C.Smax, 4), pl->shape.Q);
+        const int steps = plan_steps(pl);
         for (int s = 0; s < nslots; ++s) {
-            for (int it = 0; it < pl->iters_max; ++it) {
+            for (int it = 0; it < steps; ++it) {
                 SPVAR_CUDA_TRY(launch_phase(pl, pl->d_slots + s, 1, pl->T, grid, st, iterate));
                 if ((rc = profile_phase()) != SPVAR_OK) return rc;
-                if (iterate && it + 1 < pl->iters_max) {
+                if (iterate && it + 1 < steps) {
                     SPVAR_CUDA_TRY(cudaMemcpyAsync(pl->h_nactive, pl->d_ctr + 2, sizeof(int32_t),
                                                    cudaMemcpyDeviceToHost, st));
                     SPVAR_CUDA_TRY(cudaStreamSynchronize(st));
@@ -903,6 +928,13 @@ int spvar_plan_shape(const spvar_plan *plan, int32_t *block, int32_t *replicas_p
                                                                                                  : plan->shape.stage;
     }
     if (grid) *grid = plan->sweep_grid;
+    return SPVAR_OK;
+}
+
+int spvar_plan_sweeps_per_launch(const spvar_plan *plan, int32_t *sweeps)
+{
+    if (!plan || !sweeps) return SPVAR_EINVAL;
+    *sweeps = plan->C.chunk > 0 ? plan->C.chunk : plan->T;
     return SPVAR_OK;
 }
 

@@ -3,11 +3,13 @@
 //
 // Requests are admitted in arrival order whenever a request slot is free and
 // their device workspace fits the memory budget (first-fit arena).  Every
-// engine step runs ONE phase of Alg. 2 for every admitted start of every
-// request in one persistent launch sequence (the same kernels as the plans,
-// captured once as a CUDA graph over the whole slot table), so a request that
-// arrives while others are running joins at the next phase boundary and its
-// work overlaps theirs on the device.  Finished requests are copied back and
+// engine step runs one sweep chunk (sweeps_per_step sweeps, or a whole phase)
+// of Alg. 2 for every admitted start of every request in one persistent launch
+// sequence (the same kernels as the plans, captured once as a CUDA graph over
+// the whole slot table); a start whose chunk completes its phase's sample
+// also runs the persistence pass in that step.  A request that arrives while
+// others are running therefore joins at the next step and its work overlaps
+// theirs on the device.  Finished requests are copied back and
 // their memory released at once.  All state -- problems, samples, reduced
 // problems, fix maps -- stays on the device between steps.  Results do not
 // depend on what else is in flight: randomness is keyed by (seed, start,
@@ -118,7 +120,11 @@ struct spvar_server {
     int64_t next_id = 1;
     std::thread worker;
     bool running = false, stop = false;
+    bool failed = false;  // the background engine stopped on an error
     int64_t attempts_done = 0, requests_done = 0;
+    cudaEvent_t ev[2] = {nullptr, nullptr};  // recorded around every step's sweep launch
+    double sweep_ms = 0.0;                   // sum of the sweep launches' durations
+    int64_t sweep_launches = 0;
 };
 
 namespace {
@@ -130,7 +136,7 @@ size_t request_bytes(const spvar_server *S, const HostProblem &hp)
     size_t per = 2 * pb;
     per += a256(4 * (size_t)S->Smax * ceil_div(n0, 32));
     per += 2 * a256(4 * (size_t)n0) + a256(4 * (size_t)S->Smax) + a256(4 * (size_t)n0) + a256((size_t)n0) +
-           a256(4 * (size_t)n0) + a256(8 * (size_t)n0);
+           a256(4 * (size_t)n0) + a256(4 * slot_scratch_ints(n0));
     per += a256(8 * (size_t)S->P * S->Smax) + 2 * a256(4 * (size_t)S->P) + a256(4) + a256(8) + 2 * a256((size_t)n0);
     per += boost_slot_bytes(S->cfg.params.component_boost, n0, S->Smax, ceil_div(n0, 32));
     per += tree_slot_bytes(S->cfg.params.tree_preprocess, n0);
@@ -138,7 +144,9 @@ size_t request_bytes(const spvar_server *S, const HostProblem &hp)
 }
 
 // Lays out a request's workspace in the arena, uploads its problem and fills
-// its slot entries (host mirror).  Caller holds the lock.
+// its slot entries (host mirror).  Called without the lock: the request's
+// arena range and request slot are reserved, and only the engine thread
+// touches the slot table.
 int place_request(spvar_server *S, Request &R)
 {
     char *base = static_cast<char *>(S->arena_mem) + R.off;
@@ -178,7 +186,7 @@ int place_request(spvar_server *S, Request &R)
         s.counts = (int32_t *)take(4 * (size_t)n0);
         s.fixed = (int8_t *)take((size_t)n0);
         s.old_of_new = (int32_t *)take(4 * (size_t)n0);
-        s.scratch = (int32_t *)take(8 * (size_t)n0);
+        s.scratch = (int32_t *)take(4 * slot_scratch_ints(n0));
         s.rec_e = (int64_t *)take(8 * (size_t)S->P * S->Smax);
         s.rec_count = (int32_t *)take(4 * (size_t)S->P);
         s.rec_nfree = (int32_t *)take(4 * (size_t)S->P);
@@ -242,7 +250,10 @@ int64_t request_attempts(const spvar_server *S, const Request &R)
 // One engine iteration: admit, run one phase for everything in flight, retire.
 int server_step(spvar_server *S, int32_t *active_out)
 {
-    // admission (arrival order)
+    // admission (arrival order): reserve a request slot and an arena range under
+    // the lock, then upload without it so that submit, wait and stats never wait
+    // for a copy
+    std::vector<Request *> admitted;
     {
         std::lock_guard<std::mutex> g(S->mu);
         while (!S->queue.empty()) {
@@ -255,16 +266,28 @@ int server_step(spvar_server *S, int32_t *active_out)
             if (!S->arena.alloc(R.bytes, &off)) break;
             R.off = off;
             R.rslot = rs;
-            int rc = place_request(S, R);
-            if (rc) {
-                S->arena.release(off, R.bytes);
-                return rc;
-            }
             S->rslot_owner[rs] = R.id;
-            R.state = 1;
-            R.t_admit = now_s();
             S->queue.pop_front();
+            admitted.push_back(&R);
         }
+    }
+    for (size_t a = 0; a < admitted.size(); ++a) {
+        Request &R = *admitted[a];
+        const int rc = place_request(S, R);
+        std::lock_guard<std::mutex> g(S->mu);
+        if (rc) {
+            // give back what this and the later admissions reserved; they queue again in order
+            for (size_t b = admitted.size(); b-- > a;) {
+                Request &Q = *admitted[b];
+                S->arena.release(Q.off, Q.bytes);
+                S->rslot_owner[Q.rslot] = -1;
+                Q.rslot = -1;
+                S->queue.push_front(Q.id);
+            }
+            return rc;
+        }
+        R.state = 1;
+        R.t_admit = now_s();
     }
     int active = 0;
     for (int64_t o : S->rslot_owner) active += (o >= 0);
@@ -279,6 +302,15 @@ int server_step(spvar_server *S, int32_t *active_out)
     SPVAR_CUDA_TRY(launch_gather_modes(S->d_slots, S->nslots, S->d_modes, S->st));
     SPVAR_CUDA_TRY(cudaMemcpyAsync(S->h_modes, S->d_modes, 4 * (size_t)S->nslots, cudaMemcpyDeviceToHost, S->st));
     SPVAR_CUDA_TRY(cudaStreamSynchronize(S->st));
+    if (S->ev[0]) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, S->ev[0], S->ev[1]) == cudaSuccess) {
+            std::lock_guard<std::mutex> g(S->mu);
+            S->sweep_ms += ms;
+            S->sweep_launches += 1;
+        }
+        cudaGetLastError();
+    }
     // retirement
     std::vector<int64_t> finished;
     for (size_t r = 0; r < S->rslot_owner.size(); ++r) {
@@ -325,6 +357,7 @@ void worker_loop(spvar_server *S)
         }
         if (server_step(S, nullptr) != SPVAR_OK) {
             std::lock_guard<std::mutex> g(S->mu);
+            S->failed = true;
             S->stop = true;
             S->cv.notify_all();
             return;
@@ -337,6 +370,8 @@ void server_free(spvar_server *S)
     if (!S) return;
     if (S->graph) cudaGraphExecDestroy(S->graph);
     if (S->cap_st) cudaStreamDestroy(S->cap_st);
+    for (cudaEvent_t e : S->ev)
+        if (e) cudaEventDestroy(e);
     if (S->st) cudaStreamDestroy(S->st);
     if (S->arena_mem) cudaFree(S->arena_mem);
     if (S->fixed_mem) cudaFree(S->fixed_mem);
@@ -358,7 +393,8 @@ int spvar_server_create(const spvar_server_config *cfg, spvar_server **out)
         !(p.elite_threshold > 0.0) || !(p.elite_threshold <= 1.0) || !(p.beta0 > 0.0) || !(p.beta1 > 0.0) ||
         p.canon < -1 || p.canon > 1 || p.start_offset < 0 || p.component_boost < 0 || p.component_boost > 1 || p.tree_preprocess < 0 || p.tree_preprocess > 1 || cfg->max_n < 1 || cfg->max_nnz < 0 ||
         cfg->max_degree < 1 || cfg->max_dmax < 0 || cfg->energy_scale < 1 || cfg->max_requests < 1 ||
-        cfg->budget_bytes == 0 || check_corr_params(p) != SPVAR_OK || p.sampler != SPVAR_SAMPLER_SA)
+        cfg->budget_bytes == 0 || check_corr_params(p) != SPVAR_OK || p.sampler != SPVAR_SAMPLER_SA ||
+        cfg->sweeps_per_step < 0)
         return SPVAR_EINVAL;
     const int Smax = std::max(std::max(p.fixing_sample_size, p.solving_sample_size), p.corr_sample_size);
     if (cfg->max_n > SPVAR_MAX_N || cfg->max_degree > SPVAR_MAX_DEGREE || Smax > SPVAR_MAX_SAMPLES ||
@@ -428,21 +464,34 @@ int spvar_server_create(const spvar_server_config *cfg, spvar_server **out)
     const int blk = p.sweep_block ? p.sweep_block : 512;
     E.shape = SweepShape{0, blk, Q, 1, 0, 0};
     if (sweep_shape_smem(E.shape, cfg->max_n, stride, cfg->max_degree) > (size_t)optin) E.shape.stage = 0;
-    // +-1-only servers: the streaming +-1 kernel (one quad per CTA) when it fits
+    // +-1-only servers: the quad-group +-1 kernel (work items of Q quads of the
+    // largest admissible problem, more quads of smaller ones) when dmax <= 30 and
+    // Q quads fit shared memory, else the streaming +-1 kernel (one quad per CTA)
     const int md = cfg->max_degree <= 6 ? 6 : 8;
-    if ((p.sweep_kernel == SPVAR_SWEEP_PM1 || p.sweep_kernel == SPVAR_SWEEP_PM1S) && cfg->max_degree <= 8 &&
-        cfg->max_dmax <= 254 && pm1s_shape_ok(blk, md, cfg->max_n, 1)) {
+    const bool pm1_only = p.sweep_kernel == SPVAR_SWEEP_PM1 || p.sweep_kernel == SPVAR_SWEEP_PM1S ||
+                          p.sweep_kernel == SPVAR_SWEEP_PM1Q;
+    bool chosen = false;
+    if (pm1_only && p.sweep_kernel != SPVAR_SWEEP_PM1S && cfg->max_degree <= 8 && cfg->max_dmax <= 30) {
+        const int qb = (p.sweep_block == 128 || p.sweep_block == 256) ? p.sweep_block : 512;
+        SweepShape sh{6, qb, Q, 0, 0, md};
+        if (pm1q_shape_ok(qb, md, cfg->max_n, Q) && sweep_shape_smem(sh, cfg->max_n, stride, cfg->max_degree) <= (size_t)optin) {
+            E.shape = sh;
+            chosen = true;
+        }
+    }
+    if (!chosen && pm1_only && cfg->max_degree <= 8 && cfg->max_dmax <= 254 && pm1s_shape_ok(blk, md, cfg->max_n, 1)) {
         SweepShape sh{2, blk, 1, 0, 0, md};
         if (sweep_shape_smem(sh, cfg->max_n, stride, cfg->max_degree) <= (size_t)optin) {
             E.shape = sh;
             Q = 1;
         }
     }
-    E.C.Q = Q;
+    E.C.Q = E.shape.Q;
+    E.C.chunk = (cfg->sweeps_per_step > 0 && cfg->sweeps_per_step < T) ? cfg->sweeps_per_step : 0;
     E.sweep_smem = sweep_shape_smem(E.shape, cfg->max_n, stride, cfg->max_degree);
     if (E.sweep_smem > (size_t)optin) { server_free(S); return SPVAR_ELIMIT; }
     // +-1-only servers use the byte-wise local field; otherwise general couplers
-    E.pm1 = p.sweep_kernel == SPVAR_SWEEP_PM1 || p.sweep_kernel == SPVAR_SWEEP_PM1S;
+    E.pm1 = pm1_only;
     E.max_n0 = cfg->max_n;
     E.max_deg = cfg->max_degree;
     E.thr_stride = stride;
@@ -450,7 +499,16 @@ int spvar_server_create(const spvar_server_config *cfg, spvar_server **out)
     E.jobs = (SweepJob *)(w + o_jobs);
     E.items = (WorkItem *)(w + o_items);
     E.ctr = (int32_t *)(w + o_ctr);
-    E.ev_sweep[0] = E.ev_sweep[1] = nullptr;
+    // events around the sweep launch of every step (the serving roofline's kernel time)
+    if (cudaEventCreate(&S->ev[0]) != cudaSuccess || cudaEventCreate(&S->ev[1]) != cudaSuccess) {
+        cudaGetLastError();
+        for (cudaEvent_t &e : S->ev) {
+            if (e) cudaEventDestroy(e);
+            e = nullptr;
+        }
+    }
+    E.ev_sweep[0] = S->ev[0];
+    E.ev_sweep[1] = S->ev[1];
     E.ev_post = nullptr;
     const int occ = std::max(1, sweep_shape_occupancy(E.shape, E.pm1, E.sweep_smem));
     S->grid = occ * S->sms;
@@ -509,6 +567,7 @@ int spvar_server_start(spvar_server *S)
     std::lock_guard<std::mutex> g(S->mu);
     if (S->running) return SPVAR_OK;
     S->stop = false;
+    S->failed = false;
     S->running = true;
     S->worker = std::thread(worker_loop, S);
     return SPVAR_OK;
@@ -538,7 +597,7 @@ int spvar_server_wait(spvar_server *S, int64_t id, double timeout_s, spvar_reque
     Request &R = *it->second;
     if (timeout_s > 0 && R.state != 2) {
         const auto until = std::chrono::steady_clock::now() + std::chrono::duration<double>(timeout_s);
-        S->cv.wait_until(lk, until, [&] { return R.state == 2 || S->stop; });
+        S->cv.wait_until(lk, until, [&] { return R.state == 2 || S->stop || S->failed; });
     }
     if (info) {
         info->state = R.state;
@@ -548,7 +607,8 @@ int spvar_server_wait(spvar_server *S, int64_t id, double timeout_s, spvar_reque
         info->queue_s = R.state >= 1 ? R.t_admit - R.t_submit : -1.0;
         info->attempts = R.state == 2 ? request_attempts(S, R) : 0;
     }
-    if (R.state != 2) return S->stop && S->running ? SPVAR_ECUDA : SPVAR_ETIMEOUT;
+    // an engine error fails every wait; a clean stop leaves unfinished requests timed out
+    if (R.state != 2) return S->failed ? SPVAR_ECUDA : SPVAR_ETIMEOUT;
     return SPVAR_OK;
 }
 
@@ -577,6 +637,15 @@ int spvar_server_release(spvar_server *S, int64_t id)
     auto it = S->reqs.find(id);
     if (it == S->reqs.end() || it->second->state != 2) return SPVAR_EINVAL;
     S->reqs.erase(it);
+    return SPVAR_OK;
+}
+
+int spvar_server_sweep_time(spvar_server *S, double *total_ms, int64_t *launches)
+{
+    if (!S) return SPVAR_EINVAL;
+    std::lock_guard<std::mutex> g(S->mu);
+    if (total_ms) *total_ms = S->sweep_ms;
+    if (launches) *launches = S->sweep_launches;
     return SPVAR_OK;
 }
 

@@ -79,7 +79,9 @@ struct SweepJob {
     int32_t S, W;
     uint32_t start, phase;
     const uint32_t *init;  // [S][W] states to continue from, or null: the initial state
-    int32_t t0, pad;       // first sweep to run (the launch runs sweeps t0 .. T-1)
+    int32_t t0;            // first sweep to run
+    int32_t t1;            // end of the sweep range (exclusive); 0: the launch's T.  The launch runs
+                           // sweeps t0 .. min(t1, T) - 1 of this job
 };
 
 // A unit of sweep work: quads [quad0, quad0 + nq) of job `job`.
@@ -115,7 +117,7 @@ struct Slot {
     int32_t nfixed, n0, W0, ocur;
     uint64_t seed;
     uint32_t start;
-    int32_t pad0;
+    int32_t tsw;               // sweeps of the current phase's sample issued so far (chunked phases)
     uint32_t *spins;           // [Smax][W0] current sample
     int64_t *rec_e;            // [P][Smax] recorded full-problem energies
     int32_t *rec_count;        // [P]
@@ -129,7 +131,7 @@ struct Slot {
     int32_t *counts;           // [n0]
     int8_t *fixed;             // [n0]
     int32_t *old_of_new;       // [n0]
-    int32_t *scratch;          // [2 * n0]
+    int32_t *scratch;          // slot_scratch_ints(cap_n) ints: the fold/compact's working arrays
     // component boosting of the solving sample (Sec. II.C); null when off
     int32_t *comp;             // [n0] component of each current spin
     int32_t *part;             // [Smax][n0] twice the partial energy of sample r on component c
@@ -153,6 +155,10 @@ struct SolveConsts {
     // threads x nslot items per thread, colour classes in whole slots); 0: Q quads
     int32_t fit_block, fit_nslot, grid;  // grid: CTAs of the sweep launch
     int32_t fit_words;                   // quad-group kernel: spin words of the launch's shared memory
+    // sweeps per phase, and sweeps per launch (0: the whole phase in one launch).  With
+    // chunk > 0 a phase's sample is annealed over ceil(T / chunk) launches, each resuming
+    // from the states the previous one wrote; the persistence pass runs after the last.
+    int32_t T, chunk;
 };
 // Samples and elite size of a slot's current phase.
 __host__ __device__ inline int phase_samples(const SolveConsts &C, int mode)
@@ -205,7 +211,13 @@ inline void fill_solve_consts(const spvar_params &p, SolveConsts &C)
     C.Smax = std::max(std::max(p.fixing_sample_size, p.solving_sample_size), p.corr_sample_size);
     C.boost = p.component_boost;
     C.tree = p.tree_preprocess;
+    C.T = p.num_sweeps;
+    C.chunk = 0;
 }
+// Sweep launches per phase: ceil(T / chunk), or 1 without chunking.
+inline int launches_per_phase(int T, int chunk) { return (chunk > 0 && T > chunk) ? (T + chunk - 1) / chunk : 1; }
+// True once the slot's current phase has its whole sample (every sweep issued).
+__host__ __device__ inline bool sample_complete(const Slot &s, const SolveConsts &C) { return s.tsw >= C.T; }
 // Bytes of the tree-inference log of one slot (0 when the tree step is off).
 inline size_t tree_slot_bytes(int tree, int n0)
 {
@@ -241,11 +253,31 @@ inline void boost_slot_carve(Slot &s, char *base, int n0, int Smax, int W0)
     s.spins2 = (uint32_t *)(base + o);
 }
 
+// Multi-CTA fold/compact: chunks of kFoldChunk spins, one CTA each.  A slot's
+// scratch holds new_of_old, the free-free row lengths and the folded biases
+// (three [cap_n] arrays, by old index), then a table of kFoldStride ints per
+// chunk (free spins, free-free entries, nonzero-bias flag, the chunk's
+// reference-spin candidate, free spins per colour class) and the int64 sum of
+// the fixed spins' energy.
+constexpr int kFoldChunk = 1024;
+constexpr int kFoldMaxChunks = (SPVAR_MAX_N + kFoldChunk - 1) / kFoldChunk;
+constexpr int kFoldStride = 40;  // >= 6 + kMaxColours
+inline size_t slot_scratch_ints(int cap_n)
+{
+    const size_t base = (3 * (size_t)cap_n + 1) & ~(size_t)1;  // the table starts 8-byte aligned
+    return base + (size_t)kFoldMaxChunks * kFoldStride + 2;
+}
+__host__ __device__ inline size_t fold_table_offset(int cap_n) { return (3 * (size_t)cap_n + 1) & ~(size_t)1; }
+
 cudaError_t launch_slots_init(Slot *slots, const SolveConsts &C, int max_n0, cudaStream_t st);
 cudaError_t launch_plan(Slot *slots, const SolveConsts &C, SweepJob *jobs, WorkItem *items,
                         int32_t *nitems, int32_t *queue, cudaStream_t st);
 cudaError_t launch_elite_slots(Slot *slots, const SolveConsts &C, cudaStream_t st);
 cudaError_t launch_count_slots(Slot *slots, const SolveConsts &C, int max_n0, cudaStream_t st);
+// Fold/compact of every slot whose phase sample is complete, spread over
+// chunks of its spins (tree pre-processing off), then the phase transitions and
+// (nactive != null) the count of slots still active.
+cudaError_t launch_fold_slots(Slot *slots, const SolveConsts &C, int max_n0, int32_t *nactive, cudaStream_t st);
 cudaError_t launch_reduce_slots(Slot *slots, const SolveConsts &C, int32_t *nactive,
                                 cudaStream_t st);
 
@@ -336,6 +368,7 @@ struct SweepShape {
                       // 2 +-1 register form), nslot the acceptance-table width W, maxd the largest degree
     int ncls = 0;     // kind 5, variant 2: colour-class slots per thread (2 or 4)
     int ent32 = 0;    // kind 5, variant 2: 32-bit acceptance entries (no entry of the table is 2^32)
+    int lpp = 1;      // sweep launches per phase (the autotuner's sweeps-per-launch axis)
 };
 // The streaming and warp-per-quad kernels apply to +-1 couplers, degree <= 8
 // and dmax <= 254; the register kernel needs dmax <= 30.

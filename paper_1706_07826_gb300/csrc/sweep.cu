@@ -101,7 +101,7 @@ __device__ void run_item(const SweepLaunch &L, const SweepJob &job, int quad0, i
     const int64_t offset = P->offset;
     const uint32_t k0 = (uint32_t)job.seed, k1 = (uint32_t)(job.seed >> 32);
     const uint32_t phase_hi = job.phase << kSweepBits;
-    const int T = L.T;
+    const int T = job_end(L, job);
 
     uint32_t *sw = reinterpret_cast<uint32_t *>(smem);
     uint32_t *thr_s = sw + (size_t)L.Q * L.max_n;

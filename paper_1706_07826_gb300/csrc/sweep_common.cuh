@@ -45,6 +45,13 @@ __device__ __forceinline__ void energy2(uint32_t own, uint32_t meta, const uint3
     }
 }
 
+// End (exclusive) of the sweep range a work item of `job` runs: the job's own
+// t1 when it is set and below the launch's T, else T.
+__device__ __forceinline__ int job_end(const SweepLaunch &L, const SweepJob &job)
+{
+    return (job.t1 > 0 && job.t1 < L.T) ? job.t1 : L.T;
+}
+
 // Word of spin i (position p) for quad q.  A fresh sample starts from
 // s_i = +1 iff the top bit of the replica's random word at the initial-state
 // slot is set; a resumed one (job.init) continues from bit-packed rows

@@ -84,7 +84,7 @@ __device__ void run_item_pm1q(const SweepLaunch &L, const SweepJob &job, int qua
     const int bias = P->dmax >> 1;
     const int ns = n + 1;
     const uint32_t ns4 = 4u * (uint32_t)ns, q4 = 8u * (uint32_t)ns;  // bytes to the inverted copy / next quad
-    const int T = L.T, t0 = job.t0;
+    const int T = job_end(L, job), t0 = job.t0;
     const uint32_t k0 = (uint32_t)job.seed, k1 = (uint32_t)(job.seed >> 32);
     const uint32_t phase_hi = job.phase << kSweepBits;
     const uint32_t k0w = k0 + kW0p, k1w = k1 + kW1p;

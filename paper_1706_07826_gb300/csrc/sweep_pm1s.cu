@@ -80,7 +80,7 @@ __device__ void run_item_pm1s(const SweepLaunch &L, const SweepJob &job, int qua
     const int cap_n = P->cap_n;
     const int bias = P->dmax >> 1;
     const uint32_t phase_hi = job.phase << kSweepBits;
-    const int T = L.T;
+    const int T = job_end(L, job);
     const int S1 = n;      // one quad per item: the inverted copy follows the plain one
     const int ZERO = 2 * n;
 

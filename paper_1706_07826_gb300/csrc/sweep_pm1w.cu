@@ -78,7 +78,7 @@ __device__ void run_item_pm1w(const SweepLaunch &L, const SweepJob &job, int qua
     const int ncol = P->ncol;
     const int cap_n = P->cap_n;
     const int bias = P->dmax >> 1;
-    const int T = L.T;
+    const int T = job_end(L, job);
     const int max_n = L.max_n;
     const uint32_t k0 = (uint32_t)job.seed, k1 = (uint32_t)(job.seed >> 32);
     const uint32_t phase_hi = job.phase << kSweepBits;

@@ -48,12 +48,13 @@ class Params(ctypes.Structure):
                 ("component_boost", i32), ("tree_preprocess", i32), ("corr_sample_size", i32),
                 ("corr_num", i32), ("corr_den", i32), ("corr_elite_threshold", ctypes.c_double),
                 ("sampler", i32), ("sqa_slices", i32), ("sqa_beta", ctypes.c_double), ("sqa_gamma0", ctypes.c_double),
-                ("sqa_gamma1", ctypes.c_double)]
+                ("sqa_gamma1", ctypes.c_double), ("sweeps_per_launch", i32)]
 
 
 class ServerConfig(ctypes.Structure):
     _fields_ = [("params", Params), ("budget_bytes", ctypes.c_size_t), ("max_n", i32), ("max_nnz", i32),
-                ("max_degree", i32), ("max_dmax", i32), ("energy_scale", i32), ("max_requests", i32)]
+                ("max_degree", i32), ("max_dmax", i32), ("energy_scale", i32), ("max_requests", i32),
+                ("sweeps_per_step", i32)]
 
 
 class RequestInfo(ctypes.Structure):
@@ -107,6 +108,7 @@ def lib():
         L.spvar_plan_destroy.argtypes = [vp]
         L.spvar_plan_destroy.restype = None
         L.spvar_plan_stats.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i32)]
+        L.spvar_plan_sweeps_per_launch.argtypes = [vp, ctypes.POINTER(i32)]
         L.spvar_solve.argtypes = [vp, ctypes.POINTER(Params), u64, ctypes.POINTER(Result), vp]
         L.spvar_plan_set_profiling.argtypes = [vp, i32]
         L.spvar_plan_sweep_time.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i32)]
@@ -122,6 +124,9 @@ def lib():
         L.spvar_server_release.argtypes = [vp, i64]
         L.spvar_server_stats.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i32),
                                          ctypes.POINTER(i32)]
+        L.spvar_measure_issue_rate.argtypes = [i32, i32, ctypes.POINTER(ctypes.c_double),
+                                               ctypes.POINTER(ctypes.c_double), vp]
+        L.spvar_server_sweep_time.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)]
         L.spvar_server_destroy.argtypes = [vp]
         L.spvar_server_destroy.restype = None
         _lib = L
@@ -400,16 +405,29 @@ def reduce_noalloc(problem, fixed, row_ptr, col, val, h, offset, old_of_new, n_o
            "spvar_reduce_noalloc")
 
 
+ISSUE_FORMS = {0: "lop3", 1: "iadd3", 2: "imad", 3: "mix", 4: "wide", 5: "philox"}
+
+
+def measure_issue_rate(form, iters, stream=None):
+    """Thread-level operations/s of one integer issue probe (see
+    spvar_measure_issue_rate) and the timed launch's milliseconds."""
+    r, ms = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    _check(lib().spvar_measure_issue_rate(int(form), int(iters), ctypes.byref(r), ctypes.byref(ms),
+                                          _stream(stream)), "spvar_measure_issue_rate")
+    return r.value, ms.value
+
+
 def make_params(num_starts=1, fixing_sample_size=100, solving_sample_size=100, num_sweeps=1000, beta0=0.1,
                 beta1=3.0, elite_threshold=0.1, fix_num=1, fix_den=1, iterate=False, max_fix_phases=1, canon=-1,
                 form=FORM_BATCHED, replicas_per_block=0, sweep_kernel=SWEEP_AUTO, sweep_block=0, start_offset=0,
                 component_boost=False, tree_preprocess=False, corr_sample_size=0, corr_elite_threshold=0.2,
-                corr_num=1, corr_den=1, sampler=0, sqa_slices=16, sqa_beta=3.0, sqa_gamma0=3.0, sqa_gamma1=0.01):
+                corr_num=1, corr_den=1, sampler=0, sqa_slices=16, sqa_beta=3.0, sqa_gamma0=3.0, sqa_gamma1=0.01,
+                sweeps_per_launch=0):
     return Params(num_starts, fixing_sample_size, solving_sample_size, num_sweeps, beta0, beta1, elite_threshold,
                   fix_num, fix_den, 1 if iterate else 0, max_fix_phases, canon, form, replicas_per_block,
                   sweep_kernel, sweep_block, start_offset, 1 if component_boost else 0, 1 if tree_preprocess else 0,
                   corr_sample_size, corr_num, corr_den, float(corr_elite_threshold), sampler, sqa_slices,
-                  float(sqa_beta), float(sqa_gamma0), float(sqa_gamma1))
+                  float(sqa_beta), float(sqa_gamma0), float(sqa_gamma1), int(sweeps_per_launch))
 
 
 def phase_slots(params):
@@ -501,9 +519,11 @@ class Plan:
         b, r, s, g = i32(0), i32(0), i32(0), i32(0)
         _check(lib().spvar_plan_shape(self.handle, ctypes.byref(b), ctypes.byref(r), ctypes.byref(s), ctypes.byref(g)),
                "spvar_plan_shape")
+        spl = i32(0)
+        _check(lib().spvar_plan_sweeps_per_launch(self.handle, ctypes.byref(spl)), "spvar_plan_sweeps_per_launch")
         return dict(block=b.value, replicas_per_block=r.value, kernel=("general", "general-staged", "pm1-register", "pm1-streaming", "pm1-warp",
                                                                  "sqa", "sqa-register", "pm1-quads")[s.value],
-                    grid=g.value)
+                    grid=g.value, sweeps_per_launch=spl.value)
 
     def close(self):
         if self.handle:
@@ -552,9 +572,9 @@ class Server:
     memory budget, one Alg. 2 phase per engine step for everything in flight."""
 
     def __init__(self, params, budget_bytes, max_n, max_nnz, max_degree, max_dmax, energy_scale=1,
-                 max_requests=16):
+                 max_requests=16, sweeps_per_step=0):
         cfg = ServerConfig(params, int(budget_bytes), max_n, max_nnz, max_degree, max_dmax, energy_scale,
-                           max_requests)
+                           max_requests, int(sweeps_per_step))
         out = vp()
         _check(lib().spvar_server_create(ctypes.byref(cfg), ctypes.byref(out)), "spvar_server_create")
         self.handle = out
@@ -606,6 +626,13 @@ class Server:
         _check(lib().spvar_server_stats(self.handle, ctypes.byref(d), ctypes.byref(a), ctypes.byref(q),
                                         ctypes.byref(r)), "spvar_server_stats")
         return dict(done=d.value, attempts=a.value, queued=q.value, running=r.value)
+
+    def sweep_time(self):
+        """(total ms, launches) of the sweep launches of every engine step so far."""
+        ms, n = ctypes.c_double(0.0), i64(0)
+        _check(lib().spvar_server_sweep_time(self.handle, ctypes.byref(ms), ctypes.byref(n)),
+               "spvar_server_sweep_time")
+        return ms.value, n.value
 
     def close(self):
         if self.handle:

@@ -14,7 +14,13 @@ replicas one by one, or a whole start where that takes seconds.
 - reduced-degeneracy Chimera C8 with biases (U_10, Sec. III.C): one whole
   start and sampled replicas;
 - PTICM (Sec. III.D) on 3D +-J L = 10, 304 runs x 32 temperatures x 2
-  replicas, 1000 sweeps: two whole runs (kept lists, final states).
+  replicas, 1000 sweeps: two whole runs (kept lists, final states);
+- ISPVAR on 3D +-J L = 4 (N = 64), 256 samples, 1000 sweeps, phases until
+  every spin is fixed: every phase's energies, the fix map and the best state;
+- the served stream through spvar_server_* (3D +-J, L = 20, 13 and 8 in one
+  mix, 20 starts x (250 + 250) samples, 5000 sweeps in 500-sweep engine
+  steps, elite 0.2, the server sized for N = 8000): one whole start of the L = 8 request and sampled
+  phase-0 replicas of the L = 20 and odd-L requests.
 """
 import numpy as np
 import pytest
@@ -166,3 +172,80 @@ def test_pticm_3d_l10_full_size(cuda_lib):
             assert np.array_equal(spvar.unpack_spins(g["kept"][run, q, :nk], inst.n), ref["kept"][q, :nk]), (run, q)
         assert np.array_equal(spvar.unpack_spins(g["final_states"][run], inst.n), ref["final"]), run
         assert np.array_equal(g["final_e"][run], ref["final_e"] + inst.offset), run
+
+
+def test_c1_cubic_l4_ispvar_full_size(cuda_lib):
+    """ISPVAR (Sec. II.B) on a 3D +-J L = 4 problem at its benchmark sizes:
+    one start, 256 samples per phase, 1000 sweeps, elite 0.1, SPVAR phases
+    until every spin is fixed (autotuned batched plan, one graph launch)."""
+    from paper_1706_07826_gb300 import spvar
+    inst = I.cubic3d(4, 1100)
+    T, seed = 1000, 2
+    kw = dict(fixing_sample_size=256, solving_sample_size=0, elite_threshold=0.1, iterate=True, max_fix_phases=64)
+    plan = spvar.Plan([gpu_problem(inst)], spvar.make_params(num_starts=1, num_sweeps=T, **kw))
+    out = plan.run(seed, device=False)
+    plan.close()
+    ref = O.solve(oracle_problem(inst), table(inst, T), seed, num_starts=1, **kw)
+    assert ref.nphases[0] > 2
+    assert int(out.nphases[0]) == ref.nphases[0]
+    assert np.array_equal(np.asarray(out.counts[0]), ref.counts[0])
+    assert np.array_equal(np.asarray(out.nfree[0]), ref.nfree[0])
+    for ph in range(ref.nphases[0]):
+        c = ref.counts[0, ph]
+        assert np.array_equal(np.asarray(out.energies[0, ph, :c]), ref.energies[0, ph, :c]), ph
+    assert int(out.best_energy[0]) == ref.best_e[0]
+    assert np.array_equal(np.asarray(out.fixed[:inst.n]), ref.fixed[0])
+    assert np.all(ref.fixed[0] != 0)  # run to exhaustion: every spin fixed
+    assert np.array_equal(np.asarray(out.best_state[:inst.n]), ref.best_state[0])
+
+
+def test_c5_served_stream_full_size(cuda_lib):
+    """The served stream at its benchmark sizes: three 3D +-J requests
+    (L = 20, N = 8000; odd L = 13, three colour classes; L = 8) in one mix
+    through the continuous-batching server configured as the benchmark runs it
+    (N <= 8000, 20 starts x (250 + 250) samples, 5000 sweeps in 500-sweep
+    engine steps, elite 0.2, quad-group kernel).  The
+    oracle recomputes one whole start of the L = 8 request and sampled
+    phase-0 replicas (first, middle, last) of the other two."""
+    from paper_1706_07826_gb300 import spvar
+    T, starts = 5000, 20
+    kw = dict(fixing_sample_size=250, solving_sample_size=250, elite_threshold=0.2)
+    prm = spvar.make_params(num_starts=starts, num_sweeps=T, sweep_kernel=spvar.SWEEP_PM1, **kw)
+    srv = spvar.Server(prm, 8 << 30, max_n=8000, max_nnz=48000, max_degree=6, max_dmax=12, max_requests=32,
+                       sweeps_per_step=500)
+    insts = {20: I.cubic3d(20, 1520), 13: I.cubic3d(13, 1513), 8: I.cubic3d(8, 1508)}
+    seeds = {20: 1620, 13: 1613, 8: 1608}
+    ids = {}
+    ids[20] = srv.submit(insts[20], seeds[20])
+    srv.step()                                   # the L = 20 request runs 500 sweeps alone, the others join
+    ids[13] = srv.submit(insts[13], seeds[13])
+    ids[8] = srv.submit(insts[8], seeds[8])
+    steps = 0
+    while srv.step() > 0 or srv.stats()["queued"] > 0:
+        steps += 1
+        assert steps < 1000
+    out = {L: srv.result(ids[L]) for L in ids}
+    srv.close()
+    # one whole start of the L = 8 request
+    inst = insts[8]
+    op = oracle_problem(inst)
+    thr = table(inst, T, dmax=12)
+    st = 11
+    ref = O.solve(op, thr, seeds[8], num_starts=1, start0=st, **kw)
+    o = out[8]
+    assert np.array_equal(o.counts[st], ref.counts[0]) and np.array_equal(o.nfree[st], ref.nfree[0])
+    for ph in range(ref.nphases[0]):
+        c = ref.counts[0, ph]
+        assert np.array_equal(o.energies[st, ph, :c], ref.energies[0, ph, :c]), ph
+    assert int(o.best_energy[st]) == ref.best_e[0]
+    n = inst.n
+    assert np.array_equal(o.fixed[st * n:(st + 1) * n], ref.fixed[0])
+    assert np.array_equal(o.best_state[st * n:(st + 1) * n], ref.best_state[0])
+    # sampled phase-0 replicas of the largest and of the odd-L request
+    for L, picks in ((20, ((0, 0), (10, 124), (19, 249))), (13, ((0, 0), (7, 125), (19, 249)))):
+        inst = insts[L]
+        op = oracle_problem(inst)
+        thr = table(inst, T, dmax=12)
+        for s, r in picks:
+            _, e, _ = O.sample(op, thr, 1, seeds[L], start=s, phase=0, r0=r)
+            assert out[L].energies[s, 0, r] == e[0] + inst.offset, (L, s, r)

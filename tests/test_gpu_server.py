@@ -33,18 +33,27 @@ def _same(a, b):
             assert np.array_equal(a.energies[s, p, :c], b.energies[s, p, :c])
 
 
-def _server(spvar, budget, max_requests=3, pm1=False):
-    prm = spvar.make_params(**KW, sweep_kernel=spvar.SWEEP_PM1 if pm1 else 0)
-    return spvar.Server(prm, budget, max_n=1000, max_nnz=6000, max_degree=6, max_dmax=12, max_requests=max_requests)
+def _server(spvar, budget, max_requests=3, pm1=False, sweeps_per_step=0, kernel=None):
+    prm = spvar.make_params(**KW, sweep_kernel=(kernel if kernel is not None else spvar.SWEEP_PM1) if pm1 else 0)
+    return spvar.Server(prm, budget, max_n=1000, max_nnz=6000, max_degree=6, max_dmax=12, max_requests=max_requests,
+                        sweeps_per_step=sweeps_per_step)
 
 
-@pytest.mark.parametrize("pm1", [False, True], ids=["general", "pm1"])
-def test_results_identical_alone_and_in_the_mix(cuda_lib, pm1):
+SERVER_CASES = [("general", False, 0, None), ("pm1_quads", True, 0, None), ("pm1_quads_steps17", True, 17, None),
+                ("general_steps25", False, 25, None), ("pm1_streaming_steps9", True, 9, 3)]
+
+
+@pytest.mark.parametrize("name,pm1,sps,kernel", SERVER_CASES, ids=[c[0] for c in SERVER_CASES])
+def test_results_identical_alone_and_in_the_mix(cuda_lib, name, pm1, sps, kernel):
+    """Requests of mixed sizes that arrive while others are in flight and wait
+    for device memory: each result equals the request solved alone, whole
+    phases or sweep chunks per engine step, on the quad-group, streaming and
+    general kernels."""
     spvar = cuda_lib
     insts = [I.cubic3d(4, 61), I.chimera(4, 62), I.cubic3d(5, 63), I.cubic3d(6, 64), I.chimera(3, 65)]
     seeds = [101, 102, 103, 104, 105]
     # budget for about two of these requests at a time: the rest queue for memory
-    srv = _server(spvar, budget=600 << 10, pm1=pm1)
+    srv = _server(spvar, budget=600 << 10, pm1=pm1, sweeps_per_step=sps, kernel=kernel)
     ids = [srv.submit(insts[0], seeds[0])]
     srv.step()                                   # request 0 runs its first phase alone
     ids += [srv.submit(insts[i], seeds[i]) for i in (1, 2, 3)]
@@ -55,7 +64,7 @@ def test_results_identical_alone_and_in_the_mix(cuda_lib, pm1):
     while srv.step() > 0 or srv.stats()["queued"] > 0:
         saw_queue |= srv.stats()["queued"] > 0
         steps += 1
-        assert steps < 100
+        assert steps < 1000
     for rid, inst, seed in zip(ids, insts, seeds):
         info = srv.info(rid)
         assert info.state == 2 and info.latency_s > 0
@@ -65,10 +74,11 @@ def test_results_identical_alone_and_in_the_mix(cuda_lib, pm1):
     srv.close()
 
 
-def test_server_request_matches_oracle(cuda_lib):
+@pytest.mark.parametrize("pm1,sps", [(False, 0), (True, 7)], ids=["general", "pm1_quads_steps7"])
+def test_server_request_matches_oracle(cuda_lib, pm1, sps):
     spvar = cuda_lib
     inst = I.cubic3d(3, 70)
-    srv = _server(spvar, budget=4 << 20)
+    srv = _server(spvar, budget=4 << 20, pm1=pm1, sweeps_per_step=sps)
     rid = srv.submit(inst, 7)
     while srv.step() > 0:
         pass
@@ -106,4 +116,16 @@ def test_server_limits(cuda_lib):
     assert e.value.code == spvar.EBUDGET
     with pytest.raises(spvar.SpvarError):
         srv.submit(I.weak_strong(2, 1), 1)       # dmax beyond the table
+    srv.close()
+
+
+def test_server_sweep_time_counts_every_step(cuda_lib):
+    spvar = cuda_lib
+    srv = _server(spvar, budget=8 << 20, pm1=True, sweeps_per_step=20)
+    srv.submit(I.cubic3d(4, 90), 3)
+    steps = 0
+    while srv.step() > 0:
+        steps += 1
+    ms, n = srv.sweep_time()
+    assert n == steps + 1 and ms > 0
     srv.close()

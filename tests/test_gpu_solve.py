@@ -322,3 +322,53 @@ def test_correlation_fixing_rejects_bad_parameters(cuda_lib):
         with pytest.raises(spvar.SpvarError):
             spvar.solve(gp, spvar.make_params(num_starts=1, fixing_sample_size=8, solving_sample_size=8,
                                               num_sweeps=10, **kw), 1)
+
+
+CHUNK_CASES = [
+    # name, instance, T, sweeps per launch, replicas_per_block, kernel, block, extra oracle/plan options
+    ("register", lambda: I.chimera(3, 41), 60, 25, 8, 2, 128, {}),
+    ("quads_odd", lambda: I.cubic3d(5, 42), 50, 7, 8, 5, 256, {}),
+    ("streaming", lambda: I.cubic3d(5, 43), 40, 13, 4, 3, 256, {}),
+    ("warp", lambda: I.chimera(3, 44), 40, 16, 8, 4, 0, {}),
+    ("general_h", lambda: I.random_graph(30, 70, 3, jmax=3, hmax=2), 45, 20, 4, 1, 256, {}),
+    ("weak_strong_16bit", lambda: I.weak_strong(3, 45), 48, 17, 4, 2, 256, {}),
+    ("autotuned_ispvar", lambda: I.cubic3d(4, 46), 60, 11, 0, 0, 0, dict(iterate=True, max_fix_phases=64)),
+    ("boost_tree", lambda: I.random_graph(40, 48, 17, jmax=3, hmax=2), 36, 9, 0, 0, 0, dict(boost=True, tree=True)),
+]
+
+
+@pytest.mark.parametrize("form", [0, 1], ids=["batched", "plain"])
+@pytest.mark.parametrize("name,make,T,spl,rpb,kernel,block,opts", CHUNK_CASES, ids=[c[0] for c in CHUNK_CASES])
+def test_phase_in_several_sweep_launches(cuda_lib, form, name, make, T, spl, rpb, kernel, block, opts):
+    """A phase annealed over ceil(T / sweeps_per_launch) launches, each resuming
+    from the states the previous one wrote, equals the oracle (every random word
+    is keyed by the absolute sweep), for every sweep kernel, ISPVAR, boosting and
+    tree pre-processing."""
+    from paper_1706_07826_gb300 import spvar
+    inst = make()
+    seed, starts = 99, 3
+    iterate = opts.get("iterate", False)
+    mf = opts.get("max_fix_phases", 1)
+    Ss = 0 if iterate else 30
+    ref = _oracle_solve(inst, T, seed, num_starts=starts, fixing_sample_size=40, solving_sample_size=Ss,
+                        elite_threshold=0.2, iterate=iterate, max_fix_phases=mf, boost=opts.get("boost", False),
+                        tree=opts.get("tree", False))
+    prm = spvar.make_params(num_starts=starts, fixing_sample_size=40, solving_sample_size=Ss, num_sweeps=T,
+                            elite_threshold=0.2, iterate=iterate, max_fix_phases=mf, form=form,
+                            replicas_per_block=rpb, sweep_kernel=kernel, sweep_block=block,
+                            component_boost=opts.get("boost", False), tree_preprocess=opts.get("tree", False),
+                            sweeps_per_launch=spl)
+    plan = spvar.Plan([gpu_problem(inst)], prm)
+    assert plan.shape()["sweeps_per_launch"] == spl
+    out = plan.run(seed, device=False)
+    plan.close()
+    _check(out, ref, starts, mf + 1, inst.n)
+
+
+def test_sweeps_per_launch_rejected_with_sqa(cuda_lib):
+    from paper_1706_07826_gb300 import spvar
+    prm = spvar.make_params(num_starts=1, fixing_sample_size=8, solving_sample_size=8, num_sweeps=10,
+                            sampler=spvar.SAMPLER_SQA, sqa_slices=4, sweeps_per_launch=5)
+    with pytest.raises(spvar.SpvarError) as e:
+        spvar.Plan([gpu_problem(I.chimera(2, 1))], prm)
+    assert e.value.code == spvar.EINVAL
