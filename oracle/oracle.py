@@ -45,6 +45,10 @@ class OrParams(ctypes.Structure):
         ("sqa_gamma0", ctypes.c_double),
         ("sqa_gamma1", ctypes.c_double),
         ("energy_scale", ctypes.c_int32),
+        ("pticm_temps", ctypes.c_int32),
+        ("pticm_keep", ctypes.c_int32),
+        ("pticm_beta0", ctypes.c_double),
+        ("pticm_beta1", ctypes.c_double),
     ]
 
 
@@ -419,15 +423,19 @@ class SolveResult:
 def solve(p: Csr, thr, seed, num_starts, fixing_sample_size, solving_sample_size, elite_threshold,
           fix_num=1, fix_den=1, iterate=False, max_fix_phases=1, canon=-1, start0=0, boost=False, tree=False,
           corr_sample_size=0, corr_elite_threshold=0.2, corr_num=1, corr_den=1, sampler=0, sqa_slices=16,
-          sqa_beta=3.0, sqa_gamma0=3.0, sqa_gamma1=0.01):
+          sqa_beta=3.0, sqa_gamma0=3.0, sqa_gamma1=0.01, pticm_temps=16, pticm_keep=10, pticm_beta0=0.2,
+          pticm_beta1=3.0):
     """Multi-start SPVAR (Alg. 2); thr is the original problem's SA table (its
     length sets the sweeps).  corr_sample_size > 0 adds the correlation-fixing
-    phase for zero-bias problems; sampler = 1 samples every phase with SQA."""
+    phase for zero-bias problems; sampler = 1 samples every phase with SQA,
+    sampler = 2 with PTICM (the phase's sample is the kept lists; see
+    or_params)."""
     thr = _c(thr, np.uint32)
     prm = OrParams(num_starts, fixing_sample_size, solving_sample_size, thr.shape[0], float(elite_threshold),
                    fix_num, fix_den, 1 if iterate else 0, max_fix_phases, canon, start0, 1 if boost else 0,
                    1 if tree else 0, corr_sample_size, corr_num, corr_den, float(corr_elite_threshold), sampler,
-                   sqa_slices, float(sqa_beta), float(sqa_gamma0), float(sqa_gamma1), p.scale)
+                   sqa_slices, float(sqa_beta), float(sqa_gamma0), float(sqa_gamma1), p.scale, pticm_temps,
+                   pticm_keep, float(pticm_beta0), float(pticm_beta1))
     P = max_fix_phases + 1 + (1 if corr_sample_size > 0 else 0)
     Smax = max(fixing_sample_size, solving_sample_size, corr_sample_size)
     n0 = p.n

@@ -851,6 +851,14 @@ int or_solve(int32_t n0, const int32_t *row_ptr0, const int32_t *col0, const int
         prm->corr_sample_size < 0 ||
         (prm->corr_sample_size > 0 && (prm->corr_den <= 0 || prm->corr_num <= 0 || prm->corr_num > prm->corr_den)))
         return -1;
+    if (prm->sampler == 2) {
+        /* PTICM: the sample of a phase is the kept lists, at most 2 (R - R/2) K states */
+        const int32_t R = prm->pticm_temps, ntr = 2 * (prm->pticm_temps - prm->pticm_temps / 2);
+        if (R < 2 || R > 0x7FFF || prm->pticm_keep < 1 || prm->fixing_sample_size != ntr * prm->pticm_keep ||
+            (prm->solving_sample_size != 0 && prm->solving_sample_size != ntr * prm->pticm_keep) ||
+            prm->corr_sample_size != 0 || prm->boost || !(prm->pticm_beta0 > 0.0) || !(prm->pticm_beta1 > 0.0))
+            return -1;
+    }
 
     int32_t *colour0 = (int32_t *)malloc(sizeof(int32_t) * ((size_t)n0 + 1));
     int32_t ncol = or_colour(n0, row_ptr0, col0, colour0);
@@ -895,6 +903,37 @@ int or_solve(int32_t n0, const int32_t *row_ptr0, const int32_t *col0, const int
         free(gt);
         slice = (int32_t *)malloc(sizeof(int32_t) * ((size_t)Smax + 1));
     }
+    /* PTICM: the temperatures' Metropolis tables and the exchange table of the
+       original problem (reductions keep dmax and shrink the energy range), and
+       room for one run's kept lists */
+    uint32_t *pt_thr = NULL, *pt_xthr = NULL;
+    int8_t *pt_kept = NULL, *pt_final = NULL;
+    int64_t *pt_kept_e = NULL, *pt_final_e = NULL;
+    int32_t *pt_nkept = NULL;
+    int32_t pt_R = prm->pticm_temps, pt_K = prm->pticm_keep, pt_from = prm->pticm_temps / 2, pt_dx = 1;
+    if (prm->sampler == 2) {
+        const int32_t ntr = 2 * (pt_R - pt_from);
+        const int32_t scale = prm->energy_scale > 0 ? prm->energy_scale : 1;
+        double *bt = (double *)malloc(sizeof(double) * (size_t)pt_R);
+        double *db = (double *)malloc(sizeof(double) * (size_t)pt_R);
+        or_beta_geometric(pt_R, prm->pticm_beta0, prm->pticm_beta1, bt);
+        for (int32_t k = 0; k + 1 < pt_R; ++k) db[k] = bt[k + 1] - bt[k];
+        int64_t range = 0; /* max E - min E <= 2 (sum_{i<j} |J_ij| + sum_i |h_i|) */
+        for (int64_t q = 0; q < nnz0; ++q) range += val0[q] < 0 ? -(int64_t)val0[q] : val0[q];
+        for (int32_t i = 0; i < n0; ++i) range += 2 * (int64_t)(h0[i] < 0 ? -h0[i] : h0[i]);
+        pt_dx = range > 1 ? (int32_t)range : 1;
+        pt_thr = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)pt_R * ((size_t)dmax + 1));
+        pt_xthr = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)pt_R * ((size_t)pt_dx + 1));
+        or_thresholds(pt_R, bt, dmax, scale, pt_thr);
+        or_thresholds(pt_R - 1, db, pt_dx, scale, pt_xthr);
+        free(bt);
+        free(db);
+        pt_kept = (int8_t *)malloc((size_t)ntr * pt_K * ((size_t)n0 + 1));
+        pt_kept_e = (int64_t *)malloc(sizeof(int64_t) * (size_t)ntr * pt_K);
+        pt_nkept = (int32_t *)malloc(sizeof(int32_t) * (size_t)ntr);
+        pt_final = (int8_t *)malloc((size_t)2 * pt_R * ((size_t)n0 + 1));
+        pt_final_e = (int64_t *)malloc(sizeof(int64_t) * 2 * (size_t)pt_R);
+    }
 
     for (int32_t st = 0; st < prm->num_starts && rc == 0; ++st) {
         int b = 0;
@@ -920,7 +959,18 @@ int or_solve(int32_t n0, const int32_t *row_ptr0, const int32_t *col0, const int
             int fixing = corr || (fphase < prm->max_fix_phases && (fphase == 0 || (prm->iterate && n > 0)));
             int32_t S = corr ? prm->corr_sample_size : fixing ? prm->fixing_sample_size : prm->solving_sample_size;
             if (!fixing && S == 0) break;
-            if (prm->sampler == 1)
+            if (prm->sampler == 2) {
+                rc = or_pticm_sample(n, rp[b], cl[b], vl[b], hh[b], co[b], ncol, pt_R, prm->num_sweeps, pt_thr, dmax,
+                                     pt_xthr, pt_dx, pt_from, pt_from, pt_K, 3, seed, (uint32_t)(prm->start0 + st),
+                                     (uint32_t)phase, pt_kept, pt_kept_e, pt_nkept, pt_final, pt_final_e);
+                /* the sample: every tracked replica's kept states, in list order */
+                S = 0;
+                for (int32_t q = 0; q < 2 * (pt_R - pt_from) && rc == 0; ++q)
+                    for (int32_t x = 0; x < pt_nkept[q]; ++x, ++S) {
+                        memcpy(spins + (int64_t)S * n, pt_kept + ((int64_t)q * pt_K + x) * n, (size_t)n);
+                        e[S] = pt_kept_e[(int64_t)q * pt_K + x];
+                    }
+            } else if (prm->sampler == 1)
                 rc = or_sqa_sample(n, rp[b], cl[b], vl[b], hh[b], co[b], ncol, prm->num_sweeps, prm->sqa_slices,
                                    ent, dmax, 0, S, seed, (uint32_t)(prm->start0 + st), (uint32_t)phase, spins, e,
                                    slice);
@@ -1009,5 +1059,6 @@ int or_solve(int32_t n0, const int32_t *row_ptr0, const int32_t *col0, const int
     free(spins); free(e); free(elite);
     free(tcode); free(tpar); free(tord); free(log_child); free(log_parent); free(log_sigma);
     free(ent); free(slice);
+    free(pt_thr); free(pt_xthr); free(pt_kept); free(pt_kept_e); free(pt_nkept); free(pt_final); free(pt_final_e);
     return rc;
 }

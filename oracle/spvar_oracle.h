@@ -231,10 +231,20 @@ typedef struct or_params {
     double corr_elite_threshold;
     /* Sampler of every phase: 0 = SA with the table thr; 1 = SQA with
      * sqa_slices slices, constant sqa_beta and a transverse field linear from
-     * sqa_gamma0 to sqa_gamma1 over the sweeps (or_gamma_linear). */
+     * sqa_gamma0 to sqa_gamma1 over the sweeps (or_gamma_linear); 2 = PTICM
+     * (Sec. III.D): one run per start and phase with pticm_temps inverse
+     * temperatures geometric from pticm_beta0 to pticm_beta1, exchanges and
+     * cluster moves on, cluster moves and kept lists in the lower half of the
+     * temperatures (k >= R / 2); the phase's sample is the kept lists
+     * (pticm_keep lowest distinct states per tracked replica) in list order,
+     * so its size is the number of states kept (at most 2 (R - R/2) K, which
+     * fixing_sample_size must equal; solving_sample_size 0 or the same; no
+     * correlation step, no boosting). */
     int32_t sampler, sqa_slices;
     double sqa_beta, sqa_gamma0, sqa_gamma1;
-    int32_t energy_scale;          /* the problem's scale (SQA table; >= 1) */
+    int32_t energy_scale;          /* the problem's scale (SQA and PTICM tables; >= 1) */
+    int32_t pticm_temps, pticm_keep;
+    double pticm_beta0, pticm_beta1;
 } or_params;
 
 /* gamma[t] = g0 + (g1 - g0) t / (T - 1); gamma[0] = g0 when T = 1. */
