@@ -16,6 +16,7 @@
 //      key schedule), one per chain group
 // The count is of the probe's own operations (form 3: both kinds; form 4: the
 // wide multiplies; form 5: Philox blocks), per thread, summed over the grid.
+#include "philox.cuh"
 #include "spvar_internal.h"
 
 namespace spvar {
@@ -51,30 +52,17 @@ __global__ void __launch_bounds__(kThreads) k_issue(uint32_t s0, uint32_t s1, in
 {
     uint32_t a[kChains];
 #pragma unroll
-    for (int c = 0; c < kChains; ++c) a[c] = s0 * (threadIdx.x + 1u) + (uint32_t)c * 0x9E3779B9u + blockIdx.x;
+    for (int c = 0; c < kChains; ++c) a[c] = s0 * (threadIdx.x + 1u) + (uint32_t)c * kPhiloxW0 + blockIdx.x;
     if (FORM == 5) {
         // four chain groups of four counter words, one Philox block each per step
         for (int it = 0; it < iters; ++it) {
 #pragma unroll
             for (int g = 0; g < kChains / 4; ++g) {
-                uint32_t k0 = s1, k1 = s0;
-                uint32_t x = a[4 * g], y = a[4 * g + 1], z = a[4 * g + 2], w = a[4 * g + 3];
-#pragma unroll
-                for (int r = 0; r < 10; ++r) {
-                    const uint64_t p0 = (uint64_t)0xD2511F53u * x;
-                    const uint64_t p1 = (uint64_t)0xCD9E8D57u * z;
-                    const uint32_t nx = (uint32_t)(p1 >> 32) ^ y ^ k0, nz = (uint32_t)(p0 >> 32) ^ w ^ k1;
-                    y = (uint32_t)p1;
-                    w = (uint32_t)p0;
-                    x = nx;
-                    z = nz;
-                    k0 += 0x9E3779B9u;
-                    k1 += 0xBB67AE85u;
-                }
-                a[4 * g] = x;
-                a[4 * g + 1] = y;
-                a[4 * g + 2] = z;
-                a[4 * g + 3] = w;
+                const uint4 c = philox4x32_10(make_uint4(a[4 * g], a[4 * g + 1], a[4 * g + 2], a[4 * g + 3]), s1, s0);
+                a[4 * g] = c.x;
+                a[4 * g + 1] = c.y;
+                a[4 * g + 2] = c.z;
+                a[4 * g + 3] = c.w;
             }
         }
     } else {

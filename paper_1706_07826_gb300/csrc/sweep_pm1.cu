@@ -41,7 +41,6 @@ namespace spvar {
 namespace {
 
 constexpr int kRowE = 32;  // 64-bit entries per threshold row: index dE/2 + bias <= 2 * 15
-constexpr uint32_t kM0 = 0xD2511F53u, kM1 = 0xCD9E8D57u, kW0 = 0x9E3779B9u, kW1 = 0xBB67AE85u;
 
 template <int MAXD>
 struct SlotRegs {
@@ -62,13 +61,6 @@ __device__ __forceinline__ void sts_b(uint32_t *base, uint32_t byte_off, uint32_
     *reinterpret_cast<uint32_t *>(reinterpret_cast<char *>(base) + byte_off) = v;
 }
 
-__device__ __forceinline__ void mulhilo(uint32_t m, uint32_t a, uint32_t &hi, uint32_t &lo)
-{
-    const uint64_t p = (uint64_t)m * a;
-    hi = (uint32_t)(p >> 32);
-    lo = (uint32_t)p;
-}
-
 // a * b + c on 32 bits.
 __device__ __forceinline__ uint32_t mad_lo(uint32_t a, uint32_t b, uint32_t c)
 {
@@ -85,57 +77,36 @@ __device__ __forceinline__ void philox_setup(SlotRegs<MAXD> &s, uint32_t i, uint
                                              uint32_t k0, uint32_t k1)
 {
     uint32_t H0, L0, H1, L1, H2, L2, H3, L3;
-    mulhilo(kM0, i, H0, L0);
-    mulhilo(kM1, q, H1, L1);
+    philox_mulhilo(kPhiloxM0, i, H0, L0);
+    philox_mulhilo(kPhiloxM1, q, H1, L1);
     const uint32_t Z = H0 ^ start ^ k1;            // round-1 counter word 2
-    mulhilo(kM1, Z, H2, L2);                        // round-2 product of word 2
-    const uint32_t C1 = H2 ^ L1 ^ (k0 + kW0);       // round-2 counter word 0
-    mulhilo(kM0, C1, H3, L3);                       // round-3 product of word 0
+    philox_mulhilo(kPhiloxM1, Z, H2, L2);                        // round-2 product of word 2
+    const uint32_t C1 = H2 ^ L1 ^ (k0 + kPhiloxW0);       // round-2 counter word 0
+    philox_mulhilo(kPhiloxM0, C1, H3, L3);                       // round-3 product of word 0
     s.A = H1 ^ k0;
-    s.L0k = L0 ^ (k1 + kW1);
-    s.D = L2 ^ (k0 + 2 * kW0);
-    s.H3k = H3 ^ (k1 + 2 * kW1);
+    s.L0k = L0 ^ (k1 + kPhiloxW1);
+    s.D = L2 ^ (k0 + 2 * kPhiloxW0);
+    s.H3k = H3 ^ (k1 + 2 * kPhiloxW1);
     s.L3 = L3;
 }
 
 // Round keys 3..9 of the item's seed.
-struct RoundKeys {
-    uint32_t k0[7], k1[7];
-};
-
-__device__ __forceinline__ RoundKeys round_keys(uint32_t k0, uint32_t k1)
-{
-    RoundKeys K;
-#pragma unroll
-    for (int r = 3; r < 10; ++r) {
-        K.k0[r - 3] = k0 + (uint32_t)r * kW0;
-        K.k1[r - 3] = k1 + (uint32_t)r * kW1;
-    }
-    return K;
-}
+using RoundKeys = PhiloxKeys<3>;
 
 // (h, l): the round-2 product of word 0, M0 (A ^ y).
 template <int MAXD>
 __device__ __forceinline__ uint4 philox_slot_hl(const SlotRegs<MAXD> &s, uint32_t h, uint32_t l, const RoundKeys &K)
 {
     uint32_t h2, l2;
-    mulhilo(kM1, h ^ s.L0k, h2, l2);      // round 3: word 2 product
-    uint4 c = make_uint4(h2 ^ s.D, l2, s.H3k ^ l, s.L3);
-#pragma unroll
-    for (int r = 3; r < 10; ++r) {
-        uint32_t a, b, e, f;
-        mulhilo(kM0, c.x, a, b);
-        mulhilo(kM1, c.z, e, f);
-        c = make_uint4(e ^ c.y ^ K.k0[r - 3], f, a ^ c.w ^ K.k1[r - 3], b);
-    }
-    return c;
+    philox_mulhilo(kPhiloxM1, h ^ s.L0k, h2, l2);      // round 3: word 2 product
+    return philox_rounds<3>(make_uint4(h2 ^ s.D, l2, s.H3k ^ l, s.L3), K);
 }
 
 template <int MAXD>
 __device__ __forceinline__ uint4 philox_slot(const SlotRegs<MAXD> &s, uint32_t y, const RoundKeys &K)
 {
     uint32_t h, l;
-    mulhilo(kM0, s.A ^ y, h, l);          // round 2: word 0 product
+    philox_mulhilo(kPhiloxM0, s.A ^ y, h, l);          // round 2: word 0 product
     return philox_slot_hl(s, h, l, K);
 }
 
@@ -162,7 +133,7 @@ __device__ __forceinline__ void sweep_once(Pm1Smem<B, NSLOT> &sm, unsigned long 
                                            uint32_t k16, const uint32_t *next_src, int bias, uint32_t A0)
 {
     uint32_t hA = 0u, lA = 0u;
-    if (ONEQ) mulhilo(kM0, A0 ^ y, hA, lA);
+    if (ONEQ) philox_mulhilo(kPhiloxM0, A0 ^ y, hA, lA);
     constexpr uint32_t kInv = 4u * (uint32_t)Pm1Smem<B, NSLOT>::KW;  // byte distance to the inverted copy
     // next sweep's row (its buffer was last read in the previous sweep)
     if (SCALED) {
@@ -268,7 +239,7 @@ __device__ void run_item_pm1(const SweepLaunch &L, const SweepJob &job, int quad
     const int bias = P->dmax >> 1;
     const uint32_t k0 = (uint32_t)job.seed, k1 = (uint32_t)(job.seed >> 32);
     const uint32_t phase_hi = job.phase << kSweepBits;
-    const int T = L.T;
+    const int T = job_end(L, job);
     const int t0 = job.t0;
     // a 1 the compiler cannot fold, so the multiply-adds stay on the FMA pipe
     const uint32_t one = (uint32_t)(L.thr_stride > 0);
@@ -304,7 +275,7 @@ __device__ void run_item_pm1(const SweepLaunch &L, const SweepJob &job, int quad
     // colour-aligned slots
     SlotRegs<MAXD> s[NSLOT];
     uint32_t barmask = 0;
-    const RoundKeys K = round_keys(k0, k1);
+    const RoundKeys K = philox_keys<3>(k0, k1);
     const uint32_t dummy = 4u * (uint32_t)(KW - 1), zero = 4u * (uint32_t)(2 * KW);
 #pragma unroll
     for (int j = 0; j < NSLOT; ++j) {
@@ -369,7 +340,7 @@ __device__ void run_item_pm1(const SweepLaunch &L, const SweepJob &job, int quad
 
     if (nq == 1) {
         uint32_t H1, L1;
-        mulhilo(kM1, (uint32_t)quad0, H1, L1);
+        philox_mulhilo(kPhiloxM1, (uint32_t)quad0, H1, L1);
         sweeps<B, NSLOT, MAXD, SCALED, SI, true>(sm, drow, s, t0, T, phase_hi, K, barmask, one, k16, thr, ts, bias,
                                              H1 ^ k0);
     } else {

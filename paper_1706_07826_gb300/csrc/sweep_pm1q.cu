@@ -24,14 +24,6 @@ namespace {
 
 constexpr int kRowQ = 32;   // 64-bit entries per threshold row: index dE/2 + bias <= 30
 constexpr int kQcap = 64;   // most quads per work item
-constexpr uint32_t kM0p = 0xD2511F53u, kM1p = 0xCD9E8D57u, kW0p = 0x9E3779B9u, kW1p = 0xBB67AE85u;
-
-__device__ __forceinline__ void mulhilo_p(uint32_t m, uint32_t a, uint32_t &hi, uint32_t &lo)
-{
-    const uint64_t p = (uint64_t)m * a;
-    hi = (uint32_t)(p >> 32);
-    lo = (uint32_t)p;
-}
 
 __device__ __forceinline__ uint32_t madlo_p(uint32_t a, uint32_t b, uint32_t c)
 {
@@ -57,20 +49,13 @@ struct QuadSmem {
     int cptr[kMaxColours + 1];
 };
 
-// Counter (i, y, quad, start), rounds 3..10 from the round-2 output
-// (H2 ^ L1k, L2, HA ^ L0k, LA).  Kr: keys of rounds 3..10.
+
+// Counter (i, y, quad, start), rounds 3..10 (0-based 2..9) from the round-2
+// output (H2 ^ L1k, L2, HA ^ L0k, LA).
 __device__ __forceinline__ uint4 philox_tail(uint32_t cx, uint32_t cy, uint32_t cz, uint32_t cw,
-                                             const uint32_t (&Kr0)[8], const uint32_t (&Kr1)[8])
+                                             const PhiloxKeys<2> &K)
 {
-    uint4 c = make_uint4(cx, cy, cz, cw);
-#pragma unroll
-    for (int r = 0; r < 8; ++r) {
-        uint32_t a, b, e, f;
-        mulhilo_p(kM0p, c.x, a, b);
-        mulhilo_p(kM1p, c.z, e, f);
-        c = make_uint4(e ^ c.y ^ Kr0[r], f, a ^ c.w ^ Kr1[r], b);
-    }
-    return c;
+    return philox_rounds<2>(make_uint4(cx, cy, cz, cw), K);
 }
 
 template <int B, int MAXD>
@@ -87,7 +72,7 @@ __device__ void run_item_pm1q(const SweepLaunch &L, const SweepJob &job, int qua
     const int T = job_end(L, job), t0 = job.t0;
     const uint32_t k0 = (uint32_t)job.seed, k1 = (uint32_t)(job.seed >> 32);
     const uint32_t phase_hi = job.phase << kSweepBits;
-    const uint32_t k0w = k0 + kW0p, k1w = k1 + kW1p;
+    const uint32_t k0w = k0 + kPhiloxW0, k1w = k1 + kPhiloxW1;
     // a 1 the compiler cannot fold, so the multiply-adds stay on the FMA pipe
     const uint32_t one = (uint32_t)(L.thr_stride > 0);
 
@@ -100,9 +85,9 @@ __device__ void run_item_pm1q(const SweepLaunch &L, const SweepJob &job, int qua
     }
     for (int q = tid; q < nq; q += B) {
         uint32_t H1, L1, HA, LA;
-        mulhilo_p(kM1p, (uint32_t)(quad0 + q), H1, L1);
+        philox_mulhilo(kPhiloxM1, (uint32_t)(quad0 + q), H1, L1);
         sm.qk[q] = make_uint2(L1 ^ k0w, H1 ^ k0);
-        mulhilo_p(kM0p, H1 ^ k0 ^ (phase_hi | (uint32_t)t0), HA, LA);
+        philox_mulhilo(kPhiloxM0, H1 ^ k0 ^ (phase_hi | (uint32_t)t0), HA, LA);
         sm.qs[t0 & 1][q] = make_uint2(HA, LA);
     }
     // threshold rows: entry i = 2^32 - thr[t][2 (i - bias)] for i > bias, 0 (always accept) otherwise
@@ -115,12 +100,7 @@ __device__ void run_item_pm1q(const SweepLaunch &L, const SweepJob &job, int qua
     }
     __syncthreads();
 
-    uint32_t Kr0[8], Kr1[8];
-#pragma unroll
-    for (int r = 0; r < 8; ++r) {
-        Kr0[r] = k0 + (uint32_t)(r + 2) * kW0p;
-        Kr1[r] = k1 + (uint32_t)(r + 2) * kW1p;
-    }
+    const PhiloxKeys<2> Kr = philox_keys<2>(k0, k1);
     const uint32_t k16 = (uint32_t)(16 * bias) * M;
 
     for (int t = t0; t < T; ++t) {
@@ -134,7 +114,7 @@ __device__ void run_item_pm1q(const SweepLaunch &L, const SweepJob &job, int qua
             }
             for (int q = tid; q < nq; q += B) {
                 uint32_t HA, LA;
-                mulhilo_p(kM0p, sm.qk[q].y ^ (phase_hi | (uint32_t)(t + 1)), HA, LA);
+                philox_mulhilo(kPhiloxM0, sm.qk[q].y ^ (phase_hi | (uint32_t)(t + 1)), HA, LA);
                 sm.qs[par ^ 1][q] = make_uint2(HA, LA);
             }
         }
@@ -162,8 +142,8 @@ __device__ void run_item_pm1q(const SweepLaunch &L, const SweepJob &job, int qua
                     const uint32_t c0 = (uint32_t)(8 * (bias - deg + ((int)meta >> 16))) * M;
                     // Philox products of the spin and the start: rounds 1 (word 0) and 2 (word 2)
                     uint32_t H0, L0, H2, L2;
-                    mulhilo_p(kM0p, (uint32_t)__ldg(P->idx_of_pos + p), H0, L0);
-                    mulhilo_p(kM1p, H0 ^ job.start ^ k1, H2, L2);
+                    philox_mulhilo(kPhiloxM0, (uint32_t)__ldg(P->idx_of_pos + p), H0, L0);
+                    philox_mulhilo(kPhiloxM1, H0 ^ job.start ^ k1, H2, L2);
                     const uint32_t L0k = L0 ^ k1w;
                     const uint32_t own4 = 4u * (uint32_t)p;
                     // quads g, g + G, ... two at a time (no item reads a word another writes)
@@ -185,7 +165,7 @@ __device__ void run_item_pm1q(const SweepLaunch &L, const SweepJob &job, int qua
 #pragma unroll
                         for (int k = 0; k < 2; ++k) {
                             const uint2 qk = sm.qk[qq[k]], qs = qsp[qq[k]];
-                            const uint4 r4 = philox_tail(H2 ^ qk.x, L2, qs.x ^ L0k, qs.y, Kr0, Kr1);
+                            const uint4 r4 = philox_tail(H2 ^ qk.x, L2, qs.x ^ L0k, qs.y, Kr);
                             // 8 (dE/2 + bias) per byte: 16 x + 8 (bias - deg + h) for b_i = 0, its
                             // mirror 16 bias - that for b_i = 1
                             const uint32_t a = madlo_p(x[k], 16u * one, c0);

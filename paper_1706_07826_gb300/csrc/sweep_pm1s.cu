@@ -20,11 +20,7 @@ namespace spvar {
 namespace {
 
 constexpr int kRowWordsS = 256;
-constexpr uint32_t kSW0 = 0x9E3779B9u, kSW1 = 0xBB67AE85u;
-
-struct Keys10 {
-    uint32_t k0[10], k1[10];
-};
+using Keys10 = PhiloxKeys<0>;
 
 // Philox4x32-10 of counter (i, y, quad, start) with the quad's products
 // hoisted: L1k = lo(M1 quad) ^ key0 of round 2 (per CTA item), (HA, LA) = M0 (hi(M1 quad) ^ y ^ key0)
@@ -32,17 +28,10 @@ struct Keys10 {
 __device__ __forceinline__ uint4 philox_quad(uint32_t i, uint32_t zs, uint32_t L1k, uint32_t HA, uint32_t LA,
                                              const Keys10 &K)
 {
-    const uint64_t p0 = (uint64_t)0xD2511F53u * i;                          // round 1, word 0
-    const uint64_t p1 = (uint64_t)0xCD9E8D57u * ((uint32_t)(p0 >> 32) ^ zs);  // round 2, word 2
-    uint4 c = make_uint4((uint32_t)(p1 >> 32) ^ L1k, (uint32_t)p1, HA ^ (uint32_t)p0 ^ K.k1[1], LA);
-#pragma unroll
-    for (int r = 2; r < 10; ++r) {
-        const uint64_t q0 = (uint64_t)0xD2511F53u * c.x;
-        const uint64_t q1 = (uint64_t)0xCD9E8D57u * c.z;
-        c = make_uint4((uint32_t)(q1 >> 32) ^ c.y ^ K.k0[r], (uint32_t)q1, (uint32_t)(q0 >> 32) ^ c.w ^ K.k1[r],
-                       (uint32_t)q0);
-    }
-    return c;
+    uint32_t h0, l0, h1, l1;
+    philox_mulhilo(kPhiloxM0, i, h0, l0);       // round 1, word 0
+    philox_mulhilo(kPhiloxM1, h0 ^ zs, h1, l1);  // round 2, word 2
+    return philox_rounds<2>(make_uint4(h1 ^ L1k, l1, HA ^ l0 ^ K.k1[1], LA), K);
 }
 
 template <int MAXD>
@@ -111,24 +100,17 @@ __device__ void run_item_pm1s(const SweepLaunch &L, const SweepJob &job, int qua
             trow[(t0 & 1) * kRowWordsS + bias + e] = L.thr[(size_t)t0 * L.thr_stride + 2 * e];
     __syncthreads();
 
-    Keys10 K;
-    {
-        const uint32_t k0 = (uint32_t)job.seed, k1 = (uint32_t)(job.seed >> 32);
-#pragma unroll
-        for (int r = 0; r < 10; ++r) {
-            K.k0[r] = k0 + (uint32_t)r * kSW0;
-            K.k1[r] = k1 + (uint32_t)r * kSW1;
-        }
-    }
+    const Keys10 K = philox_keys<0>((uint32_t)job.seed, (uint32_t)(job.seed >> 32));
 
     // the quad's Philox products: round 1 word 2 per item, round 2 word 0 per sweep
-    const uint64_t pq = (uint64_t)0xCD9E8D57u * (uint32_t)quad0;
-    const uint32_t H1 = (uint32_t)(pq >> 32), L1k = (uint32_t)pq ^ K.k0[1], zs = job.start ^ K.k1[0];
+    uint32_t H1, L1;
+    philox_mulhilo(kPhiloxM1, (uint32_t)quad0, H1, L1);
+    const uint32_t L1k = L1 ^ K.k0[1], zs = job.start ^ K.k1[0];
     for (int t = t0; t < T; ++t) {
         const uint32_t *th = trow + (t & 1) * kRowWordsS;
         const uint32_t y = phase_hi | (uint32_t)t;
-        const uint64_t pa = (uint64_t)0xD2511F53u * (H1 ^ y ^ K.k0[0]);
-        const uint32_t HA = (uint32_t)(pa >> 32), LA = (uint32_t)pa;
+        uint32_t HA, LA;
+        philox_mulhilo(kPhiloxM0, H1 ^ y ^ K.k0[0], HA, LA);
         for (int c = 0; c < ncol; ++c) {
             if (c == 0 && t + 1 < T) {
                 uint32_t *nxt = trow + ((t + 1) & 1) * kRowWordsS;

@@ -22,14 +22,6 @@ namespace spvar {
 namespace {
 
 constexpr int kRowW = 128;  // one threshold row: entries for dE/2 = 1 .. bias (bias <= 127)
-constexpr uint32_t kM0w = 0xD2511F53u, kM1w = 0xCD9E8D57u, kW0w = 0x9E3779B9u, kW1w = 0xBB67AE85u;
-
-__device__ __forceinline__ void mulhilo_w(uint32_t m, uint32_t a, uint32_t &hi, uint32_t &lo)
-{
-    const uint64_t p = (uint64_t)m * a;
-    hi = (uint32_t)(p >> 32);
-    lo = (uint32_t)p;
-}
 
 // Words of shared memory per CTA for a problem of at most max_n spins.
 __host__ __device__ inline size_t pm1w_words(int max_n, int warps, int maxd)
@@ -101,12 +93,12 @@ __device__ void run_item_pm1w(const SweepLaunch &L, const SweepJob &job, int qua
     for (int p = tid; p < n; p += B) {
         meta_s[p] = P->meta[p];
         uint32_t H0, L0, H2, L2;
-        mulhilo_w(kM0w, (uint32_t)P->idx_of_pos[p], H0, L0);
+        philox_mulhilo(kPhiloxM0, (uint32_t)P->idx_of_pos[p], H0, L0);
         const uint32_t Z = H0 ^ job.start ^ k1;  // round-1 counter word 2
-        mulhilo_w(kM1w, Z, H2, L2);              // its round-2 product
-        l0k_s[p] = L0 ^ (k1 + kW1w);
+        philox_mulhilo(kPhiloxM1, Z, H2, L2);              // its round-2 product
+        l0k_s[p] = L0 ^ (k1 + kPhiloxW1);
         h2_s[p] = H2;
-        d_s[p] = L2 ^ (k0 + 2 * kW0w);
+        d_s[p] = L2 ^ (k0 + 2 * kPhiloxW0);
     }
     for (int x = tid; x < MAXD * n; x += B) {
         const int d = x / n, p = x - d * n;
@@ -133,16 +125,11 @@ __device__ void run_item_pm1w(const SweepLaunch &L, const SweepJob &job, int qua
         if (lane == 0) sw[2 * n] = 0u;
         // quad constants of rounds 1-3
         uint32_t H1, L1;
-        mulhilo_w(kM1w, q, H1, L1);
+        philox_mulhilo(kPhiloxM1, q, H1, L1);
         const uint32_t A = H1 ^ k0;                // round-1 word 0 = A ^ sweep word
-        const uint32_t L1k = L1 ^ (k0 + kW0w);     // round-2 word 0 = H2 ^ L1k
-        uint32_t K0[7], K1[7];
-#pragma unroll
-        for (int r = 3; r < 10; ++r) {
-            K0[r - 3] = k0 + (uint32_t)r * kW0w;
-            K1[r - 3] = k1 + (uint32_t)r * kW1w;
-        }
-        const uint32_t k1_2 = k1 + 2 * kW1w;
+        const uint32_t L1k = L1 ^ (k0 + kPhiloxW0);     // round-2 word 0 = H2 ^ L1k
+        const PhiloxKeys<3> Kr = philox_keys<3>(k0, k1);
+        const uint32_t k1_2 = k1 + 2 * kPhiloxW1;
         const int t0 = job.t0;
         if (t0 < T)
             for (int e = lane + 1; e <= bias; e += 32)
@@ -154,7 +141,7 @@ __device__ void run_item_pm1w(const SweepLaunch &L, const SweepJob &job, int qua
             const uint32_t y = phase_hi | (uint32_t)t;
             // round-2 product of word 0: the same for every spin of the quad
             uint32_t hh, ll;
-            mulhilo_w(kM0w, A ^ y, hh, ll);
+            philox_mulhilo(kPhiloxM0, A ^ y, hh, ll);
             const uint32_t lk = ll ^ k1_2;
             for (int c = 0; c < ncol; ++c) {
                 if (c == 0 && t + 1 < T) {
@@ -177,17 +164,9 @@ __device__ void run_item_pm1w(const SweepLaunch &L, const SweepJob &job, int qua
                     for (int k = 0; k < K; ++k) {
                         const int p = pp[k];
                         uint32_t h3, l3, HH, LL;
-                        mulhilo_w(kM1w, hh ^ l0k_s[p], h3, l3);        // round 2, word 2
-                        mulhilo_w(kM0w, h2_s[p] ^ L1k, HH, LL);        // round 3, word 0
-                        uint4 cc = make_uint4(h3 ^ d_s[p], l3, HH ^ lk, LL);
-#pragma unroll
-                        for (int r = 3; r < 10; ++r) {
-                            uint32_t a, b, e, f;
-                            mulhilo_w(kM0w, cc.x, a, b);
-                            mulhilo_w(kM1w, cc.z, e, f);
-                            cc = make_uint4(e ^ cc.y ^ K0[r - 3], f, a ^ cc.w ^ K1[r - 3], b);
-                        }
-                        u[k] = cc;
+                        philox_mulhilo(kPhiloxM1, hh ^ l0k_s[p], h3, l3);        // round 2, word 2
+                        philox_mulhilo(kPhiloxM0, h2_s[p] ^ L1k, HH, LL);        // round 3, word 0
+                        u[k] = philox_rounds<3>(make_uint4(h3 ^ d_s[p], l3, HH ^ lk, LL), Kr);
                     }
                     uint32_t w[K];
 #pragma unroll

@@ -41,34 +41,17 @@ __host__ __device__ inline size_t sqa_words(int max_n, int P, int maxdeg, int W,
     return w + 4 * (size_t)P + 4;
 }
 
-constexpr uint32_t kM0q = 0xD2511F53u, kM1q = 0xCD9E8D57u, kW0q = 0x9E3779B9u, kW1q = 0xBB67AE85u;
-
-__device__ __forceinline__ void mulhilo_q(uint32_t m, uint32_t a, uint32_t &hi, uint32_t &lo)
-{
-    const uint64_t p = (uint64_t)m * a;
-    hi = (uint32_t)(p >> 32);
-    lo = (uint32_t)p;
-}
 
 // Philox4x32-10 of counter (w0, y, quad, start) with the products that do not
 // depend on w0 hoisted: (H1, L1) = M1 * quad (round 1, per CTA) and
-// (HA, LA) = M0 * (H1 ^ y ^ k0) (round 2, per sweep).  Kr0/Kr1: keys of rounds 3..10.
+// (HA, LA) = M0 * (H1 ^ y ^ k0) (round 2, per sweep).  Kr: keys of rounds 3..10 (0-based 2..9).
 __device__ __forceinline__ uint4 philox_sqa(uint32_t w0, uint32_t start, uint32_t k1, uint32_t L1, uint32_t HA,
-                                            uint32_t LA, uint32_t k0w, uint32_t k1w, const uint32_t (&Kr0)[8],
-                                            const uint32_t (&Kr1)[8])
+                                            uint32_t LA, uint32_t k0w, uint32_t k1w, const PhiloxKeys<2> &Kr)
 {
     uint32_t h0, l0, hb, lb;
-    mulhilo_q(kM0q, w0, h0, l0);                       // round 1, word 0
-    mulhilo_q(kM1q, h0 ^ start ^ k1, hb, lb);          // round 2, word 2
-    uint4 c = make_uint4(hb ^ L1 ^ k0w, lb, HA ^ l0 ^ k1w, LA);
-#pragma unroll
-    for (int r = 0; r < 8; ++r) {
-        uint32_t a, b, e, f;
-        mulhilo_q(kM0q, c.x, a, b);
-        mulhilo_q(kM1q, c.z, e, f);
-        c = make_uint4(e ^ c.y ^ Kr0[r], f, a ^ c.w ^ Kr1[r], b);
-    }
-    return c;
+    philox_mulhilo(kPhiloxM0, w0, h0, l0);                       // round 1, word 0
+    philox_mulhilo(kPhiloxM1, h0 ^ start ^ k1, hb, lb);          // round 2, word 2
+    return philox_rounds<2>(make_uint4(hb ^ L1 ^ k0w, lb, HA ^ l0 ^ k1w, LA), Kr);
 }
 
 // a * b + c on 32 bits, on the FMA pipe.
@@ -111,8 +94,7 @@ template <int PAR, int MAXD, int U, bool E32, bool SI>
 __device__ __forceinline__ void sqa_reg_items(uint32_t *sw, const void *entv, int P, const int (&tau)[U],
                                               const uint32_t (&base)[U], const uint32_t (&iw)[U], uint32_t own4,
                                               const uint32_t (&o4)[MAXD], uint32_t c0, uint32_t jp,
-                                              const SqaRegConsts &K, const uint32_t (&Kr0)[8],
-                                              const uint32_t (&Kr1)[8], bool chain, bool have, uint32_t &prev_up)
+                                              const SqaRegConsts &K, const PhiloxKeys<2> &Kr, bool chain, bool have, uint32_t &prev_up)
 {
     constexpr uint32_t M = 0x01010101u;
     uint32_t oa[U], own[U], up[U], dn[U], x[U];
@@ -148,7 +130,7 @@ __device__ __forceinline__ void sqa_reg_items(uint32_t *sw, const void *entv, in
         const uint32_t m = own[u] * 0xFFu;
         const uint32_t kk = (a & ~m) | (b & m);
         const uint32_t full = SI ? 0u : a4 * K.W + kk;  // entry a W + k per byte, <= 3W - 1 <= 255
-        const uint4 r4 = philox_sqa(iw[u], K.start, K.k1, K.L1, K.HA, K.LA, K.k0w, K.k1w, Kr0, Kr1);
+        const uint4 r4 = philox_sqa(iw[u], K.start, K.k1, K.L1, K.HA, K.LA, K.k0w, K.k1w, Kr);
         const uint32_t ur[4] = {r4.x, r4.y, r4.z, r4.w};
         uint32_t rej = 0;
 #pragma unroll
@@ -174,8 +156,7 @@ __device__ __forceinline__ void sqa_reg_items(uint32_t *sw, const void *entv, in
 template <int PAR, int MAXD, bool E32, bool SI>
 __device__ __forceinline__ void sqa_reg_pass(uint32_t *sw, const void *ent, int g, int G, int P, uint32_t own4,
                                              const uint32_t (&o4)[MAXD], uint32_t c0, uint32_t jp, uint32_t ib,
-                                             const SqaRegConsts &K, const uint32_t (&Kr0)[8],
-                                             const uint32_t (&Kr1)[8])
+                                             const SqaRegConsts &K, const PhiloxKeys<2> &Kr)
 {
     if (g < 0) return;
     const int dt = 2 * G;
@@ -189,14 +170,14 @@ __device__ __forceinline__ void sqa_reg_pass(uint32_t *sw, const void *ent, int 
     for (; tau + dt < P; tau += 2 * dt, base += 2 * step, iw += 2 * istep) {
         const int t2[2] = {tau, tau + dt};
         const uint32_t b2[2] = {base, base + step}, i2[2] = {iw, iw + istep};
-        sqa_reg_items<PAR, MAXD, 2, E32, SI>(sw, ent, P, t2, b2, i2, own4, o4, c0, jp, K, Kr0, Kr1, chain, have,
+        sqa_reg_items<PAR, MAXD, 2, E32, SI>(sw, ent, P, t2, b2, i2, own4, o4, c0, jp, K, Kr, chain, have,
                                              prev_up);
         have = true;
     }
     if (tau < P) {
         const int t1[1] = {tau};
         const uint32_t b1[1] = {base}, i1[1] = {iw};
-        sqa_reg_items<PAR, MAXD, 1, E32, SI>(sw, ent, P, t1, b1, i1, own4, o4, c0, jp, K, Kr0, Kr1, chain, have,
+        sqa_reg_items<PAR, MAXD, 1, E32, SI>(sw, ent, P, t1, b1, i1, own4, o4, c0, jp, K, Kr, chain, have,
                                              prev_up);
     }
 }
@@ -261,14 +242,9 @@ __device__ void run_item_sqa(const SweepLaunch &L, const SweepJob &job, int quad
 
     // Philox parts fixed for this quad
     uint32_t H1, L1;
-    mulhilo_q(kM1q, (uint32_t)quad, H1, L1);
-    const uint32_t k0w = k0 + kW0q, k1w = k1 + kW1q;
-    uint32_t Kr0[8], Kr1[8];
-#pragma unroll
-    for (int r = 0; r < 8; ++r) {
-        Kr0[r] = k0 + (uint32_t)(r + 2) * kW0q;
-        Kr1[r] = k1 + (uint32_t)(r + 2) * kW1q;
-    }
+    philox_mulhilo(kPhiloxM1, (uint32_t)quad, H1, L1);
+    const uint32_t k0w = k0 + kPhiloxW0, k1w = k1 + kPhiloxW1;
+    const PhiloxKeys<2> Kr = philox_keys<2>(k0, k1);
 
     const int nt = (P > 1) ? P / 2 : 1;  // slices per parity
     // register form: +-1 couplers, two or more slices, at most NC colour classes of at most B spins
@@ -342,15 +318,13 @@ __device__ void run_item_sqa(const SweepLaunch &L, const SweepJob &job, int quad
                 else
                     for (int x = tid; x < 3 * W; x += B) rows[((t + 1) & 1) * 3 * W + x] = src[x];
             }
-            mulhilo_q(kM0q, H1 ^ (phase_hi | (uint32_t)t) ^ k0, K.HA, K.LA);
+            philox_mulhilo(kPhiloxM0, H1 ^ (phase_hi | (uint32_t)t) ^ k0, K.HA, K.LA);
 #pragma unroll
             for (int j = 0; j < NCR; ++j) {
                 if (j < ncol) {
-                    sqa_reg_pass<0, MAXD, E32, SI>(sw, ent, g[j], G[j], P, own4[j], o4[j], c0[j], jp[j], ib[j], K, Kr0,
-                                                   Kr1);
+                    sqa_reg_pass<0, MAXD, E32, SI>(sw, ent, g[j], G[j], P, own4[j], o4[j], c0[j], jp[j], ib[j], K, Kr);
                     __syncthreads();
-                    sqa_reg_pass<1, MAXD, E32, SI>(sw, ent, g[j], G[j], P, own4[j], o4[j], c0[j], jp[j], ib[j], K, Kr0,
-                                                   Kr1);
+                    sqa_reg_pass<1, MAXD, E32, SI>(sw, ent, g[j], G[j], P, own4[j], o4[j], c0[j], jp[j], ib[j], K, Kr);
                     __syncthreads();
                 }
             }
@@ -364,7 +338,7 @@ __device__ void run_item_sqa(const SweepLaunch &L, const SweepJob &job, int quad
             for (int x = tid; x < 3 * W; x += B) rows[((t + 1) & 1) * 3 * W + x] = L.ent[(size_t)(t + 1) * 3 * W + x];
         const uint32_t y = phase_hi | (uint32_t)t;
         uint32_t HA, LA;  // round 2, word 0: fixed for this quad and sweep
-        mulhilo_q(kM0q, H1 ^ y ^ k0, HA, LA);
+        philox_mulhilo(kPhiloxM0, H1 ^ y ^ k0, HA, LA);
         for (int c = 0; c < ncol; ++c) {
             const int lo = s_cptr[c], nc = s_cptr[c + 1] - lo;
             if (nc == 0) continue;
@@ -421,7 +395,7 @@ __device__ void run_item_sqa(const SweepLaunch &L, const SweepJob &job, int quad
                         }
                     }
                     const uint32_t i = idx_s[p] | ((uint32_t)tau << 16);
-                    const uint4 u = philox_sqa(i, job.start, k1, L1, HA, LA, k0w, k1w, Kr0, Kr1);
+                    const uint4 u = philox_sqa(i, job.start, k1, L1, HA, LA, k0w, k1w, Kr);
                     const uint32_t ur[4] = {u.x, u.y, u.z, u.w};
                     uint32_t flip = 0;
 #pragma unroll
