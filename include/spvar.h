@@ -352,12 +352,27 @@ typedef struct spvar_params {
                                     states the previous one wrote (results are identical: every random
                                     word is keyed by the absolute sweep).  0: the autotuner chooses
                                     between one launch per phase and four when replicas_per_block is 0,
-                                    else one launch per phase.  Must be 0 with the SQA sampler */
+                                    else one launch per phase.  Must be 0 with the SQA and PTICM
+                                    samplers */
+    int32_t pticm_temps;         /* PTICM: inverse temperatures R (2 .. 64), geometric from pticm_beta0
+                                    to pticm_beta1; cluster moves and kept lists at k >= R / 2 */
+    int32_t pticm_keep;          /* PTICM: lowest distinct states K kept per tracked replica (1 .. 64) */
+    double pticm_beta0, pticm_beta1;
 } spvar_params;
 
 #define SPVAR_SAMPLER_SA 0  /* simulated annealing (Sec. III.A) */
 #define SPVAR_SAMPLER_SQA 1 /* simulated quantum annealing: discrete-time path integral (Sec. III);
                                the sample of a run is its lowest-energy Trotter slice */
+#define SPVAR_SAMPLER_PTICM 2 /* parallel tempering with isoenergetic cluster moves (Sec. III.D), one run
+                                 per start and phase (as spvar_pticm_sample with exchanges and cluster
+                                 moves on, icm_from = keep_from = R / 2, start word = the start, phase =
+                                 the phase); the phase's sample is the kept lists, list after list, so
+                                 its size is the number of states kept, at most 2 (R - R/2) K, and the
+                                 elite is ceil(elite_threshold x that size).  fixing_sample_size must
+                                 be 2 (R - R/2) K and solving_sample_size 0 or the same; num_sweeps
+                                 >= 1; no correlation phase, no component boosting; every problem
+                                 n <= 2048 and its 2Rn + 4R(dmax + 1) + 32n bytes in one CTA's
+                                 shared memory (else SPVAR_ELIMIT).  Not taken by the server */
 
 #define SPVAR_SWEEP_AUTO 0    /* register kernel when eligible, else general */
 #define SPVAR_SWEEP_GENERAL 1 /* general integer-coupler kernel */
@@ -447,7 +462,8 @@ typedef struct spvar_server spvar_server;
 
 typedef struct spvar_server_config {
     spvar_params params;    /* Alg. 2 parameters of every request; sweep_kernel = SPVAR_SWEEP_PM1
-                               restricts the server to +-1 couplers (faster sweep) */
+                               restricts the server to +-1 couplers (faster sweep: the streaming
+                               +-1 kernel; SPVAR_SWEEP_PM1Q: the quad-group kernel) */
     size_t budget_bytes;    /* device memory for admitted requests' workspaces */
     int32_t max_n;          /* largest request: spins, CSR entries, degree */
     int32_t max_nnz;
@@ -457,7 +473,9 @@ typedef struct spvar_server_config {
     int32_t max_requests;   /* requests in flight at once */
     int32_t sweeps_per_step; /* sweeps of every in-flight anneal per engine step (0: a whole phase).  A
                                 request that arrives is admitted at the next step, so smaller steps
-                                shorten its wait; results do not depend on it */
+                                shorten its wait; results do not depend on it.  Must be 0 with the
+                                SQA sampler (params.sampler = SPVAR_SAMPLER_SQA: every request is
+                                sampled by SQA, the item walk over (slice, spin)) */
 } spvar_server_config;
 
 typedef struct spvar_request_info {

@@ -262,7 +262,7 @@ __global__ void __launch_bounds__(kBigBlock) k_elite_single(const int64_t *energ
                                                             int32_t *elite)
 {
     extern __shared__ __align__(16) unsigned long long s_key[];
-    elite_core(energies, S, k, elite, s_key);
+    elite_fast(energies, S, k, elite, s_key);
 }
 
 __global__ void __launch_bounds__(kCountBlock)
@@ -270,8 +270,7 @@ __global__ void __launch_bounds__(kCountBlock)
                    int canon, int fix_num, int fix_den, int32_t *counts, int8_t *fixed,
                    int32_t *nfixed)
 {
-    count_core(P, spins, W, elite, k, canon, fix_num, fix_den, counts, fixed, nfixed, nullptr,
-               nullptr);
+    count_bs_core(P, spins, W, elite, k, canon, fix_num, fix_den, counts, fixed, nfixed, nullptr, nullptr);
 }
 
 __global__ void __launch_bounds__(kBigBlock) k_reduce_single(const DevProb *src, DevProb *dst,
@@ -342,15 +341,19 @@ __device__ __forceinline__ int item_quads(const DevProb *P, const SolveConsts &C
 
 // Builds this phase's sweep jobs and work items (one item = item_quads quads
 // of one start) for every start that is not done, and resets the queue cursor.
+// One thread per start sizes its items; the items are then written by one warp
+// per start, a lane per item.
 __global__ void __launch_bounds__(kBigBlock)
     k_plan(Slot *slots, SolveConsts C, SweepJob *jobs, WorkItem *items, int32_t *nitems,
            int32_t *queue)
 {
     __shared__ int s_warp[32];
+    __shared__ int s_off[kBigBlock], s_groups[kBigBlock], s_qn[kBigBlock], s_nquads[kBigBlock];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int carry = 0;
     for (int base = 0; base < C.nslots; base += blockDim.x) {
         const int si = base + threadIdx.x;
-        int groups = 0;
+        int groups = 0, qn = 1, nquads = 0;
         if (si < C.nslots) {
             Slot &s = slots[si];
             if (s.mode != kDone) {
@@ -372,7 +375,9 @@ __global__ void __launch_bounds__(kBigBlock)
                 j.t0 = t0;
                 j.t1 = t1;
                 jobs[si] = j;
-                groups = ceil_div(ceil_div(S, 4), item_quads(s.cur, C, ceil_div(S, 4)));
+                nquads = ceil_div(S, 4);
+                qn = item_quads(s.cur, C, nquads);
+                groups = ceil_div(nquads, qn);
                 if (t0 == 0) {
                     s.rec_count[s.phase] = S;
                     s.rec_nfree[s.phase] = s.cur->n;
@@ -383,20 +388,25 @@ __global__ void __launch_bounds__(kBigBlock)
         }
         int tot;
         const int ex = block_scan_excl(groups, s_warp, &tot);
-        if (groups > 0) {
-            const int S = jobs[si].S;
-            const int nquads = ceil_div(S, 4);
-            const int qn = item_quads(slots[si].cur, C, nquads);
-            for (int g = 0; g < groups; ++g) {
+        s_off[threadIdx.x] = carry + ex;
+        s_groups[threadIdx.x] = groups;
+        s_qn[threadIdx.x] = qn;
+        s_nquads[threadIdx.x] = nquads;
+        __syncthreads();
+        const int nb = min((int)blockDim.x, C.nslots - base);
+        for (int k = warp; k < nb; k += (int)(blockDim.x >> 5)) {
+            const int g_n = s_groups[k], q_n = s_qn[k], nq = s_nquads[k], o = s_off[k];
+            for (int g = lane; g < g_n; g += 32) {
                 WorkItem w;
-                w.job = si;
-                w.quad0 = g * qn;
-                w.nq = min(qn, nquads - g * qn);
+                w.job = base + k;
+                w.quad0 = g * q_n;
+                w.nq = min(q_n, nq - g * q_n);
                 w.pad = 0;
-                items[carry + ex + g] = w;
+                items[o + g] = w;
             }
         }
         carry += tot;
+        __syncthreads();
     }
     if (threadIdx.x == 0) {
         *nitems = carry;
@@ -412,10 +422,12 @@ __global__ void __launch_bounds__(kBigBlock) k_elite_slots(Slot *slots, SolveCon
     __shared__ int s_better;
     Slot &s = slots[blockIdx.x];
     if (s.mode == kDone || !sample_complete(s, C)) return;
-    const int S = phase_samples(C, s.mode);
-    const int k = (s.mode == kFixing) ? C.k_fix : (s.mode == kCorr) ? C.k_corr : 1;
+    // PTICM: the sample is the states its run kept
+    const int S = C.pticm ? s.rec_count[s.phase] : phase_samples(C, s.mode);
+    const int k = (s.mode == kFixing) ? (C.pticm ? elite_count_hd(C.elite, S) : C.k_fix)
+                  : (s.mode == kCorr) ? C.k_corr : 1;
     const int64_t *e = s.rec_e + (size_t)s.phase * C.Smax;
-    elite_core(e, S, k, s.elite, s_key);
+    elite_fast(e, S, k, s.elite, s_key);
     const int rbest = s.elite[0];
     const int64_t eb = e[rbest];
     if (threadIdx.x == 0) {
@@ -445,17 +457,18 @@ __global__ void __launch_bounds__(kCountBlock) k_count_slots(Slot *slots, SolveC
     Slot &s = slots[blockIdx.y];
     if ((s.mode != kFixing && s.mode != kCorr) || !sample_complete(s, C)) return;
     const DevProb *P = s.cur;
-    if ((int)(blockIdx.x * blockDim.x) >= P->n) return;
+    if ((int)(blockIdx.x * 1024) >= P->n) return;
     if (s.mode == kCorr) {
         // correlation fixing: elite rows multiplied by their value at rho, then the
         // rule with the correlation threshold
-        count_core(P, s.spins, s.W0, s.elite, C.k_corr, 1, C.corr_num, C.corr_den, s.counts, s.fixed,
-                   &s.nfixed, s.fmap, s.orig[s.ocur]);
+        count_bs_core(P, s.spins, s.W0, s.elite, C.k_corr, 1, C.corr_num, C.corr_den, s.counts, s.fixed,
+                      &s.nfixed, s.fmap, s.orig[s.ocur]);
         return;
     }
     const int canon = (C.canon < 0) ? P->hzero : C.canon;
-    count_core(P, s.spins, s.W0, s.elite, C.k_fix, canon, C.fix_num, C.fix_den, s.counts, s.fixed,
-               &s.nfixed, s.fmap, s.orig[s.ocur]);
+    const int k = C.pticm ? elite_count_hd(C.elite, s.rec_count[s.phase]) : C.k_fix;
+    count_bs_core(P, s.spins, s.W0, s.elite, k, canon, C.fix_num, C.fix_den, s.counts, s.fixed, &s.nfixed, s.fmap,
+                  s.orig[s.ocur]);
 }
 
 // Stall rule, fold/compact into the spare buffer, and the phase transition.
@@ -538,8 +551,8 @@ __global__ void __launch_bounds__(kBigBlock) k_reduce_slots(Slot *slots, SolveCo
 //   k_fold_finish  phase transitions and the count of active slots.
 // The result is the one reduce_core computes: free spins keep their order,
 // couplers between free spins keep theirs, colour classes are inherited.
-constexpr int kFoldBlock = 256;
-constexpr int kFoldPer = kFoldChunk / kFoldBlock;
+constexpr int kFoldBlock = kFoldChunk;  // one spin per thread
+constexpr int kFoldGather = 8;          // CSR entries a thread loads at once
 
 __device__ __forceinline__ bool fold_active(const Slot &s, const SolveConsts &C)
 {
@@ -584,25 +597,35 @@ __global__ void __launch_bounds__(kFoldBlock) k_fold_count(Slot *slots, SolveCon
     int32_t *rowcnt = s.scratch + cap, *hfold = s.scratch + 2 * cap;
     const int8_t *fx = s.fixed;
     long long off = 0;
-    int nfree = 0, nnz = 0, hnz = 0;
+    int nfree = 0, nnz = 0, hnz = 0, col = -1;
     unsigned long long key = 0ull;
-#pragma unroll
-    for (int k = 0; k < kFoldPer; ++k) {
-        const int i = i0 + k * kFoldBlock + tid;
-        if (i >= n) break;
+    const int i = i0 + tid;
+    if (i < n) {
         const int vi = fx[i];
         long long hf = P->h[i];
         int nf = 0;
-        const int p1 = P->row_ptr[i + 1];
-        for (int p = P->row_ptr[i]; p < p1; ++p) {
-            const int j = P->col[p];
-            const int vj = fx[j];
-            if (vi) {
-                if (vj && j > i) off += (long long)P->val[p] * vi * vj;
-            } else if (vj) {
-                hf += (long long)P->val[p] * vj;
-            } else {
-                ++nf;
+        const int p0 = P->row_ptr[i], p1 = P->row_ptr[i + 1];
+        for (int pb = p0; pb < p1; pb += kFoldGather) {
+            // the row's entries in batches: every load of a batch is issued before any is used
+            int jj[kFoldGather], vv[kFoldGather], fj[kFoldGather];
+#pragma unroll
+            for (int d = 0; d < kFoldGather; ++d) {
+                const bool in = pb + d < p1;
+                jj[d] = in ? P->col[pb + d] : -1;
+                vv[d] = in ? P->val[pb + d] : 0;
+            }
+#pragma unroll
+            for (int d = 0; d < kFoldGather; ++d) fj[d] = jj[d] >= 0 ? fx[jj[d]] : 0;
+#pragma unroll
+            for (int d = 0; d < kFoldGather; ++d) {
+                if (jj[d] < 0) continue;
+                if (vi) {
+                    if (fj[d] && jj[d] > i) off += (long long)vv[d] * vi * fj[d];
+                } else if (fj[d]) {
+                    hf += (long long)vv[d] * fj[d];
+                } else {
+                    ++nf;
+                }
             }
         }
         if (vi) {
@@ -610,19 +633,34 @@ __global__ void __launch_bounds__(kFoldBlock) k_fold_count(Slot *slots, SolveCon
         } else {
             hfold[i] = (int32_t)hf;
             rowcnt[i] = nf;
-            ++nfree;
-            nnz += nf;
-            hnz |= hf != 0;
-            atomicAdd(&s_cls[P->colour[i]], 1);
+            nfree = 1;
+            nnz = nf;
+            hnz = hf != 0;
+            col = P->colour[i];
             // reference spin of the new problem: largest degree, lowest index
-            key = max(key, ((unsigned long long)nf << 32) | (unsigned long long)(0x7FFFFFFF - i));
+            key = ((unsigned long long)nf << 32) | (unsigned long long)(0x7FFFFFFF - i);
         }
     }
-    atomicAdd(&s_free, nfree);
-    atomicAdd(&s_nnz, nnz);
-    if (hnz) atomicOr(&s_hnz, 1);
-    atomicMax(&s_key, key);
-    atomicAdd(&s_off, (unsigned long long)off);
+    // one shared atomic per warp (and per colour class present in the warp)
+    const unsigned full = 0xFFFFFFFFu;
+    const int lane = tid & 31;
+    const unsigned same = __match_any_sync(full, col);
+    if (col >= 0 && lane == __ffs(same) - 1) atomicAdd(&s_cls[col], __popc(same));
+    nfree = __reduce_add_sync(full, nfree);
+    nnz = __reduce_add_sync(full, nnz);
+    hnz = __reduce_or_sync(full, hnz);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        key = max(key, __shfl_xor_sync(full, key, o));
+        off += __shfl_xor_sync(full, off, o);
+    }
+    if (lane == 0) {
+        atomicAdd(&s_free, nfree);
+        atomicAdd(&s_nnz, nnz);
+        if (hnz) atomicOr(&s_hnz, 1);
+        atomicMax(&s_key, key);
+        atomicAdd(&s_off, (unsigned long long)off);
+    }
     __syncthreads();
     int32_t *tab = s.scratch + fold_table_offset(cap);
     int32_t *e = tab + blockIdx.x * kFoldStride;
@@ -651,30 +689,32 @@ __global__ void __launch_bounds__(kFoldBlock) k_fold_index(Slot *slots, SolveCon
     if (chunk > 0 && i0 >= n) return;  // chunk 0 writes the header, even for n = 0
     const int nch = (n + kFoldChunk - 1) / kFoldChunk;
     const int32_t *tab = s.scratch + fold_table_offset(cap);
-    // offsets of this chunk (totals of the chunks before it) and the totals of all
-    if (tid < ncol) {
-        int b = 0, t = 0;
-        for (int q = 0; q < nch; ++q) {
-            const int v = tab[q * kFoldStride + 6 + tid];
-            b += q < chunk ? v : 0;
-            t += v;
+    // offsets of this chunk (totals of the chunks before it) and the totals of all:
+    // field f (0 free spins, 1 free-free entries, 2 + c spins of class c) summed by a warp
+    {
+        const int lane = tid & 31, warp = tid >> 5;
+        for (int f = warp; f < 3 + ncol; f += kFoldBlock / 32) {
+            const int fo = f < 3 ? f : 6 + (f - 3);  // table column (2: nonzero-bias flag)
+            int b = 0, t = 0;
+            for (int q = lane; q < nch; q += 32) {
+                const int v = tab[q * kFoldStride + fo];
+                t += f == 2 ? (v != 0) : v;
+                b += q < chunk ? v : 0;
+            }
+            b = __reduce_add_sync(0xFFFFFFFFu, b);
+            t = __reduce_add_sync(0xFFFFFFFFu, t);
+            if (lane == 0) {
+                if (f < 2) {
+                    s_base[f] = b;
+                    s_tot[f] = t;
+                } else if (f == 2) {
+                    s_hnz = t;
+                } else {
+                    s_base_cls[f - 3] = b;
+                    s_tot_cls[f - 3] = t;
+                }
+            }
         }
-        s_base_cls[tid] = b;
-        s_tot_cls[tid] = t;
-    } else if (tid >= 64 && tid < 66) {
-        const int f = tid - 64;
-        int b = 0, t = 0;
-        for (int q = 0; q < nch; ++q) {
-            const int v = tab[q * kFoldStride + f];
-            b += q < chunk ? v : 0;
-            t += v;
-        }
-        s_base[f] = b;
-        s_tot[f] = t;
-    } else if (tid == 96) {
-        int h = 0;
-        for (int q = 0; q < nch; ++q) h |= tab[q * kFoldStride + 2];
-        s_hnz = h;
     }
     __syncthreads();
     if (tid == 0) {
@@ -708,10 +748,9 @@ __global__ void __launch_bounds__(kFoldBlock) k_fold_index(Slot *slots, SolveCon
     const int32_t *rowcnt = s.scratch + cap, *hfold = s.scratch + 2 * cap;
     const int32_t *orig = s.orig[s.ocur];
     int32_t *orig2 = s.orig[s.ocur ^ 1];
-    int carry_free = s_base[0], carry_nnz = s_base[1];
-    for (int k = 0; k < kFoldPer; ++k) {
-        if (i0 + k * kFoldBlock >= n) break;  // uniform over the block
-        const int i = i0 + k * kFoldBlock + tid;
+    const int carry_free = s_base[0], carry_nnz = s_base[1];
+    {
+        const int i = i0 + tid;
         const bool valid = i < n;
         const bool f = valid && fx[i] == 0;
         const int rc = f ? rowcnt[i] : 0;
@@ -723,11 +762,8 @@ __global__ void __launch_bounds__(kFoldBlock) k_fold_index(Slot *slots, SolveCon
         int rank = 0;
         for (int c = 0; c < ncol; ++c) {
             int tc;
-            // the scan ends with a barrier, so s_base_cls[c] is settled here
             const int exc = block_scan_excl(col == c ? 1 : 0, s_warp, &tc);
             if (col == c) rank = s_base_cls[c] + exc;
-            __syncthreads();  // every thread has read the class offset before it advances
-            if (tid == 0) s_base_cls[c] += tc;
         }
         if (valid) nofo[i] = f ? carry_free + exf : -1;
         if (f) {
@@ -743,8 +779,6 @@ __global__ void __launch_bounds__(kFoldBlock) k_fold_index(Slot *slots, SolveCon
             D->idx_of_pos[pos] = a;
             D->meta[pos] = ((uint32_t)(h & 0xFFFF) << 16) | (uint32_t)rc;
         }
-        carry_free += tf;
-        carry_nnz += tr;
     }
 }
 
@@ -773,26 +807,37 @@ __global__ void __launch_bounds__(kFoldBlock) k_fold_fill(Slot *slots, SolveCons
     }
     if (i0 >= n) return;
     const int8_t *fx = s.fixed;
-#pragma unroll
-    for (int k = 0; k < kFoldPer; ++k) {
-        const int i = i0 + k * kFoldBlock + tid;
-        if (i >= n) break;
-        if (fx[i] != 0) continue;
+    const int i = i0 + tid;
+    if (i < n && fx[i] == 0) {
         const int a = nofo[i];
+        const int p0 = P->row_ptr[i], p1 = P->row_ptr[i + 1];
         int q = D->row_ptr[a];
         const int pos = D->pos_of_idx[a];
         int d = 0;
-        const int p1 = P->row_ptr[i + 1];
-        for (int p = P->row_ptr[i]; p < p1; ++p) {
-            const int j = P->col[p];
-            if (fx[j] != 0) continue;
-            const int b = nofo[j];
-            const int J = P->val[p];
-            D->col[q] = b;
-            D->val[q] = J;
-            D->ell[(size_t)d * cap + pos] = ((uint32_t)D->pos_of_idx[b] & 0xFFFFu) | ((uint32_t)(J & 0xFFFF) << 16);
-            ++q;
-            ++d;
+        for (int pb = p0; pb < p1; pb += kFoldGather) {
+            // the row's entries in batches: each dependent step loads for the whole batch
+            int jj[kFoldGather], vv[kFoldGather], bb[kFoldGather], pp[kFoldGather];
+#pragma unroll
+            for (int e = 0; e < kFoldGather; ++e) {
+                const bool in = pb + e < p1;
+                jj[e] = in ? P->col[pb + e] : -1;
+                vv[e] = in ? P->val[pb + e] : 0;
+            }
+#pragma unroll
+            for (int e = 0; e < kFoldGather; ++e) bb[e] = (jj[e] >= 0 && fx[jj[e]] == 0) ? 1 : -1;
+#pragma unroll
+            for (int e = 0; e < kFoldGather; ++e) bb[e] = bb[e] > 0 ? nofo[jj[e]] : -1;
+#pragma unroll
+            for (int e = 0; e < kFoldGather; ++e) pp[e] = bb[e] >= 0 ? D->pos_of_idx[bb[e]] : 0;
+#pragma unroll
+            for (int e = 0; e < kFoldGather; ++e) {
+                if (bb[e] < 0) continue;
+                D->col[q] = bb[e];
+                D->val[q] = vv[e];
+                D->ell[(size_t)d * cap + pos] = ((uint32_t)pp[e] & 0xFFFFu) | ((uint32_t)(vv[e] & 0xFFFF) << 16);
+                ++q;
+                ++d;
+            }
         }
     }
 }
@@ -1053,7 +1098,7 @@ cudaError_t launch_count_single(const DevProb *prob, int n_host, const uint32_t 
     cudaError_t e = cudaMemsetAsync(nfixed, 0, sizeof(int32_t), stream);
     if (e != cudaSuccess) return e;
     if (n_host <= 0) return cudaSuccess;
-    k_count_single<<<ceil_div(n_host, kCountBlock), kCountBlock, 0, stream>>>(
+    k_count_single<<<ceil_div(n_host, 1024), kCountBlock, 0, stream>>>(
         prob, spins, W, elite, k, canon, fix_num, fix_den, counts, fixed, nfixed);
     return cudaGetLastError();
 }
@@ -1089,7 +1134,7 @@ cudaError_t launch_elite_slots(Slot *slots, const SolveConsts &C, cudaStream_t s
 cudaError_t launch_count_slots(Slot *slots, const SolveConsts &C, int max_n0, cudaStream_t st)
 {
     if (max_n0 <= 0) return cudaSuccess;
-    dim3 grid(ceil_div(max_n0, kCountBlock), C.nslots);
+    dim3 grid(ceil_div(max_n0, 1024), C.nslots);
     k_count_slots<<<grid, kCountBlock, 0, st>>>(slots, C);
     return cudaGetLastError();
 }

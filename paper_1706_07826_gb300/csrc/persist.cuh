@@ -81,6 +81,111 @@ __device__ __forceinline__ void elite_core(const int64_t *energies, int S, int k
     __syncthreads();
 }
 
+// Elite selection without sorting the whole sample: the same k indices in the
+// same order as elite_core.  The lowest energy and the spread give a
+// histogram of (E - Emin) >> shift over kEliteBins bins; the bin holding the
+// k-th lowest key bounds the candidates (every key in a lower or equal bin),
+// which are compacted in index order and placed by rank (the number of
+// candidate keys below each; keys are distinct because they carry the
+// index).  k = 1 is a block-wide arg-min.  More than kEliteRankMax candidates
+// (a crowded bin) fall back to elite_core.  blockDim.x == kBigBlock; s_key as
+// for elite_core.
+constexpr int kEliteBins = 1024;
+constexpr int kEliteRankMax = 512;
+__device__ __forceinline__ void elite_fast(const int64_t *energies, int S, int k, int32_t *elite,
+                                           unsigned long long *s_key)
+{
+    __shared__ long long s_min, s_max;
+    __shared__ unsigned long long s_best;
+    __shared__ int s_hist[kEliteBins];
+    __shared__ int s_warp[32];
+    __shared__ int s_bin, s_cand;
+    const int tid = threadIdx.x, B = blockDim.x;
+    if (tid == 0) {
+        s_min = LLONG_MAX;
+        s_max = LLONG_MIN;
+        s_best = ~0ull;
+    }
+    for (int b = tid; b < kEliteBins; b += B) s_hist[b] = 0;
+    __syncthreads();
+    long long mn = LLONG_MAX, mx = LLONG_MIN;
+    for (int r = tid; r < S; r += B) {
+        const long long e = energies[r];
+        mn = min(mn, e);
+        mx = max(mx, e);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        mn = min(mn, __shfl_xor_sync(0xFFFFFFFFu, mn, o));
+        mx = max(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, o));
+    }
+    if ((tid & 31) == 0) {
+        atomicMin(&s_min, mn);
+        atomicMax(&s_max, mx);
+    }
+    __syncthreads();
+    const long long emin = s_min;
+    if (k == 1) {
+        unsigned long long best = ~0ull;
+        for (int r = tid; r < S; r += B)
+            best = min(best, ((unsigned long long)(energies[r] - emin) << 32) | (unsigned)r);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) best = min(best, __shfl_xor_sync(0xFFFFFFFFu, best, o));
+        if ((tid & 31) == 0) atomicMin(&s_best, best);
+        __syncthreads();
+        if (tid == 0) elite[0] = (int32_t)(s_best & 0xFFFFFFFFull);
+        __syncthreads();
+        return;
+    }
+    int shift = 0;
+    while (((unsigned long long)(s_max - emin) >> shift) >= (unsigned long long)kEliteBins) ++shift;
+    for (int r = tid; r < S; r += B) atomicAdd(&s_hist[(int)((unsigned long long)(energies[r] - emin) >> shift)], 1);
+    __syncthreads();
+    // the bin holding the k-th lowest key: keys in bins below it number < k, with it >= k
+    int carry = 0;
+    for (int b0 = 0; b0 < kEliteBins; b0 += B) {
+        const int b = b0 + tid;
+        const int h = b < kEliteBins ? s_hist[b] : 0;
+        int tot;
+        const int ex = block_scan_excl(h, s_warp, &tot);
+        if (b < kEliteBins && carry + ex < k && carry + ex + h >= k) {
+            s_bin = b;
+            s_cand = carry + ex + h;
+        }
+        carry += tot;
+    }
+    __syncthreads();
+    const int bstar = s_bin, C = s_cand;
+    if (C > kEliteRankMax) {
+        elite_core(energies, S, k, elite, s_key);
+        return;
+    }
+    // candidates in index order
+    carry = 0;
+    for (int r0 = 0; r0 < S; r0 += B) {
+        const int r = r0 + tid;
+        unsigned long long key = 0ull;
+        bool f = false;
+        if (r < S) {
+            const unsigned long long d = (unsigned long long)(energies[r] - emin);
+            f = (int)(d >> shift) <= bstar;
+            key = (d << 32) | (unsigned)r;
+        }
+        int tot;
+        const int ex = block_scan_excl(f ? 1 : 0, s_warp, &tot);
+        if (f) s_key[carry + ex] = key;
+        carry += tot;
+    }
+    __syncthreads();
+    for (int c = tid; c < C; c += B) {
+        const unsigned long long key = s_key[c];
+        int rank = 0;
+        for (int j = 0; j < C; ++j) rank += s_key[j] < key;
+        if (rank < k) elite[rank] = (int32_t)(key & 0xFFFFFFFFull);
+    }
+    __syncthreads();
+}
+
 // Persistence count and fixing rule for spins [i0, i0 + blockDim.x) of one
 // sample set.  With canon, each elite row is multiplied by its value at
 // prob->rho.  fmap/orig (optional): also record fixings in original order.
@@ -127,6 +232,114 @@ __device__ __forceinline__ void count_core(const DevProb *P, const uint32_t *spi
     }
     const unsigned ball = __ballot_sync(0xFFFFFFFFu, v != 0);
     if ((threadIdx.x & 31) == 0 && ball) atomicAdd(nfixed, __popc(ball));
+}
+
+// Persistence count and fixing rule, bit-sliced: one CTA of kCountBlock
+// threads covers 32 words (1024 spins) of the sample rows.  Lane l of every
+// warp owns word 32 blockIdx.x + l; the k elite rows are split over the 8
+// warps, and each lane adds its rows' words (each multiplied by its value at
+// rho when canon is set) into NB bit planes: plane b holds bit b of the
+// running count of every spin of the word (a vertical counter, two logic
+// operations per plane and row).  The warps' counters are then summed by a
+// bit-sliced ripple adder and each spin's count read off its planes.
+// Results as count_core.  NB: planes per warp (2^NB > rows per warp).
+constexpr int kCountWarps = kCountBlock / 32;
+constexpr int kCountPlanes = 12;  // 2^12 > 16384 / kCountWarps rows per warp
+template <int NB>
+__device__ __forceinline__ void count_planes(const uint32_t *spins, int W, const int32_t *elite, int k,
+                                             int canon, int rho, uint32_t (*s_planes)[kCountPlanes + 3][32],
+                                             int *s_row, uint32_t *s_flip)
+{
+    constexpr int kChunk = 1024;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int word = blockIdx.x * 32 + lane;
+    uint32_t c[NB];
+#pragma unroll
+    for (int b = 0; b < NB; ++b) c[b] = 0u;
+    for (int c0 = 0; c0 < k; c0 += kChunk) {
+        const int m = min(kChunk, k - c0);
+        for (int q = threadIdx.x; q < m; q += blockDim.x) {
+            const int r = elite[c0 + q];
+            s_row[q] = r;
+            uint32_t f = 0u;
+            if (canon && rho >= 0) f = ((spins[(size_t)r * W + (rho >> 5)] >> (rho & 31)) & 1u) ? 0u : 0xFFFFFFFFu;
+            s_flip[q] = f;
+        }
+        __syncthreads();
+        if (word < W) {
+#pragma unroll 4
+            for (int q = warp; q < m; q += kCountWarps) {
+                uint32_t carry = spins[(size_t)s_row[q] * W + word] ^ s_flip[q];
+#pragma unroll
+                for (int b = 0; b < NB; ++b) {
+                    const uint32_t t = c[b] & carry;
+                    c[b] ^= carry;
+                    carry = t;
+                }
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int b = 0; b < NB; ++b) s_planes[warp][b][lane] = c[b];
+}
+
+__device__ __forceinline__ void count_bs_core(const DevProb *P, const uint32_t *spins, int W, const int32_t *elite,
+                                              int k, int canon, int fix_num, int fix_den, int32_t *counts,
+                                              int8_t *fixed, int32_t *nfixed, int8_t *fmap, const int32_t *orig)
+{
+    __shared__ uint32_t s_planes[kCountWarps][kCountPlanes + 3][32];
+    __shared__ uint32_t s_tot[kCountPlanes + 3][32];
+    __shared__ int s_row[1024];
+    __shared__ uint32_t s_flip[1024];
+    const int n = P->n, rho = P->rho;
+    const int per_warp = (k + kCountWarps - 1) / kCountWarps;
+    const int NB = per_warp < 16 ? 4 : per_warp < 64 ? 6 : per_warp < 256 ? 8 : per_warp < 1024 ? 10 : 12;
+    if (NB == 4) count_planes<4>(spins, W, elite, k, canon, rho, s_planes, s_row, s_flip);
+    else if (NB == 6) count_planes<6>(spins, W, elite, k, canon, rho, s_planes, s_row, s_flip);
+    else if (NB == 8) count_planes<8>(spins, W, elite, k, canon, rho, s_planes, s_row, s_flip);
+    else if (NB == 10) count_planes<10>(spins, W, elite, k, canon, rho, s_planes, s_row, s_flip);
+    else count_planes<12>(spins, W, elite, k, canon, rho, s_planes, s_row, s_flip);
+    __syncthreads();
+    const int NT = NB + 3;  // the sum of 8 counters below 2^NB is below 2^(NB + 3)
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        uint32_t t[kCountPlanes + 3];
+#pragma unroll
+        for (int b = 0; b < kCountPlanes + 3; ++b) t[b] = 0u;
+        for (int w = 0; w < kCountWarps; ++w) {
+            uint32_t carry = 0u;
+#pragma unroll
+            for (int b = 0; b < kCountPlanes + 3; ++b) {
+                if (b < NT) {
+                    const uint32_t a = t[b], x = b < NB ? s_planes[w][b][lane] : 0u;
+                    t[b] = a ^ x ^ carry;
+                    carry = (a & x) | (carry & (a ^ x));
+                }
+            }
+        }
+#pragma unroll
+        for (int b = 0; b < kCountPlanes + 3; ++b)
+            if (b < NT) s_tot[b][lane] = t[b];
+    }
+    __syncthreads();
+    for (int sp = threadIdx.x; sp < 1024; sp += blockDim.x) {
+        const int i = blockIdx.x * 1024 + sp;
+        const int wl = sp >> 5, bit = sp & 31;
+        int8_t v = 0;
+        if (i < n) {
+            int cnt = 0;
+            for (int b = 0; b < NT; ++b) cnt |= (int)((s_tot[b][wl] >> bit) & 1u) << b;
+            const long long diff = 2ll * cnt - k;
+            if (diff > 0 && (long long)fix_den * diff >= (long long)fix_num * k) v = 1;
+            if (diff < 0 && (long long)fix_den * (-diff) >= (long long)fix_num * k) v = -1;
+            if (counts) counts[i] = cnt;
+            fixed[i] = v;
+            if (v && fmap) fmap[orig[i]] = v;
+        }
+        const unsigned ball = __ballot_sync(0xFFFFFFFFu, v != 0);
+        if ((threadIdx.x & 31) == 0 && ball) atomicAdd(nfixed, __popc(ball));
+    }
 }
 
 // Fold the fixed spins into h and the offset and compact the free spins into

@@ -60,7 +60,10 @@ cudaError_t engine_phase(const PhaseEngine &E, Slot *slots, int nslots, int T, i
     L.P = E.P;
     L.W = E.W;
     if (E.ev_sweep[0] && (e = record(E.ev_sweep[0])) != cudaSuccess) return e;
-    e = launch_sweep_shape(L, E.shape, E.pm1, grid, E.sweep_smem, st);
+    // the sampler: persistent sweep launch over the work items, or one PTICM run per start
+    e = E.pt_R > 0 ? launch_pticm_slots(slots, nslots, C.Smax, E.pt_thr, E.thr_stride, E.pt_xthr, E.pt_dx, E.pt_R, T,
+                                        E.pt_K, E.pt_smem, st)
+                   : launch_sweep_shape(L, E.shape, E.pm1, grid, E.sweep_smem, st);
     if (e != cudaSuccess) return e;
     if (E.ev_sweep[1] && (e = record(E.ev_sweep[1])) != cudaSuccess) return e;
     if ((e = launch_boost(slots, C, st)) != cudaSuccess) return e;
@@ -97,6 +100,10 @@ struct spvar_plan {
     uint32_t *d_thr = nullptr;
     unsigned long long *d_ent = nullptr;  // SQA acceptance entries
     int sqa_P = 0, sqa_W = 0;             // SQA slices and table width (0: SA)
+    // PTICM as the sampler: temperatures, kept states per list, exchange-table width, tables
+    int pt_R = 0, pt_K = 0, pt_dx = 0;
+    uint32_t *d_pt_thr = nullptr, *d_pt_xthr = nullptr;
+    size_t pt_smem = 0;
     bool sqa_ent32 = false;               // SQA: no acceptance entry is 2^32 (32-bit entries suffice)
     SweepJob *d_jobs = nullptr;
     WorkItem *d_items = nullptr;
@@ -187,6 +194,12 @@ PhaseEngine engine_of(const spvar_plan *pl)
     E.ev_sweep[1] = pl->ev_sweep[1];
     E.ev_post = pl->ev_post;
     E.C = pl->C;
+    E.pt_R = pl->pt_R;
+    E.pt_K = pl->pt_K;
+    E.pt_dx = pl->pt_dx;
+    E.pt_thr = pl->d_pt_thr;
+    E.pt_xthr = pl->d_pt_xthr;
+    E.pt_smem = pl->pt_smem;
     return E;
 }
 
@@ -387,9 +400,10 @@ std::vector<SweepShape> candidate_shapes(const spvar_plan *pl, int optin)
     return out;
 }
 
-// Times a short run of the plan's phases (at most 4, at most 48 sweeps each)
-// for every candidate shape and keeps the fastest; results are cached per
-// problem/plan geometry.
+// Times a short run of the plan's phases (at most 4, at most 64 sweeps each;
+// the best of two repetitions after an untimed one, and one discarded trial
+// before the first candidate) for every candidate shape and keeps the fastest;
+// results are cached per problem/plan geometry.
 void autotune(spvar_plan *pl, cudaStream_t st, int optin)
 {
     const TuneKey key{pl->max_n0, pl->max_deg, pl->pm1 ? 1 : 0, pl->C.S_fix, pl->C.nslots,
@@ -405,7 +419,7 @@ void autotune(spvar_plan *pl, cudaStream_t st, int optin)
             return;
         }
     }
-    const int Tt = std::min(pl->T, 48);
+    const int Tt = std::min(pl->T, 64);
     float best = 1e30f;
     SweepShape pick{0, 256, 1, 0, 0, 0};
     bool found = false;
@@ -435,7 +449,7 @@ void autotune(spvar_plan *pl, cudaStream_t st, int optin)
         const int launches = std::min(pl->iters_max, 4) * launches_per_phase(Tt, chunk_t);
         float ms = 1e30f;
         bool ok = true;
-        for (int rep = 0; rep < 2 && ok; ++rep) {
+        for (int rep = 0; rep < 3 && ok; ++rep) {
             ok = launch_slots_init(pl->d_slots, C, pl->max_n0, st) == cudaSuccess;
             cudaEventRecord(a, st);
             for (int it = 0; it < launches && ok; ++it)
@@ -444,12 +458,14 @@ void autotune(spvar_plan *pl, cudaStream_t st, int optin)
             if (!ok || cudaEventSynchronize(b) != cudaSuccess) { ok = false; break; }
             float m = 0.f;
             cudaEventElapsedTime(&m, a, b);
-            ms = std::min(ms, m);  // the first repetition includes one-time setup
+            if (rep > 0) ms = std::min(ms, m);  // the first repetition includes one-time setup
         }
         pl->C.chunk = 0;
         if (!ok) { cudaGetLastError(); return 1e30f; }
         return ms;
     };
+    // one discarded trial first: clocks and caches settle before the timed candidates
+    if (!cands.empty()) trial(cands.front(), 0);
     for (const SweepShape &sh : cands) {
         const float ms = trial(sh, 0);
         if (ms < best) {
@@ -550,6 +566,20 @@ int spvar_plan_create(const spvar_problem *const *problems, int32_t nproblems,
         pl->sqa_P = p.sqa_slices;
         pl->sqa_W = 2 * (dmax / 2) + 1;
     }
+    if (p.sampler == SPVAR_SAMPLER_PTICM) {
+        // every problem's replicas, tables and search queues in one CTA; the exchange
+        // table covers energy differences up to n dmax (>= max E - min E of every problem)
+        pl->pt_R = p.pticm_temps;
+        pl->pt_K = p.pticm_keep;
+        for (const Problem *P : pl->probs) {
+            if (P->hdr.n > pticm_max_n() || p.pticm_temps > pticm_max_r()) { delete pl; return SPVAR_ELIMIT; }
+            pl->pt_smem = std::max(pl->pt_smem, pticm_smem_bytes(P->hdr.n, p.pticm_temps, P->hdr.dmax));
+            pl->pt_dx = std::max(pl->pt_dx, (int)std::min<long long>((long long)P->hdr.n * P->hdr.dmax, 1 << 30));
+        }
+        pl->pt_smem = std::max(pl->pt_smem, pticm_smem_bytes(pl->max_n0, p.pticm_temps, dmax));
+        pl->pt_dx = std::max(pl->pt_dx, 1);
+        if (pl->pt_smem > (size_t)optin) { delete pl; return SPVAR_ELIMIT; }
+    }
     const int nslots = nproblems * p.num_starts;
     SolveConsts &C = pl->C;
     fill_solve_consts(p, C);
@@ -570,6 +600,8 @@ int spvar_plan_create(const spvar_problem *const *problems, int32_t nproblems,
     const size_t o_ctr = take(16);
     const size_t o_thr = take(4 * (size_t)std::max(pl->T, 1) * pl->thr_stride);
     const size_t o_ent = take(pl->sqa_P > 0 ? 8 * (size_t)std::max(pl->T, 1) * 3 * pl->sqa_W : 0);
+    const size_t o_pt_thr = take(pl->pt_R > 0 ? 4 * (size_t)pl->pt_R * pl->thr_stride : 0);
+    const size_t o_pt_xthr = take(pl->pt_R > 0 ? 4 * (size_t)(pl->pt_R - 1) * ((size_t)pl->pt_dx + 1) : 0);
     const size_t o_rec = take(8 * (size_t)nslots * P_slots * Smax);
     const size_t o_rc = take(4 * (size_t)nslots * P_slots);
     const size_t o_rn = take(4 * (size_t)nslots * P_slots);
@@ -619,6 +651,10 @@ int spvar_plan_create(const spvar_problem *const *problems, int32_t nproblems,
     pl->d_ctr = (int32_t *)(w + o_ctr);
     pl->d_thr = (uint32_t *)(w + o_thr);
     if (pl->sqa_P > 0) pl->d_ent = (unsigned long long *)(w + o_ent);
+    if (pl->pt_R > 0) {
+        pl->d_pt_thr = (uint32_t *)(w + o_pt_thr);
+        pl->d_pt_xthr = (uint32_t *)(w + o_pt_xthr);
+    }
     pl->d_rec_e = (int64_t *)(w + o_rec);
     pl->d_rec_count = (int32_t *)(w + o_rc);
     pl->d_rec_nfree = (int32_t *)(w + o_rn);
@@ -647,7 +683,23 @@ int spvar_plan_create(const spvar_problem *const *problems, int32_t nproblems,
             }
             pl->sqa_ent32 = std::all_of(ent.begin(), ent.end(), [](uint64_t v) { return (v >> 32) == 0; });
         }
-        if (cudaMemcpyAsync(pl->d_thr, thr.data(), 4 * thr.size(), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        std::vector<uint32_t> pt_thr, pt_xthr;
+        if (pl->pt_R > 0) {
+            // PTICM: the temperatures' Metropolis rows and the exchange rows (beta_{k+1} - beta_k)
+            std::vector<double> bt(pl->pt_R), db(std::max(pl->pt_R - 1, 1));
+            spvar_beta_geometric(pl->pt_R, p.pticm_beta0, p.pticm_beta1, bt.data());
+            for (int k = 0; k + 1 < pl->pt_R; ++k) db[k] = bt[k + 1] - bt[k];
+            pt_thr.assign((size_t)pl->pt_R * pl->thr_stride, 0u);
+            pt_xthr.assign((size_t)(pl->pt_R - 1) * ((size_t)pl->pt_dx + 1), 0u);
+            spvar_thresholds(pl->pt_R, bt.data(), dmax, scale, pt_thr.data());
+            spvar_thresholds(pl->pt_R - 1, db.data(), pl->pt_dx, scale, pt_xthr.data());
+        }
+        if ((pl->pt_R > 0 &&
+             (cudaMemcpyAsync(pl->d_pt_thr, pt_thr.data(), 4 * pt_thr.size(), cudaMemcpyHostToDevice, st) !=
+                  cudaSuccess ||
+              cudaMemcpyAsync(pl->d_pt_xthr, pt_xthr.data(), 4 * pt_xthr.size(), cudaMemcpyHostToDevice, st) !=
+                  cudaSuccess)) ||
+            cudaMemcpyAsync(pl->d_thr, thr.data(), 4 * thr.size(), cudaMemcpyHostToDevice, st) != cudaSuccess ||
             (pl->sqa_P > 0 &&
              cudaMemcpyAsync(pl->d_ent, ent.data(), 8 * ent.size(), cudaMemcpyHostToDevice, st) != cudaSuccess) ||
             cudaStreamSynchronize(st) != cudaSuccess) {
@@ -715,8 +767,11 @@ int spvar_plan_create(const spvar_problem *const *problems, int32_t nproblems,
     if (ok) ok = cudaStreamSynchronize(st) == cudaSuccess;
     if (!ok) { cudaGetLastError(); plan_free(pl); return SPVAR_ECUDA; }
 
-    // sweep shape
-    if (p.replicas_per_block > 0) {
+    // sweep shape (PTICM: none, its runs replace the sweep launch)
+    if (pl->pt_R > 0) {
+        pl->shape = SweepShape{0, 256, 1, 0, 0, 0};
+        pl->sweep_smem = 0;
+    } else if (p.replicas_per_block > 0) {
         // requested shape: replicas per CTA, kernel and block size
         const int Q = p.replicas_per_block / 4;
         const int blk = p.sweep_block ? p.sweep_block : 256;
@@ -951,7 +1006,8 @@ int spvar_plan_stats(const spvar_plan *plan, int64_t *attempts, int32_t *phases)
     int32_t ph = 0;
     const int64_t per = (int64_t)pl->T * (pl->sqa_P > 0 ? pl->sqa_P : 1);  // SQA: every slice is swept
     for (size_t i = 0; i < n; ++i) {
-        a += (int64_t)cnt[i] * nf[i] * per;
+        // PTICM: a phase is one run, every one of its 2R replicas swept T times
+        a += pl->pt_R > 0 ? (cnt[i] > 0 ? 2ll * pl->pt_R * nf[i] * pl->T : 0) : (int64_t)cnt[i] * nf[i] * per;
         if (cnt[i] > 0) ++ph;
     }
     if (attempts) *attempts = a;

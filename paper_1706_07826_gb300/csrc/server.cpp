@@ -109,9 +109,17 @@ struct spvar_server {
     Slot *d_slots = nullptr;
     std::vector<Slot> h_slots;
     int32_t *d_modes = nullptr, *h_modes = nullptr;
-    PhaseEngine E{};
-    int grid = 1;
-    cudaGraphExec_t graph = nullptr;
+    PhaseEngine E{};  // the engine sized for the largest admissible problem
+    // Size tiers: the same engine sized for max_n, max_n / 2, max_n / 4 and
+    // max_n / 8 spins (shared memory per CTA, hence CTAs per SM, follow the size),
+    // each with its persistent grid and captured phase graph; a step launches the
+    // smallest tier that holds every problem in flight.
+    struct Tier {
+        int max_n = 0, grid = 1;
+        PhaseEngine E{};
+        cudaGraphExec_t graph = nullptr;
+    };
+    std::vector<Tier> tiers;  // ascending max_n
     std::mutex mu;
     std::condition_variable cv;
     std::deque<int64_t> queue;
@@ -243,7 +251,10 @@ int retire_request(spvar_server *S, Request &R)
 int64_t request_attempts(const spvar_server *S, const Request &R)
 {
     int64_t a = 0;
-    for (size_t i = 0; i < R.counts.size(); ++i) a += (int64_t)R.counts[i] * R.nfree[i] * S->cfg.params.num_sweeps;
+    // SQA: every Trotter slice of every run is swept
+    const int64_t per = (int64_t)S->cfg.params.num_sweeps *
+                        (S->cfg.params.sampler == SPVAR_SAMPLER_SQA ? S->cfg.params.sqa_slices : 1);
+    for (size_t i = 0; i < R.counts.size(); ++i) a += (int64_t)R.counts[i] * R.nfree[i] * per;
     return a;
 }
 
@@ -293,11 +304,21 @@ int server_step(spvar_server *S, int32_t *active_out)
     for (int64_t o : S->rslot_owner) active += (o >= 0);
     if (active_out) *active_out = active;
     if (!active) return SPVAR_OK;
-    if (S->graph) {
-        SPVAR_CUDA_TRY(cudaGraphLaunch(S->graph, S->st));
+    // the smallest size tier that holds every problem in flight
+    int maxn = 0;
+    {
+        std::lock_guard<std::mutex> g(S->mu);
+        for (int64_t o : S->rslot_owner)
+            if (o >= 0) maxn = std::max(maxn, S->reqs[o]->hp.hdr.n);
+    }
+    const spvar_server::Tier *tier = &S->tiers.back();
+    for (const spvar_server::Tier &t : S->tiers)
+        if (t.max_n >= maxn) { tier = &t; break; }
+    if (tier->graph) {
+        SPVAR_CUDA_TRY(cudaGraphLaunch(tier->graph, S->st));
     } else {
-        SPVAR_CUDA_TRY(engine_phase(S->E, S->d_slots, S->nslots, S->cfg.params.num_sweeps, S->grid, S->st, false,
-                                    false));
+        SPVAR_CUDA_TRY(engine_phase(tier->E, S->d_slots, S->nslots, S->cfg.params.num_sweeps, tier->grid, S->st,
+                                    false, false));
     }
     SPVAR_CUDA_TRY(launch_gather_modes(S->d_slots, S->nslots, S->d_modes, S->st));
     SPVAR_CUDA_TRY(cudaMemcpyAsync(S->h_modes, S->d_modes, 4 * (size_t)S->nslots, cudaMemcpyDeviceToHost, S->st));
@@ -368,7 +389,8 @@ void worker_loop(spvar_server *S)
 void server_free(spvar_server *S)
 {
     if (!S) return;
-    if (S->graph) cudaGraphExecDestroy(S->graph);
+    for (spvar_server::Tier &t : S->tiers)
+        if (t.graph) cudaGraphExecDestroy(t.graph);
     if (S->cap_st) cudaStreamDestroy(S->cap_st);
     for (cudaEvent_t e : S->ev)
         if (e) cudaEventDestroy(e);
@@ -393,8 +415,9 @@ int spvar_server_create(const spvar_server_config *cfg, spvar_server **out)
         !(p.elite_threshold > 0.0) || !(p.elite_threshold <= 1.0) || !(p.beta0 > 0.0) || !(p.beta1 > 0.0) ||
         p.canon < -1 || p.canon > 1 || p.start_offset < 0 || p.component_boost < 0 || p.component_boost > 1 || p.tree_preprocess < 0 || p.tree_preprocess > 1 || cfg->max_n < 1 || cfg->max_nnz < 0 ||
         cfg->max_degree < 1 || cfg->max_dmax < 0 || cfg->energy_scale < 1 || cfg->max_requests < 1 ||
-        cfg->budget_bytes == 0 || check_corr_params(p) != SPVAR_OK || p.sampler != SPVAR_SAMPLER_SA ||
-        cfg->sweeps_per_step < 0)
+        cfg->budget_bytes == 0 || check_corr_params(p) != SPVAR_OK || check_sampler_params(p) != SPVAR_OK ||
+        cfg->sweeps_per_step < 0 || (p.sampler == SPVAR_SAMPLER_SQA && cfg->sweeps_per_step > 0) ||
+        p.sampler == SPVAR_SAMPLER_PTICM)
         return SPVAR_EINVAL;
     const int Smax = std::max(std::max(p.fixing_sample_size, p.solving_sample_size), p.corr_sample_size);
     if (cfg->max_n > SPVAR_MAX_N || cfg->max_degree > SPVAR_MAX_DEGREE || Smax > SPVAR_MAX_SAMPLES ||
@@ -426,6 +449,10 @@ int spvar_server_create(const spvar_server_config *cfg, spvar_server **out)
     const size_t o_ctr = take(16);
     const size_t o_modes = take(4 * (size_t)S->nslots);
     const size_t o_thr = take(4 * (size_t)std::max(T, 1) * stride);
+    // SQA: acceptance entries [T][3][W] of the path-integral sweep
+    const bool sqa = p.sampler == SPVAR_SAMPLER_SQA;
+    const int sqa_W = 2 * (cfg->max_dmax / 2) + 1;
+    const size_t o_ent = take(sqa ? 8 * (size_t)std::max(T, 1) * 3 * sqa_W : 0);
     if (cudaMalloc(&S->fixed_mem, off) != cudaSuccess || cudaMalloc(&S->arena_mem, cfg->budget_bytes) != cudaSuccess ||
         cudaMallocHost(&S->h_modes, 4 * (size_t)S->nslots) != cudaSuccess) {
         cudaGetLastError();
@@ -442,6 +469,16 @@ int spvar_server_create(const spvar_server_config *cfg, spvar_server **out)
         spvar_beta_geometric(T, p.beta0, p.beta1, beta.data());
         spvar_thresholds(T, beta.data(), cfg->max_dmax, cfg->energy_scale, thr.data());
     }
+    std::vector<uint64_t> ent;
+    if (sqa) {
+        // constant beta, transverse field linear from gamma0 to gamma1 (as the plans)
+        ent.assign((size_t)std::max(T, 1) * 3 * sqa_W, 0ull);
+        std::vector<double> sb(std::max(T, 1), p.sqa_beta), sg(std::max(T, 1));
+        if (T > 0) {
+            spvar_gamma_linear(T, p.sqa_gamma0, p.sqa_gamma1, sg.data());
+            spvar_sqa_table(T, p.sqa_slices, sb.data(), sg.data(), cfg->max_dmax, cfg->energy_scale, ent.data());
+        }
+    }
     // every slot starts free (done): the phase kernels skip it
     S->h_slots.assign(S->nslots, Slot());
     for (Slot &s : S->h_slots) {
@@ -450,6 +487,8 @@ int spvar_server_create(const spvar_server_config *cfg, spvar_server **out)
     }
     S->rslot_owner.assign(cfg->max_requests, -1);
     bool ok = cudaMemcpyAsync(w + o_thr, thr.data(), 4 * thr.size(), cudaMemcpyHostToDevice, S->st) == cudaSuccess &&
+              (!sqa ||
+               cudaMemcpyAsync(w + o_ent, ent.data(), 8 * ent.size(), cudaMemcpyHostToDevice, S->st) == cudaSuccess) &&
               cudaMemcpyAsync(S->d_slots, S->h_slots.data(), sizeof(Slot) * S->nslots, cudaMemcpyHostToDevice,
                               S->st) == cudaSuccess &&
               cudaStreamSynchronize(S->st) == cudaSuccess;
@@ -464,14 +503,20 @@ int spvar_server_create(const spvar_server_config *cfg, spvar_server **out)
     const int blk = p.sweep_block ? p.sweep_block : 512;
     E.shape = SweepShape{0, blk, Q, 1, 0, 0};
     if (sweep_shape_smem(E.shape, cfg->max_n, stride, cfg->max_degree) > (size_t)optin) E.shape.stage = 0;
-    // +-1-only servers: the quad-group +-1 kernel (work items of Q quads of the
-    // largest admissible problem, more quads of smaller ones) when dmax <= 30 and
-    // Q quads fit shared memory, else the streaming +-1 kernel (one quad per CTA)
+    // +-1-only servers: the streaming +-1 kernel (one quad per CTA, per-spin data
+    // staged once per CTA), or with SPVAR_SWEEP_PM1Q the quad-group +-1 kernel
+    // (work items of Q quads of the largest admissible problem, more quads of
+    // smaller ones).  Measured at a request's 20 starts x 250 samples of 3D +-J
+    // problems, the streaming kernel leads at every size (L = 8: 3.3e11 against
+    // 2.7e11 attempts/s; L = 12: 6.3e11 against 4.8e11; L = 20: 6.9e11 against
+    // 4.0e11): the quad-group kernel pays off only when a problem has hundreds of
+    // quads to group.
     const int md = cfg->max_degree <= 6 ? 6 : 8;
     const bool pm1_only = p.sweep_kernel == SPVAR_SWEEP_PM1 || p.sweep_kernel == SPVAR_SWEEP_PM1S ||
                           p.sweep_kernel == SPVAR_SWEEP_PM1Q;
+    const bool want_quads = p.sweep_kernel == SPVAR_SWEEP_PM1Q;
     bool chosen = false;
-    if (pm1_only && p.sweep_kernel != SPVAR_SWEEP_PM1S && cfg->max_degree <= 8 && cfg->max_dmax <= 30) {
+    if (pm1_only && want_quads && cfg->max_degree <= 8 && cfg->max_dmax <= 30) {
         const int qb = (p.sweep_block == 128 || p.sweep_block == 256) ? p.sweep_block : 512;
         SweepShape sh{6, qb, Q, 0, 0, md};
         if (pm1q_shape_ok(qb, md, cfg->max_n, Q) && sweep_shape_smem(sh, cfg->max_n, stride, cfg->max_degree) <= (size_t)optin) {
@@ -485,6 +530,22 @@ int spvar_server_create(const spvar_server_config *cfg, spvar_server **out)
             E.shape = sh;
             Q = 1;
         }
+    }
+    if (sqa) {
+        // SQA: one quad (four runs, all slices in shared memory) per CTA, the item walk
+        // over (slice, spin) (any problem that fits, +-1 or general couplers)
+        const int sb = (p.sweep_block == 128 || p.sweep_block == 256 || p.sweep_block == 512) ? p.sweep_block : 256;
+        SweepShape sh{5, sb, 1, pm1_only ? 1 : 0, sqa_W, cfg->max_degree};
+        sh.slices = p.sqa_slices;
+        if (!sqa_shape_ok(sh.stage, sb, cfg->max_n, cfg->max_degree, p.sqa_slices, sqa_W, 0) ||
+            sweep_shape_smem(sh, cfg->max_n, stride, cfg->max_degree) > (size_t)optin) {
+            server_free(S);
+            return SPVAR_ELIMIT;
+        }
+        E.shape = sh;
+        E.ent = (const unsigned long long *)(w + o_ent);
+        E.P = p.sqa_slices;
+        E.W = sqa_W;
     }
     E.C.Q = E.shape.Q;
     E.C.chunk = (cfg->sweeps_per_step > 0 && cfg->sweeps_per_step < T) ? cfg->sweeps_per_step : 0;
@@ -510,18 +571,29 @@ int spvar_server_create(const spvar_server_config *cfg, spvar_server **out)
     E.ev_sweep[0] = S->ev[0];
     E.ev_sweep[1] = S->ev[1];
     E.ev_post = nullptr;
-    const int occ = std::max(1, sweep_shape_occupancy(E.shape, E.pm1, E.sweep_smem));
-    S->grid = occ * S->sms;
-    // capture one phase over the whole slot table
-    cudaGraph_t g = nullptr;
-    if (cudaStreamBeginCapture(S->cap_st, cudaStreamCaptureModeRelaxed) == cudaSuccess) {
-        cudaError_t e = engine_phase(E, S->d_slots, S->nslots, T, S->grid, S->cap_st, false, true);
-        cudaError_t e2 = cudaStreamEndCapture(S->cap_st, &g);
-        if (e == cudaSuccess && e2 == cudaSuccess && g && cudaGraphInstantiate(&S->graph, g, 0) != cudaSuccess)
-            S->graph = nullptr;
-        if (g) cudaGraphDestroy(g);
+    // size tiers, smallest first; each captures one phase step over the whole slot table
+    for (int k = 3; k >= 0; --k) {
+        const int tn = cfg->max_n >> k;
+        if (k > 0 && (tn < 256 || (!S->tiers.empty() && S->tiers.back().max_n == tn))) continue;
+        spvar_server::Tier t;
+        t.max_n = tn;
+        t.E = E;
+        t.E.max_n0 = tn;
+        t.E.C.max_n0 = tn;
+        t.E.sweep_smem = sweep_shape_smem(E.shape, tn, stride, cfg->max_degree);
+        const int occ = std::max(1, sweep_shape_occupancy(t.E.shape, t.E.pm1, t.E.sweep_smem));
+        t.grid = occ * S->sms;
+        cudaGraph_t g = nullptr;
+        if (cudaStreamBeginCapture(S->cap_st, cudaStreamCaptureModeRelaxed) == cudaSuccess) {
+            cudaError_t e = engine_phase(t.E, S->d_slots, S->nslots, T, t.grid, S->cap_st, false, true);
+            cudaError_t e2 = cudaStreamEndCapture(S->cap_st, &g);
+            if (e == cudaSuccess && e2 == cudaSuccess && g && cudaGraphInstantiate(&t.graph, g, 0) != cudaSuccess)
+                t.graph = nullptr;
+            if (g) cudaGraphDestroy(g);
+        }
+        cudaGetLastError();
+        S->tiers.push_back(t);
     }
-    cudaGetLastError();
     *out = S;
     return SPVAR_OK;
 }

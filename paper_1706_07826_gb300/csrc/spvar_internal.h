@@ -159,7 +159,18 @@ struct SolveConsts {
     // chunk > 0 a phase's sample is annealed over ceil(T / chunk) launches, each resuming
     // from the states the previous one wrote; the persistence pass runs after the last.
     int32_t T, chunk;
+    // PTICM as the sampler: a phase's sample size is the number of states its run
+    // kept (the slot's rec_count of the phase), and the elite is ceil(elite x that)
+    int32_t pticm, pad2;
+    double elite;
 };
+// Elite count k = ceil(elite * S), clamped to [1, S] (host and device).
+__host__ __device__ inline int elite_count_hd(double elite, int S)
+{
+    const double x = ceil(elite * (double)S);
+    const int k = (x >= (double)S) ? S : (int)x;
+    return k < 1 ? 1 : (k > S ? S : k);
+}
 // Samples and elite size of a slot's current phase.
 __host__ __device__ inline int phase_samples(const SolveConsts &C, int mode)
 {
@@ -186,6 +197,16 @@ inline int check_corr_params(const spvar_params &p)
 inline int check_sampler_params(const spvar_params &p)
 {
     if (p.sampler == SPVAR_SAMPLER_SA) return SPVAR_OK;
+    if (p.sampler == SPVAR_SAMPLER_PTICM) {
+        const int R = p.pticm_temps, ntr = 2 * (p.pticm_temps - p.pticm_temps / 2);
+        if (R < 2 || R > 64 || p.pticm_keep < 1 || p.pticm_keep > SPVAR_PTICM_MAX_KEEP ||
+            p.fixing_sample_size != ntr * p.pticm_keep ||
+            (p.solving_sample_size != 0 && p.solving_sample_size != ntr * p.pticm_keep) || p.num_sweeps < 1 ||
+            p.corr_sample_size != 0 || p.component_boost != 0 || p.sweeps_per_launch != 0 ||
+            !(p.pticm_beta0 > 0.0) || !(p.pticm_beta1 > 0.0))
+            return SPVAR_EINVAL;
+        return SPVAR_OK;
+    }
     if (p.sampler != SPVAR_SAMPLER_SQA) return SPVAR_EINVAL;
     if (p.sqa_slices < 1 || (p.sqa_slices > 1 && (p.sqa_slices & 1)) || p.sqa_slices > SPVAR_SQA_MAX_SLICES ||
         !(p.sqa_beta > 0.0) || !(p.sqa_gamma0 > 0.0) || !(p.sqa_gamma1 > 0.0))
@@ -213,6 +234,9 @@ inline void fill_solve_consts(const spvar_params &p, SolveConsts &C)
     C.tree = p.tree_preprocess;
     C.T = p.num_sweeps;
     C.chunk = 0;
+    C.pticm = p.sampler == SPVAR_SAMPLER_PTICM ? 1 : 0;
+    C.pad2 = 0;
+    C.elite = p.elite_threshold;
 }
 // Sweep launches per phase: ceil(T / chunk), or 1 without chunking.
 inline int launches_per_phase(int T, int chunk) { return (chunk > 0 && T > chunk) ? (T + chunk - 1) / chunk : 1; }
@@ -259,7 +283,7 @@ inline void boost_slot_carve(Slot &s, char *base, int n0, int Smax, int W0)
 // chunk (free spins, free-free entries, nonzero-bias flag, the chunk's
 // reference-spin candidate, free spins per colour class) and the int64 sum of
 // the fixed spins' energy.
-constexpr int kFoldChunk = 1024;
+constexpr int kFoldChunk = 256;
 constexpr int kFoldMaxChunks = (SPVAR_MAX_N + kFoldChunk - 1) / kFoldChunk;
 constexpr int kFoldStride = 40;  // >= 6 + kMaxColours
 inline size_t slot_scratch_ints(int cap_n)
@@ -330,6 +354,9 @@ int pm1q_max_active_blocks(int block, int maxd, size_t smem);
 // PTICM sampler (sweep_pticm.cu): one CTA per run, every replica's spins in
 // shared memory.
 size_t pticm_smem_bytes(int n, int R, int dmax);
+// PTICM runs of every start of a slot table (the sampler of Alg. 2 in a plan).
+cudaError_t launch_pticm_slots(Slot *slots, int nslots, int Smax, const uint32_t *thr, int thr_stride,
+                               const uint32_t *xthr, int dx, int R, int T, int K, size_t smem, cudaStream_t st);
 int pticm_max_r();
 int pticm_max_n();
 cudaError_t launch_pticm(const DevProb *prob, const uint32_t *thr, int thr_stride, const uint32_t *xthr, int dx,
@@ -436,6 +463,11 @@ struct PhaseEngine {
     cudaEvent_t ev_sweep[2];
     cudaEvent_t ev_post;  // recorded after each phase's persistence pass (null: none)
     SolveConsts C;
+    // PTICM as the sampler (pt_R > 0): one run per start instead of the sweep launch
+    int pt_R = 0, pt_K = 0, pt_dx = 0;
+    const uint32_t *pt_thr = nullptr;   // [R][thr_stride]
+    const uint32_t *pt_xthr = nullptr;  // [R - 1][pt_dx + 1]
+    size_t pt_smem = 0;
 };
 // plan -> sweep -> elite -> count/fix -> fold/compact for `nslots` slots.
 cudaError_t engine_phase(const PhaseEngine &E, Slot *slots, int nslots, int T, int grid, cudaStream_t st,

@@ -27,6 +27,8 @@
 //   4. a warp per tracked replica offers its state, bit-packed in index
 //      order, to the replica's list of the K lowest distinct states seen.
 // Every wait is a CTA or warp barrier that all of its threads reach.
+#include <cstring>
+
 #include "sweep_common.cuh"
 
 namespace spvar {
@@ -49,6 +51,11 @@ struct PticmArgs {
     int32_t *nkept;        // [runs][ntr]
     uint32_t *final_bits;  // [runs][2R][W]
     int64_t *final_e;      // [runs][2R] (with offset)
+    // slot mode (the sampler of Alg. 2 in a plan): CTA b runs start b of the slot
+    // table with that start's current problem, seed and phase; the kept lists go
+    // to its sample rows and recorded energies and are compacted there
+    Slot *slots;
+    int32_t Smax;
 };
 
 __device__ __forceinline__ uint32_t word0(uint32_t w0, uint32_t y, uint32_t start, uint32_t k0, uint32_t k1)
@@ -89,18 +96,30 @@ __global__ void __launch_bounds__(B, 2) k_pticm(const PticmArgs A)
     __shared__ int sE[2 * kPtMaxR], sAcc[kPtMaxR];
     __shared__ int s_cptr[kMaxColours + 1];
     __shared__ uint32_t sPack[B / 32][kPtWarpWords];
+    __shared__ int32_t s_nk[2 * kPtMaxR];  // slot mode: the kept lists' lengths
 
-    const DevProb *P = A.prob;
+    const int run = blockIdx.x;
+    Slot *slot = A.slots ? A.slots + run : nullptr;
+    if (slot && slot->mode == kDone) return;  // the whole CTA: a finished start
+    const DevProb *P = slot ? slot->cur : A.prob;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int n = P->n, ncol = P->ncol, cap_n = P->cap_n, dmax = P->dmax;
     const int R = A.R, NR = 2 * R, T = A.T;
     const int nic = R - A.icm_from;            // temperatures with cluster moves
     const int ntr = 2 * (R - A.keep_from);     // tracked replicas
     const int W = (n + 31) >> 5;
-    const int run = blockIdx.x;
-    const uint32_t start = A.start0 + (uint32_t)run;
-    const uint32_t k0 = (uint32_t)A.seed, k1 = (uint32_t)(A.seed >> 32);
-    const uint32_t phase_hi = A.phase << kSweepBits;
+    const uint64_t seed = slot ? slot->seed : A.seed;
+    const uint32_t start = slot ? slot->start : A.start0 + (uint32_t)run;
+    const uint32_t phase = slot ? (uint32_t)slot->phase : A.phase;
+    const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+    const uint32_t phase_hi = phase << kSweepBits;
+    // kept lists: list q, entry j at kept_rows + (q K + j) kstride words, energy kept_en[q K + j], length nk[q]
+    const size_t kstride = slot ? (size_t)slot->W0 : (size_t)W;
+    uint32_t *kept_rows = slot ? slot->spins : A.kept + (size_t)run * ntr * A.K * W;
+    int64_t *kept_en = slot ? slot->rec_e + (size_t)slot->phase * A.Smax : A.kept_e + (size_t)run * ntr * A.K;
+    int32_t *nk = slot ? s_nk : A.nkept + (size_t)run * ntr;
+    if (slot)
+        for (int q = tid; q < ntr; q += B) s_nk[q] = 0;
 
     uint8_t *s8 = smem_pt;                                         // [2R][n]
     uint32_t *thr_s = reinterpret_cast<uint32_t *>(smem_pt + (((size_t)NR * n + 15) & ~(size_t)15));
@@ -313,10 +332,9 @@ __global__ void __launch_bounds__(B, 2) k_pticm(const PticmArgs A)
         for (int q = warp; q < ntr; q += B / 32) {
             const int r = 2 * (A.keep_from + q / 2) + (q & 1);
             const int64_t E = (int64_t)sE[r] + P->offset;
-            const size_t base = (size_t)run * ntr + q;
-            int32_t *cntp = A.nkept + base;
-            int64_t *le = A.kept_e + base * A.K;
-            uint32_t *lst = A.kept + base * A.K * W;
+            int32_t *cntp = nk + q;
+            int64_t *le = kept_en + (size_t)q * A.K;
+            uint32_t *lst = kept_rows + (size_t)q * A.K * kstride;
             const int cnt = *cntp;
             if (cnt == A.K && E >= le[A.K - 1]) continue;
             // the state, bit-packed in index order
@@ -331,7 +349,7 @@ __global__ void __launch_bounds__(B, 2) k_pticm(const PticmArgs A)
             for (int j = 0; j < cnt && !dup; ++j) {
                 if (le[j] != E) continue;
                 bool diff = false;
-                for (int w = lane; w < W; w += 32) diff |= lst[(size_t)j * W + w] != sPack[warp][w];
+                for (int w = lane; w < W; w += 32) diff |= lst[(size_t)j * kstride + w] != sPack[warp][w];
                 dup = !__any_sync(0xFFFFFFFFu, diff);
             }
             if (dup) continue;
@@ -339,12 +357,13 @@ __global__ void __launch_bounds__(B, 2) k_pticm(const PticmArgs A)
             while (pos > 0 && le[pos - 1] > E) --pos;
             const int last = cnt < A.K ? cnt : A.K - 1;
             for (int j = last; j > pos; --j) {
-                for (int w = lane; w < W; w += 32) lst[(size_t)j * W + w] = lst[(size_t)(j - 1) * W + w];
+                for (int w = lane; w < W; w += 32)
+                    lst[(size_t)j * kstride + w] = lst[(size_t)(j - 1) * kstride + w];
                 __syncwarp();
                 if (lane == 0) le[j] = le[j - 1];
                 __syncwarp();
             }
-            for (int w = lane; w < W; w += 32) lst[(size_t)pos * W + w] = sPack[warp][w];
+            for (int w = lane; w < W; w += 32) lst[(size_t)pos * kstride + w] = sPack[warp][w];
             if (lane == 0) {
                 le[pos] = E;
                 if (cnt < A.K) *cntp = cnt + 1;
@@ -352,6 +371,28 @@ __global__ void __launch_bounds__(B, 2) k_pticm(const PticmArgs A)
             __syncwarp();
         }
         __syncthreads();
+    }
+    if (slot) {
+        // the phase's sample: the lists one after another.  List q moves down by
+        // q K - (entries before it); rows are copied in waves of that distance, so
+        // a wave never overwrites a row a later wave still reads
+        int before = 0;
+        for (int q = 0; q < ntr; ++q) {
+            const int len = s_nk[q], shift = q * A.K - before;
+            if (shift > 0)
+                for (int j0 = 0; j0 < len; j0 += shift) {
+                    const int jn = min(len, j0 + shift);
+                    for (int x = tid; x < (jn - j0) * W; x += B) {
+                        const int j = j0 + x / W, w = x - (x / W) * W;
+                        kept_rows[(size_t)(before + j) * kstride + w] = kept_rows[(size_t)(q * A.K + j) * kstride + w];
+                    }
+                    for (int j = j0 + tid; j < jn; j += B) kept_en[before + j] = kept_en[q * A.K + j];
+                    __syncthreads();
+                }
+            before += len;
+        }
+        if (tid == 0) slot->rec_count[slot->phase] = before;
+        return;
     }
     // final states and energies of every replica
     for (int r = warp; r < NR; r += B / 32) {
@@ -401,11 +442,42 @@ cudaError_t launch_pticm(const DevProb *prob, const uint32_t *thr, int thr_strid
     A.nkept = nkept;
     A.final_bits = final_bits;
     A.final_e = final_e;
+    A.slots = nullptr;
+    A.Smax = 0;
     void *k = reinterpret_cast<void *>(k_pticm<kPtBlock>);
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     void *args[] = {&A};
     return cudaLaunchKernel(k, dim3(runs), dim3(kPtBlock), args, smem, st);
+}
+
+}  // namespace spvar
+
+namespace spvar {
+
+cudaError_t launch_pticm_slots(Slot *slots, int nslots, int Smax, const uint32_t *thr, int thr_stride,
+                               const uint32_t *xthr, int dx, int R, int T, int K, size_t smem, cudaStream_t st)
+{
+    if (nslots <= 0) return cudaSuccess;
+    PticmArgs A;
+    std::memset(&A, 0, sizeof(A));
+    A.thr = thr;
+    A.xthr = xthr;
+    A.R = R;
+    A.T = T;
+    A.thr_stride = thr_stride;
+    A.dx = dx;
+    A.icm_from = R / 2;
+    A.keep_from = R / 2;
+    A.K = K;
+    A.flags = 3;
+    A.slots = slots;
+    A.Smax = Smax;
+    void *k = reinterpret_cast<void *>(k_pticm<kPtBlock>);
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    void *args[] = {&A};
+    return cudaLaunchKernel(k, dim3(nslots), dim3(kPtBlock), args, smem, st);
 }
 
 }  // namespace spvar

@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(HERE, "libspvar.so")
 OK, EINVAL, EOVERFLOW, ENOMEM, EBUDGET, ETIMEOUT, ECUDA, ELIMIT = 0, -1, -2, -3, -4, -5, -6, -7
 FORM_BATCHED, FORM_PLAIN = 0, 1
 SWEEP_AUTO, SWEEP_GENERAL, SWEEP_PM1, SWEEP_PM1S, SWEEP_PM1W, SWEEP_PM1Q = 0, 1, 2, 3, 4, 5
-SAMPLER_SA, SAMPLER_SQA = 0, 1
+SAMPLER_SA, SAMPLER_SQA, SAMPLER_PTICM = 0, 1, 2
 MAX_N, MAX_DEGREE, MAX_SWEEPS, MAX_PHASE, MAX_SAMPLES = 32768, 32, 1048574, 4095, 16384
 NOALLOC_MAX_N = 16384
 
@@ -48,7 +48,8 @@ class Params(ctypes.Structure):
                 ("component_boost", i32), ("tree_preprocess", i32), ("corr_sample_size", i32),
                 ("corr_num", i32), ("corr_den", i32), ("corr_elite_threshold", ctypes.c_double),
                 ("sampler", i32), ("sqa_slices", i32), ("sqa_beta", ctypes.c_double), ("sqa_gamma0", ctypes.c_double),
-                ("sqa_gamma1", ctypes.c_double), ("sweeps_per_launch", i32)]
+                ("sqa_gamma1", ctypes.c_double), ("sweeps_per_launch", i32), ("pticm_temps", i32),
+                ("pticm_keep", i32), ("pticm_beta0", ctypes.c_double), ("pticm_beta1", ctypes.c_double)]
 
 
 class ServerConfig(ctypes.Structure):
@@ -422,12 +423,22 @@ def make_params(num_starts=1, fixing_sample_size=100, solving_sample_size=100, n
                 form=FORM_BATCHED, replicas_per_block=0, sweep_kernel=SWEEP_AUTO, sweep_block=0, start_offset=0,
                 component_boost=False, tree_preprocess=False, corr_sample_size=0, corr_elite_threshold=0.2,
                 corr_num=1, corr_den=1, sampler=0, sqa_slices=16, sqa_beta=3.0, sqa_gamma0=3.0, sqa_gamma1=0.01,
-                sweeps_per_launch=0):
+                sweeps_per_launch=0, pticm_temps=16, pticm_keep=10, pticm_beta0=0.2, pticm_beta1=3.0):
+    """Parameters of Alg. 2.  With the PTICM sampler the phase's sample is the
+    kept lists, so fixing_sample_size (and a nonzero solving_sample_size) must be
+    pticm_sample_size(pticm_temps, pticm_keep)."""
     return Params(num_starts, fixing_sample_size, solving_sample_size, num_sweeps, beta0, beta1, elite_threshold,
                   fix_num, fix_den, 1 if iterate else 0, max_fix_phases, canon, form, replicas_per_block,
                   sweep_kernel, sweep_block, start_offset, 1 if component_boost else 0, 1 if tree_preprocess else 0,
                   corr_sample_size, corr_num, corr_den, float(corr_elite_threshold), sampler, sqa_slices,
-                  float(sqa_beta), float(sqa_gamma0), float(sqa_gamma1), int(sweeps_per_launch))
+                  float(sqa_beta), float(sqa_gamma0), float(sqa_gamma1), int(sweeps_per_launch), int(pticm_temps),
+                  int(pticm_keep), float(pticm_beta0), float(pticm_beta1))
+
+
+def pticm_sample_size(temps, keep):
+    """Most states a PTICM phase keeps: K per replica of the lower half of the
+    temperatures, two replicas each."""
+    return 2 * (temps - temps // 2) * keep
 
 
 def phase_slots(params):

@@ -3,14 +3,16 @@ isoenergetic cluster moves, Sec. III.D; spvar_pticm_sample), against the
 oracle: every run's kept lists (states, energies, counts) and every replica's
 final state and energy identical, bit for bit, for +-1, integer and U_10
 couplers, odd and even temperature counts, and with exchanges or cluster
-moves switched off."""
+moves switched off; and Alg. 2 with PTICM as the sampler of every phase (one
+run per start and phase, the kept lists as the sample) in plans, batched and
+plain, against the oracle's Alg. 2."""
 import numpy as np
 import pytest
 
 from oracle import oracle as O
 from paper_1706_07826_gb300 import instances as I
 
-from gpu_cases import gpu_problem, oracle_problem, with_h
+from gpu_cases import gpu_problem, oracle_problem, table, with_h
 
 pytestmark = pytest.mark.gpu
 
@@ -68,3 +70,58 @@ def test_pticm_limits(cuda_lib):
     mid = I.cubic3d(12, 5)  # N = 1728: 64 temperatures of replicas and queues need more than one CTA's shared memory
     with pytest.raises(spvar.SpvarError):
         spvar.pticm_sample(gpu_problem(mid), np.geomspace(0.1, 3.0, 64), 2, spvar.energy_range(mid))
+
+
+PT_CASES = [
+    # name, instance, T, R, K, starts, iterate, max_fix, tree
+    ("cubic_L3", lambda: I.cubic3d(3, 5), 30, 6, 4, 2, False, 1, False),
+    ("chimera_C2_h", lambda: with_h(I.chimera(2, 6), 7, 2), 24, 8, 3, 3, False, 1, False),
+    ("cubic_L4_ispvar_tree", lambda: I.cubic3d(4, 8), 20, 6, 3, 2, True, 40, True),
+    ("random_odd_colours", lambda: I.random_graph(40, 90, 12, jmax=2, hmax=1), 25, 5, 5, 2, False, 1, False),
+]
+
+
+@pytest.mark.parametrize("form", [0, 1], ids=["batched", "plain"])
+@pytest.mark.parametrize("name,make,T,R,K,starts,iterate,mf,tree", PT_CASES, ids=[c[0] for c in PT_CASES])
+def test_solve_with_pticm_sampler_matches_oracle(cuda_lib, form, name, make, T, R, K, starts, iterate, mf, tree):
+    """Alg. 2 with PTICM (Sec. III.D) as the sampler of every phase: each
+    phase's sample is the run's kept lists; recorded energies, sample sizes,
+    free spins, fix maps and best states equal the oracle's."""
+    from paper_1706_07826_gb300 import spvar
+    from test_gpu_solve import _check
+    inst = make()
+    S = spvar.pticm_sample_size(R, K)
+    Ss = 0 if iterate else S
+    seed = 31
+    ref = O.solve(oracle_problem(inst), table(inst, T), seed, num_starts=starts, fixing_sample_size=S,
+                  solving_sample_size=Ss, elite_threshold=0.25, iterate=iterate, max_fix_phases=mf, tree=tree,
+                  sampler=2, pticm_temps=R, pticm_keep=K, pticm_beta0=0.3, pticm_beta1=2.5)
+    prm = spvar.make_params(num_starts=starts, fixing_sample_size=S, solving_sample_size=Ss, num_sweeps=T,
+                            elite_threshold=0.25, iterate=iterate, max_fix_phases=mf, tree_preprocess=tree, form=form,
+                            sampler=spvar.SAMPLER_PTICM, pticm_temps=R, pticm_keep=K, pticm_beta0=0.3, pticm_beta1=2.5)
+    plan = spvar.Plan([gpu_problem(inst)], prm)
+    out = plan.run(seed, device=False)
+    att, _ = plan.stats()
+    plan.close()
+    _check(out, ref, starts, mf + 1, inst.n)
+    assert att > 0
+
+
+def test_pticm_sampler_parameters_are_checked(cuda_lib):
+    from paper_1706_07826_gb300 import spvar
+    inst = I.cubic3d(3, 2)
+    bad = [dict(fixing_sample_size=10, solving_sample_size=10),        # not 2 (R - R/2) K
+           dict(fixing_sample_size=24, solving_sample_size=24, component_boost=True),
+           dict(fixing_sample_size=24, solving_sample_size=24, num_sweeps=0)]
+    for kw in bad:
+        kw.setdefault("num_sweeps", 10)
+        with pytest.raises(spvar.SpvarError) as e:
+            spvar.Plan([gpu_problem(inst)], spvar.make_params(sampler=spvar.SAMPLER_PTICM, pticm_temps=6,
+                                                               pticm_keep=4, **kw))
+        assert e.value.code == spvar.EINVAL
+    big = I.cubic3d(13, 3)  # 2197 spins > 2048
+    with pytest.raises(spvar.SpvarError) as e:
+        spvar.Plan([gpu_problem(big)], spvar.make_params(sampler=spvar.SAMPLER_PTICM, pticm_temps=6, pticm_keep=4,
+                                                         fixing_sample_size=24, solving_sample_size=24,
+                                                         num_sweeps=10))
+    assert e.value.code == spvar.ELIMIT

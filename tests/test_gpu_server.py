@@ -39,8 +39,9 @@ def _server(spvar, budget, max_requests=3, pm1=False, sweeps_per_step=0, kernel=
                         sweeps_per_step=sweeps_per_step)
 
 
-SERVER_CASES = [("general", False, 0, None), ("pm1_quads", True, 0, None), ("pm1_quads_steps17", True, 17, None),
-                ("general_steps25", False, 25, None), ("pm1_streaming_steps9", True, 9, 3)]
+SERVER_CASES = [("general", False, 0, None), ("pm1", True, 0, None), ("pm1_steps17", True, 17, None),
+                ("general_steps25", False, 25, None), ("pm1_streaming_steps9", True, 9, 3),
+                ("pm1_quads", True, 0, 5), ("pm1_quads_steps13", True, 13, 5)]
 
 
 @pytest.mark.parametrize("name,pm1,sps,kernel", SERVER_CASES, ids=[c[0] for c in SERVER_CASES])
@@ -74,7 +75,7 @@ def test_results_identical_alone_and_in_the_mix(cuda_lib, name, pm1, sps, kernel
     srv.close()
 
 
-@pytest.mark.parametrize("pm1,sps", [(False, 0), (True, 7)], ids=["general", "pm1_quads_steps7"])
+@pytest.mark.parametrize("pm1,sps", [(False, 0), (True, 7)], ids=["general", "pm1_steps7"])
 def test_server_request_matches_oracle(cuda_lib, pm1, sps):
     spvar = cuda_lib
     inst = I.cubic3d(3, 70)
@@ -129,3 +130,42 @@ def test_server_sweep_time_counts_every_step(cuda_lib):
     ms, n = srv.sweep_time()
     assert n == steps + 1 and ms > 0
     srv.close()
+
+
+@pytest.mark.parametrize("pm1", [False, True], ids=["general", "pm1"])
+def test_sqa_requests_identical_alone_and_in_the_mix(cuda_lib, pm1):
+    """The second sampler in the request loop: requests sampled by SQA (4
+    Trotter slices) give in a mix exactly what each gives solved alone, and one
+    request equals the oracle's Alg. 2 with SQA in every phase."""
+    spvar = cuda_lib
+    sqa = dict(sampler=spvar.SAMPLER_SQA, sqa_slices=4, sqa_beta=2.0, sqa_gamma0=2.5, sqa_gamma1=0.05)
+    prm = spvar.make_params(**KW, **sqa, sweep_kernel=spvar.SWEEP_PM1 if pm1 else 0)
+    srv = spvar.Server(prm, 600 << 10, max_n=400, max_nnz=3000, max_degree=6, max_dmax=12, max_requests=3)
+    insts = [I.cubic3d(4, 161), I.chimera(3, 162), I.cubic3d(5, 163), I.chimera(2, 164)]
+    ids = [srv.submit(insts[0], 11)]
+    srv.step()
+    ids += [srv.submit(x, 12 + i) for i, x in enumerate(insts[1:])]
+    steps = 0
+    while srv.step() > 0 or srv.stats()["queued"] > 0:
+        steps += 1
+        assert steps < 100
+    for rid, inst, seed in zip(ids, insts, [11, 12, 13, 14]):
+        alone = spvar.solve(gpu_problem(inst), spvar.make_params(**KW, **sqa), seed)
+        _same(srv.result(rid), alone)
+    inst = insts[1]
+    op = oracle_problem(inst)
+    ref = O.solve(op, table(inst, KW["num_sweeps"], dmax=12), 12, num_starts=3, fixing_sample_size=48,
+                  solving_sample_size=24, elite_threshold=0.2, sampler=1, sqa_slices=4, sqa_beta=2.0, sqa_gamma0=2.5,
+                  sqa_gamma1=0.05)
+    out = srv.result(ids[1])
+    assert np.array_equal(out.best_energy, ref.best_e)
+    assert np.array_equal(out.fixed.reshape(3, -1), ref.fixed)
+    srv.close()
+
+
+def test_sqa_server_rejects_sweep_steps(cuda_lib):
+    spvar = cuda_lib
+    prm = spvar.make_params(**KW, sampler=spvar.SAMPLER_SQA, sqa_slices=4)
+    with pytest.raises(spvar.SpvarError) as e:
+        spvar.Server(prm, 1 << 20, max_n=100, max_nnz=600, max_degree=6, max_dmax=12, sweeps_per_step=10)
+    assert e.value.code == spvar.EINVAL
