@@ -443,6 +443,26 @@ def measure_pticm(spvar, torch, flush):
     return {"value": att / (ms / 1000.0), "best": int(out["kept_e"][:, :, 0].min().item())}
 
 
+def measure_pticm_spvar(spvar, torch, flush):
+    """Alg. 2 with PTICM as the sampler of every phase (Sec. III.D sample) on 3D
+    +-J L=10: 304 starts (two runs per SM), 16 temperatures geometric 0.2 -> 3.0,
+    10 kept states per tracked replica (160-state samples), 1000 sweeps, elite
+    0.2; attempts count every replica's Metropolis proposals."""
+    from paper_1706_07826_gb300 import instances as I
+    inst = I.cubic3d(10, 1600)
+    prob = spvar.Problem.from_instance(inst)
+    S = spvar.pticm_sample_size(16, 10)
+    prm = spvar.make_params(num_starts=304, fixing_sample_size=S, solving_sample_size=S, num_sweeps=1000,
+                            elite_threshold=0.2, sampler=spvar.SAMPLER_PTICM, pticm_temps=16, pticm_keep=10,
+                            pticm_beta0=0.2, pticm_beta1=3.0)
+    plan = spvar.Plan([prob], prm)
+    aps, ms, att, sweep_ms, sweep_n, out = timed_plan(spvar, torch, plan, [1601], flush, "pticm_spvar")
+    nfree = out.nfree.cpu().numpy()
+    plan.close()
+    return {"value": aps, "ms": ms, "best": int(out.best_energy.min().item()),
+            "fixed_frac": float(1.0 - nfree[:, 1].mean() / inst.n)}
+
+
 def _hbm_peak_gbs():
     """Measured copy bandwidth of this GPU pool (GB/s), or the recipe's fallback."""
     try:
@@ -698,6 +718,7 @@ def gpu_arm(args, rank, world):
         extra["c5"] = measure_serving(spvar, peaks)
         extra["sqa"] = measure_sqa(spvar, torch, flush, peaks)
         extra["pticm"] = measure_pticm(spvar, torch, flush)
+        extra["pticm_spvar"] = measure_pticm_spvar(spvar, torch, flush)
         extra["persist"] = measure_persistence_scaled(spvar, torch)
         extra["spl"] = measure_sweeps_per_launch(spvar, torch, flush, peaks)
 
@@ -722,9 +743,10 @@ def gpu_arm(args, rank, world):
                          ms_per_launch=ms_per_launch, peak_kind="measured issue probe"),
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                 "api": "problem_create+solve", "ms_per_step": 1000 * statistics.mean(e2e_times)},
-        # per run: slot init, then per sweep launch of each of the two phases the six phase kernels
-        # (plan, sweep, elite, count/fix, fold/compact, active count) and the loop-condition kernel
-        "gpu_launches": K * (1 + 2 * -(-1000 // max(shape["sweeps_per_launch"], 1)) * (6 + 1)),
+        # per run: slot init, then per sweep launch of each of the two phases the nine phase kernels
+        # (work list, sweep, elite, count/fix, and the fold/compact's prep, count, index, fill and
+        # finish) and the loop-condition kernel
+        "gpu_launches": K * (1 + 2 * -(-1000 // max(shape["sweeps_per_launch"], 1)) * (9 + 1)),
         "clocks": cs,
         "plain": {"value": plain_value, "speedup": value / world / plain_value},
         "peaks": dict(peaks.summary(), sm_mhz=clk_peak.summary()["sm_mhz"]),

@@ -125,3 +125,27 @@ def test_pticm_sampler_parameters_are_checked(cuda_lib):
                                                          fixing_sample_size=24, solving_sample_size=24,
                                                          num_sweeps=10))
     assert e.value.code == spvar.ELIMIT
+
+
+def test_pticm_sampler_with_problems_of_different_size(cuda_lib):
+    """Two problems of different size and colouring in one PTICM plan (one run
+    per start of each, in one launch per phase): each equals the oracle."""
+    from paper_1706_07826_gb300 import spvar
+    from test_gpu_solve import _check
+    insts = [I.cubic3d(4, 21), I.chimera(2, 22)]
+    T, R, K, starts = 20, 6, 3, 2
+    S = spvar.pticm_sample_size(R, K)
+    prm = spvar.make_params(num_starts=starts, fixing_sample_size=S, solving_sample_size=S, num_sweeps=T,
+                            elite_threshold=0.25, sampler=spvar.SAMPLER_PTICM, pticm_temps=R, pticm_keep=K,
+                            pticm_beta0=0.3, pticm_beta1=2.5)
+    plan = spvar.Plan([gpu_problem(x) for x in insts], prm)
+    seeds = [41, 42]
+    out = plan.run(seeds, device=False)
+    plan.close()
+    fm0 = 0
+    for pi, inst in enumerate(insts):
+        ref = O.solve(oracle_problem(inst), table(inst, T), seeds[pi], num_starts=starts, fixing_sample_size=S,
+                      solving_sample_size=S, elite_threshold=0.25, sampler=2, pticm_temps=R, pticm_keep=K,
+                      pticm_beta0=0.3, pticm_beta1=2.5)
+        _check(out, ref, starts, 2, inst.n, slot0=pi * starts, fm0=fm0)
+        fm0 += starts * inst.n
