@@ -743,10 +743,9 @@ def gpu_arm(args, rank, world):
                          ms_per_launch=ms_per_launch, peak_kind="measured issue probe"),
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                 "api": "problem_create+solve", "ms_per_step": 1000 * statistics.mean(e2e_times)},
-        # per run: slot init, then per sweep launch of each of the two phases the nine phase kernels
-        # (work list, sweep, elite, count/fix, and the fold/compact's prep, count, index, fill and
-        # finish) and the loop-condition kernel
-        "gpu_launches": K * (1 + 2 * -(-1000 // max(shape["sweeps_per_launch"], 1)) * (9 + 1)),
+        # per run: slot init, then per sweep launch of each of the two phases the work list, the
+        # sweep, the persistence pass (one cluster per start) and the loop-condition kernel
+        "gpu_launches": K * (1 + 2 * -(-1000 // max(shape["sweeps_per_launch"], 1)) * 4),
         "clocks": cs,
         "plain": {"value": plain_value, "speedup": value / world / plain_value},
         "peaks": dict(peaks.summary(), sm_mhz=clk_peak.summary()["sm_mhz"]),

@@ -453,7 +453,7 @@ int spvar_sample_range(const spvar_problem *p, int32_t sweep_begin, int32_t swee
         // one coupler magnitude per spin, or small integer couplers: the register
         // kernel's 16-bit-lane variants
         const int md = H.maxdeg <= 6 ? 6 : 8;
-        for (int blk : {256, 512, 1024}) {
+        for (int blk : {256, 512, 576, 1024}) {
             int ns = pm1_nslot(P, Q, blk);
             if (ns == 3) ns = 4;
             const SweepShape c{1, blk, Q, mode16, ns, md};

@@ -2,15 +2,21 @@
 // fixing rule), fold/compact (Alg. 1: update J and h) and the per-start state
 // machine of Multi-start SPVAR (Alg. 2).
 //
-// Elite selection sorts (energy, index) keys of one sample set in shared
-// memory; the count kernel reads only the k elite rows of the bit-packed
-// sample (one broadcast word load per warp and row); fold/compact runs one
-// 1024-thread CTA per reduction with block-wide scans, writing the new CSR,
-// the inherited colour classes and the sweep layout of the smaller problem.
+// Elite selection bounds the k lowest (energy, index) keys of one sample set
+// by a histogram and places the candidates by rank in shared memory; the
+// counts read only the k elite rows of the bit-packed sample, a lane per word,
+// into bit-sliced counters; fold/compact writes the new CSR, the inherited
+// colour classes and the sweep layout of the smaller problem.  In the
+// multi-start driver one thread-block cluster per start runs all of it in one
+// launch; the standalone entry points and the tree step use one CTA per call.
 #include <algorithm>
 #include <climits>
 
+#include <cooperative_groups.h>
+
 #include "persist.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace spvar {
 
@@ -270,7 +276,8 @@ __global__ void __launch_bounds__(kCountBlock)
                    int canon, int fix_num, int fix_den, int32_t *counts, int8_t *fixed,
                    int32_t *nfixed)
 {
-    count_bs_core(P, spins, W, elite, k, canon, fix_num, fix_den, counts, fixed, nfixed, nullptr, nullptr);
+    __shared__ CountSmem sm;
+    count_bs_core(P, spins, W, elite, k, canon, fix_num, fix_den, counts, fixed, nfixed, nullptr, nullptr, blockIdx.x, sm);
 }
 
 __global__ void __launch_bounds__(kBigBlock) k_reduce_single(const DevProb *src, DevProb *dst,
@@ -345,7 +352,7 @@ __device__ __forceinline__ int item_quads(const DevProb *P, const SolveConsts &C
 // per start, a lane per item.
 __global__ void __launch_bounds__(kBigBlock)
     k_plan(Slot *slots, SolveConsts C, SweepJob *jobs, WorkItem *items, int32_t *nitems,
-           int32_t *queue)
+           int32_t *queue, int32_t *nactive)
 {
     __shared__ int s_warp[32];
     __shared__ int s_off[kBigBlock], s_groups[kBigBlock], s_qn[kBigBlock], s_nquads[kBigBlock];
@@ -411,6 +418,7 @@ __global__ void __launch_bounds__(kBigBlock)
     if (threadIdx.x == 0) {
         *nitems = carry;
         *queue = 0;
+        if (nactive) *nactive = 0;  // the persistence pass counts the starts still active
     }
 }
 
@@ -454,6 +462,7 @@ __global__ void __launch_bounds__(kBigBlock) k_elite_slots(Slot *slots, SolveCon
 
 __global__ void __launch_bounds__(kCountBlock) k_count_slots(Slot *slots, SolveConsts C)
 {
+    __shared__ CountSmem sm;
     Slot &s = slots[blockIdx.y];
     if ((s.mode != kFixing && s.mode != kCorr) || !sample_complete(s, C)) return;
     const DevProb *P = s.cur;
@@ -462,13 +471,13 @@ __global__ void __launch_bounds__(kCountBlock) k_count_slots(Slot *slots, SolveC
         // correlation fixing: elite rows multiplied by their value at rho, then the
         // rule with the correlation threshold
         count_bs_core(P, s.spins, s.W0, s.elite, C.k_corr, 1, C.corr_num, C.corr_den, s.counts, s.fixed,
-                      &s.nfixed, s.fmap, s.orig[s.ocur]);
+                      &s.nfixed, s.fmap, s.orig[s.ocur], blockIdx.x, sm);
         return;
     }
     const int canon = (C.canon < 0) ? P->hzero : C.canon;
     const int k = C.pticm ? elite_count_hd(C.elite, s.rec_count[s.phase]) : C.k_fix;
     count_bs_core(P, s.spins, s.W0, s.elite, k, canon, C.fix_num, C.fix_den, s.counts, s.fixed, &s.nfixed, s.fmap,
-                  s.orig[s.ocur]);
+                  s.orig[s.ocur], blockIdx.x, sm);
 }
 
 // Stall rule, fold/compact into the spare buffer, and the phase transition.
@@ -537,57 +546,74 @@ __global__ void __launch_bounds__(kBigBlock) k_reduce_slots(Slot *slots, SolveCo
     }
 }
 
-// ------------------------------------------- multi-CTA fold/compact (Alg. 1)
-// Alg. 1's update of J and h for every slot whose fixing (or correlation)
-// phase sample is complete, spread over chunks of kFoldChunk spins so that all
-// SMs stream the CSRs:
-//   k_fold_prep    stall rule (ISPVAR) and the zeroed energy accumulator;
-//   k_fold_count   per spin: folded bias, free-free row length, energy of the
-//                  fixed spins; per chunk: the totals k_fold_index offsets by;
-//   k_fold_index   new indices, h', row pointers, inherited colours and sweep
-//                  positions (each chunk adds the totals of the chunks before
-//                  it), and the new header (chunk 0);
-//   k_fold_fill    CSR columns and values and the ELL layout of the free spins;
-//   k_fold_finish  phase transitions and the count of active slots.
-// The result is the one reduce_core computes: free spins keep their order,
-// couplers between free spins keep theirs, colour classes are inherited.
-constexpr int kFoldBlock = kFoldChunk;  // one spin per thread
+// ------------------------------------------- the persistence pass, fused (Alg. 1)
+// After a start's sample is complete, one thread-block cluster of
+// kPassCluster CTAs runs the whole of Alg. 1 for it in one launch:
+//   1. elite sample (every CTA selects it itself: a few thousand energies,
+//      read from L2, and the list is in its own shared memory with no
+//      barrier), and the start's best assignment;
+//   2. persistence counts and the fixing rule, 1024 spins per count chunk;
+//      each CTA also keeps its chunks' fixings in shared memory;
+//   3. the stall rule (ISPVAR), then the update of J and h spread over chunks
+//      of kFoldChunk spins:
+//        fold_count  per spin: folded bias, free-free row length, energy of
+//                    the fixed spins; per chunk: the totals fold_index offsets by;
+//        fold_index  new indices, h', row pointers, inherited colours and
+//                    sweep positions (each chunk adds the totals of the chunks
+//                    before it), and the new header (chunk 0); each CTA keeps
+//                    its chunks' (new index, position) pairs in shared memory;
+//        fold_fill   CSR columns and values and the ELL layout of the free spins;
+//   4. the phase transition and the count of active starts.
+// Chunks are dealt to the cluster's CTAs round-robin, and a cluster barrier
+// stands where one stage reads what another CTA wrote in the stage before.  A
+// neighbour's fixing and its new index and position are read from the shared
+// memory of the CTA that owns its chunk (distributed shared memory), not by a
+// chain of global loads.  The result is the one the per-start kernels (elite,
+// count_bs_core, reduce_core) compute: free spins keep their order, couplers
+// between free spins keep theirs, colour classes are inherited.
+constexpr int kPassCluster = 8;
+constexpr int kPassBlock = kFoldChunk;  // one spin per thread in a fold chunk
 constexpr int kFoldGather = 8;          // CSR entries a thread loads at once
+// count chunks (1024 spins) and fold chunks a CTA owns at most
+constexpr int kOwnCount = (SPVAR_MAX_N / 1024 + kPassCluster - 1) / kPassCluster;
+constexpr int kOwnFold = (kFoldMaxChunks + kPassCluster - 1) / kPassCluster;
+static_assert(kPassBlock == kCountBlock, "the count chunks run on the pass CTAs");
+static_assert(SPVAR_MAX_N <= 32768, "new index and position are packed in 16 bits each");
 
-__device__ __forceinline__ bool fold_active(const Slot &s, const SolveConsts &C)
+// Every global write of this CTA before the barrier is visible to the
+// cluster's other CTAs after it (shared memory writes are, by the barrier).
+__device__ __forceinline__ void pass_barrier()
 {
-    return (s.mode == kFixing || s.mode == kCorr) && sample_complete(s, C);
+    __threadfence();
+    cg::this_cluster().sync();
 }
 
-__global__ void __launch_bounds__(32) k_fold_prep(Slot *slots, SolveConsts C)
+// Fixing of spin j (count chunk j / 1024, owned by CTA (j / 1024) mod kPassCluster).
+__device__ __forceinline__ int fixed_in_cluster(const int8_t *s_fx, int j)
 {
-    Slot &s = slots[blockIdx.x];
-    if (!fold_active(s, C) || threadIdx.x != 0) return;
-    const DevProb *P = s.cur;
-    int32_t *tab = s.scratch + fold_table_offset(P->cap_n);
-    *reinterpret_cast<unsigned long long *>(tab + kFoldMaxChunks * kFoldStride) = 0ull;
-    if (s.mode == kFixing && C.iterate && s.nfixed == 0 && P->n > 0) {
-        // nothing fixed: fix the lowest-index spin to its value in the best
-        // elite sample so that every SPVAR phase makes progress
-        const uint32_t w = s.spins[(size_t)s.elite[0] * s.W0];
-        const int8_t v = (w & 1u) ? 1 : -1;
-        s.fixed[0] = v;
-        s.fmap[s.orig[s.ocur][0]] = v;
-    }
+    const int c = j >> 10;
+    const int8_t *p = cg::this_cluster().map_shared_rank(s_fx, (unsigned)(c % kPassCluster));
+    return p[(c / kPassCluster) * 1024 + (j & 1023)];
 }
 
-__global__ void __launch_bounds__(kFoldBlock) k_fold_count(Slot *slots, SolveConsts C)
+// New index | position << 16 of spin j, or ~0 if j is fixed (fold chunk j / kFoldChunk).
+__device__ __forceinline__ uint32_t npos_in_cluster(const uint32_t *s_npos, int j)
+{
+    const int c = j / kFoldChunk;
+    const uint32_t *p = cg::this_cluster().map_shared_rank(s_npos, (unsigned)(c % kPassCluster));
+    return p[(c / kPassCluster) * kFoldChunk + (j % kFoldChunk)];
+}
+
+__device__ __forceinline__ void fold_count(Slot &s, int chunk, const int8_t *s_fx)
 {
     __shared__ int s_cls[kMaxColours];
     __shared__ int s_free, s_nnz, s_hnz;
     __shared__ unsigned long long s_key, s_off;
-    Slot &s = slots[blockIdx.y];
-    if (!fold_active(s, C)) return;
     const DevProb *P = s.cur;
     const int n = P->n, cap = P->cap_n, tid = threadIdx.x;
-    const int i0 = blockIdx.x * kFoldChunk;
+    const int i0 = chunk * kFoldChunk;
     if (i0 >= n) return;
-    for (int c = tid; c < kMaxColours; c += kFoldBlock) s_cls[c] = 0;
+    for (int c = tid; c < kMaxColours; c += kPassBlock) s_cls[c] = 0;
     if (tid == 0) {
         s_free = s_nnz = s_hnz = 0;
         s_key = 0ull;
@@ -595,13 +621,12 @@ __global__ void __launch_bounds__(kFoldBlock) k_fold_count(Slot *slots, SolveCon
     }
     __syncthreads();
     int32_t *rowcnt = s.scratch + cap, *hfold = s.scratch + 2 * cap;
-    const int8_t *fx = s.fixed;
     long long off = 0;
     int nfree = 0, nnz = 0, hnz = 0, col = -1;
     unsigned long long key = 0ull;
     const int i = i0 + tid;
     if (i < n) {
-        const int vi = fx[i];
+        const int vi = fixed_in_cluster(s_fx, i);
         long long hf = P->h[i];
         int nf = 0;
         const int p0 = P->row_ptr[i], p1 = P->row_ptr[i + 1];
@@ -615,7 +640,7 @@ __global__ void __launch_bounds__(kFoldBlock) k_fold_count(Slot *slots, SolveCon
                 vv[d] = in ? P->val[pb + d] : 0;
             }
 #pragma unroll
-            for (int d = 0; d < kFoldGather; ++d) fj[d] = jj[d] >= 0 ? fx[jj[d]] : 0;
+            for (int d = 0; d < kFoldGather; ++d) fj[d] = jj[d] >= 0 ? fixed_in_cluster(s_fx, jj[d]) : 0;
 #pragma unroll
             for (int d = 0; d < kFoldGather; ++d) {
                 if (jj[d] < 0) continue;
@@ -663,7 +688,7 @@ __global__ void __launch_bounds__(kFoldBlock) k_fold_count(Slot *slots, SolveCon
     }
     __syncthreads();
     int32_t *tab = s.scratch + fold_table_offset(cap);
-    int32_t *e = tab + blockIdx.x * kFoldStride;
+    int32_t *e = tab + chunk * kFoldStride;
     if (tid == 0) {
         e[0] = s_free;
         e[1] = s_nnz;
@@ -672,20 +697,19 @@ __global__ void __launch_bounds__(kFoldBlock) k_fold_count(Slot *slots, SolveCon
         e[4] = (int32_t)(s_key & 0xFFFFFFFFull);
         atomicAdd(reinterpret_cast<unsigned long long *>(tab + kFoldMaxChunks * kFoldStride), s_off);
     }
-    for (int c = tid; c < P->ncol; c += kFoldBlock) e[6 + c] = s_cls[c];
+    for (int c = tid; c < P->ncol; c += kPassBlock) e[6 + c] = s_cls[c];
+    __syncthreads();  // the shared totals are reset by this CTA's next chunk
 }
 
-__global__ void __launch_bounds__(kFoldBlock) k_fold_index(Slot *slots, SolveConsts C)
+__device__ __forceinline__ void fold_index(Slot &s, int chunk, const int8_t *s_fx, uint32_t *s_npos)
 {
     __shared__ int s_warp[32];
     __shared__ int s_base_cls[kMaxColours], s_tot_cls[kMaxColours], s_cptr[kMaxColours + 1];
     __shared__ int s_base[2], s_tot[2], s_hnz;
-    Slot &s = slots[blockIdx.y];
-    if (!fold_active(s, C)) return;
     const DevProb *P = s.cur;
     DevProb *D = s.buf[s.next];
     const int n = P->n, cap = P->cap_n, ncol = P->ncol, tid = threadIdx.x;
-    const int chunk = blockIdx.x, i0 = chunk * kFoldChunk;
+    const int i0 = chunk * kFoldChunk;
     if (chunk > 0 && i0 >= n) return;  // chunk 0 writes the header, even for n = 0
     const int nch = (n + kFoldChunk - 1) / kFoldChunk;
     const int32_t *tab = s.scratch + fold_table_offset(cap);
@@ -693,7 +717,7 @@ __global__ void __launch_bounds__(kFoldBlock) k_fold_index(Slot *slots, SolveCon
     // field f (0 free spins, 1 free-free entries, 2 + c spins of class c) summed by a warp
     {
         const int lane = tid & 31, warp = tid >> 5;
-        for (int f = warp; f < 3 + ncol; f += kFoldBlock / 32) {
+        for (int f = warp; f < 3 + ncol; f += kPassBlock / 32) {
             const int fo = f < 3 ? f : 6 + (f - 3);  // table column (2: nonzero-bias flag)
             int b = 0, t = 0;
             for (int q = lane; q < nch; q += 32) {
@@ -742,17 +766,14 @@ __global__ void __launch_bounds__(kFoldBlock) k_fold_index(Slot *slots, SolveCon
                     (long long)*reinterpret_cast<const unsigned long long *>(tab + kFoldMaxChunks * kFoldStride);
         D->row_ptr[m] = nnz2;
     }
-    if (i0 >= n) return;
-    const int8_t *fx = s.fixed;
-    int32_t *nofo = s.scratch;
-    const int32_t *rowcnt = s.scratch + cap, *hfold = s.scratch + 2 * cap;
-    const int32_t *orig = s.orig[s.ocur];
-    int32_t *orig2 = s.orig[s.ocur ^ 1];
-    const int carry_free = s_base[0], carry_nnz = s_base[1];
-    {
+    if (i0 < n) {
+        const int32_t *rowcnt = s.scratch + cap, *hfold = s.scratch + 2 * cap;
+        const int32_t *orig = s.orig[s.ocur];
+        int32_t *orig2 = s.orig[s.ocur ^ 1];
+        const int carry_free = s_base[0], carry_nnz = s_base[1];
         const int i = i0 + tid;
         const bool valid = i < n;
-        const bool f = valid && fx[i] == 0;
+        const bool f = valid && fixed_in_cluster(s_fx, i) == 0;
         const int rc = f ? rowcnt[i] : 0;
         const int col = f ? P->colour[i] : -1;
         int tf, tr;
@@ -765,11 +786,11 @@ __global__ void __launch_bounds__(kFoldBlock) k_fold_index(Slot *slots, SolveCon
             const int exc = block_scan_excl(col == c ? 1 : 0, s_warp, &tc);
             if (col == c) rank = s_base_cls[c] + exc;
         }
-        if (valid) nofo[i] = f ? carry_free + exf : -1;
+        const int a = carry_free + exf;
+        const int pos = f ? s_cptr[col] + rank : 0;
+        if (valid) s_npos[(chunk / kPassCluster) * kFoldChunk + tid] = f ? (uint32_t)a | ((uint32_t)pos << 16) : ~0u;
         if (f) {
-            const int a = carry_free + exf;
             const int h = hfold[i];
-            const int pos = s_cptr[col] + rank;
             s.old_of_new[a] = i;
             orig2[a] = orig[i];
             D->h[a] = h;
@@ -780,18 +801,16 @@ __global__ void __launch_bounds__(kFoldBlock) k_fold_index(Slot *slots, SolveCon
             D->meta[pos] = ((uint32_t)(h & 0xFFFF) << 16) | (uint32_t)rc;
         }
     }
+    __syncthreads();  // the shared offsets are rewritten by this CTA's next chunk
 }
 
-__global__ void __launch_bounds__(kFoldBlock) k_fold_fill(Slot *slots, SolveConsts C)
+__device__ __forceinline__ void fold_fill(Slot &s, int chunk, const uint32_t *s_npos)
 {
-    Slot &s = slots[blockIdx.y];
-    if (!fold_active(s, C)) return;
     const DevProb *P = s.cur;
     DevProb *D = s.buf[s.next];
     const int n = P->n, cap = P->cap_n, tid = threadIdx.x;
-    const int i0 = blockIdx.x * kFoldChunk;
-    const int32_t *nofo = s.scratch;
-    if (blockIdx.x == 0 && tid == 0) {
+    const int i0 = chunk * kFoldChunk;
+    if (chunk == 0 && tid == 0) {
         // the reference spin: the chunks' candidates, largest degree then lowest index
         const int32_t *tab = s.scratch + fold_table_offset(cap);
         unsigned long long best = 0ull;
@@ -803,20 +822,20 @@ __global__ void __launch_bounds__(kFoldBlock) k_fold_fill(Slot *slots, SolveCons
             best = max(best, k);
             any = true;
         }
-        D->rho = any ? nofo[0x7FFFFFFF - (int)(best & 0xFFFFFFFFull)] : -1;
+        D->rho = any ? (int)(npos_in_cluster(s_npos, 0x7FFFFFFF - (int)(best & 0xFFFFFFFFull)) & 0xFFFFu) : -1;
     }
     if (i0 >= n) return;
-    const int8_t *fx = s.fixed;
     const int i = i0 + tid;
-    if (i < n && fx[i] == 0) {
-        const int a = nofo[i];
+    const uint32_t own = i < n ? s_npos[(chunk / kPassCluster) * kFoldChunk + tid] : ~0u;
+    if (own != ~0u) {
+        const int a = (int)(own & 0xFFFFu), pos = (int)(own >> 16);
         const int p0 = P->row_ptr[i], p1 = P->row_ptr[i + 1];
         int q = D->row_ptr[a];
-        const int pos = D->pos_of_idx[a];
         int d = 0;
         for (int pb = p0; pb < p1; pb += kFoldGather) {
             // the row's entries in batches: each dependent step loads for the whole batch
-            int jj[kFoldGather], vv[kFoldGather], bb[kFoldGather], pp[kFoldGather];
+            int jj[kFoldGather], vv[kFoldGather];
+            uint32_t np[kFoldGather];
 #pragma unroll
             for (int e = 0; e < kFoldGather; ++e) {
                 const bool in = pb + e < p1;
@@ -824,17 +843,14 @@ __global__ void __launch_bounds__(kFoldBlock) k_fold_fill(Slot *slots, SolveCons
                 vv[e] = in ? P->val[pb + e] : 0;
             }
 #pragma unroll
-            for (int e = 0; e < kFoldGather; ++e) bb[e] = (jj[e] >= 0 && fx[jj[e]] == 0) ? 1 : -1;
-#pragma unroll
-            for (int e = 0; e < kFoldGather; ++e) bb[e] = bb[e] > 0 ? nofo[jj[e]] : -1;
-#pragma unroll
-            for (int e = 0; e < kFoldGather; ++e) pp[e] = bb[e] >= 0 ? D->pos_of_idx[bb[e]] : 0;
+            for (int e = 0; e < kFoldGather; ++e) np[e] = jj[e] >= 0 ? npos_in_cluster(s_npos, jj[e]) : ~0u;
 #pragma unroll
             for (int e = 0; e < kFoldGather; ++e) {
-                if (bb[e] < 0) continue;
-                D->col[q] = bb[e];
+                if (np[e] == ~0u) continue;
+                const uint32_t b = np[e] & 0xFFFFu, pp = np[e] >> 16;
+                D->col[q] = (int32_t)b;
                 D->val[q] = vv[e];
-                D->ell[(size_t)d * cap + pos] = ((uint32_t)pp[e] & 0xFFFFu) | ((uint32_t)(vv[e] & 0xFFFF) << 16);
+                D->ell[(size_t)d * cap + pos] = pp | ((uint32_t)(vv[e] & 0xFFFF) << 16);
                 ++q;
                 ++d;
             }
@@ -842,42 +858,127 @@ __global__ void __launch_bounds__(kFoldBlock) k_fold_fill(Slot *slots, SolveCons
     }
 }
 
-// Phase transitions after the multi-CTA fold/compact, then the active count.
-__global__ void __launch_bounds__(256) k_fold_finish(Slot *slots, SolveConsts C, int32_t *nactive)
+// Dynamic shared memory of the pass: the elite list (Smax entries), then one
+// region that holds in turn the elite's keys, a count chunk's counters and the
+// CTA's (new index, position) pairs.
+__host__ __device__ inline size_t pass_list_bytes(int Smax) { return ((size_t)Smax * 4 + 15) & ~(size_t)15; }
+__host__ __device__ inline size_t pass_smem(int Smax)
 {
-    __shared__ int s_n;
-    if (threadIdx.x == 0) s_n = 0;
-    __syncthreads();
-    int act = 0;
-    for (int si = threadIdx.x; si < C.nslots; si += blockDim.x) {
-        Slot &s = slots[si];
-        const int mode = s.mode;
-        if (mode != kDone && sample_complete(s, C)) {
-            if (mode == kSolving) {
-                s.mode = kDone;
-            } else {
-                DevProb *D = s.buf[s.next];
-                const int m = D->n;
-                s.cur = D;
-                s.next ^= 1;
-                s.ocur ^= 1;
-                if (mode == kCorr) {
-                    s.mode = kFixing;  // the SPVAR phases follow the correlation phase
-                } else {
-                    s.fix_done += 1;
-                    if (C.iterate && m > 0 && s.fix_done < C.max_fix) s.mode = kFixing;
-                    else s.mode = (C.S_solve > 0) ? kSolving : kDone;
-                }
-            }
-            s.phase += 1;
-            s.tsw = 0;
-            *s.nphases = s.phase;
-        }
-        act += s.mode != kDone;
+    size_t u = (size_t)elite_key_words(Smax) * 8;
+    if (u < sizeof(CountSmem)) u = sizeof(CountSmem);
+    if (u < (size_t)kOwnFold * kFoldChunk * 4) u = (size_t)kOwnFold * kFoldChunk * 4;
+    return pass_list_bytes(Smax) + u;
+}
+
+// The grid is kPassCluster x nslots with one cluster per row, so blockIdx.x
+// is the CTA's rank in its cluster and every CTA of a cluster reads the same
+// slot.  The slot's state is read by every CTA before the first barrier and
+// changed only by rank 0 after the last one, so all CTAs of a cluster take
+// the same path through the barriers, and none leaves while another may
+// still read its shared memory.
+__global__ void __cluster_dims__(kPassCluster, 1, 1) __launch_bounds__(kPassBlock)
+    k_pass_slots(Slot *slots, SolveConsts C, int32_t *nactive)
+{
+    extern __shared__ __align__(16) unsigned long long s_dyn[];
+    __shared__ __align__(16) int8_t s_fx[kOwnCount * 1024];
+    Slot &s = slots[blockIdx.y];
+    const int rank = blockIdx.x, tid = threadIdx.x;
+    const int mode = s.mode;
+    if (mode == kDone || !sample_complete(s, C)) {
+        // a start whose sample is still running stays active
+        if (nactive && mode != kDone && rank == 0 && tid == 0) atomicAdd(nactive, 1);
+        return;
     }
-    atomicAdd(&s_n, act);
-    __syncthreads();
-    if (threadIdx.x == 0 && nactive) *nactive = s_n;
+    int32_t *s_elite = reinterpret_cast<int32_t *>(s_dyn);
+    unsigned char *s_reg = reinterpret_cast<unsigned char *>(s_dyn) + pass_list_bytes(C.Smax);
+    // 1. elite sample (PTICM: of the states its run kept) and the best assignment
+    const int S = C.pticm ? s.rec_count[s.phase] : phase_samples(C, mode);
+    const int k = (mode == kFixing) ? (C.pticm ? elite_count_hd(C.elite, S) : C.k_fix)
+                  : (mode == kCorr) ? C.k_corr : 1;
+    const int64_t *e = s.rec_e + (size_t)s.phase * C.Smax;
+    elite_fast(e, S, k, s_elite, reinterpret_cast<unsigned long long *>(s_reg));
+    const DevProb *P = s.cur;
+    const int n = P->n;
+    const int32_t *orig = s.orig[s.ocur];
+    const int rbest = s_elite[0];
+    const int64_t eb = e[rbest];
+    const bool better = eb < *s.best_e;  // every CTA reads it before rank 0 may change it
+    constexpr int kStride = kPassCluster * kPassBlock;
+    if (better) {
+        // spins fixed in earlier phases, before this phase adds its fixings to fmap
+        for (int o = rank * kPassBlock + tid; o < s.n0; o += kStride) {
+            const int8_t v = s.fmap[o];
+            if (v) s.best_state[o] = v;
+        }
+    }
+    if (rank == 0) {
+        for (int q = tid; q < k; q += kPassBlock) s.elite[q] = s_elite[q];
+        if (tid == 0 && mode != kSolving)
+            *reinterpret_cast<unsigned long long *>(s.scratch + fold_table_offset(P->cap_n) +
+                                                    kFoldMaxChunks * kFoldStride) = 0ull;
+    }
+    pass_barrier();
+    if (better) {
+        if (rank == 0 && tid == 0) *s.best_e = eb;
+        const uint32_t *row = s.spins + (size_t)rbest * s.W0;
+        for (int a = rank * kPassBlock + tid; a < n; a += kStride)
+            s.best_state[orig[a]] = ((row[a >> 5] >> (a & 31)) & 1u) ? 1 : -1;
+    }
+    if (mode == kSolving) {
+        if (rank == 0 && tid == 0) {
+            s.phase += 1;
+            *s.nphases = s.phase;
+            s.mode = kDone;
+            s.tsw = 0;
+        }
+        return;
+    }
+    // 2. counts and the fixing rule (correlation fixing: rows times their value at rho)
+    const bool corr = mode == kCorr;
+    const int canon = corr ? 1 : (C.canon < 0 ? P->hzero : C.canon);
+    for (int c = rank; c * 1024 < n; c += kPassCluster)
+        count_bs_core(P, s.spins, s.W0, s_elite, k, canon, corr ? C.corr_num : C.fix_num,
+                      corr ? C.corr_den : C.fix_den, s.counts, s.fixed, &s.nfixed, s.fmap, orig, c,
+                      *reinterpret_cast<CountSmem *>(s_reg), s_fx + (c / kPassCluster) * 1024);
+    pass_barrier();
+    // 3. stall rule: nothing fixed in an ISPVAR phase fixes the lowest-index spin
+    //    to its value in the best elite sample, so that every phase makes progress
+    if (mode == kFixing && C.iterate && s.nfixed == 0 && n > 0) {
+        if (rank == 0 && tid == 0) {
+            const int8_t v = (s.spins[(size_t)s_elite[0] * s.W0] & 1u) ? 1 : -1;
+            s.fixed[0] = v;
+            s.fmap[orig[0]] = v;
+            s_fx[0] = v;  // spin 0 is in this CTA's first count chunk
+        }
+        pass_barrier();
+    }
+    uint32_t *s_npos = reinterpret_cast<uint32_t *>(s_reg);  // the count's counters are dead
+    const int nch = max(1, (n + kFoldChunk - 1) / kFoldChunk);
+    for (int c = rank; c < nch; c += kPassCluster) fold_count(s, c, s_fx);
+    pass_barrier();
+    for (int c = rank; c < nch; c += kPassCluster) fold_index(s, c, s_fx, s_npos);
+    pass_barrier();
+    for (int c = rank; c < nch; c += kPassCluster) fold_fill(s, c, s_npos);
+    pass_barrier();
+    // 4. the phase transition
+    if (rank == 0 && tid == 0) {
+        DevProb *D = s.buf[s.next];
+        const int m = D->n;
+        s.cur = D;
+        s.next ^= 1;
+        s.ocur ^= 1;
+        if (corr) {
+            s.mode = kFixing;  // the SPVAR phases follow the correlation phase
+        } else {
+            s.fix_done += 1;
+            if (C.iterate && m > 0 && s.fix_done < C.max_fix) s.mode = kFixing;
+            else s.mode = (C.S_solve > 0) ? kSolving : kDone;
+        }
+        s.phase += 1;
+        s.tsw = 0;
+        *s.nphases = s.phase;
+        if (nactive && s.mode != kDone) atomicAdd(nactive, 1);
+    }
 }
 
 __global__ void k_count_active(const Slot *slots, int nslots, int32_t *nactive)
@@ -1049,12 +1150,8 @@ __global__ void k_gather_modes(const Slot *slots, int nslots, int32_t *modes)
         modes[i] = slots[i].mode;
 }
 
-size_t elite_smem(int S)
-{
-    int N2 = 1;
-    while (N2 < S) N2 <<= 1;
-    return (size_t)N2 * 8;
-}
+size_t elite_smem(int S) { return (size_t)elite_key_words(S) * 8; }
+
 
 }  // namespace
 
@@ -1117,9 +1214,9 @@ cudaError_t launch_slots_init(Slot *slots, const SolveConsts &C, int, cudaStream
 }
 
 cudaError_t launch_plan(Slot *slots, const SolveConsts &C, SweepJob *jobs, WorkItem *items,
-                        int32_t *nitems, int32_t *queue, cudaStream_t st)
+                        int32_t *nitems, int32_t *queue, int32_t *nactive, cudaStream_t st)
 {
-    k_plan<<<1, kBigBlock, 0, st>>>(slots, C, jobs, items, nitems, queue);
+    k_plan<<<1, kBigBlock, 0, st>>>(slots, C, jobs, items, nitems, queue, nactive);
     return cudaGetLastError();
 }
 
@@ -1139,15 +1236,14 @@ cudaError_t launch_count_slots(Slot *slots, const SolveConsts &C, int max_n0, cu
     return cudaGetLastError();
 }
 
-cudaError_t launch_fold_slots(Slot *slots, const SolveConsts &C, int max_n0, int32_t *nactive, cudaStream_t st)
+cudaError_t launch_pass_slots(Slot *slots, const SolveConsts &C, int32_t *nactive, cudaStream_t st)
 {
     if (C.nslots <= 0) return cudaSuccess;
-    const dim3 grid(std::max(1, ceil_div(max_n0, kFoldChunk)), C.nslots);
-    k_fold_prep<<<C.nslots, 32, 0, st>>>(slots, C);
-    k_fold_count<<<grid, kFoldBlock, 0, st>>>(slots, C);
-    k_fold_index<<<grid, kFoldBlock, 0, st>>>(slots, C);
-    k_fold_fill<<<grid, kFoldBlock, 0, st>>>(slots, C);
-    k_fold_finish<<<1, 256, 0, st>>>(slots, C, nactive);
+    const size_t smem = pass_smem(C.Smax);
+    cudaError_t e = cudaFuncSetAttribute(k_pass_slots, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    // the kernel's cluster shape (kPassCluster x 1 x 1) makes each grid row one cluster
+    k_pass_slots<<<dim3(kPassCluster, C.nslots), kPassBlock, smem, st>>>(slots, C, nactive);
     return cudaGetLastError();
 }
 

@@ -90,6 +90,14 @@ __device__ __forceinline__ void elite_core(const int64_t *energies, int S, int k
 // index).  k = 1 is a block-wide arg-min.  More than kEliteRankMax candidates
 // (a crowded bin) fall back to elite_core.  blockDim.x == kBigBlock; s_key as
 // for elite_core.
+// Keys of elite_core's sort: the next power of two of S.
+__host__ __device__ inline int elite_key_words(int S)
+{
+    int N2 = 1;
+    while (N2 < S) N2 <<= 1;
+    return N2;
+}
+
 constexpr int kEliteBins = 1024;
 constexpr int kEliteRankMax = 512;
 __device__ __forceinline__ void elite_fast(const int64_t *energies, int S, int k, int32_t *elite,
@@ -141,18 +149,22 @@ __device__ __forceinline__ void elite_fast(const int64_t *energies, int S, int k
     while (((unsigned long long)(s_max - emin) >> shift) >= (unsigned long long)kEliteBins) ++shift;
     for (int r = tid; r < S; r += B) atomicAdd(&s_hist[(int)((unsigned long long)(energies[r] - emin) >> shift)], 1);
     __syncthreads();
-    // the bin holding the k-th lowest key: keys in bins below it number < k, with it >= k
-    int carry = 0;
-    for (int b0 = 0; b0 < kEliteBins; b0 += B) {
-        const int b = b0 + tid;
-        const int h = b < kEliteBins ? s_hist[b] : 0;
+    // the bin holding the k-th lowest key (keys in bins below it number < k, with
+    // it >= k): each thread scans a run of consecutive bins after one block scan
+    {
+        const int per = (kEliteBins + B - 1) / B, b0 = tid * per;
+        int h = 0;
+        for (int b = b0; b < b0 + per && b < kEliteBins; ++b) h += s_hist[b];
         int tot;
-        const int ex = block_scan_excl(h, s_warp, &tot);
-        if (b < kEliteBins && carry + ex < k && carry + ex + h >= k) {
-            s_bin = b;
-            s_cand = carry + ex + h;
+        int below = block_scan_excl(h, s_warp, &tot);
+        for (int b = b0; b < b0 + per && b < kEliteBins; ++b) {
+            const int hb = s_hist[b];
+            if (below < k && below + hb >= k) {
+                s_bin = b;
+                s_cand = below + hb;
+            }
+            below += hb;
         }
-        carry += tot;
     }
     __syncthreads();
     const int bstar = s_bin, C = s_cand;
@@ -160,21 +172,18 @@ __device__ __forceinline__ void elite_fast(const int64_t *energies, int S, int k
         elite_core(energies, S, k, elite, s_key);
         return;
     }
-    // candidates in index order
-    carry = 0;
-    for (int r0 = 0; r0 < S; r0 += B) {
-        const int r = r0 + tid;
-        unsigned long long key = 0ull;
-        bool f = false;
-        if (r < S) {
-            const unsigned long long d = (unsigned long long)(energies[r] - emin);
-            f = (int)(d >> shift) <= bstar;
-            key = (d << 32) | (unsigned)r;
-        }
+    // candidates in index order: each thread takes a run of consecutive samples
+    {
+        const int per = (S + B - 1) / B, r0 = tid * per;
+        int f = 0;
+        for (int r = r0; r < r0 + per && r < S; ++r)
+            f += (int)((unsigned long long)(energies[r] - emin) >> shift) <= bstar;
         int tot;
-        const int ex = block_scan_excl(f ? 1 : 0, s_warp, &tot);
-        if (f) s_key[carry + ex] = key;
-        carry += tot;
+        int o = block_scan_excl(f, s_warp, &tot);
+        for (int r = r0; r < r0 + per && r < S; ++r) {
+            const unsigned long long d = (unsigned long long)(energies[r] - emin);
+            if ((int)(d >> shift) <= bstar) s_key[o++] = (d << 32) | (unsigned)r;
+        }
     }
     __syncthreads();
     for (int c = tid; c < C; c += B) {
@@ -235,24 +244,33 @@ __device__ __forceinline__ void count_core(const DevProb *P, const uint32_t *spi
 }
 
 // Persistence count and fixing rule, bit-sliced: one CTA of kCountBlock
-// threads covers 32 words (1024 spins) of the sample rows.  Lane l of every
-// warp owns word 32 blockIdx.x + l; the k elite rows are split over the 8
+// threads covers 32 words (1024 spins, chunk `chunk`) of the sample rows.
+// Lane l of every warp owns word 32 chunk + l; the k elite rows are split over the 8
 // warps, and each lane adds its rows' words (each multiplied by its value at
 // rho when canon is set) into NB bit planes: plane b holds bit b of the
 // running count of every spin of the word (a vertical counter, two logic
 // operations per plane and row).  The warps' counters are then summed by a
 // bit-sliced ripple adder and each spin's count read off its planes.
 // Results as count_core.  NB: planes per warp (2^NB > rows per warp).
+// fixed_copy (optional, shared memory): the chunk's 1024 fixings (0 past n).
 constexpr int kCountWarps = kCountBlock / 32;
 constexpr int kCountPlanes = 12;  // 2^12 > 16384 / kCountWarps rows per warp
+// Shared memory of one count chunk (callers place it, so the multi-start pass
+// can overlay it on buffers of other steps).
+struct CountSmem {
+    uint32_t planes[kCountWarps][kCountPlanes + 3][32];
+    uint32_t tot[kCountPlanes + 3][32];
+    int row[1024];
+    uint32_t flip[1024];
+};
 template <int NB>
 __device__ __forceinline__ void count_planes(const uint32_t *spins, int W, const int32_t *elite, int k,
                                              int canon, int rho, uint32_t (*s_planes)[kCountPlanes + 3][32],
-                                             int *s_row, uint32_t *s_flip)
+                                             int *s_row, uint32_t *s_flip, int chunk)
 {
     constexpr int kChunk = 1024;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int word = blockIdx.x * 32 + lane;
+    const int word = chunk * 32 + lane;
     uint32_t c[NB];
 #pragma unroll
     for (int b = 0; b < NB; ++b) c[b] = 0u;
@@ -267,7 +285,7 @@ __device__ __forceinline__ void count_planes(const uint32_t *spins, int W, const
         }
         __syncthreads();
         if (word < W) {
-#pragma unroll 4
+#pragma unroll 8
             for (int q = warp; q < m; q += kCountWarps) {
                 uint32_t carry = spins[(size_t)s_row[q] * W + word] ^ s_flip[q];
 #pragma unroll
@@ -286,20 +304,21 @@ __device__ __forceinline__ void count_planes(const uint32_t *spins, int W, const
 
 __device__ __forceinline__ void count_bs_core(const DevProb *P, const uint32_t *spins, int W, const int32_t *elite,
                                               int k, int canon, int fix_num, int fix_den, int32_t *counts,
-                                              int8_t *fixed, int32_t *nfixed, int8_t *fmap, const int32_t *orig)
+                                              int8_t *fixed, int32_t *nfixed, int8_t *fmap, const int32_t *orig,
+                                              int chunk, CountSmem &sm, int8_t *fixed_copy = nullptr)
 {
-    __shared__ uint32_t s_planes[kCountWarps][kCountPlanes + 3][32];
-    __shared__ uint32_t s_tot[kCountPlanes + 3][32];
-    __shared__ int s_row[1024];
-    __shared__ uint32_t s_flip[1024];
+    uint32_t(*s_planes)[kCountPlanes + 3][32] = sm.planes;
+    uint32_t(*s_tot)[32] = sm.tot;
+    int *s_row = sm.row;
+    uint32_t *s_flip = sm.flip;
     const int n = P->n, rho = P->rho;
     const int per_warp = (k + kCountWarps - 1) / kCountWarps;
     const int NB = per_warp < 16 ? 4 : per_warp < 64 ? 6 : per_warp < 256 ? 8 : per_warp < 1024 ? 10 : 12;
-    if (NB == 4) count_planes<4>(spins, W, elite, k, canon, rho, s_planes, s_row, s_flip);
-    else if (NB == 6) count_planes<6>(spins, W, elite, k, canon, rho, s_planes, s_row, s_flip);
-    else if (NB == 8) count_planes<8>(spins, W, elite, k, canon, rho, s_planes, s_row, s_flip);
-    else if (NB == 10) count_planes<10>(spins, W, elite, k, canon, rho, s_planes, s_row, s_flip);
-    else count_planes<12>(spins, W, elite, k, canon, rho, s_planes, s_row, s_flip);
+    if (NB == 4) count_planes<4>(spins, W, elite, k, canon, rho, s_planes, s_row, s_flip, chunk);
+    else if (NB == 6) count_planes<6>(spins, W, elite, k, canon, rho, s_planes, s_row, s_flip, chunk);
+    else if (NB == 8) count_planes<8>(spins, W, elite, k, canon, rho, s_planes, s_row, s_flip, chunk);
+    else if (NB == 10) count_planes<10>(spins, W, elite, k, canon, rho, s_planes, s_row, s_flip, chunk);
+    else count_planes<12>(spins, W, elite, k, canon, rho, s_planes, s_row, s_flip, chunk);
     __syncthreads();
     const int NT = NB + 3;  // the sum of 8 counters below 2^NB is below 2^(NB + 3)
     if (threadIdx.x < 32) {
@@ -324,7 +343,7 @@ __device__ __forceinline__ void count_bs_core(const DevProb *P, const uint32_t *
     }
     __syncthreads();
     for (int sp = threadIdx.x; sp < 1024; sp += blockDim.x) {
-        const int i = blockIdx.x * 1024 + sp;
+        const int i = chunk * 1024 + sp;
         const int wl = sp >> 5, bit = sp & 31;
         int8_t v = 0;
         if (i < n) {
@@ -337,6 +356,7 @@ __device__ __forceinline__ void count_bs_core(const DevProb *P, const uint32_t *
             fixed[i] = v;
             if (v && fmap) fmap[orig[i]] = v;
         }
+        if (fixed_copy) fixed_copy[sp] = v;  // the chunk's fixings, also in shared memory
         const unsigned ball = __ballot_sync(0xFFFFFFFFu, v != 0);
         if ((threadIdx.x & 31) == 0 && ball) atomicAdd(nfixed, __popc(ball));
     }

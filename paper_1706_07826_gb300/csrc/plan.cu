@@ -41,7 +41,7 @@ cudaError_t engine_phase(const PhaseEngine &E, Slot *slots, int nslots, int T, i
     C.fit_words = E.shape.kind == 6 ? 2 * E.shape.Q * (E.max_n0 + 1) : 0;
     C.grid = grid;
     C.T = T;
-    cudaError_t e = launch_plan(slots, C, E.jobs, E.items, E.ctr + 0, E.ctr + 1, st);
+    cudaError_t e = launch_plan(slots, C, E.jobs, E.items, E.ctr + 0, E.ctr + 1, E.ctr + 2, st);
     if (e != cudaSuccess) return e;
     SweepLaunch L;
     std::memset(&L, 0, sizeof(L));
@@ -67,11 +67,16 @@ cudaError_t engine_phase(const PhaseEngine &E, Slot *slots, int nslots, int T, i
     if (e != cudaSuccess) return e;
     if (E.ev_sweep[1] && (e = record(E.ev_sweep[1])) != cudaSuccess) return e;
     if ((e = launch_boost(slots, C, st)) != cudaSuccess) return e;
-    if ((e = launch_elite_slots(slots, C, st)) != cudaSuccess) return e;
-    if ((e = launch_count_slots(slots, C, E.max_n0, st)) != cudaSuccess) return e;
-    // fold/compact: spread over chunks of spins, or one CTA per start when the tree step follows
-    e = C.tree ? launch_reduce_slots(slots, C, count_active ? E.ctr + 2 : nullptr, st)
-               : launch_fold_slots(slots, C, E.max_n0, count_active ? E.ctr + 2 : nullptr, st);
+    int32_t *nactive = count_active ? E.ctr + 2 : nullptr;
+    if (C.tree) {
+        // one CTA per start for each step, the tree step after the fold/compact
+        if ((e = launch_elite_slots(slots, C, st)) != cudaSuccess) return e;
+        if ((e = launch_count_slots(slots, C, E.max_n0, st)) != cudaSuccess) return e;
+        e = launch_reduce_slots(slots, C, nactive, st);
+    } else {
+        // the whole pass in one launch, one thread-block cluster per start
+        e = launch_pass_slots(slots, C, nactive, st);
+    }
     if (e != cudaSuccess) return e;
     // end of the persistence pass (boosting, elite, counts and fixing, fold/compact)
     if (E.ev_post && (e = record(E.ev_post)) != cudaSuccess) return e;
@@ -386,7 +391,7 @@ std::vector<SweepShape> candidate_shapes(const spvar_plan *pl, int optin)
         // one coupler magnitude per spin, or small integer couplers: the register
         // kernel's 16-bit-lane variants
         const int md = pl->max_deg <= 6 ? 6 : 8;
-        for (int blk : {128, 256, 512, 1024})
+        for (int blk : {128, 256, 512, 576, 1024})
             for (int Q : {1, 2, 4}) {
                 if (Q > 1 && quads < Q) continue;
                 int ns = plan_nslot(pl, Q, blk);
@@ -521,7 +526,9 @@ int spvar_plan_create(const spvar_problem *const *problems, int32_t nproblems,
         p.canon < -1 || p.canon > 1 || (p.form != SPVAR_FORM_BATCHED && p.form != SPVAR_FORM_PLAIN) ||
         p.replicas_per_block < 0 || (p.replicas_per_block % 4) != 0 || p.sweep_kernel < 0 ||
         p.sweep_kernel > 5 || p.start_offset < 0 || p.component_boost < 0 || p.component_boost > 1 || p.tree_preprocess < 0 || p.tree_preprocess > 1 || (p.sweep_block != 0 && p.sweep_block != 128 && p.sweep_block != 256 &&
-                               p.sweep_block != 512 && p.sweep_block != 1024) ||
+                               p.sweep_block != 512 && p.sweep_block != 1024 &&
+                               !(p.sweep_block == 576 && p.sweep_kernel == SPVAR_SWEEP_PM1 &&
+                                 p.sampler == SPVAR_SAMPLER_SA)) ||
         check_corr_params(p) != SPVAR_OK || check_sampler_params(p) != SPVAR_OK || p.sweeps_per_launch < 0 ||
         (p.sampler != SPVAR_SAMPLER_SA && p.sweeps_per_launch != 0))
         return SPVAR_EINVAL;
@@ -809,6 +816,10 @@ int spvar_plan_create(const spvar_problem *const *problems, int32_t nproblems,
                 sh = cu;
             else if (elig && pm1s_shape_ok(blk, md, pl->max_n0, Q)) sh = SweepShape{2, blk, Q, 0, 0, md};
             else { plan_free(pl); return SPVAR_ELIMIT; }
+            if (blk == 576 && (sh.kind != 1 || sh.stage == 0)) {  // the 16-bit-lane register kernel only
+                plan_free(pl);
+                return SPVAR_ELIMIT;
+            }
         } else if (p.sweep_kernel == SPVAR_SWEEP_PM1Q) {
             const int md = pl->max_deg <= 6 ? 6 : 8;
             if (!pm1r_kernel_eligible(pl->pm1, pl->dmax, pl->max_deg) || !pm1q_shape_ok(blk, md, pl->max_n0, Q)) {

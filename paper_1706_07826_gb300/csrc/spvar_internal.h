@@ -294,16 +294,21 @@ inline size_t slot_scratch_ints(int cap_n)
 __host__ __device__ inline size_t fold_table_offset(int cap_n) { return (3 * (size_t)cap_n + 1) & ~(size_t)1; }
 
 cudaError_t launch_slots_init(Slot *slots, const SolveConsts &C, int max_n0, cudaStream_t st);
+// Work list of the phase's sweep launch; also zeroes *nactive (if not null),
+// which the persistence pass then counts up.
 cudaError_t launch_plan(Slot *slots, const SolveConsts &C, SweepJob *jobs, WorkItem *items,
-                        int32_t *nitems, int32_t *queue, cudaStream_t st);
+                        int32_t *nitems, int32_t *queue, int32_t *nactive, cudaStream_t st);
+// Tree pre-processing on: elite, counts, then fold/compact and the tree step,
+// one CTA per slot (nactive != null: the count of slots still active).
 cudaError_t launch_elite_slots(Slot *slots, const SolveConsts &C, cudaStream_t st);
 cudaError_t launch_count_slots(Slot *slots, const SolveConsts &C, int max_n0, cudaStream_t st);
-// Fold/compact of every slot whose phase sample is complete, spread over
-// chunks of its spins (tree pre-processing off), then the phase transitions and
-// (nactive != null) the count of slots still active.
-cudaError_t launch_fold_slots(Slot *slots, const SolveConsts &C, int max_n0, int32_t *nactive, cudaStream_t st);
 cudaError_t launch_reduce_slots(Slot *slots, const SolveConsts &C, int32_t *nactive,
                                 cudaStream_t st);
+// Tree pre-processing off: the whole persistence pass (elite, best state,
+// counts and fixing, fold/compact, phase transition) of every slot whose phase
+// sample is complete, one thread-block cluster per slot; nactive (zeroed by
+// launch_plan) is counted up by the slots still active.
+cudaError_t launch_pass_slots(Slot *slots, const SolveConsts &C, int32_t *nactive, cudaStream_t st);
 
 size_t sweep_smem_bytes(int max_n, int Q, int thr_stride, int maxdeg, bool stage_ell);
 cudaError_t launch_sweep(const SweepLaunch &L, bool pm1, int block, int grid, size_t smem,

@@ -116,7 +116,7 @@ def test_register_kernel_rejects_general_couplers(cuda_lib):
         spvar.Plan([gpu_problem(I.random_graph(30, 60, 2, jmax=5, hmax=3))], prm)
 
 
-UJ_SHAPES = [(4, 256), (8, 256), (16, 256), (4, 512), (4, 1024), (8, 1024)]
+UJ_SHAPES = [(4, 256), (8, 256), (16, 256), (4, 512), (4, 576), (8, 576), (4, 1024), (8, 1024)]
 
 
 @pytest.mark.parametrize("rpb,block", UJ_SHAPES, ids=["%d-%d" % s for s in UJ_SHAPES])
