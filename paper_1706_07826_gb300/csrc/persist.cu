@@ -573,20 +573,19 @@ __global__ void __launch_bounds__(kBigBlock) k_reduce_slots(Slot *slots, SolveCo
 // between free spins keep theirs, colour classes are inherited.
 constexpr int kPassCluster = 8;
 constexpr int kPassBlock = kFoldChunk;  // one spin per thread in a fold chunk
-constexpr int kFoldGather = 8;          // CSR entries a thread loads at once
+constexpr int kFoldGather = 4;          // CSR entries of each row a thread loads at once
+// Four resident CTAs per SM (64 registers): 64 starts (512 CTAs) run in one wave.
+constexpr int kPassMinBlocks = 4;
 // count chunks (1024 spins) and fold chunks a CTA owns at most
 constexpr int kOwnCount = (SPVAR_MAX_N / 1024 + kPassCluster - 1) / kPassCluster;
 constexpr int kOwnFold = (kFoldMaxChunks + kPassCluster - 1) / kPassCluster;
 static_assert(kPassBlock == kCountBlock, "the count chunks run on the pass CTAs");
 static_assert(SPVAR_MAX_N <= 32768, "new index and position are packed in 16 bits each");
 
-// Every global write of this CTA before the barrier is visible to the
-// cluster's other CTAs after it (shared memory writes are, by the barrier).
-__device__ __forceinline__ void pass_barrier()
-{
-    __threadfence();
-    cg::this_cluster().sync();
-}
+// Cluster barrier: its arrive releases and its wait acquires at cluster
+// scope, so every write (global or shared) a CTA makes before it is visible to
+// the cluster's other CTAs after it.
+__device__ __forceinline__ void pass_barrier() { cg::this_cluster().sync(); }
 
 // Fixing of spin j (count chunk j / 1024, owned by CTA (j / 1024) mod kPassCluster).
 __device__ __forceinline__ int fixed_in_cluster(const int8_t *s_fx, int j)
@@ -604,106 +603,136 @@ __device__ __forceinline__ uint32_t npos_in_cluster(const uint32_t *s_npos, int 
     return p[(c / kPassCluster) * kFoldChunk + (j % kFoldChunk)];
 }
 
-__device__ __forceinline__ void fold_count(Slot &s, int chunk, const int8_t *s_fx)
+// Chunks ch[0..G) of the CTA (-1: none) at once, so that the loads of all of
+// them are in flight together.
+template <int G>
+__device__ __forceinline__ void fold_count(Slot &s, const int (&ch)[G], const int8_t *s_fx)
 {
-    __shared__ int s_cls[kMaxColours];
-    __shared__ int s_free, s_nnz, s_hnz;
-    __shared__ unsigned long long s_key, s_off;
+    __shared__ int s_cls[G][kMaxColours];
+    __shared__ int s_free[G], s_nnz[G], s_hnz[G];
+    __shared__ unsigned long long s_key[G], s_off[G];
     const DevProb *P = s.cur;
     const int n = P->n, cap = P->cap_n, tid = threadIdx.x;
-    const int i0 = chunk * kFoldChunk;
-    if (i0 >= n) return;
-    for (int c = tid; c < kMaxColours; c += kPassBlock) s_cls[c] = 0;
-    if (tid == 0) {
-        s_free = s_nnz = s_hnz = 0;
-        s_key = 0ull;
-        s_off = 0ull;
+    for (int x = tid; x < G * kMaxColours; x += kPassBlock) s_cls[x / kMaxColours][x % kMaxColours] = 0;
+    if (tid < G) {
+        s_free[tid] = s_nnz[tid] = s_hnz[tid] = 0;
+        s_key[tid] = 0ull;
+        s_off[tid] = 0ull;
     }
     __syncthreads();
     int32_t *rowcnt = s.scratch + cap, *hfold = s.scratch + 2 * cap;
-    long long off = 0;
-    int nfree = 0, nnz = 0, hnz = 0, col = -1;
-    unsigned long long key = 0ull;
-    const int i = i0 + tid;
-    if (i < n) {
-        const int vi = fixed_in_cluster(s_fx, i);
-        long long hf = P->h[i];
-        int nf = 0;
-        const int p0 = P->row_ptr[i], p1 = P->row_ptr[i + 1];
-        for (int pb = p0; pb < p1; pb += kFoldGather) {
-            // the row's entries in batches: every load of a batch is issued before any is used
-            int jj[kFoldGather], vv[kFoldGather], fj[kFoldGather];
+    int i[G], vi[G], p0[G], p1[G], nf[G], h0[G], cl[G];
+    long long hf[G], off[G];
+    bool ok[G];
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+        i[g] = ch[g] * kFoldChunk + tid;
+        ok[g] = ch[g] >= 0 && i[g] < n;
+        vi[g] = ok[g] ? fixed_in_cluster(s_fx, i[g]) : 0;
+        h0[g] = ok[g] ? P->h[i[g]] : 0;
+        cl[g] = ok[g] ? P->colour[i[g]] : -1;
+        p0[g] = ok[g] ? P->row_ptr[i[g]] : 0;
+        p1[g] = ok[g] ? P->row_ptr[i[g] + 1] : 0;
+        hf[g] = h0[g];
+        nf[g] = 0;
+        off[g] = 0;
+    }
+    int len = 0;
+#pragma unroll
+    for (int g = 0; g < G; ++g) len = max(len, p1[g] - p0[g]);
+    for (int d0 = 0; d0 < len; d0 += kFoldGather) {
+        // kFoldGather entries of every row: all loads issued before any is used
+        int jj[G][kFoldGather], vv[G][kFoldGather], fj[G][kFoldGather];
+#pragma unroll
+        for (int g = 0; g < G; ++g)
 #pragma unroll
             for (int d = 0; d < kFoldGather; ++d) {
-                const bool in = pb + d < p1;
-                jj[d] = in ? P->col[pb + d] : -1;
-                vv[d] = in ? P->val[pb + d] : 0;
+                const bool in = p0[g] + d0 + d < p1[g];
+                jj[g][d] = in ? P->col[p0[g] + d0 + d] : -1;
+                vv[g][d] = in ? P->val[p0[g] + d0 + d] : 0;
             }
 #pragma unroll
-            for (int d = 0; d < kFoldGather; ++d) fj[d] = jj[d] >= 0 ? fixed_in_cluster(s_fx, jj[d]) : 0;
+        for (int g = 0; g < G; ++g)
+#pragma unroll
+            for (int d = 0; d < kFoldGather; ++d) fj[g][d] = jj[g][d] >= 0 ? fixed_in_cluster(s_fx, jj[g][d]) : 0;
+#pragma unroll
+        for (int g = 0; g < G; ++g)
 #pragma unroll
             for (int d = 0; d < kFoldGather; ++d) {
-                if (jj[d] < 0) continue;
-                if (vi) {
-                    if (fj[d] && jj[d] > i) off += (long long)vv[d] * vi * fj[d];
-                } else if (fj[d]) {
-                    hf += (long long)vv[d] * fj[d];
+                if (jj[g][d] < 0) continue;
+                if (vi[g]) {
+                    if (fj[g][d] && jj[g][d] > i[g]) off[g] += (long long)vv[g][d] * vi[g] * fj[g][d];
+                } else if (fj[g][d]) {
+                    hf[g] += (long long)vv[g][d] * fj[g][d];
                 } else {
-                    ++nf;
+                    ++nf[g];
                 }
             }
-        }
-        if (vi) {
-            off += (long long)P->h[i] * vi;
-        } else {
-            hfold[i] = (int32_t)hf;
-            rowcnt[i] = nf;
-            nfree = 1;
-            nnz = nf;
-            hnz = hf != 0;
-            col = P->colour[i];
-            // reference spin of the new problem: largest degree, lowest index
-            key = ((unsigned long long)nf << 32) | (unsigned long long)(0x7FFFFFFF - i);
-        }
     }
-    // one shared atomic per warp (and per colour class present in the warp)
     const unsigned full = 0xFFFFFFFFu;
     const int lane = tid & 31;
-    const unsigned same = __match_any_sync(full, col);
-    if (col >= 0 && lane == __ffs(same) - 1) atomicAdd(&s_cls[col], __popc(same));
-    nfree = __reduce_add_sync(full, nfree);
-    nnz = __reduce_add_sync(full, nnz);
-    hnz = __reduce_or_sync(full, hnz);
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        key = max(key, __shfl_xor_sync(full, key, o));
-        off += __shfl_xor_sync(full, off, o);
-    }
-    if (lane == 0) {
-        atomicAdd(&s_free, nfree);
-        atomicAdd(&s_nnz, nnz);
-        if (hnz) atomicOr(&s_hnz, 1);
-        atomicMax(&s_key, key);
-        atomicAdd(&s_off, (unsigned long long)off);
+    for (int g = 0; g < G; ++g) {
+        int nfree = 0, nnz = 0, hnz = 0, col = -1;
+        unsigned long long key = 0ull;
+        long long o = 0;
+        if (ok[g]) {
+            if (vi[g]) {
+                o = off[g] + (long long)h0[g] * vi[g];
+            } else {
+                hfold[i[g]] = (int32_t)hf[g];
+                rowcnt[i[g]] = nf[g];
+                nfree = 1;
+                nnz = nf[g];
+                hnz = hf[g] != 0;
+                col = cl[g];
+                // reference spin of the new problem: largest degree, lowest index
+                key = ((unsigned long long)nf[g] << 32) | (unsigned long long)(0x7FFFFFFF - i[g]);
+            }
+        }
+        // one shared atomic per warp (and per colour class present in the warp)
+        const unsigned same = __match_any_sync(full, col);
+        if (col >= 0 && lane == __ffs(same) - 1) atomicAdd(&s_cls[g][col], __popc(same));
+        nfree = __reduce_add_sync(full, nfree);
+        nnz = __reduce_add_sync(full, nnz);
+        hnz = __reduce_or_sync(full, hnz);
+#pragma unroll
+        for (int sh = 16; sh > 0; sh >>= 1) {
+            key = max(key, __shfl_xor_sync(full, key, sh));
+            o += __shfl_xor_sync(full, o, sh);
+        }
+        if (lane == 0 && ch[g] >= 0) {
+            atomicAdd(&s_free[g], nfree);
+            atomicAdd(&s_nnz[g], nnz);
+            if (hnz) atomicOr(&s_hnz[g], 1);
+            atomicMax(&s_key[g], key);
+            atomicAdd(&s_off[g], (unsigned long long)o);
+        }
     }
     __syncthreads();
     int32_t *tab = s.scratch + fold_table_offset(cap);
-    int32_t *e = tab + chunk * kFoldStride;
-    if (tid == 0) {
-        e[0] = s_free;
-        e[1] = s_nnz;
-        e[2] = s_hnz;
-        e[3] = (int32_t)(s_key >> 32);
-        e[4] = (int32_t)(s_key & 0xFFFFFFFFull);
-        atomicAdd(reinterpret_cast<unsigned long long *>(tab + kFoldMaxChunks * kFoldStride), s_off);
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+        if (ch[g] < 0 || ch[g] * kFoldChunk >= n) continue;
+        int32_t *e = tab + ch[g] * kFoldStride;
+        if (tid == 0) {
+            e[0] = s_free[g];
+            e[1] = s_nnz[g];
+            e[2] = s_hnz[g];
+            e[3] = (int32_t)(s_key[g] >> 32);
+            e[4] = (int32_t)(s_key[g] & 0xFFFFFFFFull);
+            atomicAdd(reinterpret_cast<unsigned long long *>(tab + kFoldMaxChunks * kFoldStride), s_off[g]);
+        }
+        for (int c = tid; c < P->ncol; c += kPassBlock) e[6 + c] = s_cls[g][c];
     }
-    for (int c = tid; c < P->ncol; c += kPassBlock) e[6 + c] = s_cls[c];
-    __syncthreads();  // the shared totals are reset by this CTA's next chunk
+    __syncthreads();  // the shared totals are reset by this CTA's next chunks
 }
+
+constexpr int kScanCols = 6;  // colour classes ranked per multi-value scan
 
 __device__ __forceinline__ void fold_index(Slot &s, int chunk, const int8_t *s_fx, uint32_t *s_npos)
 {
-    __shared__ int s_warp[32];
+    __shared__ int s_w[32 * (2 + kScanCols)];
     __shared__ int s_base_cls[kMaxColours], s_tot_cls[kMaxColours], s_cptr[kMaxColours + 1];
     __shared__ int s_base[2], s_tot[2], s_hnz;
     const DevProb *P = s.cur;
@@ -713,29 +742,37 @@ __device__ __forceinline__ void fold_index(Slot &s, int chunk, const int8_t *s_f
     if (chunk > 0 && i0 >= n) return;  // chunk 0 writes the header, even for n = 0
     const int nch = (n + kFoldChunk - 1) / kFoldChunk;
     const int32_t *tab = s.scratch + fold_table_offset(cap);
+    // the spin's own values first (they do not wait for the table)
+    const int i = i0 + tid;
+    const bool valid = i < n;
+    const int32_t *rowcnt = s.scratch + cap, *hfold = s.scratch + 2 * cap;
+    const int32_t *orig = s.orig[s.ocur];
+    const bool f = valid && fixed_in_cluster(s_fx, i) == 0;
+    const int rc = valid ? rowcnt[i] : 0, colv = valid ? P->colour[i] : -1;
+    const int h = valid ? hfold[i] : 0, oi = valid ? orig[i] : 0;
     // offsets of this chunk (totals of the chunks before it) and the totals of all:
     // field f (0 free spins, 1 free-free entries, 2 + c spins of class c) summed by a warp
     {
         const int lane = tid & 31, warp = tid >> 5;
-        for (int f = warp; f < 3 + ncol; f += kPassBlock / 32) {
-            const int fo = f < 3 ? f : 6 + (f - 3);  // table column (2: nonzero-bias flag)
+        for (int fld = warp; fld < 3 + ncol; fld += kPassBlock / 32) {
+            const int fo = fld < 3 ? fld : 6 + (fld - 3);  // table column (2: nonzero-bias flag)
             int b = 0, t = 0;
             for (int q = lane; q < nch; q += 32) {
                 const int v = tab[q * kFoldStride + fo];
-                t += f == 2 ? (v != 0) : v;
+                t += fld == 2 ? (v != 0) : v;
                 b += q < chunk ? v : 0;
             }
             b = __reduce_add_sync(0xFFFFFFFFu, b);
             t = __reduce_add_sync(0xFFFFFFFFu, t);
             if (lane == 0) {
-                if (f < 2) {
-                    s_base[f] = b;
-                    s_tot[f] = t;
-                } else if (f == 2) {
+                if (fld < 2) {
+                    s_base[fld] = b;
+                    s_tot[fld] = t;
+                } else if (fld == 2) {
                     s_hnz = t;
                 } else {
-                    s_base_cls[f - 3] = b;
-                    s_tot_cls[f - 3] = t;
+                    s_base_cls[fld - 3] = b;
+                    s_tot_cls[fld - 3] = t;
                 }
             }
         }
@@ -767,35 +804,35 @@ __device__ __forceinline__ void fold_index(Slot &s, int chunk, const int8_t *s_f
         D->row_ptr[m] = nnz2;
     }
     if (i0 < n) {
-        const int32_t *rowcnt = s.scratch + cap, *hfold = s.scratch + 2 * cap;
-        const int32_t *orig = s.orig[s.ocur];
         int32_t *orig2 = s.orig[s.ocur ^ 1];
-        const int carry_free = s_base[0], carry_nnz = s_base[1];
-        const int i = i0 + tid;
-        const bool valid = i < n;
-        const bool f = valid && fixed_in_cluster(s_fx, i) == 0;
-        const int rc = f ? rowcnt[i] : 0;
-        const int col = f ? P->colour[i] : -1;
-        int tf, tr;
-        const int exf = block_scan_excl(f ? 1 : 0, s_warp, &tf);
-        const int exr = block_scan_excl(rc, s_warp, &tr);
-        // rank among this step's free spins of the same colour class
-        int rank = 0;
-        for (int c = 0; c < ncol; ++c) {
-            int tc;
-            const int exc = block_scan_excl(col == c ? 1 : 0, s_warp, &tc);
-            if (col == c) rank = s_base_cls[c] + exc;
+        const int col = f ? colv : -1;
+        // new index, row pointer and rank among the chunk's free spins of the same
+        // colour class: one multi-value scan per group of kScanCols classes
+        int exf = 0, exr = 0, rank = 0;
+        for (int cb = 0; cb < max(ncol, 1); cb += kScanCols) {
+            int v[2 + kScanCols], ex[2 + kScanCols], tot[2 + kScanCols];
+            v[0] = cb == 0 && f ? 1 : 0;
+            v[1] = cb == 0 && f ? rc : 0;
+#pragma unroll
+            for (int q = 0; q < kScanCols; ++q) v[2 + q] = col == cb + q ? 1 : 0;
+            block_scan_multi<2 + kScanCols>(v, ex, tot, s_w);
+            if (cb == 0) {
+                exf = ex[0];
+                exr = ex[1];
+            }
+#pragma unroll
+            for (int q = 0; q < kScanCols; ++q)
+                if (col == cb + q) rank = s_base_cls[col] + ex[2 + q];
         }
-        const int a = carry_free + exf;
+        const int a = s_base[0] + exf;
         const int pos = f ? s_cptr[col] + rank : 0;
         if (valid) s_npos[(chunk / kPassCluster) * kFoldChunk + tid] = f ? (uint32_t)a | ((uint32_t)pos << 16) : ~0u;
         if (f) {
-            const int h = hfold[i];
             s.old_of_new[a] = i;
-            orig2[a] = orig[i];
+            orig2[a] = oi;
             D->h[a] = h;
             D->colour[a] = col;
-            D->row_ptr[a] = carry_nnz + exr;
+            D->row_ptr[a] = s_base[1] + exr;
             D->pos_of_idx[a] = pos;
             D->idx_of_pos[pos] = a;
             D->meta[pos] = ((uint32_t)(h & 0xFFFF) << 16) | (uint32_t)rc;
@@ -804,13 +841,13 @@ __device__ __forceinline__ void fold_index(Slot &s, int chunk, const int8_t *s_f
     __syncthreads();  // the shared offsets are rewritten by this CTA's next chunk
 }
 
-__device__ __forceinline__ void fold_fill(Slot &s, int chunk, const uint32_t *s_npos)
+template <int G>
+__device__ __forceinline__ void fold_fill(Slot &s, const int (&ch)[G], const uint32_t *s_npos)
 {
     const DevProb *P = s.cur;
     DevProb *D = s.buf[s.next];
     const int n = P->n, cap = P->cap_n, tid = threadIdx.x;
-    const int i0 = chunk * kFoldChunk;
-    if (chunk == 0 && tid == 0) {
+    if (ch[0] == 0 && tid == 0) {
         // the reference spin: the chunks' candidates, largest degree then lowest index
         const int32_t *tab = s.scratch + fold_table_offset(cap);
         unsigned long long best = 0ull;
@@ -824,47 +861,62 @@ __device__ __forceinline__ void fold_fill(Slot &s, int chunk, const uint32_t *s_
         }
         D->rho = any ? (int)(npos_in_cluster(s_npos, 0x7FFFFFFF - (int)(best & 0xFFFFFFFFull)) & 0xFFFFu) : -1;
     }
-    if (i0 >= n) return;
-    const int i = i0 + tid;
-    const uint32_t own = i < n ? s_npos[(chunk / kPassCluster) * kFoldChunk + tid] : ~0u;
-    if (own != ~0u) {
-        const int a = (int)(own & 0xFFFFu), pos = (int)(own >> 16);
-        const int p0 = P->row_ptr[i], p1 = P->row_ptr[i + 1];
-        int q = D->row_ptr[a];
-        int d = 0;
-        for (int pb = p0; pb < p1; pb += kFoldGather) {
-            // the row's entries in batches: each dependent step loads for the whole batch
-            int jj[kFoldGather], vv[kFoldGather];
-            uint32_t np[kFoldGather];
+    int p0[G], p1[G], q[G], pos[G], d[G];
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+        const int i = ch[g] * kFoldChunk + tid;
+        const uint32_t own =
+            ch[g] >= 0 && i < n ? s_npos[(ch[g] / kPassCluster) * kFoldChunk + tid] : ~0u;  // free spins only
+        const bool free = own != ~0u;
+        p0[g] = free ? P->row_ptr[i] : 0;
+        p1[g] = free ? P->row_ptr[i + 1] : 0;
+        q[g] = free ? D->row_ptr[own & 0xFFFFu] : 0;
+        pos[g] = (int)(own >> 16);
+        d[g] = 0;
+    }
+    int len = 0;
+#pragma unroll
+    for (int g = 0; g < G; ++g) len = max(len, p1[g] - p0[g]);
+    for (int d0 = 0; d0 < len; d0 += kFoldGather) {
+        // kFoldGather entries of every row: each dependent step loads for all of them
+        int vv[G][kFoldGather];
+        uint32_t np[G][kFoldGather];
+#pragma unroll
+        for (int g = 0; g < G; ++g)
 #pragma unroll
             for (int e = 0; e < kFoldGather; ++e) {
-                const bool in = pb + e < p1;
-                jj[e] = in ? P->col[pb + e] : -1;
-                vv[e] = in ? P->val[pb + e] : 0;
+                const bool in = p0[g] + d0 + e < p1[g];
+                np[g][e] = in ? (uint32_t)P->col[p0[g] + d0 + e] : ~0u;
+                vv[g][e] = in ? P->val[p0[g] + d0 + e] : 0;
             }
 #pragma unroll
-            for (int e = 0; e < kFoldGather; ++e) np[e] = jj[e] >= 0 ? npos_in_cluster(s_npos, jj[e]) : ~0u;
+        for (int g = 0; g < G; ++g)
+#pragma unroll
+            for (int e = 0; e < kFoldGather; ++e)
+                np[g][e] = np[g][e] != ~0u ? npos_in_cluster(s_npos, (int)np[g][e]) : ~0u;
+#pragma unroll
+        for (int g = 0; g < G; ++g)
 #pragma unroll
             for (int e = 0; e < kFoldGather; ++e) {
-                if (np[e] == ~0u) continue;
-                const uint32_t b = np[e] & 0xFFFFu, pp = np[e] >> 16;
-                D->col[q] = (int32_t)b;
-                D->val[q] = vv[e];
-                D->ell[(size_t)d * cap + pos] = pp | ((uint32_t)(vv[e] & 0xFFFF) << 16);
-                ++q;
-                ++d;
+                if (np[g][e] == ~0u) continue;
+                const uint32_t b = np[g][e] & 0xFFFFu, pp = np[g][e] >> 16;
+                D->col[q[g]] = (int32_t)b;
+                D->val[q[g]] = vv[g][e];
+                D->ell[(size_t)d[g] * cap + pos[g]] = pp | ((uint32_t)(vv[g][e] & 0xFFFF) << 16);
+                ++q[g];
+                ++d[g];
             }
-        }
     }
 }
 
 // Dynamic shared memory of the pass: the elite list (Smax entries), then one
-// region that holds in turn the elite's keys, a count chunk's counters and the
-// CTA's (new index, position) pairs.
+// region that holds in turn the elite's candidate keys and energies, a count
+// chunk's counters and the CTA's (new index, position) pairs.
 __host__ __device__ inline size_t pass_list_bytes(int Smax) { return ((size_t)Smax * 4 + 15) & ~(size_t)15; }
 __host__ __device__ inline size_t pass_smem(int Smax)
 {
     size_t u = (size_t)elite_key_words(Smax) * 8;
+    if (u < (size_t)(kEliteRankMax + Smax) * 8) u = (size_t)(kEliteRankMax + Smax) * 8;  // keys, then energies
     if (u < sizeof(CountSmem)) u = sizeof(CountSmem);
     if (u < (size_t)kOwnFold * kFoldChunk * 4) u = (size_t)kOwnFold * kFoldChunk * 4;
     return pass_list_bytes(Smax) + u;
@@ -876,7 +928,7 @@ __host__ __device__ inline size_t pass_smem(int Smax)
 // changed only by rank 0 after the last one, so all CTAs of a cluster take
 // the same path through the barriers, and none leaves while another may
 // still read its shared memory.
-__global__ void __cluster_dims__(kPassCluster, 1, 1) __launch_bounds__(kPassBlock)
+__global__ void __cluster_dims__(kPassCluster, 1, 1) __launch_bounds__(kPassBlock, kPassMinBlocks)
     k_pass_slots(Slot *slots, SolveConsts C, int32_t *nactive)
 {
     extern __shared__ __align__(16) unsigned long long s_dyn[];
@@ -896,7 +948,8 @@ __global__ void __cluster_dims__(kPassCluster, 1, 1) __launch_bounds__(kPassBloc
     const int k = (mode == kFixing) ? (C.pticm ? elite_count_hd(C.elite, S) : C.k_fix)
                   : (mode == kCorr) ? C.k_corr : 1;
     const int64_t *e = s.rec_e + (size_t)s.phase * C.Smax;
-    elite_fast(e, S, k, s_elite, reinterpret_cast<unsigned long long *>(s_reg));
+    elite_fast(e, S, k, s_elite, reinterpret_cast<unsigned long long *>(s_reg),
+               reinterpret_cast<int64_t *>(s_reg) + kEliteRankMax);
     const DevProb *P = s.cur;
     const int n = P->n;
     const int32_t *orig = s.orig[s.ocur];
@@ -906,9 +959,15 @@ __global__ void __cluster_dims__(kPassCluster, 1, 1) __launch_bounds__(kPassBloc
     constexpr int kStride = kPassCluster * kPassBlock;
     if (better) {
         // spins fixed in earlier phases, before this phase adds its fixings to fmap
-        for (int o = rank * kPassBlock + tid; o < s.n0; o += kStride) {
-            const int8_t v = s.fmap[o];
-            if (v) s.best_state[o] = v;
+        // (four loads in flight per thread)
+        const int n0 = s.n0;
+        for (int o0 = rank * kPassBlock + tid; o0 < n0; o0 += 4 * kStride) {
+            int8_t v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) v[u] = o0 + u * kStride < n0 ? s.fmap[o0 + u * kStride] : 0;
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (v[u]) s.best_state[o0 + u * kStride] = v[u];
         }
     }
     if (rank == 0) {
@@ -921,8 +980,19 @@ __global__ void __cluster_dims__(kPassCluster, 1, 1) __launch_bounds__(kPassBloc
     if (better) {
         if (rank == 0 && tid == 0) *s.best_e = eb;
         const uint32_t *row = s.spins + (size_t)rbest * s.W0;
-        for (int a = rank * kPassBlock + tid; a < n; a += kStride)
-            s.best_state[orig[a]] = ((row[a >> 5] >> (a & 31)) & 1u) ? 1 : -1;
+        for (int a0 = rank * kPassBlock + tid; a0 < n; a0 += 4 * kStride) {
+            int o[4];
+            uint32_t w[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int a = a0 + u * kStride;
+                o[u] = a < n ? orig[a] : -1;
+                w[u] = a < n ? row[a >> 5] : 0u;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (o[u] >= 0) s.best_state[o[u]] = ((w[u] >> ((a0 + u * kStride) & 31)) & 1u) ? 1 : -1;
+        }
     }
     if (mode == kSolving) {
         if (rank == 0 && tid == 0) {
@@ -954,11 +1024,18 @@ __global__ void __cluster_dims__(kPassCluster, 1, 1) __launch_bounds__(kPassBloc
     }
     uint32_t *s_npos = reinterpret_cast<uint32_t *>(s_reg);  // the count's counters are dead
     const int nch = max(1, (n + kFoldChunk - 1) / kFoldChunk);
-    for (int c = rank; c < nch; c += kPassCluster) fold_count(s, c, s_fx);
+    // this CTA's chunks rank, rank + kPassCluster, ..., two at a time in the gather stages
+    for (int c = rank; c < nch; c += 2 * kPassCluster) {
+        const int ch[2] = {c, c + kPassCluster < nch ? c + kPassCluster : -1};
+        fold_count<2>(s, ch, s_fx);
+    }
     pass_barrier();
     for (int c = rank; c < nch; c += kPassCluster) fold_index(s, c, s_fx, s_npos);
     pass_barrier();
-    for (int c = rank; c < nch; c += kPassCluster) fold_fill(s, c, s_npos);
+    for (int c = rank; c < nch; c += 2 * kPassCluster) {
+        const int ch[2] = {c, c + kPassCluster < nch ? c + kPassCluster : -1};
+        fold_fill<2>(s, ch, s_npos);
+    }
     pass_barrier();
     // 4. the phase transition
     if (rank == 0 && tid == 0) {

@@ -40,6 +40,50 @@ __device__ __forceinline__ int block_scan_excl(int v, int *s_warp, int *total)
     return prefix;
 }
 
+// Exclusive block-wide scans of V ints per thread at once, with the three
+// barriers of one scan.  s_w: >= 32 V ints of shared memory.  Contains
+// __syncthreads: call uniformly.
+template <int V>
+__device__ __forceinline__ void block_scan_multi(const int (&v)[V], int (&ex)[V], int (&tot)[V], int *s_w)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (int)(blockDim.x >> 5);
+    int x[V];
+#pragma unroll
+    for (int q = 0; q < V; ++q) x[q] = v[q];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+#pragma unroll
+        for (int q = 0; q < V; ++q) {
+            const int y = __shfl_up_sync(0xFFFFFFFFu, x[q], o);
+            if (lane >= o) x[q] += y;
+        }
+    }
+    if (lane == 31) {
+#pragma unroll
+        for (int q = 0; q < V; ++q) s_w[q * 32 + warp] = x[q];
+    }
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int q = 0; q < V; ++q) {
+            int w = lane < nw ? s_w[q * 32 + lane] : 0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xFFFFFFFFu, w, o);
+                if (lane >= o) w += y;
+            }
+            s_w[q * 32 + lane] = w;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < V; ++q) {
+        ex[q] = (warp > 0 ? s_w[q * 32 + warp - 1] : 0) + x[q] - v[q];
+        tot[q] = s_w[q * 32 + nw - 1];
+    }
+    __syncthreads();
+}
+
 // Elite selection: indices of the k lowest (energy, index) pairs, in order.
 // Bitonic sort of packed 64-bit keys (energy - min) << 32 | index in shared
 // memory (s_key >= next power of two of S entries).  blockDim.x == kBigBlock.
@@ -88,8 +132,10 @@ __device__ __forceinline__ void elite_core(const int64_t *energies, int S, int k
 // which are compacted in index order and placed by rank (the number of
 // candidate keys below each; keys are distinct because they carry the
 // index).  k = 1 is a block-wide arg-min.  More than kEliteRankMax candidates
-// (a crowded bin) fall back to elite_core.  blockDim.x == kBigBlock; s_key as
-// for elite_core.
+// (a crowded bin) fall back to elite_core.  Any block size; s_key as for
+// elite_core.  s_e (optional, shared memory, S entries, apart from the first
+// kEliteRankMax keys): the energies are read from global memory once and kept
+// there for the later passes.
 // Keys of elite_core's sort: the next power of two of S.
 __host__ __device__ inline int elite_key_words(int S)
 {
@@ -101,7 +147,7 @@ __host__ __device__ inline int elite_key_words(int S)
 constexpr int kEliteBins = 1024;
 constexpr int kEliteRankMax = 512;
 __device__ __forceinline__ void elite_fast(const int64_t *energies, int S, int k, int32_t *elite,
-                                           unsigned long long *s_key)
+                                           unsigned long long *s_key, int64_t *s_e = nullptr)
 {
     __shared__ long long s_min, s_max;
     __shared__ unsigned long long s_best;
@@ -117,10 +163,20 @@ __device__ __forceinline__ void elite_fast(const int64_t *energies, int S, int k
     for (int b = tid; b < kEliteBins; b += B) s_hist[b] = 0;
     __syncthreads();
     long long mn = LLONG_MAX, mx = LLONG_MIN;
-    for (int r = tid; r < S; r += B) {
-        const long long e = energies[r];
-        mn = min(mn, e);
-        mx = max(mx, e);
+    for (int r0 = tid; r0 < S; r0 += 4 * B) {
+        // four loads in flight per thread
+        long long ev[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) ev[u] = r0 + u * B < S ? (long long)energies[r0 + u * B] : 0;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int r = r0 + u * B;
+            if (r < S) {
+                if (s_e) s_e[r] = ev[u];
+                mn = min(mn, ev[u]);
+                mx = max(mx, ev[u]);
+            }
+        }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -133,10 +189,11 @@ __device__ __forceinline__ void elite_fast(const int64_t *energies, int S, int k
     }
     __syncthreads();
     const long long emin = s_min;
+    const int64_t *E = s_e ? s_e : energies;  // the later passes
     if (k == 1) {
         unsigned long long best = ~0ull;
         for (int r = tid; r < S; r += B)
-            best = min(best, ((unsigned long long)(energies[r] - emin) << 32) | (unsigned)r);
+            best = min(best, ((unsigned long long)(E[r] - emin) << 32) | (unsigned)r);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) best = min(best, __shfl_xor_sync(0xFFFFFFFFu, best, o));
         if ((tid & 31) == 0) atomicMin(&s_best, best);
@@ -147,7 +204,7 @@ __device__ __forceinline__ void elite_fast(const int64_t *energies, int S, int k
     }
     int shift = 0;
     while (((unsigned long long)(s_max - emin) >> shift) >= (unsigned long long)kEliteBins) ++shift;
-    for (int r = tid; r < S; r += B) atomicAdd(&s_hist[(int)((unsigned long long)(energies[r] - emin) >> shift)], 1);
+    for (int r = tid; r < S; r += B) atomicAdd(&s_hist[(int)((unsigned long long)(E[r] - emin) >> shift)], 1);
     __syncthreads();
     // the bin holding the k-th lowest key (keys in bins below it number < k, with
     // it >= k): each thread scans a run of consecutive bins after one block scan
@@ -177,11 +234,11 @@ __device__ __forceinline__ void elite_fast(const int64_t *energies, int S, int k
         const int per = (S + B - 1) / B, r0 = tid * per;
         int f = 0;
         for (int r = r0; r < r0 + per && r < S; ++r)
-            f += (int)((unsigned long long)(energies[r] - emin) >> shift) <= bstar;
+            f += (int)((unsigned long long)(E[r] - emin) >> shift) <= bstar;
         int tot;
         int o = block_scan_excl(f, s_warp, &tot);
         for (int r = r0; r < r0 + per && r < S; ++r) {
-            const unsigned long long d = (unsigned long long)(energies[r] - emin);
+            const unsigned long long d = (unsigned long long)(E[r] - emin);
             if ((int)(d >> shift) <= bstar) s_key[o++] = (d << 32) | (unsigned)r;
         }
     }
@@ -342,23 +399,35 @@ __device__ __forceinline__ void count_bs_core(const DevProb *P, const uint32_t *
             if (b < NT) s_tot[b][lane] = t[b];
     }
     __syncthreads();
-    for (int sp = threadIdx.x; sp < 1024; sp += blockDim.x) {
-        const int i = chunk * 1024 + sp;
-        const int wl = sp >> 5, bit = sp & 31;
-        int8_t v = 0;
-        if (i < n) {
-            int cnt = 0;
-            for (int b = 0; b < NT; ++b) cnt |= (int)((s_tot[b][wl] >> bit) & 1u) << b;
-            const long long diff = 2ll * cnt - k;
-            if (diff > 0 && (long long)fix_den * diff >= (long long)fix_num * k) v = 1;
-            if (diff < 0 && (long long)fix_den * (-diff) >= (long long)fix_num * k) v = -1;
-            if (counts) counts[i] = cnt;
-            fixed[i] = v;
-            if (v && fmap) fmap[orig[i]] = v;
+    for (int sp0 = threadIdx.x; sp0 < 1024; sp0 += 4 * blockDim.x) {
+        // the original indices of four spins loaded before any store
+        int oi[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int i = chunk * 1024 + sp0 + u * (int)blockDim.x;
+            oi[u] = (fmap && sp0 + u * (int)blockDim.x < 1024 && i < n) ? orig[i] : 0;
         }
-        if (fixed_copy) fixed_copy[sp] = v;  // the chunk's fixings, also in shared memory
-        const unsigned ball = __ballot_sync(0xFFFFFFFFu, v != 0);
-        if ((threadIdx.x & 31) == 0 && ball) atomicAdd(nfixed, __popc(ball));
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int sp = sp0 + u * (int)blockDim.x;
+            if (sp >= 1024) break;
+            const int i = chunk * 1024 + sp;
+            const int wl = sp >> 5, bit = sp & 31;
+            int8_t v = 0;
+            if (i < n) {
+                int cnt = 0;
+                for (int b = 0; b < NT; ++b) cnt |= (int)((s_tot[b][wl] >> bit) & 1u) << b;
+                const long long diff = 2ll * cnt - k;
+                if (diff > 0 && (long long)fix_den * diff >= (long long)fix_num * k) v = 1;
+                if (diff < 0 && (long long)fix_den * (-diff) >= (long long)fix_num * k) v = -1;
+                if (counts) counts[i] = cnt;
+                fixed[i] = v;
+                if (v && fmap) fmap[oi[u]] = v;
+            }
+            if (fixed_copy) fixed_copy[sp] = v;  // the chunk's fixings, also in shared memory
+            const unsigned ball = __ballot_sync(0xFFFFFFFFu, v != 0);
+            if ((threadIdx.x & 31) == 0 && ball) atomicAdd(nfixed, __popc(ball));
+        }
     }
 }
 

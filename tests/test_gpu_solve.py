@@ -39,6 +39,10 @@ SCASES = [
     ("weak_strong_C3", lambda: I.weak_strong(3, 1300), 80, 4, 40, 40, 0.2, False, 1),
     ("cubic_L5_odd_ispvar3", lambda: I.cubic3d(5, 1401), 60, 2, 64, 30, 0.2, True, 3),
     ("random_h", lambda: I.random_graph(30, 70, 3, jmax=3, hmax=2), 60, 3, 33, 19, 0.3, False, 1),
+    # large problems: the persistence pass's CTAs own several 1024-spin count chunks and run
+    # their 256-spin fold chunks in several rounds (odd L: more than two colour classes)
+    ("cubic_L24_large", lambda: I.cubic3d(24, 1500), 12, 2, 16, 8, 0.25, False, 1),
+    ("cubic_L31_odd_ispvar", lambda: I.cubic3d(31, 1501), 8, 1, 12, 8, 0.5, True, 2),
 ]
 
 
