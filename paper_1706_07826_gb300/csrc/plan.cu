@@ -150,27 +150,6 @@ struct TuneKey {
 std::map<TuneKey, SweepShape> g_tune_cache;
 std::mutex g_tune_mu;
 
-SweepLaunch make_launch(const spvar_plan *pl, int T)
-{
-    SweepLaunch L;
-    std::memset(&L, 0, sizeof(L));
-    L.jobs = pl->d_jobs;
-    L.items = pl->d_items;
-    L.nitems = pl->d_ctr + 0;
-    L.queue = pl->d_ctr + 1;
-    L.thr = pl->d_thr;
-    L.thr_stride = pl->thr_stride;
-    L.T = T;
-    L.Q = pl->shape.Q;
-    L.stage_ell = pl->shape.stage;
-    L.max_n = pl->max_n0;
-    L.max_deg = pl->max_deg;
-    L.ent = pl->d_ent;
-    L.P = pl->sqa_P;
-    L.W = pl->sqa_W;
-    return L;
-}
-
 int grid_for(const spvar_plan *pl, int items)
 {
     const int occ = std::max(1, sweep_shape_occupancy(pl->shape, pl->pm1, pl->sweep_smem));

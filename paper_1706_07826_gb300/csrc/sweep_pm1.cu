@@ -354,13 +354,16 @@ __device__ void run_item_pm1(const SweepLaunch &L, const SweepJob &job, int quad
 // Resident CTAs per SM asked of the register allocator (0: no request).  The
 // 128 x 4 byte-lane kernel for degree <= 6 uses 86 registers unasked, which
 // leaves room for five 128-thread CTAs per SM; capped at 71 (seven CTAs, no
-// spills) it runs 6 % faster on the Chimera C8 workload.  For the other shapes
-// a cap either spilled or was not faster, and an explicit minimum of 1 makes
-// the allocator take more registers than it does unasked.
+// spills) it runs 6 % faster on the Chimera C8 workload.  The 576-thread
+// 16-bit-lane forms fit two CTAs per SM at 56 registers without spills (the
+// degree-6 one-magnitude form takes 56 unasked; the others took 70 to 84).
+// For the other shapes a cap either spilled or was not faster, and an
+// explicit minimum of 1 makes the allocator take more registers than it does
+// unasked.
 template <int B, int NSLOT, int MAXD, bool SCALED>
 constexpr int pm1_min_blocks()
 {
-    return (B == 128 && NSLOT == 4 && MAXD == 6 && !SCALED) ? 7 : 0;
+    return (B == 128 && NSLOT == 4 && MAXD == 6 && !SCALED) ? 7 : (B == 576 && SCALED) ? 2 : 0;
 }
 
 template <int B, int NSLOT, int MAXD, bool SCALED, bool SI>
