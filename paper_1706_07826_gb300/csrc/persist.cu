@@ -553,32 +553,28 @@ __global__ void __launch_bounds__(kBigBlock) k_reduce_slots(Slot *slots, SolveCo
 //      read from L2, and the list is in its own shared memory with no
 //      barrier), and the start's best assignment;
 //   2. persistence counts and the fixing rule, 1024 spins per count chunk;
-//      each CTA also keeps its chunks' fixings in shared memory;
 //   3. the stall rule (ISPVAR), then the update of J and h spread over chunks
 //      of kFoldChunk spins:
 //        fold_count  per spin: folded bias, free-free row length, energy of
 //                    the fixed spins; per chunk: the totals fold_index offsets by;
 //        fold_index  new indices, h', row pointers, inherited colours and
 //                    sweep positions (each chunk adds the totals of the chunks
-//                    before it), and the new header (chunk 0); each CTA keeps
-//                    its chunks' (new index, position) pairs in shared memory;
+//                    before it), and the new header (chunk 0);
 //        fold_fill   CSR columns and values and the ELL layout of the free spins;
 //   4. the phase transition and the count of active starts.
 // Chunks are dealt to the cluster's CTAs round-robin, and a cluster barrier
 // stands where one stage reads what another CTA wrote in the stage before.  A
-// neighbour's fixing and its new index and position are read from the shared
-// memory of the CTA that owns its chunk (distributed shared memory), not by a
-// chain of global loads.  The result is the one the per-start kernels (elite,
-// count_bs_core, reduce_core) compute: free spins keep their order, couplers
-// between free spins keep theirs, colour classes are inherited.
+// neighbour's fixing, and then its new index and position packed in one word,
+// are single global loads; these per-start arrays (n bytes and 4n bytes) stay
+// in L1 and L2, which measured faster than reading them from the owning CTA's
+// shared memory over the cluster.  The result is the one the per-start
+// kernels (elite, count_bs_core, reduce_core) compute: free spins keep their
+// order, couplers between free spins keep theirs, colour classes are inherited.
 constexpr int kPassCluster = 8;
 constexpr int kPassBlock = kFoldChunk;  // one spin per thread in a fold chunk
 constexpr int kFoldGather = 4;          // CSR entries of each row a thread loads at once
 // Four resident CTAs per SM (64 registers): 64 starts (512 CTAs) run in one wave.
 constexpr int kPassMinBlocks = 4;
-// count chunks (1024 spins) and fold chunks a CTA owns at most
-constexpr int kOwnCount = (SPVAR_MAX_N / 1024 + kPassCluster - 1) / kPassCluster;
-constexpr int kOwnFold = (kFoldMaxChunks + kPassCluster - 1) / kPassCluster;
 static_assert(kPassBlock == kCountBlock, "the count chunks run on the pass CTAs");
 static_assert(SPVAR_MAX_N <= 32768, "new index and position are packed in 16 bits each");
 
@@ -587,26 +583,14 @@ static_assert(SPVAR_MAX_N <= 32768, "new index and position are packed in 16 bit
 // the cluster's other CTAs after it.
 __device__ __forceinline__ void pass_barrier() { cg::this_cluster().sync(); }
 
-// Fixing of spin j (count chunk j / 1024, owned by CTA (j / 1024) mod kPassCluster).
-__device__ __forceinline__ int fixed_in_cluster(const int8_t *s_fx, int j)
-{
-    const int c = j >> 10;
-    const int8_t *p = cg::this_cluster().map_shared_rank(s_fx, (unsigned)(c % kPassCluster));
-    return p[(c / kPassCluster) * 1024 + (j & 1023)];
-}
-
-// New index | position << 16 of spin j, or ~0 if j is fixed (fold chunk j / kFoldChunk).
-__device__ __forceinline__ uint32_t npos_in_cluster(const uint32_t *s_npos, int j)
-{
-    const int c = j / kFoldChunk;
-    const uint32_t *p = cg::this_cluster().map_shared_rank(s_npos, (unsigned)(c % kPassCluster));
-    return p[(c / kPassCluster) * kFoldChunk + (j % kFoldChunk)];
-}
+// New index | position << 16 of every old spin (~0 if fixed), in the slot's
+// scratch area (the one-CTA reduction keeps its new indices there).
+__device__ __forceinline__ uint32_t *npos_of(const Slot &s) { return reinterpret_cast<uint32_t *>(s.scratch); }
 
 // Chunks ch[0..G) of the CTA (-1: none) at once, so that the loads of all of
 // them are in flight together.
 template <int G>
-__device__ __forceinline__ void fold_count(Slot &s, const int (&ch)[G], const int8_t *s_fx)
+__device__ __forceinline__ void fold_count(Slot &s, const int (&ch)[G])
 {
     __shared__ int s_cls[G][kMaxColours];
     __shared__ int s_free[G], s_nnz[G], s_hnz[G];
@@ -628,7 +612,7 @@ __device__ __forceinline__ void fold_count(Slot &s, const int (&ch)[G], const in
     for (int g = 0; g < G; ++g) {
         i[g] = ch[g] * kFoldChunk + tid;
         ok[g] = ch[g] >= 0 && i[g] < n;
-        vi[g] = ok[g] ? fixed_in_cluster(s_fx, i[g]) : 0;
+        vi[g] = ok[g] ? s.fixed[i[g]] : 0;
         h0[g] = ok[g] ? P->h[i[g]] : 0;
         cl[g] = ok[g] ? P->colour[i[g]] : -1;
         p0[g] = ok[g] ? P->row_ptr[i[g]] : 0;
@@ -654,7 +638,7 @@ __device__ __forceinline__ void fold_count(Slot &s, const int (&ch)[G], const in
 #pragma unroll
         for (int g = 0; g < G; ++g)
 #pragma unroll
-            for (int d = 0; d < kFoldGather; ++d) fj[g][d] = jj[g][d] >= 0 ? fixed_in_cluster(s_fx, jj[g][d]) : 0;
+            for (int d = 0; d < kFoldGather; ++d) fj[g][d] = jj[g][d] >= 0 ? s.fixed[jj[g][d]] : 0;
 #pragma unroll
         for (int g = 0; g < G; ++g)
 #pragma unroll
@@ -730,7 +714,7 @@ __device__ __forceinline__ void fold_count(Slot &s, const int (&ch)[G], const in
 
 constexpr int kScanCols = 6;  // colour classes ranked per multi-value scan
 
-__device__ __forceinline__ void fold_index(Slot &s, int chunk, const int8_t *s_fx, uint32_t *s_npos)
+__device__ __forceinline__ void fold_index(Slot &s, int chunk)
 {
     __shared__ int s_w[32 * (2 + kScanCols)];
     __shared__ int s_base_cls[kMaxColours], s_tot_cls[kMaxColours], s_cptr[kMaxColours + 1];
@@ -747,7 +731,7 @@ __device__ __forceinline__ void fold_index(Slot &s, int chunk, const int8_t *s_f
     const bool valid = i < n;
     const int32_t *rowcnt = s.scratch + cap, *hfold = s.scratch + 2 * cap;
     const int32_t *orig = s.orig[s.ocur];
-    const bool f = valid && fixed_in_cluster(s_fx, i) == 0;
+    const bool f = valid && s.fixed[i] == 0;
     const int rc = valid ? rowcnt[i] : 0, colv = valid ? P->colour[i] : -1;
     const int h = valid ? hfold[i] : 0, oi = valid ? orig[i] : 0;
     // offsets of this chunk (totals of the chunks before it) and the totals of all:
@@ -826,7 +810,7 @@ __device__ __forceinline__ void fold_index(Slot &s, int chunk, const int8_t *s_f
         }
         const int a = s_base[0] + exf;
         const int pos = f ? s_cptr[col] + rank : 0;
-        if (valid) s_npos[(chunk / kPassCluster) * kFoldChunk + tid] = f ? (uint32_t)a | ((uint32_t)pos << 16) : ~0u;
+        if (valid) npos_of(s)[i] = f ? (uint32_t)a | ((uint32_t)pos << 16) : ~0u;
         if (f) {
             s.old_of_new[a] = i;
             orig2[a] = oi;
@@ -842,8 +826,9 @@ __device__ __forceinline__ void fold_index(Slot &s, int chunk, const int8_t *s_f
 }
 
 template <int G>
-__device__ __forceinline__ void fold_fill(Slot &s, const int (&ch)[G], const uint32_t *s_npos)
+__device__ __forceinline__ void fold_fill(Slot &s, const int (&ch)[G])
 {
+    const uint32_t *npos = npos_of(s);
     const DevProb *P = s.cur;
     DevProb *D = s.buf[s.next];
     const int n = P->n, cap = P->cap_n, tid = threadIdx.x;
@@ -859,14 +844,13 @@ __device__ __forceinline__ void fold_fill(Slot &s, const int (&ch)[G], const uin
             best = max(best, k);
             any = true;
         }
-        D->rho = any ? (int)(npos_in_cluster(s_npos, 0x7FFFFFFF - (int)(best & 0xFFFFFFFFull)) & 0xFFFFu) : -1;
+        D->rho = any ? (int)(npos[0x7FFFFFFF - (int)(best & 0xFFFFFFFFull)] & 0xFFFFu) : -1;
     }
     int p0[G], p1[G], q[G], pos[G], d[G];
 #pragma unroll
     for (int g = 0; g < G; ++g) {
         const int i = ch[g] * kFoldChunk + tid;
-        const uint32_t own =
-            ch[g] >= 0 && i < n ? s_npos[(ch[g] / kPassCluster) * kFoldChunk + tid] : ~0u;  // free spins only
+        const uint32_t own = ch[g] >= 0 && i < n ? npos[i] : ~0u;  // free spins only
         const bool free = own != ~0u;
         p0[g] = free ? P->row_ptr[i] : 0;
         p1[g] = free ? P->row_ptr[i + 1] : 0;
@@ -893,7 +877,7 @@ __device__ __forceinline__ void fold_fill(Slot &s, const int (&ch)[G], const uin
         for (int g = 0; g < G; ++g)
 #pragma unroll
             for (int e = 0; e < kFoldGather; ++e)
-                np[g][e] = np[g][e] != ~0u ? npos_in_cluster(s_npos, (int)np[g][e]) : ~0u;
+                np[g][e] = np[g][e] != ~0u ? npos[np[g][e]] : ~0u;
 #pragma unroll
         for (int g = 0; g < G; ++g)
 #pragma unroll
@@ -910,15 +894,14 @@ __device__ __forceinline__ void fold_fill(Slot &s, const int (&ch)[G], const uin
 }
 
 // Dynamic shared memory of the pass: the elite list (Smax entries), then one
-// region that holds in turn the elite's candidate keys and energies, a count
-// chunk's counters and the CTA's (new index, position) pairs.
+// region that holds in turn the elite's candidate keys and energies and a
+// count chunk's counters.
 __host__ __device__ inline size_t pass_list_bytes(int Smax) { return ((size_t)Smax * 4 + 15) & ~(size_t)15; }
 __host__ __device__ inline size_t pass_smem(int Smax)
 {
     size_t u = (size_t)elite_key_words(Smax) * 8;
     if (u < (size_t)(kEliteRankMax + Smax) * 8) u = (size_t)(kEliteRankMax + Smax) * 8;  // keys, then energies
     if (u < sizeof(CountSmem)) u = sizeof(CountSmem);
-    if (u < (size_t)kOwnFold * kFoldChunk * 4) u = (size_t)kOwnFold * kFoldChunk * 4;
     return pass_list_bytes(Smax) + u;
 }
 
@@ -926,13 +909,11 @@ __host__ __device__ inline size_t pass_smem(int Smax)
 // is the CTA's rank in its cluster and every CTA of a cluster reads the same
 // slot.  The slot's state is read by every CTA before the first barrier and
 // changed only by rank 0 after the last one, so all CTAs of a cluster take
-// the same path through the barriers, and none leaves while another may
-// still read its shared memory.
+// the same path through the barriers.
 __global__ void __cluster_dims__(kPassCluster, 1, 1) __launch_bounds__(kPassBlock, kPassMinBlocks)
     k_pass_slots(Slot *slots, SolveConsts C, int32_t *nactive)
 {
     extern __shared__ __align__(16) unsigned long long s_dyn[];
-    __shared__ __align__(16) int8_t s_fx[kOwnCount * 1024];
     Slot &s = slots[blockIdx.y];
     const int rank = blockIdx.x, tid = threadIdx.x;
     const int mode = s.mode;
@@ -1009,7 +990,7 @@ __global__ void __cluster_dims__(kPassCluster, 1, 1) __launch_bounds__(kPassBloc
     for (int c = rank; c * 1024 < n; c += kPassCluster)
         count_bs_core(P, s.spins, s.W0, s_elite, k, canon, corr ? C.corr_num : C.fix_num,
                       corr ? C.corr_den : C.fix_den, s.counts, s.fixed, &s.nfixed, s.fmap, orig, c,
-                      *reinterpret_cast<CountSmem *>(s_reg), s_fx + (c / kPassCluster) * 1024);
+                      *reinterpret_cast<CountSmem *>(s_reg));
     pass_barrier();
     // 3. stall rule: nothing fixed in an ISPVAR phase fixes the lowest-index spin
     //    to its value in the best elite sample, so that every phase makes progress
@@ -1018,23 +999,21 @@ __global__ void __cluster_dims__(kPassCluster, 1, 1) __launch_bounds__(kPassBloc
             const int8_t v = (s.spins[(size_t)s_elite[0] * s.W0] & 1u) ? 1 : -1;
             s.fixed[0] = v;
             s.fmap[orig[0]] = v;
-            s_fx[0] = v;  // spin 0 is in this CTA's first count chunk
         }
         pass_barrier();
     }
-    uint32_t *s_npos = reinterpret_cast<uint32_t *>(s_reg);  // the count's counters are dead
     const int nch = max(1, (n + kFoldChunk - 1) / kFoldChunk);
     // this CTA's chunks rank, rank + kPassCluster, ..., two at a time in the gather stages
     for (int c = rank; c < nch; c += 2 * kPassCluster) {
         const int ch[2] = {c, c + kPassCluster < nch ? c + kPassCluster : -1};
-        fold_count<2>(s, ch, s_fx);
+        fold_count<2>(s, ch);
     }
     pass_barrier();
-    for (int c = rank; c < nch; c += kPassCluster) fold_index(s, c, s_fx, s_npos);
+    for (int c = rank; c < nch; c += kPassCluster) fold_index(s, c);
     pass_barrier();
     for (int c = rank; c < nch; c += 2 * kPassCluster) {
         const int ch[2] = {c, c + kPassCluster < nch ? c + kPassCluster : -1};
-        fold_fill<2>(s, ch, s_npos);
+        fold_fill<2>(s, ch);
     }
     pass_barrier();
     // 4. the phase transition

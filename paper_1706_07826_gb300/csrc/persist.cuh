@@ -309,7 +309,6 @@ __device__ __forceinline__ void count_core(const DevProb *P, const uint32_t *spi
 // operations per plane and row).  The warps' counters are then summed by a
 // bit-sliced ripple adder and each spin's count read off its planes.
 // Results as count_core.  NB: planes per warp (2^NB > rows per warp).
-// fixed_copy (optional, shared memory): the chunk's 1024 fixings (0 past n).
 constexpr int kCountWarps = kCountBlock / 32;
 constexpr int kCountPlanes = 12;  // 2^12 > 16384 / kCountWarps rows per warp
 // Shared memory of one count chunk (callers place it, so the multi-start pass
@@ -362,7 +361,7 @@ __device__ __forceinline__ void count_planes(const uint32_t *spins, int W, const
 __device__ __forceinline__ void count_bs_core(const DevProb *P, const uint32_t *spins, int W, const int32_t *elite,
                                               int k, int canon, int fix_num, int fix_den, int32_t *counts,
                                               int8_t *fixed, int32_t *nfixed, int8_t *fmap, const int32_t *orig,
-                                              int chunk, CountSmem &sm, int8_t *fixed_copy = nullptr)
+                                              int chunk, CountSmem &sm)
 {
     uint32_t(*s_planes)[kCountPlanes + 3][32] = sm.planes;
     uint32_t(*s_tot)[32] = sm.tot;
@@ -424,7 +423,6 @@ __device__ __forceinline__ void count_bs_core(const DevProb *P, const uint32_t *
                 fixed[i] = v;
                 if (v && fmap) fmap[oi[u]] = v;
             }
-            if (fixed_copy) fixed_copy[sp] = v;  // the chunk's fixings, also in shared memory
             const unsigned ball = __ballot_sync(0xFFFFFFFFu, v != 0);
             if ((threadIdx.x & 31) == 0 && ball) atomicAdd(nfixed, __popc(ball));
         }
