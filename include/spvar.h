@@ -435,9 +435,23 @@ int spvar_plan_run(spvar_plan *plan, const uint64_t *seeds, const spvar_result *
 
 void spvar_plan_destroy(spvar_plan *plan);
 
-/* Convenience: plan_create + plan_run + plan_destroy for one problem. */
+/* Convenience: plan_create + plan_run for one problem.  The plan is kept
+ * after the call and reused by a later call whose problem has the same
+ * structure (n, nnz, capacities, degree bound, dmax, energy scale, colour
+ * class sizes, coupler kind) and whose parameters are byte-for-byte the same:
+ * that call skips plan creation (workspace allocation, autotuning lookup,
+ * graph capture) and runs the kept plan on its own problem's data, with
+ * results identical to a fresh plan.  At most 4 plans are kept, each holding
+ * at most 256 MB of device memory (larger ones are freed after the call);
+ * spvar_solve_cache_release frees them.  Safe to call from several threads
+ * (a kept plan serves one call at a time).
+ * Errors: as spvar_plan_create and spvar_plan_run. */
 int spvar_solve(const spvar_problem *p, const spvar_params *prm, uint64_t seed,
                 const spvar_result *res, void *stream);
+
+/* Frees every plan spvar_solve keeps (their device memory and graphs).  Call
+ * it with no spvar_solve in flight, e.g. before freeing the device. */
+void spvar_solve_cache_release(void);
 
 /* Work statistics of the last plan_run: spin-flip attempts (sum over
  * phases of samples x sweeps x free spins) and phases executed. */

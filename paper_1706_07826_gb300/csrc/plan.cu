@@ -14,6 +14,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <list>
 #include <map>
 #include <mutex>
 #include <new>
@@ -149,6 +150,67 @@ struct TuneKey {
 };
 std::map<TuneKey, SweepShape> g_tune_cache;
 std::mutex g_tune_mu;
+
+void plan_free(spvar_plan *pl);
+
+// Plans spvar_solve keeps between calls, most recent first.  A plan depends on
+// its problem only through the fields in solve_key (sizes, capacities, colour
+// classes, coupler kind, dmax and scale decide its workspace, tables and
+// sweep shape); the problem's own data is read on the device through the
+// starts' problem pointers, which are rebound before each run.  A plan is
+// taken out of the cache while it runs, so concurrent calls never share one.
+constexpr size_t kSolveCacheMax = 4;
+constexpr size_t kSolveCacheBytes = size_t(256) << 20;  // larger workspaces are freed after the call
+std::list<std::pair<std::vector<int64_t>, spvar_plan *>> g_solve_cache;
+std::mutex g_solve_mu;
+
+void solve_key(const Problem *P, const spvar_params &prm, std::vector<int64_t> &key)
+{
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const DevProb &H = P->hdr;
+    key = {dev, H.n, H.nnz, H.cap_n, H.cap_nnz, H.maxdeg, H.dmax, H.scale, H.ncol, H.pm1, H.ujs, H.hzero,
+           P->jabs_max};
+    for (int c = 0; c < H.ncol && c < kMaxColours; ++c) key.push_back(P->csize[c]);
+    // the parameters bytewise (padding included: a mismatch there only misses the cache)
+    unsigned char raw[sizeof(spvar_params)];
+    std::memcpy(raw, &prm, sizeof(prm));
+    for (size_t i = 0; i < sizeof(raw); i += 8) {
+        int64_t w = 0;
+        std::memcpy(&w, raw + i, std::min<size_t>(8, sizeof(raw) - i));
+        key.push_back(w);
+    }
+}
+
+spvar_plan *solve_cache_take(const std::vector<int64_t> &key)
+{
+    std::lock_guard<std::mutex> g(g_solve_mu);
+    for (auto it = g_solve_cache.begin(); it != g_solve_cache.end(); ++it)
+        if (it->first == key) {
+            spvar_plan *pl = it->second;
+            g_solve_cache.erase(it);
+            return pl;
+        }
+    return nullptr;
+}
+
+void solve_cache_put(std::vector<int64_t> key, spvar_plan *pl)
+{
+    if (pl->ws_bytes > kSolveCacheBytes) {
+        plan_free(pl);
+        return;
+    }
+    spvar_plan *evict = nullptr;
+    {
+        std::lock_guard<std::mutex> g(g_solve_mu);
+        g_solve_cache.emplace_front(std::move(key), pl);
+        if (g_solve_cache.size() > kSolveCacheMax) {
+            evict = g_solve_cache.back().second;
+            g_solve_cache.pop_back();
+        }
+    }
+    if (evict) plan_free(evict);
+}
 
 int grid_for(const spvar_plan *pl, int items)
 {
@@ -1010,13 +1072,37 @@ void spvar_plan_destroy(spvar_plan *plan) { plan_free(plan); }
 int spvar_solve(const spvar_problem *p, const spvar_params *prm, uint64_t seed, const spvar_result *res,
                 void *stream)
 {
-    spvar_plan *pl = nullptr;
-    const spvar_problem *arr[1] = {p};
-    int rc = spvar_plan_create(arr, 1, prm, 0, stream, &pl);
-    if (rc) return rc;
-    rc = spvar_plan_run(pl, &seed, res, stream);
-    plan_free(pl);
+    if (!p || !prm) return SPVAR_EINVAL;
+    const Problem *P = reinterpret_cast<const Problem *>(p);
+    std::vector<int64_t> key;
+    solve_key(P, *prm, key);
+    spvar_plan *pl = solve_cache_take(key);
+    if (pl) {
+        // a plan built for a problem of the same structure: point its starts at this one
+        pl->probs[0] = P;
+        for (Slot &S : pl->h_slots) {
+            S.orig_prob = P->dev;
+            S.cur = P->dev;
+        }
+    } else {
+        const spvar_problem *arr[1] = {p};
+        const int rc = spvar_plan_create(arr, 1, prm, 0, stream, &pl);
+        if (rc) return rc;
+    }
+    const int rc = spvar_plan_run(pl, &seed, res, stream);
+    if (rc == SPVAR_OK) solve_cache_put(std::move(key), pl);
+    else plan_free(pl);
     return rc;
+}
+
+void spvar_solve_cache_release(void)
+{
+    std::list<std::pair<std::vector<int64_t>, spvar_plan *>> drop;
+    {
+        std::lock_guard<std::mutex> g(g_solve_mu);
+        drop.swap(g_solve_cache);
+    }
+    for (auto &e : drop) plan_free(e.second);
 }
 
 }  // extern "C"

@@ -111,6 +111,8 @@ def lib():
         L.spvar_plan_stats.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i32)]
         L.spvar_plan_sweeps_per_launch.argtypes = [vp, ctypes.POINTER(i32)]
         L.spvar_solve.argtypes = [vp, ctypes.POINTER(Params), u64, ctypes.POINTER(Result), vp]
+        L.spvar_solve_cache_release.argtypes = []
+        L.spvar_solve_cache_release.restype = None
         L.spvar_plan_set_profiling.argtypes = [vp, i32]
         L.spvar_plan_sweep_time.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i32)]
         L.spvar_plan_shape.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32),
@@ -558,6 +560,12 @@ def solve(problem, params, seed, device=False, stream=None):
     _check(lib().spvar_solve(problem.handle, ctypes.byref(params), int(seed), ctypes.byref(res), _stream(stream)),
            "spvar_solve")
     return out
+
+
+def solve_cache_release():
+    """Free the plans that solve() keeps for later calls on problems of the
+    same structure with the same parameters."""
+    lib().spvar_solve_cache_release()
 
 
 def unpack_spins(words, n):

@@ -376,3 +376,57 @@ def test_sweeps_per_launch_rejected_with_sqa(cuda_lib):
     with pytest.raises(spvar.SpvarError) as e:
         spvar.Plan([gpu_problem(I.chimera(2, 1))], prm)
     assert e.value.code == spvar.EINVAL
+
+
+def test_solve_keeps_and_rebinds_its_plan(cuda_lib):
+    """spvar_solve keeps its plan for problems of the same structure: problems
+    with the same graph but other couplers, solved in turn (and a problem of
+    another structure in between), each give the oracle's result; so do
+    solves after the kept plans are released."""
+    from paper_1706_07826_gb300 import spvar
+    T, seed = 40, 77
+    kw = dict(num_starts=2, fixing_sample_size=48, solving_sample_size=24, elite_threshold=0.2)
+    prm = spvar.make_params(num_sweeps=T, **kw)
+    same = [I.chimera(4, 1201), I.chimera(4, 1202), I.chimera(4, 1203)]
+    other = I.cubic3d(5, 1204)
+    refs = {id(x): _oracle_solve(x, T, seed, **kw) for x in same + [other]}
+    spvar.solve_cache_release()
+    for x in same + [other] + same[::-1]:
+        out = spvar.solve(gpu_problem(x), prm, seed)
+        _check(out, refs[id(x)], 2, 2, x.n)
+    spvar.solve_cache_release()
+    out = spvar.solve(gpu_problem(same[1]), prm, seed)
+    _check(out, refs[id(same[1])], 2, 2, same[1].n)
+    spvar.solve_cache_release()
+
+
+def test_solve_from_several_threads(cuda_lib):
+    """Concurrent spvar_solve calls on problems of one structure: each call
+    takes a kept plan for itself (or builds one), results as the oracle's."""
+    import threading
+    from paper_1706_07826_gb300 import spvar
+    T, seed = 30, 91
+    kw = dict(num_starts=2, fixing_sample_size=40, solving_sample_size=20, elite_threshold=0.2)
+    prm = spvar.make_params(num_sweeps=T, **kw)
+    insts = [I.chimera(3, 1300 + i) for i in range(6)]
+    refs = [_oracle_solve(x, T, seed, **kw) for x in insts]
+    probs = [gpu_problem(x) for x in insts]
+    outs = [None] * len(insts)
+    errs = []
+
+    def work(i):
+        try:
+            for _ in range(3):
+                outs[i] = spvar.solve(probs[i], prm, seed)
+        except Exception as e:  # reported below
+            errs.append(e)
+
+    th = [threading.Thread(target=work, args=(i,)) for i in range(len(insts))]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    assert not errs, errs
+    for i, x in enumerate(insts):
+        _check(outs[i], refs[i], 2, 2, x.n)
+    spvar.solve_cache_release()
