@@ -221,23 +221,29 @@ int host_problem_upload(const HostProblem &hp, void *blob, cudaStream_t st, DevP
     DevProb H = hp.hdr;
     prob_carve(&H, blob, hp.cap_n, hp.cap_nnz, hp.md);
     const int n = H.n, nnz = H.nnz;
-    bool ok = true;
-    auto up = [&](void *dst, const void *src, size_t bytes) {
-        if (bytes && ok) ok = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st) == cudaSuccess;
-    };
     *hdr_out = H;
-    up(blob, hdr_out, sizeof(DevProb));
-    up(H.row_ptr, hp.row_ptr.data(), 4 * ((size_t)n + 1));
-    up(H.col, hp.col.data(), 4 * (size_t)nnz);
-    up(H.val, hp.val.data(), 4 * (size_t)nnz);
-    up(H.h, hp.h.data(), 4 * (size_t)n);
-    up(H.colour, hp.colour.data(), 4 * (size_t)n);
-    up(H.cptr, hp.cptr.data(), 4 * hp.cptr.size());
-    up(H.idx_of_pos, hp.idx_of_pos.data(), 4 * (size_t)n);
-    up(H.pos_of_idx, hp.pos_of_idx.data(), 4 * (size_t)n);
-    up(H.meta, hp.meta.data(), 4 * (size_t)n);
-    up(H.ell, hp.ell.data(), 4 * hp.ell.size());
-    return ok ? SPVAR_OK : SPVAR_ECUDA;
+    // the blob's image on the host (header with device pointers, then every array at
+    // its offset), sent with one copy
+    const size_t bytes = prob_blob_bytes(hp.cap_n, hp.cap_nnz, hp.md);
+    std::vector<char> img(bytes, 0);
+    char *const base = static_cast<char *>(blob);
+    auto put = [&](const void *dst, const void *src, size_t nb) {
+        if (nb) std::memcpy(img.data() + (static_cast<const char *>(dst) - base), src, nb);
+    };
+    put(blob, hdr_out, sizeof(DevProb));
+    put(H.row_ptr, hp.row_ptr.data(), 4 * ((size_t)n + 1));
+    put(H.col, hp.col.data(), 4 * (size_t)nnz);
+    put(H.val, hp.val.data(), 4 * (size_t)nnz);
+    put(H.h, hp.h.data(), 4 * (size_t)n);
+    put(H.colour, hp.colour.data(), 4 * (size_t)n);
+    put(H.cptr, hp.cptr.data(), 4 * hp.cptr.size());
+    put(H.idx_of_pos, hp.idx_of_pos.data(), 4 * (size_t)n);
+    put(H.pos_of_idx, hp.pos_of_idx.data(), 4 * (size_t)n);
+    put(H.meta, hp.meta.data(), 4 * (size_t)n);
+    put(H.ell, hp.ell.data(), 4 * hp.ell.size());
+    // a copy from pageable memory returns once the source is staged, so img may go
+    return cudaMemcpyAsync(blob, img.data(), bytes, cudaMemcpyHostToDevice, st) == cudaSuccess ? SPVAR_OK
+                                                                                               : SPVAR_ECUDA;
 }
 
 }  // namespace spvar
