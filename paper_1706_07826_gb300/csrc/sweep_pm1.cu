@@ -28,8 +28,11 @@
 // (weak-strong cluster problems: every |J| = 100): the byte-wise neighbour sum
 // is the same, the local field is h + J0 (2x - deg), and the flip-cost index
 // 16 (dE/2 + bias) of two replicas at a time is formed in 16-bit lanes; the
-// two acceptance rows (2 dmax + 2 entries) are interleaved in dynamic shared
-// memory.  Needs dmax <= 4094.  With SI (small integer couplers, every
+// two acceptance rows (2 bias + 1 entries each, rounded up to 16) are in
+// dynamic shared memory with entry i at slot i ^ ((i >> 4) & 15): the indices
+// a warp reads differ by multiples of the coupler magnitude (100 for the
+// weak-strong problems), which in a plain layout put most of them on one or
+// two banks.  Needs dmax <= 4094.  With SI (small integer couplers, every
 // |J| <= 15: the reduced-degeneracy problems of Sec. III.C) the byte-wise sum
 // is weighted, X = sum_j |J_ij| b'_j <= 120 per byte with the magnitudes packed
 // four bits per neighbour in one register, and the local field is
@@ -120,6 +123,12 @@ struct Pm1Smem {
     int cptr[kMaxColours + 1];
 };
 
+// SCALED acceptance rows: row length (2 bias + 1 rounded up to 16 entries) and
+// the slot of entry i, a bijection on every aligned block of 16 slots that
+// spreads indices with the same low bits over the 16 bank pairs.
+__device__ __forceinline__ int row_len(int bias) { return (2 * bias + 16) & ~15; }
+__device__ __forceinline__ int row_slot(int i) { return i ^ ((i >> 4) & 15); }
+
 // One sweep over the slots, reading threshold row PAR.  Every lane runs every
 // slot (lanes without an item anneal the dummy word: no branch per slot); a
 // barrier precedes slot j when it starts a new colour class (bit j of
@@ -137,14 +146,16 @@ __device__ __forceinline__ void sweep_once(Pm1Smem<B, NSLOT> &sm, unsigned long 
     constexpr uint32_t kInv = 4u * (uint32_t)Pm1Smem<B, NSLOT>::KW;  // byte distance to the inverted copy
     // next sweep's row (its buffer was last read in the previous sweep)
     if (SCALED) {
-        if (next_src)
+        if (next_src) {
+            unsigned long long *nrow = drow + (PAR ^ 1) * row_len(bias);
             for (int e = (int)threadIdx.x + 1; e <= bias; e += B)
-                drow[2 * (bias + e) + (PAR ^ 1)] = (1ull << 32) - (unsigned long long)next_src[2 * e];
+                nrow[row_slot(bias + e)] = (1ull << 32) - (unsigned long long)next_src[2 * e];
+        }
     } else if (next_src && (int)threadIdx.x < bias) {
         const int e = (int)threadIdx.x + 1;
         sm.row[PAR ^ 1][bias + e] = (1ull << 32) - (unsigned long long)next_src[2 * e];
     }
-    const char *rowb = SCALED ? reinterpret_cast<const char *>(drow) + 8 * PAR
+    const char *rowb = SCALED ? reinterpret_cast<const char *>(drow + PAR * row_len(bias))
                               : reinterpret_cast<const char *>(sm.row[PAR]);
 #pragma unroll
     for (int j = 0; j < NSLOT; ++j) {
@@ -169,10 +180,14 @@ __device__ __forceinline__ void sweep_once(Pm1Smem<B, NSLOT> &sm, unsigned long 
                 const uint32_t al = mad_lo(xl, s[j].tj, s[j].c0), ah = mad_lo(xh, s[j].tj, s[j].c0);
                 const uint32_t bl = mad_lo(al, 0u - one, k16), bh = mad_lo(ah, 0u - one, k16);
                 const uint32_t kl = (al & ~ml) | (bl & ml), kh = (ah & ~mh) | (bh & mh);
-                off[0] = kl & 0xFFFFu;
-                off[1] = kh & 0xFFFFu;
-                off[2] = kl >> 16;
-                off[3] = kh >> 16;
+                // byte offsets 8 row_slot(i) of both lanes: 16 i halved, bits 4..7 of i
+                // xor-ed into bits 0..3 (16 i < 2^16, so no bit crosses a lane)
+                const uint32_t ol = (kl >> 1) ^ ((kl >> 5) & 0x00780078u);
+                const uint32_t oh = (kh >> 1) ^ ((kh >> 5) & 0x00780078u);
+                off[0] = ol & 0xFFFFu;
+                off[1] = oh & 0xFFFFu;
+                off[2] = ol >> 16;
+                off[3] = oh >> 16;
             } else {
                 // the flip-cost index dE/2 + bias is 2x + bias - deg + h if b_i = 0 and its
                 // mirror 2 bias - that if b_i = 1; all scaled by 8 (the byte offset of a
@@ -253,13 +268,14 @@ __device__ void run_item_pm1(const SweepLaunch &L, const SweepJob &job, int quad
     }
     // threshold rows: entry i = 2^32 - thr[t][2 (i - bias)] for i > bias, 0 (always accept) otherwise
     if (SCALED) {
-        // two rows interleaved: entry i of row par at 2 i + par
-        for (int x = tid; x < 2 * (2 * bias + 1); x += B) {
-            const int par = x & 1, e = (x >> 1) - bias;
+        // row par holds entry i at par * row_len + row_slot(i)
+        const int rl = row_len(bias);
+        for (int x = tid; x < 2 * rl; x += B) {
+            const int par = x >= rl, i = x - par * rl, e = i - bias;
             unsigned long long v = 0;
-            if (e > 0 && par == (t0 & 1) && t0 < T)
+            if (e > 0 && i <= 2 * bias && par == (t0 & 1) && t0 < T)
                 v = (1ull << 32) - (unsigned long long)L.thr[(size_t)t0 * L.thr_stride + 2 * e];
-            drow[x] = v;
+            drow[par * rl + row_slot(i)] = v;
         }
     } else {
         for (int i = tid; i < 2 * kRowE; i += B) {
@@ -420,8 +436,12 @@ void *select_kernel(int block, int nslot, int maxd, int mode)
 
 bool pm1_shape_ok(int block, int nslot, int maxd, int mode) { return select_kernel(block, nslot, maxd, mode) != nullptr; }
 
-// SCALED: two interleaved rows of thr_stride (= dmax + 1 >= 2 bias + 1) 64-bit entries.
-size_t pm1_smem_bytes(bool scaled, int thr_stride) { return scaled ? 2 * 8 * (size_t)thr_stride : 0; }
+// SCALED: two rows of 64-bit entries, each at most thr_stride (= dmax + 1 >= 2 bias + 1)
+// rounded up to 16.
+size_t pm1_smem_bytes(bool scaled, int thr_stride)
+{
+    return scaled ? 2 * 8 * (size_t)((thr_stride + 15) & ~15) : 0;
+}
 
 cudaError_t launch_sweep_pm1(const SweepLaunch &L, int block, int nslot, int maxd, int mode, int grid,
                              size_t smem, cudaStream_t st)
