@@ -422,6 +422,9 @@ __global__ void __launch_bounds__(kBigBlock)
     }
 }
 
+// The per-step kernels of the persistence pass, one CTA per start, used when
+// tree pre-processing follows each fold/compact (k_pass_slots does all of it
+// otherwise).
 // Elite sample of each active start; also keeps the start's best assignment
 // (lifted to the original variables through its fix map).
 __global__ void __launch_bounds__(kBigBlock) k_elite_slots(Slot *slots, SolveConsts C)
