@@ -430,3 +430,32 @@ def test_solve_from_several_threads(cuda_lib):
     for i, x in enumerate(insts):
         _check(outs[i], refs[i], 2, 2, x.n)
     spvar.solve_cache_release()
+
+
+LARGE_ELITE_CASES = [
+    # name, instance, T, S_fix, S_solve, elite: every case has k > 512, where the elite's
+    # candidates (at least k) exceed the rank placement's 512 and the full sort runs
+    # inside the persistence pass
+    ("ferromagnet_C2_ties", lambda: _ferromagnet(I.chimera(2, 1601)), 80, 1500, 300, 0.6),
+    ("random_16_S8192", lambda: I.random_graph(16, 30, 1602, jmax=2, hmax=1), 30, 8192, 64, 0.1),
+    ("random_8_S16384_max", lambda: I.random_graph(8, 12, 1603, jmax=2, hmax=0), 20, 16384, 32, 0.1),
+]
+
+
+def _ferromagnet(inst):
+    inst.J = -np.ones_like(inst.J)
+    return inst
+
+
+@pytest.mark.parametrize("name,make,T,Sf,Ss,elite", LARGE_ELITE_CASES, ids=[c[0] for c in LARGE_ELITE_CASES])
+def test_persistence_pass_with_large_elites(cuda_lib, name, make, T, Sf, Ss, elite):
+    """The fused persistence pass with elites larger than 512 samples (heavily
+    tied energies; sample counts up to the library's maximum, the pass's
+    largest shared-memory layout): identical to the oracle."""
+    from paper_1706_07826_gb300 import spvar
+    inst = make()
+    seed = 5150
+    kw = dict(num_starts=2, fixing_sample_size=Sf, solving_sample_size=Ss, elite_threshold=elite)
+    ref = _oracle_solve(inst, T, seed, **kw)
+    out = spvar.solve(gpu_problem(inst), spvar.make_params(num_sweeps=T, **kw), seed)
+    _check(out, ref, 2, 2, inst.n)
