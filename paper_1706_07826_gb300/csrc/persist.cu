@@ -552,9 +552,9 @@ __global__ void __launch_bounds__(kBigBlock) k_reduce_slots(Slot *slots, SolveCo
 // ------------------------------------------- the persistence pass, fused (Alg. 1)
 // After a start's sample is complete, one thread-block cluster of
 // kPassCluster CTAs runs the whole of Alg. 1 for it in one launch:
-//   1. elite sample (every CTA selects it itself: a few thousand energies,
-//      read from L2, and the list is in its own shared memory with no
-//      barrier), and the start's best assignment;
+//   1. elite sample (rank 0 selects it; every other CTA finds only the best
+//      sample and, after the first barrier, copies rank 0's list from its
+//      shared memory over the cluster), and the start's best assignment;
 //   2. persistence counts and the fixing rule, 1024 spins per count chunk;
 //   3. the stall rule (ISPVAR), then the update of J and h spread over chunks
 //      of kFoldChunk spins:
@@ -566,7 +566,9 @@ __global__ void __launch_bounds__(kBigBlock) k_reduce_slots(Slot *slots, SolveCo
 //        fold_fill   CSR columns and values and the ELL layout of the free spins;
 //   4. the phase transition and the count of active starts.
 // Chunks are dealt to the cluster's CTAs round-robin, and a cluster barrier
-// stands where one stage reads what another CTA wrote in the stage before.  A
+// stands where one stage reads what another CTA wrote in the stage before.
+// Each stage issues its global loads for all of a CTA's chunks (up to two,
+// or kIndexBatch for the index stage) before it uses any of them.  A
 // neighbour's fixing, and then its new index and position packed in one word,
 // are single global loads; these per-start arrays (n bytes and 4n bytes) stay
 // in L1 and L2, which measured faster than reading them from the owning CTA's
@@ -575,7 +577,8 @@ __global__ void __launch_bounds__(kBigBlock) k_reduce_slots(Slot *slots, SolveCo
 // order, couplers between free spins keep theirs, colour classes are inherited.
 constexpr int kPassCluster = 8;
 constexpr int kPassBlock = kFoldChunk;  // one spin per thread in a fold chunk
-constexpr int kFoldGather = 4;          // CSR entries of each row a thread loads at once
+constexpr int kFoldGather = 6;          // CSR entries of each row a thread loads at once
+constexpr int kIndexBatch = 4;          // fold chunks a CTA indexes after one round of loads
 // Four resident CTAs per SM (64 registers): 64 starts (512 CTAs) run in one wave.
 constexpr int kPassMinBlocks = 4;
 static_assert(kPassBlock == kCountBlock, "the count chunks run on the pass CTAs");
@@ -717,49 +720,68 @@ __device__ __forceinline__ void fold_count(Slot &s, const int (&ch)[G])
 
 constexpr int kScanCols = 6;  // colour classes ranked per multi-value scan
 
-__device__ __forceinline__ void fold_index(Slot &s, int chunk)
+// Chunks ch[0..CB) of the CTA (-1: none).  The spins' own values and the
+// table of chunk totals are loaded once for all of them, so the chunks' scans
+// follow one another without a global load in between.
+template <int CB>
+__device__ __forceinline__ void fold_index(Slot &s, const int (&ch)[CB])
 {
     __shared__ int s_w[32 * (2 + kScanCols)];
-    __shared__ int s_base_cls[kMaxColours], s_tot_cls[kMaxColours], s_cptr[kMaxColours + 1];
-    __shared__ int s_base[2], s_tot[2], s_hnz;
+    __shared__ int s_base_cls[CB][kMaxColours], s_tot_cls[kMaxColours], s_cptr[kMaxColours + 1];
+    __shared__ int s_base[CB][2], s_tot[2], s_hnz;
     const DevProb *P = s.cur;
     DevProb *D = s.buf[s.next];
     const int n = P->n, cap = P->cap_n, ncol = P->ncol, tid = threadIdx.x;
-    const int i0 = chunk * kFoldChunk;
-    if (chunk > 0 && i0 >= n) return;  // chunk 0 writes the header, even for n = 0
     const int nch = (n + kFoldChunk - 1) / kFoldChunk;
     const int32_t *tab = s.scratch + fold_table_offset(cap);
-    // the spin's own values first (they do not wait for the table)
-    const int i = i0 + tid;
-    const bool valid = i < n;
+    // a chunk takes part if it holds spins; chunk 0 also writes the header, even for n = 0
+    bool on[CB];
+#pragma unroll
+    for (int b = 0; b < CB; ++b) on[b] = ch[b] >= 0 && (ch[b] == 0 || ch[b] * kFoldChunk < n);
+    // the spins' own values first (they do not wait for the table)
     const int32_t *rowcnt = s.scratch + cap, *hfold = s.scratch + 2 * cap;
     const int32_t *orig = s.orig[s.ocur];
-    const bool f = valid && s.fixed[i] == 0;
-    const int rc = valid ? rowcnt[i] : 0, colv = valid ? P->colour[i] : -1;
-    const int h = valid ? hfold[i] : 0, oi = valid ? orig[i] : 0;
-    // offsets of this chunk (totals of the chunks before it) and the totals of all:
+    bool f[CB], valid[CB];
+    int rc[CB], colv[CB], h[CB], oi[CB];
+#pragma unroll
+    for (int b = 0; b < CB; ++b) {
+        const int i = ch[b] * kFoldChunk + tid;
+        valid[b] = on[b] && i < n;
+        f[b] = valid[b] && s.fixed[i] == 0;
+        rc[b] = valid[b] ? rowcnt[i] : 0;
+        colv[b] = valid[b] ? P->colour[i] : -1;
+        h[b] = valid[b] ? hfold[i] : 0;
+        oi[b] = valid[b] ? orig[i] : 0;
+    }
+    // offsets of each chunk (totals of the chunks before it) and the totals of all:
     // field f (0 free spins, 1 free-free entries, 2 + c spins of class c) summed by a warp
     {
         const int lane = tid & 31, warp = tid >> 5;
         for (int fld = warp; fld < 3 + ncol; fld += kPassBlock / 32) {
             const int fo = fld < 3 ? fld : 6 + (fld - 3);  // table column (2: nonzero-bias flag)
-            int b = 0, t = 0;
+            int bs[CB], t = 0;
+#pragma unroll
+            for (int b = 0; b < CB; ++b) bs[b] = 0;
             for (int q = lane; q < nch; q += 32) {
                 const int v = tab[q * kFoldStride + fo];
                 t += fld == 2 ? (v != 0) : v;
-                b += q < chunk ? v : 0;
+#pragma unroll
+                for (int b = 0; b < CB; ++b) bs[b] += q < ch[b] ? v : 0;
             }
-            b = __reduce_add_sync(0xFFFFFFFFu, b);
+#pragma unroll
+            for (int b = 0; b < CB; ++b) bs[b] = __reduce_add_sync(0xFFFFFFFFu, bs[b]);
             t = __reduce_add_sync(0xFFFFFFFFu, t);
             if (lane == 0) {
                 if (fld < 2) {
-                    s_base[fld] = b;
                     s_tot[fld] = t;
+#pragma unroll
+                    for (int b = 0; b < CB; ++b) s_base[b][fld] = bs[b];
                 } else if (fld == 2) {
                     s_hnz = t;
                 } else {
-                    s_base_cls[fld - 3] = b;
                     s_tot_cls[fld - 3] = t;
+#pragma unroll
+                    for (int b = 0; b < CB; ++b) s_base_cls[b][fld - 3] = bs[b];
                 }
             }
         }
@@ -774,8 +796,8 @@ __device__ __forceinline__ void fold_index(Slot &s, int chunk)
         s_cptr[ncol] = c0;
     }
     __syncthreads();
-    if (chunk == 0 && tid <= ncol) D->cptr[tid] = s_cptr[tid];
-    if (chunk == 0 && tid == 0) {
+    if (ch[0] == 0 && tid <= ncol) D->cptr[tid] = s_cptr[tid];
+    if (ch[0] == 0 && tid == 0) {
         const int m = s_tot[0], nnz2 = s_tot[1];
         D->n = m;
         D->nnz = nnz2;
@@ -790,16 +812,19 @@ __device__ __forceinline__ void fold_index(Slot &s, int chunk)
                     (long long)*reinterpret_cast<const unsigned long long *>(tab + kFoldMaxChunks * kFoldStride);
         D->row_ptr[m] = nnz2;
     }
-    if (i0 < n) {
-        int32_t *orig2 = s.orig[s.ocur ^ 1];
-        const int col = f ? colv : -1;
+    int32_t *orig2 = s.orig[s.ocur ^ 1];
+#pragma unroll
+    for (int b = 0; b < CB; ++b) {
+        if (!on[b] || ch[b] * kFoldChunk >= n) continue;  // uniform over the CTA
+        const int i = ch[b] * kFoldChunk + tid;
+        const int col = f[b] ? colv[b] : -1;
         // new index, row pointer and rank among the chunk's free spins of the same
         // colour class: one multi-value scan per group of kScanCols classes
         int exf = 0, exr = 0, rank = 0;
         for (int cb = 0; cb < max(ncol, 1); cb += kScanCols) {
             int v[2 + kScanCols], ex[2 + kScanCols], tot[2 + kScanCols];
-            v[0] = cb == 0 && f ? 1 : 0;
-            v[1] = cb == 0 && f ? rc : 0;
+            v[0] = cb == 0 && f[b] ? 1 : 0;
+            v[1] = cb == 0 && f[b] ? rc[b] : 0;
 #pragma unroll
             for (int q = 0; q < kScanCols; ++q) v[2 + q] = col == cb + q ? 1 : 0;
             block_scan_multi<2 + kScanCols>(v, ex, tot, s_w);
@@ -809,23 +834,23 @@ __device__ __forceinline__ void fold_index(Slot &s, int chunk)
             }
 #pragma unroll
             for (int q = 0; q < kScanCols; ++q)
-                if (col == cb + q) rank = s_base_cls[col] + ex[2 + q];
+                if (col == cb + q) rank = s_base_cls[b][col] + ex[2 + q];
         }
-        const int a = s_base[0] + exf;
-        const int pos = f ? s_cptr[col] + rank : 0;
-        if (valid) npos_of(s)[i] = f ? (uint32_t)a | ((uint32_t)pos << 16) : ~0u;
-        if (f) {
+        const int a = s_base[b][0] + exf;
+        const int pos = f[b] ? s_cptr[col] + rank : 0;
+        if (valid[b]) npos_of(s)[i] = f[b] ? (uint32_t)a | ((uint32_t)pos << 16) : ~0u;
+        if (f[b]) {
             s.old_of_new[a] = i;
-            orig2[a] = oi;
-            D->h[a] = h;
+            orig2[a] = oi[b];
+            D->h[a] = h[b];
             D->colour[a] = col;
-            D->row_ptr[a] = s_base[1] + exr;
+            D->row_ptr[a] = s_base[b][1] + exr;
             D->pos_of_idx[a] = pos;
             D->idx_of_pos[pos] = a;
-            D->meta[pos] = ((uint32_t)(h & 0xFFFF) << 16) | (uint32_t)rc;
+            D->meta[pos] = ((uint32_t)(h[b] & 0xFFFF) << 16) | (uint32_t)rc[b];
         }
     }
-    __syncthreads();  // the shared offsets are rewritten by this CTA's next chunk
+    __syncthreads();  // the shared offsets are rewritten by this CTA's next chunks
 }
 
 template <int G>
@@ -850,15 +875,22 @@ __device__ __forceinline__ void fold_fill(Slot &s, const int (&ch)[G])
         D->rho = any ? (int)(npos[0x7FFFFFFF - (int)(best & 0xFFFFFFFFull)] & 0xFFFFu) : -1;
     }
     int p0[G], p1[G], q[G], pos[G], d[G];
+    uint32_t own[G];
+    // the spin's new index and position, and its row bounds (which do not wait for them)
 #pragma unroll
     for (int g = 0; g < G; ++g) {
         const int i = ch[g] * kFoldChunk + tid;
-        const uint32_t own = ch[g] >= 0 && i < n ? npos[i] : ~0u;  // free spins only
-        const bool free = own != ~0u;
-        p0[g] = free ? P->row_ptr[i] : 0;
-        p1[g] = free ? P->row_ptr[i + 1] : 0;
-        q[g] = free ? D->row_ptr[own & 0xFFFFu] : 0;
-        pos[g] = (int)(own >> 16);
+        const bool ok = ch[g] >= 0 && i < n;
+        own[g] = ok ? npos[i] : ~0u;  // ~0: fixed
+        p0[g] = ok ? P->row_ptr[i] : 0;
+        p1[g] = ok ? P->row_ptr[i + 1] : 0;
+    }
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+        const bool free = own[g] != ~0u;  // free spins only
+        if (!free) p1[g] = p0[g];
+        q[g] = free ? D->row_ptr[own[g] & 0xFFFFu] : 0;
+        pos[g] = (int)(own[g] >> 16);
         d[g] = 0;
     }
     int len = 0;
@@ -932,7 +964,9 @@ __global__ void __cluster_dims__(kPassCluster, 1, 1) __launch_bounds__(kPassBloc
     const int k = (mode == kFixing) ? (C.pticm ? elite_count_hd(C.elite, S) : C.k_fix)
                   : (mode == kCorr) ? C.k_corr : 1;
     const int64_t *e = s.rec_e + (size_t)s.phase * C.Smax;
-    elite_fast(e, S, k, s_elite, reinterpret_cast<unsigned long long *>(s_reg),
+    // rank 0 selects the whole elite, which the other CTAs copy from its shared
+    // memory after the barrier; they need only its best sample before it
+    elite_fast(e, S, rank == 0 ? k : 1, s_elite, reinterpret_cast<unsigned long long *>(s_reg),
                reinterpret_cast<int64_t *>(s_reg) + kEliteRankMax);
     const DevProb *P = s.cur;
     const int n = P->n;
@@ -961,6 +995,11 @@ __global__ void __cluster_dims__(kPassCluster, 1, 1) __launch_bounds__(kPassBloc
                                                     kFoldMaxChunks * kFoldStride) = 0ull;
     }
     pass_barrier();
+    if (rank != 0 && k > 1) {
+        const int32_t *r0 = cg::this_cluster().map_shared_rank(s_elite, 0);
+        for (int q = tid; q < k; q += kPassBlock) s_elite[q] = r0[q];
+        __syncthreads();
+    }
     if (better) {
         if (rank == 0 && tid == 0) *s.best_e = eb;
         const uint32_t *row = s.spins + (size_t)rbest * s.W0;
@@ -1012,7 +1051,12 @@ __global__ void __cluster_dims__(kPassCluster, 1, 1) __launch_bounds__(kPassBloc
         fold_count<2>(s, ch);
     }
     pass_barrier();
-    for (int c = rank; c < nch; c += kPassCluster) fold_index(s, c);
+    for (int c = rank; c < nch; c += kIndexBatch * kPassCluster) {
+        int ch[kIndexBatch];
+#pragma unroll
+        for (int b = 0; b < kIndexBatch; ++b) ch[b] = c + b * kPassCluster < nch ? c + b * kPassCluster : -1;
+        fold_index<kIndexBatch>(s, ch);
+    }
     pass_barrier();
     for (int c = rank; c < nch; c += 2 * kPassCluster) {
         const int ch[2] = {c, c + kPassCluster < nch ? c + kPassCluster : -1};

@@ -9,9 +9,11 @@
 // (spin k, quad group g): a thread loads its spin's neighbour word offsets
 // (the inverted copy folded in for J < 0), flip-cost constant and the Philox
 // products that depend only on the spin and the start once, then sweeps that
-// spin in every quad of its group, two quads at a time.  The Philox products
-// that depend only on the quad and the sweep come from a small per-CTA table
-// refreshed once per sweep, so an item pays 16 wide multiplies.  The flip-cost
+// spin in every quad of its group, two quads at a time; units left over for a
+// last partial round of the block are split over more threads (class_split).
+// The Philox products that depend only on the quad and the sweep come from a
+// small per-CTA table refreshed once per sweep, so an item pays 16 wide
+// multiplies.  The flip-cost
 // index of the four replicas is formed byte-wise (SWAR), pre-scaled to the
 // byte offset of a 64-bit carry entry (2^32 - thr, 0 where dE <= 0): u + entry
 // carries into bit 32 exactly when the move is rejected.
@@ -47,7 +49,36 @@ struct QuadSmem {
     uint2 qs[2][kQcap];                // per quad and sweep parity: M0 (hi(M1 q) ^ y ^ key0) (round 2, word 0)
     int e2[4 * kQcap];
     int cptr[kMaxColours + 1];
+    int4 split[kMaxColours];           // per colour class: G, full units, remainder units, their split
 };
+
+// How a colour class of nc spins is dealt over the block for nq quads.  Units
+// (spin, group g of quads g, g + G, ...) fill full rounds of B threads; the
+// units left for a last partial round are each split into G2 sub-units
+// (every G2-th quad of the unit's group), so that round uses the whole block.
+// G is the choice that minimises the rounds' length in quad pairs plus one
+// pair's worth of set-up per two rounds (a unit loads its spin's offsets and
+// products once).  Returns (G, full units, remainder units, G2).
+__device__ __forceinline__ int4 class_split(int nc, int nq, int B)
+{
+    int best = 0x7FFFFFFF;
+    int4 pick = make_int4(1, 0, 0, 1);
+    for (int G = 1; G <= nq; ++G) {
+        const int qpu = (nq + G - 1) / G;
+        const int U = nc * G, R = U / B, Ur = U - R * B;
+        int cost = R * (2 * ((qpu + 1) / 2) + 1), G2 = 1;
+        if (Ur > 0) {
+            G2 = max(1, min(qpu, B / Ur));
+            const int q2 = (qpu + G2 - 1) / G2;
+            cost += 2 * ((q2 + 1) / 2) + 1;
+        }
+        if (cost < best) {
+            best = cost;
+            pick = make_int4(G, R * B, Ur, G2);
+        }
+    }
+    return pick;
+}
 
 
 // Counter (i, y, quad, start), rounds 3..10 (0-based 2..9) from the round-2
@@ -77,6 +108,7 @@ __device__ void run_item_pm1q(const SweepLaunch &L, const SweepJob &job, int qua
     const uint32_t one = (uint32_t)(L.thr_stride > 0);
 
     for (int c = tid; c <= ncol; c += B) sm.cptr[c] = P->cptr[c];
+    for (int c = tid; c < ncol; c += B) sm.split[c] = class_split(P->cptr[c + 1] - P->cptr[c], nq, B);
     for (int x = tid; x < nq * ns; x += B) {
         const int q = x / ns, p = x - q * ns;
         const uint32_t w = p < n ? start_word(P, job, quad0 + q, p) : 0u;
@@ -123,10 +155,19 @@ __device__ void run_item_pm1q(const SweepLaunch &L, const SweepJob &job, int qua
         for (int c = 0; c < ncol; ++c) {
             const int lo = sm.cptr[c], nc = sm.cptr[c + 1] - lo;
             if (nc > 0) {
-                // units (spin k, quad group g), k fastest; group g sweeps quads g, g + G, ...
-                const int G = max(1, min(nq, B / nc));
-                for (int u = tid; u < nc * G; u += B) {
-                    const int g = u / nc, p = lo + (u - g * nc);
+                // units (spin k, quad group g), k fastest; group g sweeps quads g, g + G, ...;
+                // a remainder unit's sub-unit j sweeps every G2-th of them from the j-th
+                const int4 sp = sm.split[c];
+                const int G = sp.x, full = sp.y, Ur = sp.z, G2 = sp.w;
+                for (int u = tid; u < full + Ur * G2; u += B) {
+                    int uu = u, j = 0;
+                    if (u >= full) {
+                        const int v = u - full;
+                        j = v / Ur;
+                        uu = full + (v - j * Ur);
+                    }
+                    const int g = uu / nc, p = lo + (uu - g * nc);
+                    const int qst = u < full ? G : G * G2;
                     const uint32_t meta = __ldg(P->meta + p);
                     const int deg = (int)(meta & 0xFFFFu);
                     uint32_t o4[MAXD];
@@ -147,9 +188,9 @@ __device__ void run_item_pm1q(const SweepLaunch &L, const SweepJob &job, int qua
                     const uint32_t L0k = L0 ^ k1w;
                     const uint32_t own4 = 4u * (uint32_t)p;
                     // quads g, g + G, ... two at a time (no item reads a word another writes)
-                    for (int q = g; q < nq; q += 2 * G) {
-                        const bool two = q + G < nq;
-                        const int qq[2] = {q, two ? q + G : q};
+                    for (int q = g + j * G; q < nq; q += 2 * qst) {
+                        const bool two = q + qst < nq;
+                        const int qq[2] = {q, two ? q + qst : q};
                         uint32_t own[2], x[2], oa[2];
 #pragma unroll
                         for (int k = 0; k < 2; ++k) {
@@ -200,7 +241,7 @@ __device__ void run_item_pm1q(const SweepLaunch &L, const SweepJob &job, int qua
 }
 
 template <int B, int MAXD>
-__global__ void __launch_bounds__(B) k_sweep_pm1q(const SweepLaunch L)
+__global__ void __launch_bounds__(B, B == 512 ? (MAXD == 6 ? 2 : 1) : 1024 / B) k_sweep_pm1q(const SweepLaunch L)
 {
     __shared__ QuadSmem sm;
     extern __shared__ __align__(16) uint32_t sw_pm1q[];
