@@ -577,7 +577,7 @@ __global__ void __launch_bounds__(kBigBlock) k_reduce_slots(Slot *slots, SolveCo
 // order, couplers between free spins keep theirs, colour classes are inherited.
 constexpr int kPassCluster = 8;
 constexpr int kPassBlock = kFoldChunk;  // one spin per thread in a fold chunk
-constexpr int kFoldGather = 6;          // CSR entries of each row a thread loads at once
+constexpr int kFoldGather = 4;          // CSR entries of each row a thread loads at once
 constexpr int kIndexBatch = 4;          // fold chunks a CTA indexes after one round of loads
 // Four resident CTAs per SM (64 registers): 64 starts (512 CTAs) run in one wave.
 constexpr int kPassMinBlocks = 4;
@@ -812,7 +812,13 @@ __device__ __forceinline__ void fold_index(Slot &s, const int (&ch)[CB])
                     (long long)*reinterpret_cast<const unsigned long long *>(tab + kFoldMaxChunks * kFoldStride);
         D->row_ptr[m] = nnz2;
     }
-    int32_t *orig2 = s.orig[s.ocur ^ 1];
+    // the output arrays in locals: a store through one of them cannot change where the others are
+    int32_t *__restrict__ orig2 = s.orig[s.ocur ^ 1];
+    int32_t *__restrict__ oon = s.old_of_new;
+    uint32_t *__restrict__ npos = npos_of(s);
+    int32_t *__restrict__ dh = D->h, *__restrict__ dcolour = D->colour, *__restrict__ drow = D->row_ptr;
+    int32_t *__restrict__ dpos = D->pos_of_idx, *__restrict__ didx = D->idx_of_pos;
+    uint32_t *__restrict__ dmeta = D->meta;
 #pragma unroll
     for (int b = 0; b < CB; ++b) {
         if (!on[b] || ch[b] * kFoldChunk >= n) continue;  // uniform over the CTA
@@ -838,16 +844,16 @@ __device__ __forceinline__ void fold_index(Slot &s, const int (&ch)[CB])
         }
         const int a = s_base[b][0] + exf;
         const int pos = f[b] ? s_cptr[col] + rank : 0;
-        if (valid[b]) npos_of(s)[i] = f[b] ? (uint32_t)a | ((uint32_t)pos << 16) : ~0u;
+        if (valid[b]) npos[i] = f[b] ? (uint32_t)a | ((uint32_t)pos << 16) : ~0u;
         if (f[b]) {
-            s.old_of_new[a] = i;
+            oon[a] = i;
             orig2[a] = oi[b];
-            D->h[a] = h[b];
-            D->colour[a] = col;
-            D->row_ptr[a] = s_base[b][1] + exr;
-            D->pos_of_idx[a] = pos;
-            D->idx_of_pos[pos] = a;
-            D->meta[pos] = ((uint32_t)(h[b] & 0xFFFF) << 16) | (uint32_t)rc[b];
+            dh[a] = h[b];
+            dcolour[a] = col;
+            drow[a] = s_base[b][1] + exr;
+            dpos[a] = pos;
+            didx[pos] = a;
+            dmeta[pos] = ((uint32_t)(h[b] & 0xFFFF) << 16) | (uint32_t)rc[b];
         }
     }
     __syncthreads();  // the shared offsets are rewritten by this CTA's next chunks
@@ -856,10 +862,15 @@ __device__ __forceinline__ void fold_index(Slot &s, const int (&ch)[CB])
 template <int G>
 __device__ __forceinline__ void fold_fill(Slot &s, const int (&ch)[G])
 {
-    const uint32_t *npos = npos_of(s);
+    const uint32_t *__restrict__ npos = npos_of(s);
     const DevProb *P = s.cur;
     DevProb *D = s.buf[s.next];
     const int n = P->n, cap = P->cap_n, tid = threadIdx.x;
+    // the arrays in locals: a store through one of them cannot change where the others are
+    const int32_t *__restrict__ prow = P->row_ptr, *__restrict__ pcol = P->col, *__restrict__ pval = P->val;
+    const int32_t *__restrict__ drow = D->row_ptr;
+    int32_t *__restrict__ dcol = D->col, *__restrict__ dval = D->val;
+    uint32_t *__restrict__ dell = D->ell;
     if (ch[0] == 0 && tid == 0) {
         // the reference spin: the chunks' candidates, largest degree then lowest index
         const int32_t *tab = s.scratch + fold_table_offset(cap);
@@ -882,14 +893,14 @@ __device__ __forceinline__ void fold_fill(Slot &s, const int (&ch)[G])
         const int i = ch[g] * kFoldChunk + tid;
         const bool ok = ch[g] >= 0 && i < n;
         own[g] = ok ? npos[i] : ~0u;  // ~0: fixed
-        p0[g] = ok ? P->row_ptr[i] : 0;
-        p1[g] = ok ? P->row_ptr[i + 1] : 0;
+        p0[g] = ok ? prow[i] : 0;
+        p1[g] = ok ? prow[i + 1] : 0;
     }
 #pragma unroll
     for (int g = 0; g < G; ++g) {
         const bool free = own[g] != ~0u;  // free spins only
         if (!free) p1[g] = p0[g];
-        q[g] = free ? D->row_ptr[own[g] & 0xFFFFu] : 0;
+        q[g] = free ? drow[own[g] & 0xFFFFu] : 0;
         pos[g] = (int)(own[g] >> 16);
         d[g] = 0;
     }
@@ -905,8 +916,8 @@ __device__ __forceinline__ void fold_fill(Slot &s, const int (&ch)[G])
 #pragma unroll
             for (int e = 0; e < kFoldGather; ++e) {
                 const bool in = p0[g] + d0 + e < p1[g];
-                np[g][e] = in ? (uint32_t)P->col[p0[g] + d0 + e] : ~0u;
-                vv[g][e] = in ? P->val[p0[g] + d0 + e] : 0;
+                np[g][e] = in ? (uint32_t)pcol[p0[g] + d0 + e] : ~0u;
+                vv[g][e] = in ? pval[p0[g] + d0 + e] : 0;
             }
 #pragma unroll
         for (int g = 0; g < G; ++g)
@@ -919,9 +930,9 @@ __device__ __forceinline__ void fold_fill(Slot &s, const int (&ch)[G])
             for (int e = 0; e < kFoldGather; ++e) {
                 if (np[g][e] == ~0u) continue;
                 const uint32_t b = np[g][e] & 0xFFFFu, pp = np[g][e] >> 16;
-                D->col[q[g]] = (int32_t)b;
-                D->val[q[g]] = vv[g][e];
-                D->ell[(size_t)d[g] * cap + pos[g]] = pp | ((uint32_t)(vv[g][e] & 0xFFFF) << 16);
+                dcol[q[g]] = (int32_t)b;
+                dval[q[g]] = vv[g][e];
+                dell[(size_t)d[g] * cap + pos[g]] = pp | ((uint32_t)(vv[g][e] & 0xFFFF) << 16);
                 ++q[g];
                 ++d[g];
             }
@@ -975,17 +986,19 @@ __global__ void __cluster_dims__(kPassCluster, 1, 1) __launch_bounds__(kPassBloc
     const int64_t eb = e[rbest];
     const bool better = eb < *s.best_e;  // every CTA reads it before rank 0 may change it
     constexpr int kStride = kPassCluster * kPassBlock;
+    int8_t *__restrict__ bstate = s.best_state;
     if (better) {
         // spins fixed in earlier phases, before this phase adds its fixings to fmap
         // (four loads in flight per thread)
         const int n0 = s.n0;
+        const int8_t *__restrict__ fm = s.fmap;
         for (int o0 = rank * kPassBlock + tid; o0 < n0; o0 += 4 * kStride) {
             int8_t v[4];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) v[u] = o0 + u * kStride < n0 ? s.fmap[o0 + u * kStride] : 0;
+            for (int u = 0; u < 4; ++u) v[u] = o0 + u * kStride < n0 ? fm[o0 + u * kStride] : 0;
 #pragma unroll
             for (int u = 0; u < 4; ++u)
-                if (v[u]) s.best_state[o0 + u * kStride] = v[u];
+                if (v[u]) bstate[o0 + u * kStride] = v[u];
         }
     }
     if (rank == 0) {
@@ -1014,7 +1027,7 @@ __global__ void __cluster_dims__(kPassCluster, 1, 1) __launch_bounds__(kPassBloc
             }
 #pragma unroll
             for (int u = 0; u < 4; ++u)
-                if (o[u] >= 0) s.best_state[o[u]] = ((w[u] >> ((a0 + u * kStride) & 31)) & 1u) ? 1 : -1;
+                if (o[u] >= 0) bstate[o[u]] = ((w[u] >> ((a0 + u * kStride) & 31)) & 1u) ? 1 : -1;
         }
     }
     if (mode == kSolving) {

@@ -151,10 +151,13 @@ __device__ __forceinline__ void sweep_once(Pm1Smem<B, NSLOT> &sm, unsigned long 
             for (int e = (int)threadIdx.x + 1; e <= bias; e += B)
                 nrow[row_slot(bias + e)] = (1ull << 32) - (unsigned long long)next_src[2 * e];
         }
-    } else if (next_src && (int)threadIdx.x < bias) {
-        const int e = (int)threadIdx.x + 1;
-        sm.row[PAR ^ 1][bias + e] = (1ull << 32) - (unsigned long long)next_src[2 * e];
     }
+    // byte lanes: the next row's entry is loaded now and stored after the slots
+    // (with at most two slots, so that a short sweep does not wait for the load;
+    // with more, at once, which keeps a register free for the slots)
+    const bool stage = !SCALED && next_src && (int)threadIdx.x < bias;
+    const uint32_t nthr = stage ? __ldg(next_src + 2 * ((int)threadIdx.x + 1)) : 0u;
+    if (NSLOT > 2 && stage) sm.row[PAR ^ 1][bias + (int)threadIdx.x + 1] = (1ull << 32) - (unsigned long long)nthr;
     const char *rowb = SCALED ? reinterpret_cast<const char *>(drow + PAR * row_len(bias))
                               : reinterpret_cast<const char *>(sm.row[PAR]);
 #pragma unroll
@@ -215,6 +218,7 @@ __device__ __forceinline__ void sweep_once(Pm1Smem<B, NSLOT> &sm, unsigned long 
             sts_b(sm.sw, s[j].own + kInv, inv);
         }
     }
+    if (NSLOT <= 2 && stage) sm.row[PAR ^ 1][bias + (int)threadIdx.x + 1] = (1ull << 32) - (unsigned long long)nthr;
     __syncthreads();
 }
 
