@@ -121,6 +121,7 @@ struct Pm1Smem {
     uint32_t sw[2 * KW + 1];
     unsigned long long row[2][kRowE];
     int cptr[kMaxColours + 1];
+    int late;  // the item's problem is small: its sweeps are short
 };
 
 // SCALED acceptance rows: row length (2 bias + 1 rounded up to 16 entries) and
@@ -152,12 +153,14 @@ __device__ __forceinline__ void sweep_once(Pm1Smem<B, NSLOT> &sm, unsigned long 
                 nrow[row_slot(bias + e)] = (1ull << 32) - (unsigned long long)next_src[2 * e];
         }
     }
-    // byte lanes: the next row's entry is loaded now and stored after the slots
-    // (with at most two slots, so that a short sweep does not wait for the load;
-    // with more, at once, which keeps a register free for the slots)
+    // byte lanes: the next row's entry is loaded now; with at most two slots and a
+    // small problem it is stored after the slots, so that a short sweep does not
+    // wait for the load, otherwise at once (which keeps a register free for the
+    // slots of a long sweep)
     const bool stage = !SCALED && next_src && (int)threadIdx.x < bias;
+    const bool late = NSLOT <= 2 && sm.late;
     const uint32_t nthr = stage ? __ldg(next_src + 2 * ((int)threadIdx.x + 1)) : 0u;
-    if (NSLOT > 2 && stage) sm.row[PAR ^ 1][bias + (int)threadIdx.x + 1] = (1ull << 32) - (unsigned long long)nthr;
+    if (!late && stage) sm.row[PAR ^ 1][bias + (int)threadIdx.x + 1] = (1ull << 32) - (unsigned long long)nthr;
     const char *rowb = SCALED ? reinterpret_cast<const char *>(drow + PAR * row_len(bias))
                               : reinterpret_cast<const char *>(sm.row[PAR]);
 #pragma unroll
@@ -218,7 +221,7 @@ __device__ __forceinline__ void sweep_once(Pm1Smem<B, NSLOT> &sm, unsigned long 
             sts_b(sm.sw, s[j].own + kInv, inv);
         }
     }
-    if (NSLOT <= 2 && stage) sm.row[PAR ^ 1][bias + (int)threadIdx.x + 1] = (1ull << 32) - (unsigned long long)nthr;
+    if (late && stage) sm.row[PAR ^ 1][bias + (int)threadIdx.x + 1] = (1ull << 32) - (unsigned long long)nthr;
     __syncthreads();
 }
 
@@ -264,6 +267,7 @@ __device__ void run_item_pm1(const SweepLaunch &L, const SweepJob &job, int quad
     const uint32_t one = (uint32_t)(L.thr_stride > 0);
 
     for (int c = tid; c <= ncol; c += B) sm.cptr[c] = P->cptr[c];
+    if (tid == 0) sm.late = P->n <= 256;
     init_spins(P, job, quad0, nq, sm.sw, sm.sw + KW);
     if (tid == 0) {
         sm.sw[KW - 1] = 0u;
