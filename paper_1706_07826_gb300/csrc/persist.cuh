@@ -252,54 +252,6 @@ __device__ __forceinline__ void elite_fast(const int64_t *energies, int S, int k
     __syncthreads();
 }
 
-// Persistence count and fixing rule for spins [i0, i0 + blockDim.x) of one
-// sample set.  With canon, each elite row is multiplied by its value at
-// prob->rho.  fmap/orig (optional): also record fixings in original order.
-__device__ __forceinline__ void count_core(const DevProb *P, const uint32_t *spins, int W,
-                                           const int32_t *elite, int k, int canon, int fix_num,
-                                           int fix_den, int32_t *counts, int8_t *fixed,
-                                           int32_t *nfixed, int8_t *fmap, const int32_t *orig)
-{
-    constexpr int kChunk = 512;
-    __shared__ int s_row[kChunk];
-    __shared__ unsigned s_flip[kChunk];
-    const int n = P->n;
-    const int rho = P->rho;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int word = i >> 5;
-    const unsigned bit = (unsigned)(i & 31);
-    int cnt = 0;
-    for (int c0 = 0; c0 < k; c0 += kChunk) {
-        const int m = min(kChunk, k - c0);
-        for (int q = threadIdx.x; q < m; q += blockDim.x) {
-            const int r = elite[c0 + q];
-            s_row[q] = r;
-            unsigned f = 0;
-            if (canon && rho >= 0) {
-                const unsigned b = (spins[(size_t)r * W + (rho >> 5)] >> (rho & 31)) & 1u;
-                f = b ? 0u : 0xFFFFFFFFu;
-            }
-            s_flip[q] = f;
-        }
-        __syncthreads();
-        if (i < n)
-            for (int q = 0; q < m; ++q)
-                cnt += (int)(((spins[(size_t)s_row[q] * W + word] ^ s_flip[q]) >> bit) & 1u);
-        __syncthreads();
-    }
-    int8_t v = 0;
-    if (i < n) {
-        const long long diff = 2ll * cnt - k;
-        if (diff > 0 && (long long)fix_den * diff >= (long long)fix_num * k) v = 1;
-        if (diff < 0 && (long long)fix_den * (-diff) >= (long long)fix_num * k) v = -1;
-        if (counts) counts[i] = cnt;
-        fixed[i] = v;
-        if (v && fmap) fmap[orig[i]] = v;
-    }
-    const unsigned ball = __ballot_sync(0xFFFFFFFFu, v != 0);
-    if ((threadIdx.x & 31) == 0 && ball) atomicAdd(nfixed, __popc(ball));
-}
-
 // Persistence count and fixing rule, bit-sliced: one CTA of kCountBlock
 // threads covers 32 words (1024 spins, chunk `chunk`) of the sample rows.
 // Lane l of every warp owns word 32 chunk + l; the k elite rows are split over the 8
@@ -308,7 +260,10 @@ __device__ __forceinline__ void count_core(const DevProb *P, const uint32_t *spi
 // running count of every spin of the word (a vertical counter, two logic
 // operations per plane and row).  The warps' counters are then summed by a
 // bit-sliced ripple adder and each spin's count read off its planes.
-// Results as count_core.  NB: planes per warp (2^NB > rows per warp).
+// counts[i] (if not null) is the number of elite rows with s_i = +1 (after
+// the canonicalisation), fixed[i] the fixing rule's value (+1, -1 or 0),
+// *nfixed grows by the spins fixed, and with fmap/orig the fixings are also
+// recorded by original index.  NB: planes per warp (2^NB > rows per warp).
 constexpr int kCountWarps = kCountBlock / 32;
 constexpr int kCountPlanes = 12;  // 2^12 > 16384 / kCountWarps rows per warp
 // Shared memory of one count chunk (callers place it, so the multi-start pass
