@@ -9,6 +9,9 @@
   when p = 0), multiplied by the total sample size of one start;
 - the figures report the mean over 1000 bootstrap resamples of the problems of
   the median of the measurable R99 values (Sec. III.C).
+
+Also the split of a start's total sample between the steps of Alg. 2 that
+the paper's benchmarking used (appendix, Table II).
 """
 import math
 
@@ -67,3 +70,18 @@ def bootstrap_median_r99(r99s, resamples=1000, seed=0):
         if m:
             meds.append(float(np.median(m)))
     return float(np.mean(meds)) if meds else None
+
+
+def sample_split(total, zero_bias):
+    """(correlation, fixing, solving) sample sizes of one start whose total
+    sample is `total` (appendix, Table II): for problems with bias, half for
+    the SPVAR fixing step and half for solving; for zero-bias problems 40 % for
+    the correlation pre-fixing step and the rest divided equally between
+    fixing and solving.  Where the shares are not whole, the correlation step
+    takes 40 % rounded down and the solving step the odd sample left over."""
+    if total < 0:
+        raise ValueError("total sample size must be >= 0")
+    corr = (2 * total) // 5 if zero_bias else 0
+    rest = total - corr
+    fixing = rest // 2
+    return corr, fixing, rest - fixing

@@ -43,3 +43,37 @@ def test_bootstrap_median():
     g = np.random.default_rng(5)
     big = list(g.integers(1, 1000, 401).astype(float))
     assert abs(M.bootstrap_median_r99(big, resamples=300) - np.median(big)) < 0.15 * np.median(big)
+
+
+def _table2():
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "table2_parameters.txt")
+    rows = []
+    for line in open(path):
+        if line.startswith("#") or not line.strip():
+            continue
+        name, elite, corr_elite, starts, total, sweeps = [c.strip() for c in line.split("|")]
+        lo, _, hi = total.partition("-")
+        rows.append(dict(name=name, elite=float(elite), corr_elite=None if corr_elite == "-" else float(corr_elite),
+                         starts=int(starts), totals=sorted({int(lo), int(hi or lo)}),
+                         sweeps=[int(x) for x in sweeps.split(",")]))
+    return rows
+
+
+def test_sample_split_of_the_paper_parameters():
+    """The appendix's split of Table II's total sample sizes: half and half
+    with bias; 40 % for the correlation step and the rest halved without."""
+    rows = _table2()
+    assert len(rows) == 6
+    seen = set()
+    for r in rows:
+        for total in r["totals"]:
+            c, f, s = M.sample_split(total, zero_bias=False)
+            assert (c, f, s) == (0, total // 2, total - total // 2) and f == s
+            c, f, s = M.sample_split(total, zero_bias=True)
+            assert c + f + s == total and abs(c - 0.4 * total) < 1 and f == s
+            seen.add((total, c, f))
+    # the sizes the paper's sets used: 100, 500 and 1000 samples per start
+    assert (500, 200, 150) in seen and (1000, 400, 300) in seen and (100, 40, 30) in seen
+    assert M.sample_split(7, True) == (2, 2, 3) and M.sample_split(7, False) == (0, 3, 4)
+
